@@ -1,0 +1,284 @@
+"""Plain FP64 CPU oracle of the CONCORD/PseudoNet proximal-gradient method.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The GPU library and
+its Python binding never import, call or execute anything here, and this
+package shares no code with them; the two meet only through the seeded arrays
+of ``workloads``.
+
+What it computes (HP-CONCORD, arXiv:1710.10769):
+
+* ``gram``            S = X^T X / n                       (Alg. 1 step 2, Alg. 2 step 2)
+* ``soft_threshold``  the elementwise operator of eq. (2)
+* ``prox``            eq. (2) applied to the off-diagonal entries only
+* ``gradient``        G = -diag(1/w_ii) + (W + W^T)/2 + lam2*Omega, W = Omega S
+                                                            (Alg. 1 step 4, Alg. 2 steps 5-6)
+* ``smooth``          g(Omega) = -sum log w_ii + tr(W Omega)/2 + lam2/2 ||Omega||_F^2
+                                                            (Alg. 2 step 7, scaled as below)
+* ``iterate``/``solve``  Alg. 1 / Alg. 2: backtracking over tau = 1, 1/2, 1/4, ...
+                      with a fresh W+ = Omega+ S per trial and the sufficient-
+                      decrease test of Alg. 1 step 9 / Alg. 2 step 12
+* ``solve_obs``       Alg. 3 (Y = Omega X^T, Z = Y X / n, ||Y||^2 / n)
+* ``*_entries``       single entries of S and G formed straight from X, for
+                      sampled checks at sizes where the dense oracle is too slow
+
+Readings of the paper (where it is silent, ambiguous or garbled):
+
+* Scaling (eq. 1 vs Alg. 1 step 4): the smooth part is
+  f = -sum log w_ii + tr(Omega S Omega)/2 + lam2/2 ||Omega||_F^2, whose gradient
+  is exactly the G of Alg. 1 step 4; the line search uses this f.
+* The l1 term counts every off-diagonal entry (both triangles); each entry is
+  thresholded at tau*lam1.
+* The diagonal is not thresholded (the penalty is on Omega_X only).
+* A trial with any w+_ii <= 0 fails (the log needs a positive diagonal) and tau halves.
+* tau restarts at 1 every outer iteration, shrinks by 1/2, at most 60 halvings.
+* Ties in eq. (2): |z| <= alpha maps to 0.
+* Stopping: ||Omega+ - Omega||_F / ||Omega||_F < eps.
+* Obs scaling: Y = Omega X^T unscaled, Z = Y X / n, tr(Omega S Omega) = ||Y||_F^2 / n.
+* S is not centred and is divided by n.
+
+Numerical floor.  The test of Alg. 1 step 9 compares two O(|g|) numbers whose
+difference is O(||Delta||^2); in FP64 it decides reliably while
+||Delta||_F / ||Omega||_F stays above ~1e-8.  Parity references therefore stop
+at eps = 1e-9 at most, and a line search that runs out of halvings after the
+relative change has already dropped below 1e-8 is reported as converged
+(``status == "floor"``) rather than as a failure.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+
+# ----------------------------------------------------------------- building blocks
+
+def gram(X) -> np.ndarray:
+    """S = X^T X / n in FP64 (Alg. 1 step 2); X is n x p, rows are observations."""
+    X = np.asarray(X, dtype=np.float64)
+    return (X.T @ X) / X.shape[0]
+
+
+def soft_threshold(Z, alpha):
+    """Eq. (2): z - alpha if z > alpha, z + alpha if z < -alpha, otherwise 0."""
+    Z = np.asarray(Z, dtype=np.float64)
+    return np.where(Z > alpha, Z - alpha, np.where(Z < -alpha, Z + alpha, 0.0))
+
+
+def prox(Z, alpha):
+    """Proximal map of alpha*||Z_X||_1: eq. (2) off the diagonal, diagonal kept."""
+    out = soft_threshold(Z, alpha)
+    np.fill_diagonal(out, np.diag(Z))
+    return out
+
+
+def times_S(Omega, S):
+    """W = Omega S, the sparse-dense product of Alg. 2 steps 3 and 10."""
+    return np.asarray(sp.csr_matrix(Omega) @ S)
+
+
+def gradient(Omega, W, lam2):
+    """G = -(Omega_D)^-1 + (W^T + W)/2 + lam2*Omega (Alg. 2 step 6, W = Omega S)."""
+    G = 0.5 * (W.T + W) + lam2 * Omega
+    G[np.diag_indices_from(G)] -= 1.0 / np.diag(Omega)
+    return G
+
+
+def smooth(Omega, W, lam2):
+    """g(Omega) = -sum_i log w_ii + tr(W Omega)/2 + lam2/2 ||Omega||_F^2 (Alg. 2 step 7).
+
+    Returns +inf when a diagonal entry is not positive (the log is undefined).
+    """
+    d = np.diag(Omega)
+    if np.any(d <= 0.0):
+        return np.inf
+    tr_wo = np.sum(W * Omega.T)          # tr(W Omega) = sum_ij W_ij Omega_ji
+    return -np.sum(np.log(d)) + 0.5 * tr_wo + 0.5 * lam2 * np.sum(Omega * Omega)
+
+
+def penalty(Omega, lam1):
+    """lam1 * sum_{i != j} |w_ij| (both triangles)."""
+    a = np.abs(Omega)
+    return lam1 * (a.sum() - np.trace(a))
+
+
+def objective(S, Omega, lam1, lam2):
+    """F(Omega) = g(Omega) + lam1 ||Omega_X||_1."""
+    return smooth(Omega, times_S(Omega, S), lam2) + penalty(Omega, lam1)
+
+
+# ----------------------------------------------------------------- Alg. 1 / Alg. 2
+
+@dataclasses.dataclass
+class Step:
+    omega: np.ndarray
+    W: np.ndarray
+    tau: float
+    trials: int
+    accepted: bool
+    G: np.ndarray
+    g: float
+
+
+def iterate(S, Omega, W, lam1, lam2, tau0=1.0, shrink=0.5, max_halvings=60) -> Step:
+    """One outer iteration of Alg. 2 (steps 5-12) from the iterate Omega with W = Omega S."""
+    G = gradient(Omega, W, lam2)
+    g = smooth(Omega, W, lam2)
+    tau = tau0
+    for h in range(max_halvings + 1):
+        Op = prox(Omega - tau * G, tau * lam1)             # step 9
+        if np.all(np.diag(Op) > 0.0):
+            Wp = times_S(Op, S)                             # step 10
+            gp = smooth(Op, Wp, lam2)                       # step 11
+            D = Op - Omega
+            # step 12: g(O+) <= g(O) - tr((O - O+)^T G) + ||O - O+||^2 / (2 tau)
+            rhs = g - np.sum((Omega - Op) * G) + np.sum(D * D) / (2.0 * tau)
+            if gp <= rhs:
+                return Step(Op, Wp, tau, h + 1, True, G, g)
+        tau *= shrink
+    return Step(Omega, W, tau, max_halvings + 1, False, G, g)
+
+
+@dataclasses.dataclass
+class Result:
+    omega: np.ndarray
+    iterations: int
+    trials: list
+    taus: list
+    F: list                 # F(Omega^k) for k = 0..iterations
+    rel_change: float
+    status: str             # "converged" | "floor" | "max_iter" | "ls_fail"
+
+
+def solve(S, lam1, lam2, eps=1e-6, max_iter=1000, omega0=None, tau0=1.0, shrink=0.5,
+          max_halvings=60) -> Result:
+    """Alg. 2 (the Cov variant of Alg. 1): Omega^0 = I, iterate until the relative change < eps."""
+    S = np.asarray(S, dtype=np.float64)
+    p = S.shape[0]
+    Omega = np.eye(p) if omega0 is None else np.array(omega0, dtype=np.float64)
+    W = times_S(Omega, S)                                   # step 3
+    F = [smooth(Omega, W, lam2) + penalty(Omega, lam1)]
+    trials, taus = [], []
+    rel = np.inf
+    status = "max_iter"
+    for _ in range(max_iter):
+        st = iterate(S, Omega, W, lam1, lam2, tau0, shrink, max_halvings)
+        if not st.accepted:
+            status = "floor" if rel < 1e-8 else "ls_fail"
+            break
+        rel = np.linalg.norm(st.omega - Omega) / np.linalg.norm(Omega)
+        Omega, W = st.omega, st.W
+        trials.append(st.trials)
+        taus.append(st.tau)
+        F.append(smooth(Omega, W, lam2) + penalty(Omega, lam1))
+        if rel < eps:
+            status = "converged"
+            break
+    return Result(Omega, len(trials), trials, taus, F, float(rel), status)
+
+
+# ----------------------------------------------------------------- Alg. 3 (Obs)
+
+def solve_obs(X, lam1, lam2, eps=1e-6, max_iter=1000, tau0=1.0, shrink=0.5,
+              max_halvings=60) -> Result:
+    """Alg. 3: never forms S; Y = Omega X^T, Z = Y X / n, tr(Omega S Omega) = ||Y||^2 / n."""
+    X = np.asarray(X, dtype=np.float64)
+    n, p = X.shape
+    Xt = X.T
+
+    def g_of(Om, Y):
+        d = np.diag(Om)
+        if np.any(d <= 0.0):
+            return np.inf
+        return -np.sum(np.log(d)) + 0.5 * np.sum(Y * Y) / n + 0.5 * lam2 * np.sum(Om * Om)
+
+    Omega = np.eye(p)
+    Y = np.asarray(sp.csr_matrix(Omega) @ Xt)               # step 2
+    F = [g_of(Omega, Y) + penalty(Omega, lam1)]
+    trials, taus = [], []
+    rel = np.inf
+    status = "max_iter"
+    for _ in range(max_iter):
+        Z = (Y @ X) / n                                     # step 4
+        G = gradient(Omega, Z, lam2)                        # steps 5-6
+        g = g_of(Omega, Y)                                  # step 7
+        tau, accepted = tau0, False
+        for h in range(max_halvings + 1):
+            Op = prox(Omega - tau * G, tau * lam1)          # step 9
+            if np.all(np.diag(Op) > 0.0):
+                Yp = np.asarray(sp.csr_matrix(Op) @ Xt)     # step 10
+                gp = g_of(Op, Yp)                           # step 11
+                D = Op - Omega
+                if gp <= g - np.sum((Omega - Op) * G) + np.sum(D * D) / (2.0 * tau):
+                    accepted = True
+                    break
+            tau *= shrink
+        if not accepted:
+            status = "floor" if rel < 1e-8 else "ls_fail"
+            break
+        rel = np.linalg.norm(Op - Omega) / np.linalg.norm(Omega)
+        Omega, Y = Op, Yp
+        trials.append(h + 1)
+        taus.append(tau)
+        F.append(g_of(Omega, Y) + penalty(Omega, lam1))
+        if rel < eps:
+            status = "converged"
+            break
+    return Result(Omega, len(trials), trials, taus, F, float(rel), status)
+
+
+# ----------------------------------------------------------------- sampled entries
+
+def _columns(X, idx):
+    return np.asarray(X[:, idx], dtype=np.float64)
+
+
+def gram_entries(X, rows, cols) -> np.ndarray:
+    """S_ij = sum_k X_ki X_kj / n for the listed pairs, in FP64, straight from X."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    n = X.shape[0]
+    uniq, inv = np.unique(np.concatenate([rows, cols]), return_inverse=True)
+    C = _columns(X, uniq)
+    a = C[:, inv[: rows.size]]
+    b = C[:, inv[rows.size:]]
+    return np.einsum("ki,ki->i", a, b) / n
+
+
+def gradient_entries(X, omega_csr: sp.csr_matrix, lam2, rows, cols) -> np.ndarray:
+    """G_ij of Alg. 1 step 4 at the listed pairs for a sparse symmetric Omega, from X.
+
+    W_ij = sum_k w_ik S_kj and W_ji = sum_k w_jk S_ki with every S entry formed
+    from X in FP64.
+    """
+    om = sp.csr_matrix(omega_csr, dtype=np.float64)
+    om.sort_indices()
+    n = X.shape[0]
+    out = np.empty(len(rows))
+    for t, (i, j) in enumerate(zip(rows, cols)):
+        i, j = int(i), int(j)
+        ki = om.indices[om.indptr[i]:om.indptr[i + 1]]
+        vi = om.data[om.indptr[i]:om.indptr[i + 1]]
+        kj = om.indices[om.indptr[j]:om.indptr[j + 1]]
+        vj = om.data[om.indptr[j]:om.indptr[j + 1]]
+        xi = _columns(X, [i])[:, 0]
+        xj = _columns(X, [j])[:, 0]
+        w_ij = vi @ ((_columns(X, ki).T @ xj) / n) if ki.size else 0.0
+        w_ji = vj @ ((_columns(X, kj).T @ xi) / n) if kj.size else 0.0
+        g = 0.5 * (w_ij + w_ji) + lam2 * om[i, j]
+        if i == j:
+            g -= 1.0 / om[i, i]
+        out[t] = g
+    return out
+
+
+def smooth_sparse_from_S(S, omega_csr: sp.csr_matrix, lam2) -> float:
+    """g(Omega) for a sparse symmetric Omega and a dense S (row sums of w_i^T S w_i)."""
+    om = sp.csr_matrix(omega_csr, dtype=np.float64)
+    d = om.diagonal()
+    if np.any(d <= 0.0):
+        return np.inf
+    W = om @ S
+    tr = float(np.sum(om.multiply(W)))
+    return -float(np.sum(np.log(d))) + 0.5 * tr + 0.5 * lam2 * float(om.multiply(om).sum())
