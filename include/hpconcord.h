@@ -1,0 +1,191 @@
+/*
+ * hpconcord.h -- C ABI of a single-GPU (GB300, sm_103a) implementation of the
+ * HP-CONCORD proximal-gradient solver for the CONCORD/PseudoNet sparse inverse
+ * covariance estimator (Koanantakool et al., arXiv:1710.10769).
+ *
+ * Problem (Section 2, eq. 1, with the gradient of Alg. 1 step 4): given the
+ * observations X (n x p, one observation per row) and lambda1, lambda2 >= 0,
+ *
+ *   minimise  f(Omega) + lambda1 * sum_{i != j} |w_ij|,
+ *   f(Omega) = -sum_i log w_ii + tr(Omega S Omega)/2 + lambda2/2 ||Omega||_F^2,
+ *   S = X^T X / n   (no centring),
+ *
+ * whose smooth-part gradient is G = -diag(1/w_ii) + (S Omega + Omega S)/2 +
+ * lambda2 Omega (Alg. 1 step 4).  The solver is Alg. 1: Omega^0 = I; each
+ * iteration backtracks over tau = 1, 1/2, 1/4, ... with the soft-threshold
+ * prox of eq. (2) applied to the off-diagonal entries, and accepts the first tau
+ * passing the sufficient-decrease test of Alg. 1 step 9; it stops when
+ * ||Omega^{k+1} - Omega^k||_F / ||Omega^k||_F < eps.  Cov (Alg. 2) forms S once;
+ * Obs (Alg. 3) works from X directly.
+ *
+ * Conventions for every call:
+ *  - Dense matrices are row-major.  Pointers are device pointers unless the
+ *    argument or option says "host".  The caller owns every buffer it passes;
+ *    the library copies what it keeps, so inputs may be freed after the call.
+ *  - Work is ordered on the CUDA stream given to hpc_create (NULL = legacy
+ *    default stream).  Calls return after the work they enqueue has finished
+ *    on that stream, except where stated.
+ *  - Every call returns an int status (HPC_OK = 0).  Negative values are
+ *    errors; the handle stays usable after HPC_ERR_ARG, HPC_ERR_CAPACITY and
+ *    solver errors, and must be destroyed after HPC_ERR_CUDA.
+ *  - A handle may be used by one host thread at a time.
+ *  - The sparse iterate is symmetric and stored in CSR with both triangles and
+ *    the diagonal, columns ascending within each row.
+ */
+#ifndef HPCONCORD_H
+#define HPCONCORD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define HPC_OK                   0
+#define HPC_NOT_CONVERGED        1   /* max_iter reached; the iterate is valid            */
+#define HPC_ERR_ARG             -1   /* bad argument: lambda < 0, eps <= 0, n/p < 1, NULL */
+#define HPC_ERR_OOM             -2   /* device allocation failed                          */
+#define HPC_ERR_CAPACITY        -3   /* candidate/iterate capacity exceeded (max_capacity) */
+#define HPC_ERR_NONPOS_DIAG     -4   /* a supplied iterate has a diagonal entry <= 0      */
+#define HPC_ERR_NAN             -5   /* NaN/Inf met in the gradient or the objective      */
+#define HPC_ERR_LS_FAIL         -6   /* no step passed the test within max_halvings       */
+#define HPC_ERR_CUDA            -7   /* a CUDA runtime call failed (hpc_last_error())     */
+#define HPC_ERR_NOT_IMPLEMENTED -8   /* combination of options not built                  */
+#define HPC_ERR_DEVICE_TIMEOUT  -9   /* a bounded device-side wait gave up                */
+
+/* ---------------------------------------------------------------- enums */
+typedef struct hpc_ctx* hpc_handle;         /* opaque, owned by the library */
+
+typedef enum { HPC_COV = 0, HPC_OBS = 1 } hpc_variant;          /* Alg. 2 / Alg. 3 */
+
+typedef enum { HPC_F32 = 0, HPC_F64 = 1, HPC_BF16 = 2 } hpc_dtype;
+
+/* Arithmetic of the dense products S = X^T X / n (Alg. 2 step 2) and
+ * Z = Y X / n (Alg. 3 step 4).  Everything else follows value_dtype. */
+typedef enum {
+    HPC_PREC_AUTO   = -1,  /* FP64 for FP64 iterates, BF16X3 otherwise            */
+    HPC_PREC_FP64   = 0,   /* SIMT FP64 fused multiply-adds                        */
+    HPC_PREC_FP32   = 1,   /* SIMT FP32 fused multiply-adds ("plain FP32")         */
+    HPC_PREC_BF16X3 = 2,   /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo +
+                              lo*hi accumulated in FP32; one term when X is BF16  */
+    HPC_PREC_TF32   = 3    /* tensor cores, TF32 inputs, FP32 accumulation        */
+} hpc_precision;
+
+/* ---------------------------------------------------------------- options / stats */
+typedef struct {
+    double  eps;            /* stopping tolerance on ||dOmega||_F/||Omega||_F (1e-6)   */
+    int64_t max_iter;       /* outer iterations per hpc_solve (1000)                   */
+    int32_t max_halvings;   /* tau = 2^-h, h = 0..max_halvings (60)                    */
+    int32_t precision;      /* hpc_precision (HPC_PREC_AUTO)                           */
+    int32_t value_dtype;    /* HPC_F32 (default) or HPC_F64: S, Omega, G arithmetic    */
+    int32_t ls_window;      /* tau values tested per line-search launch, 1..16 (8)     */
+    int64_t capacity;       /* initial candidate capacity in entries (0 = 32 p)        */
+    int64_t max_capacity;   /* growth limit in entries (0 = p*p)                       */
+    int32_t x_on_host;      /* X passed to hpc_create / hpc_load_x is a host pointer   */
+    int32_t timing;         /* record CUDA events per phase into hpc_stats (1)         */
+} hpc_options;
+
+typedef struct {
+    int64_t iterations;       /* outer iterations done by the last call                 */
+    int64_t ls_trials;        /* tau values tried (the paper's t summed over iterations) */
+    int64_t nnz;              /* entries of the current iterate (both triangles + diag)  */
+    int32_t status;           /* same as the call's return value                         */
+    int32_t accepted_halvings;/* h of the last accepted tau = 2^-h                       */
+    double  f;                /* smooth part f(Omega^k) at the last gradient pass (FP64) */
+    double  F;                /* f + lambda1 * sum_{i!=j} |w_ij| at that iterate          */
+    double  rel_change;       /* last ||Omega^{k+1}-Omega^k||_F / ||Omega^k||_F          */
+    double  ms_total;         /* device time of the call                                 */
+    double  ms_gram;          /* device time of the dense product that formed S (load)   */
+    double  ms_grad_pass;     /* device time in the gradient-screening pass (Cov SpMM)   */
+    int64_t grad_pass_launches;
+    int64_t kernel_launches;  /* kernels this library launched during the call           */
+    int64_t capacity_regrows; /* times the candidate buffers grew                        */
+    int64_t candidates;       /* candidate entries of the last gradient pass             */
+} hpc_stats;
+
+/* Fill *opt with the defaults listed above. */
+void hpc_default_options(hpc_options* opt);
+
+/* Human-readable text for a status code (static storage). */
+const char* hpc_status_string(int status);
+
+/* Text of the last CUDA error seen on this thread ("" if none). */
+const char* hpc_last_error(void);
+
+/* ---------------------------------------------------------------- solver handle */
+
+/* Create a solver for X (n x p, dtype xdt, row-major; host pointer when
+ * opt->x_on_host) with tuning parameters lambda1, lambda2 >= 0.
+ * Cov: computes S = X^T X / n now (Alg. 2 step 2).  Obs: keeps X^T.
+ * The iterate starts at Omega = I (Alg. 1 step 1).  cuda_stream is a
+ * cudaStream_t (NULL = default stream).  X may be NULL: then call hpc_load_x
+ * before solving.  Errors: HPC_ERR_ARG (n,p < 1; lambda < 0; eps <= 0; bad
+ * enum), HPC_ERR_OOM, HPC_ERR_CUDA, HPC_ERR_NOT_IMPLEMENTED. */
+int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t p,
+               double lambda1, double lambda2, hpc_variant variant,
+               const hpc_options* opt, void* cuda_stream);
+
+/* Replace the data by a new X of the same n, p (host pointer if x_on_host != 0),
+ * recompute S (Cov) or X^T (Obs) and reset the iterate to I.  This is the whole
+ * set-up cost of a solve: a time-to-converge is hpc_load_x + hpc_solve. */
+int hpc_load_x(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host);
+
+/* Run Alg. 1 from the current iterate until the stopping rule holds (HPC_OK),
+ * max_iter is reached (HPC_NOT_CONVERGED) or an error occurs.  stats may be NULL. */
+int hpc_solve(hpc_handle h, hpc_stats* stats);
+
+/* Run exactly k outer iterations from the current iterate, ignoring the stopping
+ * rule (for tracing trajectories).  stats may be NULL. */
+int hpc_iterate(hpc_handle h, int64_t k, hpc_stats* stats);
+
+/* Copy the current iterate out in CSR.  Call with row_ptr == NULL to query:
+ * *nnz_inout receives the entry count.  Otherwise *nnz_inout is the capacity of
+ * col/val on entry and the count on return; row_ptr has p+1 entries.  val has
+ * dtype vdt (HPC_F32 or HPC_F64).  on_device != 0: all three are device
+ * pointers; else host pointers.  HPC_ERR_CAPACITY if the arrays are too short. */
+int hpc_get_omega(hpc_handle h, int64_t* nnz_inout, int64_t* row_ptr, int32_t* col,
+                  void* val, hpc_dtype vdt, int on_device);
+
+/* Set the iterate (warm start / resume) from a symmetric CSR with a positive
+ * diagonal present in every row, columns ascending.  HPC_ERR_NONPOS_DIAG if a
+ * diagonal entry is missing or <= 0; HPC_ERR_ARG if not sorted or out of range. */
+int hpc_set_omega(hpc_handle h, int64_t nnz, const int64_t* row_ptr, const int32_t* col,
+                  const void* val, hpc_dtype vdt, int on_device);
+
+/* Change lambda1, lambda2 (>= 0) keeping S and the current iterate (warm start). */
+int hpc_set_lambda(hpc_handle h, double lambda1, double lambda2);
+
+/* Read m entries S_{rows[t], cols[t]} of the Cov sample covariance into out
+ * (FP64, host arrays).  For checking the Gram at sizes where S is too large to
+ * copy.  HPC_ERR_ARG for an index outside [0, p) or for the Obs variant. */
+int hpc_get_s_entries(hpc_handle h, int64_t m, const int64_t* rows, const int64_t* cols,
+                      double* out);
+
+/* Copy out the screened gradient of the last gradient pass: every entry (i, j)
+ * that is in the support of the iterate, on the diagonal, or has |G_ij| >
+ * lambda1 -- the only entries any prox step can make nonzero (eq. 2) -- with
+ * the iterate value w_ij and G_ij (Alg. 1 step 4), as host FP64/int64 arrays.
+ * Query with rows == NULL (count into *m_inout).  Entries outside this set
+ * satisfy w_ij = 0 and |G_ij| <= lambda1. */
+int hpc_get_candidates(hpc_handle h, int64_t* m_inout, int64_t* rows, int64_t* cols,
+                       double* omega, double* grad);
+
+/* Free the handle and all device memory it owns.  NULL is accepted. */
+int hpc_destroy(hpc_handle h);
+
+/* ---------------------------------------------------------------- stateless products */
+
+/* S = X^T X / n (Alg. 2 step 2) for device X (n x p, dtype xdt, row-major)
+ * into device S (p x lds, dtype sdt = HPC_F32 or HPC_F64, lds >= p), both
+ * triangles written, S bitwise symmetric.  precision as hpc_precision
+ * (HPC_PREC_FP64 needs sdt = HPC_F64).  Enqueued on stream; returns without
+ * synchronising.  Allocates scratch for the tensor-core modes. */
+int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dtype sdt,
+             int64_t lds, int precision, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPCONCORD_H */

@@ -1,0 +1,273 @@
+"""Python binding of the GB300 HP-CONCORD library (``libhpconcord.so``).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels behind the C ABI of ``include/hpconcord.h``.  Functions keep the C
+names without the ``hpc_`` prefix.  Device arrays are torch CUDA tensors (used
+for device memory and streams); host arrays are numpy arrays.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+OK, NOT_CONVERGED = 0, 1
+ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_NONPOS_DIAG, ERR_NAN, ERR_LS_FAIL, ERR_CUDA, ERR_NOT_IMPLEMENTED, \
+    ERR_DEVICE_TIMEOUT = -1, -2, -3, -4, -5, -6, -7, -8, -9
+COV, OBS = 0, 1
+F32, F64, BF16 = 0, 1, 2
+PREC_AUTO, PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_TF32 = -1, 0, 1, 2, 3
+
+
+class Options(C.Structure):
+    _fields_ = [("eps", C.c_double), ("max_iter", C.c_int64), ("max_halvings", C.c_int32),
+                ("precision", C.c_int32), ("value_dtype", C.c_int32), ("ls_window", C.c_int32),
+                ("capacity", C.c_int64), ("max_capacity", C.c_int64), ("x_on_host", C.c_int32),
+                ("timing", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("ls_trials", C.c_int64), ("nnz", C.c_int64),
+                ("status", C.c_int32), ("accepted_halvings", C.c_int32), ("f", C.c_double),
+                ("F", C.c_double), ("rel_change", C.c_double), ("ms_total", C.c_double),
+                ("ms_gram", C.c_double), ("ms_grad_pass", C.c_double), ("grad_pass_launches", C.c_int64),
+                ("kernel_launches", C.c_int64), ("capacity_regrows", C.c_int64), ("candidates", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HpcError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.hpc_status_string(status).decode()
+        extra = lib.hpc_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){' - ' + extra if extra else ''}")
+        self.status = status
+
+
+_P = C.c_void_p
+_SIGS = {
+    "hpc_default_options": (None, [C.POINTER(Options)]),
+    "hpc_status_string": (C.c_char_p, [C.c_int]),
+    "hpc_last_error": (C.c_char_p, []),
+    "hpc_create": (C.c_int, [C.POINTER(_P), _P, C.c_int, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_int,
+                             C.POINTER(Options), _P]),
+    "hpc_load_x": (C.c_int, [_P, _P, C.c_int, C.c_int]),
+    "hpc_solve": (C.c_int, [_P, C.POINTER(Stats)]),
+    "hpc_iterate": (C.c_int, [_P, C.c_int64, C.POINTER(Stats)]),
+    "hpc_get_omega": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int, C.c_int]),
+    "hpc_set_omega": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int]),
+    "hpc_set_lambda": (C.c_int, [_P, C.c_double, C.c_double]),
+    "hpc_get_s_entries": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
+    "hpc_get_candidates": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P]),
+    "hpc_destroy": (C.c_int, [_P]),
+    "hpc_gram": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int, C.c_int64, C.c_int, _P]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "libhpconcord.so")
+
+
+def load(build_if_missing: bool = True):
+    """Load libhpconcord.so (building it first if absent); raise if that fails."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path) and build_if_missing:
+        from . import _build
+
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status, where, allow=(OK,)):
+    if status not in allow:
+        raise HpcError(status, where)
+    return status
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().hpc_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _dtype_code(t) -> int:
+    import torch
+
+    if isinstance(t, np.ndarray):
+        return {np.dtype(np.float32): F32, np.dtype(np.float64): F64}[t.dtype]
+    return {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16}[t.dtype]
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclasses.dataclass
+class Csr:
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    def to_scipy(self, p):
+        import scipy.sparse as sp
+
+        return sp.csr_matrix((self.val, self.col, self.row_ptr), shape=(p, p))
+
+
+class Solver:
+    """A solver handle (``hpc_create`` ... ``hpc_destroy``)."""
+
+    def __init__(self, X, lambda1, lambda2, variant=COV, stream=None, n=None, p=None, xdtype=None, **options):
+        lib = load()
+        self._lib = lib
+        self.options = default_options(**options)
+        if isinstance(X, np.ndarray):
+            self.options.x_on_host = 1
+            X = np.ascontiguousarray(X)
+            ptr = X.ctypes.data_as(C.c_void_p)
+            n, p = X.shape
+            xdt = _dtype_code(X)
+        elif X is None:
+            ptr = None
+            xdt = F32 if xdtype is None else xdtype
+        else:
+            assert X.is_cuda and X.is_contiguous() and X.dim() == 2
+            ptr = C.c_void_p(X.data_ptr())
+            n, p = X.shape
+            xdt = _dtype_code(X)
+        self.n, self.p = int(n), int(p)
+        self._stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        st = lib.hpc_create(C.byref(h), ptr, xdt, self.n, self.p, float(lambda1), float(lambda2), variant,
+                            C.byref(self.options), self._stream)
+        _check(st, "hpc_create")
+        self._h = h
+        self.stats = Stats()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hpc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_x(self, X):
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X)
+            st = self._lib.hpc_load_x(self._h, X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1)
+        else:
+            st = self._lib.hpc_load_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 0)
+        return _check(st, "hpc_load_x")
+
+    def solve(self, allow_not_converged=True) -> Stats:
+        st = self._lib.hpc_solve(self._h, C.byref(self.stats))
+        _check(st, "hpc_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
+        return self.stats
+
+    def iterate(self, k) -> Stats:
+        st = self._lib.hpc_iterate(self._h, int(k), C.byref(self.stats))
+        _check(st, "hpc_iterate")
+        return self.stats
+
+    def nnz(self) -> int:
+        m = C.c_int64(0)
+        _check(self._lib.hpc_get_omega(self._h, C.byref(m), None, None, None, F64, 0), "hpc_get_omega")
+        return m.value
+
+    def get_omega(self, dtype=np.float64) -> Csr:
+        m = C.c_int64(self.nnz())
+        rp = np.empty(self.p + 1, np.int64)
+        ci = np.empty(max(m.value, 1), np.int32)
+        v = np.empty(max(m.value, 1), dtype)
+        code = F64 if np.dtype(dtype) == np.float64 else F32
+        _check(self._lib.hpc_get_omega(self._h, C.byref(m), rp.ctypes.data_as(C.c_void_p),
+                                       ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p), code, 0),
+               "hpc_get_omega")
+        return Csr(rp, ci[: m.value], v[: m.value])
+
+    def get_omega_device(self, row_ptr, col, val):
+        m = C.c_int64(col.numel())
+        code = F64 if str(val.dtype) == "torch.float64" else F32
+        _check(self._lib.hpc_get_omega(self._h, C.byref(m), C.c_void_p(row_ptr.data_ptr()),
+                                       C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()), code, 1),
+               "hpc_get_omega")
+        return m.value
+
+    def omega_dense(self) -> np.ndarray:
+        return self.get_omega().to_scipy(self.p).toarray()
+
+    def set_omega(self, csr: Csr):
+        rp = np.ascontiguousarray(csr.row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(csr.col, dtype=np.int32)
+        v = np.ascontiguousarray(csr.val, dtype=np.float64)
+        return _check(self._lib.hpc_set_omega(self._h, int(ci.size), rp.ctypes.data_as(C.c_void_p),
+                                              ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p), F64, 0),
+                      "hpc_set_omega")
+
+    def set_lambda(self, lambda1, lambda2):
+        return _check(self._lib.hpc_set_lambda(self._h, float(lambda1), float(lambda2)), "hpc_set_lambda")
+
+    def s_entries(self, rows, cols) -> np.ndarray:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cols = np.ascontiguousarray(cols, dtype=np.int64)
+        out = np.empty(rows.size, np.float64)
+        _check(self._lib.hpc_get_s_entries(self._h, rows.size, rows.ctypes.data_as(C.c_void_p),
+                                           cols.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)),
+               "hpc_get_s_entries")
+        return out
+
+    def candidates(self):
+        m = C.c_int64(0)
+        _check(self._lib.hpc_get_candidates(self._h, C.byref(m), None, None, None, None), "hpc_get_candidates")
+        k = m.value
+        r = np.empty(max(k, 1), np.int64)
+        c = np.empty(max(k, 1), np.int64)
+        o = np.empty(max(k, 1), np.float64)
+        g = np.empty(max(k, 1), np.float64)
+        _check(self._lib.hpc_get_candidates(self._h, C.byref(m), r.ctypes.data_as(C.c_void_p),
+                                            c.ctypes.data_as(C.c_void_p), o.ctypes.data_as(C.c_void_p),
+                                            g.ctypes.data_as(C.c_void_p)), "hpc_get_candidates")
+        return r[:k], c[:k], o[:k], g[:k]
+
+
+def gram(X, S, precision=PREC_AUTO, stream=None):
+    """S = X^T X / n on the device (``hpc_gram``); S is a (p, lds) tensor, lds >= p."""
+    n, p = X.shape
+    st = load().hpc_gram(C.c_void_p(X.data_ptr()), _dtype_code(X), n, p, C.c_void_p(S.data_ptr()),
+                         _dtype_code(S), S.stride(0), precision, _stream_ptr(stream))
+    return _check(st, "hpc_gram")

@@ -1,0 +1,708 @@
+// C ABI of the solver: handle life cycle, data loading (the Gram of Alg. 2
+// step 2), and the host driver of Alg. 1 that enqueues each outer iteration's
+// kernels and reads back a small control block twice per iteration.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+void set_cuda_error(cudaError_t e, const char* what, int line) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s (api.cu:%d)", what, cudaGetErrorString(e), line);
+}
+
+#define CUDA_TRY(expr)                                     \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) {                           \
+            set_cuda_error(e_, #expr, __LINE__);           \
+            return e_ == cudaErrorMemoryAllocation ? HPC_ERR_OOM : HPC_ERR_CUDA; \
+        }                                                  \
+    } while (0)
+
+#define STATUS_TRY(expr)             \
+    do {                             \
+        int st_ = (expr);            \
+        if (st_ < 0) return st_;     \
+    } while (0)
+
+size_t dtype_size(int dt) { return dt == HPC_F64 ? 8 : dt == HPC_F32 ? 4 : 2; }
+
+template <typename T>
+T* as(void* p) { return static_cast<T*>(p); }
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct hpc_ctx {
+    int64_t n = 0, p = 0, ld = 0;
+    int variant = HPC_COV;
+    int vdt = HPC_F32;      // value dtype of S / Omega / G
+    int precision = HPC_PREC_AUTO;
+    double lam1 = 0, lam2 = 0;
+    hpc_options opt{};
+    cudaStream_t stream = nullptr;
+    bool loaded = false;
+
+    // dense data
+    void* S = nullptr;              // p x ld, vdt
+    // iterate (double-buffered CSR)
+    int* rp[2] = {nullptr, nullptr};
+    int* ci[2] = {nullptr, nullptr};
+    void* cv[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t csr_cap = 0;
+    int64_t nnz = 0;
+    // screening output and candidate structure
+    int64_t cap = 0;                // emission capacity
+    int* em_row = nullptr;
+    int* em_col = nullptr;
+    void* em_w = nullptr;
+    void* em_om = nullptr;
+    int* bk_cnt = nullptr; int* bk_off = nullptr; int* bk_cur = nullptr; int* bk_len = nullptr;
+    int* col_a = nullptr; void* w_a = nullptr; void* om_a = nullptr; unsigned char* fl_a = nullptr;
+    int* col_b = nullptr; void* w_b = nullptr; void* om_b = nullptr; unsigned char* fl_b = nullptr;
+    void* g_b = nullptr;
+    int* cnt2 = nullptr;
+    double* part_obj = nullptr;
+    double* part_ls = nullptr;
+    int nblk = 0;
+    hpc::Ctrl* d_ctrl = nullptr;
+    hpc::Ctrl* h_ctrl = nullptr;    // pinned
+    // scratch for the tensor-core Gram
+    void* gram_scratch = nullptr;
+    size_t gram_scratch_bytes = 0;
+    // events
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_scr0 = nullptr, ev_scr1 = nullptr;
+    int64_t regrows = 0;
+    double ms_gram = 0.0;
+};
+
+namespace {
+
+void free_candidates(hpc_ctx* h) {
+    void* ptrs[] = {h->em_row, h->em_col, h->em_w, h->em_om, h->col_a, h->w_a, h->om_a, h->fl_a,
+                    h->col_b, h->w_b, h->om_b, h->fl_b, h->g_b};
+    for (void* q : ptrs) if (q) cudaFree(q);
+    h->em_row = h->em_col = nullptr; h->em_w = h->em_om = nullptr;
+    h->col_a = h->col_b = nullptr; h->w_a = h->om_a = h->w_b = h->om_b = h->g_b = nullptr;
+    h->fl_a = h->fl_b = nullptr;
+}
+
+int alloc_candidates(hpc_ctx* h, int64_t cap) {
+    const size_t vs = dtype_size(h->vdt);
+    const int64_t bcap = 2 * cap;
+    free_candidates(h);
+    CUDA_TRY(cudaMalloc(&h->em_row, cap * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&h->em_col, cap * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&h->em_w, cap * vs));
+    CUDA_TRY(cudaMalloc(&h->em_om, cap * vs));
+    CUDA_TRY(cudaMalloc(&h->col_a, bcap * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&h->w_a, bcap * vs));
+    CUDA_TRY(cudaMalloc(&h->om_a, bcap * vs));
+    CUDA_TRY(cudaMalloc(&h->fl_a, bcap));
+    CUDA_TRY(cudaMalloc(&h->col_b, bcap * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&h->w_b, bcap * vs));
+    CUDA_TRY(cudaMalloc(&h->om_b, bcap * vs));
+    CUDA_TRY(cudaMalloc(&h->fl_b, bcap));
+    CUDA_TRY(cudaMalloc(&h->g_b, bcap * vs));
+    h->cap = cap;
+    return HPC_OK;
+}
+
+// (Re)allocate the double-buffered CSR with capacity newcap, keeping the current iterate.
+int grow_csr(hpc_ctx* h, int64_t newcap) {
+    const size_t vs = dtype_size(h->vdt);
+    for (int b = 0; b < 2; ++b) {
+        int* ci = nullptr;
+        void* cv = nullptr;
+        CUDA_TRY(cudaMalloc(&ci, newcap * sizeof(int)));
+        CUDA_TRY(cudaMalloc(&cv, newcap * vs));
+        if (b == h->cur && h->ci[b] && h->nnz > 0) {
+            CUDA_TRY(cudaMemcpyAsync(ci, h->ci[b], h->nnz * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+            CUDA_TRY(cudaMemcpyAsync(cv, h->cv[b], h->nnz * vs, cudaMemcpyDeviceToDevice, h->stream));
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+        }
+        if (h->ci[b]) cudaFree(h->ci[b]);
+        if (h->cv[b]) cudaFree(h->cv[b]);
+        h->ci[b] = ci;
+        h->cv[b] = cv;
+    }
+    h->csr_cap = newcap;
+    return HPC_OK;
+}
+
+int set_identity(hpc_ctx* h) {
+    if (h->vdt == HPC_F64)
+        hpc::launch_set_identity<double>({h->rp[h->cur], h->ci[h->cur], as<double>(h->cv[h->cur])}, (int)h->p, h->stream);
+    else
+        hpc::launch_set_identity<float>({h->rp[h->cur], h->ci[h->cur], as<float>(h->cv[h->cur])}, (int)h->p, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    h->nnz = h->p;
+    return HPC_OK;
+}
+
+template <typename T>
+hpc::IterBufs<T> bufs(hpc_ctx* h) {
+    hpc::IterBufs<T> b;
+    b.S = static_cast<const T*>(h->S);
+    b.ld = h->ld;
+    b.p = (int)h->p;
+    b.cur = {h->rp[h->cur], h->ci[h->cur], as<T>(h->cv[h->cur])};
+    b.next = {h->rp[1 - h->cur], h->ci[1 - h->cur], as<T>(h->cv[1 - h->cur])};
+    b.csr_cap = (int)std::min<int64_t>(h->csr_cap, 0x7fffffff);
+    b.em = {h->em_row, h->em_col, as<T>(h->em_w), as<T>(h->em_om), (int)h->cap};
+    b.bk.cnt = h->bk_cnt; b.bk.off = h->bk_off; b.bk.cur = h->bk_cur; b.bk.len = h->bk_len;
+    b.bk.col_a = h->col_a; b.bk.w_a = as<T>(h->w_a); b.bk.om_a = as<T>(h->om_a); b.bk.fl_a = h->fl_a;
+    b.bk.col_b = h->col_b; b.bk.w_b = as<T>(h->w_b); b.bk.om_b = as<T>(h->om_b); b.bk.fl_b = h->fl_b;
+    b.bk.g = as<T>(h->g_b);
+    b.bk.cap = (int)std::min<int64_t>(2 * h->cap, 0x7fffffff);
+    b.cnt2 = h->cnt2;
+    b.part_obj = h->part_obj;
+    b.part_ls = h->part_ls;
+    b.nblk = h->nblk;
+    b.ctrl = h->d_ctrl;
+    b.lam1 = (T)h->lam1;
+    b.lam2 = (T)h->lam2;
+    b.eps = h->opt.eps;
+    b.max_halvings = h->opt.max_halvings;
+    b.ls_window = h->opt.ls_window;
+    return b;
+}
+
+int read_ctrl(hpc_ctx* h) {
+    CUDA_TRY(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, sizeof(hpc::Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return HPC_OK;
+}
+
+int flags_to_status(int flags) {
+    if (flags & hpc::kFlagNaN) return HPC_ERR_NAN;
+    if (flags & hpc::kFlagLsFail) return HPC_ERR_LS_FAIL;
+    if (flags & hpc::kFlagBadStructure) return HPC_ERR_CUDA;
+    return HPC_OK;
+}
+
+// Grow the candidate (and iterate) capacity after an overflow.  Returns HPC_OK or
+// HPC_ERR_CAPACITY when max_capacity is reached.
+int regrow(hpc_ctx* h, int64_t need) {
+    const int64_t limit = h->opt.max_capacity > 0 ? h->opt.max_capacity : h->p * h->p;
+    int64_t nc = std::max<int64_t>(2 * h->cap, need);
+    nc = std::min<int64_t>(nc, std::min<int64_t>(limit, 0x3fffffff));
+    if (nc <= h->cap) {
+        std::snprintf(g_last_error, sizeof g_last_error, "candidate capacity %lld exhausted",
+                      (long long)h->cap);
+        return HPC_ERR_CAPACITY;
+    }
+    STATUS_TRY(alloc_candidates(h, nc));
+    if (2 * nc > h->csr_cap) STATUS_TRY(grow_csr(h, 2 * nc));
+    h->regrows += 1;
+    return HPC_OK;
+}
+
+// One outer iteration.  *done is set when the stopping rule holds.
+template <typename T>
+int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        hpc::IterBufs<T> b = bufs<T>(h);
+        hpc::launch_iter_begin<T>(b, h->stream);
+        if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_scr0, h->stream));
+        hpc::launch_grad_screen<T>(b, h->stream);
+        if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_scr1, h->stream));
+        hpc::launch_candidates<T>(b, h->stream);
+        CUDA_TRY(cudaGetLastError());
+        int launches = hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesCandidates;
+        bool accepted = false, overflow = false;
+        for (int hb = 0; hb <= h->opt.max_halvings; hb += h->opt.ls_window) {
+            hpc::launch_ls_window<T>(b, hb, hb == 0, h->stream);
+            CUDA_TRY(cudaGetLastError());
+            launches += hpc::kLaunchesLsWindow;
+            STATUS_TRY(read_ctrl(h));
+            const hpc::Ctrl& c = *h->h_ctrl;
+            if (c.flags & (hpc::kFlagEmOverflow | hpc::kFlagBucketOverflow)) { overflow = true; break; }
+            if (c.flags) break;
+            if (c.ls_accept >= 0) { accepted = true; break; }
+        }
+        if (h->opt.timing && st) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, h->ev_scr0, h->ev_scr1));
+            st->ms_grad_pass += ms;
+            st->grad_pass_launches += 1;
+        }
+        if (st) st->kernel_launches += launches;
+        const hpc::Ctrl c = *h->h_ctrl;
+        if (st) {
+            st->f = c.f_cur;
+            st->F = c.f_cur + c.pen_cur;
+            st->candidates = c.em_count;
+        }
+        if (overflow) {
+            const int64_t need = (int64_t)c.em_count + 1;
+            STATUS_TRY(regrow(h, need));
+            continue;
+        }
+        if (!accepted) {
+            const int s = flags_to_status(c.flags);
+            return s != HPC_OK ? s : HPC_ERR_LS_FAIL;
+        }
+        hpc::launch_accept<T>(b, h->stream);
+        CUDA_TRY(cudaGetLastError());
+        if (st) st->kernel_launches += hpc::kLaunchesAccept;
+        STATUS_TRY(read_ctrl(h));
+        const hpc::Ctrl& c2 = *h->h_ctrl;
+        if (c2.flags & hpc::kFlagNnzOverflow) {
+            STATUS_TRY(grow_csr(h, std::max<int64_t>(2 * h->csr_cap, (int64_t)c2.nnz_next + 1)));
+            h->regrows += 1;
+            continue;
+        }
+        if (c2.flags) return flags_to_status(c2.flags);
+        h->cur = 1 - h->cur;
+        h->nnz = c2.nnz_next;
+        if (st) {
+            st->iterations += 1;
+            st->rel_change = c2.rel;
+            st->accepted_halvings = c2.ls_accept;
+            st->nnz = h->nnz;
+        }
+        *done = use_stop && c2.converged;
+        return HPC_OK;
+    }
+    return HPC_ERR_CAPACITY;
+}
+
+template <typename T>
+int run_iterations(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* st) {
+    hpc_stats local{};
+    hpc_stats* s = st ? st : &local;
+    std::memset(s, 0, sizeof *s);
+    const int64_t regrows0 = h->regrows;
+    // reset the accumulators of the control block
+    h->h_ctrl->iter = 0;
+    h->h_ctrl->ls_trials = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h->d_ctrl->iter, &h->h_ctrl->iter, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&h->d_ctrl->ls_trials, &h->h_ctrl->ls_trials, sizeof(long long),
+                             cudaMemcpyHostToDevice, h->stream));
+    if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
+    int status = use_stop ? HPC_NOT_CONVERGED : HPC_OK;
+    for (int64_t it = 0; it < k; ++it) {
+        bool done = false;
+        const int r = one_iteration<T>(h, s, use_stop, &done);
+        if (r != HPC_OK) { status = r; break; }
+        if (done) { status = HPC_OK; break; }
+    }
+    if (h->opt.timing) {
+        CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
+        CUDA_TRY(cudaEventSynchronize(h->ev[1]));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+        s->ms_total = ms;
+    }
+    STATUS_TRY(read_ctrl(h));
+    s->ls_trials = h->h_ctrl->ls_trials;
+    s->nnz = h->nnz;
+    s->ms_gram = h->ms_gram;
+    s->capacity_regrows = h->regrows - regrows0;
+    s->status = status;
+    return status;
+}
+
+int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
+    const void* Xd = X;
+    void* tmp = nullptr;
+    const size_t xbytes = (size_t)h->n * h->p * dtype_size(xdt);
+    if (on_host) {
+        CUDA_TRY(cudaMalloc(&tmp, xbytes));
+        CUDA_TRY(cudaMemcpyAsync(tmp, X, xbytes, cudaMemcpyHostToDevice, h->stream));
+        Xd = tmp;
+    }
+    int launches = 0;
+    if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
+    cudaError_t e;
+    int prec = h->precision;
+    if (prec == HPC_PREC_FP64 || prec == HPC_PREC_FP32) {
+        e = hpc::gram_simt(Xd, xdt, h->n, h->p, h->S, h->vdt, h->ld, h->stream, &launches);
+    } else {
+        const size_t need = hpc::gram_tc_scratch_bytes(xdt, h->n, h->p, prec);
+        if (need > h->gram_scratch_bytes) {
+            if (h->gram_scratch) cudaFree(h->gram_scratch);
+            h->gram_scratch = nullptr;
+            h->gram_scratch_bytes = 0;
+            CUDA_TRY(cudaMalloc(&h->gram_scratch, need));
+            h->gram_scratch_bytes = need;
+        }
+        e = hpc::gram_tc(Xd, xdt, h->n, h->p, static_cast<float*>(h->S), h->ld, prec, h->gram_scratch,
+                         h->gram_scratch_bytes, h->stream, &launches);
+        if (e == cudaErrorNotSupported) {
+            if (tmp) cudaFree(tmp);
+            std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
+            return HPC_ERR_NOT_IMPLEMENTED;
+        }
+    }
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "gram", __LINE__);
+        if (tmp) cudaFree(tmp);
+        return HPC_ERR_CUDA;
+    }
+    if (h->opt.timing) {
+        CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
+        CUDA_TRY(cudaEventSynchronize(h->ev[3]));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+        h->ms_gram = ms;
+    }
+    if (tmp) {
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        cudaFree(tmp);
+    }
+    h->cur = 0;
+    STATUS_TRY(set_identity(h));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->loaded = true;
+    return HPC_OK;
+}
+
+void destroy(hpc_ctx* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_candidates(h);
+    void* ptrs[] = {h->S, h->rp[0], h->rp[1], h->ci[0], h->ci[1], h->cv[0], h->cv[1], h->bk_cnt, h->bk_off,
+                    h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch};
+    for (void* q : ptrs) if (q) cudaFree(q);
+    if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    for (auto& e : h->ev) if (e) cudaEventDestroy(e);
+    if (h->ev_scr0) cudaEventDestroy(h->ev_scr0);
+    if (h->ev_scr1) cudaEventDestroy(h->ev_scr1);
+    delete h;
+}
+
+bool valid_dtype(int d) { return d == HPC_F32 || d == HPC_F64 || d == HPC_BF16; }
+
+}  // namespace
+
+extern "C" {
+
+void hpc_default_options(hpc_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->eps = 1e-6;
+    opt->max_iter = 1000;
+    opt->max_halvings = 60;
+    opt->precision = HPC_PREC_AUTO;
+    opt->value_dtype = HPC_F32;
+    opt->ls_window = 8;
+    opt->capacity = 0;
+    opt->max_capacity = 0;
+    opt->x_on_host = 0;
+    opt->timing = 1;
+}
+
+const char* hpc_status_string(int s) {
+    switch (s) {
+        case HPC_OK: return "ok";
+        case HPC_NOT_CONVERGED: return "not converged (max_iter reached)";
+        case HPC_ERR_ARG: return "invalid argument";
+        case HPC_ERR_OOM: return "device out of memory";
+        case HPC_ERR_CAPACITY: return "candidate capacity exceeded";
+        case HPC_ERR_NONPOS_DIAG: return "non-positive or missing diagonal entry";
+        case HPC_ERR_NAN: return "NaN or Inf in gradient or objective";
+        case HPC_ERR_LS_FAIL: return "line search failed within max_halvings";
+        case HPC_ERR_CUDA: return "CUDA error";
+        case HPC_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case HPC_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* hpc_last_error(void) { return g_last_error; }
+
+int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t p, double lambda1,
+               double lambda2, hpc_variant variant, const hpc_options* opt, void* cuda_stream) {
+    if (!out) return HPC_ERR_ARG;
+    *out = nullptr;
+    hpc_options o;
+    if (opt) o = *opt; else hpc_default_options(&o);
+    if (n < 1 || p < 1 || p > (1ll << 30) || !(lambda1 >= 0.0) || !(lambda2 >= 0.0) || !(o.eps > 0.0) ||
+        o.max_iter < 0 || o.max_halvings < 0 || o.max_halvings > 1000 || !valid_dtype(xdt) ||
+        (o.value_dtype != HPC_F32 && o.value_dtype != HPC_F64) ||
+        !(o.ls_window == 1 || o.ls_window == 2 || o.ls_window == 4 || o.ls_window == 8 || o.ls_window == 16) ||
+        o.precision < HPC_PREC_AUTO || o.precision > HPC_PREC_TF32)
+        return HPC_ERR_ARG;
+    if (variant != HPC_COV) {
+        std::snprintf(g_last_error, sizeof g_last_error, "variant %d not built", (int)variant);
+        return HPC_ERR_NOT_IMPLEMENTED;
+    }
+    int prec = o.precision;
+    if (prec == HPC_PREC_AUTO) prec = (o.value_dtype == HPC_F64) ? HPC_PREC_FP64 : HPC_PREC_BF16X3;
+    if (prec == HPC_PREC_FP64 && o.value_dtype != HPC_F64) return HPC_ERR_ARG;
+    if (o.value_dtype == HPC_F64 && prec != HPC_PREC_FP64) return HPC_ERR_ARG;
+
+    hpc_ctx* h = new (std::nothrow) hpc_ctx();
+    if (!h) return HPC_ERR_OOM;
+    h->n = n; h->p = p; h->variant = variant; h->vdt = o.value_dtype; h->precision = prec;
+    h->lam1 = lambda1; h->lam2 = lambda2; h->opt = o;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ld = (p + 127) / 128 * 128;
+
+    auto fail = [&](int st) { destroy(h); return st; };
+    auto cu = [&](cudaError_t e, const char* what, int line) -> int {
+        if (e == cudaSuccess) return HPC_OK;
+        set_cuda_error(e, what, line);
+        return e == cudaErrorMemoryAllocation ? HPC_ERR_OOM : HPC_ERR_CUDA;
+    };
+#define CK(expr) do { int s_ = cu((expr), #expr, __LINE__); if (s_ != HPC_OK) return fail(s_); } while (0)
+    const size_t vs = dtype_size(h->vdt);
+    CK(cudaMalloc(&h->S, (size_t)p * h->ld * vs));
+    CK(cudaMemsetAsync(h->S, 0, (size_t)p * h->ld * vs, h->stream));
+    for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->rp[b], (p + 1) * sizeof(int)));
+    const int64_t cap0 = o.capacity > 0 ? o.capacity : std::max<int64_t>(32 * p, 1024);
+    {
+        const int s = alloc_candidates(h, cap0);
+        if (s != HPC_OK) return fail(s);
+        const int s2 = grow_csr(h, 2 * cap0);
+        if (s2 != HPC_OK) return fail(s2);
+    }
+    CK(cudaMalloc(&h->bk_cnt, p * sizeof(int)));
+    CK(cudaMalloc(&h->bk_off, (p + 1) * sizeof(int)));
+    CK(cudaMalloc(&h->bk_cur, p * sizeof(int)));
+    CK(cudaMalloc(&h->bk_len, p * sizeof(int)));
+    CK(cudaMalloc(&h->cnt2, p * sizeof(int)));
+    h->nblk = (int)std::min<int64_t>((p + 7) / 8, 152 * 4);
+    CK(cudaMalloc(&h->part_obj, (size_t)h->nblk * 4 * sizeof(double)));
+    CK(cudaMalloc(&h->part_ls, (size_t)h->nblk * 16 * 4 * sizeof(double)));
+    CK(cudaMalloc(&h->d_ctrl, sizeof(hpc::Ctrl)));
+    CK(cudaMemsetAsync(h->d_ctrl, 0, sizeof(hpc::Ctrl), h->stream));
+    CK(cudaMallocHost(&h->h_ctrl, sizeof(hpc::Ctrl)));
+    std::memset(h->h_ctrl, 0, sizeof(hpc::Ctrl));
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreate(&h->ev_scr0));
+    CK(cudaEventCreate(&h->ev_scr1));
+#undef CK
+    if (X) {
+        const int s = load_x(h, X, xdt, o.x_on_host);
+        if (s != HPC_OK) return fail(s);
+    }
+    *out = h;
+    return HPC_OK;
+}
+
+int hpc_load_x(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host) {
+    if (!h || !X || !valid_dtype(xdt)) return HPC_ERR_ARG;
+    return load_x(h, X, xdt, x_on_host);
+}
+
+int hpc_solve(hpc_handle h, hpc_stats* stats) {
+    if (!h || !h->loaded) return HPC_ERR_ARG;
+    return h->vdt == HPC_F64 ? run_iterations<double>(h, h->opt.max_iter, true, stats)
+                             : run_iterations<float>(h, h->opt.max_iter, true, stats);
+}
+
+int hpc_iterate(hpc_handle h, int64_t k, hpc_stats* stats) {
+    if (!h || !h->loaded || k < 0) return HPC_ERR_ARG;
+    return h->vdt == HPC_F64 ? run_iterations<double>(h, k, false, stats)
+                             : run_iterations<float>(h, k, false, stats);
+}
+
+int hpc_get_omega(hpc_handle h, int64_t* nnz_inout, int64_t* row_ptr, int32_t* col, void* val, hpc_dtype vdt,
+                  int on_device) {
+    if (!h || !nnz_inout) return HPC_ERR_ARG;
+    if (!row_ptr) { *nnz_inout = h->nnz; return HPC_OK; }
+    if (!col || !val || (vdt != HPC_F32 && vdt != HPC_F64)) return HPC_ERR_ARG;
+    if (*nnz_inout < h->nnz) { *nnz_inout = h->nnz; return HPC_ERR_CAPACITY; }
+    const int64_t p = h->p, nnz = h->nnz;
+    const size_t ovs = dtype_size(vdt);
+    int64_t* d_rp = row_ptr;
+    int32_t* d_ci = col;
+    void* d_v = val;
+    if (!on_device) {
+        CUDA_TRY(cudaMalloc(&d_rp, (p + 1) * sizeof(int64_t)));
+        CUDA_TRY(cudaMalloc(&d_ci, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+        CUDA_TRY(cudaMalloc(&d_v, std::max<int64_t>(nnz, 1) * ovs));
+    }
+    if (h->vdt == HPC_F64)
+        hpc::launch_csr_export<double>(h->rp[h->cur], h->ci[h->cur], as<double>(h->cv[h->cur]), (int)p, (int)nnz,
+                                       d_rp, d_ci, d_v, vdt, h->stream);
+    else
+        hpc::launch_csr_export<float>(h->rp[h->cur], h->ci[h->cur], as<float>(h->cv[h->cur]), (int)p, (int)nnz,
+                                      d_rp, d_ci, d_v, vdt, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(row_ptr, d_rp, (p + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(col, d_ci, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(val, d_v, nnz * ovs, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        cudaFree(d_rp); cudaFree(d_ci); cudaFree(d_v);
+    } else {
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    *nnz_inout = nnz;
+    return HPC_OK;
+}
+
+int hpc_set_omega(hpc_handle h, int64_t nnz, const int64_t* row_ptr, const int32_t* col, const void* val,
+                  hpc_dtype vdt, int on_device) {
+    if (!h || !row_ptr || !col || !val || nnz < h->p || (vdt != HPC_F32 && vdt != HPC_F64)) return HPC_ERR_ARG;
+    const int64_t p = h->p;
+    std::vector<int64_t> rp(p + 1);
+    std::vector<int32_t> ci(nnz);
+    std::vector<double> v(nnz);
+    if (on_device) {
+        CUDA_TRY(cudaMemcpy(rp.data(), row_ptr, (p + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(ci.data(), col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (vdt == HPC_F64) {
+            CUDA_TRY(cudaMemcpy(v.data(), val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f(nnz);
+            CUDA_TRY(cudaMemcpy(f.data(), val, nnz * sizeof(float), cudaMemcpyDeviceToHost));
+            for (int64_t t = 0; t < nnz; ++t) v[t] = f[t];
+        }
+    } else {
+        std::memcpy(rp.data(), row_ptr, (p + 1) * sizeof(int64_t));
+        std::memcpy(ci.data(), col, nnz * sizeof(int32_t));
+        if (vdt == HPC_F64) std::memcpy(v.data(), val, nnz * sizeof(double));
+        else for (int64_t t = 0; t < nnz; ++t) v[t] = static_cast<const float*>(val)[t];
+    }
+    // validate: row_ptr monotone, columns sorted and in range, positive diagonal present
+    if (rp[0] != 0 || rp[p] != nnz) return HPC_ERR_ARG;
+    for (int64_t i = 0; i < p; ++i) {
+        if (rp[i + 1] < rp[i]) return HPC_ERR_ARG;
+        bool diag = false;
+        for (int64_t t = rp[i]; t < rp[i + 1]; ++t) {
+            if (ci[t] < 0 || ci[t] >= p) return HPC_ERR_ARG;
+            if (t > rp[i] && ci[t] <= ci[t - 1]) return HPC_ERR_ARG;
+            if (ci[t] == i) {
+                if (!(v[t] > 0.0)) return HPC_ERR_NONPOS_DIAG;
+                diag = true;
+            }
+            if (!std::isfinite(v[t])) return HPC_ERR_NAN;
+        }
+        if (!diag) return HPC_ERR_NONPOS_DIAG;
+    }
+    if (nnz > h->csr_cap) STATUS_TRY(grow_csr(h, 2 * nnz));
+    std::vector<int> rp32(p + 1);
+    for (int64_t i = 0; i <= p; ++i) rp32[i] = (int)rp[i];
+    const int c = h->cur;
+    CUDA_TRY(cudaMemcpyAsync(h->rp[c], rp32.data(), (p + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->ci[c], ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (h->vdt == HPC_F64) {
+        CUDA_TRY(cudaMemcpyAsync(h->cv[c], v.data(), nnz * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    } else {
+        std::vector<float> f(nnz);
+        for (int64_t t = 0; t < nnz; ++t) f[t] = (float)v[t];
+        CUDA_TRY(cudaMemcpyAsync(h->cv[c], f.data(), nnz * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    h->nnz = nnz;
+    return HPC_OK;
+}
+
+int hpc_set_lambda(hpc_handle h, double lambda1, double lambda2) {
+    if (!h || !(lambda1 >= 0.0) || !(lambda2 >= 0.0)) return HPC_ERR_ARG;
+    h->lam1 = lambda1;
+    h->lam2 = lambda2;
+    return HPC_OK;
+}
+
+int hpc_get_s_entries(hpc_handle h, int64_t m, const int64_t* rows, const int64_t* cols, double* out) {
+    if (!h || m < 0 || (m > 0 && (!rows || !cols || !out))) return HPC_ERR_ARG;
+    if (!h->S || h->variant != HPC_COV) return HPC_ERR_ARG;
+    for (int64_t t = 0; t < m; ++t)
+        if (rows[t] < 0 || rows[t] >= h->p || cols[t] < 0 || cols[t] >= h->p) return HPC_ERR_ARG;
+    if (m == 0) return HPC_OK;
+    int64_t* d_idx = nullptr;
+    double* d_out = nullptr;
+    CUDA_TRY(cudaMalloc(&d_idx, 2 * m * sizeof(int64_t)));
+    CUDA_TRY(cudaMalloc(&d_out, m * sizeof(double)));
+    CUDA_TRY(cudaMemcpyAsync(d_idx, rows, m * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(d_idx + m, cols, m * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    hpc::launch_gather_s(h->S, h->vdt == HPC_F64, h->ld, m, d_idx, d_idx + m, d_out, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out, d_out, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaFree(d_idx);
+    cudaFree(d_out);
+    return HPC_OK;
+}
+
+int hpc_get_candidates(hpc_handle h, int64_t* m_inout, int64_t* rows, int64_t* cols, double* omega, double* grad) {
+    if (!h || !m_inout) return HPC_ERR_ARG;
+    const int64_t p = h->p;
+    std::vector<int> off(p + 1), len(p);
+    CUDA_TRY(cudaMemcpyAsync(off.data(), h->bk_off, (p + 1) * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(len.data(), h->bk_len, p * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const int64_t tot = off[p];
+    std::vector<int> col(std::max<int64_t>(tot, 1));
+    std::vector<unsigned char> fl(std::max<int64_t>(tot, 1));
+    const size_t vs = dtype_size(h->vdt);
+    std::vector<char> om(std::max<int64_t>(tot, 1) * vs), g(std::max<int64_t>(tot, 1) * vs);
+    if (tot > 0) {
+        CUDA_TRY(cudaMemcpyAsync(col.data(), h->col_b, tot * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(fl.data(), h->fl_b, tot, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(om.data(), h->om_b, tot * vs, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(g.data(), h->g_b, tot * vs, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    auto val = [&](const std::vector<char>& a, int64_t t) {
+        return h->vdt == HPC_F64 ? reinterpret_cast<const double*>(a.data())[t]
+                                 : (double)reinterpret_cast<const float*>(a.data())[t];
+    };
+    int64_t m = 0;
+    for (int64_t i = 0; i < p; ++i)
+        for (int64_t t = off[i]; t < off[i] + len[i]; ++t)
+            if (fl[t] & hpc::kEntKeep) {
+                if (rows) {
+                    if (m >= *m_inout) return HPC_ERR_CAPACITY;
+                    rows[m] = i; cols[m] = col[t];
+                    if (omega) omega[m] = val(om, t);
+                    if (grad) grad[m] = val(g, t);
+                }
+                ++m;
+            }
+    *m_inout = m;
+    return HPC_OK;
+}
+
+int hpc_destroy(hpc_handle h) {
+    destroy(h);
+    return HPC_OK;
+}
+
+int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dtype sdt, int64_t lds,
+             int precision, void* cuda_stream) {
+    if (!X || !S || n < 1 || p < 1 || lds < p || !valid_dtype(xdt) || (sdt != HPC_F32 && sdt != HPC_F64))
+        return HPC_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (precision == HPC_PREC_AUTO) precision = sdt == HPC_F64 ? HPC_PREC_FP64 : HPC_PREC_BF16X3;
+    if (precision == HPC_PREC_FP64 || precision == HPC_PREC_FP32) {
+        if ((precision == HPC_PREC_FP64) != (sdt == HPC_F64)) return HPC_ERR_ARG;
+        cudaError_t e = hpc::gram_simt(X, xdt, n, p, S, sdt, lds, s, nullptr);
+        if (e != cudaSuccess) { set_cuda_error(e, "gram_simt", __LINE__); return HPC_ERR_CUDA; }
+        return HPC_OK;
+    }
+    if (sdt != HPC_F32 || (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32)) return HPC_ERR_ARG;
+    const size_t need = hpc::gram_tc_scratch_bytes(xdt, n, p, precision);
+    void* scratch = nullptr;
+    if (need) CUDA_TRY(cudaMallocAsync(&scratch, need, s));
+    cudaError_t e = hpc::gram_tc(X, xdt, n, p, static_cast<float*>(S), lds, precision, scratch, need, s, nullptr);
+    if (scratch) cudaFreeAsync(scratch, s);
+    if (e == cudaErrorNotSupported) return HPC_ERR_NOT_IMPLEMENTED;
+    if (e != cudaSuccess) { set_cuda_error(e, "gram_tc", __LINE__); return HPC_ERR_CUDA; }
+    return HPC_OK;
+}
+
+}  // extern "C"

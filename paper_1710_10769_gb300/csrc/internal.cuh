@@ -1,0 +1,124 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "hpconcord.h"
+
+namespace hpc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Device-resident control block of one solver handle.  Kernels write it; the
+// host reads it back (one small copy) at the two synchronisation points of an
+// outer iteration.
+struct Ctrl {
+    int em_count;        // entries emitted by the gradient-screening pass
+    int bucket_total;    // entries of the symmetric candidate structure (before de-dup)
+    int flags;           // kFlag* bits
+    int ls_accept;       // accepted number of halvings h (tau = 2^-h), -1 while searching
+    int ls_base;         // first h of the next line-search window
+    int nnz_next;        // entries of the accepted iterate
+    int converged;       // relative change < eps
+    int iter;            // outer iterations done since the last reset
+    double tau;          // accepted step
+    double f_cur;        // smooth part f(Omega^k)
+    double pen_cur;      // lambda1 * sum_{i != j} |w_ij| at Omega^k
+    double norm2_cur;    // ||Omega^k||_F^2
+    double delta2;       // ||Omega^{k+1} - Omega^k||_F^2 for the accepted tau
+    double rel;          // sqrt(delta2 / norm2_cur)
+    long long ls_trials; // accumulated trials (the paper's t)
+};
+
+enum : int {
+    kFlagEmOverflow = 1,
+    kFlagBucketOverflow = 2,
+    kFlagNaN = 4,
+    kFlagLsFail = 8,
+    kFlagNnzOverflow = 16,
+    kFlagBadStructure = 32,
+};
+
+// Flags on candidate entries.
+enum : unsigned char { kEntSupp = 1, kEntOwn = 2, kEntMirror = 4, kEntKeep = 8 };
+
+template <typename T>
+struct Csr {
+    int* rp;
+    int* ci;
+    T* cv;
+};
+
+// Output of the screening pass: one record per emitted (i, j).
+template <typename T>
+struct Emit {
+    int* row;
+    int* col;     // bit 31 set: (i, j) is in the support of the iterate
+    T* w;         // W_ij = (Omega S)_ij
+    T* om;        // w_ij (0 off the support)
+    int cap;
+};
+
+// Per-row candidate structure (symmetric pattern, columns ascending after sort).
+template <typename T>
+struct Buckets {
+    int* cnt;     // p: entries per row before de-dup
+    int* off;     // p+1: row offsets
+    int* cur;     // p: scatter cursors
+    int* len;     // p: entries per row after de-dup
+    int* col_a; T* w_a; T* om_a; unsigned char* fl_a;    // scattered
+    int* col_b; T* w_b; T* om_b; unsigned char* fl_b;    // sorted, de-duplicated
+    T* g;         // G_ij of the sorted entries
+    int cap;
+};
+
+// ---------------------------------------------------------------- launchers (iterate.cu)
+template <typename T>
+struct IterBufs {
+    const T* S;
+    int64_t ld;
+    int p;
+    Csr<T> cur;
+    Csr<T> next;
+    int csr_cap;
+    Emit<T> em;
+    Buckets<T> bk;
+    int* cnt2;            // p: per-row entry counts of the accepted iterate
+    double* part_obj;     // objective partials   [nblk][4]
+    double* part_ls;      // line-search partials [nblk][16][4]
+    int nblk;             // blocks of the warp-per-row kernels
+    Ctrl* ctrl;
+    T lam1, lam2;
+    double eps;
+    int max_halvings;
+    int ls_window;
+};
+
+template <typename T> void launch_iter_begin(const IterBufs<T>& b, cudaStream_t s);
+template <typename T> void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s);
+template <typename T> void launch_candidates(const IterBufs<T>& b, cudaStream_t s);
+template <typename T> void launch_ls_window(const IterBufs<T>& b, int h_base, bool first, cudaStream_t s);
+template <typename T> void launch_accept(const IterBufs<T>& b, cudaStream_t s);
+template <typename T> void launch_set_identity(Csr<T> c, int p, cudaStream_t s);
+template <typename T> void launch_csr_export(const int* rp, const int* ci, const T* cv, int p, int nnz,
+                                             int64_t* rp64, int32_t* ci_out, void* val, int vdt,
+                                             cudaStream_t s);
+void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int64_t* rows,
+                     const int64_t* cols, double* out, cudaStream_t s);
+
+constexpr int kLaunchesScreen = 1;
+constexpr int kLaunchesBegin = 1;
+constexpr int kLaunchesCandidates = 6;
+constexpr int kLaunchesLsWindow = 2;
+constexpr int kLaunchesAccept = 4;
+
+// ---------------------------------------------------------------- dense products (gram*.cu)
+// S = X^T X / n into S (p x lds).  Returns a CUDA error code.
+cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int sdt, int64_t lds,
+                      cudaStream_t s, int* launches);
+cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches);
+size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
+
+}  // namespace hpc

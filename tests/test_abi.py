@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point the
+public header declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(hpc_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("hpc_create", "hpc_solve", "hpc_get_omega", "hpc_destroy", "hpc_gram"):
+        assert name in d
+
+
+def test_library_loads_and_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.library_path())
+    missing = [n for n in _declared() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(lib):
+    assert sorted(set(_declared()) - set(lib.EXPORTED)) == []
+
+
+def test_status_strings_without_gpu(lib):
+    so = lib.load()
+    assert so.hpc_status_string(0) == b"ok"
+    assert b"capacity" in so.hpc_status_string(-3)
+    o = lib.default_options()
+    assert o.eps == 1e-6 and o.max_halvings == 60 and o.ls_window == 8
+
+
+def test_build_is_sm103a_only():
+    from paper_1710_10769_gb300 import _build
+
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
