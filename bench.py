@@ -1,0 +1,351 @@
+"""Benchmark: prox-grad iterations/s and time-to-converge of the Cov solver at
+p = 65536, n = 32768 (X stored BF16, S FP32, lambda = (0.15, 0.05)).
+
+A step is one whole solve from X resident in HBM: the Gram S = X^T X / n
+(hpc_load_x) plus prox-grad iterations until ||dOmega||_F/||Omega||_F < 1e-6
+(hpc_solve).  value = iterations of all timed steps / device time of those
+steps; ms_per_step is the time-to-converge.  Inputs (X 4.3 GB, S 17 GB) are
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica of the workload on its GPU
+(the solver does not shard); value sums the ranks' iterations over the
+slowest rank's time.  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "prox-grad iters/s, Cov solve at p=65536 n=32768 (time-to-converge = ms_per_step)"
+UNIT = "iters/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained"), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_run(workload, X_host_cols, p_sample, max_seconds=25.0):
+    """Time the FP64 oracle (as it stands) on the leading p_sample x p_sample sub-problem.
+
+    The oracle's cost per iteration and of its Gram both grow as p^2 at fixed n and
+    row density, so its rate at p is rate(p_sample) * (p_sample / p)^2.
+    """
+    import numpy as np
+
+    import oracle
+
+    t0 = time.perf_counter()
+    S = oracle.gram(X_host_cols)
+    res = oracle.solve(S, workload.lambda1, workload.lambda2, eps=workload.eps, max_iter=100000)
+    dt = time.perf_counter() - t0
+    rate_sample = res.iterations / dt
+    scale = (p_sample / workload.p) ** 2
+    try:
+        from threadpoolctl import threadpool_info
+
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": rate_sample * scale, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": (f"full FP64 oracle solve (Gram + {res.iterations} iterations, {dt:.1f} s) of the leading "
+                       f"{p_sample}x{p_sample} sub-problem (same n={X_host_cols.shape[0]}, lambda), "
+                       f"rate scaled by ({p_sample}/{workload.p})^2"),
+            "seconds": dt, "iterations": res.iterations}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from workloads import WORKLOADS, omega0_for, round_to_bf16, sample_x_cpu
+
+    w = WORKLOADS[args.workload]
+    ps = args.cpu_sample_p
+    # the leading principal sub-problem of the workload's law: Omega0's leading block
+    om = omega0_for(w)[:ps, :ps]
+    X = sample_x_cpu(om, w.n, w.seed)
+    if w.x_dtype == "bf16":
+        X = round_to_bf16(X.astype(np.float32)).astype(np.float64)
+    vals, secs, its = [], [], []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline_run(w, X, ps)
+        if k >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+            its.append(r["iterations"])
+    value = sum(its) / sum(secs) * (ps / w.p) ** 2
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs) / (ps / w.p) ** 2,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generator, leading sub-problem of the workload)",
+            "config": {"workload": w.name, "p": w.p, "n": w.n, "lambda1": w.lambda1, "lambda2": w.lambda2,
+                       "eps": w.eps, "sample_p": ps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bf16_p65536")
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3", "tf32"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-sample-p", type=int, default=2048)
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1710_10769_gb300 as hpc
+    from workloads import WORKLOADS, make_x
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    w = WORKLOADS[args.workload]
+    prec = {"auto": hpc.PREC_AUTO, "fp32": hpc.PREC_FP32, "bf16x3": hpc.PREC_BF16X3, "tf32": hpc.PREC_TF32}[
+        args.precision]
+    X = make_x(w, device="cuda")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    solver = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=hpc.BF16 if w.x_dtype == "bf16" else hpc.F32,
+                        precision=prec, eps=w.eps, max_iter=100000)
+
+    def step(Xsrc):
+        solver.load_x(Xsrc)
+        st = solver.solve().as_dict()
+        st["ms_gram_step"] = st["ms_gram"]
+        return st
+
+    for _ in range(args.warmup):
+        step(X)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    recs = []
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            recs.append(step(X))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = ev0.elapsed_time(ev1)
+    iters = sum(r["iterations"] for r in recs)
+    if pg:
+        t = torch.tensor([ms, float(iters)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax[:1], op=pg.ReduceOp.MAX)
+        pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
+        ms_all, iters_all = float(tmax[0]), float(t[1])
+    else:
+        ms_all, iters_all = ms, float(iters)
+    value = iters_all / (ms_all / 1000.0)
+
+    # dominant kernel: the Gram (one launch per step) or the screening SpMM (one per iteration)
+    hbm, bf16, bf16_sus, peak_src = _peaks()
+    gram_ms = sum(r["ms_gram_step"] for r in recs)
+    scr_ms = sum(r["ms_grad_pass"] for r in recs)
+    scr_launches = sum(r["grad_pass_launches"] for r in recs)
+    p, n = w.p, w.n
+    tensor_gram = solver.precision_used() in (hpc.PREC_BF16X3, hpc.PREC_TF32)
+    if gram_ms >= scr_ms:
+        flops = float(n) * p * (p + 1)               # symmetric half of X^T X (n p (p+1) FMA-flops)
+        achieved = flops / (gram_ms / len(recs) / 1000.0) / 1e12
+        if tensor_gram:
+            peak = bf16 if solver.precision_used() == hpc.PREC_BF16X3 else bf16 / 2.0
+            bound = "tensor"
+        else:
+            peak = 152 * 128 * 2 * 2.07e9 / 1e12      # SIMT FP32 FMA peak at the max SM clock
+            bound = "alu"
+        roof = {"kernel": "gram", "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src if bound == "tensor" else
+                "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    else:
+        per = scr_ms / max(scr_launches, 1) / 1000.0
+        achieved = 4.0 * p * p / per / 1e9           # S read once per pass (FP32), bytes / launch time
+        roof = {"kernel": "grad_screen", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": peak_src}
+
+    # end to end through the C ABI with host buffers: H2D of X inside the timed region,
+    # D2H of the CSR result
+    Xh = X.cpu().pin_memory()
+    e2e_ms, e2e_its, d2h = 0.0, 0, 0
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.load_x(Xh)
+        st = solver.solve().as_dict()
+        csr = solver.get_omega(np.float32)
+        t1 = time.perf_counter()
+        if k >= 1:
+            e2e_ms += (t1 - t0) * 1000
+            e2e_its += st["iterations"]
+            d2h += csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes
+    e2e = {"value": e2e_its / (e2e_ms / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
+           "d2h_bytes_per_step": int(d2h // max(args.e2e_steps, 1))}
+
+    plain = None
+    if not args.no_plain and solver.precision_used() != hpc.PREC_FP32 and rank == 0:
+        ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=hpc.BF16 if w.x_dtype == "bf16" else hpc.F32,
+                        precision=hpc.PREC_FP32, eps=w.eps, max_iter=100000)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ps.load_x(X)
+        pst = ps.solve().as_dict()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        om_plain = ps.get_omega()
+        om_mixed = solver.get_omega()
+        A = om_plain.to_scipy(p)
+        B = om_mixed.to_scipy(p)
+        plain = {"time_to_converge_ms": e0.elapsed_time(e1), "iterations": pst["iterations"],
+                 "gram_ms": pst["ms_gram"], "rel_diff_vs_mixed": float(
+                     math.sqrt((A - B).multiply(A - B).sum()) / math.sqrt(A.multiply(A).sum()))}
+        ps.close()
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        from workloads import omega0_for, round_to_bf16, sample_x_cpu
+
+        om0 = omega0_for(w)[: args.cpu_sample_p, : args.cpu_sample_p]
+        Xs = sample_x_cpu(om0, w.n, w.seed)
+        if w.x_dtype == "bf16":
+            Xs = round_to_bf16(Xs.astype(np.float32)).astype(np.float64)
+        c = cpu_baseline_run(w, Xs, args.cpu_sample_p)
+        cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        gpu_launches = sum(r["kernel_launches"] for r in recs) + sum(1 for _ in recs)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if (w.x_dtype == "bf16" and tensor_gram) else "f32",
+            "data": "synthetic (seeded: random SDD Omega0 with ~8 nnz/row, X = Z L^-T)",
+            "config": {"workload": w.name, "p": p, "n": n, "lambda1": w.lambda1, "lambda2": w.lambda2,
+                       "eps": w.eps, "x_dtype": w.x_dtype, "s_dtype": "f32",
+                       "gram_precision": solver.precision_name(), "parallelism": f"replicas x{ws}",
+                       "l2": "inputs > L2 (X 4.3 GB, S 17.2 GB); no flush"},
+            "iterations_per_step": [r["iterations"] for r in recs],
+            "ls_trials_per_step": [r["ls_trials"] for r in recs],
+            "time_to_converge_ms": ms_all / args.steps,
+            "gram_ms_per_step": gram_ms / len(recs),
+            "iteration_loop_its": iters / (sum(r["ms_total"] for r in recs) / 1000.0),
+            "grad_pass_ms": scr_ms / max(scr_launches, 1),
+            "final_nnz": recs[-1]["nnz"], "final_F": recs[-1]["F"],
+            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
+            "cpu_baseline": cpu, "plain_fp32": plain,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

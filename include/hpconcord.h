@@ -172,6 +172,22 @@ int hpc_get_s_entries(hpc_handle h, int64_t m, const int64_t* rows, const int64_
 int hpc_get_candidates(hpc_handle h, int64_t* m_inout, int64_t* rows, int64_t* cols,
                        double* omega, double* grad);
 
+/* Resolved configuration of a handle. */
+typedef struct {
+    int64_t n, p;
+    int64_t ld;               /* leading dimension of the stored S (elements)          */
+    int32_t variant;          /* hpc_variant                                            */
+    int32_t precision;        /* hpc_precision after resolving HPC_PREC_AUTO            */
+    int32_t value_dtype;      /* HPC_F32 or HPC_F64                                     */
+    int32_t pad_;
+    int64_t capacity;         /* current candidate capacity (entries)                   */
+    int64_t device_bytes;     /* device memory held by the handle                       */
+    double  lambda1, lambda2;
+} hpc_info;
+
+/* Fill *info for handle h. */
+int hpc_get_info(hpc_handle h, hpc_info* info);
+
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 int hpc_destroy(hpc_handle h);
 
@@ -180,8 +196,11 @@ int hpc_destroy(hpc_handle h);
 /* S = X^T X / n (Alg. 2 step 2) for device X (n x p, dtype xdt, row-major)
  * into device S (p x lds, dtype sdt = HPC_F32 or HPC_F64, lds >= p), both
  * triangles written, S bitwise symmetric.  precision as hpc_precision
- * (HPC_PREC_FP64 needs sdt = HPC_F64).  Enqueued on stream; returns without
- * synchronising.  Allocates scratch for the tensor-core modes. */
+ * (HPC_PREC_FP64 needs sdt = HPC_F64).  Enqueued on stream.  The SIMT modes
+ * return without synchronising; the tensor-core modes (BF16X3, TF32) allocate
+ * stream-ordered scratch for the transposed operand panels and synchronise the
+ * stream to check the kernel's error word (HPC_ERR_DEVICE_TIMEOUT if a bounded
+ * wait gave up). */
 int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dtype sdt,
              int64_t lds, int precision, void* cuda_stream);
 

@@ -43,6 +43,16 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("ld", C.c_int64), ("variant", C.c_int32),
+                ("precision", C.c_int32), ("value_dtype", C.c_int32), ("pad_", C.c_int32),
+                ("capacity", C.c_int64), ("device_bytes", C.c_int64), ("lambda1", C.c_double),
+                ("lambda2", C.c_double)]
+
+
+PRECISION_NAMES = {PREC_FP64: "fp64", PREC_FP32: "fp32", PREC_BF16X3: "bf16x3", PREC_TF32: "tf32"}
+
+
 class HpcError(RuntimeError):
     def __init__(self, status, where):
         lib = load()
@@ -67,6 +77,7 @@ _SIGS = {
     "hpc_set_lambda": (C.c_int, [_P, C.c_double, C.c_double]),
     "hpc_get_s_entries": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "hpc_get_candidates": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P]),
+    "hpc_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "hpc_destroy": (C.c_int, [_P]),
     "hpc_gram": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int, C.c_int64, C.c_int, _P]),
 }
@@ -152,6 +163,12 @@ class Solver:
             ptr = X.ctypes.data_as(C.c_void_p)
             n, p = X.shape
             xdt = _dtype_code(X)
+        elif X is not None and not X.is_cuda:
+            assert X.is_contiguous() and X.dim() == 2
+            self.options.x_on_host = 1
+            ptr = C.c_void_p(X.data_ptr())
+            n, p = X.shape
+            xdt = _dtype_code(X)
         elif X is None:
             ptr = None
             xdt = F32 if xdtype is None else xdtype
@@ -190,6 +207,9 @@ class Solver:
         if isinstance(X, np.ndarray):
             X = np.ascontiguousarray(X)
             st = self._lib.hpc_load_x(self._h, X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1)
+        elif not X.is_cuda:
+            assert X.is_contiguous()
+            st = self._lib.hpc_load_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 1)
         else:
             st = self._lib.hpc_load_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 0)
         return _check(st, "hpc_load_x")
@@ -203,6 +223,17 @@ class Solver:
         st = self._lib.hpc_iterate(self._h, int(k), C.byref(self.stats))
         _check(st, "hpc_iterate")
         return self.stats
+
+    def info(self) -> Info:
+        inf = Info()
+        _check(self._lib.hpc_get_info(self._h, C.byref(inf)), "hpc_get_info")
+        return inf
+
+    def precision_used(self) -> int:
+        return self.info().precision
+
+    def precision_name(self) -> str:
+        return PRECISION_NAMES[self.precision_used()]
 
     def nnz(self) -> int:
         m = C.c_int64(0)

@@ -368,6 +368,14 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         cudaFree(tmp);
     }
+    if (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) {
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        const int w = hpc::gram_tc_take_error();
+        if (w != 0) {
+            std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram: bounded wait %d gave up", w);
+            return HPC_ERR_DEVICE_TIMEOUT;
+        }
+    }
     h->cur = 0;
     STATUS_TRY(set_identity(h));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -677,6 +685,25 @@ int hpc_get_candidates(hpc_handle h, int64_t* m_inout, int64_t* rows, int64_t* c
     return HPC_OK;
 }
 
+int hpc_get_info(hpc_handle h, hpc_info* info) {
+    if (!h || !info) return HPC_ERR_ARG;
+    std::memset(info, 0, sizeof *info);
+    info->n = h->n;
+    info->p = h->p;
+    info->ld = h->ld;
+    info->variant = h->variant;
+    info->precision = h->precision;
+    info->value_dtype = h->vdt;
+    info->capacity = h->cap;
+    const size_t vs = dtype_size(h->vdt);
+    info->device_bytes = (int64_t)((size_t)h->p * h->ld * vs + h->cap * (8 + 2 * vs) +
+                                   2 * h->cap * (2 * 4 + 5 * vs + 2) + 2 * h->csr_cap * (4 + vs) +
+                                   (size_t)h->p * 32 + h->gram_scratch_bytes);
+    info->lambda1 = h->lam1;
+    info->lambda2 = h->lam2;
+    return HPC_OK;
+}
+
 int hpc_destroy(hpc_handle h) {
     destroy(h);
     return HPC_OK;
@@ -702,6 +729,8 @@ int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dt
     if (scratch) cudaFreeAsync(scratch, s);
     if (e == cudaErrorNotSupported) return HPC_ERR_NOT_IMPLEMENTED;
     if (e != cudaSuccess) { set_cuda_error(e, "gram_tc", __LINE__); return HPC_ERR_CUDA; }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hpc::gram_tc_take_error() != 0) return HPC_ERR_DEVICE_TIMEOUT;
     return HPC_OK;
 }
 

@@ -1,12 +1,504 @@
-// Tensor-core Gram S = X^T X / n (tcgen05 + TMA), BF16 split and TF32 modes.
+// Tensor-core Gram S = X^T X / n (Alg. 2 step 2) for sm_103a: tcgen05.mma with the
+// accumulator in tensor memory, operands staged in shared memory by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier pipeline.
+//
+// Operands.  The Gram is a "TN" product of X^T with itself, so X (n x p,
+// row-major) is first transposed into K-major panels A = X^T (p_pad x n_pad,
+// zero padded) in the MMA input type:
+//   BF16X3 on FP32 X : x = hi + lo, hi = bf16(x), lo = bf16(x - hi); the tile
+//                      accumulates hi*hi^T + hi*lo^T + lo*hi^T in FP32 (the
+//                      dropped lo*lo^T term is below FP32 rounding of S);
+//   BF16 X           : one panel, one product (bf16 x bf16 is exact in FP32);
+//   TF32             : FP32 panel rounded to TF32, kind::tf32 products.
+//
+// Tiles.  One CTA computes a 128 x 256 tile S[I, J] (UMMA M = 128, N = 256,
+// 256 TMEM columns) over the whole K = n, for the tiles that touch the upper
+// triangle, visited in bands of 16 row blocks so that CTAs in flight share A
+// and B panels in L2.  Each entry with i <= j is written together with its
+// mirror S[j, i]: S is bitwise symmetric by construction.
+//
+// Roles (128 threads): thread 0 issues TMA loads, thread 32 issues MMAs and
+// commits, warp 1 owns the TMEM allocation, and all four warps drain the
+// accumulator (warp w reads TMEM lanes 32w..32w+31).  Every mbarrier wait is
+// bounded; on timeout the CTA records an error word, stops issuing, waits
+// (bounded) for its own copies and MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace hpc {
+namespace {
 
-size_t gram_tc_scratch_bytes(int, int64_t, int64_t, int) { return 0; }
+constexpr int kBM = 128;           // rows of A per tile (UMMA M)
+constexpr int kBN = 256;           // rows of B per tile (UMMA N)
+constexpr int kRowBytes = 128;     // one swizzle row = one K-slab of a panel row
+constexpr int kABytes = kBM * kRowBytes;   // 16 KB
+constexpr int kBBytes = kBN * kRowBytes;   // 32 KB
+constexpr int kBand = 16;          // row blocks per band of the tile order
+constexpr uint32_t kTmemCols = 256;
+constexpr long long kWaitLimit = 1ll << 26;
 
-cudaError_t gram_tc(const void*, int, int64_t, int64_t, float*, int64_t, int, void*, size_t, cudaStream_t, int*) {
-    return cudaErrorNotSupported;
+enum : int { kModeBf16 = 0, kModeBf16x3 = 1, kModeTf32 = 2 };
+
+__device__ int g_gram_error = 0;   // first error word recorded by any CTA
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false on timeout or when another role raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int code) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 255) {
+            if (*abort_flag) return false;
+            __nanosleep(64);
+        }
+    }
+    *abort_flag = 1;
+    atomicCAS(&g_gram_error, 0, code);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if constexpr (MODE == kModeTf32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 TMEM lanes x 32 consecutive 32-bit columns: thread t gets lane (base + t).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05 format): K-major, 128-byte swizzle,
+// 8-row core groups 1024 bytes apart (SBO), version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: D = F32, A/B = BF16 (kind::f16) or TF32 (kind::tf32),
+// both K-major, N = 256, M = 128.
+template <int MODE>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4)                                          // D format F32
+           | ((MODE == kModeTf32 ? 2u : 1u) << 7)             // A format
+           | ((MODE == kModeTf32 ? 2u : 1u) << 10)            // B format
+           | ((uint32_t)(kBN >> 3) << 17)                     // N >> 3
+           | ((uint32_t)(kBM >> 4) << 24);                    // M >> 4
+}
+
+template <int MODE>
+struct Cfg {
+    static constexpr int kPieces = (MODE == kModeBf16x3) ? 2 : 1;       // panels in smem per stage
+    static constexpr int kTerms = (MODE == kModeBf16x3) ? 3 : 1;        // products per K step
+    static constexpr int kElem = (MODE == kModeTf32) ? 4 : 2;
+    static constexpr int kBK = kRowBytes / kElem;                      // K elements per stage
+    static constexpr int kMmaK = 32 / kElem;                           // K per instruction
+    static constexpr int kStageBytes = kPieces * (kABytes + kBBytes);
+    static constexpr int kStages = (MODE == kModeBf16x3) ? 2 : 4;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+          const int2* __restrict__ tiles, int k_tiles, int64_t p, int64_t n, float* __restrict__ S, int64_t lds,
+          int vec_ok) {
+    using C = Cfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
+    uint64_t* empty = full + C::kStages;
+    uint64_t* accum = empty + C::kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 tile = tiles[blockIdx.x];
+    const int I0 = tile.x * kBM, J0 = tile.y * kBN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(accum, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
+        if (C::kPieces > 1) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;   // stages whose TMA loads were issued (producer thread)
+    if (threadIdx.x == 0) {
+        // ---------------- TMA producer
+        for (int kt = 0; kt < k_tiles; ++kt) {
+            const int s = kt % C::kStages;
+            const uint32_t ph = (uint32_t)(kt / C::kStages) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 1)) break;
+            uint8_t* st = smem + s * C::kStageBytes;
+            mbar_expect_tx(&full[s], C::kStageBytes);
+            const int kc = kt * C::kBK;
+            for (int pc = 0; pc < C::kPieces; ++pc) {
+                const CUtensorMap* m = pc == 0 ? &map_hi : &map_lo;
+                uint8_t* a = st + pc * (kABytes + kBBytes);
+                uint8_t* b = a + kABytes;
+                tma_load_2d(a, m, &full[s], kc, I0);
+                tma_load_2d(b, m, &full[s], kc, J0);
+                tma_load_2d(b + kABytes, m, &full[s], kc, J0 + kBM);
+            }
+            ++issued;
+        }
+    } else if (threadIdx.x == 32) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = instr_desc<MODE>();
+        bool ok = true;
+        for (int kt = 0; kt < k_tiles && ok; ++kt) {
+            const int s = kt % C::kStages;
+            const uint32_t ph = (uint32_t)(kt / C::kStages) & 1u;
+            if (!mbar_wait(&full[s], ph, abort_flag, 2)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+            const uint32_t a_hi = st, b_hi = st + kABytes;
+            const uint32_t a_lo = st + (kABytes + kBBytes), b_lo = a_lo + kABytes;
+#pragma unroll
+            for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
+                const uint32_t off = kk * 32;   // bytes along the swizzled K row
+                const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+                umma<MODE>(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
+                if constexpr (C::kTerms == 3) {
+                    umma<MODE>(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+                    umma<MODE>(tmem, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+                }
+            }
+            umma_commit(&empty[s]);    // frees the stage once these MMAs have read it
+        }
+        umma_commit(accum);            // accumulator complete (or all issued MMAs done)
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: TMEM -> registers -> S (owner rule i <= j, plus mirror)
+    bool have = mbar_wait(accum, 0, abort_flag, 3) && !*abort_flag;
+    have = __all_sync(kFull, have);     // tcgen05.ld is warp-collective
+    tc_fence_after();
+    if (have) {
+        const float dn = (float)n;
+        const int r = warp * 32 + lane;
+        const int64_t i = I0 + r;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld_wait();
+            if (i >= p) continue;
+            const int64_t jb = J0 + c0;
+            float o[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) o[q] = __uint_as_float(v[q]) / dn;
+            // direct row segment S[i, jb .. jb+31]
+            if (vec_ok && jb >= i && jb + 31 < p) {     // 16-byte aligned rows only
+                float4* dst = reinterpret_cast<float4*>(S + i * lds + jb);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int64_t j = jb + q;
+                    if (j >= i && j < p) S[i * lds + j] = o[q];
+                }
+            }
+            // mirror S[j, i] for j > i: for fixed q the warp writes 32 consecutive floats
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int64_t j = jb + q;
+                if (j > i && j < p) S[j * lds + i] = o[q];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) {
+        // drain: bounded waits for the loads this CTA issued, so no copy lands after exit
+        for (int kt = max(0, issued - C::kStages); kt < issued; ++kt) {
+            const int s = kt % C::kStages;
+            const uint32_t ph = (uint32_t)(kt / C::kStages) & 1u;
+            for (long long it = 0; it < (1ll << 22) && !mbar_try_wait(&full[s], ph); ++it) __nanosleep(64);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// Transpose X (n x p) into K-major panels (p_pad x n_pad) of the MMA input type.
+template <typename TX, int MODE>
+__global__ void __launch_bounds__(256)
+k_prep(const TX* __restrict__ X, int64_t n, int64_t p, void* __restrict__ hi, void* __restrict__ lo,
+       int64_t n_pad, int64_t p_pad) {
+    __shared__ float tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t k = k0 + r, i = i0 + tx;
+        float v = 0.f;
+        if (k < n && i < p) {
+            if constexpr (std::is_same<TX, __nv_bfloat16>::value) v = __bfloat162float(X[k * p + i]);
+            else v = (float)X[k * p + i];
+        }
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, k = k0 + tx;
+        if (i >= p_pad || k >= n_pad) continue;
+        const float x = tile[tx][r];
+        const int64_t o = i * n_pad + k;
+        if constexpr (MODE == kModeTf32) {
+            uint32_t t;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
+            static_cast<float*>(hi)[o] = __uint_as_float(t);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            static_cast<__nv_bfloat16*>(hi)[o] = h;
+            if constexpr (MODE == kModeBf16x3)
+                static_cast<__nv_bfloat16*>(lo)[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int mode_of(int xdt, int precision) {
+    if (precision == HPC_PREC_TF32) return kModeTf32;
+    return xdt == HPC_BF16 ? kModeBf16 : kModeBf16x3;
+}
+
+struct Geometry {
+    int64_t p_pad, n_pad;
+    size_t panel_bytes;
+    int pieces;
+    int64_t ntiles;
+};
+
+Geometry geometry(int xdt, int64_t n, int64_t p, int precision) {
+    const int mode = mode_of(xdt, precision);
+    Geometry g;
+    g.p_pad = (p + kBN - 1) / kBN * kBN;
+    g.n_pad = (n + 63) / 64 * 64;
+    const int es = mode == kModeTf32 ? 4 : 2;
+    g.panel_bytes = (size_t)g.p_pad * g.n_pad * es;
+    g.panel_bytes = (g.panel_bytes + 1023) / 1024 * 1024;
+    g.pieces = mode == kModeBf16x3 ? 2 : 1;
+    const int64_t nbi = g.p_pad / kBM, nbj = g.p_pad / kBN;
+    int64_t t = 0;
+    for (int64_t bj = 0; bj < nbj; ++bj) t += std::min<int64_t>(2 * bj + 2, nbi);
+    g.ntiles = t;
+    return g;
+}
+
+// Upper-triangle tiles (128 bi <= 256 bj + 255) in bands of kBand row blocks;
+// within a band, columns left to right, rows top to bottom.
+std::vector<int2> tile_order(int64_t p_pad) {
+    const int64_t nbi = p_pad / kBM, nbj = p_pad / kBN;
+    std::vector<int2> t;
+    for (int64_t b0 = 0; b0 < nbi; b0 += kBand)
+        for (int64_t bj = 0; bj < nbj; ++bj)
+            for (int64_t bi = b0; bi < std::min<int64_t>(b0 + kBand, nbi); ++bi)
+                if (bi * kBM <= bj * kBN + kBN - 1) t.push_back(make_int2((int)bi, (int)bj));
+    return t;
+}
+
+bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int es = mode == kModeTf32 ? 4 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)g.n_pad, (cuuint64_t)g.p_pad};
+    cuuint64_t strides[1] = {(cuuint64_t)g.n_pad * es};
+    cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / es), (cuuint32_t)kBM};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, mode == kModeTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles, int64_t n, int64_t p, float* S,
+                        int64_t lds, cudaStream_t s) {
+    using C = Cfg<MODE>;
+    CUtensorMap mh, ml;
+    std::memset(&mh, 0, sizeof mh);
+    std::memset(&ml, 0, sizeof ml);
+    if (!make_map(&mh, hi, MODE, g)) return cudaErrorNotSupported;
+    if (C::kPieces > 1 && !make_map(&ml, lo, MODE, g)) return cudaErrorNotSupported;
+    if (C::kPieces == 1) ml = mh;
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    const int k_tiles = (int)(g.n_pad / C::kBK);
+    // float4 row stores need 16-byte aligned rows: lds % 4 == 0 and an aligned base
+    const int vec_ok = (lds % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0) ? 1 : 0;
+    k_gram_tc<MODE><<<(unsigned)g.ntiles, 128, C::kSmem, s>>>(mh, ml, tiles, k_tiles, p, n, S, lds, vec_ok);
+    return cudaGetLastError();
+}
+
+template <typename TX>
+void launch_prep(const void* X, int mode, int64_t n, int64_t p, void* hi, void* lo, const Geometry& g,
+                 cudaStream_t s) {
+    dim3 grid((unsigned)((g.n_pad + 31) / 32), (unsigned)((g.p_pad + 31) / 32));
+    const TX* x = static_cast<const TX*>(X);
+    if (mode == kModeTf32) k_prep<TX, kModeTf32><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
+    else if (mode == kModeBf16x3) k_prep<TX, kModeBf16x3><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
+    else k_prep<TX, kModeBf16><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
+}
+
+}  // namespace
+
+size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision) {
+    const Geometry g = geometry(xdt, n, p, precision);
+    return g.pieces * g.panel_bytes + (size_t)g.ntiles * sizeof(int2) + 1024;
+}
+
+cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches) {
+    if (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32) return cudaErrorInvalidValue;
+    if (xdt == HPC_F64) return cudaErrorNotSupported;
+    if (!encode_fn()) return cudaErrorNotSupported;
+    const int mode = mode_of(xdt, precision);
+    const Geometry g = geometry(xdt, n, p, precision);
+    if (g.ntiles > 0x7fffffff || g.n_pad / 64 > 0x7fffffff || g.p_pad > 0x7fffffff) return cudaErrorNotSupported;
+    if (scratch_bytes < gram_tc_scratch_bytes(xdt, n, p, precision)) return cudaErrorInvalidValue;
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    void* hi = base;
+    void* lo = g.pieces > 1 ? base + g.panel_bytes : nullptr;
+    int2* tiles = reinterpret_cast<int2*>(base + g.pieces * g.panel_bytes);
+    const std::vector<int2> order = tile_order(g.p_pad);
+    cudaError_t e = cudaMemcpyAsync(tiles, order.data(), order.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    // the host vector must outlive the copy
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (xdt == HPC_BF16) launch_prep<__nv_bfloat16>(X, mode, n, p, hi, lo, g, s);
+    else launch_prep<float>(X, mode, n, p, hi, lo, g, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (launches) *launches += 2;
+    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s);
+    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s);
+    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s);
+}
+
+int gram_tc_take_error() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_gram_error, sizeof v) != cudaSuccess) return -1;
+    if (v != 0) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_gram_error, &zero, sizeof zero);
+    }
+    return v;
 }
 
 }  // namespace hpc

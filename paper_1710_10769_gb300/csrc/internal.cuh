@@ -120,5 +120,7 @@ cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches);
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
+// Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
+int gram_tc_take_error();
 
 }  // namespace hpc

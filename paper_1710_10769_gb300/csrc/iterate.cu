@@ -94,118 +94,159 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
 }
 
 // ------------------------------------------------------------------ 1. screening SpMM
-// Grid: x = chunks of kRows rows, y = column blocks of BJ = 32*V columns.  x runs
-// fastest, so the CTAs in flight share one column block S[:, J] (p*BJ*sizeof(T)
-// bytes), which stays in L2 while every row gathers its d rows of it: S is read
-// from HBM about once per pass.  A warp owns one row at a time; lane l holds
-// columns J*BJ + l*V .. +V-1 and loads them as one 16-byte vector per CSR entry.
-constexpr int kScreenRows = 64;
+// Grid: x = chunks of 128 rows, y = column blocks of BJ = 32*V columns.  x runs
+// fastest, so the CTAs in flight share a few column blocks S[:, J] (p*BJ*sizeof(T)
+// bytes each), which stay in L2 while every row gathers its d rows of them: S is
+// read from HBM about once per pass.  Lane l of a warp holds columns J*BJ + l*V
+// .. +V-1 and loads them as one 16-byte vector per CSR entry.  A warp owns 16
+// consecutive rows and walks their CSR entries as one stream, kScreenUnroll
+// loads in flight at a time; when the stream crosses a row boundary the
+// finished row is screened and its emitted entries appended.
+constexpr int kScreenRowsPerWarp = 16;
+constexpr int kScreenRows = kScreenRowsPerWarp * kWarps;
+constexpr int kScreenUnroll = 8;
+
+template <typename T>
+struct ScreenRow {
+    static constexpr int V = 16 / sizeof(T);
+    static constexpr int BJ = 32 * V;
+
+    // Screen row i of the block: emit the support entries, the diagonal and every
+    // |W_ij| > lambda1 (NaN included).  Warp-collective.
+    static __device__ __forceinline__ void finalize(int i, int rb, int re, const T (&acc)[V], int j0, int p,
+                                                    const int* __restrict__ ci, const T* __restrict__ cv, T lam1,
+                                                    const Emit<T>& em, Ctrl* ctrl, int lane) {
+        unsigned mbits = 0;
+        T om[V];
+        bool big = false;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            om[v] = T(0);
+            big |= !(fabs(acc[v]) <= lam1);
+        }
+        for (int q = rb; q < re; q += 32) {
+            const int c = (q + lane < re) ? ci[q + lane] : -1;
+            unsigned bal = __ballot_sync(kFull, c >= j0 && c < j0 + BJ);
+            while (bal) {
+                const int src = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int o = __shfl_sync(kFull, c, src) - j0;
+                if (lane == o / V) {
+                    const T w = cv[q + src];
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        if (o % V == v) om[v] = w;
+                    mbits |= 1u << (o % V);
+                }
+            }
+        }
+        if (!__any_sync(kFull, big || mbits != 0)) return;
+        bool emit[V];
+        int c = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int j = j0 + lane * V + v;
+            emit[v] = (j < p) && (((mbits >> v) & 1u) || !(fabs(acc[v]) <= lam1));
+            c += emit[v] ? 1 : 0;
+        }
+        const int incl = warp_incl_scan(c, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (!total) return;
+        int base_pos = 0;
+        if (lane == 0) base_pos = atomicAdd(&ctrl->em_count, total);
+        base_pos = __shfl_sync(kFull, base_pos, 0);
+        int pos = base_pos + incl - c;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (emit[v]) {
+                if (pos < em.cap) {
+                    const int j = j0 + lane * V + v;
+                    const bool sup = (mbits >> v) & 1u;
+                    em.row[pos] = i;
+                    em.col[pos] = sup ? (int)((unsigned)j | 0x80000000u) : j;
+                    em.w[pos] = acc[v];
+                    em.om[pos] = sup ? om[v] : T(0);
+                }
+                ++pos;
+            }
+        }
+    }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_grad_screen(const T* __restrict__ S, int64_t ld, int p, const int* __restrict__ rp,
               const int* __restrict__ ci, const T* __restrict__ cv, T lam1, Emit<T> em,
               Ctrl* __restrict__ ctrl) {
-    constexpr int V = 16 / sizeof(T);
-    constexpr int BJ = 32 * V;
-    __shared__ unsigned smask[kWarps][32];
-    __shared__ T somg[kWarps][BJ];
+    using R = ScreenRow<T>;
+    constexpr int V = R::V;
+    constexpr int BJ = R::BJ;
+    constexpr int U = kScreenUnroll;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j0 = blockIdx.y * BJ;
-    const int row0 = blockIdx.x * kScreenRows;
+    const int rbase = blockIdx.x * kScreenRows + warp * kScreenRowsPerWarp;
+    if (rbase >= p) return;
+    const int nr = min(kScreenRowsPerWarp, p - rbase);
     const T* sblk = S + j0 + lane * V;
+    // lanes 0..nr hold the row pointers of the warp's rows (lane nr: end of the last row)
+    const int my_rp = (lane <= nr) ? rp[rbase + lane] : 0;
+    const int e_beg = __shfl_sync(kFull, my_rp, 0);
+    const int e_end = __shfl_sync(kFull, my_rp, nr);
+    int cur = 0;
+    int cur_beg = e_beg;
+    int cur_end = __shfl_sync(kFull, my_rp, 1);
+    T acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = T(0);
 
-    for (int r = warp; r < kScreenRows; r += kWarps) {
-        const int i = row0 + r;
-        if (i >= p) break;
-        const int beg = rp[i], end = rp[i + 1];
-        T acc[V];
+    for (int eb = e_beg; eb < e_end; eb += 32) {
+        const int e = eb + lane;
+        const int k_l = (e < e_end) ? ci[e] : 0;
+        const T w_l = (e < e_end) ? cv[e] : T(0);
+        const int cnt = min(32, e_end - eb);
+        for (int t = 0; t < cnt; t += U) {
+            const int g = min(U, cnt - t);          // entries in this group
+            const int gbase = eb + t;               // stream index of the group's first entry
+            T sv[U][V];
+            T wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (u < g) {
+                    const int k = __shfl_sync(kFull, k_l, t + u);
+                    wv[u] = __shfl_sync(kFull, w_l, t + u);
+                    vload(sv[u], sblk + (int64_t)k * ld);
+                }
+            }
+            int u0 = 0;
+            while (true) {
+                // entries [u0, stop) of the group belong to row cur (CSR order kept)
+                const int stop = min(g, cur_end - gbase);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (u >= u0 && u < stop) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fmaT(wv[u], sv[u][v], acc[v]);
+                    }
+                }
+                u0 = max(u0, stop);
+                if (u0 >= g) break;
+                // the stream left row cur: screen it and move on
+                R::finalize(rbase + cur, cur_beg, cur_end, acc, j0, p, ci, cv, lam1, em, ctrl, lane);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = T(0);
+                ++cur;
+                cur_beg = cur_end;
+                cur_end = __shfl_sync(kFull, my_rp, cur + 1);
+            }
+        }
+    }
+    while (cur < nr) {
+        R::finalize(rbase + cur, cur_beg, cur_end, acc, j0, p, ci, cv, lam1, em, ctrl, lane);
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = T(0);
-        smask[warp][lane] = 0u;
-        __syncwarp();
-        for (int base = beg; base < end; base += 32) {
-            const int e = base + lane;
-            int k_l = 0;
-            T w_l = T(0);
-            if (e < end) {
-                k_l = ci[e];
-                w_l = cv[e];
-                const int o = k_l - j0;
-                if (o >= 0 && o < BJ) {
-                    atomicOr(&smask[warp][o / V], 1u << (o % V));
-                    somg[warp][o] = w_l;
-                }
-            }
-            const int cnt = min(32, end - base);
-            int t = 0;
-            // loads first, then the FMAs in CSR order (same order as the gather fill)
-            for (; t + 4 <= cnt; t += 4) {
-                const int k0 = __shfl_sync(kFull, k_l, t + 0);
-                const int k1 = __shfl_sync(kFull, k_l, t + 1);
-                const int k2 = __shfl_sync(kFull, k_l, t + 2);
-                const int k3 = __shfl_sync(kFull, k_l, t + 3);
-                const T w0 = __shfl_sync(kFull, w_l, t + 0);
-                const T w1 = __shfl_sync(kFull, w_l, t + 1);
-                const T w2 = __shfl_sync(kFull, w_l, t + 2);
-                const T w3 = __shfl_sync(kFull, w_l, t + 3);
-                T s0[V], s1[V], s2[V], s3[V];
-                vload(s0, sblk + (int64_t)k0 * ld);
-                vload(s1, sblk + (int64_t)k1 * ld);
-                vload(s2, sblk + (int64_t)k2 * ld);
-                vload(s3, sblk + (int64_t)k3 * ld);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaT(w0, s0[v], acc[v]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaT(w1, s1[v], acc[v]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaT(w2, s2[v], acc[v]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaT(w3, s3[v], acc[v]);
-            }
-            for (; t < cnt; ++t) {
-                const int k0 = __shfl_sync(kFull, k_l, t);
-                const T w0 = __shfl_sync(kFull, w_l, t);
-                T s0[V];
-                vload(s0, sblk + (int64_t)k0 * ld);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = fmaT(w0, s0[v], acc[v]);
-            }
-        }
-        __syncwarp();
-        const unsigned m = smask[warp][lane];
-        bool emit[V];
-        int c = 0;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const int j = j0 + lane * V + v;
-            // !(|W| <= lambda1) also emits NaN, which the gradient stage reports
-            emit[v] = (j < p) && (((m >> v) & 1u) || !(fabs(acc[v]) <= lam1));
-            c += emit[v] ? 1 : 0;
-        }
-        const int incl = warp_incl_scan(c, lane);
-        const int total = __shfl_sync(kFull, incl, 31);
-        if (total) {
-            int base_pos = 0;
-            if (lane == 0) base_pos = atomicAdd(&ctrl->em_count, total);
-            base_pos = __shfl_sync(kFull, base_pos, 0);
-            int pos = base_pos + incl - c;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if (emit[v]) {
-                    if (pos < em.cap) {
-                        const int j = j0 + lane * V + v;
-                        const bool sup = (m >> v) & 1u;
-                        em.row[pos] = i;
-                        em.col[pos] = sup ? (int)((unsigned)j | 0x80000000u) : j;
-                        em.w[pos] = acc[v];
-                        em.om[pos] = sup ? somg[warp][lane * V + v] : T(0);
-                    }
-                    ++pos;
-                }
-            }
-        }
-        __syncwarp();
+        ++cur;
+        cur_beg = cur_end;
+        cur_end = __shfl_sync(kFull, my_rp, min(cur + 1, nr));
     }
 }
 
@@ -430,7 +471,7 @@ k_gradient(int p, Buckets<T> bk, T lam1, T lam2, double* part_obj, Ctrl* ctrl) {
 
 // ------------------------------------------------------------------ 3. line search
 constexpr int kMaxWindow = 16;
-template <int M> constexpr int ls_chunk() { return M >= 16 ? 32 : 64; }
+template <int M> __host__ __device__ constexpr int ls_chunk() { return M >= 16 ? 32 : 64; }
 
 // Partials per block and per tau of the window:
 //   [0] sum_{e,f} D_e D_f S_{j_e j_f}   (= tr(D S D) restricted to row i, summed over rows)

@@ -1,0 +1,97 @@
+"""Tensor-core Gram (tcgen05 + TMA) against the FP64 oracle's S = X^T X / n.
+
+Error bounds per entry, with D_ij = sqrt(S_ii S_jj) >= sum_k |x_ki x_kj| / n:
+  BF16 X   : products exact, FP32 accumulation       |dS| <= 2 n u D
+  BF16X3   : x = hi + lo (+ r), per product <= 2^-15  |dS| <= (2^-15 + 2 n u) D
+  TF32     : inputs rounded to 10-bit mantissas       |dS| <= (2^-10 + 2 n u) D
+with u = 2^-24.  Shapes cover ragged p (not a multiple of the 128 x 256 tile),
+ragged n (not a multiple of the 64-element K slab), n = 1 and p = 1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+def _gram(lib, X, precision, lds_extra=5):
+    import torch
+
+    n, p = X.shape
+    S = torch.full((p, p + lds_extra), float("nan"), dtype=torch.float32, device="cuda")
+    lib.gram(X, S, precision=precision)
+    torch.cuda.synchronize()
+    return S
+
+
+def _check(got, Xd, rel):
+    n = Xd.shape[0]
+    ref = oracle.gram(Xd)
+    D = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    err = np.abs(got - ref)
+    bound = (rel + 2 * n * U) * D + 1e-30
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert np.array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("n,p", [(257, 300), (64, 256), (1, 40), (700, 513), (96, 1)])
+def test_bf16x3_on_fp32_x(lib, n, p):
+    import torch
+
+    rng = np.random.default_rng(n + 3 * p)
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    S = _gram(lib, torch.as_tensor(X).cuda(), lib.PREC_BF16X3)
+    got = S[:, :p].double().cpu().numpy()
+    _check(got, X.astype(np.float64), 2.0 ** -15)
+    assert torch.isnan(S[:, p:]).all()
+
+
+@pytest.mark.parametrize("n,p", [(300, 700), (33, 257)])
+def test_single_product_on_bf16_x(lib, n, p):
+    import torch
+
+    rng = np.random.default_rng(p)
+    Xb = torch.as_tensor(rng.standard_normal((n, p)).astype(np.float32)).to(torch.bfloat16)
+    S = _gram(lib, Xb.cuda(), lib.PREC_BF16X3)
+    got = S[:, :p].double().cpu().numpy()
+    _check(got, Xb.float().numpy().astype(np.float64), 0.0)
+
+
+def test_tf32(lib):
+    import torch
+
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((200, 330)).astype(np.float32)
+    S = _gram(lib, torch.as_tensor(X).cuda(), lib.PREC_TF32)
+    got = S[:, :330].double().cpu().numpy()
+    _check(got, X.astype(np.float64), 2.0 ** -10)
+
+
+def test_bf16x3_at_several_bands(lib):
+    """p = 4200 spans more than one band of 16 row blocks and 17 column blocks (ragged)."""
+    import torch
+
+    rng = np.random.default_rng(17)
+    X = rng.standard_normal((640, 4200)).astype(np.float32)
+    S = _gram(lib, torch.as_tensor(X).cuda(), lib.PREC_BF16X3, lds_extra=0)
+    got = S.double().cpu().numpy()
+    _check(got, X.astype(np.float64), 2.0 ** -15)
+
+
+def test_solver_with_tensor_core_gram_matches_oracle(lib):
+    """A whole solve on the BF16X3 Gram reaches the oracle's estimate to the FP32 tolerance."""
+    import torch
+
+    from workloads import small_problem
+
+    X = small_problem(900, 600, 5.0, 12).astype(np.float32)
+    S = oracle.gram(X)
+    ref = oracle.solve(S, 0.15, 0.1, eps=1e-9, max_iter=20000)
+    with lib.Solver(torch.as_tensor(X).cuda(), 0.15, 0.1, precision=lib.PREC_BF16X3, eps=1e-7) as s:
+        assert s.precision_name() == "bf16x3"
+        s.solve()
+        om = s.omega_dense()
+    assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-5
