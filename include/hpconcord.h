@@ -204,6 +204,39 @@ int hpc_destroy(hpc_handle h);
 int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dtype sdt,
              int64_t lds, int precision, void* cuda_stream);
 
+/* Allocation-free variant of the tensor-core hpc_gram (the paper has no
+ * counterpart: this serves callers of the library, not the method).
+ *
+ * For callers that must not allocate device memory while they run: code whose
+ * device memory belongs to another allocator (for example a framework's caching
+ * allocator that has already reserved the budget, so a raw cudaMalloc fails or
+ * fragments it), services whose memory budget is fixed at start-up, and
+ * latency-critical loops in which cudaMalloc/cudaFree would synchronise the
+ * device.  It computes the same S = X^T X / n as hpc_gram with precision
+ * HPC_PREC_BF16X3 (also for HPC_PREC_AUTO) or HPC_PREC_TF32, for X of dtype
+ * HPC_F32 or HPC_BF16; the caller still passes X and S (device pointers, S is
+ * p x lds FP32).  It calls no allocating routine: its scratch is a static
+ * 64 MiB device array (HPC_GRAM_NOALLOC_SCRATCH_BYTES) that every GPU loading
+ * the library holds until the process exits.
+ *
+ * Limit: the scratch needed, (panels) * p_pad * n_pad * (2 or 4) bytes plus
+ * 8 bytes per tile, with p_pad = p rounded up to 256, n_pad = n rounded up to
+ * 64, two BF16 panels for FP32 X in BF16X3, one BF16 panel for BF16 X, one
+ * FP32 panel for TF32, must fit in HPC_GRAM_NOALLOC_SCRATCH_BYTES; otherwise
+ * the call returns HPC_ERR_ARG and hpc_last_error() states the sizes.
+ *
+ * The first call on a device looks up the array's device address there (with
+ * that device current), so make the first call on each device before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (each call writes everything it reads); calls that overlap on the
+ * GPU -- on other streams or from other host threads -- race on it.  The call
+ * synchronises the stream before returning (to check the kernel's error word).
+ * Errors as hpc_gram; HPC_ERR_NOT_IMPLEMENTED if TMA descriptors are
+ * unavailable. */
+#define HPC_GRAM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* S, int64_t lds,
+                     int precision, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,7 @@ _SIGS = {
     "hpc_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "hpc_destroy": (C.c_int, [_P]),
     "hpc_gram": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int, C.c_int64, C.c_int, _P]),
+    "hpc_gram_noalloc": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int64, C.c_int, _P]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -302,3 +303,16 @@ def gram(X, S, precision=PREC_AUTO, stream=None):
     st = load().hpc_gram(C.c_void_p(X.data_ptr()), _dtype_code(X), n, p, C.c_void_p(S.data_ptr()),
                          _dtype_code(S), S.stride(0), precision, _stream_ptr(stream))
     return _check(st, "hpc_gram")
+
+
+GRAM_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def gram_noalloc(X, S, precision=PREC_AUTO, stream=None):
+    """S = X^T X / n through ``hpc_gram_noalloc``: the tensor-core Gram with its scratch in a
+    static device array, for callers that must not allocate device memory; S is a float32
+    (p, lds) tensor."""
+    n, p = X.shape
+    st = load().hpc_gram_noalloc(C.c_void_p(X.data_ptr()), _dtype_code(X), n, p, C.c_void_p(S.data_ptr()),
+                                 S.stride(0), precision, _stream_ptr(stream))
+    return _check(st, "hpc_gram_noalloc")

@@ -47,6 +47,10 @@ struct DevBuf {
 
 }  // namespace
 
+namespace hpc {
+void set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+}  // namespace hpc
+
 struct hpc_ctx {
     int64_t n = 0, p = 0, ld = 0;
     int variant = HPC_COV;

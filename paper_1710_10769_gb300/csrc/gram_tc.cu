@@ -501,4 +501,110 @@ int gram_tc_take_error() {
     return v;
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+//
+// hpc_gram_noalloc runs the same tensor-core Gram as hpc_gram, but takes its
+// scratch (the transposed operand panels and the tile list) from the fixed
+// device array below instead of allocating.  It exists for callers that must
+// not allocate device memory while they run: code whose device memory is owned
+// by another allocator (a framework's caching allocator that has reserved the
+// budget, so a raw cudaMalloc fails or fragments it), services with a fixed
+// memory budget decided at start-up, and latency-critical loops where
+// cudaMalloc/cudaFree would synchronise the device.
+//
+// The array costs kNoAllocScratchBytes of memory on every GPU that loads the
+// library, held until the process exits.  All calls share it and it keeps the
+// last call's contents: every byte a call reads is first written by that call
+// (the panels, padding included, and the tile list), and calls that overlap on
+// the GPU (other streams, other host threads) race on it.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;     // 64 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kMaxDevices] = {};   // device address of g_noalloc_scratch, per device
+
+// The tile order of tile_order(), written on the device (no host staging buffer).
+__global__ void k_tile_order(int2* __restrict__ out, int64_t p_pad) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int64_t nbi = p_pad / kBM, nbj = p_pad / kBN;
+    int64_t t = 0;
+    for (int64_t b0 = 0; b0 < nbi; b0 += kBand)
+        for (int64_t bj = 0; bj < nbj; ++bj)
+            for (int64_t bi = b0; bi < (b0 + kBand < nbi ? b0 + kBand : nbi); ++bi)
+                if (bi * kBM <= bj * kBN + kBN - 1) out[t++] = make_int2((int)bi, (int)bj);
+}
+
+// Device address of the scratch array for the current device; the first call on
+// a device looks it up (cudaGetSymbolAddress with that device current).
+cudaError_t noalloc_base(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
 }  // namespace hpc
+
+extern "C" int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* S, int64_t lds,
+                                int precision, void* cuda_stream) {
+    using namespace hpc;
+    if (!X || !S || n < 1 || p < 1 || lds < p || (xdt != HPC_F32 && xdt != HPC_BF16)) return HPC_ERR_ARG;
+    if (precision == HPC_PREC_AUTO) precision = HPC_PREC_BF16X3;
+    if (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32) return HPC_ERR_ARG;
+    const size_t need = gram_tc_scratch_bytes(xdt, n, p, precision);
+    if (need > kNoAllocScratchBytes) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg,
+                      "hpc_gram_noalloc: n=%lld p=%lld needs %zu bytes of scratch; the static scratch holds %zu",
+                      (long long)n, (long long)p, need, kNoAllocScratchBytes);
+        set_last_error(msg);
+        return HPC_ERR_ARG;
+    }
+    if (!encode_fn()) return HPC_ERR_NOT_IMPLEMENTED;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    void* base_v = nullptr;
+    cudaError_t e = noalloc_base(&base_v);
+    if (e != cudaSuccess) {
+        set_last_error("hpc_gram_noalloc: cudaGetSymbolAddress of the static scratch failed");
+        return HPC_ERR_CUDA;
+    }
+    const int mode = mode_of(xdt, precision);
+    const Geometry g = geometry(xdt, n, p, precision);
+    uint8_t* base = static_cast<uint8_t*>(base_v);
+    void* hi = base;
+    void* lo = g.pieces > 1 ? base + g.panel_bytes : nullptr;
+    int2* tiles = reinterpret_cast<int2*>(base + g.pieces * g.panel_bytes);
+    k_tile_order<<<1, 1, 0, s>>>(tiles, g.p_pad);
+    if (xdt == HPC_BF16) launch_prep<__nv_bfloat16>(X, mode, n, p, hi, lo, g, s);
+    else launch_prep<float>(X, mode, n, p, hi, lo, g, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        if (mode == kModeBf16) e = launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s);
+        else if (mode == kModeBf16x3) e = launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s);
+        else e = launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s);
+    }
+    if (e == cudaErrorNotSupported) return HPC_ERR_NOT_IMPLEMENTED;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg, "hpc_gram_noalloc: %s", cudaGetErrorString(e));
+        set_last_error(msg);
+        return HPC_ERR_CUDA;
+    }
+    if (gram_tc_take_error() != 0) return HPC_ERR_DEVICE_TIMEOUT;
+    return HPC_OK;
+}

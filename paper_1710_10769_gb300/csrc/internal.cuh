@@ -123,4 +123,7 @@ size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();
 
+// Set the text returned by hpc_last_error() for this thread (api.cu).
+void set_last_error(const char* msg);
+
 }  // namespace hpc
