@@ -157,6 +157,34 @@ int hpc_set_omega(hpc_handle h, int64_t nnz, const int64_t* row_ptr, const int32
 /* Change lambda1, lambda2 (>= 0) keeping S and the current iterate (warm start). */
 int hpc_set_lambda(hpc_handle h, double lambda1, double lambda2);
 
+/* One point of a regularisation path. */
+typedef struct {
+    double  lambda1;
+    int64_t iterations;       /* outer iterations of this point's solve          */
+    int64_t ls_trials;
+    int64_t nnz;              /* entries of the estimate (both triangles + diag) */
+    int32_t status;           /* HPC_OK, HPC_NOT_CONVERGED or an error           */
+    int32_t pad_;
+    double  f, F;             /* at the last gradient pass of the solve          */
+    double  rel_change;
+    double  ms;               /* device time of this point's solve               */
+} hpc_path_point;
+
+/* Solve along a grid of lambda1 values at fixed lambda2 -- the grids of tuning
+ * parameters that cross-validation and stability selection need (Section 2,
+ * "Key bottlenecks") -- in the given order, each solve warm-started from the
+ * previous estimate (the first from the current iterate).  Descending lambda1
+ * (sparse to dense) keeps warm starts close.  The minimiser is unique for
+ * lambda2 > 0, so a warm start changes the path taken, not the estimate.
+ * points (host, k entries) receives per-point results.  If row_ptr != NULL the
+ * estimates are returned too (host arrays): row_ptr holds k*(p+1) offsets, point
+ * t's at row_ptr + t*(p+1), each relative to that point's first entry; col/val
+ * (FP32) receive the points' entries back to back, capacity *cap_inout entries,
+ * total written on return.  Stops at the first point that returns an error
+ * (its status says which); HPC_ERR_CAPACITY if col/val are too short. */
+int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
+                   int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout);
+
 /* Read m entries S_{rows[t], cols[t]} of the Cov sample covariance into out
  * (FP64, host arrays).  For checking the Gram at sizes where S is too large to
  * copy.  HPC_ERR_ARG for an index outside [0, p) or for the Obs variant. */
@@ -187,6 +215,49 @@ typedef struct {
 
 /* Fill *info for handle h. */
 int hpc_get_info(hpc_handle h, hpc_info* info);
+
+/* ---------------------------------------------------------------- differentiation */
+
+/* Smooth part f(Omega) = -sum log w_ii + tr(Omega S Omega)/2 + lambda2/2 ||Omega||_F^2 at the
+ * current iterate (the loss whose gradients hpc_backward returns), into *f (host). */
+int hpc_smooth_value(hpc_handle h, double* f);
+
+/* Gradients of L(Omega, X) = f(Omega; S = X^T X / n) at the current (symmetric)
+ * iterate, times grad_loss (the upstream derivative of a scalar loss):
+ *   dOmega = grad_loss * ( -diag(1/w_ii) + (Omega S + S Omega)/2 + lambda2 Omega )
+ *            -- Alg. 1 step 4's G, dense p x ld_domega, bitwise equal to the
+ *            solver's G on its candidate entries when grad_loss = 1;
+ *   dX     = grad_loss * X Omega^2 / n   (= Y Omega / n with Y = X Omega), n x p.
+ * At a non-symmetric Omega the general forms are (Omega^T S + S Omega^T)/2 and
+ * (X Omega Omega + X Omega^T Omega^T)/(2n); the iterate is always symmetric.
+ * X: the device data (n x p, dtype xdt) the handle was loaded with; needed only
+ * for dX.  dOmega, dX: device buffers in the handle's value dtype (FP32, or
+ * FP64 for FP64 handles); either may be NULL.  Allocates scratch on first use. */
+int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, void* dOmega, int64_t ld_domega,
+                 void* dX);
+
+typedef struct {
+    int64_t cg_iterations;
+    double  rel_residual;     /* ||r|| / ||b|| of the CG solve                     */
+    int64_t support;          /* |A|, entries of the estimate (both triangles)     */
+    int32_t converged;        /* rel_residual <= cg_tol reached                    */
+    int32_t pad_;
+} hpc_hypergrad_info;
+
+/* Gradient of a held-out loss with respect to (lambda1, lambda2) through the
+ * fixed point of Alg. 1 (the paper motivates grids of tuning parameters for
+ * model selection; this gives their gradient).  With L_val(Omega) = -sum log
+ * w_ii + tr(Omega S_val Omega)/2, S_val = X_val^T X_val / n_val (unpenalised),
+ * and A the support of the current estimate (held fixed: valid while the
+ * support is locally constant in lambda), the implicit function theorem on
+ * G_A(Omega) + lambda1 sign_off(Omega_A) = 0 gives
+ *   dL_val/dlambda1 = -<v, sign_off(Omega_A)>,  dL_val/dlambda2 = -<v, Omega_A>,
+ *   H_A v = grad_A L_val,  H[E] = (E S + S E)/2 + lambda2 E + diag(E_ii / w_ii^2),
+ * solved by conjugate gradients (FP64 vectors, relative residual cg_tol, at
+ * most cg_max_iter iterations).  Xval: device, nval x p.  Returns HPC_OK, or
+ * HPC_NOT_CONVERGED when cg_max_iter was reached (results still written). */
+int hpc_hypergrad(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double cg_tol, int64_t cg_max_iter,
+                  double* dlambda1, double* dlambda2, hpc_hypergrad_info* info);
 
 /* Free the handle and all device memory it owns.  NULL is accepted. */
 int hpc_destroy(hpc_handle h);

@@ -282,3 +282,127 @@ def smooth_sparse_from_S(S, omega_csr: sp.csr_matrix, lam2) -> float:
     W = om @ S
     tr = float(np.sum(om.multiply(W)))
     return -float(np.sum(np.log(d))) + 0.5 * tr + 0.5 * lam2 * float(om.multiply(om).sum())
+
+
+# ----------------------------------------------------------------- differentiation
+
+def smooth_loss(X, Omega, lam2):
+    """L(Omega, X) = -sum log w_ii + tr(Omega S Omega)/2 + lam2/2 ||Omega||_F^2 with S = X^T X / n:
+    the smooth part of the objective under the scaling reading, as a function of both inputs."""
+    X = np.asarray(X, dtype=np.float64)
+    S = gram(X)
+    d = np.diag(Omega)
+    return -np.sum(np.log(d)) + 0.5 * np.trace(Omega @ S @ Omega) + 0.5 * lam2 * np.sum(Omega * Omega)
+
+
+def smooth_loss_grads(X, Omega, lam2):
+    """(dL/dOmega, dL/dX) of smooth_loss for any square Omega with a positive diagonal.
+
+    d tr(Omega S Omega) = <dOmega, Omega^T S + S Omega^T> gives
+        dL/dOmega = -diag(1/w_ii) + (Omega^T S + S Omega^T)/2 + lam2 Omega;
+    tr(Omega X^T X Omega) / (2n) differentiates to
+        dL/dX = (X Omega Omega + X Omega^T Omega^T) / (2n),
+    which at a symmetric Omega are Alg. 1's G and Y Omega / n with Y = X Omega.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    S = gram(X)
+    dOm = 0.5 * (Omega.T @ S + S @ Omega.T) + lam2 * Omega
+    dOm[np.diag_indices_from(dOm)] -= 1.0 / np.diag(Omega)
+    dX = (X @ Omega @ Omega + X @ Omega.T @ Omega.T) / (2.0 * n)
+    return dOm, dX
+
+
+def heldout_loss(S_val, Omega):
+    """L_val(Omega) = -sum log w_ii + tr(Omega S_val Omega)/2: the unpenalised pseudolikelihood loss on
+    held-out data (the model-selection criterion differentiated by hypergrad)."""
+    d = np.diag(Omega)
+    return -np.sum(np.log(d)) + 0.5 * np.sum((Omega @ S_val) * Omega.T)
+
+
+def hypergrad(S, S_val, Omega, lam1, lam2):
+    """(dL_val/dlambda1, dL_val/dlambda2) at the estimate Omega(lambda) by the implicit function theorem.
+
+    On the support A of Omega (both triangles and the diagonal) the fixed point of Alg. 1 satisfies
+    G_ij(Omega) + lambda1 s_ij = 0 with s_ij = sign(w_ij) off the diagonal and 0 on it.  With A held
+    fixed, d/dlambda of that system gives H_A[dOmega/dlambda1] = -s and H_A[dOmega/dlambda2] = -Omega_A,
+    where H_A is the Hessian of the smooth part restricted to symmetric matrices supported on A,
+        H[E] = (E S + S E)/2 + lambda2 E + diag(E_ii / w_ii^2),
+    so dL_val/dlambda = <grad L_val, dOmega/dlambda> with grad L_val = -diag(1/w) + (Omega S_val + S_val Omega)/2.
+    H_A is formed explicitly on the unique pairs i <= j of A and solved densely: small p only.
+    """
+    p = S.shape[0]
+    iu, ju = np.nonzero(np.triu(Omega != 0.0))
+    m = iu.size
+    idx = {(int(i), int(j)): t for t, (i, j) in enumerate(zip(iu, ju))}
+    d = np.diag(Omega)
+    Hm = np.zeros((m, m))
+    for t, (a, b) in enumerate(zip(iu, ju)):
+        E = np.zeros((p, p))
+        E[a, b] = E[b, a] = 1.0
+        HE = 0.5 * (E @ S + S @ E) + lam2 * E
+        HE[np.diag_indices(p)] += np.diag(E) / d ** 2
+        Hm[:, t] = HE[iu, ju]
+    gval = 0.5 * (Omega @ S_val + S_val @ Omega)
+    gval[np.diag_indices(p)] -= 1.0 / d
+    v = np.linalg.solve(Hm, gval[iu, ju])
+    w = np.where(iu == ju, 1.0, 2.0)          # full-entry inner product on symmetric matrices
+    s = np.where(iu == ju, 0.0, np.sign(Omega[iu, ju]))
+    return float(-np.sum(w * v * s)), float(-np.sum(w * v * Omega[iu, ju]))
+
+
+def hypergrad_sparse(X, Xval, omega_csr: sp.csr_matrix, lam1, lam2):
+    """hypergrad() at a sparse estimate for large p: the same implicit-function gradient, with
+    H_A assembled as a sparse matrix on the unique pairs (i <= j) of the support and every S
+    and S_val entry it needs formed from X and X_val in FP64 (gram_entries).  Returns
+    (dL_val/dlambda1, dL_val/dlambda2)."""
+    import scipy.sparse.linalg as spla
+
+    om = sp.csr_matrix(omega_csr, dtype=np.float64)
+    om.sort_indices()
+    p = om.shape[0]
+    rows = np.repeat(np.arange(p), np.diff(om.indptr))
+    cols = om.indices
+    vals = om.data
+    up = rows <= cols
+    U = list(zip(rows[up].tolist(), cols[up].tolist()))
+    uid = {u: t for t, u in enumerate(U)}
+    supp = [om.indices[om.indptr[i]:om.indptr[i + 1]] for i in range(p)]
+    wrow = [om.data[om.indptr[i]:om.indptr[i + 1]] for i in range(p)]
+    diag = om.diagonal()
+    # every S entry (k, j) with k, j in the support of one row
+    need_k, need_j = [], []
+    for i in range(p):
+        for k in supp[i]:
+            for j in supp[i]:
+                need_k.append(k)
+                need_j.append(j)
+    need_k = np.asarray(need_k, np.int64)
+    need_j = np.asarray(need_j, np.int64)
+    Sv = dict(zip(zip(need_k.tolist(), need_j.tolist()), gram_entries(X, need_k, need_j).tolist()))
+    Svv = dict(zip(zip(need_k.tolist(), need_j.tolist()), gram_entries(Xval, need_k, need_j).tolist()))
+
+    def key(a, b):
+        return uid[(a, b) if a <= b else (b, a)]
+
+    # H on U: H[E]_ij = ((E S)_ij + (E S)_ji)/2 + lambda2 E_ij + [i=j] E_ii / w_ii^2,
+    # (E S)_ij = sum_{k in supp(i)} E_ik S_kj with E symmetric on the support
+    r_, c_, v_ = [], [], []
+    for t, (i, j) in enumerate(U):
+        for k in supp[i]:
+            r_.append(t); c_.append(key(i, k)); v_.append(0.5 * Sv[(k, j)])
+        for k in supp[j]:
+            r_.append(t); c_.append(key(j, k)); v_.append(0.5 * Sv[(k, i)])
+        r_.append(t); c_.append(t); v_.append(lam2 + (1.0 / diag[i] ** 2 if i == j else 0.0))
+    H = sp.csr_matrix((v_, (r_, c_)), shape=(len(U), len(U)))
+    # gradient of L_val on U
+    b = np.empty(len(U))
+    for t, (i, j) in enumerate(U):
+        a1 = sum(w * Svv[(k, j)] for k, w in zip(supp[i], wrow[i]))
+        a2 = sum(w * Svv[(k, i)] for k, w in zip(supp[j], wrow[j]))
+        b[t] = 0.5 * (a1 + a2) - (1.0 / diag[i] if i == j else 0.0)
+    v = spla.spsolve(H.tocsc(), b)
+    wgt = np.array([1.0 if i == j else 2.0 for i, j in U])
+    om_u = np.array([om[i, j] for i, j in U])
+    s_u = np.where(np.array([i == j for i, j in U]), 0.0, np.sign(om_u))
+    return float(-np.sum(wgt * v * s_u)), float(-np.sum(wgt * v * om_u))

@@ -53,6 +53,23 @@ class Info(C.Structure):
 PRECISION_NAMES = {PREC_FP64: "fp64", PREC_FP32: "fp32", PREC_BF16X3: "bf16x3", PREC_TF32: "tf32"}
 
 
+class PathPoint(C.Structure):
+    _fields_ = [("lambda1", C.c_double), ("iterations", C.c_int64), ("ls_trials", C.c_int64), ("nnz", C.c_int64),
+                ("status", C.c_int32), ("pad_", C.c_int32), ("f", C.c_double), ("F", C.c_double),
+                ("rel_change", C.c_double), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class HypergradInfo(C.Structure):
+    _fields_ = [("cg_iterations", C.c_int64), ("rel_residual", C.c_double), ("support", C.c_int64),
+                ("converged", C.c_int32), ("pad_", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
 class HpcError(RuntimeError):
     def __init__(self, status, where):
         lib = load()
@@ -75,9 +92,14 @@ _SIGS = {
     "hpc_get_omega": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int, C.c_int]),
     "hpc_set_omega": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int]),
     "hpc_set_lambda": (C.c_int, [_P, C.c_double, C.c_double]),
+    "hpc_solve_path": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "hpc_get_s_entries": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "hpc_get_candidates": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P]),
     "hpc_get_info": (C.c_int, [_P, C.POINTER(Info)]),
+    "hpc_smooth_value": (C.c_int, [_P, C.POINTER(C.c_double)]),
+    "hpc_backward": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, C.c_int64, _P]),
+    "hpc_hypergrad": (C.c_int, [_P, _P, C.c_int, C.c_int64, C.c_double, C.c_int64, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.POINTER(HypergradInfo)]),
     "hpc_destroy": (C.c_int, [_P]),
     "hpc_gram": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "hpc_gram_noalloc": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int64, C.c_int, _P]),
@@ -274,6 +296,80 @@ class Solver:
     def set_lambda(self, lambda1, lambda2):
         return _check(self._lib.hpc_set_lambda(self._h, float(lambda1), float(lambda2)), "hpc_set_lambda")
 
+    def solve_path(self, lambda1s, lambda2, return_estimates=True, capacity=None):
+        """Warm-started path over lambda1s (``hpc_solve_path``): (points, [Csr per point])."""
+        lam = np.ascontiguousarray(lambda1s, dtype=np.float64)
+        k = lam.size
+        pts = (PathPoint * max(k, 1))()
+        if not return_estimates:
+            st = self._lib.hpc_solve_path(self._h, lam.ctypes.data_as(C.c_void_p), k, float(lambda2), pts,
+                                          None, None, None, None)
+            _check(st, "hpc_solve_path", (OK, NOT_CONVERGED))
+            return [pts[t].as_dict() for t in range(k)], None
+        cap = capacity or max(64 * self.p * k, 1024)
+        while True:
+            rp = np.empty(k * (self.p + 1), np.int64)
+            ci = np.empty(cap, np.int32)
+            v = np.empty(cap, np.float32)
+            c = C.c_int64(cap)
+            st = self._lib.hpc_solve_path(self._h, lam.ctypes.data_as(C.c_void_p), k, float(lambda2), pts,
+                                          rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
+                                          v.ctypes.data_as(C.c_void_p), C.byref(c))
+            if st == ERR_CAPACITY and c.value > cap:
+                raise HpcError(st, "hpc_solve_path (output capacity %d < %d)" % (cap, c.value))
+            _check(st, "hpc_solve_path", (OK, NOT_CONVERGED))
+            break
+        out, off = [], 0
+        for t in range(k):
+            r = rp[t * (self.p + 1):(t + 1) * (self.p + 1)]
+            m = int(r[-1])
+            out.append(Csr(r.copy(), ci[off:off + m].copy(), v[off:off + m].astype(np.float64)))
+            off += m
+        return [pts[t].as_dict() for t in range(k)], out
+
+    # ------------------------------------------------------------ differentiation
+    def smooth_value(self) -> float:
+        """f(Omega) at the current estimate (``hpc_smooth_value``)."""
+        f = C.c_double(0.0)
+        _check(self._lib.hpc_smooth_value(self._h, C.byref(f)), "hpc_smooth_value")
+        return f.value
+
+    def backward(self, X, grad_loss=1.0, domega=True, dx=True):
+        """(dL/dOmega dense (p, p), dL/dX (n, p)) times grad_loss at the current estimate
+        (``hpc_backward``); X is the device data the solver was loaded with."""
+        import torch
+
+        dt = torch.float64 if self.info().value_dtype == F64 else torch.float32
+        dO = torch.empty((self.p, self.p), dtype=dt, device=X.device) if domega else None
+        dX = torch.empty((self.n, self.p), dtype=dt, device=X.device) if dx else None
+        st = self._lib.hpc_backward(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), float(grad_loss),
+                                    C.c_void_p(dO.data_ptr()) if dO is not None else None,
+                                    dO.stride(0) if dO is not None else self.p,
+                                    C.c_void_p(dX.data_ptr()) if dX is not None else None)
+        _check(st, "hpc_backward")
+        return dO, dX
+
+    def hypergrad(self, Xval, tol=1e-8, max_iter=20000):
+        """(dL_val/dlambda1, dL_val/dlambda2, info) at the current estimate (``hpc_hypergrad``)."""
+        d1, d2 = C.c_double(0.0), C.c_double(0.0)
+        inf = HypergradInfo()
+        st = self._lib.hpc_hypergrad(self._h, C.c_void_p(Xval.data_ptr()), _dtype_code(Xval), Xval.shape[0],
+                                     float(tol), int(max_iter), C.byref(d1), C.byref(d2), C.byref(inf))
+        _check(st, "hpc_hypergrad", (OK, NOT_CONVERGED))
+        return d1.value, d2.value, inf.as_dict()
+
+    def omega_values(self, device="cuda", dtype=None):
+        """The estimate's CSR (row_ptr, col, val) as device tensors (``hpc_get_omega`` on device)."""
+        import torch
+
+        m = self.nnz()
+        dt = dtype or (torch.float64 if self.info().value_dtype == F64 else torch.float32)
+        rp = torch.empty(self.p + 1, dtype=torch.int64, device=device)
+        ci = torch.empty(max(m, 1), dtype=torch.int32, device=device)
+        v = torch.empty(max(m, 1), dtype=dt, device=device)
+        self.get_omega_device(rp, ci, v)
+        return rp, ci[:m], v[:m]
+
     def s_entries(self, rows, cols) -> np.ndarray:
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         cols = np.ascontiguousarray(cols, dtype=np.int64)
@@ -316,3 +412,56 @@ def gram_noalloc(X, S, precision=PREC_AUTO, stream=None):
     st = load().hpc_gram_noalloc(C.c_void_p(X.data_ptr()), _dtype_code(X), n, p, C.c_void_p(S.data_ptr()),
                                  S.stride(0), precision, _stream_ptr(stream))
     return _check(st, "hpc_gram_noalloc")
+
+
+def _make_smooth_loss():
+    import torch
+
+    class ConcordSmoothLoss(torch.autograd.Function):
+        """L(Omega, X) = -sum log w_ii + tr(Omega S Omega)/2 + lambda2/2 ||Omega||_F^2, S = X^T X / n,
+        at a solver's current estimate, with the library's adjoint as backward.
+
+        Inputs: X (n, p) device tensor the solver was loaded with; omega, the estimate as either its
+        CSR values (nnz,) from Solver.omega_values() or a dense (p, p) tensor; the solver.  The
+        forward value is computed by the library at the solver's estimate (omega only carries the
+        gradient).  Backward returns dL/dX and dL/dOmega (dense, or gathered on the support for the
+        CSR-values form), both from hpc_backward."""
+
+        @staticmethod
+        def forward(ctx, X, omega, solver):
+            ctx.solver = solver
+            ctx.save_for_backward(X)
+            ctx.omega_shape = tuple(omega.shape)
+            ctx.omega_dtype = omega.dtype
+            return torch.tensor(solver.smooth_value(), dtype=torch.float64, device=X.device)
+
+        @staticmethod
+        def backward(ctx, gL):
+            (X,) = ctx.saved_tensors
+            s = ctx.solver
+            want_o, want_x = ctx.needs_input_grad[1], ctx.needs_input_grad[0]
+            dO, dX = s.backward(X, float(gL), domega=want_o, dx=want_x)
+            g_om = None
+            if want_o:
+                if ctx.omega_shape == (s.p, s.p):
+                    g_om = dO.to(ctx.omega_dtype)
+                else:
+                    rp, ci, _ = s.omega_values(device=X.device)
+                    rows = torch.repeat_interleave(torch.arange(s.p, device=X.device), rp[1:] - rp[:-1])
+                    g_om = dO[rows, ci.long()].to(ctx.omega_dtype)
+            if want_x:
+                dX = dX.to(X.dtype)
+            return dX, g_om, None
+
+    return ConcordSmoothLoss
+
+
+_SMOOTH_LOSS = None
+
+
+def concord_smooth_loss(X, omega, solver):
+    """Autograd entry point of the smooth CONCORD loss (see ConcordSmoothLoss)."""
+    global _SMOOTH_LOSS
+    if _SMOOTH_LOSS is None:
+        _SMOOTH_LOSS = _make_smooth_loss()
+    return _SMOOTH_LOSS.apply(X, omega, solver)

@@ -8,9 +8,11 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace {
 
@@ -86,6 +88,12 @@ struct hpc_ctx {
     int nblk = 0;
     hpc::Ctrl* d_ctrl = nullptr;
     hpc::Ctrl* h_ctrl = nullptr;    // pinned
+    // screening pass: TMA descriptor of S, per-row set-up, persistent grid size
+    CUtensorMap smap;
+    int4* rinfo = nullptr;
+    int* offlist = nullptr;
+    void* rdv = nullptr;
+    int num_sms = 0;
     // scratch for the tensor-core Gram
     void* gram_scratch = nullptr;
     size_t gram_scratch_bytes = 0;
@@ -94,6 +102,18 @@ struct hpc_ctx {
     cudaEvent_t ev_scr0 = nullptr, ev_scr1 = nullptr;
     int64_t regrows = 0;
     double ms_gram = 0.0;
+    // differentiation scratch (grown on demand)
+    void* adj_buf = nullptr;
+    size_t adj_bytes = 0;
+    // Obs variant (Alg. 3): X^T and Y^T in FP32 (p x ldx), their MMA panels, tile pairs
+    float* xt = nullptr;
+    float* yt = nullptr;
+    int64_t ldx = 0;
+    void* xp[2] = {nullptr, nullptr};
+    void* yp[2] = {nullptr, nullptr};
+    int2* pairs = nullptr;
+    int64_t npairs = 0;
+    CUtensorMap obs_maps[4];
 };
 
 namespace {
@@ -185,6 +205,14 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.eps = h->opt.eps;
     b.max_halvings = h->opt.max_halvings;
     b.ls_window = h->opt.ls_window;
+    b.smap = &h->smap;
+    b.rinfo = h->rinfo;
+    b.offlist = h->offlist;
+    b.rdv = as<T>(h->rdv);
+    b.num_sms = h->num_sms;
+    b.xt = h->xt;
+    b.ldx = h->ldx;
+    b.n = h->n;
     return b;
 }
 
@@ -197,6 +225,7 @@ int read_ctrl(hpc_ctx* h) {
 int flags_to_status(int flags) {
     if (flags & hpc::kFlagNaN) return HPC_ERR_NAN;
     if (flags & hpc::kFlagLsFail) return HPC_ERR_LS_FAIL;
+    if (flags & hpc::kFlagTimeout) return HPC_ERR_DEVICE_TIMEOUT;
     if (flags & hpc::kFlagBadStructure) return HPC_ERR_CUDA;
     return HPC_OK;
 }
@@ -218,6 +247,20 @@ int regrow(hpc_ctx* h, int64_t need) {
     return HPC_OK;
 }
 
+// Obs (Alg. 3 steps 2, 4-6): Y^T = Omega X^T, its MMA panels, and the paired-tile
+// Z GEMM with the screening emission.
+int obs_screen(hpc_ctx* h, const hpc::IterBufs<float>& b) {
+    const int p = (int)h->p;
+    hpc::launch_row_info<float>(p, b.cur, h->rinfo, as<float>(h->rdv), h->stream);
+    hpc::launch_spmm_dense<float>(p, b.cur, h->rinfo, as<float>(h->rdv), h->xt, h->ldx, h->ldx, h->yt, h->ldx,
+                                  h->stream);
+    hpc::launch_obs_split(h->precision, h->yt, p, h->ldx, h->ldx, h->yp[0], h->yp[1], h->n, h->p, h->stream);
+    cudaError_t e = hpc::launch_obs_pairs(h->precision, h->obs_maps, h->pairs, h->npairs, h->n, p, b.cur.rp, b.cur.ci,
+                                          b.cur.cv, (float)h->lam1, b.em, h->d_ctrl, h->stream);
+    if (e != cudaSuccess) { set_cuda_error(e, "obs pair GEMM", __LINE__); return HPC_ERR_CUDA; }
+    return HPC_OK;
+}
+
 // One outer iteration.  *done is set when the stopping rule holds.
 template <typename T>
 int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
@@ -225,14 +268,24 @@ int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
         hpc::IterBufs<T> b = bufs<T>(h);
         hpc::launch_iter_begin<T>(b, h->stream);
         if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_scr0, h->stream));
-        hpc::launch_grad_screen<T>(b, h->stream);
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->variant == HPC_OBS) STATUS_TRY(obs_screen(h, b));
+            else hpc::launch_grad_screen<T>(b, h->stream);
+        } else {
+            hpc::launch_grad_screen<T>(b, h->stream);
+        }
         if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_scr1, h->stream));
         hpc::launch_candidates<T>(b, h->stream);
         CUDA_TRY(cudaGetLastError());
         int launches = hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesCandidates;
         bool accepted = false, overflow = false;
         for (int hb = 0; hb <= h->opt.max_halvings; hb += h->opt.ls_window) {
-            hpc::launch_ls_window<T>(b, hb, hb == 0, h->stream);
+            if constexpr (std::is_same<T, float>::value) {
+                if (h->variant == HPC_OBS) hpc::launch_ls_window_obs(b, hb, hb == 0, h->stream);
+                else hpc::launch_ls_window<T>(b, hb, hb == 0, h->stream);
+            } else {
+                hpc::launch_ls_window<T>(b, hb, hb == 0, h->stream);
+            }
             CUDA_TRY(cudaGetLastError());
             launches += hpc::kLaunchesLsWindow;
             STATUS_TRY(read_ctrl(h));
@@ -324,6 +377,12 @@ int run_iterations(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* st) {
     return status;
 }
 
+int load_x_obs(hpc_ctx* h, const void* Xd) {
+    // X^T (p x ldx, FP32, zero padded) and its MMA panels
+    CUDA_TRY(cudaMemsetAsync(h->xt, 0, (size_t)h->p * h->ldx * sizeof(float), h->stream));
+    return HPC_OK;
+}
+
 int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
     const void* Xd = X;
     void* tmp = nullptr;
@@ -337,7 +396,12 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
     if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
     cudaError_t e;
     int prec = h->precision;
-    if (prec == HPC_PREC_FP64 || prec == HPC_PREC_FP32) {
+    if (h->variant == HPC_OBS) {
+        STATUS_TRY(load_x_obs(h, Xd));
+        hpc::launch_transpose(Xd, xdt, h->n, h->p, h->p, h->xt, HPC_F32, h->ldx, 1.0f, h->stream);
+        hpc::launch_obs_split(prec, h->xt, h->p, h->ldx, h->ldx, h->xp[0], h->xp[1], h->n, h->p, h->stream);
+        e = cudaGetLastError();
+    } else if (prec == HPC_PREC_FP64 || prec == HPC_PREC_FP32) {
         e = hpc::gram_simt(Xd, xdt, h->n, h->p, h->S, h->vdt, h->ld, h->stream, &launches);
     } else {
         const size_t need = hpc::gram_tc_scratch_bytes(xdt, h->n, h->p, prec);
@@ -392,7 +456,9 @@ void destroy(hpc_ctx* h) {
     cudaStreamSynchronize(h->stream);
     free_candidates(h);
     void* ptrs[] = {h->S, h->rp[0], h->rp[1], h->ci[0], h->ci[1], h->cv[0], h->cv[1], h->bk_cnt, h->bk_off,
-                    h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch};
+                    h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
+                    h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
+                    h->yp[0], h->yp[1], h->pairs};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -453,12 +519,14 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         !(o.ls_window == 1 || o.ls_window == 2 || o.ls_window == 4 || o.ls_window == 8 || o.ls_window == 16) ||
         o.precision < HPC_PREC_AUTO || o.precision > HPC_PREC_TF32)
         return HPC_ERR_ARG;
-    if (variant != HPC_COV) {
-        std::snprintf(g_last_error, sizeof g_last_error, "variant %d not built", (int)variant);
-        return HPC_ERR_NOT_IMPLEMENTED;
-    }
+    if (variant != HPC_COV && variant != HPC_OBS) return HPC_ERR_ARG;
     int prec = o.precision;
     if (prec == HPC_PREC_AUTO) prec = (o.value_dtype == HPC_F64) ? HPC_PREC_FP64 : HPC_PREC_BF16X3;
+    if (variant == HPC_OBS && (o.value_dtype != HPC_F32 || (prec != HPC_PREC_BF16X3 && prec != HPC_PREC_TF32))) {
+        std::snprintf(g_last_error, sizeof g_last_error,
+                      "the Obs variant runs its Z product on tensor cores: FP32 values with BF16X3 or TF32");
+        return HPC_ERR_NOT_IMPLEMENTED;
+    }
     if (prec == HPC_PREC_FP64 && o.value_dtype != HPC_F64) return HPC_ERR_ARG;
     if (o.value_dtype == HPC_F64 && prec != HPC_PREC_FP64) return HPC_ERR_ARG;
 
@@ -477,8 +545,46 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     };
 #define CK(expr) do { int s_ = cu((expr), #expr, __LINE__); if (s_ != HPC_OK) return fail(s_); } while (0)
     const size_t vs = dtype_size(h->vdt);
+    {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if (variant == HPC_OBS) {
+        h->ldx = (n + 63) / 64 * 64;
+        CK(cudaMalloc(&h->xt, (size_t)p * h->ldx * sizeof(float)));
+        CK(cudaMalloc(&h->yt, (size_t)p * h->ldx * sizeof(float)));
+        const size_t pb = hpc::obs_panel_bytes(prec, n, p);
+        for (int t = 0; t < hpc::obs_pieces(prec); ++t) {
+            CK(cudaMalloc(&h->xp[t], pb));
+            CK(cudaMalloc(&h->yp[t], pb));
+        }
+        std::vector<int2> pl;
+        hpc::obs_pair_list(p, pl);
+        h->npairs = (int64_t)pl.size();
+        CK(cudaMalloc(&h->pairs, pl.size() * sizeof(int2)));
+        CK(cudaMemcpy(h->pairs, pl.data(), pl.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        if (!hpc::obs_make_maps(prec, h->yp[0], h->yp[1], h->xp[0], h->xp[1], n, p, h->obs_maps)) {
+            std::snprintf(g_last_error, sizeof g_last_error, "TMA descriptors of the Obs panels could not be encoded");
+            return fail(HPC_ERR_NOT_IMPLEMENTED);
+        }
+    }
+    if (variant == HPC_COV) {
     CK(cudaMalloc(&h->S, (size_t)p * h->ld * vs));
     CK(cudaMemsetAsync(h->S, 0, (size_t)p * h->ld * vs, h->stream));
+    }
+    if (variant == HPC_COV) {
+        const int box_cols = h->vdt == HPC_F64 ? hpc::screen_box_cols<double>() : hpc::screen_box_cols<float>();
+        std::memset(&h->smap, 0, sizeof h->smap);
+        if (!hpc::encode_tensor_map_2d(&h->smap, h->S, (int)vs, (uint64_t)h->ld, (uint64_t)p, (uint64_t)h->ld * vs,
+                                       (uint32_t)box_cols, (uint32_t)hpc::kScreenBoxRows)) {
+            std::snprintf(g_last_error, sizeof g_last_error, "TMA descriptor of S could not be encoded");
+            return fail(HPC_ERR_NOT_IMPLEMENTED);
+        }
+    }
+    CK(cudaMalloc(&h->rinfo, p * sizeof(int4)));
+    CK(cudaMalloc(&h->offlist, p * sizeof(int)));
+    CK(cudaMalloc(&h->rdv, p * vs));
     for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->rp[b], (p + 1) * sizeof(int)));
     const int64_t cap0 = o.capacity > 0 ? o.capacity : std::max<int64_t>(32 * p, 1024);
     {
@@ -492,7 +598,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     CK(cudaMalloc(&h->bk_cur, p * sizeof(int)));
     CK(cudaMalloc(&h->bk_len, p * sizeof(int)));
     CK(cudaMalloc(&h->cnt2, p * sizeof(int)));
-    h->nblk = (int)std::min<int64_t>((p + 7) / 8, 152 * 4);
+    h->nblk = (int)std::min<int64_t>((p + 7) / 8, 152 * 16);
     CK(cudaMalloc(&h->part_obj, (size_t)h->nblk * 4 * sizeof(double)));
     CK(cudaMalloc(&h->part_ls, (size_t)h->nblk * 16 * 4 * sizeof(double)));
     CK(cudaMalloc(&h->d_ctrl, sizeof(hpc::Ctrl)));
@@ -622,6 +728,45 @@ int hpc_set_omega(hpc_handle h, int64_t nnz, const int64_t* row_ptr, const int32
     return HPC_OK;
 }
 
+int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
+                   int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout) {
+    if (!h || !h->loaded || k < 0 || (k > 0 && (!lambda1 || !points)) || !(lambda2 >= 0.0)) return HPC_ERR_ARG;
+    if (row_ptr && (!col || !val || !cap_inout)) return HPC_ERR_ARG;
+    for (int64_t t = 0; t < k; ++t)
+        if (!(lambda1[t] >= 0.0)) return HPC_ERR_ARG;
+    const int64_t cap = row_ptr ? *cap_inout : 0;
+    int64_t used = 0;
+    int status = HPC_OK;
+    for (int64_t t = 0; t < k; ++t) {
+        h->lam1 = lambda1[t];
+        h->lam2 = lambda2;
+        hpc_stats st{};
+        const int r = h->vdt == HPC_F64 ? run_iterations<double>(h, h->opt.max_iter, true, &st)
+                                        : run_iterations<float>(h, h->opt.max_iter, true, &st);
+        hpc_path_point& pt = points[t];
+        std::memset(&pt, 0, sizeof pt);
+        pt.lambda1 = lambda1[t];
+        pt.iterations = st.iterations;
+        pt.ls_trials = st.ls_trials;
+        pt.nnz = h->nnz;
+        pt.status = r;
+        pt.f = st.f;
+        pt.F = st.F;
+        pt.rel_change = st.rel_change;
+        pt.ms = st.ms_total;
+        if (r < 0) { status = r; break; }
+        if (row_ptr) {
+            if (used + h->nnz > cap) { *cap_inout = used + h->nnz; return HPC_ERR_CAPACITY; }
+            int64_t m = cap - used;
+            const int e = hpc_get_omega(h, &m, row_ptr + t * (h->p + 1), col + used, val + used, HPC_F32, 0);
+            if (e != HPC_OK) return e;
+            used += m;
+        }
+    }
+    if (row_ptr) *cap_inout = used;
+    return status;
+}
+
 int hpc_set_lambda(hpc_handle h, double lambda1, double lambda2) {
     if (!h || !(lambda1 >= 0.0) || !(lambda2 >= 0.0)) return HPC_ERR_ARG;
     h->lam1 = lambda1;
@@ -687,6 +832,211 @@ int hpc_get_candidates(hpc_handle h, int64_t* m_inout, int64_t* rows, int64_t* c
             }
     *m_inout = m;
     return HPC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int adj_reserve(hpc_ctx* h, size_t bytes) {
+    if (bytes <= h->adj_bytes) return HPC_OK;
+    if (h->adj_buf) cudaFree(h->adj_buf);
+    h->adj_buf = nullptr;
+    h->adj_bytes = 0;
+    CUDA_TRY(cudaMalloc(&h->adj_buf, bytes));
+    h->adj_bytes = bytes;
+    return HPC_OK;
+}
+
+template <typename T>
+hpc::Csr<T> cur_csr(hpc_ctx* h) { return {h->rp[h->cur], h->ci[h->cur], as<T>(h->cv[h->cur])}; }
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+template <typename T>
+int smooth_value_t(hpc_ctx* h, double* f) {
+    const int p = (int)h->p;
+    const int64_t nnz = h->nnz;
+    const size_t b_v = align256(nnz * sizeof(double));
+    STATUS_TRY(adj_reserve(h, 2 * b_v + align256(1024 * 3 * sizeof(double)) + 256));
+    uint8_t* base = static_cast<uint8_t*>(h->adj_buf);
+    double* om_d = reinterpret_cast<double*>(base);
+    double* Tv = reinterpret_cast<double*>(base + b_v);
+    double* part = reinterpret_cast<double*>(base + 2 * b_v);
+    double* out3 = reinterpret_cast<double*>(base + 2 * b_v + align256(1024 * 3 * sizeof(double)));
+    hpc::Csr<T> om = cur_csr<T>(h);
+    hpc::launch_row_info<T>(p, om, h->rinfo, as<T>(h->rdv), h->stream);
+    hpc::launch_support_vectors<T>(p, nnz, om, om_d, Tv, h->stream);     // Tv used as scratch for signs
+    hpc::launch_support_product<T>(p, om, h->rinfo, om_d, static_cast<const T*>(h->S), h->ld, Tv, h->stream);
+    hpc::launch_smooth_parts<T>(p, om, Tv, part, out3, h->stream);
+    CUDA_TRY(cudaGetLastError());
+    double o[3];
+    CUDA_TRY(cudaMemcpyAsync(o, out3, sizeof o, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *f = -o[2] + 0.5 * o[0] + 0.5 * h->lam2 * o[1];
+    return HPC_OK;
+}
+
+template <typename T>
+int backward_t(hpc_ctx* h, const void* X, int xdt, double grad_loss, void* dOmega, int64_t ld_domega, void* dX) {
+    const int p = (int)h->p;
+    const int64_t n = h->n;
+    hpc::Csr<T> om = cur_csr<T>(h);
+    hpc::launch_row_info<T>(p, om, h->rinfo, as<T>(h->rdv), h->stream);
+    if (dOmega)
+        hpc::launch_dense_grad<T>(p, om, h->rinfo, as<T>(h->rdv), static_cast<const T*>(h->S), h->ld,
+                                  static_cast<T*>(dOmega), ld_domega, (T)h->lam2, (T)grad_loss, h->stream);
+    if (dX) {
+        const size_t plane = align256((size_t)p * n * sizeof(T));
+        STATUS_TRY(adj_reserve(h, 2 * plane));
+        T* xt = static_cast<T*>(h->adj_buf);
+        T* yt = reinterpret_cast<T*>(static_cast<uint8_t*>(h->adj_buf) + plane);
+        const int tdt = sizeof(T) == 8 ? HPC_F64 : HPC_F32;
+        hpc::launch_transpose(X, xdt, n, p, p, xt, tdt, n, 1.0f, h->stream);                 // X^T (p x n)
+        hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), xt, n, n, yt, n, h->stream);  // Y^T = Omega X^T
+        hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), yt, n, n, xt, n, h->stream);  // Omega Y^T
+        hpc::launch_transpose(xt, tdt, p, n, n, dX, tdt, p, (float)(grad_loss / (double)n), h->stream);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return HPC_OK;
+}
+
+template <typename T>
+int hypergrad_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double cg_tol, int64_t cg_max, double* dl1,
+                double* dl2, hpc_hypergrad_info* info) {
+    const int p = (int)h->p;
+    const int64_t nnz = h->nnz;
+    const size_t vs = sizeof(T);
+    const size_t b_s = align256((size_t)p * h->ld * vs);
+    const size_t b_v = align256(nnz * sizeof(double));
+    const size_t b_i = align256(nnz * sizeof(int));
+    const size_t b_p = align256(1024 * sizeof(double));
+    STATUS_TRY(adj_reserve(h, b_s + 8 * b_v + b_i + b_p + 4 * 256));
+    uint8_t* q = static_cast<uint8_t*>(h->adj_buf);
+    T* Sv = reinterpret_cast<T*>(q); q += b_s;
+    double* om_d = reinterpret_cast<double*>(q); q += b_v;
+    double* sgn = reinterpret_cast<double*>(q); q += b_v;
+    double* Tv = reinterpret_cast<double*>(q); q += b_v;
+    double* bvec = reinterpret_cast<double*>(q); q += b_v;
+    double* x = reinterpret_cast<double*>(q); q += b_v;
+    double* r = reinterpret_cast<double*>(q); q += b_v;
+    double* pv = reinterpret_cast<double*>(q); q += b_v;
+    double* Ap = reinterpret_cast<double*>(q); q += b_v;
+    int* tr = reinterpret_cast<int*>(q); q += b_i;
+    double* part = reinterpret_cast<double*>(q); q += b_p;
+    void* cg = q; q += 256;
+    double* out = reinterpret_cast<double*>(q);
+    cudaStream_t s = h->stream;
+    hpc::Csr<T> om = cur_csr<T>(h);
+
+    // S_val = X_val^T X_val / n_val in the handle's precision
+    CUDA_TRY(cudaMemsetAsync(Sv, 0, b_s, s));
+    cudaError_t e;
+    if (h->precision == HPC_PREC_FP64 || h->precision == HPC_PREC_FP32) {
+        e = hpc::gram_simt(Xval, xdt, nval, p, Sv, h->vdt, h->ld, s, nullptr);
+    } else {
+        const size_t need = hpc::gram_tc_scratch_bytes(xdt, nval, p, h->precision);
+        if (need > h->gram_scratch_bytes) {
+            if (h->gram_scratch) cudaFree(h->gram_scratch);
+            h->gram_scratch = nullptr;
+            h->gram_scratch_bytes = 0;
+            CUDA_TRY(cudaMalloc(&h->gram_scratch, need));
+            h->gram_scratch_bytes = need;
+        }
+        e = hpc::gram_tc(Xval, xdt, nval, p, reinterpret_cast<float*>(Sv), h->ld, h->precision, h->gram_scratch,
+                         h->gram_scratch_bytes, s, nullptr);
+    }
+    if (e != cudaSuccess) { set_cuda_error(e, "held-out Gram", __LINE__); return HPC_ERR_CUDA; }
+
+    hpc::launch_row_info<T>(p, om, h->rinfo, as<T>(h->rdv), s);
+    hpc::launch_transpose_index<T>(p, om, tr, s);
+    hpc::launch_support_vectors<T>(p, nnz, om, om_d, sgn, s);
+    // b = gradient of the held-out loss on the support
+    hpc::launch_support_product<T>(p, om, h->rinfo, om_d, Sv, h->ld, Tv, s);
+    hpc::launch_support_combine<T>(p, om, tr, Tv, om_d, h->lam2, 1, bvec, s);
+    // CG on H_A v = b
+    CUDA_TRY(cudaMemsetAsync(x, 0, nnz * sizeof(double), s));
+    CUDA_TRY(cudaMemcpyAsync(r, bvec, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(pv, bvec, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int nb = hpc::cg_part_blocks(nnz);
+    const double tol2 = cg_tol * cg_tol;
+    hpc::launch_dot_part(nnz, r, r, part, s);
+    hpc::launch_cg_scalar(part, nb, 0, tol2, cg, s);
+    int64_t it = 0;
+    int done = 0;
+    for (; it < cg_max; ++it) {
+        hpc::launch_support_product<T>(p, om, h->rinfo, pv, static_cast<const T*>(h->S), h->ld, Tv, s);
+        hpc::launch_support_combine<T>(p, om, tr, Tv, pv, h->lam2, 0, Ap, s);
+        hpc::launch_dot_part(nnz, pv, Ap, part, s);
+        hpc::launch_cg_scalar(part, nb, 1, tol2, cg, s);
+        hpc::launch_cg_xr(nnz, cg, pv, Ap, x, r, s);
+        hpc::launch_dot_part(nnz, r, r, part, s);
+        hpc::launch_cg_scalar(part, nb, 2, tol2, cg, s);
+        hpc::launch_cg_p(nnz, cg, r, pv, s);
+        if ((it & 7) == 7 || it + 1 == cg_max) {
+            CUDA_TRY(cudaGetLastError());
+            int dd = 0;
+            CUDA_TRY(cudaMemcpyAsync(&dd, reinterpret_cast<uint8_t*>(cg) + 5 * sizeof(double), sizeof(int),
+                                     cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (dd) { done = dd; ++it; break; }
+        }
+    }
+    // dL_val/dlambda1 = -<v, sgn_off>, dL_val/dlambda2 = -<v, Omega_A>
+    hpc::launch_dot_part(nnz, x, sgn, part, s);
+    hpc::launch_reduce_parts(part, nb, out, s);
+    hpc::launch_dot_part(nnz, x, om_d, part, s);
+    hpc::launch_reduce_parts(part, nb, out + 1, s);
+    CUDA_TRY(cudaGetLastError());
+    double o[2], st[2];
+    CUDA_TRY(cudaMemcpyAsync(o, out, sizeof o, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(st, cg, sizeof st, cudaMemcpyDeviceToHost, s));   // rr, rr0
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *dl1 = -o[0];
+    *dl2 = -o[1];
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->cg_iterations = it;
+        info->rel_residual = st[1] > 0.0 ? std::sqrt(st[0] / st[1]) : 0.0;
+        info->support = nnz;
+        info->converged = done == 1 ? 1 : 0;
+    }
+    if (done == 2) {
+        std::snprintf(g_last_error, sizeof g_last_error, "CG met a non-positive curvature on the support");
+        return HPC_ERR_NAN;
+    }
+    return done == 1 ? HPC_OK : HPC_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hpc_smooth_value(hpc_handle h, double* f) {
+    if (!h || !h->loaded || !f) return HPC_ERR_ARG;
+    if (!h->S) return HPC_ERR_NOT_IMPLEMENTED;      // needs S (Cov variant)
+    return h->vdt == HPC_F64 ? smooth_value_t<double>(h, f) : smooth_value_t<float>(h, f);
+}
+
+int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, void* dOmega, int64_t ld_domega,
+                 void* dX) {
+    if (!h || !h->loaded || (dX && !X) || (dOmega && ld_domega < h->p) || !valid_dtype(xdt) ||
+        !std::isfinite(grad_loss))
+        return HPC_ERR_ARG;
+    if (!h->S) return HPC_ERR_NOT_IMPLEMENTED;      // needs S (Cov variant)
+    return h->vdt == HPC_F64 ? backward_t<double>(h, X, xdt, grad_loss, dOmega, ld_domega, dX)
+                             : backward_t<float>(h, X, xdt, grad_loss, dOmega, ld_domega, dX);
+}
+
+int hpc_hypergrad(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double cg_tol, int64_t cg_max_iter,
+                  double* dlambda1, double* dlambda2, hpc_hypergrad_info* info) {
+    if (!h || !h->loaded || !Xval || nval < 1 || !valid_dtype(xdt) || !(cg_tol > 0.0) || cg_max_iter < 1 ||
+        !dlambda1 || !dlambda2)
+        return HPC_ERR_ARG;
+    if (!h->S) return HPC_ERR_NOT_IMPLEMENTED;      // needs S (Cov variant)
+    return h->vdt == HPC_F64 ? hypergrad_t<double>(h, Xval, xdt, nval, cg_tol, cg_max_iter, dlambda1, dlambda2, info)
+                             : hypergrad_t<float>(h, Xval, xdt, nval, cg_tol, cg_max_iter, dlambda1, dlambda2, info);
 }
 
 int hpc_get_info(hpc_handle h, hpc_info* info) {

@@ -1,8 +1,10 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 #include "hpconcord.h"
 
@@ -29,6 +31,8 @@ struct Ctrl {
     double delta2;       // ||Omega^{k+1} - Omega^k||_F^2 for the accepted tau
     double rel;          // sqrt(delta2 / norm2_cur)
     long long ls_trials; // accumulated trials (the paper's t)
+    int n_offrows;       // rows of the iterate with off-diagonal entries (screening pass)
+    int pad_;
 };
 
 enum : int {
@@ -38,6 +42,7 @@ enum : int {
     kFlagLsFail = 8,
     kFlagNnzOverflow = 16,
     kFlagBadStructure = 32,
+    kFlagTimeout = 64,      // a bounded device-side wait gave up
 };
 
 // Flags on candidate entries.
@@ -93,6 +98,15 @@ struct IterBufs {
     double eps;
     int max_halvings;
     int ls_window;
+    const CUtensorMap* smap;  // TMA descriptor of S (rows p, columns ld), 64 x BJ boxes
+    int4* rinfo;              // p: CSR bounds, diagonal position, pure-diagonal flag of each row
+    int* offlist;             // p: rows with off-diagonal entries
+    T* rdv;                   // p: diagonal value of each row
+    int num_sms;
+    // Obs variant: X^T (p x ldx, FP32) and n
+    const float* xt;
+    int64_t ldx;
+    int64_t n;
 };
 
 template <typename T> void launch_iter_begin(const IterBufs<T>& b, cudaStream_t s);
@@ -107,11 +121,56 @@ template <typename T> void launch_csr_export(const int* rp, const int* ci, const
 void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int64_t* rows,
                      const int64_t* cols, double* out, cudaStream_t s);
 
-constexpr int kLaunchesScreen = 1;
+constexpr int kLaunchesScreen = 3;
 constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 6;
 constexpr int kLaunchesLsWindow = 2;
 constexpr int kLaunchesAccept = 4;
+
+template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
+void launch_ls_window_obs(const IterBufs<float>& b, int h_base, bool first, cudaStream_t s);
+
+// ---------------------------------------------------------------- Obs variant (obs_tc.cu)
+size_t obs_panel_bytes(int precision, int64_t n, int64_t p);
+int obs_pieces(int precision);
+int64_t obs_npairs(int64_t p);
+void obs_pair_list(int64_t p, std::vector<int2>& out);
+void launch_obs_split(int precision, const float* in, int64_t rows, int64_t cols, int64_t ldi, void* hi, void* lo,
+                      int64_t n, int64_t p, cudaStream_t s);
+bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void* x_hi, const void* x_lo, int64_t n,
+                   int64_t p, CUtensorMap* maps);
+cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
+                             int p, const int* rp, const int* ci, const float* cv, float lam1, Emit<float> em,
+                             Ctrl* ctrl, cudaStream_t s);
+int obs_take_error();
+
+// ---------------------------------------------------------------- differentiation (adjoint.cu)
+template <typename T>
+void launch_dense_grad(int p, Csr<T> om, const int4* rinfo, const T* rdv, const T* S, int64_t lds, T* G, int64_t ldg,
+                       T lam2, T scale, cudaStream_t s);
+template <typename T>
+void launch_spmm_dense(int p, Csr<T> om, const int4* rinfo, const T* rdv, const T* B, int64_t ldb, int64_t m, T* C,
+                       int64_t ldc, cudaStream_t s);
+void launch_transpose(const void* in, int in_dt, int64_t rows, int64_t cols, int64_t ldi, void* out, int out_dt,
+                      int64_t ldo, float scale, cudaStream_t s);
+template <typename T> void launch_transpose_index(int p, Csr<T> om, int* tr, cudaStream_t s);
+template <typename T>
+void launch_support_product(int p, Csr<T> om, const int4* rinfo, const double* v, const T* S, int64_t lds,
+                            double* out, cudaStream_t s);
+template <typename T>
+void launch_support_combine(int p, Csr<T> om, const int* tr, const double* Tv, const double* v, double lam2, int mode,
+                            double* out, cudaStream_t s);
+template <typename T>
+void launch_support_vectors(int p, int64_t nnz, Csr<T> om, double* omega_d, double* sign_off, cudaStream_t s);
+int cg_part_blocks(int64_t n);
+void launch_dot_part(int64_t n, const double* a, const double* b, double* part, cudaStream_t s);
+void launch_cg_scalar(const double* part, int nb, int stage, double tol2, void* cg, cudaStream_t s);
+void launch_cg_xr(int64_t n, const void* cg, const double* p, const double* Ap, double* x, double* r, cudaStream_t s);
+void launch_cg_p(int64_t n, const void* cg, const double* r, double* p, cudaStream_t s);
+size_t cg_state_bytes();
+template <typename T>
+int launch_smooth_parts(int p, Csr<T> om, const double* Tv, double* part, double* out3, cudaStream_t s);
+void launch_reduce_parts(const double* part, int nb, double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- dense products (gram*.cu)
 // S = X^T X / n into S (p x lds).  Returns a CUDA error code.
@@ -125,5 +184,9 @@ int gram_tc_take_error();
 
 // Set the text returned by hpc_last_error() for this thread (api.cu).
 void set_last_error(const char* msg);
+
+// Box of the TMA descriptor of S used by the screening pass: 64 rows x BJ columns.
+constexpr int kScreenBoxRows = 64;
+template <typename T> constexpr int screen_box_cols() { return 32 * (16 / (int)sizeof(T)); }
 
 }  // namespace hpc

@@ -23,9 +23,11 @@
 //                     gathers of S on the candidate pattern and FP64 sums.
 //  4. accept          compaction of the accepted Omega+ into CSR (ballot/popc row
 //                     counts, scan, ordered write) and the stopping rule.
+#include <algorithm>
 #include <cstdio>
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace hpc {
 
@@ -61,6 +63,61 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
+// Compensated FP32 accumulator for sums that would otherwise need FP64, whose
+// rate on this GPU is a small fraction of FP32: every addition is Knuth's
+// TwoSum, the rounding errors collect in lo, and the pair carries ~44 bits.
+// FP64 appears only in the final cross-block reductions.
+struct F2 {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void acc_add(F2& a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float bp = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+    a.hi = s;
+    a.lo = __fadd_rn(a.lo, err);
+}
+__device__ __forceinline__ void acc_add(double& a, double b) { a += b; }
+__device__ __forceinline__ double acc_value(const F2& a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ F2 warp_sum(F2 a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(kFull, a.hi, o);
+        const float l = __shfl_xor_sync(kFull, a.lo, o);
+        acc_add(a, h);
+        a.lo = __fadd_rn(a.lo, l);
+    }
+    return a;
+}
+template <typename T> struct AccOf { using type = F2; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ float mulT(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulT(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float logT(float a) { return logf(a); }
+__device__ __forceinline__ double logT(double a) { return log(a); }
+
+// phi(x) = x - log(1 + x) for x > -1.  FP32: for |x| < 1/8 the Taylor series
+// sum_{k>=0} (-1)^k x^(k+2) / (k+2), truncated after x^10 (relative error
+// < 2e-9), avoids the cancellation of x - log1p(x); otherwise x - log1pf(x).
+__device__ __forceinline__ float phiT(float x) {
+    if (fabsf(x) < 0.125f) {
+        float r = 1.0f / 10.0f;
+        r = fmaf(x, r, -1.0f / 9.0f);
+        r = fmaf(x, r, 1.0f / 8.0f);
+        r = fmaf(x, r, -1.0f / 7.0f);
+        r = fmaf(x, r, 1.0f / 6.0f);
+        r = fmaf(x, r, -1.0f / 5.0f);
+        r = fmaf(x, r, 1.0f / 4.0f);
+        r = fmaf(x, r, -1.0f / 3.0f);
+        r = fmaf(x, r, 1.0f / 2.0f);
+        return x * x * r;
+    }
+    return x - log1pf(x);
+}
+__device__ __forceinline__ double phiT(double x) { return x - log1p(x); }
+
 // Prox of eq. (2) for one candidate entry at step tau (tau and tau*lambda1 are
 // exact: tau is a power of two).  The diagonal is not thresholded.
 template <typename T>
@@ -82,6 +139,7 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
     }
     if (tid == 0) {
         ctrl->em_count = 0;
+        ctrl->n_offrows = 0;
         ctrl->bucket_total = 0;
         ctrl->flags = 0;
         ctrl->ls_accept = -1;
@@ -94,36 +152,71 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
 }
 
 // ------------------------------------------------------------------ 1. screening SpMM
-// Grid: x = chunks of 128 rows, y = column blocks of BJ = 32*V columns.  x runs
-// fastest, so the CTAs in flight share a few column blocks S[:, J] (p*BJ*sizeof(T)
-// bytes each), which stay in L2 while every row gathers its d rows of them: S is
-// read from HBM about once per pass.  Lane l of a warp holds columns J*BJ + l*V
-// .. +V-1 and loads them as one 16-byte vector per CSR entry.  A warp owns 16
-// consecutive rows and walks their CSR entries as one stream, kScreenUnroll
-// loads in flight at a time; when the stream crosses a row boundary the
-// finished row is screened and its emitted entries appended.
-constexpr int kScreenRowsPerWarp = 16;
-constexpr int kScreenRows = kScreenRowsPerWarp * kWarps;
-constexpr int kScreenUnroll = 8;
+// W = Omega S is split as W = diag(w) S + O S, O the off-diagonal part of Omega.
+// Every entry is accumulated in one canonical order -- the diagonal term first,
+// W_ij = w_ii * S_ij, then fma(w_ik, S_kj, .) over the off-diagonal k of row i
+// in ascending column order -- which the gather fill of partner entries
+// repeats, so both produce the same bits.
+//
+// The diagonal term streams S itself, so the pass is staged like a copy: one
+// persistent CTA per SM, a producer thread loading 64-row x BJ-column tiles of S
+// (32 KB, BJ = 32*V) with TMA into a kScreenStages-deep mbarrier ring, and eight
+// consumer warps, each screening eight rows of every tile (lane l holds columns
+// l*V .. l*V+V-1, one 16-byte shared-memory read per row).  This kernel takes the
+// pure-diagonal rows, which need no other row of S: CTA c owns row chunks c,
+// c+G, c+2G, ... and walks each chunk's column blocks in order, so DRAM sees long
+// runs of each row.  Rows with off-diagonal entries are screened by
+// k_grad_screen_rows.  Row set-up (CSR bounds, diagonal position and value, the
+// pure-diagonal flag) comes from k_row_info, cached in shared memory.
+constexpr int kScreenTileRows = 64;
+constexpr int kScreenStages = 5;
+constexpr int kScreenMaxChunks = 32;              // row chunks per CTA (shared-memory row cache)
+constexpr int kScreenThreads = kThreads + 32;     // 8 consumer warps + 1 producer warp
+constexpr long long kScreenWaitLimit = 1ll << 26;
 
 template <typename T>
-struct ScreenRow {
+constexpr int screen_smem_bytes() {
+    return kScreenStages * kScreenTileRows * 32 * (16 / (int)sizeof(T)) * (int)sizeof(T)  // tiles
+           + kScreenMaxChunks * kScreenTileRows * (16 + (int)sizeof(T))                   // row cache
+           + 2 * kScreenStages * 8 + 16                                                   // barriers + flag
+           + 1024;                                                                        // alignment
+}
+
+// Per row of the iterate: CSR bounds, position of the diagonal (-1 if absent),
+// its value; rows with off-diagonal entries (or no diagonal) are appended to
+// offlist (any order: the screening output is re-sorted per row downstream).
+template <typename T>
+__global__ void k_row_info(int p, Csr<T> om, int4* __restrict__ rinfo, T* __restrict__ rdv,
+                           int* __restrict__ offlist, Ctrl* __restrict__ ctrl) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x) {
+        const int rb = om.rp[i], re = om.rp[i + 1];
+        int pd = -1;
+        T dv = T(0);
+        for (int q = rb; q < re; ++q)
+            if (om.ci[q] == i) { pd = q; dv = om.cv[q]; break; }
+        const bool pure = (re - rb == 1) && pd >= 0;
+        rinfo[i] = make_int4(rb, re, pd, pure ? 1 : 0);
+        rdv[i] = dv;
+        if (!pure && offlist) offlist[atomicAdd(&ctrl->n_offrows, 1)] = i;
+    }
+}
+
+template <typename T>
+struct Screen {
     static constexpr int V = 16 / sizeof(T);
     static constexpr int BJ = 32 * V;
 
-    // Screen row i of the block: emit the support entries, the diagonal and every
-    // |W_ij| > lambda1 (NaN included).  Warp-collective.
-    static __device__ __forceinline__ void finalize(int i, int rb, int re, const T (&acc)[V], int j0, int p,
-                                                    const int* __restrict__ ci, const T* __restrict__ cv, T lam1,
-                                                    const Emit<T>& em, Ctrl* ctrl, int lane) {
+    // Append the entries of row i in this block that a prox step can touch: the
+    // support (diagonal included) and every |W_ij| > lambda1 (NaN included).
+    // (values by value, so callers' accumulators stay in registers)
+    static __device__ __noinline__ void emit(int i, T a0, T a1, T a2, T a3, int rb, int re, int j0, int p,
+                                             const int* __restrict__ ci, const T* __restrict__ cv, T lam1,
+                                             Emit<T> em, Ctrl* ctrl, int lane) {
+        const T acc[4] = {a0, a1, a2, a3};
         unsigned mbits = 0;
         T om[V];
-        bool big = false;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            om[v] = T(0);
-            big |= !(fabs(acc[v]) <= lam1);
-        }
+        for (int v = 0; v < V; ++v) om[v] = T(0);
         for (int q = rb; q < re; q += 32) {
             const int c = (q + lane < re) ? ci[q + lane] : -1;
             unsigned bal = __ballot_sync(kFull, c >= j0 && c < j0 + BJ);
@@ -140,14 +233,13 @@ struct ScreenRow {
                 }
             }
         }
-        if (!__any_sync(kFull, big || mbits != 0)) return;
-        bool emit[V];
+        bool emit_v[V];
         int c = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int j = j0 + lane * V + v;
-            emit[v] = (j < p) && (((mbits >> v) & 1u) || !(fabs(acc[v]) <= lam1));
-            c += emit[v] ? 1 : 0;
+            emit_v[v] = (j < p) && (((mbits >> v) & 1u) || !(fabs(acc[v]) <= lam1));
+            c += emit_v[v] ? 1 : 0;
         }
         const int incl = warp_incl_scan(c, lane);
         const int total = __shfl_sync(kFull, incl, 31);
@@ -158,7 +250,7 @@ struct ScreenRow {
         int pos = base_pos + incl - c;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            if (emit[v]) {
+            if (emit_v[v]) {
                 if (pos < em.cap) {
                     const int j = j0 + lane * V + v;
                     const bool sup = (mbits >> v) & 1u;
@@ -174,79 +266,203 @@ struct ScreenRow {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_grad_screen(const T* __restrict__ S, int64_t ld, int p, const int* __restrict__ rp,
-              const int* __restrict__ ci, const T* __restrict__ cv, T lam1, Emit<T> em,
-              Ctrl* __restrict__ ctrl) {
-    using R = ScreenRow<T>;
-    constexpr int V = R::V;
-    constexpr int BJ = R::BJ;
-    constexpr int U = kScreenUnroll;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j0 = blockIdx.y * BJ;
-    const int rbase = blockIdx.x * kScreenRows + warp * kScreenRowsPerWarp;
-    if (rbase >= p) return;
-    const int nr = min(kScreenRowsPerWarp, p - rbase);
-    const T* sblk = S + j0 + lane * V;
-    // lanes 0..nr hold the row pointers of the warp's rows (lane nr: end of the last row)
-    const int my_rp = (lane <= nr) ? rp[rbase + lane] : 0;
-    const int e_beg = __shfl_sync(kFull, my_rp, 0);
-    const int e_end = __shfl_sync(kFull, my_rp, nr);
-    int cur = 0;
-    int cur_beg = e_beg;
-    int cur_end = __shfl_sync(kFull, my_rp, 1);
-    T acc[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = T(0);
+__global__ void __launch_bounds__(kScreenThreads, 1)
+k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S, int64_t ld, int p,
+              const int4* __restrict__ rinfo, const T* __restrict__ rdv, const int* __restrict__ ci,
+              const T* __restrict__ cv, T lam1, Emit<T> em, Ctrl* __restrict__ ctrl) {
+    using Sc = Screen<T>;
+    constexpr int V = Sc::V;
+    constexpr int BJ = Sc::BJ;
+    constexpr int R = kScreenTileRows;
+    constexpr int kTileBytes = R * BJ * (int)sizeof(T);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    T* tiles = reinterpret_cast<T*>(smem);
+    int4* s_info = reinterpret_cast<int4*>(smem + kScreenStages * kTileBytes);
+    T* s_dv = reinterpret_cast<T*>(s_info + kScreenMaxChunks * R);
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_dv + kScreenMaxChunks * R);
+    uint64_t* empty = full + kScreenStages;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kScreenStages);
 
-    for (int eb = e_beg; eb < e_end; eb += 32) {
-        const int e = eb + lane;
-        const int k_l = (e < e_end) ? ci[e] : 0;
-        const T w_l = (e < e_end) ? cv[e] : T(0);
-        const int cnt = min(32, e_end - eb);
-        for (int t = 0; t < cnt; t += U) {
-            const int g = min(U, cnt - t);          // entries in this group
-            const int gbase = eb + t;               // stream index of the group's first entry
-            T sv[U][V];
-            T wv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (u < g) {
-                    const int k = __shfl_sync(kFull, k_l, t + u);
-                    wv[u] = __shfl_sync(kFull, w_l, t + u);
-                    vload(sv[u], sblk + (int64_t)k * ld);
-                }
-            }
-            int u0 = 0;
-            while (true) {
-                // entries [u0, stop) of the group belong to row cur (CSR order kept)
-                const int stop = min(g, cur_end - gbase);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (u >= u0 && u < stop) {
-#pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] = fmaT(wv[u], sv[u][v], acc[v]);
-                    }
-                }
-                u0 = max(u0, stop);
-                if (u0 >= g) break;
-                // the stream left row cur: screen it and move on
-                R::finalize(rbase + cur, cur_beg, cur_end, acc, j0, p, ci, cv, lam1, em, ctrl, lane);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[v] = T(0);
-                ++cur;
-                cur_beg = cur_end;
-                cur_end = __shfl_sync(kFull, my_rp, cur + 1);
+    if (2 * ctrl->n_offrows > p) return;      // dense rows: k_grad_screen_rows covers every row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+    const int nchunks = (p + R - 1) / R;
+    const int mine = blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / G + 1 : 0;   // <= kScreenMaxChunks
+    const int nblocks = (p + BJ - 1) / BJ;
+    const int items = mine * nblocks;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kScreenStages; ++st) {
+            ptx::mbar_init(&full[st], 1);
+            ptx::mbar_init(&empty[st], kWarps);
+        }
+        *abort_flag = 0;
+        ptx::mbar_init_fence();
+    }
+    // cache the row set-up of this CTA's chunks
+    for (int t = threadIdx.x; t < mine * R; t += blockDim.x) {
+        const int i = (blockIdx.x + (t / R) * G) * R + (t % R);
+        s_info[t] = i < p ? rinfo[i] : make_int4(0, 0, -1, 0);
+        s_dv[t] = i < p ? rdv[i] : T(0);
+    }
+    __syncthreads();
+
+    if (warp == kWarps) {
+        // ---------------- producer: one TMA tile per (column block, chunk), block-major
+        if (lane == 0) {
+            ptx::prefetch_tensormap(&smap);
+            for (int t = 0; t < items; ++t) {
+                const int st = t % kScreenStages;
+                const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
+                if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort_flag, kScreenWaitLimit)) break;
+                const int m = t / nblocks, jb = t % nblocks;
+                const int chunk = blockIdx.x + m * G;
+                ptx::mbar_expect_tx(&full[st], kTileBytes);
+                ptx::tma_load_2d(reinterpret_cast<uint8_t*>(tiles) + st * kTileBytes, &smap, &full[st], jb * BJ,
+                                 chunk * R);
             }
         }
-    }
-    while (cur < nr) {
-        R::finalize(rbase + cur, cur_beg, cur_end, acc, j0, p, ci, cv, lam1, em, ctrl, lane);
+    } else {
+        // ---------------- consumers: warp w screens rows 8w .. 8w+7 of every tile
+        for (int t = 0; t < items; ++t) {
+            const int st = t % kScreenStages;
+            const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
+            if (!ptx::mbar_wait_bounded(&full[st], ph, abort_flag, kScreenWaitLimit)) break;
+            const int m = t / nblocks, jb = t % nblocks;
+            const int chunk = blockIdx.x + m * G;
+            const int j0 = jb * BJ;
+            const T* tile = tiles + (size_t)st * R * BJ;
+            // eight rows at once: independent shared-memory reads, the diagonal-term
+            // products, and one warp-wide OR of the per-row "something to emit" bits
+            T acc[8][V];
+            int4 info[8];
+            unsigned want = 0;
 #pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = T(0);
-        ++cur;
-        cur_beg = cur_end;
-        cur_end = __shfl_sync(kFull, my_rp, min(cur + 1, nr));
+            for (int q = 0; q < 8; ++q) {
+                const int r = warp * 8 + q;
+                info[q] = s_info[m * R + r];
+                const T dv = s_dv[m * R + r];
+                T sv[V];
+                if constexpr (V == 4) {
+                    const float4 x = *reinterpret_cast<const float4*>(tile + r * BJ + lane * V);
+                    sv[0] = x.x; sv[1] = x.y; sv[2] = x.z; sv[3] = x.w;
+                } else {
+                    const double2 x = *reinterpret_cast<const double2*>(tile + r * BJ + lane * V);
+                    sv[0] = x.x; sv[1] = x.y;
+                }
+                bool big = false;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    acc[q][v] = mulT(dv, sv[v]);
+                    big |= !(fabs(acc[q][v]) <= lam1);
+                }
+                want |= (big ? 1u : 0u) << q;
+            }
+            want = __reduce_or_sync(kFull, want);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = chunk * R + warp * 8 + q;
+                // pure-diagonal rows only (the others belong to k_grad_screen_rows); the
+                // diagonal's own column block always emits (support)
+                const bool diag_here = (i >= j0 && i < j0 + BJ);
+                if (i < p && info[q].w && (((want >> q) & 1u) || diag_here))
+                    Sc::emit(i, acc[q][0], acc[q][V > 1 ? 1 : 0], acc[q][V > 2 ? 2 : 0], acc[q][V > 3 ? 3 : 0], info[q].x,
+                             info[q].y, j0, p, ci, cv, lam1, em, ctrl, lane);
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[st]);
+        }
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicOr(&ctrl->flags, kFlagTimeout);
+            // drain: bounded waits so that no TMA copy lands after the CTA exits
+            for (int t = max(0, items - kScreenStages); t < items; ++t) {
+                const int st = t % kScreenStages;
+                const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
+                for (long long it = 0; it < (1ll << 22) && !ptx::mbar_try_wait(&full[st], ph); ++it) __nanosleep(64);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Rows with off-diagonal entries (or, when they are the majority, every row):
+// persistent warps over items (column block, group of 8 listed rows), column
+// block outermost so that in-flight warps share S[:, J] in L2.  A warp issues the
+// eight diagonal-term loads of its rows first, then per row gathers the
+// off-diagonal terms four at a time, in the canonical order, and screens.
+constexpr int kRowsPerItem = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __restrict__ rinfo,
+                   const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
+                   const T* __restrict__ cv, T lam1, Emit<T> em, Ctrl* __restrict__ ctrl) {
+    using Sc = Screen<T>;
+    constexpr int V = Sc::V;
+    constexpr int BJ = Sc::BJ;
+    const int lane = threadIdx.x & 31;
+    const bool all_rows = 2 * ctrl->n_offrows > p;
+    const int nrows = all_rows ? p : ctrl->n_offrows;
+    const int ngroups = (nrows + kRowsPerItem - 1) / kRowsPerItem;
+    const int nblocks = (p + BJ - 1) / BJ;
+    const long long items = (long long)ngroups * nblocks;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long it = gw; it < items; it += nw) {
+        const int jb = (int)(it / ngroups), grp = (int)(it % ngroups);
+        const int j0 = jb * BJ;
+        const int nr = min(kRowsPerItem, nrows - grp * kRowsPerItem);
+        int my_row = -1;
+        if (lane < nr) my_row = all_rows ? grp * kRowsPerItem + lane : offlist[grp * kRowsPerItem + lane];
+        T sd[kRowsPerItem][V];
+#pragma unroll
+        for (int r = 0; r < kRowsPerItem; ++r) {
+            const int i = __shfl_sync(kFull, my_row, r);
+            if (r < nr) vload(sd[r], S + (int64_t)i * ld + j0 + lane * V);
+        }
+#pragma unroll
+        for (int r = 0; r < kRowsPerItem; ++r) {
+            if (r >= nr) break;
+            const int i = __shfl_sync(kFull, my_row, r);
+            const int4 info = rinfo[i];
+            const T dv = rdv[i];
+            T acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = mulT(dv, sd[r][v]);
+            bool sup_here = (i >= j0 && i < j0 + BJ);
+            for (int q0 = info.x; q0 < info.y; q0 += 4) {
+                T s4[4][V];
+                T w4[4];
+                int k4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int qq = q0 + u;
+                    k4[u] = -1;
+                    if (qq < info.y && qq != info.z) {
+                        k4[u] = ci[qq];
+                        w4[u] = cv[qq];
+                        vload(s4[u], S + (int64_t)k4[u] * ld + j0 + lane * V);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (k4[u] >= 0) {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fmaT(w4[u], s4[u][v], acc[v]);
+                        sup_here |= (k4[u] >= j0 && k4[u] < j0 + BJ);
+                    }
+                }
+            }
+            bool big = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) big |= !(fabs(acc[v]) <= lam1);
+            if (__any_sync(kFull, big) || sup_here) Sc::emit(i, acc[0], acc[V > 1 ? 1 : 0], acc[V > 2 ? 2 : 0], acc[V > 3 ? 3 : 0], info.x, info.y, j0, p,
+                         ci, cv, lam1, em, ctrl, lane);
+        }
     }
 }
 
@@ -262,7 +478,8 @@ __global__ void k_bucket_count(Emit<T> em, Buckets<T> bk, Ctrl* ctrl) {
         const int i = em.row[e];
         const int cj = em.col[e];
         atomicAdd(&bk.cnt[i], 1);
-        if (cj >= 0) atomicAdd(&bk.cnt[cj], 1);   // off the support: partner request in row j
+        // off the support and not emitted from both sides: partner request in row j
+        if (cj >= 0 && !(cj & 0x40000000)) atomicAdd(&bk.cnt[cj], 1);
     }
 }
 
@@ -321,13 +538,13 @@ __global__ void k_bucket_scatter(Emit<T> em, Buckets<T> bk, const Ctrl* ctrl) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
         const int i = em.row[e];
         const int cj = em.col[e];
-        const int j = cj & 0x7fffffff;
+        const int j = cj & 0x3fffffff;
         const int pos = bk.off[i] + atomicAdd(&bk.cur[i], 1);
         bk.col_a[pos] = j;
         bk.w_a[pos] = em.w[e];
         bk.om_a[pos] = em.om[e];
         bk.fl_a[pos] = (unsigned char)(kEntOwn | (cj < 0 ? kEntSupp : 0));
-        if (cj >= 0) {
+        if (cj >= 0 && !(cj & 0x40000000)) {
             const int q = bk.off[j] + atomicAdd(&bk.cur[j], 1);
             bk.col_a[q] = i;
             bk.w_a[q] = T(0);
@@ -350,6 +567,45 @@ k_bucket_sort(Buckets<T> bk, int p, const Ctrl* ctrl) {
     for (int i = gw; i < p; i += nw) {
         const int beg = bk.off[i];
         const int c = bk.cnt[i];
+        if (c <= 32) {
+            // whole row in registers: rank by shuffles (keys are distinct), drop a partner
+            // request whose predecessor in column order is the own entry of that column,
+            // and write the kept entries in order
+            const bool valid = lane < c;
+            int col = 0;
+            T w = T(0), om = T(0);
+            unsigned char fl = 0;
+            if (valid) {
+                col = bk.col_a[beg + lane];
+                w = bk.w_a[beg + lane];
+                om = bk.om_a[beg + lane];
+                fl = bk.fl_a[beg + lane];
+            }
+            const int key = valid ? col * 2 + ((fl & kEntMirror) ? 1 : 0) : 0x7fffffff;
+            int rank = 0;
+            for (int t = 0; t < 32; ++t) rank += (__shfl_sync(kFull, key, t) < key) ? 1 : 0;
+            int pred_col = -1;
+            for (int t = 0; t < 32; ++t) {
+                const int rt = __shfl_sync(kFull, rank, t);
+                const int ct = __shfl_sync(kFull, col, t);
+                if (t < c && rt == rank - 1) pred_col = ct;
+            }
+            const bool keep = valid && !((fl & kEntMirror) && rank > 0 && pred_col == col);
+            const unsigned kb = __ballot_sync(kFull, keep);
+            int pos = 0;
+            for (int t = 0; t < 32; ++t) {
+                const int rt = __shfl_sync(kFull, rank, t);
+                pos += (((kb >> t) & 1u) && rt < rank) ? 1 : 0;
+            }
+            if (keep) {
+                bk.col_b[beg + pos] = col;
+                bk.w_b[beg + pos] = w;
+                bk.om_b[beg + pos] = om;
+                bk.fl_b[beg + pos] = fl;
+            }
+            if (lane == 0) bk.len[i] = __popc(kb);
+            continue;
+        }
         for (int e = lane; e < c; e += 32) {
             const int ke = bk.col_a[beg + e] * 2 + ((bk.fl_a[beg + e] & kEntMirror) ? 1 : 0);
             int rank = 0;
@@ -408,8 +664,14 @@ k_fill_w(const T* __restrict__ S, int64_t ld, int p, Csr<T> om, Buckets<T> bk, c
         for (int e = lane; e < L; e += 32) {
             if (!(bk.fl_b[beg + e] & kEntMirror)) continue;
             const int j = bk.col_b[beg + e];
-            T acc = T(0);
-            for (int q = rb; q < re; ++q) acc = fmaT(om.cv[q], S[(int64_t)om.ci[q] * ld + j], acc);
+            // canonical order of the screening pass: diagonal term, then off-diagonals
+            int pd = -1;
+            T dv = T(0);
+            for (int q = rb; q < re; ++q)
+                if (om.ci[q] == i) { pd = q; dv = om.cv[q]; break; }
+            T acc = mulT(dv, S[(int64_t)i * ld + j]);
+            for (int q = rb; q < re; ++q)
+                if (q != pd) acc = fmaT(om.cv[q], S[(int64_t)om.ci[q] * ld + j], acc);
             bk.w_b[beg + e] = acc;
         }
     }
@@ -419,12 +681,13 @@ k_fill_w(const T* __restrict__ S, int64_t ld, int p, Csr<T> om, Buckets<T> bk, c
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gradient(int p, Buckets<T> bk, T lam1, T lam2, double* part_obj, Ctrl* ctrl) {
+    using A = typename AccOf<T>::type;
     __shared__ double red[kWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool skip = ctrl->flags != 0;
-    double s_ow = 0.0, s_o2 = 0.0, s_log = 0.0, s_abs = 0.0;
+    A s_ow{}, s_o2{}, s_log{}, s_abs{};
     int bad = 0;
     for (int i = skip ? p : gw; i < p; i += nw) {
         const int beg = bk.off[i], L = bk.len[i];
@@ -444,23 +707,26 @@ k_gradient(int p, Buckets<T> bk, T lam1, T lam2, double* part_obj, Ctrl* ctrl) {
             }
             if (pos < 0) { bad |= kFlagBadStructure; continue; }
             const T wji = bk.w_b[jb + pos];
-            T g = T(0.5) * (wij + wji) + lam2 * om;
+            // G_ij = (W_ij + W_ji)/2 + lambda2 w_ij - [i=j]/w_ii, one fixed rounding sequence
+            T g = fmaT(lam2, om, T(0.5) * (wij + wji));
             if (i == j) g -= T(1) / om;
             bk.g[beg + e] = g;
             const bool keep = (fl & kEntSupp) || (i == j) || !(fabs(g) <= lam1);
             if (keep) bk.fl_b[beg + e] = fl | kEntKeep;
             if (!(g == g) || isinf((double)g)) bad |= kFlagNaN;
             if (fl & kEntSupp) {
-                const double od = (double)om;
-                s_ow += od * (double)wij;
-                s_o2 += od * od;
-                if (i == j) s_log += log(od); else s_abs += fabs(od);
+                acc_add(s_ow, mulT(om, wij));
+                acc_add(s_o2, mulT(om, om));
+                if (i == j) acc_add(s_log, logT(om)); else acc_add(s_abs, fabs(om));
             }
         }
     }
     if (bad) atomicOr(&ctrl->flags, bad);
     s_ow = warp_sum(s_ow); s_o2 = warp_sum(s_o2); s_log = warp_sum(s_log); s_abs = warp_sum(s_abs);
-    if (lane == 0) { red[warp][0] = s_ow; red[warp][1] = s_o2; red[warp][2] = s_log; red[warp][3] = s_abs; }
+    if (lane == 0) {
+        red[warp][0] = acc_value(s_ow); red[warp][1] = acc_value(s_o2);
+        red[warp][2] = acc_value(s_log); red[warp][3] = acc_value(s_abs);
+    }
     __syncthreads();
     if (threadIdx.x < 4) {
         double a = 0.0;
@@ -480,6 +746,7 @@ template <typename T, int M>
 __global__ void __launch_bounds__(kThreads)
 k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, double tau0, int h_base,
           double* part_ls, const Ctrl* ctrl) {
+    using A = typename AccOf<T>::type;
     constexpr int kChunk = ls_chunk<M>();
     __shared__ int s_col[kWarps][kChunk];
     __shared__ T s_del[kWarps][M][kChunk];
@@ -495,9 +762,10 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
         tau[m] = (T)ldexp(tau0, -(h_base + m));
         tl1[m] = tau[m] * lam1;
     }
-    double q[M], n2[M], ph[M], nb[M];
+    A q[M]{}, n2[M]{}, ph[M]{};
+    int nb[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) { q[m] = 0.0; n2[m] = 0.0; ph[m] = 0.0; nb[m] = 0.0; }
+    for (int m = 0; m < M; ++m) nb[m] = 0;
 
     for (int i = skip ? p : gw; i < p; i += nw) {
         const int beg = bk.off[i], L = bk.len[i];
@@ -515,14 +783,10 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
                     const T np_ = prox_entry(om, g, tau[m], tl1[m], diag);
                     de[m] = np_ - om;
                     act_e |= (de[m] != T(0));
-                    const double dd = (double)de[m];
-                    n2[m] += dd * dd;
+                    acc_add(n2[m], mulT(de[m], de[m]));
                     if (diag) {
-                        if (!(np_ > T(0))) nb[m] += 1.0;
-                        else {
-                            const double x = dd / (double)om;
-                            ph[m] += x - log1p(x);
-                        }
+                        if (!(np_ > T(0))) nb[m] += 1;
+                        else acc_add(ph[m], phiT(de[m] / om));
                     }
                 }
             } else {
@@ -559,21 +823,27 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
                         const int f = fb + t;
                         const int jf = s_col[warp][t];
                         if (f < e || jf < 0) continue;
-                        const T s = srow[jf];
+                        const T sv = srow[jf];
                         const T wgt = (f == e) ? T(1) : T(2);
 #pragma unroll
-                        for (int m = 0; m < M; ++m) qf[m] = fmaT(wgt * de[m] * s_del[warp][m][t], s, qf[m]);
+                        for (int m = 0; m < M; ++m) qf[m] = fmaT(wgt * de[m] * s_del[warp][m][t], sv, qf[m]);
                     }
 #pragma unroll
-                    for (int m = 0; m < M; ++m) q[m] += (double)qf[m];
+                    for (int m = 0; m < M; ++m) acc_add(q[m], qf[m]);
                 }
             }
         }
     }
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        const double a = warp_sum(q[m]), b = warp_sum(n2[m]), c = warp_sum(ph[m]), d = warp_sum(nb[m]);
-        if (lane == 0) { red[warp][m][0] = a; red[warp][m][1] = b; red[warp][m][2] = c; red[warp][m][3] = d; }
+        const A a = warp_sum(q[m]), b = warp_sum(n2[m]), c = warp_sum(ph[m]);
+        int d = nb[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+        if (lane == 0) {
+            red[warp][m][0] = acc_value(a); red[warp][m][1] = acc_value(b);
+            red[warp][m][2] = acc_value(c); red[warp][m][3] = (double)d;
+        }
     }
     __syncthreads();
     if (threadIdx.x < M * 4) {
@@ -584,27 +854,129 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
     }
 }
 
-// Reduce the partials in a fixed order and take the decision of Alg. 1 step 9.
-__global__ void __launch_bounds__(128)
+// Obs form of the line-search partials (Alg. 3 step 11): tr(D S D) restricted to
+// row i is ||X D_i||^2 / n with X D_i = sum_e D_e X^T[j_e, :]; lanes hold 4
+// consecutive samples of each 128-sample chunk of n.  [1]-[3] as in k_ls_eval.
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, float lam1, double tau0,
+              int h_base, double* part_ls, const Ctrl* ctrl) {
+    __shared__ double red[kWarps][M][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const bool skip = (ctrl->flags != 0) || (ctrl->ls_accept >= 0);
+    float tau[M], tl1[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        tau[m] = (float)ldexp(tau0, -(h_base + m));
+        tl1[m] = tau[m] * lam1;
+    }
+    F2 q[M]{}, n2[M]{}, ph[M]{};
+    int nb[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) nb[m] = 0;
+    for (int i = skip ? p : gw; i < p; i += nw) {
+        const int beg = bk.off[i], L = bk.len[i];
+        for (int e = lane; e < L; e += 32) {
+            const int je = bk.col_b[beg + e];
+            const float om = bk.om_b[beg + e], g = bk.g[beg + e];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const float np_ = prox_entry(om, g, tau[m], tl1[m], je == i);
+                const float d = np_ - om;
+                acc_add(n2[m], mulT(d, d));
+                if (je == i) {
+                    if (!(np_ > 0.f)) nb[m] += 1;
+                    else acc_add(ph[m], phiT(d / om));
+                }
+            }
+        }
+        for (int64_t c0 = 0; c0 < n; c0 += 128) {
+            const int64_t c = c0 + lane * 4;
+            float u[M][4];
+#pragma unroll
+            for (int m = 0; m < M; ++m) u[m][0] = u[m][1] = u[m][2] = u[m][3] = 0.f;
+            bool any = false;
+            for (int e = 0; e < L; ++e) {
+                const int je = bk.col_b[beg + e];
+                const float om = bk.om_b[beg + e], g = bk.g[beg + e];
+                float d[M];
+                bool act = false;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    d[m] = prox_entry(om, g, tau[m], tl1[m], je == i) - om;
+                    act |= d[m] != 0.f;
+                }
+                if (!act) continue;
+                any = true;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (c < ldx) x = __ldg(reinterpret_cast<const float4*>(Xt + (int64_t)je * ldx + c));
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    u[m][0] = fmaf(d[m], x.x, u[m][0]);
+                    u[m][1] = fmaf(d[m], x.y, u[m][1]);
+                    u[m][2] = fmaf(d[m], x.z, u[m][2]);
+                    u[m][3] = fmaf(d[m], x.w, u[m][3]);
+                }
+            }
+            if (!any) break;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                float sq = u[m][0] * u[m][0];
+                sq = fmaf(u[m][1], u[m][1], sq);
+                sq = fmaf(u[m][2], u[m][2], sq);
+                sq = fmaf(u[m][3], u[m][3], sq);
+                acc_add(q[m], sq);
+            }
+        }
+    }
+    const double inv_n = 1.0 / (double)n;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const F2 a = warp_sum(q[m]), b = warp_sum(n2[m]), c = warp_sum(ph[m]);
+        int dd = nb[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(kFull, dd, o);
+        if (lane == 0) {
+            red[warp][m][0] = acc_value(a) * inv_n; red[warp][m][1] = acc_value(b);
+            red[warp][m][2] = acc_value(c); red[warp][m][3] = (double)dd;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < M * 4) {
+        const int m = threadIdx.x / 4, k = threadIdx.x % 4;
+        double a = 0.0;
+        for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
+        part_ls[(size_t)blockIdx.x * kMaxWindow * 4 + m * 4 + k] = a;
+    }
+}
+
+// Reduce the partials in a fixed order (one warp per quantity, lanes over strided
+// blocks, then a butterfly) and take the decision of Alg. 1 step 9.
+__global__ void __launch_bounds__(1024)
 k_ls_decide(const double* __restrict__ part_ls, const double* __restrict__ part_obj, int nblk, int M,
             int h_base, int max_halvings, double tau0, double lam1, double lam2, int first,
             Ctrl* ctrl) {
     __shared__ double sums[kMaxWindow * 4];
     __shared__ double obj[4];
-    const int t = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (ctrl->flags != 0 || ctrl->ls_accept >= 0) return;
-    if (t < M * 4) {
+    const int nq = M * 4 + (first ? 4 : 0);
+    for (int q = warp; q < nq; q += 32) {
         double a = 0.0;
-        for (int b = 0; b < nblk; ++b) a += part_ls[(size_t)b * kMaxWindow * 4 + t];
-        sums[t] = a;
-    }
-    if (first && t >= 64 && t < 68) {
-        double a = 0.0;
-        for (int b = 0; b < nblk; ++b) a += part_obj[b * 4 + (t - 64)];
-        obj[t - 64] = a;
+        if (q < M * 4) {
+            for (int b = lane; b < nblk; b += 32) a += part_ls[(size_t)b * kMaxWindow * 4 + q];
+        } else {
+            for (int b = lane; b < nblk; b += 32) a += part_obj[b * 4 + (q - M * 4)];
+        }
+        a = warp_sum(a);
+        if (lane == 0) {
+            if (q < M * 4) sums[q] = a; else obj[q - M * 4] = a;
+        }
     }
     __syncthreads();
-    if (t != 0) return;
+    if (threadIdx.x != 0) return;
     if (first) {
         // f = -sum log w_ii + tr(Omega S Omega)/2 + lambda2/2 ||Omega||^2, tr = sum w_ij W_ij
         ctrl->f_cur = -obj[2] + 0.5 * obj[0] + 0.5 * lam2 * obj[1];
@@ -735,11 +1107,26 @@ void launch_iter_begin(const IterBufs<T>& b, cudaStream_t s) {
 }
 
 template <typename T>
+int screen_grid(int p, int num_sms) {
+    const int nchunks = (p + kScreenTileRows - 1) / kScreenTileRows;
+    const int need = (nchunks + kScreenMaxChunks - 1) / kScreenMaxChunks;
+    return std::max(1, std::min(nchunks, std::max(num_sms, need)));
+}
+
+template <typename T>
 void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
-    constexpr int BJ = 32 * (16 / sizeof(T));
-    dim3 grid((b.p + kScreenRows - 1) / kScreenRows, (b.p + BJ - 1) / BJ);
-    k_grad_screen<T><<<grid, kThreads, 0, s>>>(b.S, b.ld, b.p, b.cur.rp, b.cur.ci, b.cur.cv, b.lam1,
-                                               b.em, b.ctrl);
+    constexpr int smem = screen_smem_bytes<T>();
+    cudaFuncSetAttribute(k_grad_screen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.offlist, b.ctrl);
+    k_grad_screen<T><<<screen_grid<T>(b.p, b.num_sms), kScreenThreads, smem, s>>>(
+        *b.smap, b.S, b.ld, b.p, b.rinfo, b.rdv, b.cur.ci, b.cur.cv, b.lam1, b.em, b.ctrl);
+    k_grad_screen_rows<T><<<b.num_sms * 4, kThreads, 0, s>>>(b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci,
+                                                            b.cur.cv, b.lam1, b.em, b.ctrl);
+}
+
+template <typename T>
+void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s) {
+    k_row_info<T><<<(p + 255) / 256, 256, 0, s>>>(p, om, rinfo, rdv, nullptr, nullptr);
 }
 
 template <typename T>
@@ -769,9 +1156,27 @@ void launch_ls_window(const IterBufs<T>& b, int h_base, bool first, cudaStream_t
         case 8: ls_eval_m<T, 8>(b, h_base, s); break;
         default: ls_eval_m<T, 16>(b, h_base, s); break;
     }
-    k_ls_decide<<<1, 128, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M == 1 || M == 2 || M == 4 || M == 8 ? M : 16,
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M == 1 || M == 2 || M == 4 || M == 8 ? M : 16,
                                   h_base, b.max_halvings, 1.0, (double)b.lam1, (double)b.lam2, first ? 1 : 0,
                                   b.ctrl);
+}
+
+template <int M>
+static void ls_eval_obs_m(const IterBufs<float>& b, int h_base, cudaStream_t s) {
+    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, b.lam1, 1.0, h_base, b.part_ls, b.ctrl);
+}
+
+void launch_ls_window_obs(const IterBufs<float>& b, int h_base, bool first, cudaStream_t s) {
+    const int M = b.ls_window;
+    switch (M) {
+        case 1: ls_eval_obs_m<1>(b, h_base, s); break;
+        case 2: ls_eval_obs_m<2>(b, h_base, s); break;
+        case 4: ls_eval_obs_m<4>(b, h_base, s); break;
+        case 8: ls_eval_obs_m<8>(b, h_base, s); break;
+        default: ls_eval_obs_m<16>(b, h_base, s); break;
+    }
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M == 1 || M == 2 || M == 4 || M == 8 ? M : 16,
+                                   h_base, b.max_halvings, 1.0, (double)b.lam1, (double)b.lam2, first ? 1 : 0, b.ctrl);
 }
 
 template <typename T>
@@ -808,6 +1213,7 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
     template void launch_ls_window<T>(const IterBufs<T>&, int, bool, cudaStream_t);                \
     template void launch_accept<T>(const IterBufs<T>&, cudaStream_t);                              \
     template void launch_set_identity<T>(Csr<T>, int, cudaStream_t);                               \
+    template void launch_row_info<T>(int, Csr<T>, int4*, T*, cudaStream_t);                        \
     template void launch_csr_export<T>(const int*, const int*, const T*, int, int, int64_t*, int32_t*, \
                                        void*, int, cudaStream_t);
 

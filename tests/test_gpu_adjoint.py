@@ -1,0 +1,154 @@
+"""Differentiation through the C ABI against the FP64 oracle.
+
+* hpc_backward: dL/dOmega (dense) and dL/dX of the smooth loss at the estimate, against
+  oracle.smooth_loss_grads (itself pinned by central differences), and dL/dOmega against
+  the solver's own G on its candidates, bitwise.
+* ConcordSmoothLoss (torch.autograd.Function) gives the same gradients through autograd.
+* hpc_hypergrad: the implicit lambda-gradient of the held-out loss, against oracle.hypergrad
+  (dense, pinned by central differences of re-solved estimates) at small p and against the
+  sparse FP64 form at the differentiation workload's size.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from workloads import WORKLOADS, make_x, omega0_for, sample_x_cpu, small_problem
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4     # gradient tolerance against the FP64 reference
+
+
+def _solved(lib, X, lam1, lam2, eps=1e-7):
+    import torch
+
+    Xt = torch.as_tensor(X).cuda()
+    s = lib.Solver(Xt, lam1, lam2, precision=lib.PREC_FP32, eps=eps, max_iter=20000)
+    s.solve()
+    return s, Xt
+
+
+def test_backward_matches_oracle_gradients(lib):
+    X = small_problem(260, 180, 4.0, 41).astype(np.float32)
+    lam1, lam2 = 0.12, 0.1
+    s, Xt = _solved(lib, X, lam1, lam2)
+    Om = s.omega_dense()
+    dO, dX = s.backward(Xt, grad_loss=1.0)
+    rO, rX = oracle.smooth_loss_grads(X.astype(np.float64), Om, lam2)
+    dO, dX = dO.double().cpu().numpy(), dX.double().cpu().numpy()
+    assert np.max(np.abs(dO - rO)) <= REL * np.max(np.abs(rO))
+    assert np.max(np.abs(dX - rX)) <= REL * np.max(np.abs(rX))
+    assert np.array_equal(dO, dO.T)
+    # scaling by the upstream derivative
+    dO2, dX2 = s.backward(Xt, grad_loss=-2.5)
+    assert np.allclose(dO2.double().cpu().numpy(), -2.5 * dO, rtol=1e-6, atol=1e-7)
+    assert np.allclose(dX2.double().cpu().numpy(), -2.5 * dX, rtol=1e-6, atol=1e-9)
+    s.close()
+
+
+def test_backward_domega_is_the_solvers_gradient_bitwise(lib):
+    X = small_problem(300, 200, 4.0, 42).astype(np.float32)
+    s, Xt = _solved(lib, X, 0.15, 0.1, eps=1e-4)
+    dO, _ = s.backward(Xt, dx=False)
+    s.iterate(1)                       # its gradient pass runs at the estimate backward used
+    r, c, _, g = s.candidates()
+    assert np.array_equal(dO.cpu().numpy()[r, c].astype(np.float64), g)
+    s.close()
+
+
+def test_smooth_value_matches_oracle(lib):
+    X = small_problem(200, 150, 3.0, 43).astype(np.float32)
+    s, Xt = _solved(lib, X, 0.1, 0.1)
+    f = s.smooth_value()
+    ref = oracle.smooth_loss(X.astype(np.float64), s.omega_dense(), 0.1)
+    assert f == pytest.approx(ref, rel=1e-6)
+    s.close()
+
+
+@pytest.mark.parametrize("form", ["values", "dense"])
+def test_autograd_function(lib, form):
+    import torch
+
+    X = small_problem(180, 120, 3.0, 44).astype(np.float32)
+    lam2 = 0.1
+    s, Xt = _solved(lib, X, 0.12, lam2)
+    Om = s.omega_dense()
+    rO, rX = oracle.smooth_loss_grads(X.astype(np.float64), Om, lam2)
+    Xg = Xt.clone().requires_grad_(True)
+    if form == "values":
+        rp, ci, v = s.omega_values()
+        om = v.clone().requires_grad_(True)
+    else:
+        om = torch.as_tensor(Om, dtype=torch.float32, device="cuda").requires_grad_(True)
+    loss = lib.concord_smooth_loss(Xg, om, s)
+    assert float(loss) == pytest.approx(oracle.smooth_loss(X.astype(np.float64), Om, lam2), rel=1e-6)
+    (3.0 * loss).backward()
+    gx = Xg.grad.double().cpu().numpy()
+    assert np.max(np.abs(gx - 3.0 * rX)) <= REL * 3.0 * np.max(np.abs(rX))
+    go = om.grad.double().cpu().numpy()
+    if form == "values":
+        rows = np.repeat(np.arange(180), np.diff(rp.cpu().numpy()))
+        ref = 3.0 * rO[rows, ci.cpu().numpy()]
+    else:
+        ref = 3.0 * rO
+    assert np.max(np.abs(go - ref)) <= REL * np.max(np.abs(ref))
+    s.close()
+
+
+def test_hypergrad_matches_dense_oracle(lib):
+    import torch
+
+    p = 60
+    Xtr = small_problem(p, 90, 3.0, 45).astype(np.float32)
+    Xva = small_problem(p, 50, 3.0, 46).astype(np.float32)
+    lam1, lam2 = 0.1, 0.15
+    s, Xt = _solved(lib, Xtr, lam1, lam2)
+    d1, d2, info = s.hypergrad(torch.as_tensor(Xva).cuda(), tol=1e-10)
+    assert info["converged"] == 1
+    Om = s.omega_dense()
+    r1, r2 = oracle.hypergrad(oracle.gram(Xtr), oracle.gram(Xva), Om, lam1, lam2)
+    assert d1 == pytest.approx(r1, rel=REL)
+    assert d2 == pytest.approx(r2, rel=REL)
+    # and at the oracle's own estimate: the end-to-end value
+    ref_om = oracle.solve(oracle.gram(Xtr), lam1, lam2, eps=1e-9, max_iter=100000).omega
+    assert np.array_equal(ref_om != 0, Om != 0)
+    e1, e2 = oracle.hypergrad(oracle.gram(Xtr), oracle.gram(Xva), ref_om, lam1, lam2)
+    assert d1 == pytest.approx(e1, rel=1e-3) and d2 == pytest.approx(e2, rel=1e-3)
+    s.close()
+
+
+@pytest.mark.slow
+def test_differentiation_workload_full_size(lib):
+    """p = 16384, n = 4096 train + 2048 held-out (same Omega0 law): backward at sampled
+    entries and the hypergradient against the sparse FP64 reference on the GPU's support."""
+    import torch
+
+    w = WORKLOADS["adjoint_p16384"]
+    om0 = omega0_for(w)
+    from workloads import sample_x_cuda
+
+    Xtr = sample_x_cuda(om0, w.n, w.seed)
+    Xva = sample_x_cuda(om0, 2048, w.seed + 7919)
+    s = lib.Solver(Xtr, w.lambda1, w.lambda2, precision=lib.PREC_FP32, eps=1e-6, max_iter=20000)
+    s.solve()
+    d1, d2, info = s.hypergrad(Xva, tol=1e-10)
+    assert info["converged"] == 1
+    csr = s.get_omega().to_scipy(w.p)
+    Xh, Xvh = Xtr.cpu().numpy(), Xva.cpu().numpy()
+    r1, r2 = oracle.hypergrad_sparse(Xh, Xvh, csr, w.lambda1, w.lambda2)
+    assert d1 == pytest.approx(r1, rel=REL) and d2 == pytest.approx(r2, rel=REL)
+    # backward: dL/dX and dL/dOmega at sampled entries against FP64 formulas from X
+    dO, dX = s.backward(Xtr)
+    rng = np.random.default_rng(0)
+    ri = rng.integers(0, w.p, 300)
+    rj = rng.integers(0, w.p, 300)
+    gref = oracle.gradient_entries(Xh, csr, w.lambda2, ri, rj)
+    got = dO[torch.as_tensor(ri).cuda(), torch.as_tensor(rj).cuda()].double().cpu().numpy()
+    assert np.max(np.abs(got - gref)) <= REL * max(np.max(np.abs(gref)), 1.0)
+    rr = rng.integers(0, w.n, 20)
+    Y = Xh[rr].astype(np.float64) @ csr          # rows of X Omega
+    dx_ref = (Y @ csr) / w.n
+    dx_got = dX[torch.as_tensor(rr).cuda()].double().cpu().numpy()
+    assert np.max(np.abs(dx_got - dx_ref)) <= REL * np.max(np.abs(dx_ref))
+    s.close()

@@ -270,3 +270,73 @@ def test_entry_helpers_match_dense():
     assert np.allclose(oracle.gradient_entries(X, om, 0.1, r, c), G[r, c], rtol=1e-10, atol=1e-13)
     assert oracle.smooth_sparse_from_S(S, om, 0.1) == pytest.approx(
         oracle.smooth(res.omega, oracle.times_S(res.omega, S), 0.1), rel=1e-12)
+
+
+# ------------------------------------------------------------------ differentiation
+
+def test_smooth_loss_grads_by_central_differences():
+    """dL/dX is exact for central differences (L is quadratic in X); dL/dOmega to O(h^2)."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((9, 6))
+    A = rng.standard_normal((6, 6)) * 0.1
+    Om = np.eye(6) * 1.5 + A                      # deliberately not symmetric
+    lam2 = 0.3
+    dOm, dX = oracle.smooth_loss_grads(X, Om, lam2)
+    h = 1e-3
+    for (a, b) in [(0, 0), (1, 3), (4, 2), (5, 5)]:
+        E = np.zeros_like(Om)
+        E[a, b] = 1.0
+        fd = (oracle.smooth_loss(X, Om + h * E, lam2) - oracle.smooth_loss(X, Om - h * E, lam2)) / (2 * h)
+        assert dOm[a, b] == pytest.approx(fd, rel=1e-5, abs=1e-7)
+    for (a, b) in [(0, 0), (3, 1), (8, 5)]:
+        E = np.zeros_like(X)
+        E[a, b] = 1.0
+        fd = (oracle.smooth_loss(X + h * E, Om, lam2) - oracle.smooth_loss(X - h * E, Om, lam2)) / (2 * h)
+        assert dX[a, b] == pytest.approx(fd, rel=1e-9, abs=1e-12)
+
+
+def test_smooth_loss_grads_reduce_to_G_and_Y_Omega_at_symmetric_omega():
+    X, S = _rand_problem(10, 14, 3)
+    Om = oracle.solve(S, 0.1, 0.2, eps=1e-7).omega
+    dOm, dX = oracle.smooth_loss_grads(X, Om, 0.2)
+    assert np.allclose(dOm, oracle.gradient(Om, oracle.times_S(Om, S), 0.2), rtol=1e-12, atol=1e-12)
+    assert np.allclose(dX, (X @ Om) @ Om / X.shape[0], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_hypergrad_by_central_differences_of_resolved_estimates(seed):
+    """Implicit lambda-gradients against central differences (h = 1e-3) of L_val at re-solved
+    estimates, on a support that stays constant over [lambda - h, lambda + h]."""
+    p = 12
+    Xtr = small_problem(p, 40, 3.0, 100 + seed)
+    Xva = small_problem(p, 30, 3.0, 200 + seed)
+    S, Sv = oracle.gram(Xtr), oracle.gram(Xva)
+    lam2, h = 0.15, 1e-3
+    sol = lambda l1, l2: oracle.solve(S, l1, l2, eps=1e-9, max_iter=200000).omega
+    # the gradient exists where the support is locally constant: take the first such lambda1
+    for lam1 in (0.12, 0.1, 0.14, 0.16, 0.09):
+        Om = sol(lam1, lam2)
+        ups = [sol(lam1 + h, lam2), sol(lam1 - h, lam2), sol(lam1, lam2 + h), sol(lam1, lam2 - h)]
+        if all(np.array_equal(U != 0, Om != 0) for U in ups):
+            break
+    else:
+        pytest.fail("no lambda1 with a support constant on the stencil")
+    g1, g2 = oracle.hypergrad(S, Sv, Om, lam1, lam2)
+    fd1 = (oracle.heldout_loss(Sv, ups[0]) - oracle.heldout_loss(Sv, ups[1])) / (2 * h)
+    fd2 = (oracle.heldout_loss(Sv, ups[2]) - oracle.heldout_loss(Sv, ups[3])) / (2 * h)
+    assert g1 == pytest.approx(fd1, rel=2e-3, abs=1e-5)
+    assert g2 == pytest.approx(fd2, rel=2e-3, abs=1e-5)
+
+
+def test_sparse_hypergrad_equals_dense_hypergrad():
+    """The large-p form (sparse H from single S entries) against the dense form."""
+    import scipy.sparse as sp
+
+    p = 15
+    Xtr = small_problem(p, 50, 3.0, 300)
+    Xva = small_problem(p, 35, 3.0, 301)
+    S, Sv = oracle.gram(Xtr), oracle.gram(Xva)
+    Om = oracle.solve(S, 0.1, 0.2, eps=1e-9, max_iter=100000).omega
+    a = oracle.hypergrad(S, Sv, Om, 0.1, 0.2)
+    b = oracle.hypergrad_sparse(Xtr, Xva, sp.csr_matrix(Om), 0.1, 0.2)
+    assert a[0] == pytest.approx(b[0], rel=1e-10) and a[1] == pytest.approx(b[1], rel=1e-10)
