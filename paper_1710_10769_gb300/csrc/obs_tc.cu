@@ -1,0 +1,392 @@
+// Obs variant (Alg. 3): the products that replace S.
+//
+//   Y^T = Omega X^T (p x n)            row-split SpMM (adjoint.cu), canonical order
+//   Z   = Y X / n = Y^T (X^T)^T / n    this file: tcgen05 GEMM on K-major panels
+//
+// Z equals W = Omega S, so the screening rule of the Cov pass applies: an entry
+// can enter a prox step only if it is in the support or |G_ij| > lambda1, and
+// |G_ij| > lambda1 needs max(|Z_ij|, |Z_ji|) > lambda1.  One CTA computes the
+// tile pair Z[I, J] and Z[J, I] (I <= J, 128 x 128 tiles) into two TMEM
+// accumulators, transposes the second through shared memory, and emits both
+// (i, j) and (j, i) -- flagged as paired, so no partner request follows -- for
+// every pair in the support or above the threshold (Alg. 3 steps 4-6 with the
+// transpose done inside the CTA).  Z is never stored.
+//
+// Operands are BF16 hi/lo panels (BF16X3: hi*hi + hi*lo + lo*hi) or TF32
+// panels, K-major, zero padded; loaded by TMA (128-byte swizzle) through an
+// mbarrier ring; every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+#include "ptx.cuh"
+
+namespace hpc {
+namespace {
+
+constexpr int kT = 128;                    // tile edge (UMMA M = N = 128)
+constexpr int kRowB = 128;                 // bytes per swizzle row
+constexpr int kPanelTile = kT * kRowB;     // 16 KB
+constexpr uint32_t kTmemCols = 256;        // two 128-column FP32 accumulators
+constexpr long long kWaitLimit = 1ll << 26;
+
+enum : int { kObsBf16x3 = 0, kObsTf32 = 1 };
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int MODE>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if constexpr (MODE == kObsTf32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     ptx::smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// K-major, 128-byte swizzle, 8-row groups 1024 bytes apart, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+template <int MODE>
+__host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4) | ((MODE == kObsTf32 ? 2u : 1u) << 7) | ((MODE == kObsTf32 ? 2u : 1u) << 10) |
+           ((uint32_t)(kT >> 3) << 17) | ((uint32_t)(kT >> 4) << 24);
+}
+
+template <int MODE>
+struct ObsCfg {
+    static constexpr int kPieces = MODE == kObsBf16x3 ? 2 : 1;
+    static constexpr int kTerms = MODE == kObsBf16x3 ? 3 : 1;
+    static constexpr int kElem = MODE == kObsTf32 ? 4 : 2;
+    static constexpr int kBK = kRowB / kElem;
+    static constexpr int kMmaK = 32 / kElem;
+    static constexpr int kStageBytes = kPieces * 2 * kPanelTile;    // A and B tiles, each piece
+    static constexpr int kStages = MODE == kObsBf16x3 ? 3 : 5;
+    static constexpr int kTransBytes = kT * (kT + 1) * 4;           // Z[J, I] staged for the transpose
+    static constexpr int kSmem = (kStages * kStageBytes > kTransBytes ? kStages * kStageBytes : kTransBytes) + 1024 +
+                                 256;
+};
+
+__device__ int g_obs_error = 0;
+
+// Pair (bi, bj), bi <= bj, of 128-row blocks; Z[I, J] = Y^T[I] X^T[J]^T / n and
+// Z[J, I] = Y^T[J] X^T[I]^T / n; emission of both sides.
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUtensorMap yb,
+           const __grid_constant__ CUtensorMap xa, const __grid_constant__ CUtensorMap xb, const int2* __restrict__ pairs,
+           int k_tiles, int p, int64_t n, const int* __restrict__ rp, const int* __restrict__ ci,
+           const float* __restrict__ cv, float lam1, Emit<float> em, Ctrl* __restrict__ ctrl) {
+    using C = ObsCfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int region = C::kStages * C::kStageBytes > C::kTransBytes ? C::kStages * C::kStageBytes : C::kTransBytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + region);
+    uint64_t* empty = full + C::kStages;
+    uint64_t* accum = empty + C::kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 pr = pairs[blockIdx.x];
+    const int I0 = pr.x * kT, J0 = pr.y * kT;
+    const bool diag_pair = pr.x == pr.y;
+    const int phases = diag_pair ? 1 : 2;
+    const int items = phases * k_tiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], 1); }
+        ptx::mbar_init(accum, 1);
+        *abort_flag = 0;
+        ptx::mbar_init_fence();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        // producer: phase 0 streams (Y^T[I], X^T[J]), phase 1 (Y^T[J], X^T[I])
+        for (int t = 0; t < items; ++t) {
+            const int s = t % C::kStages;
+            const uint32_t ph = (uint32_t)(t / C::kStages) & 1u;
+            if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, kWaitLimit)) {
+                atomicCAS(&g_obs_error, 0, 1);
+                break;
+            }
+            const int phase = t / k_tiles, kt = t % k_tiles;
+            const int ra = phase == 0 ? I0 : J0, rb = phase == 0 ? J0 : I0;
+            uint8_t* st = smem + s * C::kStageBytes;
+            ptx::mbar_expect_tx(&full[s], C::kStageBytes);
+            const int kc = kt * C::kBK;
+            ptx::tma_load_2d(st, &ya, &full[s], kc, ra);
+            ptx::tma_load_2d(st + kPanelTile, &xa, &full[s], kc, rb);
+            if (C::kPieces > 1) {
+                ptx::tma_load_2d(st + 2 * kPanelTile, &yb, &full[s], kc, ra);
+                ptx::tma_load_2d(st + 3 * kPanelTile, &xb, &full[s], kc, rb);
+            }
+            ++issued;
+        }
+    } else if (threadIdx.x == 32) {
+        constexpr uint32_t idesc = instr_desc<MODE>();
+        for (int t = 0; t < items; ++t) {
+            const int s = t % C::kStages;
+            const uint32_t ph = (uint32_t)(t / C::kStages) & 1u;
+            if (!ptx::mbar_wait_bounded(&full[s], ph, abort_flag, kWaitLimit)) {
+                atomicCAS(&g_obs_error, 0, 2);
+                break;
+            }
+            tc_fence_after();
+            const int phase = t / k_tiles, kt = t % k_tiles;
+            const uint32_t d = tmem + (uint32_t)(phase * kT);
+            const uint32_t st = ptx::smem_u32(smem + s * C::kStageBytes);
+            const uint32_t a_hi = st, b_hi = st + kPanelTile, a_lo = st + 2 * kPanelTile, b_lo = st + 3 * kPanelTile;
+#pragma unroll
+            for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+                umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
+                if constexpr (C::kTerms == 3) {
+                    umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+                    umma<MODE>(d, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+                }
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(accum);
+    }
+    __syncwarp();
+
+    // ---------------- epilogue
+    bool have = ptx::mbar_wait_bounded(accum, 0, abort_flag, kWaitLimit) && !*abort_flag;
+    have = __all_sync(kFull, have);
+    tc_fence_after();
+    __syncthreads();      // every stage consumed: the ring's memory now holds the transpose tile
+    float* zt = reinterpret_cast<float*>(smem);      // [kT][kT + 1]
+    const int r = warp * 32 + lane;                   // TMEM lane = local row
+    const float dn = (float)n;
+    if (have) {
+        // stage the second accumulator (Z[J, I], or Z[I, I] for a diagonal pair) row by row
+        const uint32_t src = diag_pair ? 0u : (uint32_t)kT;
+        for (int c0 = 0; c0 < kT; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + src + (uint32_t)c0, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) zt[r * (kT + 1) + c0 + q] = __uint_as_float(v[q]) / dn;
+        }
+    }
+    __syncthreads();
+    if (have) {
+        const int i = I0 + r;
+        // this row's support entries in columns [J0, J0 + kT), consumed in column order
+        int q = 0, qe = 0;
+        if (i < p) {
+            q = rp[i];
+            qe = rp[i + 1];
+            while (q < qe && ci[q] < J0) ++q;
+        }
+        for (int c0 = 0; c0 < kT; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld_wait();
+            if (i >= p) continue;
+            for (int cc = 0; cc < 32; ++cc) {
+                const int c = c0 + cc;
+                const int j = J0 + c;
+                if (j >= p) break;
+                while (q < qe && ci[q] < j) ++q;             // support merge, column order
+                if (diag_pair && j < i) continue;            // the (j, i) thread emits this pair
+                const float a = __uint_as_float(v[cc]) / dn; // Z_ij
+                const float b = zt[c * (kT + 1) + r];         // Z_ji
+                const bool sup = q < qe && ci[q] == j;
+                const float om = sup ? cv[q] : 0.f;
+                const bool big = !(fabsf(a) <= lam1) || !(fabsf(b) <= lam1);
+                if (!(sup || big || i == j)) continue;
+                const int cnt = (i == j) ? 1 : 2;
+                const int pos = atomicAdd(&ctrl->em_count, cnt);
+                const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);   // paired, support
+                if (pos < em.cap) {
+                    em.row[pos] = i;
+                    em.col[pos] = (int)((unsigned)j | fl);
+                    em.w[pos] = a;
+                    em.om[pos] = om;
+                }
+                if (i != j && pos + 1 < em.cap) {
+                    em.row[pos + 1] = j;
+                    em.col[pos + 1] = (int)((unsigned)i | fl);
+                    em.w[pos + 1] = b;
+                    em.om[pos + 1] = om;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) {
+            atomicOr(&ctrl->flags, kFlagTimeout);
+            for (int t = max(0, issued - C::kStages); t < issued; ++t) {
+                const int s = t % C::kStages;
+                const uint32_t ph = (uint32_t)(t / C::kStages) & 1u;
+                for (long long it = 0; it < (1ll << 22) && !ptx::mbar_try_wait(&full[s], ph); ++it) __nanosleep(64);
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// FP32 rows (rows x ldi, K contiguous) -> K-major panels (rows_pad x n_pad) of the MMA input type.
+template <int MODE>
+__global__ void k_obs_split(const float* __restrict__ in, int64_t rows, int64_t cols, int64_t ldi, void* hi, void* lo,
+                            int64_t rows_pad, int64_t n_pad) {
+    const int64_t total = rows_pad * n_pad;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / n_pad, k = t % n_pad;
+        const float x = (r < rows && k < cols) ? in[r * ldi + k] : 0.f;
+        if constexpr (MODE == kObsTf32) {
+            uint32_t u;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+            static_cast<float*>(hi)[t] = __uint_as_float(u);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            static_cast<__nv_bfloat16*>(hi)[t] = h;
+            static_cast<__nv_bfloat16*>(lo)[t] = __float2bfloat16_rn(x - __bfloat162float(h));
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+size_t obs_panel_bytes(int precision, int64_t n, int64_t p) {
+    const int64_t p_pad = (p + kT - 1) / kT * kT, n_pad = (n + 63) / 64 * 64;
+    const int es = precision == HPC_PREC_TF32 ? 4 : 2;
+    return ((size_t)p_pad * n_pad * es + 1023) / 1024 * 1024;
+}
+
+int obs_pieces(int precision) { return precision == HPC_PREC_TF32 ? 1 : 2; }
+
+int64_t obs_npairs(int64_t p) {
+    const int64_t nb = (p + kT - 1) / kT;
+    return nb * (nb + 1) / 2;
+}
+
+void obs_pair_list(int64_t p, std::vector<int2>& out) {
+    const int64_t nb = (p + kT - 1) / kT;
+    out.clear();
+    // bands of 8 row blocks, columns left to right: pairs in flight share panels in L2
+    for (int64_t b0 = 0; b0 < nb; b0 += 8)
+        for (int64_t bj = 0; bj < nb; ++bj)
+            for (int64_t bi = b0; bi < std::min<int64_t>(b0 + 8, nb); ++bi)
+                if (bi <= bj) out.push_back(make_int2((int)bi, (int)bj));
+}
+
+void launch_obs_split(int precision, const float* in, int64_t rows, int64_t cols, int64_t ldi, void* hi, void* lo,
+                      int64_t n, int64_t p, cudaStream_t s) {
+    const int64_t rows_pad = (p + kT - 1) / kT * kT, n_pad = (n + 63) / 64 * 64;
+    if (precision == HPC_PREC_TF32)
+        k_obs_split<kObsTf32><<<2048, 256, 0, s>>>(in, rows, cols, ldi, hi, lo, rows_pad, n_pad);
+    else
+        k_obs_split<kObsBf16x3><<<2048, 256, 0, s>>>(in, rows, cols, ldi, hi, lo, rows_pad, n_pad);
+}
+
+bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void* x_hi, const void* x_lo, int64_t n,
+                   int64_t p, CUtensorMap* maps /*4: ya, yb, xa, xb*/) {
+    const int64_t p_pad = (p + kT - 1) / kT * kT, n_pad = (n + 63) / 64 * 64;
+    const int es = precision == HPC_PREC_TF32 ? 4 : 2;
+    const void* bases[4] = {y_hi, precision == HPC_PREC_TF32 ? y_hi : y_lo, x_hi,
+                            precision == HPC_PREC_TF32 ? x_hi : x_lo};
+    for (int t = 0; t < 4; ++t)
+        if (!encode_tensor_map_2d_sw128(&maps[t], bases[t], es, (uint64_t)n_pad, (uint64_t)p_pad,
+                                        (uint64_t)n_pad * es, (uint32_t)(kRowB / es), (uint32_t)kT))
+            return false;
+    return true;
+}
+
+cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
+                             int p, const int* rp, const int* ci, const float* cv, float lam1, Emit<float> em,
+                             Ctrl* ctrl, cudaStream_t s) {
+    const int64_t n_pad = (n + 63) / 64 * 64;
+    if (precision == HPC_PREC_TF32) {
+        using C = ObsCfg<kObsTf32>;
+        cudaError_t e = cudaFuncSetAttribute(k_obs_pair<kObsTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        if (e != cudaSuccess) return e;
+        k_obs_pair<kObsTf32><<<(unsigned)npairs, 128, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
+                                                                     (int)(n_pad / C::kBK), p, n, rp, ci, cv,
+                                                                     lam1, em, ctrl);
+    } else {
+        using C = ObsCfg<kObsBf16x3>;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_obs_pair<kObsBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        if (e != cudaSuccess) return e;
+        k_obs_pair<kObsBf16x3><<<(unsigned)npairs, 128, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
+                                                                       (int)(n_pad / C::kBK), p, n, rp, ci, cv,
+                                                                       lam1, em, ctrl);
+    }
+    return cudaGetLastError();
+}
+
+int obs_take_error() {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_obs_error, sizeof v) != cudaSuccess) return -1;
+    if (v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_obs_error, &z, sizeof z);
+    }
+    return v;
+}
+
+}  // namespace hpc
