@@ -98,6 +98,37 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_over_ranks(ms, iters, pg, device):
+    """Slowest rank's time and the summed iterations of all ranks (replicas)."""
+    if pg is None:
+        return float(ms), float(iters)
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
+def screen_traffic(p):
+    """DRAM bytes of one screening pass from the committed ncu summary, scaled to p
+    (the pass streams S once: bytes grow as p^2); None when the summary was taken on a
+    different version of the kernels' source."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "grad_screen_traffic.txt")
+    src = os.path.join(ROOT, "paper_1710_10769_gb300", "csrc", "iterate.cu")
+    try:
+        kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
+        with open(src, "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != kv["iterate_cu_sha256"]:
+                return None
+        return float(kv["dram_bytes_per_pass"]) * (p / float(kv["p"])) ** 2
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -233,14 +264,7 @@ def main(argv=None):
         pg.barrier()
     ms = ev0.elapsed_time(ev1)
     iters = sum(r["iterations"] for r in recs)
-    if pg:
-        t = torch.tensor([ms, float(iters)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax[:1], op=pg.ReduceOp.MAX)
-        pg.all_reduce(t[1:], op=pg.ReduceOp.SUM)
-        ms_all, iters_all = float(tmax[0]), float(t[1])
-    else:
-        ms_all, iters_all = ms, float(iters)
+    ms_all, iters_all = reduce_over_ranks(ms, iters, pg, "cuda")
     value = iters_all / (ms_all / 1000.0)
 
     # dominant kernel: the Gram (one launch per step) or the screening SpMM (one per iteration)
@@ -266,7 +290,7 @@ def main(argv=None):
         per = scr_ms / max(scr_launches, 1) / 1000.0
         achieved = 4.0 * p * p / per / 1e9           # S read once per pass (FP32), bytes / launch time
         roof = {"kernel": "grad_screen", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": peak_src}
+                "frac": achieved / hbm, "traffic": screen_traffic(p), "peak_source": peak_src}
 
     # end to end through the C ABI with host buffers: H2D of X inside the timed region,
     # D2H of the CSR result
