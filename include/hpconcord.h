@@ -84,7 +84,13 @@ typedef struct {
     int64_t capacity;       /* initial candidate capacity in entries (0 = 32 p)        */
     int64_t max_capacity;   /* growth limit in entries (0 = p*p)                       */
     int32_t x_on_host;      /* X passed to hpc_create / hpc_load_x is a host pointer   */
-    int32_t timing;         /* record CUDA events per phase into hpc_stats (1)         */
+    int32_t timing;         /* time the phases into hpc_stats (1): CUDA events around
+                               each screening pass, or device timestamps in the device
+                               loop                                                    */
+    int32_t device_loop;    /* 1 (default): the iteration and line-search loops run on
+                               the device, one CUDA-graph launch per solve (conditional
+                               WHILE nodes); 0: the host drives every iteration       */
+    int32_t reserved_;
 } hpc_options;
 
 typedef struct {
@@ -184,6 +190,16 @@ typedef struct {
  * (its status says which); HPC_ERR_CAPACITY if col/val are too short. */
 int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
                    int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout);
+
+/* Solve `count` independent problems (handles created on distinct CUDA streams)
+ * concurrently: a pool of at most `threads` host threads (0 = one per handle)
+ * drives the handles' solves, so their kernels overlap on the GPU and their
+ * host synchronisation points overlap in time.  stats (host, count entries,
+ * may be NULL) receives each handle's hpc_solve statistics.  Returns HPC_OK if
+ * every solve returned HPC_OK, HPC_NOT_CONVERGED if any stopped at max_iter, and
+ * otherwise the first error (by handle index); per-handle statuses are in
+ * stats[t].status.  Handles sharing a stream are solved one after another. */
+int hpc_solve_batch(hpc_handle* handles, int count, int threads, hpc_stats* stats);
 
 /* Read m entries S_{rows[t], cols[t]} of the Cov sample covariance into out
  * (FP64, host arrays).  For checking the Gram at sizes where S is too large to

@@ -29,7 +29,7 @@ class Options(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_iter", C.c_int64), ("max_halvings", C.c_int32),
                 ("precision", C.c_int32), ("value_dtype", C.c_int32), ("ls_window", C.c_int32),
                 ("capacity", C.c_int64), ("max_capacity", C.c_int64), ("x_on_host", C.c_int32),
-                ("timing", C.c_int32)]
+                ("timing", C.c_int32), ("device_loop", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -92,6 +92,7 @@ _SIGS = {
     "hpc_get_omega": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int, C.c_int]),
     "hpc_set_omega": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_int, C.c_int]),
     "hpc_set_lambda": (C.c_int, [_P, C.c_double, C.c_double]),
+    "hpc_solve_batch": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.POINTER(Stats)]),
     "hpc_solve_path": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "hpc_get_s_entries": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "hpc_get_candidates": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, _P]),
@@ -465,3 +466,14 @@ def concord_smooth_loss(X, omega, solver):
     if _SMOOTH_LOSS is None:
         _SMOOTH_LOSS = _make_smooth_loss()
     return _SMOOTH_LOSS.apply(X, omega, solver)
+
+
+def solve_batch(solvers, threads=0):
+    """Solve independent problems concurrently (``hpc_solve_batch``); each Solver should have
+    been created on its own CUDA stream.  Returns the list of per-problem stats dicts."""
+    lib = load()
+    k = len(solvers)
+    hs = (C.c_void_p * max(k, 1))(*[s._h for s in solvers])
+    st = (Stats * max(k, 1))()
+    _check(lib.hpc_solve_batch(hs, k, int(threads), st), "hpc_solve_batch", (OK, NOT_CONVERGED))
+    return [st[t].as_dict() for t in range(k)]

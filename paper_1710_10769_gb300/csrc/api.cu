@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -79,6 +81,8 @@ struct hpc_ctx {
     void* em_w = nullptr;
     void* em_om = nullptr;
     int* bk_cnt = nullptr; int* bk_off = nullptr; int* bk_cur = nullptr; int* bk_len = nullptr;
+    long long* bk_uoff = nullptr;
+    int2* bk_mir = nullptr;
     int* col_a = nullptr; void* w_a = nullptr; void* om_a = nullptr; unsigned char* fl_a = nullptr;
     int* col_b = nullptr; void* w_b = nullptr; void* om_b = nullptr; unsigned char* fl_b = nullptr;
     void* g_b = nullptr;
@@ -102,6 +106,15 @@ struct hpc_ctx {
     cudaEvent_t ev_scr0 = nullptr, ev_scr1 = nullptr;
     int64_t regrows = 0;
     double ms_gram = 0.0;
+    // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
+    // WHILE node) captured on a private stream; rebuilt when a buffer it captured
+    // is reallocated (epoch), when the current CSR buffer changes, or with timing
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t epoch = 0;
+    int64_t g_epoch = -1;
+    int g_cur = -1, g_timing = -1;
     // differentiation scratch (grown on demand)
     void* adj_buf = nullptr;
     size_t adj_bytes = 0;
@@ -120,11 +133,12 @@ namespace {
 
 void free_candidates(hpc_ctx* h) {
     void* ptrs[] = {h->em_row, h->em_col, h->em_w, h->em_om, h->col_a, h->w_a, h->om_a, h->fl_a,
-                    h->col_b, h->w_b, h->om_b, h->fl_b, h->g_b};
+                    h->col_b, h->w_b, h->om_b, h->fl_b, h->g_b, h->bk_mir};
     for (void* q : ptrs) if (q) cudaFree(q);
     h->em_row = h->em_col = nullptr; h->em_w = h->em_om = nullptr;
     h->col_a = h->col_b = nullptr; h->w_a = h->om_a = h->w_b = h->om_b = h->g_b = nullptr;
     h->fl_a = h->fl_b = nullptr;
+    h->bk_mir = nullptr;
 }
 
 int alloc_candidates(hpc_ctx* h, int64_t cap) {
@@ -144,7 +158,9 @@ int alloc_candidates(hpc_ctx* h, int64_t cap) {
     CUDA_TRY(cudaMalloc(&h->om_b, bcap * vs));
     CUDA_TRY(cudaMalloc(&h->fl_b, bcap));
     CUDA_TRY(cudaMalloc(&h->g_b, bcap * vs));
+    CUDA_TRY(cudaMalloc(&h->bk_mir, bcap * sizeof(int2)));
     h->cap = cap;
+    h->epoch += 1;
     return HPC_OK;
 }
 
@@ -167,6 +183,7 @@ int grow_csr(hpc_ctx* h, int64_t newcap) {
         h->cv[b] = cv;
     }
     h->csr_cap = newcap;
+    h->epoch += 1;
     return HPC_OK;
 }
 
@@ -194,6 +211,8 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.bk.col_a = h->col_a; b.bk.w_a = as<T>(h->w_a); b.bk.om_a = as<T>(h->om_a); b.bk.fl_a = h->fl_a;
     b.bk.col_b = h->col_b; b.bk.w_b = as<T>(h->w_b); b.bk.om_b = as<T>(h->om_b); b.bk.fl_b = h->fl_b;
     b.bk.g = as<T>(h->g_b);
+    b.bk.uoff = h->bk_uoff;
+    b.bk.mir = h->bk_mir;
     b.bk.cap = (int)std::min<int64_t>(2 * h->cap, 0x7fffffff);
     b.cnt2 = h->cnt2;
     b.part_obj = h->part_obj;
@@ -249,14 +268,13 @@ int regrow(hpc_ctx* h, int64_t need) {
 
 // Obs (Alg. 3 steps 2, 4-6): Y^T = Omega X^T, its MMA panels, and the paired-tile
 // Z GEMM with the screening emission.
-int obs_screen(hpc_ctx* h, const hpc::IterBufs<float>& b) {
+int obs_screen(hpc_ctx* h, const hpc::IterBufs<float>& b, cudaStream_t s) {
     const int p = (int)h->p;
-    hpc::launch_row_info<float>(p, b.cur, h->rinfo, as<float>(h->rdv), h->stream);
-    hpc::launch_spmm_dense<float>(p, b.cur, h->rinfo, as<float>(h->rdv), h->xt, h->ldx, h->ldx, h->yt, h->ldx,
-                                  h->stream);
-    hpc::launch_obs_split(h->precision, h->yt, p, h->ldx, h->ldx, h->yp[0], h->yp[1], h->n, h->p, h->stream);
+    hpc::launch_row_info<float>(p, b.cur, h->rinfo, as<float>(h->rdv), s);
+    hpc::launch_spmm_dense<float>(p, b.cur, h->rinfo, as<float>(h->rdv), h->xt, h->ldx, h->ldx, h->yt, h->ldx, s);
+    hpc::launch_obs_split(h->precision, h->yt, p, h->ldx, h->ldx, h->yp[0], h->yp[1], h->n, h->p, s);
     cudaError_t e = hpc::launch_obs_pairs(h->precision, h->obs_maps, h->pairs, h->npairs, h->n, p, b.cur.rp, b.cur.ci,
-                                          b.cur.cv, (float)h->lam1, b.em, h->d_ctrl, h->stream);
+                                          b.cur.cv, b.em, h->d_ctrl, s);
     if (e != cudaSuccess) { set_cuda_error(e, "obs pair GEMM", __LINE__); return HPC_ERR_CUDA; }
     return HPC_OK;
 }
@@ -266,10 +284,11 @@ template <typename T>
 int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
     for (int attempt = 0; attempt < 64; ++attempt) {
         hpc::IterBufs<T> b = bufs<T>(h);
-        hpc::launch_iter_begin<T>(b, h->stream);
+        const hpc::LoopCond host_loop{};
+        hpc::launch_iter_begin<T>(b, host_loop, h->stream);
         if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_scr0, h->stream));
         if constexpr (std::is_same<T, float>::value) {
-            if (h->variant == HPC_OBS) STATUS_TRY(obs_screen(h, b));
+            if (h->variant == HPC_OBS) STATUS_TRY(obs_screen(h, b, h->stream));
             else hpc::launch_grad_screen<T>(b, h->stream);
         } else {
             hpc::launch_grad_screen<T>(b, h->stream);
@@ -281,10 +300,10 @@ int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
         bool accepted = false, overflow = false;
         for (int hb = 0; hb <= h->opt.max_halvings; hb += h->opt.ls_window) {
             if constexpr (std::is_same<T, float>::value) {
-                if (h->variant == HPC_OBS) hpc::launch_ls_window_obs(b, hb, hb == 0, h->stream);
-                else hpc::launch_ls_window<T>(b, hb, hb == 0, h->stream);
+                if (h->variant == HPC_OBS) hpc::launch_ls_window_obs(b, host_loop, h->stream);
+                else hpc::launch_ls_window<T>(b, host_loop, h->stream);
             } else {
-                hpc::launch_ls_window<T>(b, hb, hb == 0, h->stream);
+                hpc::launch_ls_window<T>(b, host_loop, h->stream);
             }
             CUDA_TRY(cudaGetLastError());
             launches += hpc::kLaunchesLsWindow;
@@ -341,18 +360,228 @@ int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
     return HPC_ERR_CAPACITY;
 }
 
+// Reset the counters of the control block and load the solve's parameters
+// (lambda, iteration limit, stopping rule) into it.
+int load_ctrl(hpc_ctx* h, int64_t k, bool use_stop) {
+    hpc::Ctrl& c = *h->h_ctrl;
+    c.iter = 0;
+    c.ls_trials = 0;
+    c.ls_windows = 0;
+    c.iter_attempts = 0;
+    c.screen_ns = 0;
+    c.t_stamp = 0;
+    c.flags = 0;
+    c.converged = 0;
+    c.lam1 = h->lam1;
+    c.lam2 = h->lam2;
+    c.nnz_cur = (int)h->nnz;
+    c.iter_limit = (int)std::min<int64_t>(k, 0x7fffffff);
+    c.use_stop = use_stop ? 1 : 0;
+    CUDA_TRY(cudaMemcpyAsync(h->d_ctrl, h->h_ctrl, sizeof(hpc::Ctrl), cudaMemcpyHostToDevice, h->stream));
+    return HPC_OK;
+}
+
+void destroy_graph(hpc_ctx* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+    h->g_epoch = -1;
+}
+
+// The last node captured on stream cs (captures here are linear chains).
+int capture_leaf(cudaStream_t cs, cudaGraphNode_t* leaf) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    CUDA_TRY(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &nd));
+    if (st != cudaStreamCaptureStatusActive || nd != 1) {
+        std::snprintf(g_last_error, sizeof g_last_error, "device loop capture: unexpected capture state");
+        return HPC_ERR_CUDA;
+    }
+    *leaf = deps[0];
+    return HPC_OK;
+}
+
+// End a capture into an existing graph, keeping the first error.
+int end_capture(cudaStream_t cs, cudaGraph_t g, int status) {
+    cudaGraph_t out = g;
+    const cudaError_t e = cudaStreamEndCapture(cs, &out);
+    if (status != HPC_OK) return status;
+    CUDA_TRY(e);
+    CUDA_TRY(cudaGetLastError());
+    return HPC_OK;
+}
+
+int add_while(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHandle* hnd, cudaGraphNode_t* node,
+              cudaGraph_t* body) {
+    CUDA_TRY(cudaGraphConditionalHandleCreate(hnd, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = *hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    CUDA_TRY(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
+    *body = np.conditional.phGraph_out[0];
+    return HPC_OK;
+}
+
+template <typename T>
+int capture_screen(hpc_ctx* h, const hpc::IterBufs<T>& b, cudaStream_t cs) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->variant == HPC_OBS) return obs_screen(h, b, cs);
+    }
+    hpc::launch_grad_screen<T>(b, cs);
+    return HPC_OK;
+}
+
+template <typename T>
+void capture_window(hpc_ctx* h, const hpc::IterBufs<T>& b, const hpc::LoopCond& lc, cudaStream_t cs) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->variant == HPC_OBS) { hpc::launch_ls_window_obs(b, lc, cs); return; }
+    }
+    hpc::launch_ls_window<T>(b, lc, cs);
+}
+
+// Capture the device loop:
+//   WHILE (iteration condition) {
+//       begin, [stamp], screening pass, [stamp], candidates, gradient
+//       WHILE (line-search condition) { window evaluation, decision }
+//       compaction, stopping rule, commit of the accepted iterate
+//   }
+// k_iter_begin arms the line-search loop, k_ls_decide ends it, and the commit
+// kernel continues or ends the iteration loop.
+template <typename T>
+int build_graph(hpc_ctx* h) {
+    destroy_graph(h);
+    if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream;
+    const hpc::IterBufs<T> b = bufs<T>(h);
+    const bool timing = h->opt.timing != 0;
+    CUDA_TRY(cudaGraphCreate(&h->graph, 0));
+    hpc::LoopCond lc;
+    lc.use = 1;
+    cudaGraphNode_t outer, inner, leaf;
+    cudaGraph_t body, ls_body;
+    STATUS_TRY(add_while(h->graph, nullptr, &lc.iter, &outer, &body));
+    // line-search handle lives in the body that holds its node
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&lc.ls, body, 1, cudaGraphCondAssignDefault));
+    {
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        int st = HPC_OK;
+        hpc::launch_iter_begin<T>(b, lc, cs);
+        if (timing) hpc::launch_stamp(h->d_ctrl, 0, cs);
+        st = capture_screen<T>(h, b, cs);
+        if (st == HPC_OK) {
+            if (timing) hpc::launch_stamp(h->d_ctrl, 1, cs);
+            hpc::launch_candidates<T>(b, cs);
+            st = capture_leaf(cs, &leaf);
+        }
+        STATUS_TRY(end_capture(cs, body, st));
+    }
+    {
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = lc.ls;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        CUDA_TRY(cudaGraphAddNode(&inner, body, &leaf, nullptr, 1, &np));
+        ls_body = np.conditional.phGraph_out[0];
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, ls_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        capture_window<T>(h, b, lc, cs);
+        STATUS_TRY(end_capture(cs, ls_body, HPC_OK));
+    }
+    {
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, &inner, nullptr, 1, cudaStreamCaptureModeRelaxed));
+        hpc::launch_accept<T>(b, cs);
+        hpc::launch_commit<T>(b, lc, cs);
+        STATUS_TRY(end_capture(cs, body, HPC_OK));
+    }
+    CUDA_TRY(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->g_epoch = h->epoch;
+    h->g_cur = h->cur;
+    h->g_timing = timing ? 1 : 0;
+    return HPC_OK;
+}
+
+// Launches of one outer iteration of the device loop besides its line-search
+// windows (two each).
+int loop_launches(const hpc_ctx* h) {
+    return hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesCandidates + hpc::kLaunchesAccept + 1 +
+           (h->opt.timing ? 2 : 0);
+}
+
+// The device loop: one graph launch runs iterations until the stopping rule, the
+// iteration limit or a raised flag; the host only grows buffers after an
+// overflow (the failed iteration is repeated) and reads the control block.
+template <typename T>
+int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s) {
+    const int64_t regrows0 = h->regrows;
+    STATUS_TRY(load_ctrl(h, k, use_stop));
+    if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
+    int status = HPC_OK;
+    bool ran = false;
+    for (int attempt = 0; attempt < 64 && k > 0; ++attempt) {
+        if (!h->gexec || h->g_epoch != h->epoch || h->g_cur != h->cur || h->g_timing != (h->opt.timing ? 1 : 0))
+            STATUS_TRY(build_graph<T>(h));
+        CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
+        STATUS_TRY(read_ctrl(h));
+        const hpc::Ctrl& c = *h->h_ctrl;
+        h->nnz = c.nnz_cur;
+        ran = true;
+        if (c.flags & (hpc::kFlagEmOverflow | hpc::kFlagBucketOverflow)) {
+            STATUS_TRY(regrow(h, (int64_t)c.em_count + 1));
+            ran = false;
+            continue;
+        }
+        if (c.flags & hpc::kFlagNnzOverflow) {
+            STATUS_TRY(grow_csr(h, std::max<int64_t>(2 * h->csr_cap, (int64_t)c.nnz_next + 1)));
+            h->regrows += 1;
+            ran = false;
+            continue;
+        }
+        break;
+    }
+    if (k > 0 && !ran) return HPC_ERR_CAPACITY;
+    const hpc::Ctrl& c = *h->h_ctrl;
+    if (c.flags) {
+        status = flags_to_status(c.flags);
+        if (status == HPC_OK) status = HPC_ERR_CUDA;
+    } else if (use_stop) {
+        status = c.converged ? HPC_OK : HPC_NOT_CONVERGED;
+    }
+    if (h->opt.timing) {
+        CUDA_TRY(cudaEventRecord(h->ev[1], h->stream));
+        CUDA_TRY(cudaEventSynchronize(h->ev[1]));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+        s->ms_total = ms;
+        s->ms_grad_pass = (double)c.screen_ns * 1e-6;
+    }
+    s->iterations = c.iter;
+    s->ls_trials = c.ls_trials;
+    s->nnz = h->nnz;
+    s->accepted_halvings = c.ls_accept;
+    s->f = c.f_cur;
+    s->F = c.f_cur + c.pen_cur;
+    s->rel_change = c.rel;
+    s->candidates = c.em_count;
+    s->grad_pass_launches = c.iter_attempts;
+    s->kernel_launches = c.iter_attempts * loop_launches(h) + 2 * c.ls_windows;
+    s->ms_gram = h->ms_gram;
+    s->capacity_regrows = h->regrows - regrows0;
+    s->status = status;
+    return status;
+}
+
 template <typename T>
 int run_iterations(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* st) {
     hpc_stats local{};
     hpc_stats* s = st ? st : &local;
     std::memset(s, 0, sizeof *s);
+    if (h->opt.device_loop) return run_device_loop<T>(h, k, use_stop, s);
     const int64_t regrows0 = h->regrows;
-    // reset the accumulators of the control block
-    h->h_ctrl->iter = 0;
-    h->h_ctrl->ls_trials = 0;
-    CUDA_TRY(cudaMemcpyAsync(&h->d_ctrl->iter, &h->h_ctrl->iter, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(&h->d_ctrl->ls_trials, &h->h_ctrl->ls_trials, sizeof(long long),
-                             cudaMemcpyHostToDevice, h->stream));
+    STATUS_TRY(load_ctrl(h, k, use_stop));
     if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
     int status = use_stop ? HPC_NOT_CONVERGED : HPC_OK;
     for (int64_t it = 0; it < k; ++it) {
@@ -454,11 +683,13 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
 void destroy(hpc_ctx* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    destroy_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     free_candidates(h);
     void* ptrs[] = {h->S, h->rp[0], h->rp[1], h->ci[0], h->ci[1], h->cv[0], h->cv[1], h->bk_cnt, h->bk_off,
                     h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
-                    h->yp[0], h->yp[1], h->pairs};
+                    h->yp[0], h->yp[1], h->pairs, h->bk_uoff};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -486,6 +717,7 @@ void hpc_default_options(hpc_options* opt) {
     opt->max_capacity = 0;
     opt->x_on_host = 0;
     opt->timing = 1;
+    opt->device_loop = 1;
 }
 
 const char* hpc_status_string(int s) {
@@ -597,6 +829,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     CK(cudaMalloc(&h->bk_off, (p + 1) * sizeof(int)));
     CK(cudaMalloc(&h->bk_cur, p * sizeof(int)));
     CK(cudaMalloc(&h->bk_len, p * sizeof(int)));
+    CK(cudaMalloc(&h->bk_uoff, (p + 1) * sizeof(long long)));
     CK(cudaMalloc(&h->cnt2, p * sizeof(int)));
     h->nblk = (int)std::min<int64_t>((p + 7) / 8, 152 * 16);
     CK(cudaMalloc(&h->part_obj, (size_t)h->nblk * 4 * sizeof(double)));
@@ -765,6 +998,45 @@ int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda
     }
     if (row_ptr) *cap_inout = used;
     return status;
+}
+
+int hpc_solve_batch(hpc_handle* handles, int count, int threads, hpc_stats* stats) {
+    if (count < 0 || (count > 0 && !handles)) return HPC_ERR_ARG;
+    for (int t = 0; t < count; ++t)
+        if (!handles[t] || !handles[t]->loaded) return HPC_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HPC_ERR_CUDA;
+    std::vector<int> status(count, HPC_OK);
+    std::vector<hpc_stats> st(count);
+    // handles that share a stream go to the same worker, in index order
+    std::vector<std::vector<int>> groups;
+    {
+        std::vector<cudaStream_t> keys;
+        for (int t = 0; t < count; ++t) {
+            size_t g = 0;
+            while (g < keys.size() && keys[g] != handles[t]->stream) ++g;
+            if (g == keys.size()) { keys.push_back(handles[t]->stream); groups.emplace_back(); }
+            groups[g].push_back(t);
+        }
+    }
+    const int nw = threads > 0 ? std::min<int>(threads, (int)groups.size()) : (int)groups.size();
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (int g = next.fetch_add(1); g < (int)groups.size(); g = next.fetch_add(1))
+            for (int t : groups[g]) status[t] = hpc_solve(handles[t], &st[t]);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    int ret = HPC_OK;
+    for (int t = 0; t < count; ++t) {
+        if (stats) stats[t] = st[t];
+        if (status[t] < 0 && ret >= 0) ret = status[t];
+        else if (status[t] == HPC_NOT_CONVERGED && ret == HPC_OK) ret = HPC_NOT_CONVERGED;
+    }
+    return ret;
 }
 
 int hpc_set_lambda(hpc_handle h, double lambda1, double lambda2) {

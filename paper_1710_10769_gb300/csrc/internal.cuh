@@ -32,7 +32,16 @@ struct Ctrl {
     double rel;          // sqrt(delta2 / norm2_cur)
     long long ls_trials; // accumulated trials (the paper's t)
     int n_offrows;       // rows of the iterate with off-diagonal entries (screening pass)
-    int pad_;
+    int n_mirror;        // partner entries whose W_ij the gather fill computes
+    double lam1, lam2;   // regularisation of the current solve (read by the kernels)
+    long long ls_windows;     // line-search launches (window evaluations) since the last reset
+    long long iter_attempts;  // outer iterations started since the last reset
+    long long screen_ns;      // device time of the screening passes (device-loop timing)
+    long long t_stamp;        // last timestamp of k_stamp
+    int nnz_cur;         // entries of the current iterate (device loop)
+    int iter_limit;      // the device loop stops after this many accepted iterations
+    int use_stop;        // the device loop stops at the stopping rule
+    int pad2_;
 };
 
 enum : int {
@@ -75,6 +84,8 @@ struct Buckets {
     int* col_a; T* w_a; T* om_a; unsigned char* fl_a;    // scattered
     int* col_b; T* w_b; T* om_b; unsigned char* fl_b;    // sorted, de-duplicated
     T* g;         // G_ij of the sorted entries
+    long long* uoff;  // p+1: prefix of line-search work units per row (pairs of 32-entry chunks)
+    int2* mir;    // cap: (position, row) of every kept partner entry
     int cap;
 };
 
@@ -109,10 +120,19 @@ struct IterBufs {
     int64_t n;
 };
 
-template <typename T> void launch_iter_begin(const IterBufs<T>& b, cudaStream_t s);
+// Device-side loop control (CUDA graph conditional nodes); use = 0 outside a graph.
+struct LoopCond {
+    int use = 0;
+    cudaGraphConditionalHandle ls = 0;    // line-search window loop
+    cudaGraphConditionalHandle iter = 0;  // outer iteration loop
+};
+
+template <typename T> void launch_iter_begin(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s);
+template <typename T> void launch_commit(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s);
+void launch_stamp(Ctrl* ctrl, int end, cudaStream_t s);
 template <typename T> void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s);
 template <typename T> void launch_candidates(const IterBufs<T>& b, cudaStream_t s);
-template <typename T> void launch_ls_window(const IterBufs<T>& b, int h_base, bool first, cudaStream_t s);
+template <typename T> void launch_ls_window(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s);
 template <typename T> void launch_accept(const IterBufs<T>& b, cudaStream_t s);
 template <typename T> void launch_set_identity(Csr<T> c, int p, cudaStream_t s);
 template <typename T> void launch_csr_export(const int* rp, const int* ci, const T* cv, int p, int nnz,
@@ -128,7 +148,7 @@ constexpr int kLaunchesLsWindow = 2;
 constexpr int kLaunchesAccept = 4;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
-void launch_ls_window_obs(const IterBufs<float>& b, int h_base, bool first, cudaStream_t s);
+void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s);
 
 // ---------------------------------------------------------------- Obs variant (obs_tc.cu)
 size_t obs_panel_bytes(int precision, int64_t n, int64_t p);
@@ -140,7 +160,7 @@ void launch_obs_split(int precision, const float* in, int64_t rows, int64_t cols
 bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void* x_hi, const void* x_lo, int64_t n,
                    int64_t p, CUtensorMap* maps);
 cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
-                             int p, const int* rp, const int* ci, const float* cv, float lam1, Emit<float> em,
+                             int p, const int* rp, const int* ci, const float* cv, Emit<float> em,
                              Ctrl* ctrl, cudaStream_t s);
 int obs_take_error();
 
@@ -181,6 +201,11 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();
+
+// Raise a kernel's dynamic shared-memory limit once per device (the attribute call
+// is a host round trip that must stay out of the iteration loop).
+cudaError_t set_smem_once(const void* func, int bytes, int slot);
+enum : int { kSmemSlotScreenF = 0, kSmemSlotScreenD = 1, kSmemSlotObsBf16x3 = 2, kSmemSlotObsTf32 = 3, kSmemSlots = 4 };
 
 // Set the text returned by hpc_last_error() for this thread (api.cu).
 void set_last_error(const char* msg);

@@ -131,7 +131,7 @@ __device__ __forceinline__ T prox_entry(T om, T g, T tau, T tl1, bool diag) {
 
 // ------------------------------------------------------------------ 0. reset
 template <typename T>
-__global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
+__global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl, int use_cond, cudaGraphConditionalHandle ls_cond) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     for (int i = tid; i < p; i += gridDim.x * blockDim.x) {
         bk.cnt[i] = 0;
@@ -140,6 +140,7 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
     if (tid == 0) {
         ctrl->em_count = 0;
         ctrl->n_offrows = 0;
+        ctrl->n_mirror = 0;
         ctrl->bucket_total = 0;
         ctrl->flags = 0;
         ctrl->ls_accept = -1;
@@ -148,6 +149,40 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
         ctrl->converged = 0;
         ctrl->tau = 0.0;
         ctrl->delta2 = 0.0;
+        ctrl->iter_attempts += 1;
+        // device loop: the line-search loop of this iteration runs at least once
+        if (use_cond) cudaGraphSetConditional(ls_cond, 1u);
+    }
+}
+
+// Device-loop timing: globaltimer stamps around the screening pass.
+__global__ void k_stamp(Ctrl* ctrl, int end) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (end) ctrl->screen_ns += (long long)t - ctrl->t_stamp;
+    else ctrl->t_stamp = (long long)t;
+}
+
+// Device loop: copy the accepted iterate into the buffers the next iteration's
+// kernels read, and decide whether the loop goes on (an accepted step, below the
+// iteration limit, stopping rule not met or not in use, no flag raised).
+template <typename T>
+__global__ void k_csr_commit(Csr<T> nx, Csr<T> cu, int p, Ctrl* ctrl, int use_cond, cudaGraphConditionalHandle cond) {
+    const bool ok = ctrl->flags == 0 && ctrl->ls_accept >= 0;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nt = gridDim.x * blockDim.x;
+    if (ok) {
+        const int nnz = nx.rp[p];
+        for (int i = tid; i <= p; i += nt) cu.rp[i] = nx.rp[i];
+        for (int q = tid; q < nnz; q += nt) {
+            cu.ci[q] = nx.ci[q];
+            cu.cv[q] = nx.cv[q];
+        }
+    }
+    if (tid == 0) {
+        if (ok) ctrl->nnz_cur = nx.rp[p];
+        const bool more = ok && ctrl->iter < ctrl->iter_limit && !(ctrl->use_stop && ctrl->converged);
+        if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
     }
 }
 
@@ -163,9 +198,9 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl) {
 // (32 KB, BJ = 32*V) with TMA into a kScreenStages-deep mbarrier ring, and eight
 // consumer warps, each screening eight rows of every tile (lane l holds columns
 // l*V .. l*V+V-1, one 16-byte shared-memory read per row).  This kernel takes the
-// pure-diagonal rows, which need no other row of S: CTA c owns row chunks c,
-// c+G, c+2G, ... and walks each chunk's column blocks in order, so DRAM sees long
-// runs of each row.  Rows with off-diagonal entries are screened by
+// pure-diagonal rows, which need no other row of S: CTA c owns a contiguous
+// share of the (row chunk, column block) items in chunk-major order (equal shares
+// for every SM, whatever p), so DRAM sees long runs of each row.  Rows with off-diagonal entries are screened by
 // k_grad_screen_rows.  Row set-up (CSR bounds, diagonal position and value, the
 // pure-diagonal flag) comes from k_row_info, cached in shared memory.
 constexpr int kScreenTileRows = 64;
@@ -269,7 +304,7 @@ template <typename T>
 __global__ void __launch_bounds__(kScreenThreads, 1)
 k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S, int64_t ld, int p,
               const int4* __restrict__ rinfo, const T* __restrict__ rdv, const int* __restrict__ ci,
-              const T* __restrict__ cv, T lam1, Emit<T> em, Ctrl* __restrict__ ctrl) {
+              const T* __restrict__ cv, Emit<T> em, Ctrl* __restrict__ ctrl) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
     constexpr int BJ = Sc::BJ;
@@ -285,12 +320,17 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kScreenStages);
 
     if (2 * ctrl->n_offrows > p) return;      // dense rows: k_grad_screen_rows covers every row
+    const T lam1 = (T)ctrl->lam1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x;
     const int nchunks = (p + R - 1) / R;
-    const int mine = blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / G + 1 : 0;   // <= kScreenMaxChunks
     const int nblocks = (p + BJ - 1) / BJ;
-    const int items = mine * nblocks;
+    // this CTA's contiguous share of the (chunk, column block) items, chunk-major
+    const long long total = (long long)nchunks * nblocks;
+    const long long lo = total * blockIdx.x / G, hi = total * (blockIdx.x + 1) / G;
+    const int items = (int)(hi - lo);
+    const int c_first = (int)(lo / nblocks);
+    const int mine = items > 0 ? (int)((hi - 1) / nblocks) - c_first + 1 : 0;   // <= kScreenMaxChunks
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < kScreenStages; ++st) {
@@ -302,7 +342,7 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
     }
     // cache the row set-up of this CTA's chunks
     for (int t = threadIdx.x; t < mine * R; t += blockDim.x) {
-        const int i = (blockIdx.x + (t / R) * G) * R + (t % R);
+        const int i = (c_first + t / R) * R + (t % R);
         s_info[t] = i < p ? rinfo[i] : make_int4(0, 0, -1, 0);
         s_dv[t] = i < p ? rdv[i] : T(0);
     }
@@ -316,8 +356,8 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
                 const int st = t % kScreenStages;
                 const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
                 if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort_flag, kScreenWaitLimit)) break;
-                const int m = t / nblocks, jb = t % nblocks;
-                const int chunk = blockIdx.x + m * G;
+                const long long g = lo + t;
+                const int chunk = (int)(g / nblocks), jb = (int)(g % nblocks);
                 ptx::mbar_expect_tx(&full[st], kTileBytes);
                 ptx::tma_load_2d(reinterpret_cast<uint8_t*>(tiles) + st * kTileBytes, &smap, &full[st], jb * BJ,
                                  chunk * R);
@@ -329,8 +369,9 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
             const int st = t % kScreenStages;
             const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
             if (!ptx::mbar_wait_bounded(&full[st], ph, abort_flag, kScreenWaitLimit)) break;
-            const int m = t / nblocks, jb = t % nblocks;
-            const int chunk = blockIdx.x + m * G;
+            const long long g = lo + t;
+            const int chunk = (int)(g / nblocks), jb = (int)(g % nblocks);
+            const int m = chunk - c_first;
             const int j0 = jb * BJ;
             const T* tile = tiles + (size_t)st * R * BJ;
             // eight rows at once: independent shared-memory reads, the diagonal-term
@@ -391,23 +432,34 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
 
 // Rows with off-diagonal entries (or, when they are the majority, every row):
 // persistent warps over items (column block, group of 8 listed rows), column
-// block outermost so that in-flight warps share S[:, J] in L2.  A warp issues the
-// eight diagonal-term loads of its rows first, then per row gathers the
-// off-diagonal terms four at a time, in the canonical order, and screens.
+// block outermost so that in-flight warps share S[:, J] in L2.  The terms of the
+// item's rows -- per row the diagonal term w_ii S[i, J] (0 if absent) followed by
+// the off-diagonal terms w_ik S[k, J] in CSR order -- form one stream whose
+// (k, w_ik) the lanes fetch 32 at a time; the S-row segments are then loaded
+// kTermBatch at a time across row boundaries, so every batch keeps that many
+// loads in flight whatever the row lengths, and each row still accumulates in
+// the canonical order.
 constexpr int kRowsPerItem = 8;
+constexpr int kTermBatch = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __restrict__ rinfo,
                    const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
-                   const T* __restrict__ cv, T lam1, Emit<T> em, Ctrl* __restrict__ ctrl) {
+                   const T* __restrict__ cv, Emit<T> em, Ctrl* __restrict__ ctrl) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
     constexpr int BJ = Sc::BJ;
-    const int lane = threadIdx.x & 31;
+    constexpr int R = kRowsPerItem;
+    __shared__ int s_row[kWarps][R], s_rb[kWarps][R], s_re[kWarps][R], s_pd[kWarps][R], s_start[kWarps][R];
+    __shared__ T s_dv[kWarps][R];
+    __shared__ T s_acc[kWarps][R][V][32];
+    __shared__ int s_sup[kWarps][R];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T lam1 = (T)ctrl->lam1;
     const bool all_rows = 2 * ctrl->n_offrows > p;
     const int nrows = all_rows ? p : ctrl->n_offrows;
-    const int ngroups = (nrows + kRowsPerItem - 1) / kRowsPerItem;
+    const int ngroups = (nrows + R - 1) / R;
     const int nblocks = (p + BJ - 1) / BJ;
     const long long items = (long long)ngroups * nblocks;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -415,53 +467,106 @@ k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __res
     for (long long it = gw; it < items; it += nw) {
         const int jb = (int)(it / ngroups), grp = (int)(it % ngroups);
         const int j0 = jb * BJ;
-        const int nr = min(kRowsPerItem, nrows - grp * kRowsPerItem);
-        int my_row = -1;
-        if (lane < nr) my_row = all_rows ? grp * kRowsPerItem + lane : offlist[grp * kRowsPerItem + lane];
-        T sd[kRowsPerItem][V];
-#pragma unroll
-        for (int r = 0; r < kRowsPerItem; ++r) {
-            const int i = __shfl_sync(kFull, my_row, r);
-            if (r < nr) vload(sd[r], S + (int64_t)i * ld + j0 + lane * V);
+        const int nr = min(R, nrows - grp * R);
+        // lanes < nr: the row's set-up and the length of its term stream
+        int slen = 0;
+        __syncwarp();
+        if (lane < nr) {
+            const int row = all_rows ? grp * R + lane : offlist[grp * R + lane];
+            const int4 inf = rinfo[row];
+            s_row[warp][lane] = row;
+            s_rb[warp][lane] = inf.x;
+            s_re[warp][lane] = inf.y;
+            s_pd[warp][lane] = inf.z;
+            s_dv[warp][lane] = rdv[row];
+            slen = 1 + (inf.y - inf.x) - (inf.z >= 0 ? 1 : 0);
         }
+        const int incl = warp_incl_scan(slen, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (lane < nr) s_start[warp][lane] = incl - slen;
+        __syncwarp();
+
+        int cur = -1;
+        T acc[V];
+        bool sup = false;
 #pragma unroll
-        for (int r = 0; r < kRowsPerItem; ++r) {
-            if (r >= nr) break;
-            const int i = __shfl_sync(kFull, my_row, r);
-            const int4 info = rinfo[i];
-            const T dv = rdv[i];
-            T acc[V];
+        for (int v = 0; v < V; ++v) acc[v] = T(0);
+        for (int w0 = 0; w0 < total; w0 += 32) {
+            // lane l fetches term w0 + l: its row slot, S row k and weight
+            const int x = w0 + lane;
+            int tk = 0, tr = -1;
+            T tw = T(0);
+            if (x < total) {
+                int r = 0;
+                for (int q = 1; q < nr; ++q)
+                    if (s_start[warp][q] <= x) r = q;
+                const int y = x - s_start[warp][r];
+                tr = r;
+                if (y == 0) {
+                    tk = s_row[warp][r];
+                    tw = s_dv[warp][r];
+                } else {
+                    int qq = s_rb[warp][r] + y - 1;
+                    if (s_pd[warp][r] >= 0 && qq >= s_pd[warp][r]) ++qq;
+                    tk = ci[qq];
+                    tw = cv[qq];
+                }
+            }
+            const int nt = min(32, total - w0);
+            for (int b0 = 0; b0 < nt; b0 += kTermBatch) {
+                T sv[kTermBatch][V];
+                int kk[kTermBatch], rr[kTermBatch];
+                T ww[kTermBatch];
 #pragma unroll
-            for (int v = 0; v < V; ++v) acc[v] = mulT(dv, sd[r][v]);
-            bool sup_here = (i >= j0 && i < j0 + BJ);
-            for (int q0 = info.x; q0 < info.y; q0 += 4) {
-                T s4[4][V];
-                T w4[4];
-                int k4[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int qq = q0 + u;
-                    k4[u] = -1;
-                    if (qq < info.y && qq != info.z) {
-                        k4[u] = ci[qq];
-                        w4[u] = cv[qq];
-                        vload(s4[u], S + (int64_t)k4[u] * ld + j0 + lane * V);
-                    }
+                for (int u = 0; u < kTermBatch; ++u) {
+                    const int t = b0 + u;
+                    kk[u] = __shfl_sync(kFull, tk, t & 31);
+                    ww[u] = __shfl_sync(kFull, tw, t & 31);
+                    rr[u] = __shfl_sync(kFull, tr, t & 31);
+                    if (t >= nt) rr[u] = -1;
+                    if (rr[u] >= 0) vload(sv[u], S + (int64_t)kk[u] * ld + j0 + lane * V);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (k4[u] >= 0) {
+                for (int u = 0; u < kTermBatch; ++u) {
+                    if (rr[u] < 0) break;
+                    const bool in_blk = kk[u] >= j0 && kk[u] < j0 + BJ;
+                    if (rr[u] != cur) {
+                        if (cur >= 0) {
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc[v] = fmaT(w4[u], s4[u][v], acc[v]);
-                        sup_here |= (k4[u] >= j0 && k4[u] < j0 + BJ);
+                            for (int v = 0; v < V; ++v) s_acc[warp][cur][v][lane] = acc[v];
+                            if (lane == 0) s_sup[warp][cur] = sup ? 1 : 0;
+                        }
+                        cur = rr[u];
+                        // a row's stream starts with its diagonal term
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = mulT(ww[u], sv[u][v]);
+                        sup = in_blk;
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fmaT(ww[u], sv[u][v], acc[v]);
+                        sup |= in_blk;
                     }
                 }
             }
+        }
+        if (cur >= 0) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) s_acc[warp][cur][v][lane] = acc[v];
+            if (lane == 0) s_sup[warp][cur] = sup ? 1 : 0;
+        }
+        __syncwarp();
+        // screen the item's rows
+        for (int r = 0; r < nr; ++r) {
+            T a[V];
             bool big = false;
 #pragma unroll
-            for (int v = 0; v < V; ++v) big |= !(fabs(acc[v]) <= lam1);
-            if (__any_sync(kFull, big) || sup_here) Sc::emit(i, acc[0], acc[V > 1 ? 1 : 0], acc[V > 2 ? 2 : 0], acc[V > 3 ? 3 : 0], info.x, info.y, j0, p,
-                         ci, cv, lam1, em, ctrl, lane);
+            for (int v = 0; v < V; ++v) {
+                a[v] = s_acc[warp][r][v][lane];
+                big |= !(fabs(a[v]) <= lam1);
+            }
+            if (__any_sync(kFull, big) || s_sup[warp][r])
+                Sc::emit(s_row[warp][r], a[0], a[V > 1 ? 1 : 0], a[V > 2 ? 2 : 0], a[V > 3 ? 3 : 0], s_rb[warp][r],
+                         s_re[warp][r], j0, p, ci, cv, lam1, em, ctrl, lane);
         }
     }
 }
@@ -483,49 +588,82 @@ __global__ void k_bucket_count(Emit<T> em, Buckets<T> bk, Ctrl* ctrl) {
     }
 }
 
+// Line-search work units of a row with c candidate entries before de-dup: the
+// pairs (a <= b) of its 32-entry chunks.
+__device__ __forceinline__ long long ls_units(int c) {
+    const long long t = (c + 31) >> 5;
+    return t * (t + 1) / 2;
+}
+
+__device__ __forceinline__ long long warp_incl_scan64(long long x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
 // Single-block exclusive scan of n ints (chunks of 4096), out[n] = total.
-// If total > cap, sets flag.
+// If total > cap, sets flag.  With uoff, also the exclusive 64-bit scan of
+// ls_units(in[i]) (uoff[n] = total units).
 __global__ void __launch_bounds__(1024)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
-       int* total_dst) {
+       int* total_dst, long long* __restrict__ uoff) {
     __shared__ int wsum[32];
+    __shared__ long long usum[32];
     __shared__ int carry;
+    __shared__ long long ucarry;
     if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) {
-        if (threadIdx.x == 0) out[n] = 0;
+        if (threadIdx.x == 0) {
+            out[n] = 0;
+            if (uoff) uoff[n] = 0;
+        }
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
+    if (threadIdx.x == 0) { carry = 0; ucarry = 0; }
     __syncthreads();
     for (int base = 0; base < n; base += 4096) {
         const int idx = base + threadIdx.x * 4;
         int v[4];
+        long long uv[4];
         int s = 0;
+        long long us = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             v[q] = (idx + q < n) ? in[idx + q] : 0;
+            uv[q] = (uoff && idx + q < n) ? ls_units(v[q]) : 0;
             s += v[q];
+            us += uv[q];
         }
         const int x = warp_incl_scan(s, lane);
-        if (lane == 31) wsum[warp] = x;
+        const long long ux = uoff ? warp_incl_scan64(us, lane) : 0;
+        if (lane == 31) { wsum[warp] = x; usum[warp] = ux; }
         __syncthreads();
         if (warp == 0) {
-            const int y = warp_incl_scan(wsum[lane], lane);
-            wsum[lane] = y;
+            wsum[lane] = warp_incl_scan(wsum[lane], lane);
+            if (uoff) usum[lane] = warp_incl_scan64(usum[lane], lane);
         }
         __syncthreads();
         int run = x - s + (warp ? wsum[warp - 1] : 0) + carry;
+        long long urun = ux - us + (warp ? usum[warp - 1] : 0) + ucarry;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            if (idx + q < n) out[idx + q] = run;
+            if (idx + q < n) {
+                out[idx + q] = run;
+                if (uoff) uoff[idx + q] = urun;
+            }
             run += v[q];
+            urun += uv[q];
         }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = run;
+        if (threadIdx.x == 1023) { carry = run; ucarry = urun; }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         out[n] = carry;
+        if (uoff) uoff[n] = ucarry;
         if (total_dst) *total_dst = carry;
         if (carry > cap) atomicOr(&ctrl->flags, flag);
     }
@@ -554,139 +692,222 @@ __global__ void k_bucket_scatter(Emit<T> em, Buckets<T> bk, const Ctrl* ctrl) {
     }
 }
 
-// Warp per row: rank sort by (column, own-before-partner) into the b arrays, then
-// drop partner requests whose own entry exists.  Rows are short (the support plus
-// a few screened entries), so an O(c^2) rank sort is cheap and deterministic.
+// Sort key of a scattered entry: column, own entry before the partner request.
+template <typename T>
+__device__ __forceinline__ unsigned sort_key(const Buckets<T>& bk, int pos) {
+    return (unsigned)bk.col_a[pos] * 2u + ((bk.fl_a[pos] & kEntMirror) ? 1u : 0u);
+}
+
+// Append the kept partner entries of this warp (flag `mir`, final position pos in
+// row i) to the fill list.
+template <typename T>
+__device__ __forceinline__ void push_mirrors(const Buckets<T>& bk, Ctrl* ctrl, bool mir, int pos, int i, int lane) {
+    const unsigned mb = __ballot_sync(kFull, mir);
+    if (!mb) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&ctrl->n_mirror, __popc(mb));
+    base = __shfl_sync(kFull, base, 0);
+    if (mir) bk.mir[base + __popc(mb & ((1u << lane) - 1u))] = make_int2(pos, i);
+}
+
+// Rows longer than one warp are sorted by a whole block in shared memory (bitonic
+// on 64-bit (key, index) words) up to this many entries; beyond it, by ranks.
+constexpr int kSortSmem = 4096;
+constexpr int kSortShort = 32;
+
+// Sort by (column, own-before-partner) into the b arrays, then drop partner
+// requests whose own entry exists (the own entry sorts just before).  Rows of at
+// most 32 entries: one warp each, in registers.  Longer rows: one block each, so a
+// hub row with thousands of candidates does not serialise a warp.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_bucket_sort(Buckets<T> bk, int p, const Ctrl* ctrl) {
+k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
+    __shared__ unsigned long long s_key[kSortSmem];
+    __shared__ int s_long[kThreads];
+    __shared__ int s_cnt[kWarps];
+    __shared__ int s_nlong, s_out;
     if (ctrl->flags) return;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = gw; i < p; i += nw) {
         const int beg = bk.off[i];
         const int c = bk.cnt[i];
-        if (c <= 32) {
-            // whole row in registers: rank by shuffles (keys are distinct), drop a partner
-            // request whose predecessor in column order is the own entry of that column,
-            // and write the kept entries in order
-            const bool valid = lane < c;
-            int col = 0;
-            T w = T(0), om = T(0);
-            unsigned char fl = 0;
-            if (valid) {
-                col = bk.col_a[beg + lane];
-                w = bk.w_a[beg + lane];
-                om = bk.om_a[beg + lane];
-                fl = bk.fl_a[beg + lane];
-            }
-            const int key = valid ? col * 2 + ((fl & kEntMirror) ? 1 : 0) : 0x7fffffff;
-            int rank = 0;
-            for (int t = 0; t < 32; ++t) rank += (__shfl_sync(kFull, key, t) < key) ? 1 : 0;
-            int pred_col = -1;
-            for (int t = 0; t < 32; ++t) {
-                const int rt = __shfl_sync(kFull, rank, t);
-                const int ct = __shfl_sync(kFull, col, t);
-                if (t < c && rt == rank - 1) pred_col = ct;
-            }
-            const bool keep = valid && !((fl & kEntMirror) && rank > 0 && pred_col == col);
-            const unsigned kb = __ballot_sync(kFull, keep);
-            int pos = 0;
-            for (int t = 0; t < 32; ++t) {
-                const int rt = __shfl_sync(kFull, rank, t);
-                pos += (((kb >> t) & 1u) && rt < rank) ? 1 : 0;
-            }
-            if (keep) {
-                bk.col_b[beg + pos] = col;
-                bk.w_b[beg + pos] = w;
-                bk.om_b[beg + pos] = om;
-                bk.fl_b[beg + pos] = fl;
-            }
-            if (lane == 0) bk.len[i] = __popc(kb);
-            continue;
+        if (c > kSortShort) continue;
+        // whole row in registers: rank by shuffles (keys are distinct), drop a partner
+        // request whose predecessor in column order is the own entry of that column,
+        // and write the kept entries in order
+        const bool valid = lane < c;
+        int col = 0;
+        T w = T(0), om = T(0);
+        unsigned char fl = 0;
+        if (valid) {
+            col = bk.col_a[beg + lane];
+            w = bk.w_a[beg + lane];
+            om = bk.om_a[beg + lane];
+            fl = bk.fl_a[beg + lane];
         }
-        for (int e = lane; e < c; e += 32) {
-            const int ke = bk.col_a[beg + e] * 2 + ((bk.fl_a[beg + e] & kEntMirror) ? 1 : 0);
-            int rank = 0;
-            for (int f = 0; f < c; ++f) {
-                const int kf = bk.col_a[beg + f] * 2 + ((bk.fl_a[beg + f] & kEntMirror) ? 1 : 0);
-                rank += (kf < ke) ? 1 : 0;
-            }
-            bk.col_b[beg + rank] = bk.col_a[beg + e];
-            bk.w_b[beg + rank] = bk.w_a[beg + e];
-            bk.om_b[beg + rank] = bk.om_a[beg + e];
-            bk.fl_b[beg + rank] = bk.fl_a[beg + e];
+        const int key = valid ? col * 2 + ((fl & kEntMirror) ? 1 : 0) : 0x7fffffff;
+        int rank = 0;
+        for (int t = 0; t < 32; ++t) rank += (__shfl_sync(kFull, key, t) < key) ? 1 : 0;
+        int pred_col = -1;
+        for (int t = 0; t < 32; ++t) {
+            const int rt = __shfl_sync(kFull, rank, t);
+            const int ct = __shfl_sync(kFull, col, t);
+            if (t < c && rt == rank - 1) pred_col = ct;
         }
-        __syncwarp();
-        int out = 0;
-        for (int base = 0; base < c; base += 32) {
-            const int e = base + lane;
-            int col = 0;
-            T w = T(0), om = T(0);
-            unsigned char fl = 0;
-            bool keep = false;
-            if (e < c) {
-                col = bk.col_b[beg + e];
-                w = bk.w_b[beg + e];
-                om = bk.om_b[beg + e];
-                fl = bk.fl_b[beg + e];
-                keep = !((fl & kEntMirror) && e > 0 && bk.col_b[beg + e - 1] == col);
-            }
-            const unsigned bal = __ballot_sync(kFull, keep);
-            __syncwarp();
-            if (keep) {
-                const int q = out + __popc(bal & ((1u << lane) - 1u));
-                bk.col_b[beg + q] = col;
-                bk.w_b[beg + q] = w;
-                bk.om_b[beg + q] = om;
-                bk.fl_b[beg + q] = fl;
-            }
-            out += __popc(bal);
-            __syncwarp();
+        const bool keep = valid && !((fl & kEntMirror) && rank > 0 && pred_col == col);
+        const unsigned kb = __ballot_sync(kFull, keep);
+        int pos = 0;
+        for (int t = 0; t < 32; ++t) {
+            const int rt = __shfl_sync(kFull, rank, t);
+            pos += (((kb >> t) & 1u) && rt < rank) ? 1 : 0;
         }
-        if (lane == 0) bk.len[i] = out;
+        if (keep) {
+            bk.col_b[beg + pos] = col;
+            bk.w_b[beg + pos] = w;
+            bk.om_b[beg + pos] = om;
+            bk.fl_b[beg + pos] = fl;
+        }
+        push_mirrors(bk, ctrl, keep && (fl & kEntMirror), beg + pos, i, lane);
+        if (lane == 0) bk.len[i] = __popc(kb);
+    }
+
+    // long rows: row i belongs to block i mod gridDim.x
+    for (int base = blockIdx.x; base < p; base += gridDim.x * kThreads) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_nlong = 0;
+        __syncthreads();
+        const int i0 = base + threadIdx.x * gridDim.x;
+        if (i0 < p && bk.cnt[i0] > kSortShort) s_long[atomicAdd(&s_nlong, 1)] = i0;
+        __syncthreads();
+        const int nlong = s_nlong;
+        for (int r = 0; r < nlong; ++r) {
+            const int i = s_long[r];
+            const int beg = bk.off[i];
+            const int c = bk.cnt[i];
+            if (c <= kSortSmem) {
+                int n2 = 1;
+                while (n2 < c) n2 <<= 1;
+                for (int e = threadIdx.x; e < n2; e += kThreads)
+                    s_key[e] = e < c ? ((unsigned long long)sort_key(bk, beg + e) << 32) | (unsigned)e : ~0ull;
+                __syncthreads();
+                for (int k = 2; k <= n2; k <<= 1) {
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        for (int t = threadIdx.x; t < n2; t += kThreads) {
+                            const int u = t ^ j;
+                            if (u > t) {
+                                const unsigned long long x = s_key[t], y = s_key[u];
+                                if ((x > y) == ((t & k) == 0)) { s_key[t] = y; s_key[u] = x; }
+                            }
+                        }
+                        __syncthreads();
+                    }
+                }
+                for (int q = threadIdx.x; q < c; q += kThreads) {
+                    const int e = beg + (int)(s_key[q] & 0xffffffffu);
+                    bk.col_b[beg + q] = bk.col_a[e];
+                    bk.w_b[beg + q] = bk.w_a[e];
+                    bk.om_b[beg + q] = bk.om_a[e];
+                    bk.fl_b[beg + q] = bk.fl_a[e];
+                }
+            } else {
+                // rank of each entry against all keys of the row, streamed in tiles
+                unsigned* s_k32 = reinterpret_cast<unsigned*>(s_key);
+                constexpr int kTile = 2 * kSortSmem;
+                for (int e0 = 0; e0 < c; e0 += kThreads) {
+                    const int e = e0 + threadIdx.x;
+                    const unsigned ke = e < c ? sort_key(bk, beg + e) : 0xffffffffu;
+                    int rank = 0;
+                    for (int f0 = 0; f0 < c; f0 += kTile) {
+                        __syncthreads();
+                        for (int f = threadIdx.x; f < kTile; f += kThreads)
+                            s_k32[f] = f0 + f < c ? sort_key(bk, beg + f0 + f) : 0xffffffffu;
+                        __syncthreads();
+                        const int fn = min(kTile, c - f0);
+                        for (int f = 0; f < fn; ++f) rank += (s_k32[f] < ke) ? 1 : 0;
+                    }
+                    if (e < c) {
+                        bk.col_b[beg + rank] = bk.col_a[beg + e];
+                        bk.w_b[beg + rank] = bk.w_a[beg + e];
+                        bk.om_b[beg + rank] = bk.om_a[beg + e];
+                        bk.fl_b[beg + rank] = bk.fl_a[beg + e];
+                    }
+                }
+            }
+            __syncthreads();
+            // de-dup in place, chunk by chunk (a chunk only writes at or before the
+            // positions it read, and the predecessor it compares with keeps its value)
+            if (threadIdx.x == 0) s_out = 0;
+            for (int c0 = 0; c0 < c; c0 += kThreads) {
+                const int e = c0 + threadIdx.x;
+                int col = 0;
+                T w = T(0), om = T(0);
+                unsigned char fl = 0;
+                bool keep = false;
+                if (e < c) {
+                    col = bk.col_b[beg + e];
+                    w = bk.w_b[beg + e];
+                    om = bk.om_b[beg + e];
+                    fl = bk.fl_b[beg + e];
+                    keep = !((fl & kEntMirror) && e > 0 && bk.col_b[beg + e - 1] == col);
+                }
+                const unsigned bal = __ballot_sync(kFull, keep);
+                if (lane == 0) s_cnt[warp] = __popc(bal);
+                __syncthreads();
+                int before = s_out;
+                for (int w2 = 0; w2 < warp; ++w2) before += s_cnt[w2];
+                int total = 0;
+                for (int w2 = 0; w2 < kWarps; ++w2) total += s_cnt[w2];
+                const int q = before + __popc(bal & ((1u << lane) - 1u));
+                if (keep) {
+                    bk.col_b[beg + q] = col;
+                    bk.w_b[beg + q] = w;
+                    bk.om_b[beg + q] = om;
+                    bk.fl_b[beg + q] = fl;
+                }
+                push_mirrors(bk, ctrl, keep && (fl & kEntMirror), beg + q, i, lane);
+                __syncthreads();
+                if (threadIdx.x == 0) s_out += total;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) bk.len[i] = s_out;
+        }
     }
 }
 
-// W_ij for partner entries, by gathers in the CSR order of row i (bitwise equal to
-// the value the screening pass computes for that entry).
+// W_ij for partner entries, one thread per entry of the fill list, by gathers in
+// the CSR order of row i: diagonal term first, then the off-diagonals ascending
+// (bitwise equal to the value the screening pass computes for that entry).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_fill_w(const T* __restrict__ S, int64_t ld, int p, Csr<T> om, Buckets<T> bk, const Ctrl* ctrl) {
+k_fill_w(const T* __restrict__ S, int64_t ld, Csr<T> om, const int4* __restrict__ rinfo, const T* __restrict__ rdv,
+         Buckets<T> bk, const Ctrl* ctrl) {
     if (ctrl->flags) return;
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = gw; i < p; i += nw) {
-        const int beg = bk.off[i], L = bk.len[i];
-        const int rb = om.rp[i], re = om.rp[i + 1];
-        for (int e = lane; e < L; e += 32) {
-            if (!(bk.fl_b[beg + e] & kEntMirror)) continue;
-            const int j = bk.col_b[beg + e];
-            // canonical order of the screening pass: diagonal term, then off-diagonals
-            int pd = -1;
-            T dv = T(0);
-            for (int q = rb; q < re; ++q)
-                if (om.ci[q] == i) { pd = q; dv = om.cv[q]; break; }
-            T acc = mulT(dv, S[(int64_t)i * ld + j]);
-            for (int q = rb; q < re; ++q)
-                if (q != pd) acc = fmaT(om.cv[q], S[(int64_t)om.ci[q] * ld + j], acc);
-            bk.w_b[beg + e] = acc;
-        }
+    const int nm = ctrl->n_mirror;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nm; k += gridDim.x * blockDim.x) {
+        const int2 m = bk.mir[k];
+        const int i = m.y;
+        const int j = bk.col_b[m.x];
+        const int4 ri = rinfo[i];
+        T acc = mulT(rdv[i], S[(int64_t)i * ld + j]);
+        for (int q = ri.x; q < ri.y; ++q)
+            if (q != ri.z) acc = fmaT(om.cv[q], S[(int64_t)om.ci[q] * ld + j], acc);
+        bk.w_b[m.x] = acc;
     }
 }
 
 // G on the candidates (Alg. 2 steps 5-6) and the objective partials of Omega^k.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gradient(int p, Buckets<T> bk, T lam1, T lam2, double* part_obj, Ctrl* ctrl) {
+k_gradient(int p, Buckets<T> bk, double* part_obj, Ctrl* ctrl) {
     using A = typename AccOf<T>::type;
     __shared__ double red[kWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool skip = ctrl->flags != 0;
+    const T lam1 = (T)ctrl->lam1, lam2 = (T)ctrl->lam2;
     A s_ow{}, s_o2{}, s_log{}, s_abs{};
     int bad = 0;
     for (int i = skip ? p : gw; i < p; i += nw) {
@@ -737,24 +958,45 @@ k_gradient(int p, Buckets<T> bk, T lam1, T lam2, double* part_obj, Ctrl* ctrl) {
 
 // ------------------------------------------------------------------ 3. line search
 constexpr int kMaxWindow = 16;
-template <int M> __host__ __device__ constexpr int ls_chunk() { return M >= 16 ? 32 : 64; }
+
+// Row i of the unit-offset prefix containing unit u (uoff[i] <= u < uoff[i+1]): a
+// 32-way search by the whole warp (each step narrows the range 32-fold).
+__device__ __forceinline__ int find_unit_row(const long long* __restrict__ uoff, int p, long long u, int lane) {
+    int lo = 0, hi = p;
+    while (hi - lo > 1) {
+        const int span = hi - lo;
+        const int q = lo + (int)(((long long)span * (lane + 1)) >> 5);
+        const bool le = lane < 31 && uoff[q] <= u;
+        const unsigned bal = __ballot_sync(kFull, le);
+        const int c = __popc(bal);
+        const int nlo = c ? __shfl_sync(kFull, q, c - 1) : lo;
+        const int nhi = c < 31 ? __shfl_sync(kFull, q, c) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
 
 // Partials per block and per tau of the window:
 //   [0] sum_{e,f} D_e D_f S_{j_e j_f}   (= tr(D S D) restricted to row i, summed over rows)
 //   [1] ||D||_F^2                       [2] sum_i phi(D_ii / w_ii)     [3] #{w+_ii <= 0}
+// The quadratic form of row i is split into work units, the pairs (a <= b) of its
+// 32-entry chunks; every warp takes an equal contiguous range of the units of all
+// rows (prefix uoff), so rows with thousands of candidates spread over many warps.
 template <typename T, int M>
 __global__ void __launch_bounds__(kThreads)
-k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, double tau0, int h_base,
-          double* part_ls, const Ctrl* ctrl) {
+k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0, double* part_ls,
+          const Ctrl* ctrl) {
     using A = typename AccOf<T>::type;
-    constexpr int kChunk = ls_chunk<M>();
-    __shared__ int s_col[kWarps][kChunk];
-    __shared__ T s_del[kWarps][M][kChunk];
+    __shared__ int s_col[kWarps][32];
+    __shared__ T s_del[kWarps][M][32];
     __shared__ double red[kWarps][M][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const bool skip = (ctrl->flags != 0) || (ctrl->ls_accept >= 0);
+    const T lam1 = (T)ctrl->lam1;
+    const int h_base = ctrl->ls_base;
 
     T tau[M], tl1[M];
 #pragma unroll
@@ -767,36 +1009,51 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
 #pragma unroll
     for (int m = 0; m < M; ++m) nb[m] = 0;
 
-    for (int i = skip ? p : gw; i < p; i += nw) {
+    const long long U = skip ? 0 : bk.uoff[p];
+    long long u = U * gw / nw;
+    const long long u1 = U * (gw + 1) / nw;
+    int i = u < u1 ? find_unit_row(bk.uoff, p, u, lane) : 0;
+    while (u < u1) {
+        while (bk.uoff[i + 1] <= u) ++i;
+        const long long uend = min(bk.uoff[i + 1], u1);
+        const int tc = (bk.cnt[i] + 31) >> 5;
+        int k = (int)(u - bk.uoff[i]);
+        int a = 0;
+        while (k >= tc - a) { k -= tc - a; ++a; }
+        int cb = a + k;
         const int beg = bk.off[i], L = bk.len[i];
-        for (int eb = 0; eb < L; eb += 32) {
-            const int e = eb + lane;
-            T de[M];
-            int je = 0;
-            bool act_e = false;
-            if (e < L) {
-                je = bk.col_b[beg + e];
-                const T om = bk.om_b[beg + e], g = bk.g[beg + e];
-                const bool diag = (je == i);
+        for (; u < uend; ++u) {
+            const int eb = a * 32, fb = cb * 32;
+            const bool diag_unit = (a == cb);
+            if (fb < L) {
+                const int e = eb + lane;
+                T de[M];
+                int je = 0;
+                bool act_e = false;
+                if (e < L) {
+                    je = bk.col_b[beg + e];
+                    const T om = bk.om_b[beg + e], g = bk.g[beg + e];
+                    const bool diag = (je == i);
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const T np_ = prox_entry(om, g, tau[m], tl1[m], diag);
-                    de[m] = np_ - om;
-                    act_e |= (de[m] != T(0));
-                    acc_add(n2[m], mulT(de[m], de[m]));
-                    if (diag) {
-                        if (!(np_ > T(0))) nb[m] += 1;
-                        else acc_add(ph[m], phiT(de[m] / om));
+                    for (int m = 0; m < M; ++m) {
+                        const T np_ = prox_entry(om, g, tau[m], tl1[m], diag);
+                        de[m] = np_ - om;
+                        act_e |= (de[m] != T(0));
+                        if (diag_unit) {
+                            acc_add(n2[m], mulT(de[m], de[m]));
+                            if (diag) {
+                                if (!(np_ > T(0))) nb[m] += 1;
+                                else acc_add(ph[m], phiT(de[m] / om));
+                            }
+                        }
                     }
-                }
-            } else {
+                } else {
 #pragma unroll
-                for (int m = 0; m < M; ++m) de[m] = T(0);
-            }
-            for (int fb = eb; fb < L; fb += kChunk) {
+                    for (int m = 0; m < M; ++m) de[m] = T(0);
+                }
                 __syncwarp();
-                for (int t = lane; t < kChunk; t += 32) {
-                    const int f = fb + t;
+                {
+                    const int f = fb + lane;
                     int jf = -1;
                     if (f < L) {
                         jf = bk.col_b[beg + f];
@@ -805,12 +1062,15 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
 #pragma unroll
                         for (int m = 0; m < M; ++m) {
                             const T d = prox_entry(om, g, tau[m], tl1[m], jf == i) - om;
-                            s_del[warp][m][t] = d;
+                            s_del[warp][m][lane] = d;
                             act |= (d != T(0));
                         }
                         if (!act) jf = -1;
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < M; ++m) s_del[warp][m][lane] = T(0);
                     }
-                    s_col[warp][t] = jf;
+                    s_col[warp][lane] = jf;
                 }
                 __syncwarp();
                 if (act_e) {
@@ -818,13 +1078,12 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
 #pragma unroll
                     for (int m = 0; m < M; ++m) qf[m] = T(0);
                     const T* srow = S + (int64_t)je * ld;
-                    const int tmax = min(kChunk, L - fb);
-                    for (int t = 0; t < tmax; ++t) {
-                        const int f = fb + t;
+#pragma unroll 8
+                    for (int t = 0; t < 32; ++t) {
                         const int jf = s_col[warp][t];
-                        if (f < e || jf < 0) continue;
-                        const T sv = srow[jf];
-                        const T wgt = (f == e) ? T(1) : T(2);
+                        const bool use = jf >= 0 && (!diag_unit || t >= lane);
+                        const T sv = use ? srow[jf] : T(0);
+                        const T wgt = (diag_unit && t == lane) ? T(1) : T(2);
 #pragma unroll
                         for (int m = 0; m < M; ++m) qf[m] = fmaT(wgt * de[m] * s_del[warp][m][t], sv, qf[m]);
                     }
@@ -832,6 +1091,7 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
                     for (int m = 0; m < M; ++m) acc_add(q[m], qf[m]);
                 }
             }
+            if (++cb == tc) { ++a; cb = a; }
         }
     }
 #pragma unroll
@@ -859,13 +1119,15 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, T lam1, dou
 // consecutive samples of each 128-sample chunk of n.  [1]-[3] as in k_ls_eval.
 template <int M>
 __global__ void __launch_bounds__(kThreads)
-k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, float lam1, double tau0,
-              int h_base, double* part_ls, const Ctrl* ctrl) {
+k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, double tau0,
+              double* part_ls, const Ctrl* ctrl) {
     __shared__ double red[kWarps][M][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool skip = (ctrl->flags != 0) || (ctrl->ls_accept >= 0);
+    const float lam1 = (float)ctrl->lam1;
+    const int h_base = ctrl->ls_base;
     float tau[M], tl1[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
@@ -952,31 +1214,9 @@ k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Bucke
     }
 }
 
-// Reduce the partials in a fixed order (one warp per quantity, lanes over strided
-// blocks, then a butterfly) and take the decision of Alg. 1 step 9.
-__global__ void __launch_bounds__(1024)
-k_ls_decide(const double* __restrict__ part_ls, const double* __restrict__ part_obj, int nblk, int M,
-            int h_base, int max_halvings, double tau0, double lam1, double lam2, int first,
-            Ctrl* ctrl) {
-    __shared__ double sums[kMaxWindow * 4];
-    __shared__ double obj[4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (ctrl->flags != 0 || ctrl->ls_accept >= 0) return;
-    const int nq = M * 4 + (first ? 4 : 0);
-    for (int q = warp; q < nq; q += 32) {
-        double a = 0.0;
-        if (q < M * 4) {
-            for (int b = lane; b < nblk; b += 32) a += part_ls[(size_t)b * kMaxWindow * 4 + q];
-        } else {
-            for (int b = lane; b < nblk; b += 32) a += part_obj[b * 4 + (q - M * 4)];
-        }
-        a = warp_sum(a);
-        if (lane == 0) {
-            if (q < M * 4) sums[q] = a; else obj[q - M * 4] = a;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
+// The sufficient-decrease decision of one window (thread 0 of k_ls_decide).
+__device__ void decide_window(const double* sums, const double* obj, int M, int h_base, int max_halvings,
+                              double tau0, double lam1, double lam2, int first, Ctrl* ctrl) {
     if (first) {
         // f = -sum log w_ii + tr(Omega S Omega)/2 + lambda2/2 ||Omega||^2, tr = sum w_ij W_ij
         ctrl->f_cur = -obj[2] + 0.5 * obj[0] + 0.5 * lam2 * obj[1];
@@ -1003,16 +1243,52 @@ k_ls_decide(const double* __restrict__ part_ls, const double* __restrict__ part_
     if (h_base + M > max_halvings) ctrl->flags |= kFlagLsFail;
 }
 
+// Reduce the partials in a fixed order (one warp per quantity, lanes over strided
+// blocks, then a butterfly) and take the decision of Alg. 1 step 9.
+__global__ void __launch_bounds__(1024)
+k_ls_decide(const double* __restrict__ part_ls, const double* __restrict__ part_obj, int nblk, int M,
+            int max_halvings, double tau0, int use_cond, cudaGraphConditionalHandle cond, Ctrl* ctrl) {
+    __shared__ double sums[kMaxWindow * 4];
+    __shared__ double obj[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (ctrl->flags != 0 || ctrl->ls_accept >= 0) {
+        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        return;
+    }
+    const int h_base = ctrl->ls_base;
+    const int first = h_base == 0;
+    const double lam1 = ctrl->lam1, lam2 = ctrl->lam2;
+    const int nq = M * 4 + (first ? 4 : 0);
+    for (int q = warp; q < nq; q += 32) {
+        double a = 0.0;
+        if (q < M * 4) {
+            for (int b = lane; b < nblk; b += 32) a += part_ls[(size_t)b * kMaxWindow * 4 + q];
+        } else {
+            for (int b = lane; b < nblk; b += 32) a += part_obj[b * 4 + (q - M * 4)];
+        }
+        a = warp_sum(a);
+        if (lane == 0) {
+            if (q < M * 4) sums[q] = a; else obj[q - M * 4] = a;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    ctrl->ls_windows += 1;
+    decide_window(sums, obj, M, h_base, max_halvings, tau0, lam1, lam2, first, ctrl);
+    // another window while nothing is accepted and nothing went wrong
+    if (use_cond) cudaGraphSetConditional(cond, (ctrl->flags == 0 && ctrl->ls_accept < 0) ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------ 4. accept
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_compact_count(int p, Buckets<T> bk, T lam1, int* cnt2, const Ctrl* ctrl) {
+k_compact_count(int p, Buckets<T> bk, int* cnt2, const Ctrl* ctrl) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
     const T tau = (T)ctrl->tau;
-    const T tl1 = tau * lam1;
+    const T tl1 = tau * (T)ctrl->lam1;
     for (int i = gw; i < p; i += nw) {
         const int beg = bk.off[i], L = bk.len[i];
         int c = 0;
@@ -1032,13 +1308,13 @@ k_compact_count(int p, Buckets<T> bk, T lam1, int* cnt2, const Ctrl* ctrl) {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_compact_write(int p, Buckets<T> bk, T lam1, Csr<T> nx, int cap, const Ctrl* ctrl) {
+k_compact_write(int p, Buckets<T> bk, Csr<T> nx, int cap, const Ctrl* ctrl) {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
     const T tau = (T)ctrl->tau;
-    const T tl1 = tau * lam1;
+    const T tl1 = tau * (T)ctrl->lam1;
     for (int i = gw; i < p; i += nw) {
         const int beg = bk.off[i], L = bk.len[i];
         int out = nx.rp[i];
@@ -1102,26 +1378,30 @@ __global__ void k_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, con
 
 // ------------------------------------------------------------------ launchers
 template <typename T>
-void launch_iter_begin(const IterBufs<T>& b, cudaStream_t s) {
-    k_iter_begin<T><<<64, 256, 0, s>>>(b.bk, b.p, b.ctrl);
+void launch_iter_begin(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
+    k_iter_begin<T><<<64, 256, 0, s>>>(b.bk, b.p, b.ctrl, lc.use, lc.ls);
 }
 
+// One CTA per SM; more when the row-cache bound (kScreenMaxChunks chunks per CTA,
+// a share spans at most items/nblocks + 2 chunks) needs it.
 template <typename T>
 int screen_grid(int p, int num_sms) {
-    const int nchunks = (p + kScreenTileRows - 1) / kScreenTileRows;
-    const int need = (nchunks + kScreenMaxChunks - 1) / kScreenMaxChunks;
-    return std::max(1, std::min(nchunks, std::max(num_sms, need)));
+    constexpr int BJ = 32 * (16 / (int)sizeof(T));
+    const long long nchunks = (p + kScreenTileRows - 1) / kScreenTileRows;
+    const long long nblocks = (p + BJ - 1) / BJ;
+    const long long need = (nchunks + (kScreenMaxChunks - 2) - 1) / (kScreenMaxChunks - 2);
+    return (int)std::max(1LL, std::min(nchunks * nblocks, std::max((long long)num_sms, need)));
 }
 
 template <typename T>
 void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     constexpr int smem = screen_smem_bytes<T>();
-    cudaFuncSetAttribute(k_grad_screen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    set_smem_once((const void*)k_grad_screen<T>, smem, sizeof(T) == 8 ? kSmemSlotScreenD : kSmemSlotScreenF);
     k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.offlist, b.ctrl);
     k_grad_screen<T><<<screen_grid<T>(b.p, b.num_sms), kScreenThreads, smem, s>>>(
-        *b.smap, b.S, b.ld, b.p, b.rinfo, b.rdv, b.cur.ci, b.cur.cv, b.lam1, b.em, b.ctrl);
-    k_grad_screen_rows<T><<<b.num_sms * 4, kThreads, 0, s>>>(b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci,
-                                                            b.cur.cv, b.lam1, b.em, b.ctrl);
+        *b.smap, b.S, b.ld, b.p, b.rinfo, b.rdv, b.cur.ci, b.cur.cv, b.em, b.ctrl);
+    k_grad_screen_rows<T><<<b.num_sms * 2, kThreads, 0, s>>>(b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci,
+                                                            b.cur.cv, b.em, b.ctrl);
 }
 
 template <typename T>
@@ -1134,58 +1414,64 @@ void launch_candidates(const IterBufs<T>& b, cudaStream_t s) {
     const int g = 152 * 4;
     k_bucket_count<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
     k_scan<<<1, 1024, 0, s>>>(b.bk.cnt, b.bk.off, b.p, b.bk.cap, b.ctrl, kFlagBucketOverflow,
-                              &b.ctrl->bucket_total);
+                              &b.ctrl->bucket_total, b.bk.uoff);
     k_bucket_scatter<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
     k_bucket_sort<T><<<b.nblk, kThreads, 0, s>>>(b.bk, b.p, b.ctrl);
-    k_fill_w<T><<<b.nblk, kThreads, 0, s>>>(b.S, b.ld, b.p, b.cur, b.bk, b.ctrl);
-    k_gradient<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.lam1, b.lam2, b.part_obj, b.ctrl);
+    k_fill_w<T><<<b.num_sms * 8, kThreads, 0, s>>>(b.S, b.ld, b.cur, b.rinfo, b.rdv, b.bk, b.ctrl);
+    k_gradient<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.part_obj, b.ctrl);
 }
 
 template <typename T, int M>
-static void ls_eval_m(const IterBufs<T>& b, int h_base, cudaStream_t s) {
-    k_ls_eval<T, M><<<b.nblk, kThreads, 0, s>>>(b.S, b.ld, b.p, b.bk, b.lam1, 1.0, h_base, b.part_ls, b.ctrl);
+static void ls_eval_m(const IterBufs<T>& b, cudaStream_t s) {
+    k_ls_eval<T, M><<<b.nblk, kThreads, 0, s>>>(b.S, b.ld, b.p, b.bk, 1.0, b.part_ls, b.ctrl);
 }
 
+static int window_m(int M) { return M == 1 || M == 2 || M == 4 || M == 8 ? M : 16; }
+
 template <typename T>
-void launch_ls_window(const IterBufs<T>& b, int h_base, bool first, cudaStream_t s) {
-    const int M = b.ls_window;
+void launch_ls_window(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
+    const int M = window_m(b.ls_window);
     switch (M) {
-        case 1: ls_eval_m<T, 1>(b, h_base, s); break;
-        case 2: ls_eval_m<T, 2>(b, h_base, s); break;
-        case 4: ls_eval_m<T, 4>(b, h_base, s); break;
-        case 8: ls_eval_m<T, 8>(b, h_base, s); break;
-        default: ls_eval_m<T, 16>(b, h_base, s); break;
+        case 1: ls_eval_m<T, 1>(b, s); break;
+        case 2: ls_eval_m<T, 2>(b, s); break;
+        case 4: ls_eval_m<T, 4>(b, s); break;
+        case 8: ls_eval_m<T, 8>(b, s); break;
+        default: ls_eval_m<T, 16>(b, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M == 1 || M == 2 || M == 4 || M == 8 ? M : 16,
-                                  h_base, b.max_halvings, 1.0, (double)b.lam1, (double)b.lam2, first ? 1 : 0,
-                                  b.ctrl);
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls, b.ctrl);
 }
 
 template <int M>
-static void ls_eval_obs_m(const IterBufs<float>& b, int h_base, cudaStream_t s) {
-    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, b.lam1, 1.0, h_base, b.part_ls, b.ctrl);
+static void ls_eval_obs_m(const IterBufs<float>& b, cudaStream_t s) {
+    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, 1.0, b.part_ls, b.ctrl);
 }
 
-void launch_ls_window_obs(const IterBufs<float>& b, int h_base, bool first, cudaStream_t s) {
-    const int M = b.ls_window;
+void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s) {
+    const int M = window_m(b.ls_window);
     switch (M) {
-        case 1: ls_eval_obs_m<1>(b, h_base, s); break;
-        case 2: ls_eval_obs_m<2>(b, h_base, s); break;
-        case 4: ls_eval_obs_m<4>(b, h_base, s); break;
-        case 8: ls_eval_obs_m<8>(b, h_base, s); break;
-        default: ls_eval_obs_m<16>(b, h_base, s); break;
+        case 1: ls_eval_obs_m<1>(b, s); break;
+        case 2: ls_eval_obs_m<2>(b, s); break;
+        case 4: ls_eval_obs_m<4>(b, s); break;
+        case 8: ls_eval_obs_m<8>(b, s); break;
+        default: ls_eval_obs_m<16>(b, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M == 1 || M == 2 || M == 4 || M == 8 ? M : 16,
-                                   h_base, b.max_halvings, 1.0, (double)b.lam1, (double)b.lam2, first ? 1 : 0, b.ctrl);
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls, b.ctrl);
 }
 
 template <typename T>
 void launch_accept(const IterBufs<T>& b, cudaStream_t s) {
-    k_compact_count<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.lam1, b.cnt2, b.ctrl);
-    k_scan<<<1, 1024, 0, s>>>(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr);
-    k_compact_write<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.lam1, b.next, b.csr_cap, b.ctrl);
+    k_compact_count<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.cnt2, b.ctrl);
+    k_scan<<<1, 1024, 0, s>>>(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr);
+    k_compact_write<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.next, b.csr_cap, b.ctrl);
     k_converge<<<1, 1, 0, s>>>(b.next.rp, b.p, b.csr_cap, b.eps, b.ctrl);
 }
+
+template <typename T>
+void launch_commit(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
+    k_csr_commit<T><<<b.num_sms * 2, 256, 0, s>>>(b.next, b.cur, b.p, b.ctrl, lc.use, lc.iter);
+}
+
+void launch_stamp(Ctrl* ctrl, int end, cudaStream_t s) { k_stamp<<<1, 1, 0, s>>>(ctrl, end); }
 
 template <typename T>
 void launch_set_identity(Csr<T> c, int p, cudaStream_t s) {
@@ -1207,10 +1493,11 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
 }
 
 #define HPC_INSTANTIATE(T)                                                                       \
-    template void launch_iter_begin<T>(const IterBufs<T>&, cudaStream_t);                          \
+    template void launch_iter_begin<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);         \
+    template void launch_commit<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);             \
     template void launch_grad_screen<T>(const IterBufs<T>&, cudaStream_t);                         \
     template void launch_candidates<T>(const IterBufs<T>&, cudaStream_t);                          \
-    template void launch_ls_window<T>(const IterBufs<T>&, int, bool, cudaStream_t);                \
+    template void launch_ls_window<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);          \
     template void launch_accept<T>(const IterBufs<T>&, cudaStream_t);                              \
     template void launch_set_identity<T>(Csr<T>, int, cudaStream_t);                               \
     template void launch_row_info<T>(int, Csr<T>, int4*, T*, cudaStream_t);                        \

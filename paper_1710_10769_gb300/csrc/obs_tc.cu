@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(128, 1)
 k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUtensorMap yb,
            const __grid_constant__ CUtensorMap xa, const __grid_constant__ CUtensorMap xb, const int2* __restrict__ pairs,
            int k_tiles, int p, int64_t n, const int* __restrict__ rp, const int* __restrict__ ci,
-           const float* __restrict__ cv, float lam1, Emit<float> em, Ctrl* __restrict__ ctrl) {
+           const float* __restrict__ cv, Emit<float> em, Ctrl* __restrict__ ctrl) {
     using C = ObsCfg<MODE>;
+    const float lam1 = (float)ctrl->lam1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int region = C::kStages * C::kStageBytes > C::kTransBytes ? C::kStages * C::kStageBytes : C::kTransBytes;
@@ -357,24 +358,23 @@ bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void
 }
 
 cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
-                             int p, const int* rp, const int* ci, const float* cv, float lam1, Emit<float> em,
+                             int p, const int* rp, const int* ci, const float* cv, Emit<float> em,
                              Ctrl* ctrl, cudaStream_t s) {
     const int64_t n_pad = (n + 63) / 64 * 64;
     if (precision == HPC_PREC_TF32) {
         using C = ObsCfg<kObsTf32>;
-        cudaError_t e = cudaFuncSetAttribute(k_obs_pair<kObsTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        cudaError_t e = set_smem_once((const void*)k_obs_pair<kObsTf32>, C::kSmem, kSmemSlotObsTf32);
         if (e != cudaSuccess) return e;
         k_obs_pair<kObsTf32><<<(unsigned)npairs, 128, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
                                                                      (int)(n_pad / C::kBK), p, n, rp, ci, cv,
-                                                                     lam1, em, ctrl);
+                                                                     em, ctrl);
     } else {
         using C = ObsCfg<kObsBf16x3>;
-        cudaError_t e =
-            cudaFuncSetAttribute(k_obs_pair<kObsBf16x3>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        cudaError_t e = set_smem_once((const void*)k_obs_pair<kObsBf16x3>, C::kSmem, kSmemSlotObsBf16x3);
         if (e != cudaSuccess) return e;
         k_obs_pair<kObsBf16x3><<<(unsigned)npairs, 128, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
                                                                        (int)(n_pad / C::kBK), p, n, rp, ci, cv,
-                                                                       lam1, em, ctrl);
+                                                                       em, ctrl);
     }
     return cudaGetLastError();
 }

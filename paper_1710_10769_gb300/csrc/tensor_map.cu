@@ -5,6 +5,7 @@
 
 #include <mutex>
 
+#include "internal.cuh"
 #include "ptx.cuh"
 
 namespace hpc {
@@ -52,6 +53,21 @@ bool encode_tensor_map_2d_sw128(CUtensorMap* map, const void* base, int elem_byt
                                 uint64_t row_stride_bytes, uint32_t box_inner, uint32_t box_outer) {
     return encode(map, base, elem_bytes, inner, outer, row_stride_bytes, box_inner, box_outer,
                   CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+cudaError_t set_smem_once(const void* func, int bytes, int slot) {
+    static std::mutex mu;
+    static bool done[64][kSmemSlots] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= kSmemSlots)
+        return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev][slot]) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done[dev][slot] = true;
+    return e;
 }
 
 }  // namespace hpc

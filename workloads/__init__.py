@@ -58,6 +58,11 @@ WORKLOADS = {
     "adjoint_p16384": Workload("adjoint_p16384", 16384, 4096, "random", 5.0, 0, 0.2, 0.1, 1e-6, "f32", 4),
 }
 
+# Batch of independent problems of uneven size: p = 1024 k (k = 1..16), n = p / 2,
+# banded Omega0 of bandwidth 3 (FP32 X).
+BATCH_PROBLEMS = tuple(Workload(f"batch_p{1024 * k}", 1024 * k, 512 * k, "banded", 0.0, 3, 0.15, 0.1, 1e-6, "f32",
+                                100 + k) for k in range(1, 17))
+
 # Regularisation grid of the batched path workload: 32 values of lambda1,
 # log-spaced over [0.05, 0.8], at lambda2 = 0.1.
 PATH_LAMBDA1 = tuple(float(v) for v in np.logspace(math.log10(0.05), math.log10(0.8), 32))
