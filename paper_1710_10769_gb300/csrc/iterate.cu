@@ -604,16 +604,16 @@ __device__ __forceinline__ long long warp_incl_scan64(long long x, int lane) {
     return x;
 }
 
-// Single-block exclusive scan of n ints (chunks of 4096), out[n] = total.
-// If total > cap, sets flag.  With uoff, also the exclusive 64-bit scan of
-// ls_units(in[i]) (uoff[n] = total units).
+// Single-block exclusive scan of n ints, out[n] = total; if total > cap, sets
+// flag.  With uoff, also the exclusive 64-bit scan of ls_units(in[i]) (uoff[n] =
+// total units).  Thread t owns the contiguous run [t E, t E + E): one pass sums
+// the runs (16-byte loads), one block-wide scan of the 1024 run sums, and a
+// second pass writes the run's prefixes.
 __global__ void __launch_bounds__(1024)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
        int* total_dst, long long* __restrict__ uoff) {
     __shared__ int wsum[32];
     __shared__ long long usum[32];
-    __shared__ int carry;
-    __shared__ long long ucarry;
     if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) {
         if (threadIdx.x == 0) {
             out[n] = 0;
@@ -622,50 +622,51 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* 
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) { carry = 0; ucarry = 0; }
-    __syncthreads();
-    for (int base = 0; base < n; base += 4096) {
-        const int idx = base + threadIdx.x * 4;
+    const int E = ((n + 1023) / 1024 + 3) & ~3;
+    const int b0 = min(n, threadIdx.x * E), b1 = min(n, b0 + E);
+    int s = 0;
+    long long us = 0;
+    for (int j = b0; j < b1; j += 4) {
         int v[4];
-        long long uv[4];
-        int s = 0;
-        long long us = 0;
+        if (j + 4 <= b1) {
+            const int4 x = *reinterpret_cast<const int4*>(in + j);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = j + q < b1 ? in[j + q] : 0;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            v[q] = (idx + q < n) ? in[idx + q] : 0;
-            uv[q] = (uoff && idx + q < n) ? ls_units(v[q]) : 0;
             s += v[q];
-            us += uv[q];
+            if (uoff && j + q < b1) us += ls_units(v[q]);
         }
-        const int x = warp_incl_scan(s, lane);
-        const long long ux = uoff ? warp_incl_scan64(us, lane) : 0;
-        if (lane == 31) { wsum[warp] = x; usum[warp] = ux; }
-        __syncthreads();
-        if (warp == 0) {
-            wsum[lane] = warp_incl_scan(wsum[lane], lane);
-            if (uoff) usum[lane] = warp_incl_scan64(usum[lane], lane);
-        }
-        __syncthreads();
-        int run = x - s + (warp ? wsum[warp - 1] : 0) + carry;
-        long long urun = ux - us + (warp ? usum[warp - 1] : 0) + ucarry;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (idx + q < n) {
-                out[idx + q] = run;
-                if (uoff) uoff[idx + q] = urun;
-            }
-            run += v[q];
-            urun += uv[q];
-        }
-        __syncthreads();
-        if (threadIdx.x == 1023) { carry = run; ucarry = urun; }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        out[n] = carry;
-        if (uoff) uoff[n] = ucarry;
-        if (total_dst) *total_dst = carry;
-        if (carry > cap) atomicOr(&ctrl->flags, flag);
+    const int x = warp_incl_scan(s, lane);
+    const long long ux = uoff ? warp_incl_scan64(us, lane) : 0;
+    if (lane == 31) { wsum[warp] = x; usum[warp] = ux; }
+    __syncthreads();
+    if (warp == 0) {
+        wsum[lane] = warp_incl_scan(wsum[lane], lane);
+        if (uoff) usum[lane] = warp_incl_scan64(usum[lane], lane);
+    }
+    __syncthreads();
+    int run = x - s + (warp ? wsum[warp - 1] : 0);
+    long long urun = ux - us + (warp ? usum[warp - 1] : 0);
+    for (int j = b0; j < b1; ++j) {
+        const int v = in[j];
+        out[j] = run;
+        run += v;
+        if (uoff) {
+            uoff[j] = urun;
+            urun += ls_units(v);
+        }
+    }
+    if (threadIdx.x == 1023) {
+        const int total = wsum[31];
+        out[n] = total;
+        if (uoff) uoff[n] = usum[31];
+        if (total_dst) *total_dst = total;
+        if (total > cap) atomicOr(&ctrl->flags, flag);
     }
 }
 
@@ -900,7 +901,7 @@ k_fill_w(const T* __restrict__ S, int64_t ld, Csr<T> om, const int4* __restrict_
 // G on the candidates (Alg. 2 steps 5-6) and the objective partials of Omega^k.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gradient(int p, Buckets<T> bk, double* part_obj, Ctrl* ctrl) {
+k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
     using A = typename AccOf<T>::type;
     __shared__ double red[kWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -952,7 +953,7 @@ k_gradient(int p, Buckets<T> bk, double* part_obj, Ctrl* ctrl) {
     if (threadIdx.x < 4) {
         double a = 0.0;
         for (int w = 0; w < kWarps; ++w) a += red[w][threadIdx.x];
-        part_obj[blockIdx.x * 4 + threadIdx.x] = a;
+        part_obj[(size_t)threadIdx.x * stride + blockIdx.x] = a;
     }
 }
 
@@ -977,19 +978,40 @@ __device__ __forceinline__ int find_unit_row(const long long* __restrict__ uoff,
     return lo;
 }
 
-// Partials per block and per tau of the window:
+// tau = 2^-h in T, exactly (what ldexp(1, -h) rounds to, denormals and 0 included).
+template <typename T> __device__ __forceinline__ T tau_pow2(int h);
+template <> __device__ __forceinline__ float tau_pow2<float>(int h) {
+    return h <= 126 ? __int_as_float((127 - h) << 23) : (h <= 149 ? __int_as_float(1 << (149 - h)) : 0.f);
+}
+template <> __device__ __forceinline__ double tau_pow2<double>(int h) {
+    return h <= 1022 ? __longlong_as_double((long long)(1023 - h) << 52)
+                     : (h <= 1074 ? __longlong_as_double(1ll << (1074 - h)) : 0.0);
+}
+
+__device__ __forceinline__ F2 to_acc(float x) { F2 a; a.hi = x; return a; }
+__device__ __forceinline__ double to_acc(double x) { return x; }
+__device__ __forceinline__ void acc_merge(F2& a, const F2& b) { acc_add(a, b.hi); a.lo = __fadd_rn(a.lo, b.lo); }
+__device__ __forceinline__ void acc_merge(double& a, double b) { a += b; }
+
+// Partials per block and per tau of the window, stored quantity-major
+// (part_ls[(4 m + k) * stride + block]):
 //   [0] sum_{e,f} D_e D_f S_{j_e j_f}   (= tr(D S D) restricted to row i, summed over rows)
 //   [1] ||D||_F^2                       [2] sum_i phi(D_ii / w_ii)     [3] #{w+_ii <= 0}
 // The quadratic form of row i is split into work units, the pairs (a <= b) of its
 // 32-entry chunks; every warp takes an equal contiguous range of the units of all
 // rows (prefix uoff), so rows with thousands of candidates spread over many warps.
+// Terms [1]-[3] are per entry: each diagonal unit (a = b) warp-reduces them into
+// the warp's shared accumulators, which keeps the register count (and so the
+// number of resident warps on a persistent grid) where the gathers need it.
 template <typename T, int M>
-__global__ void __launch_bounds__(kThreads)
-k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0, double* part_ls,
+__global__ void __launch_bounds__(kThreads, 2)
+k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride, double* part_ls,
           const Ctrl* ctrl) {
     using A = typename AccOf<T>::type;
     __shared__ int s_col[kWarps][32];
     __shared__ T s_del[kWarps][M][32];
+    __shared__ A s_acc[kWarps][M][2];
+    __shared__ int s_nb[kWarps][M];
     __shared__ double red[kWarps][M][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -997,17 +1019,12 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
     const bool skip = (ctrl->flags != 0) || (ctrl->ls_accept >= 0);
     const T lam1 = (T)ctrl->lam1;
     const int h_base = ctrl->ls_base;
-
-    T tau[M], tl1[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        tau[m] = (T)ldexp(tau0, -(h_base + m));
-        tl1[m] = tau[m] * lam1;
+    if (lane < M) {
+        s_acc[warp][lane][0] = A{};
+        s_acc[warp][lane][1] = A{};
+        s_nb[warp][lane] = 0;
     }
-    A q[M]{}, n2[M]{}, ph[M]{};
-    int nb[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) nb[m] = 0;
+    A q[M]{};
 
     const long long U = skip ? 0 : bk.uoff[p];
     long long u = U * gw / nw;
@@ -1030,26 +1047,43 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
                 T de[M];
                 int je = 0;
                 bool act_e = false;
-                if (e < L) {
-                    je = bk.col_b[beg + e];
-                    const T om = bk.om_b[beg + e], g = bk.g[beg + e];
-                    const bool diag = (je == i);
+                {
+                    T om = T(0), g = T(0);
+                    bool diag = false;
+                    if (e < L) {
+                        je = bk.col_b[beg + e];
+                        om = bk.om_b[beg + e];
+                        g = bk.g[beg + e];
+                        diag = (je == i);
+                    }
 #pragma unroll
                     for (int m = 0; m < M; ++m) {
-                        const T np_ = prox_entry(om, g, tau[m], tl1[m], diag);
-                        de[m] = np_ - om;
+                        const T tau = tau_pow2<T>(h_base + m);
+                        const T np_ = prox_entry(om, g, tau, tau * lam1, diag);
+                        de[m] = e < L ? np_ - om : T(0);
                         act_e |= (de[m] != T(0));
-                        if (diag_unit) {
-                            acc_add(n2[m], mulT(de[m], de[m]));
+                    }
+                    if (diag_unit) {
+                        // per-entry terms of this chunk: ||D||^2, phi(D_ii / w_ii), #{w+_ii <= 0}
+#pragma unroll
+                        for (int m = 0; m < M; ++m) {
+                            T ph = T(0);
+                            bool bad = false;
                             if (diag) {
-                                if (!(np_ > T(0))) nb[m] += 1;
-                                else acc_add(ph[m], phiT(de[m] / om));
+                                const T np_ = om + de[m];
+                                if (!(np_ > T(0))) bad = true;
+                                else ph = phiT(de[m] / om);
+                            }
+                            const A n2 = warp_sum(to_acc(mulT(de[m], de[m])));
+                            const A pp = warp_sum(to_acc(ph));
+                            const int nbad = __popc(__ballot_sync(kFull, bad));
+                            if (lane == 0) {
+                                acc_merge(s_acc[warp][m][0], n2);
+                                acc_merge(s_acc[warp][m][1], pp);
+                                s_nb[warp][m] += nbad;
                             }
                         }
                     }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < M; ++m) de[m] = T(0);
                 }
                 __syncwarp();
                 {
@@ -1061,7 +1095,8 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
                         bool act = false;
 #pragma unroll
                         for (int m = 0; m < M; ++m) {
-                            const T d = prox_entry(om, g, tau[m], tl1[m], jf == i) - om;
+                            const T tau = tau_pow2<T>(h_base + m);
+                            const T d = prox_entry(om, g, tau, tau * lam1, jf == i) - om;
                             s_del[warp][m][lane] = d;
                             act |= (d != T(0));
                         }
@@ -1078,7 +1113,7 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
 #pragma unroll
                     for (int m = 0; m < M; ++m) qf[m] = T(0);
                     const T* srow = S + (int64_t)je * ld;
-#pragma unroll 8
+#pragma unroll 4
                     for (int t = 0; t < 32; ++t) {
                         const int jf = s_col[warp][t];
                         const bool use = jf >= 0 && (!diag_unit || t >= lane);
@@ -1094,15 +1129,15 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
             if (++cb == tc) { ++a; cb = a; }
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-        const A a = warp_sum(q[m]), b = warp_sum(n2[m]), c = warp_sum(ph[m]);
-        int d = nb[m];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+        const A a = warp_sum(q[m]);
         if (lane == 0) {
-            red[warp][m][0] = acc_value(a); red[warp][m][1] = acc_value(b);
-            red[warp][m][2] = acc_value(c); red[warp][m][3] = (double)d;
+            red[warp][m][0] = acc_value(a);
+            red[warp][m][1] = acc_value(s_acc[warp][m][0]);
+            red[warp][m][2] = acc_value(s_acc[warp][m][1]);
+            red[warp][m][3] = (double)s_nb[warp][m];
         }
     }
     __syncthreads();
@@ -1110,7 +1145,7 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
         const int m = threadIdx.x / 4, k = threadIdx.x % 4;
         double a = 0.0;
         for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
-        part_ls[(size_t)blockIdx.x * kMaxWindow * 4 + m * 4 + k] = a;
+        part_ls[(size_t)(m * 4 + k) * stride + blockIdx.x] = a;
     }
 }
 
@@ -1120,7 +1155,7 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, double tau0
 template <int M>
 __global__ void __launch_bounds__(kThreads)
 k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, double tau0,
-              double* part_ls, const Ctrl* ctrl) {
+              int stride, double* part_ls, const Ctrl* ctrl) {
     __shared__ double red[kWarps][M][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1210,7 +1245,7 @@ k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Bucke
         const int m = threadIdx.x / 4, k = threadIdx.x % 4;
         double a = 0.0;
         for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
-        part_ls[(size_t)blockIdx.x * kMaxWindow * 4 + m * 4 + k] = a;
+        part_ls[(size_t)(m * 4 + k) * stride + blockIdx.x] = a;
     }
 }
 
@@ -1246,8 +1281,8 @@ __device__ void decide_window(const double* sums, const double* obj, int M, int 
 // Reduce the partials in a fixed order (one warp per quantity, lanes over strided
 // blocks, then a butterfly) and take the decision of Alg. 1 step 9.
 __global__ void __launch_bounds__(1024)
-k_ls_decide(const double* __restrict__ part_ls, const double* __restrict__ part_obj, int nblk, int M,
-            int max_halvings, double tau0, int use_cond, cudaGraphConditionalHandle cond, Ctrl* ctrl) {
+k_ls_decide(const double* __restrict__ part_ls, int n_ls, const double* __restrict__ part_obj, int n_obj, int stride,
+            int M, int max_halvings, double tau0, int use_cond, cudaGraphConditionalHandle cond, Ctrl* ctrl) {
     __shared__ double sums[kMaxWindow * 4];
     __shared__ double obj[4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1262,9 +1297,9 @@ k_ls_decide(const double* __restrict__ part_ls, const double* __restrict__ part_
     for (int q = warp; q < nq; q += 32) {
         double a = 0.0;
         if (q < M * 4) {
-            for (int b = lane; b < nblk; b += 32) a += part_ls[(size_t)b * kMaxWindow * 4 + q];
+            for (int b = lane; b < n_ls; b += 32) a += part_ls[(size_t)q * stride + b];
         } else {
-            for (int b = lane; b < nblk; b += 32) a += part_obj[b * 4 + (q - M * 4)];
+            for (int b = lane; b < n_obj; b += 32) a += part_obj[(size_t)(q - M * 4) * stride + b];
         }
         a = warp_sum(a);
         if (lane == 0) {
@@ -1418,12 +1453,28 @@ void launch_candidates(const IterBufs<T>& b, cudaStream_t s) {
     k_bucket_scatter<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
     k_bucket_sort<T><<<b.nblk, kThreads, 0, s>>>(b.bk, b.p, b.ctrl);
     k_fill_w<T><<<b.num_sms * 8, kThreads, 0, s>>>(b.S, b.ld, b.cur, b.rinfo, b.rdv, b.bk, b.ctrl);
-    k_gradient<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.part_obj, b.ctrl);
+    k_gradient<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.nblk, b.part_obj, b.ctrl);
+}
+
+// Persistent grid of the line-search evaluation: resident blocks x SMs (at most
+// nblk, the partial arrays' stride).
+template <typename T, int M>
+static int ls_eval_grid(const IterBufs<T>& b) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int v = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ls_eval<T, M>, kThreads, 0) != cudaSuccess || v < 1)
+            v = 1;
+        per_sm = v;
+    }
+    return std::max(1, std::min(b.nblk, per_sm * b.num_sms));
 }
 
 template <typename T, int M>
-static void ls_eval_m(const IterBufs<T>& b, cudaStream_t s) {
-    k_ls_eval<T, M><<<b.nblk, kThreads, 0, s>>>(b.S, b.ld, b.p, b.bk, 1.0, b.part_ls, b.ctrl);
+static int ls_eval_m(const IterBufs<T>& b, cudaStream_t s) {
+    const int g = ls_eval_grid<T, M>(b);
+    k_ls_eval<T, M><<<g, kThreads, 0, s>>>(b.S, b.ld, b.p, b.bk, b.nblk, b.part_ls, b.ctrl);
+    return g;
 }
 
 static int window_m(int M) { return M == 1 || M == 2 || M == 4 || M == 8 ? M : 16; }
@@ -1431,19 +1482,21 @@ static int window_m(int M) { return M == 1 || M == 2 || M == 4 || M == 8 ? M : 1
 template <typename T>
 void launch_ls_window(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
     const int M = window_m(b.ls_window);
+    int g = 0;
     switch (M) {
-        case 1: ls_eval_m<T, 1>(b, s); break;
-        case 2: ls_eval_m<T, 2>(b, s); break;
-        case 4: ls_eval_m<T, 4>(b, s); break;
-        case 8: ls_eval_m<T, 8>(b, s); break;
-        default: ls_eval_m<T, 16>(b, s); break;
+        case 1: g = ls_eval_m<T, 1>(b, s); break;
+        case 2: g = ls_eval_m<T, 2>(b, s); break;
+        case 4: g = ls_eval_m<T, 4>(b, s); break;
+        case 8: g = ls_eval_m<T, 8>(b, s); break;
+        default: g = ls_eval_m<T, 16>(b, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls, b.ctrl);
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, g, b.part_obj, b.nblk, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls,
+                                  b.ctrl);
 }
 
 template <int M>
 static void ls_eval_obs_m(const IterBufs<float>& b, cudaStream_t s) {
-    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, 1.0, b.part_ls, b.ctrl);
+    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, 1.0, b.nblk, b.part_ls, b.ctrl);
 }
 
 void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s) {
@@ -1455,7 +1508,8 @@ void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStre
         case 8: ls_eval_obs_m<8>(b, s); break;
         default: ls_eval_obs_m<16>(b, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.part_obj, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls, b.ctrl);
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.nblk, b.part_obj, b.nblk, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls,
+                                   b.ctrl);
 }
 
 template <typename T>
