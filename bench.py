@@ -111,20 +111,23 @@ def reduce_over_ranks(ms, iters, pg, device):
     return float(t[0]), float(u[0])
 
 
-def screen_traffic(p):
-    """DRAM bytes of one screening pass from the committed ncu summary, scaled to p
-    (the pass streams S once: bytes grow as p^2); None when the summary was taken on a
-    different version of the kernels' source."""
+def measured_traffic(kernel, p, n):
+    """DRAM bytes per launch of `kernel` ("screen_pass" or "gram") from the committed
+    ncu summary (profiles/roofline_traffic.txt, a 1-pass capture at the full
+    workload); None when it was taken on other sizes or another version of the
+    kernel's source."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", "grad_screen_traffic.txt")
-    src = os.path.join(ROOT, "paper_1710_10769_gb300", "csrc", "iterate.cu")
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    srcs = {"screen_pass": "iterate.cu", "gram": "gram_tc.cu"}
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
-        with open(src, "rb") as fh:
-            if hashlib.sha256(fh.read()).hexdigest() != kv["iterate_cu_sha256"]:
+        with open(os.path.join(ROOT, "paper_1710_10769_gb300", "csrc", srcs[kernel]), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != kv[f"{kernel}.src_sha256"]:
                 return None
-        return float(kv["dram_bytes_per_pass"]) * (p / float(kv["p"])) ** 2
+        if int(kv[f"{kernel}.p"]) != p or int(kv[f"{kernel}.n"]) != n:
+            return None
+        return float(kv[f"{kernel}.dram_bytes"])
     except Exception:
         return None
 
@@ -213,6 +216,11 @@ def main(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-sample-p", type=int, default=2048)
+    ap.add_argument("--device-loop", type=int, default=0, choices=[0, 1],
+                    help="1: iterations run as one CUDA-graph launch per solve (the per-pass screening "
+                         "time then comes from device timestamps instead of CUDA events)")
+    ap.add_argument("--compare-loops", type=int, default=1, choices=[0, 1],
+                    help="also time one solve with the other loop driver")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -237,8 +245,9 @@ def main(argv=None):
     X = make_x(w, device="cuda")
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    solver = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=hpc.BF16 if w.x_dtype == "bf16" else hpc.F32,
-                        precision=prec, eps=w.eps, max_iter=100000)
+    xdt = hpc.BF16 if w.x_dtype == "bf16" else hpc.F32
+    solver = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=prec, eps=w.eps,
+                        max_iter=100000, device_loop=args.device_loop)
 
     def step(Xsrc):
         solver.load_x(Xsrc)
@@ -267,54 +276,83 @@ def main(argv=None):
     ms_all, iters_all = reduce_over_ranks(ms, iters, pg, "cuda")
     value = iters_all / (ms_all / 1000.0)
 
-    # dominant kernel: the Gram (one launch per step) or the screening SpMM (one per iteration)
+    # rooflines of the two kernels that take the step's time: the Gram (one launch per
+    # step) and the screening pass (one per iteration); the line's "roofline" is the
+    # one with more device time per step
     hbm, bf16, bf16_sus, peak_src = _peaks()
     gram_ms = sum(r["ms_gram_step"] for r in recs)
     scr_ms = sum(r["ms_grad_pass"] for r in recs)
     scr_launches = sum(r["grad_pass_launches"] for r in recs)
     p, n = w.p, w.n
     tensor_gram = solver.precision_used() in (hpc.PREC_BF16X3, hpc.PREC_TF32)
-    if gram_ms >= scr_ms:
-        flops = float(n) * p * (p + 1)               # symmetric half of X^T X (n p (p+1) FMA-flops)
-        achieved = flops / (gram_ms / len(recs) / 1000.0) / 1e12
-        if tensor_gram:
-            peak = bf16 if solver.precision_used() == hpc.PREC_BF16X3 else bf16 / 2.0
-            bound = "tensor"
-        else:
-            peak = 152 * 128 * 2 * 2.07e9 / 1e12      # SIMT FP32 FMA peak at the max SM clock
-            bound = "alu"
-        roof = {"kernel": "gram", "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src if bound == "tensor" else
-                "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"}
+    flops = float(n) * p * (p + 1)                   # symmetric half of X^T X: n p (p+1) FMA-flops
+    g_achieved = flops / (gram_ms / len(recs) / 1000.0) / 1e12
+    if tensor_gram:
+        # a long kernel inside a long step: the sustained bf16 peak; TF32 at half the bf16 rate
+        g_peak = bf16_sus if bf16_sus else bf16
+        if solver.precision_used() == hpc.PREC_TF32:
+            g_peak = g_peak / 2.0
+        g_bound, g_src = "tensor", f"{peak_src} (bf16 sustained)"
     else:
-        per = scr_ms / max(scr_launches, 1) / 1000.0
-        achieved = 4.0 * p * p / per / 1e9           # S read once per pass (FP32), bytes / launch time
-        roof = {"kernel": "grad_screen", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": screen_traffic(p), "peak_source": peak_src}
+        g_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # SIMT FP32 FMA peak at the max SM clock
+        g_bound, g_src = "alu", "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    roof_gram = {"kernel": "gram", "bound": g_bound, "achieved": g_achieved, "peak": g_peak, "unit": "TFLOP/s",
+                 "frac": g_achieved / g_peak, "traffic": measured_traffic("gram", p, n), "peak_source": g_src,
+                 "ms_per_launch": gram_ms / len(recs)}
+    per = scr_ms / max(scr_launches, 1) / 1000.0
+    uniq = 4.0 * p * (p + 1) / 2.0                   # each distinct entry of the symmetric S read once
+    s_achieved = uniq / per / 1e9
+    roof_scr = {"kernel": "screen_pass", "bound": "hbm", "achieved": s_achieved, "peak": hbm, "unit": "GB/s",
+                "frac": s_achieved / hbm, "traffic": measured_traffic("screen_pass", p, n), "peak_source": peak_src,
+                "ms_per_launch": per * 1000.0, "algorithmic_bytes": uniq,
+                "frac_full_S": 4.0 * p * p / per / 1e9 / hbm}
+    roof = roof_gram if gram_ms >= scr_ms else roof_scr
 
     # end to end through the C ABI with host buffers: H2D of X inside the timed region,
     # D2H of the CSR result
-    Xh = X.cpu().pin_memory()
-    e2e_ms, e2e_its, d2h = 0.0, 0, 0
-    for k in range(args.e2e_steps + 1):
+    e2e = None
+    if args.e2e_steps > 0:
+        Xh = X.cpu().pin_memory()
+        e2e_ms, e2e_its, d2h = 0.0, 0, 0
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            solver.load_x(Xh)
+            st = solver.solve().as_dict()
+            csr = solver.get_omega(np.float32)
+            t1 = time.perf_counter()
+            if k >= 1:
+                e2e_ms += (t1 - t0) * 1000
+                e2e_its += st["iterations"]
+                d2h += csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes
+        e2e = {"value": e2e_its / (e2e_ms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
+               "d2h_bytes_per_step": int(d2h // max(args.e2e_steps, 1))}
+        del Xh
+
+    # the same step with the other loop driver (host-driven iterations vs one CUDA-graph
+    # launch per solve), for comparison
+    other = None
+    if args.compare_loops and rank == 0:
+        alt = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=prec, eps=w.eps,
+                         max_iter=100000, device_loop=1 - args.device_loop)
+        alt.load_x(X)
+        alt.solve()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        alt.load_x(X)
+        ast = alt.solve().as_dict()
+        e1.record(stream)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        solver.load_x(Xh)
-        st = solver.solve().as_dict()
-        csr = solver.get_omega(np.float32)
-        t1 = time.perf_counter()
-        if k >= 1:
-            e2e_ms += (t1 - t0) * 1000
-            e2e_its += st["iterations"]
-            d2h += csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes
-    e2e = {"value": e2e_its / (e2e_ms / 1000.0), "unit": UNIT,
-           "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
-           "d2h_bytes_per_step": int(d2h // max(args.e2e_steps, 1))}
+        other = {"device_loop": 1 - args.device_loop, "ms_per_step": e0.elapsed_time(e1),
+                 "value": ast["iterations"] / (e0.elapsed_time(e1) / 1000.0), "iterations": ast["iterations"]}
+        alt.close()
 
     plain = None
     if not args.no_plain and solver.precision_used() != hpc.PREC_FP32 and rank == 0:
-        ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=hpc.BF16 if w.x_dtype == "bf16" else hpc.F32,
-                        precision=hpc.PREC_FP32, eps=w.eps, max_iter=100000)
+        ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=hpc.PREC_FP32, eps=w.eps,
+                        max_iter=100000, device_loop=args.device_loop)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -353,6 +391,7 @@ def main(argv=None):
             "config": {"workload": w.name, "p": p, "n": n, "lambda1": w.lambda1, "lambda2": w.lambda2,
                        "eps": w.eps, "x_dtype": w.x_dtype, "s_dtype": "f32",
                        "gram_precision": solver.precision_name(), "parallelism": f"replicas x{ws}",
+                       "loop": "device (one CUDA graph per solve)" if args.device_loop else "host-driven",
                        "l2": "inputs > L2 (X 4.3 GB, S 17.2 GB); no flush"},
             "iterations_per_step": [r["iterations"] for r in recs],
             "ls_trials_per_step": [r["ls_trials"] for r in recs],
@@ -361,8 +400,8 @@ def main(argv=None):
             "iteration_loop_its": iters / (sum(r["ms_total"] for r in recs) / 1000.0),
             "grad_pass_ms": scr_ms / max(scr_launches, 1),
             "final_nnz": recs[-1]["nnz"], "final_F": recs[-1]["F"],
-            "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
-            "cpu_baseline": cpu, "plain_fp32": plain,
+            "roofline": roof, "roofline_kernels": [roof_gram, roof_scr], "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
+            "cpu_baseline": cpu, "plain_fp32": plain, "other_loop": other,
         }
         print(json.dumps(line), flush=True)
     solver.close()

@@ -96,7 +96,10 @@ struct hpc_ctx {
     CUtensorMap smap;
     int4* rinfo = nullptr;
     int* offlist = nullptr;
-    void* rdv = nullptr;
+    void* rdv = nullptr;            // ld entries, zero padded
+    unsigned* pmask = nullptr;      // ld / 32 words
+    long long* seqoff = nullptr;    // folded tile sequence of the screening pass
+    int screen_grid = 1;
     int num_sms = 0;
     // scratch for the tensor-core Gram
     void* gram_scratch = nullptr;
@@ -228,6 +231,9 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.rinfo = h->rinfo;
     b.offlist = h->offlist;
     b.rdv = as<T>(h->rdv);
+    b.pmask = h->pmask;
+    b.seqoff = h->seqoff;
+    b.screen_grid = h->screen_grid;
     b.num_sms = h->num_sms;
     b.xt = h->xt;
     b.ldx = h->ldx;
@@ -689,7 +695,7 @@ void destroy(hpc_ctx* h) {
     void* ptrs[] = {h->S, h->rp[0], h->rp[1], h->ci[0], h->ci[1], h->cv[0], h->cv[1], h->bk_cnt, h->bk_off,
                     h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
-                    h->yp[0], h->yp[1], h->pairs, h->bk_uoff};
+                    h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -816,7 +822,17 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     }
     CK(cudaMalloc(&h->rinfo, p * sizeof(int4)));
     CK(cudaMalloc(&h->offlist, p * sizeof(int)));
-    CK(cudaMalloc(&h->rdv, p * vs));
+    CK(cudaMalloc(&h->rdv, h->ld * vs));
+    CK(cudaMemsetAsync(h->rdv, 0, h->ld * vs, h->stream));
+    CK(cudaMalloc(&h->pmask, (h->ld / 32) * sizeof(unsigned)));
+    CK(cudaMemsetAsync(h->pmask, 0, (h->ld / 32) * sizeof(unsigned), h->stream));
+    if (variant == HPC_COV) {
+        std::vector<long long> so;
+        h->screen_grid = h->vdt == HPC_F64 ? hpc::screen_plan<double>((int)p, h->num_sms, so)
+                                           : hpc::screen_plan<float>((int)p, h->num_sms, so);
+        CK(cudaMalloc(&h->seqoff, so.size() * sizeof(long long)));
+        CK(cudaMemcpy(h->seqoff, so.data(), so.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    }
     for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->rp[b], (p + 1) * sizeof(int)));
     const int64_t cap0 = o.capacity > 0 ? o.capacity : std::max<int64_t>(32 * p, 1024);
     {

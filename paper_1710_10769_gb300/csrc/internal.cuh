@@ -112,7 +112,10 @@ struct IterBufs {
     const CUtensorMap* smap;  // TMA descriptor of S (rows p, columns ld), 64 x BJ boxes
     int4* rinfo;              // p: CSR bounds, diagonal position, pure-diagonal flag of each row
     int* offlist;             // p: rows with off-diagonal entries
-    T* rdv;                   // p: diagonal value of each row
+    T* rdv;                   // ld (zero padded): diagonal value of each row
+    unsigned* pmask;          // ld/32: pure-diagonal bit of each row
+    const long long* seqoff;  // screening pass: prefix of the folded tile sequence
+    int screen_grid;          // screening pass: CTAs
     int num_sms;
     // Obs variant: X^T (p x ldx, FP32) and n
     const float* xt;
@@ -148,6 +151,7 @@ constexpr int kLaunchesLsWindow = 2;
 constexpr int kLaunchesAccept = 4;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
+template <typename T> int screen_plan(int p, int num_sms, std::vector<long long>& seqoff);
 void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s);
 
 // ---------------------------------------------------------------- Obs variant (obs_tc.cu)

@@ -25,6 +25,7 @@
 //                     counts, scan, ordered write) and the stopping rule.
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 
 #include "internal.cuh"
 #include "ptx.cuh"
@@ -198,41 +199,74 @@ __global__ void k_csr_commit(Csr<T> nx, Csr<T> cu, int p, Ctrl* ctrl, int use_co
 // (32 KB, BJ = 32*V) with TMA into a kScreenStages-deep mbarrier ring, and eight
 // consumer warps, each screening eight rows of every tile (lane l holds columns
 // l*V .. l*V+V-1, one 16-byte shared-memory read per row).  This kernel takes the
-// pure-diagonal rows, which need no other row of S: CTA c owns a contiguous
-// share of the (row chunk, column block) items in chunk-major order (equal shares
-// for every SM, whatever p), so DRAM sees long runs of each row.  Rows with off-diagonal entries are screened by
-// k_grad_screen_rows.  Row set-up (CSR bounds, diagonal position and value, the
-// pure-diagonal flag) comes from k_row_info, cached in shared memory.
+// pure-diagonal rows, whose W row is w_ii S_i,: and needs no other row of S.
+// S is symmetric (bitwise: the Gram writes one triangle and mirrors it), so for
+// i < j the element S_ij gives both W_ij = w_ii S_ij (row i pure) and
+// W_ji = w_jj S_ij (row j pure): only the tiles on or above the diagonal are
+// streamed -- half of S -- and an entry of a pair of pure rows is emitted from
+// both sides at once, flagged as paired (no partner gather downstream).  When
+// only one of the two rows is pure, its side is emitted alone and the other row
+// is screened by k_grad_screen_rows.  Row set-up (CSR bounds, diagonal position
+// and value, the pure-diagonal flag) comes from k_row_info, cached in shared
+// memory; the column side reads the diagonal values and the purity bitmask.
+//
+// Work order: the upper-triangle tiles of row chunk c are the column blocks
+// jb >= jbmin(c) = floor(64 c / BJ); chunks are taken in the folded order
+// 0, nc-1, 1, nc-2, ... so that consecutive chunks pair a long tile row with a
+// short one, and CTA g owns a contiguous, equal share of that sequence (the
+// host precomputes its prefix, seqoff).
 constexpr int kScreenTileRows = 64;
 constexpr int kScreenStages = 5;
 constexpr int kScreenMaxChunks = 32;              // row chunks per CTA (shared-memory row cache)
 constexpr int kScreenThreads = kThreads + 32;     // 8 consumer warps + 1 producer warp
 constexpr long long kScreenWaitLimit = 1ll << 26;
 
+// Column side of a tile, loaded with it: the BJ diagonal values and 16 bytes of the
+// purity bitmask around the block.
+template <typename T>
+constexpr int screen_col_bytes() { return 32 * (16 / (int)sizeof(T)) * (int)sizeof(T) + 16; }
+
 template <typename T>
 constexpr int screen_smem_bytes() {
     return kScreenStages * kScreenTileRows * 32 * (16 / (int)sizeof(T)) * (int)sizeof(T)  // tiles
+           + kScreenStages * screen_col_bytes<T>()                                        // column side
            + kScreenMaxChunks * kScreenTileRows * (16 + (int)sizeof(T))                   // row cache
            + 2 * kScreenStages * 8 + 16                                                   // barriers + flag
            + 1024;                                                                        // alignment
 }
 
-// Per row of the iterate: CSR bounds, position of the diagonal (-1 if absent),
-// its value; rows with off-diagonal entries (or no diagonal) are appended to
-// offlist (any order: the screening output is re-sorted per row downstream).
+__host__ __device__ __forceinline__ int screen_seq_chunk(int s, int nc) { return (s & 1) ? nc - 1 - (s >> 1) : (s >> 1); }
+
+// Per row of the iterate: CSR bounds, position of the diagonal (-1 if absent,
+// found by binary search: columns ascend), its value, and the pure-diagonal bit
+// (pmask, one word per 32 rows); rows with off-diagonal entries (or no
+// diagonal) are appended to offlist (any order: the screening output is
+// re-sorted per row downstream).
 template <typename T>
 __global__ void k_row_info(int p, Csr<T> om, int4* __restrict__ rinfo, T* __restrict__ rdv,
-                           int* __restrict__ offlist, Ctrl* __restrict__ ctrl) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x) {
-        const int rb = om.rp[i], re = om.rp[i + 1];
-        int pd = -1;
-        T dv = T(0);
-        for (int q = rb; q < re; ++q)
-            if (om.ci[q] == i) { pd = q; dv = om.cv[q]; break; }
-        const bool pure = (re - rb == 1) && pd >= 0;
-        rinfo[i] = make_int4(rb, re, pd, pure ? 1 : 0);
-        rdv[i] = dv;
-        if (!pure && offlist) offlist[atomicAdd(&ctrl->n_offrows, 1)] = i;
+                           unsigned* __restrict__ pmask, int* __restrict__ offlist, Ctrl* __restrict__ ctrl) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int base = gw * 32; base < p; base += nw * 32) {
+        const int i = base + lane;
+        bool pure = false;
+        if (i < p) {
+            const int rb = om.rp[i], re = om.rp[i + 1];
+            int lo = rb, hi = re;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (om.ci[mid] < i) lo = mid + 1; else hi = mid;
+            }
+            const int pd = (lo < re && om.ci[lo] == i) ? lo : -1;
+            const T dv = pd >= 0 ? om.cv[pd] : T(0);
+            pure = (re - rb == 1) && pd >= 0;
+            rinfo[i] = make_int4(rb, re, pd, pure ? 1 : 0);
+            rdv[i] = dv;
+            if (!pure && offlist) offlist[atomicAdd(&ctrl->n_offrows, 1)] = i;
+        }
+        const unsigned word = __ballot_sync(kFull, pure);
+        if (pmask && lane == 0) pmask[base >> 5] = word;
     }
 }
 
@@ -300,20 +334,45 @@ struct Screen {
     }
 };
 
+// Append the entries a lane found in one tile: n records (row, col word, W, w_ij)
+// staged in registers by the caller; one atomicAdd per warp.
+template <typename T>
+__device__ __forceinline__ int warp_reserve(int n, Ctrl* ctrl, int lane) {
+    const int incl = warp_incl_scan(n, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
+    int base = 0;
+    if (total && lane == 0) base = atomicAdd(&ctrl->em_count, total);
+    base = __shfl_sync(kFull, base, 0);
+    return base + incl - n;
+}
+
+template <typename T>
+__device__ __forceinline__ void put_entry(const Emit<T>& em, int& pos, int i, unsigned colw, T w, T om) {
+    if (pos < em.cap) {
+        em.row[pos] = i;
+        em.col[pos] = (int)colw;
+        em.w[pos] = w;
+        em.om[pos] = om;
+    }
+    ++pos;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kScreenThreads, 1)
-k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S, int64_t ld, int p,
-              const int4* __restrict__ rinfo, const T* __restrict__ rdv, const int* __restrict__ ci,
-              const T* __restrict__ cv, Emit<T> em, Ctrl* __restrict__ ctrl) {
+k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* __restrict__ seqoff,
+              const int4* __restrict__ rinfo, const T* __restrict__ rdv, const unsigned* __restrict__ pmask,
+              Emit<T> em, Ctrl* __restrict__ ctrl) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
     constexpr int BJ = Sc::BJ;
     constexpr int R = kScreenTileRows;
     constexpr int kTileBytes = R * BJ * (int)sizeof(T);
+    constexpr int kColBytes = screen_col_bytes<T>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     T* tiles = reinterpret_cast<T*>(smem);
-    int4* s_info = reinterpret_cast<int4*>(smem + kScreenStages * kTileBytes);
+    uint8_t* cols = smem + kScreenStages * kTileBytes;       // per stage: BJ values, then 4 mask words
+    int4* s_info = reinterpret_cast<int4*>(cols + kScreenStages * kColBytes);
     T* s_dv = reinterpret_cast<T*>(s_info + kScreenMaxChunks * R);
     uint64_t* full = reinterpret_cast<uint64_t*>(s_dv + kScreenMaxChunks * R);
     uint64_t* empty = full + kScreenStages;
@@ -323,14 +382,23 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
     const T lam1 = (T)ctrl->lam1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x;
-    const int nchunks = (p + R - 1) / R;
+    const int nc = (p + R - 1) / R;
     const int nblocks = (p + BJ - 1) / BJ;
-    // this CTA's contiguous share of the (chunk, column block) items, chunk-major
-    const long long total = (long long)nchunks * nblocks;
+    // this CTA's contiguous share of the folded tile sequence
+    const long long total = seqoff[nc];
     const long long lo = total * blockIdx.x / G, hi = total * (blockIdx.x + 1) / G;
     const int items = (int)(hi - lo);
-    const int c_first = (int)(lo / nblocks);
-    const int mine = items > 0 ? (int)((hi - 1) / nblocks) - c_first + 1 : 0;   // <= kScreenMaxChunks
+    int s_first = 0, s_last = 0;
+    if (items > 0) {
+        int a = 0, b = nc - 1;                       // last s with seqoff[s] <= lo
+        while (a < b) { const int m = (a + b + 1) >> 1; if (seqoff[m] <= lo) a = m; else b = m - 1; }
+        s_first = a;
+        a = s_first; b = nc - 1;                     // last s with seqoff[s] <= hi - 1
+        while (a < b) { const int m = (a + b + 1) >> 1; if (seqoff[m] <= hi - 1) a = m; else b = m - 1; }
+        s_last = a;
+    }
+    const int mine = items > 0 ? s_last - s_first + 1 : 0;   // <= kScreenMaxChunks (host-checked grid)
+    const int jb_first = items > 0 ? (int)((long long)screen_seq_chunk(s_first, nc) * R / BJ + (lo - seqoff[s_first])) : 0;
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < kScreenStages; ++st) {
@@ -340,79 +408,153 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, const T* __restrict__ S,
         *abort_flag = 0;
         ptx::mbar_init_fence();
     }
-    // cache the row set-up of this CTA's chunks
+    // cache the row set-up of this CTA's chunks (slot m: the chunk at position s_first + m)
     for (int t = threadIdx.x; t < mine * R; t += blockDim.x) {
-        const int i = (c_first + t / R) * R + (t % R);
+        const int i = screen_seq_chunk(s_first + t / R, nc) * R + (t % R);
         s_info[t] = i < p ? rinfo[i] : make_int4(0, 0, -1, 0);
         s_dv[t] = i < p ? rdv[i] : T(0);
     }
     __syncthreads();
 
     if (warp == kWarps) {
-        // ---------------- producer: one TMA tile per (column block, chunk), block-major
+        // ---------------- producer: one TMA tile per (row chunk, column block) item
         if (lane == 0) {
             ptx::prefetch_tensormap(&smap);
+            int sq = s_first, jb = jb_first, chunk = screen_seq_chunk(s_first, nc);
             for (int t = 0; t < items; ++t) {
                 const int st = t % kScreenStages;
                 const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
                 if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort_flag, kScreenWaitLimit)) break;
-                const long long g = lo + t;
-                const int chunk = (int)(g / nblocks), jb = (int)(g % nblocks);
-                ptx::mbar_expect_tx(&full[st], kTileBytes);
+                ptx::mbar_expect_tx(&full[st], kTileBytes + kColBytes);
                 ptx::tma_load_2d(reinterpret_cast<uint8_t*>(tiles) + st * kTileBytes, &smap, &full[st], jb * BJ,
                                  chunk * R);
+                uint8_t* cdst = cols + st * kColBytes;
+                ptx::bulk_load(cdst, rdv + (size_t)jb * BJ, BJ * (int)sizeof(T), &full[st]);
+                ptx::bulk_load(cdst + BJ * sizeof(T), pmask + (((jb * BJ) >> 5) & ~3), 16, &full[st]);
+                if (++jb == nblocks) {
+                    ++sq;
+                    chunk = sq < nc ? screen_seq_chunk(sq, nc) : 0;
+                    jb = (int)((long long)chunk * R / BJ);
+                }
             }
         }
     } else {
         // ---------------- consumers: warp w screens rows 8w .. 8w+7 of every tile
+        int sq = s_first, jb = jb_first, chunk = screen_seq_chunk(s_first, nc);
         for (int t = 0; t < items; ++t) {
             const int st = t % kScreenStages;
             const uint32_t ph = (uint32_t)(t / kScreenStages) & 1u;
-            if (!ptx::mbar_wait_bounded(&full[st], ph, abort_flag, kScreenWaitLimit)) break;
-            const long long g = lo + t;
-            const int chunk = (int)(g / nblocks), jb = (int)(g % nblocks);
-            const int m = chunk - c_first;
             const int j0 = jb * BJ;
+            const int jl = j0 + lane * V;
+            if (!ptx::mbar_wait_bounded(&full[st], ph, abort_flag, kScreenWaitLimit)) break;
+            // column side, staged with the tile: diagonal values and purity of rows jl..jl+V-1
+            const uint8_t* csrc = cols + st * kColBytes;
+            T cdv[V];
+            if constexpr (V == 4) {
+                const float4 x = *reinterpret_cast<const float4*>(csrc + lane * 16);
+                cdv[0] = x.x; cdv[1] = x.y; cdv[2] = x.z; cdv[3] = x.w;
+            } else {
+                const double2 x = *reinterpret_cast<const double2*>(csrc + lane * 16);
+                cdv[0] = x.x; cdv[1] = x.y;
+            }
+            const unsigned* cw = reinterpret_cast<const unsigned*>(csrc + BJ * sizeof(T));
+            const unsigned cbits = (cw[(jl >> 5) - ((j0 >> 5) & ~3)] >> (jl & 31)) & ((1u << V) - 1u);
+            const int m = sq - s_first;
             const T* tile = tiles + (size_t)st * R * BJ;
-            // eight rows at once: independent shared-memory reads, the diagonal-term
-            // products, and one warp-wide OR of the per-row "something to emit" bits
-            T acc[8][V];
-            int4 info[8];
-            unsigned want = 0;
+            const int r0 = chunk * R + warp * 8;
+            // Filter: off the diagonal band and the ragged edges, an element can emit only
+            // if fl(max(|w_ii|, |w_jj|) |S_ij|) > lambda1 over the pure sides (rounding is
+            // monotone, so this is the larger of the two products); warps with a hit, and
+            // the tiles on the diagonal or at p, take the exact path below.
+            const bool edge = (j0 < chunk * R + R) || (j0 + BJ > p) || (chunk * R + R > p);
+            bool hit = edge;
+            if (!edge) {
+                T cm[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) cm[v] = ((cbits >> v) & 1u) ? fabs(cdv[v]) : T(0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const T rm = s_info[m * R + warp * 8 + q].w ? fabs(s_dv[m * R + warp * 8 + q]) : T(0);
+                    T sv[V];
+                    if constexpr (V == 4) {
+                        const float4 x = *reinterpret_cast<const float4*>(tile + (warp * 8 + q) * BJ + lane * V);
+                        sv[0] = x.x; sv[1] = x.y; sv[2] = x.z; sv[3] = x.w;
+                    } else {
+                        const double2 x = *reinterpret_cast<const double2*>(tile + (warp * 8 + q) * BJ + lane * V);
+                        sv[0] = x.x; sv[1] = x.y;
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; ++v) hit |= !(fabs(mulT(fmax(rm, cm[v]), sv[v])) <= lam1);
+                }
+            }
+            if (__any_sync(kFull, hit)) {
+            // rows r0..r0+7 x columns jl..jl+V-1: count the records, then write them
+            T av[8][V], bv[8][V];
+            unsigned ea = 0, eb = 0;     // bit (q*V + v): emit row side / column side
+            unsigned pairbits = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int r = warp * 8 + q;
-                info[q] = s_info[m * R + r];
-                const T dv = s_dv[m * R + r];
+                const int r = r0 + q;
+                const int4 info = s_info[m * R + warp * 8 + q];
+                const T dv = s_dv[m * R + warp * 8 + q];
+                const bool rpure = info.w != 0;
                 T sv[V];
                 if constexpr (V == 4) {
-                    const float4 x = *reinterpret_cast<const float4*>(tile + r * BJ + lane * V);
+                    const float4 x = *reinterpret_cast<const float4*>(tile + (warp * 8 + q) * BJ + lane * V);
                     sv[0] = x.x; sv[1] = x.y; sv[2] = x.z; sv[3] = x.w;
                 } else {
-                    const double2 x = *reinterpret_cast<const double2*>(tile + r * BJ + lane * V);
+                    const double2 x = *reinterpret_cast<const double2*>(tile + (warp * 8 + q) * BJ + lane * V);
                     sv[0] = x.x; sv[1] = x.y;
                 }
-                bool big = false;
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    acc[q][v] = mulT(dv, sv[v]);
-                    big |= !(fabs(acc[q][v]) <= lam1);
+                    const int j = jl + v;
+                    const bool cpure = (cbits >> v) & 1u;
+                    av[q][v] = mulT(dv, sv[v]);
+                    bv[q][v] = mulT(cdv[v], sv[v]);
+                    const unsigned bit = 1u << (q * V + v);
+                    if (r < p && j < p && j >= r) {
+                        if (j == r) {
+                            if (rpure) ea |= bit;                       // the diagonal: support
+                        } else {
+                            const bool ba = rpure && !(fabs(av[q][v]) <= lam1);
+                            const bool bb = cpure && !(fabs(bv[q][v]) <= lam1);
+                            if (rpure && cpure) {
+                                if (ba || bb) { ea |= bit; eb |= bit; pairbits |= bit; }
+                            } else {
+                                if (ba) ea |= bit;
+                                if (bb) eb |= bit;
+                            }
+                        }
+                    }
                 }
-                want |= (big ? 1u : 0u) << q;
             }
-            want = __reduce_or_sync(kFull, want);
+            const int n = __popc(ea) + __popc(eb);
+            if (__any_sync(kFull, n != 0)) {
+                int pos = warp_reserve<T>(n, ctrl, lane);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int i = chunk * R + warp * 8 + q;
-                // pure-diagonal rows only (the others belong to k_grad_screen_rows); the
-                // diagonal's own column block always emits (support)
-                const bool diag_here = (i >= j0 && i < j0 + BJ);
-                if (i < p && info[q].w && (((want >> q) & 1u) || diag_here))
-                    Sc::emit(i, acc[q][0], acc[q][V > 1 ? 1 : 0], acc[q][V > 2 ? 2 : 0], acc[q][V > 3 ? 3 : 0], info[q].x,
-                             info[q].y, j0, p, ci, cv, lam1, em, ctrl, lane);
+                for (int q = 0; q < 8; ++q) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const unsigned bit = 1u << (q * V + v);
+                        const int r = r0 + q, j = jl + v;
+                        const unsigned pf = (pairbits & bit) ? 0x40000000u : 0u;
+                        if (ea & bit) {
+                            if (j == r) put_entry(em, pos, r, (unsigned)j | 0x80000000u, av[q][v], s_dv[m * R + warp * 8 + q]);
+                            else put_entry(em, pos, r, (unsigned)j | pf, av[q][v], T(0));
+                        }
+                        if (eb & bit) put_entry(em, pos, j, (unsigned)r | pf, bv[q][v], T(0));
+                    }
+                }
+            }
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&empty[st]);
+            if (++jb == nblocks) {
+                ++sq;
+                chunk = sq < nc ? screen_seq_chunk(sq, nc) : 0;
+                jb = (int)((long long)chunk * R / BJ);
+            }
         }
     }
     __syncthreads();
@@ -652,13 +794,38 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* 
     __syncthreads();
     int run = x - s + (warp ? wsum[warp - 1] : 0);
     long long urun = ux - us + (warp ? usum[warp - 1] : 0);
-    for (int j = b0; j < b1; ++j) {
-        const int v = in[j];
-        out[j] = run;
-        run += v;
-        if (uoff) {
-            uoff[j] = urun;
-            urun += ls_units(v);
+    // second pass over the run, 16 bytes at a time (the loads hit L1/L2)
+#pragma unroll 4
+    for (int j = b0; j < b1; j += 4) {
+        int v[4];
+        const bool full = j + 4 <= b1;
+        if (full) {
+            const int4 x4 = *reinterpret_cast<const int4*>(in + j);
+            v[0] = x4.x; v[1] = x4.y; v[2] = x4.z; v[3] = x4.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = j + q < b1 ? in[j + q] : 0;
+        }
+        int o[4];
+        long long uo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            o[q] = run;
+            run += v[q];
+            uo[q] = urun;
+            if (uoff) urun += ls_units(v[q]);
+        }
+        if (full) {
+            *reinterpret_cast<int4*>(out + j) = make_int4(o[0], o[1], o[2], o[3]);
+            if (uoff) {
+                *reinterpret_cast<longlong2*>(uoff + j) = make_longlong2(uo[0], uo[1]);
+                *reinterpret_cast<longlong2*>(uoff + j + 2) = make_longlong2(uo[2], uo[3]);
+            }
+        } else {
+            for (int q = 0; q < 4 && j + q < b1; ++q) {
+                out[j + q] = o[q];
+                if (uoff) uoff[j + q] = uo[q];
+            }
         }
     }
     if (threadIdx.x == 1023) {
@@ -1417,31 +1584,51 @@ void launch_iter_begin(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s)
     k_iter_begin<T><<<64, 256, 0, s>>>(b.bk, b.p, b.ctrl, lc.use, lc.ls);
 }
 
-// One CTA per SM; more when the row-cache bound (kScreenMaxChunks chunks per CTA,
-// a share spans at most items/nblocks + 2 chunks) needs it.
+// Prefix of the folded tile sequence of the screening pass (seqoff, nc+1 entries)
+// and its grid: one CTA per SM, more while some CTA's share would span more row
+// chunks than its shared-memory row cache holds.
 template <typename T>
-int screen_grid(int p, int num_sms) {
+int screen_plan(int p, int num_sms, std::vector<long long>& seqoff) {
+    constexpr int R = kScreenTileRows;
     constexpr int BJ = 32 * (16 / (int)sizeof(T));
-    const long long nchunks = (p + kScreenTileRows - 1) / kScreenTileRows;
-    const long long nblocks = (p + BJ - 1) / BJ;
-    const long long need = (nchunks + (kScreenMaxChunks - 2) - 1) / (kScreenMaxChunks - 2);
-    return (int)std::max(1LL, std::min(nchunks * nblocks, std::max((long long)num_sms, need)));
+    const int nc = (p + R - 1) / R;
+    const int nb = (p + BJ - 1) / BJ;
+    seqoff.assign(nc + 1, 0);
+    for (int q = 0; q < nc; ++q) {
+        const int c = screen_seq_chunk(q, nc);
+        seqoff[q + 1] = seqoff[q] + (nb - (int)((long long)c * R / BJ));
+    }
+    const long long total = seqoff[nc];
+    auto last_le = [&](long long x) {
+        return (int)(std::upper_bound(seqoff.begin(), seqoff.begin() + nc, x) - seqoff.begin()) - 1;
+    };
+    long long G = std::max<long long>(1, std::min<long long>(total, num_sms));
+    for (;;) {
+        int span = 0;
+        for (long long g = 0; g < G; ++g) {
+            const long long lo = total * g / G, hi = total * (g + 1) / G;
+            if (hi > lo) span = std::max(span, last_le(hi - 1) - last_le(lo) + 1);
+        }
+        if (span <= kScreenMaxChunks || G >= total) break;
+        G = std::min<long long>(total, G + num_sms);
+    }
+    return (int)G;
 }
 
 template <typename T>
 void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     constexpr int smem = screen_smem_bytes<T>();
     set_smem_once((const void*)k_grad_screen<T>, smem, sizeof(T) == 8 ? kSmemSlotScreenD : kSmemSlotScreenF);
-    k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.offlist, b.ctrl);
-    k_grad_screen<T><<<screen_grid<T>(b.p, b.num_sms), kScreenThreads, smem, s>>>(
-        *b.smap, b.S, b.ld, b.p, b.rinfo, b.rdv, b.cur.ci, b.cur.cv, b.em, b.ctrl);
+    k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.pmask, b.offlist, b.ctrl);
+    k_grad_screen<T><<<b.screen_grid, kScreenThreads, smem, s>>>(*b.smap, b.p, b.seqoff, b.rinfo, b.rdv, b.pmask,
+                                                                 b.em, b.ctrl);
     k_grad_screen_rows<T><<<b.num_sms * 2, kThreads, 0, s>>>(b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci,
                                                             b.cur.cv, b.em, b.ctrl);
 }
 
 template <typename T>
 void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s) {
-    k_row_info<T><<<(p + 255) / 256, 256, 0, s>>>(p, om, rinfo, rdv, nullptr, nullptr);
+    k_row_info<T><<<(p + 255) / 256, 256, 0, s>>>(p, om, rinfo, rdv, nullptr, nullptr, nullptr);
 }
 
 template <typename T>
@@ -1555,6 +1742,7 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
     template void launch_accept<T>(const IterBufs<T>&, cudaStream_t);                              \
     template void launch_set_identity<T>(Csr<T>, int, cudaStream_t);                               \
     template void launch_row_info<T>(int, Csr<T>, int4*, T*, cudaStream_t);                        \
+    template int screen_plan<T>(int, int, std::vector<long long>&);                                 \
     template void launch_csr_export<T>(const int*, const int*, const T*, int, int, int64_t*, int32_t*, \
                                        void*, int, cudaStream_t);
 
