@@ -221,6 +221,8 @@ def main(argv=None):
                          "time then comes from device timestamps instead of CUDA events)")
     ap.add_argument("--compare-loops", type=int, default=1, choices=[0, 1],
                     help="also time one solve with the other loop driver")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="pick the launch shapes with the library's autotuner before the warm-up")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -248,6 +250,14 @@ def main(argv=None):
     xdt = hpc.BF16 if w.x_dtype == "bf16" else hpc.F32
     solver = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=prec, eps=w.eps,
                         max_iter=100000, device_loop=args.device_loop)
+
+    tuning, tune_trials = solver.get_tuning(), []
+    if args.autotune:
+        # the Gram's band (reloads X), then the iteration knobs from a mid-solve iterate
+        _, tr0 = solver.autotune(X, iters=0)
+        solver.iterate(8)
+        tuning, tr1 = solver.autotune(None, iters=3)
+        tune_trials = tr0 + tr1
 
     def step(Xsrc):
         solver.load_x(Xsrc)
@@ -336,6 +346,7 @@ def main(argv=None):
     if args.compare_loops and rank == 0:
         alt = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=prec, eps=w.eps,
                          max_iter=100000, device_loop=1 - args.device_loop)
+        alt.set_tuning(**tuning)
         alt.load_x(X)
         alt.solve()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -353,6 +364,7 @@ def main(argv=None):
     if not args.no_plain and solver.precision_used() != hpc.PREC_FP32 and rank == 0:
         ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=hpc.PREC_FP32, eps=w.eps,
                         max_iter=100000, device_loop=args.device_loop)
+        ps.set_tuning(**tuning)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -392,6 +404,7 @@ def main(argv=None):
                        "eps": w.eps, "x_dtype": w.x_dtype, "s_dtype": "f32",
                        "gram_precision": solver.precision_name(), "parallelism": f"replicas x{ws}",
                        "loop": "device (one CUDA graph per solve)" if args.device_loop else "host-driven",
+                       "tuning": tuning, "autotuned": bool(args.autotune),
                        "l2": "inputs > L2 (X 4.3 GB, S 17.2 GB); no flush"},
             "iterations_per_step": [r["iterations"] for r in recs],
             "ls_trials_per_step": [r["ls_trials"] for r in recs],
@@ -402,6 +415,7 @@ def main(argv=None):
             "final_nnz": recs[-1]["nnz"], "final_F": recs[-1]["F"],
             "roofline": roof, "roofline_kernels": [roof_gram, roof_scr], "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
             "cpu_baseline": cpu, "plain_fp32": plain, "other_loop": other,
+            "autotune_trials": [(t["knob"], t["value"], round(t["ms"], 4)) for t in tune_trials],
         }
         print(json.dumps(line), flush=True)
     solver.close()

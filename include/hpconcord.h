@@ -324,6 +324,55 @@ int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dt
 int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* S, int64_t lds,
                      int precision, void* cuda_stream);
 
+/* ---------------------------------------------------------------- tuning */
+/* Launch shapes of a handle's kernels.  None of them changes a result bit: the
+ * Gram's tiles are summed in the same order whatever their schedule, and the
+ * iterations run the same kernels on the same data.  The paper tunes its
+ * replication factors and grid shapes per machine (Section 4); these are the
+ * single-GPU counterparts. */
+typedef struct {
+    int32_t gram_band;         /* row blocks of 128 per band of the tensor-core Gram's
+                                  tile order, 1..256 (16): sets which X panels the
+                                  tiles running together share in L2               */
+    int32_t ls_window;         /* tau values per line-search launch: 1, 2, 4, 8, 16 */
+    int32_t ls_blocks_per_sm;  /* resident blocks per SM of the line-search
+                                  evaluation, 0 = as many as fit (2)               */
+    int32_t rows_ctas_per_sm;  /* CTAs per SM of the off-diagonal row kernel, 1..4 (2) */
+} hpc_tuning;
+
+/* Read / replace a handle's tuning.  HPC_ERR_ARG for a value out of range. */
+int hpc_get_tuning(hpc_handle h, hpc_tuning* t);
+int hpc_set_tuning(hpc_handle h, const hpc_tuning* t);
+
+#define HPC_TUNE_MAX_TRIALS 48
+typedef struct {
+    int32_t knob;              /* 0 gram_band, 1 ls_window, 2 ls_blocks_per_sm,
+                                  3 rows_ctas_per_sm                                */
+    int32_t value;
+    double  ms;                /* Gram: one launch; the others: one iteration        */
+} hpc_tune_trial;
+
+typedef struct {
+    int32_t ntrials;
+    int32_t pad_;
+    hpc_tune_trial trials[HPC_TUNE_MAX_TRIALS];
+} hpc_tune_report;
+
+/* The autotuner: times the candidate values of each knob on the handle's own
+ * problem and keeps the fastest, one knob after another.
+ *  - If X != NULL (same conventions as hpc_load_x) the Gram is timed once per
+ *    gram_band candidate; S is rewritten with identical values.
+ *  - The iteration knobs are timed over `iters` outer iterations (>= 1) each,
+ *    every trial starting from the handle's current iterate, which is restored
+ *    afterwards: the call leaves the estimate unchanged.  Start from a
+ *    representative iterate (for example after a few hpc_iterate calls) for
+ *    timings that reflect a solve.
+ * The chosen tuning is applied to the handle and written to *best (nullable);
+ * every trial is listed in *report (nullable).  Times are CUDA events on the
+ * handle's stream.  Errors as hpc_iterate / hpc_load_x. */
+int hpc_autotune(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host, int64_t iters, hpc_tuning* best,
+                 hpc_tune_report* report);
+
 #ifdef __cplusplus
 }
 #endif

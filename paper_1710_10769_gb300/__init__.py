@@ -70,6 +70,29 @@ class HypergradInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("gram_band", C.c_int32), ("ls_window", C.c_int32), ("ls_blocks_per_sm", C.c_int32),
+                ("rows_ctas_per_sm", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TUNE_MAX_TRIALS = 48
+TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm")
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("knob", C.c_int32), ("value", C.c_int32), ("ms", C.c_double)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("ntrials", C.c_int32), ("pad_", C.c_int32), ("trials", TuneTrial * TUNE_MAX_TRIALS)]
+
+    def as_list(self):
+        return [{"knob": TUNE_KNOBS[t.knob], "value": t.value, "ms": t.ms} for t in self.trials[: self.ntrials]]
+
+
 class HpcError(RuntimeError):
     def __init__(self, status, where):
         lib = load()
@@ -104,6 +127,9 @@ _SIGS = {
     "hpc_destroy": (C.c_int, [_P]),
     "hpc_gram": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "hpc_gram_noalloc": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int64, C.c_int, _P]),
+    "hpc_get_tuning": (C.c_int, [_P, _P]),
+    "hpc_set_tuning": (C.c_int, [_P, _P]),
+    "hpc_autotune": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _P, _P]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -247,6 +273,35 @@ class Solver:
         st = self._lib.hpc_iterate(self._h, int(k), C.byref(self.stats))
         _check(st, "hpc_iterate")
         return self.stats
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(self._lib.hpc_get_tuning(self._h, C.byref(t)), "hpc_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(self._lib.hpc_get_tuning(self._h, C.byref(t)), "hpc_get_tuning")
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(self._lib.hpc_set_tuning(self._h, C.byref(t)), "hpc_set_tuning")
+
+    def autotune(self, X=None, iters=5):
+        """hpc_autotune: time the launch-shape candidates on this problem and keep the
+        fastest.  With X the Gram's band is tuned too (the data is reloaded and the
+        iterate returns to the identity, as in load_x).  Returns (tuning, trials)."""
+        t = Tuning()
+        rep = TuneReport()
+        if X is None:
+            ptr, xdt, host = None, F32, 0
+        elif isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X)
+            ptr, xdt, host = X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1
+        else:
+            assert X.is_contiguous() and X.dim() == 2
+            ptr, xdt, host = C.c_void_p(X.data_ptr()), _dtype_code(X), 0 if X.is_cuda else 1
+        _check(self._lib.hpc_autotune(self._h, ptr, xdt, host, int(iters), C.byref(t), C.byref(rep)), "hpc_autotune")
+        return t.as_dict(), rep.as_list()
 
     def info(self) -> Info:
         inf = Info()

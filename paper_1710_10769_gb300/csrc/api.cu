@@ -109,6 +109,8 @@ struct hpc_ctx {
     cudaEvent_t ev_scr0 = nullptr, ev_scr1 = nullptr;
     int64_t regrows = 0;
     double ms_gram = 0.0;
+    // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
+    hpc_tuning tune{16, 8, 0, 2};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -226,7 +228,9 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.lam2 = (T)h->lam2;
     b.eps = h->opt.eps;
     b.max_halvings = h->opt.max_halvings;
-    b.ls_window = h->opt.ls_window;
+    b.ls_window = h->tune.ls_window;
+    b.ls_blocks_per_sm = h->tune.ls_blocks_per_sm;
+    b.rows_ctas_per_sm = h->tune.rows_ctas_per_sm;
     b.smap = &h->smap;
     b.rinfo = h->rinfo;
     b.offlist = h->offlist;
@@ -304,7 +308,7 @@ int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
         CUDA_TRY(cudaGetLastError());
         int launches = hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesCandidates;
         bool accepted = false, overflow = false;
-        for (int hb = 0; hb <= h->opt.max_halvings; hb += h->opt.ls_window) {
+        for (int hb = 0; hb <= h->opt.max_halvings; hb += h->tune.ls_window) {
             if constexpr (std::is_same<T, float>::value) {
                 if (h->variant == HPC_OBS) hpc::launch_ls_window_obs(b, host_loop, h->stream);
                 else hpc::launch_ls_window<T>(b, host_loop, h->stream);
@@ -648,7 +652,7 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
             h->gram_scratch_bytes = need;
         }
         e = hpc::gram_tc(Xd, xdt, h->n, h->p, static_cast<float*>(h->S), h->ld, prec, h->gram_scratch,
-                         h->gram_scratch_bytes, h->stream, &launches);
+                         h->gram_scratch_bytes, h->stream, &launches, h->tune.gram_band);
         if (e == cudaErrorNotSupported) {
             if (tmp) cudaFree(tmp);
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
@@ -772,6 +776,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     if (!h) return HPC_ERR_OOM;
     h->n = n; h->p = p; h->variant = variant; h->vdt = o.value_dtype; h->precision = prec;
     h->lam1 = lambda1; h->lam2 = lambda2; h->opt = o;
+    h->tune.ls_window = o.ls_window;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     h->ld = (p + 127) / 128 * 128;
 
@@ -1297,9 +1302,166 @@ int hypergrad_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double cg_t
     return done == 1 ? HPC_OK : HPC_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------- autotuner
+bool tuning_ok(const hpc_tuning& t) {
+    const int w = t.ls_window;
+    return t.gram_band >= 1 && t.gram_band <= 256 && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16) &&
+           t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4;
+}
+
+void apply_tuning(hpc_ctx* h, const hpc_tuning& t) {
+    h->tune = t;
+    h->epoch += 1;          // the device-loop graph captured the old launch shapes
+}
+
+// A copy of the current iterate (CSR) that trials restore before they run.
+struct IterateCopy {
+    int* rp = nullptr;
+    int* ci = nullptr;
+    void* cv = nullptr;
+    int64_t nnz = 0;
+    ~IterateCopy() {
+        if (rp) cudaFree(rp);
+        if (ci) cudaFree(ci);
+        if (cv) cudaFree(cv);
+    }
+};
+
+int save_iterate(hpc_ctx* h, IterateCopy& c) {
+    const size_t vs = dtype_size(h->vdt);
+    c.nnz = h->nnz;
+    CUDA_TRY(cudaMalloc(&c.rp, (h->p + 1) * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&c.ci, std::max<int64_t>(c.nnz, 1) * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&c.cv, std::max<int64_t>(c.nnz, 1) * vs));
+    CUDA_TRY(cudaMemcpyAsync(c.rp, h->rp[h->cur], (h->p + 1) * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(c.ci, h->ci[h->cur], c.nnz * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(c.cv, h->cv[h->cur], c.nnz * vs, cudaMemcpyDeviceToDevice, h->stream));
+    return HPC_OK;
+}
+
+int restore_iterate(hpc_ctx* h, const IterateCopy& c) {
+    const size_t vs = dtype_size(h->vdt);
+    if (c.nnz > h->csr_cap) STATUS_TRY(grow_csr(h, c.nnz));
+    CUDA_TRY(cudaMemcpyAsync(h->rp[h->cur], c.rp, (h->p + 1) * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->ci[h->cur], c.ci, c.nnz * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->cv[h->cur], c.cv, c.nnz * vs, cudaMemcpyDeviceToDevice, h->stream));
+    h->nnz = c.nnz;
+    return HPC_OK;
+}
+
+void add_trial(hpc_tune_report* r, int knob, int value, double ms) {
+    if (!r || r->ntrials >= HPC_TUNE_MAX_TRIALS) return;
+    r->trials[r->ntrials].knob = knob;
+    r->trials[r->ntrials].value = value;
+    r->trials[r->ntrials].ms = ms;
+    r->ntrials += 1;
+}
+
+// Milliseconds per iteration of `iters` iterations from the saved iterate under
+// tuning t (one untimed iteration first, which also captures the graph).
+template <typename T>
+int time_iterations(hpc_ctx* h, const IterateCopy& c, const hpc_tuning& t, int64_t iters, double* ms) {
+    apply_tuning(h, t);
+    hpc_stats st{};
+    STATUS_TRY(restore_iterate(h, c));
+    int r = run_iterations<T>(h, 1, false, &st);
+    if (r != HPC_OK) return r;
+    STATUS_TRY(restore_iterate(h, c));
+    r = run_iterations<T>(h, iters, false, &st);
+    if (r != HPC_OK) return r;
+    *ms = st.ms_total / (double)std::max<int64_t>(st.iterations, 1);
+    return HPC_OK;
+}
+
+template <typename T>
+int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, hpc_tuning* best,
+               hpc_tune_report* rep) {
+    const int timing0 = h->opt.timing;
+    h->opt.timing = 1;
+    hpc_tuning t = h->tune;
+    int status = HPC_OK;
+    // 1. the Gram's tile-order band (tensor-core Gram only)
+    const bool tc_gram = h->variant == HPC_COV && (h->precision == HPC_PREC_BF16X3 || h->precision == HPC_PREC_TF32);
+    if (X && tc_gram) {
+        const int nbi = (int)((h->p + 255) / 256 * 256 / 128);
+        const int cands[] = {2, 4, 8, 16, 32, 64};
+        double best_ms = 1e300;
+        int best_band = t.gram_band;
+        for (int b : cands) {
+            if (b > nbi && b != cands[0]) continue;
+            hpc_tuning u = t;
+            u.gram_band = b;
+            apply_tuning(h, u);
+            double ms = 1e300;
+            for (int rep_i = 0; rep_i < 2 && status == HPC_OK; ++rep_i) {
+                status = load_x(h, X, xdt, on_host);
+                ms = std::min(ms, h->ms_gram);
+            }
+            if (status != HPC_OK) break;
+            add_trial(rep, 0, b, ms);
+            if (ms < best_ms) { best_ms = ms; best_band = b; }
+        }
+        t.gram_band = best_band;
+        apply_tuning(h, t);
+    } else if (X) {
+        status = load_x(h, X, xdt, on_host);
+    }
+    // 2. iteration knobs, one after another, from the current iterate
+    if (status == HPC_OK && iters > 0) {
+        IterateCopy c;
+        status = save_iterate(h, c);
+        struct Knob { int id; std::vector<int> vals; };
+        const Knob knobs[] = {{1, {2, 4, 8, 16}}, {3, {1, 2, 3, 4}}, {2, {1, 2}}};
+        for (const Knob& k : knobs) {
+            if (status != HPC_OK) break;
+            if (k.id == 3 && h->variant == HPC_OBS) continue;       // Obs has no row kernel
+            double best_ms = 1e300;
+            int best_v = 0;
+            for (int v : k.vals) {
+                hpc_tuning u = t;
+                if (k.id == 1) u.ls_window = v; else if (k.id == 2) u.ls_blocks_per_sm = v; else u.rows_ctas_per_sm = v;
+                double ms = 0;
+                status = time_iterations<T>(h, c, u, iters, &ms);
+                if (status != HPC_OK) break;
+                add_trial(rep, k.id, v, ms);
+                if (ms < best_ms) { best_ms = ms; best_v = v; }
+            }
+            if (status != HPC_OK) break;
+            if (k.id == 1) t.ls_window = best_v; else if (k.id == 2) t.ls_blocks_per_sm = best_v; else t.rows_ctas_per_sm = best_v;
+        }
+        if (status == HPC_OK) status = restore_iterate(h, c);
+        if (status == HPC_OK) status = cudaStreamSynchronize(h->stream) == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+    }
+    apply_tuning(h, t);
+    h->opt.timing = timing0;
+    if (best) *best = t;
+    return status;
+}
+
 }  // namespace
 
 extern "C" {
+
+int hpc_get_tuning(hpc_handle h, hpc_tuning* t) {
+    if (!h || !t) return HPC_ERR_ARG;
+    *t = h->tune;
+    return HPC_OK;
+}
+
+int hpc_set_tuning(hpc_handle h, const hpc_tuning* t) {
+    if (!h || !t || !tuning_ok(*t)) return HPC_ERR_ARG;
+    apply_tuning(h, *t);
+    return HPC_OK;
+}
+
+int hpc_autotune(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host, int64_t iters, hpc_tuning* best,
+                 hpc_tune_report* report) {
+    if (!h || iters < 0 || (X && !valid_dtype(xdt))) return HPC_ERR_ARG;
+    if (!X && !h->loaded) return HPC_ERR_ARG;
+    if (report) std::memset(report, 0, sizeof *report);
+    return h->vdt == HPC_F64 ? autotune_t<double>(h, X, xdt, x_on_host, iters, best, report)
+                             : autotune_t<float>(h, X, xdt, x_on_host, iters, best, report);
+}
 
 int hpc_smooth_value(hpc_handle h, double* f) {
     if (!h || !h->loaded || !f) return HPC_ERR_ARG;

@@ -400,14 +400,15 @@ Geometry geometry(int xdt, int64_t n, int64_t p, int precision) {
     return g;
 }
 
-// Upper-triangle tiles (128 bi <= 256 bj + 255) in bands of kBand row blocks;
-// within a band, columns left to right, rows top to bottom.
-std::vector<int2> tile_order(int64_t p_pad) {
+// Upper-triangle tiles (128 bi <= 256 bj + 255) in bands of `band` row blocks;
+// within a band, columns left to right, rows top to bottom.  The band sets
+// which X panels the concurrently running tiles share in L2 (a tuning knob).
+std::vector<int2> tile_order(int64_t p_pad, int band) {
     const int64_t nbi = p_pad / kBM, nbj = p_pad / kBN;
     std::vector<int2> t;
-    for (int64_t b0 = 0; b0 < nbi; b0 += kBand)
+    for (int64_t b0 = 0; b0 < nbi; b0 += band)
         for (int64_t bj = 0; bj < nbj; ++bj)
-            for (int64_t bi = b0; bi < std::min<int64_t>(b0 + kBand, nbi); ++bi)
+            for (int64_t bi = b0; bi < std::min<int64_t>(b0 + band, nbi); ++bi)
                 if (bi * kBM <= bj * kBN + kBN - 1) t.push_back(make_int2((int)bi, (int)bj));
     return t;
 }
@@ -463,7 +464,8 @@ size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision) {
 }
 
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
-                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches) {
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band) {
+    if (band <= 0) band = kBand;
     if (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32) return cudaErrorInvalidValue;
     if (xdt == HPC_F64) return cudaErrorNotSupported;
     if (!encode_fn()) return cudaErrorNotSupported;
@@ -475,7 +477,7 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     void* hi = base;
     void* lo = g.pieces > 1 ? base + g.panel_bytes : nullptr;
     int2* tiles = reinterpret_cast<int2*>(base + g.pieces * g.panel_bytes);
-    const std::vector<int2> order = tile_order(g.p_pad);
+    const std::vector<int2> order = tile_order(g.p_pad, band);
     cudaError_t e = cudaMemcpyAsync(tiles, order.data(), order.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     // the host vector must outlive the copy

@@ -116,6 +116,8 @@ struct IterBufs {
     unsigned* pmask;          // ld/32: pure-diagonal bit of each row
     const long long* seqoff;  // screening pass: prefix of the folded tile sequence
     int screen_grid;          // screening pass: CTAs
+    int ls_blocks_per_sm;     // line-search evaluation: resident blocks per SM (0 = occupancy)
+    int rows_ctas_per_sm;     // off-diagonal row kernel: CTAs per SM
     int num_sms;
     // Obs variant: X^T (p x ldx, FP32) and n
     const float* xt;
@@ -200,8 +202,9 @@ void launch_reduce_parts(const double* part, int nb, double* out, cudaStream_t s
 // S = X^T X / n into S (p x lds).  Returns a CUDA error code.
 cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int sdt, int64_t lds,
                       cudaStream_t s, int* launches);
+// band: row blocks per band of the tile order (<= 0: the default, 16).
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
-                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches);
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0);
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();

@@ -1622,8 +1622,8 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.pmask, b.offlist, b.ctrl);
     k_grad_screen<T><<<b.screen_grid, kScreenThreads, smem, s>>>(*b.smap, b.p, b.seqoff, b.rinfo, b.rdv, b.pmask,
                                                                  b.em, b.ctrl);
-    k_grad_screen_rows<T><<<b.num_sms * 2, kThreads, 0, s>>>(b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci,
-                                                            b.cur.cv, b.em, b.ctrl);
+    k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
+        b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.em, b.ctrl);
 }
 
 template <typename T>
@@ -1654,7 +1654,8 @@ static int ls_eval_grid(const IterBufs<T>& b) {
             v = 1;
         per_sm = v;
     }
-    return std::max(1, std::min(b.nblk, per_sm * b.num_sms));
+    const int want = b.ls_blocks_per_sm > 0 ? std::min(b.ls_blocks_per_sm, per_sm) : per_sm;
+    return std::max(1, std::min(b.nblk, want * b.num_sms));
 }
 
 template <typename T, int M>

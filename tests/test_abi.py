@@ -48,3 +48,10 @@ def test_build_is_sm103a_only():
     from paper_1710_10769_gb300 import _build
 
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layouts_match_the_header(lib):
+    """ctypes mirrors of the header's structs: sizes from the header's field list."""
+    assert ctypes.sizeof(lib.Options) == 64
+    assert ctypes.sizeof(lib.Tuning) == 16
+    assert ctypes.sizeof(lib.TuneReport) == 8 + lib.TUNE_MAX_TRIALS * 16
