@@ -191,14 +191,19 @@ typedef struct {
 int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
                    int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout);
 
-/* Solve `count` independent problems (handles created on distinct CUDA streams)
- * concurrently: a pool of at most `threads` host threads (0 = one per handle)
- * drives the handles' solves, so their kernels overlap on the GPU and their
- * host synchronisation points overlap in time.  stats (host, count entries,
- * may be NULL) receives each handle's hpc_solve statistics.  Returns HPC_OK if
- * every solve returned HPC_OK, HPC_NOT_CONVERGED if any stopped at max_iter, and
- * otherwise the first error (by handle index); per-handle statuses are in
- * stats[t].status.  Handles sharing a stream are solved one after another. */
+/* Solve `count` independent problems (handles of the same device) concurrently.
+ * When every handle uses the device loop (hpc_options.device_loop, the default)
+ * the whole batch is ONE CUDA-graph launch: each handle's iteration loop is an
+ * independent branch of the graph, launched on handles[0]'s stream after it
+ * waits for the other handles' streams; `threads` is unused.  A handle whose
+ * candidate buffers overflow grows them and finishes alone.  Otherwise a pool of
+ * at most `threads` host threads (0 = one per stream) drives the handles' solves,
+ * so their kernels overlap on the GPU; handles sharing a stream are then solved
+ * one after another.  stats (host, count entries, may be NULL) receives each
+ * handle's hpc_solve statistics (ms_total: the batch launch's device time).
+ * Returns HPC_OK if every solve returned HPC_OK, HPC_NOT_CONVERGED if any stopped
+ * at max_iter, and otherwise the first error (by handle index); per-handle
+ * statuses are in stats[t].status. */
 int hpc_solve_batch(hpc_handle* handles, int count, int threads, hpc_stats* stats);
 
 /* Read m entries S_{rows[t], cols[t]} of the Cov sample covariance into out

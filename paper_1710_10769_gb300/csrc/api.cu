@@ -423,12 +423,12 @@ int end_capture(cudaStream_t cs, cudaGraph_t g, int status) {
     return HPC_OK;
 }
 
-int add_while(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHandle* hnd, cudaGraphNode_t* node,
+// A WHILE node of graph g on condition handle hnd (created for g), after dep if any.
+int add_while(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHandle hnd, cudaGraphNode_t* node,
               cudaGraph_t* body) {
-    CUDA_TRY(cudaGraphConditionalHandleCreate(hnd, g, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams np{};
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = *hnd;
+    np.conditional.handle = hnd;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     CUDA_TRY(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
@@ -461,20 +461,26 @@ void capture_window(hpc_ctx* h, const hpc::IterBufs<T>& b, const hpc::LoopCond& 
 //   }
 // k_iter_begin arms the line-search loop, k_ls_decide ends it, and the commit
 // kernel continues or ends the iteration loop.
+// Capture the iteration loop as a WHILE node of graph g (after dep, if any) on
+// the handle lc.iter, which the caller created for g:
+//   WHILE (iteration condition) {
+//       begin, [stamp], screening pass, [stamp], candidates, gradient
+//       WHILE (line-search condition) { window evaluation, decision }
+//       compaction, stopping rule, commit of the accepted iterate
+//   }
+// k_iter_begin arms the line-search loop, k_ls_decide ends it, and the commit
+// kernel continues or ends the iteration loop.
 template <typename T>
-int build_graph(hpc_ctx* h) {
-    destroy_graph(h);
-    if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+int capture_iteration_loop(hpc_ctx* h, cudaGraph_t g, const cudaGraphNode_t* dep, hpc::LoopCond& lc,
+                           cudaGraphNode_t* node) {
     cudaStream_t cs = h->cap_stream;
     const hpc::IterBufs<T> b = bufs<T>(h);
     const bool timing = h->opt.timing != 0;
-    CUDA_TRY(cudaGraphCreate(&h->graph, 0));
-    hpc::LoopCond lc;
     lc.use = 1;
-    cudaGraphNode_t outer, inner, leaf;
+    cudaGraphNode_t inner, leaf;
     cudaGraph_t body, ls_body;
-    STATUS_TRY(add_while(h->graph, nullptr, &lc.iter, &outer, &body));
-    // line-search handle lives in the body that holds its node
+    STATUS_TRY(add_while(g, dep, lc.iter, node, &body));
+    // the line-search handle lives in the body that holds its node
     CUDA_TRY(cudaGraphConditionalHandleCreate(&lc.ls, body, 1, cudaGraphCondAssignDefault));
     {
         CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
@@ -489,14 +495,8 @@ int build_graph(hpc_ctx* h) {
         }
         STATUS_TRY(end_capture(cs, body, st));
     }
+    STATUS_TRY(add_while(body, &leaf, lc.ls, &inner, &ls_body));
     {
-        cudaGraphNodeParams np{};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = lc.ls;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        CUDA_TRY(cudaGraphAddNode(&inner, body, &leaf, nullptr, 1, &np));
-        ls_body = np.conditional.phGraph_out[0];
         CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, ls_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         capture_window<T>(h, b, lc, cs);
         STATUS_TRY(end_capture(cs, ls_body, HPC_OK));
@@ -507,10 +507,58 @@ int build_graph(hpc_ctx* h) {
         hpc::launch_commit<T>(b, lc, cs);
         STATUS_TRY(end_capture(cs, body, HPC_OK));
     }
+    return HPC_OK;
+}
+
+int ensure_cap_stream(hpc_ctx* h) {
+    if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    return HPC_OK;
+}
+
+// The solve graph: the iteration loop alone (its condition is 1 at every launch).
+template <typename T>
+int build_graph(hpc_ctx* h) {
+    destroy_graph(h);
+    STATUS_TRY(ensure_cap_stream(h));
+    CUDA_TRY(cudaGraphCreate(&h->graph, 0));
+    hpc::LoopCond lc;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&lc.iter, h->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t loop;
+    STATUS_TRY(capture_iteration_loop<T>(h, h->graph, nullptr, lc, &loop));
     CUDA_TRY(cudaGraphInstantiate(&h->gexec, h->graph, 0));
     h->g_epoch = h->epoch;
     h->g_cur = h->cur;
-    h->g_timing = timing ? 1 : 0;
+    h->g_timing = h->opt.timing ? 1 : 0;
+    return HPC_OK;
+}
+
+// The path graph: WHILE (points) { k_point_begin, iteration loop, k_point_end }.
+template <typename T>
+int build_path_graph(hpc_ctx* h, const hpc::PathOut& out, cudaGraph_t* graph, cudaGraphExec_t* exec) {
+    STATUS_TRY(ensure_cap_stream(h));
+    cudaStream_t cs = h->cap_stream;
+    CUDA_TRY(cudaGraphCreate(graph, 0));
+    cudaGraphConditionalHandle path_cond;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&path_cond, *graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t outer, begin_leaf, loop;
+    cudaGraph_t body;
+    STATUS_TRY(add_while(*graph, nullptr, path_cond, &outer, &body));
+    hpc::LoopCond lc;
+    CUDA_TRY(cudaGraphConditionalHandleCreate(&lc.iter, body, 1, cudaGraphCondAssignDefault));
+    {
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        hpc::launch_point_begin(h->d_ctrl, out, lc, cs);
+        const int st = capture_leaf(cs, &begin_leaf);
+        STATUS_TRY(end_capture(cs, body, st));
+    }
+    STATUS_TRY(capture_iteration_loop<T>(h, body, &begin_leaf, lc, &loop));
+    {
+        const hpc::IterBufs<T> b = bufs<T>(h);
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, &loop, nullptr, 1, cudaStreamCaptureModeRelaxed));
+        hpc::launch_point_end<T>(b, out, path_cond, cs);
+        STATUS_TRY(end_capture(cs, body, HPC_OK));
+    }
+    CUDA_TRY(cudaGraphInstantiate(exec, *graph, 0));
     return HPC_OK;
 }
 
@@ -525,9 +573,9 @@ int loop_launches(const hpc_ctx* h) {
 // iteration limit or a raised flag; the host only grows buffers after an
 // overflow (the failed iteration is repeated) and reads the control block.
 template <typename T>
-int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s) {
+int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s, bool fresh = true) {
     const int64_t regrows0 = h->regrows;
-    STATUS_TRY(load_ctrl(h, k, use_stop));
+    if (fresh) STATUS_TRY(load_ctrl(h, k, use_stop));
     if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[0], h->stream));
     int status = HPC_OK;
     bool ran = false;
@@ -582,6 +630,107 @@ int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s) {
     s->capacity_regrows = h->regrows - regrows0;
     s->status = status;
     return status;
+}
+
+// Independent handles (device loop, same device) solved by one graph launch:
+// each handle's iteration loop is a WHILE branch of the same graph, with no
+// edges between branches.  The graph runs on the first handle's stream after it
+// waits for the others.  A handle whose buffers overflowed grows them and
+// finishes alone with its own graph, its counters continuing.
+int solve_batch_device(const std::vector<hpc_ctx*>& hs, std::vector<int>& status, std::vector<hpc_stats>& st) {
+    const size_t m = hs.size();
+    cudaStream_t s0 = hs[0]->stream;
+    std::vector<int64_t> regrows0(m);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    auto cleanup = [&]() {
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+    };
+    int r = HPC_OK;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return HPC_ERR_CUDA;
+    for (size_t t = 0; t < m && r == HPC_OK; ++t) {
+        hpc_ctx* h = hs[t];
+        regrows0[t] = h->regrows;
+        r = load_ctrl(h, h->opt.max_iter, true);
+        if (r == HPC_OK) r = ensure_cap_stream(h);
+        if (r != HPC_OK) break;
+        if (h->opt.max_iter <= 0) continue;          // nothing to run: reported as not converged
+        hpc::LoopCond lc;
+        if (cudaGraphConditionalHandleCreate(&lc.iter, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            r = HPC_ERR_CUDA;
+            break;
+        }
+        cudaGraphNode_t node;
+        r = h->vdt == HPC_F64 ? capture_iteration_loop<double>(h, g, nullptr, lc, &node)
+                              : capture_iteration_loop<float>(h, g, nullptr, lc, &node);
+    }
+    if (r == HPC_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) r = HPC_ERR_CUDA;
+    // order the launch after every handle's pending work (its control-block upload)
+    for (size_t t = 1; t < m && r == HPC_OK; ++t) {
+        if (hs[t]->stream == s0) continue;
+        if (cudaEventRecord(hs[t]->ev[2], hs[t]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s0, hs[t]->ev[2], 0) != cudaSuccess)
+            r = HPC_ERR_CUDA;
+    }
+    float batch_ms = 0.f;
+    if (r == HPC_OK) {
+        cudaEventRecord(hs[0]->ev[0], s0);
+        if (cudaGraphLaunch(ge, s0) != cudaSuccess) r = HPC_ERR_CUDA;
+        cudaEventRecord(hs[0]->ev[1], s0);
+        if (r == HPC_OK && cudaEventSynchronize(hs[0]->ev[1]) != cudaSuccess) r = HPC_ERR_CUDA;
+        if (r == HPC_OK) cudaEventElapsedTime(&batch_ms, hs[0]->ev[0], hs[0]->ev[1]);
+    }
+    cleanup();
+    if (r != HPC_OK) return r;
+    for (size_t t = 0; t < m; ++t) {
+        hpc_ctx* h = hs[t];
+        hpc_stats& s = st[t];
+        std::memset(&s, 0, sizeof s);
+        int rr = read_ctrl(h);
+        if (rr != HPC_OK) { status[t] = rr; continue; }
+        const hpc::Ctrl c = *h->h_ctrl;
+        h->nnz = c.nnz_cur;
+        if (c.flags & (hpc::kFlagEmOverflow | hpc::kFlagBucketOverflow | hpc::kFlagNnzOverflow)) {
+            if (c.flags & hpc::kFlagNnzOverflow) {
+                rr = grow_csr(h, std::max<int64_t>(2 * h->csr_cap, (int64_t)c.nnz_next + 1));
+                h->regrows += 1;
+            } else {
+                rr = regrow(h, (int64_t)c.em_count + 1);
+            }
+            if (rr == HPC_OK)
+                rr = h->vdt == HPC_F64 ? run_device_loop<double>(h, h->opt.max_iter, true, &s, false)
+                                       : run_device_loop<float>(h, h->opt.max_iter, true, &s, false);
+            s.ms_total += batch_ms;
+            s.capacity_regrows = h->regrows - regrows0[t];
+            status[t] = rr;
+            continue;
+        }
+        int stt = HPC_OK;
+        if (c.flags) {
+            stt = flags_to_status(c.flags);
+            if (stt == HPC_OK) stt = HPC_ERR_CUDA;
+        } else {
+            stt = c.converged ? HPC_OK : HPC_NOT_CONVERGED;
+        }
+        s.iterations = c.iter;
+        s.ls_trials = c.ls_trials;
+        s.nnz = h->nnz;
+        s.accepted_halvings = c.ls_accept;
+        s.f = c.f_cur;
+        s.F = c.f_cur + c.pen_cur;
+        s.rel_change = c.rel;
+        s.candidates = c.em_count;
+        s.ms_total = batch_ms;
+        s.ms_grad_pass = h->opt.timing ? (double)c.screen_ns * 1e-6 : 0.0;
+        s.grad_pass_launches = c.iter_attempts;
+        s.kernel_launches = c.iter_attempts * loop_launches(h) + 2 * c.ls_windows;
+        s.ms_gram = h->ms_gram;
+        s.capacity_regrows = h->regrows - regrows0[t];
+        s.status = stt;
+        status[t] = stt;
+    }
+    return HPC_OK;
 }
 
 template <typename T>
@@ -982,12 +1131,118 @@ int hpc_set_omega(hpc_handle h, int64_t nnz, const int64_t* row_ptr, const int32
     return HPC_OK;
 }
 
-int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
-                   int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout) {
-    if (!h || !h->loaded || k < 0 || (k > 0 && (!lambda1 || !points)) || !(lambda2 >= 0.0)) return HPC_ERR_ARG;
-    if (row_ptr && (!col || !val || !cap_inout)) return HPC_ERR_ARG;
-    for (int64_t t = 0; t < k; ++t)
-        if (!(lambda1[t] >= 0.0)) return HPC_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// The lambda path as one graph launch (device loop): WHILE (points) { begin,
+// iteration loop, end }.  Per-point statistics and, if asked for, the estimates
+// are written to device buffers and copied back once.  An overflow ends the
+// launch; the buffers grow, the graph is rebuilt and the point resumes.
+template <typename T>
+int solve_path_device(hpc_ctx* h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
+                      int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout) {
+    const int64_t p = h->p;
+    const int64_t cap = row_ptr ? *cap_inout : 0;
+    struct Bufs {
+        void* q[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        ~Bufs() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+            for (void* x : q) if (x) cudaFree(x);
+        }
+    } bf;
+    hpc::PathOut out{};
+    CUDA_TRY(cudaMalloc(&bf.q[0], k * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&bf.q[1], k * sizeof(hpc_path_point)));
+    out.lam1 = static_cast<const double*>(bf.q[0]);
+    out.points = static_cast<hpc_path_point*>(bf.q[1]);
+    if (row_ptr) {
+        CUDA_TRY(cudaMalloc(&bf.q[2], (size_t)k * (p + 1) * sizeof(int64_t)));
+        CUDA_TRY(cudaMalloc(&bf.q[3], std::max<int64_t>(cap, 1) * sizeof(int32_t)));
+        CUDA_TRY(cudaMalloc(&bf.q[4], std::max<int64_t>(cap, 1) * sizeof(float)));
+        out.rp = static_cast<int64_t*>(bf.q[2]);
+        out.ci = static_cast<int32_t*>(bf.q[3]);
+        out.cv = static_cast<float*>(bf.q[4]);
+    }
+    out.cap = cap;
+    out.k = (int)k;
+    CUDA_TRY(cudaMemcpyAsync(bf.q[0], lambda1, k * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemsetAsync(bf.q[1], 0, k * sizeof(hpc_path_point), h->stream));
+    h->lam1 = lambda1[0];
+    h->lam2 = lambda2;
+    hpc::Ctrl& c0 = *h->h_ctrl;
+    c0.path_pt = c0.path_pt_next = 0;
+    c0.path_k = (int)k;
+    c0.path_keep = 0;
+    c0.path_off = c0.path_off_next = c0.path_need = 0;
+    c0.path_full = 0;
+    STATUS_TRY(load_ctrl(h, h->opt.max_iter, true));
+    int64_t epoch = -1;
+    bool ran = false;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        if (!bf.e || epoch != h->epoch) {
+            if (bf.e) { cudaGraphExecDestroy(bf.e); bf.e = nullptr; }
+            if (bf.g) { cudaGraphDestroy(bf.g); bf.g = nullptr; }
+            STATUS_TRY(build_path_graph<T>(h, out, &bf.g, &bf.e));
+            epoch = h->epoch;
+        }
+        CUDA_TRY(cudaGraphLaunch(bf.e, h->stream));
+        STATUS_TRY(read_ctrl(h));
+        const hpc::Ctrl& c = *h->h_ctrl;
+        h->nnz = c.nnz_cur;
+        ran = true;
+        int grow = 0;
+        if (c.flags & (hpc::kFlagEmOverflow | hpc::kFlagBucketOverflow)) {
+            STATUS_TRY(regrow(h, (int64_t)c.em_count + 1));
+            grow = 1;
+        } else if (c.flags & hpc::kFlagNnzOverflow) {
+            STATUS_TRY(grow_csr(h, std::max<int64_t>(2 * h->csr_cap, (int64_t)c.nnz_next + 1)));
+            h->regrows += 1;
+            grow = 1;
+        }
+        if (!grow) break;
+        ran = false;
+        // resume the interrupted point with its counters
+        const int one = 1;
+        CUDA_TRY(cudaMemcpyAsync(&h->d_ctrl->path_keep, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    if (!ran) return HPC_ERR_CAPACITY;
+    const hpc::Ctrl c = *h->h_ctrl;
+    const int64_t reached = std::min<int64_t>(c.path_pt_next, k);
+    std::vector<hpc_path_point> pts(k);
+    CUDA_TRY(cudaMemcpy(pts.data(), bf.q[1], k * sizeof(hpc_path_point), cudaMemcpyDeviceToHost));
+    int status = HPC_OK;
+    for (int64_t t = 0; t < reached; ++t) {
+        points[t] = pts[t];
+        if (pts[t].status < 0 && status == HPC_OK) status = pts[t].status;
+    }
+    if (reached > 0) h->lam1 = lambda1[reached - 1];
+    if (row_ptr) {
+        CUDA_TRY(cudaMemcpy(row_ptr, bf.q[2], (size_t)reached * (p + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        const int64_t used = c.path_off_next;
+        if (used > 0) {
+            CUDA_TRY(cudaMemcpy(col, bf.q[3], used * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(val, bf.q[4], used * sizeof(float), cudaMemcpyDeviceToHost));
+        }
+        if (c.path_full) {
+            *cap_inout = c.path_need;
+            return HPC_ERR_CAPACITY;
+        }
+        *cap_inout = used;
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+static int solve_path_host(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
+                           int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout) {
     const int64_t cap = row_ptr ? *cap_inout : 0;
     int64_t used = 0;
     int status = HPC_OK;
@@ -1021,6 +1276,18 @@ int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda
     return status;
 }
 
+int hpc_solve_path(hpc_handle h, const double* lambda1, int64_t k, double lambda2, hpc_path_point* points,
+                   int64_t* row_ptr, int32_t* col, float* val, int64_t* cap_inout) {
+    if (!h || !h->loaded || k < 0 || (k > 0 && (!lambda1 || !points)) || !(lambda2 >= 0.0)) return HPC_ERR_ARG;
+    if (row_ptr && (!col || !val || !cap_inout)) return HPC_ERR_ARG;
+    for (int64_t t = 0; t < k; ++t)
+        if (!(lambda1[t] >= 0.0)) return HPC_ERR_ARG;
+    if (k == 0 || !h->opt.device_loop || k > 0x7fffffff)
+        return solve_path_host(h, lambda1, k, lambda2, points, row_ptr, col, val, cap_inout);
+    return h->vdt == HPC_F64 ? solve_path_device<double>(h, lambda1, k, lambda2, points, row_ptr, col, val, cap_inout)
+                             : solve_path_device<float>(h, lambda1, k, lambda2, points, row_ptr, col, val, cap_inout);
+}
+
 int hpc_solve_batch(hpc_handle* handles, int count, int threads, hpc_stats* stats) {
     if (count < 0 || (count > 0 && !handles)) return HPC_ERR_ARG;
     for (int t = 0; t < count; ++t)
@@ -1029,6 +1296,21 @@ int hpc_solve_batch(hpc_handle* handles, int count, int threads, hpc_stats* stat
     if (cudaGetDevice(&dev) != cudaSuccess) return HPC_ERR_CUDA;
     std::vector<int> status(count, HPC_OK);
     std::vector<hpc_stats> st(count);
+    bool all_device = count > 0;
+    for (int t = 0; t < count; ++t) all_device = all_device && handles[t]->opt.device_loop;
+    if (all_device) {
+        // one graph launch for the whole batch
+        std::vector<hpc_ctx*> hs(handles, handles + count);
+        const int r = solve_batch_device(hs, status, st);
+        if (r != HPC_OK) return r;
+        int ret = HPC_OK;
+        for (int t = 0; t < count; ++t) {
+            if (stats) stats[t] = st[t];
+            if (status[t] < 0 && ret >= 0) ret = status[t];
+            else if (status[t] == HPC_NOT_CONVERGED && ret == HPC_OK) ret = HPC_NOT_CONVERGED;
+        }
+        return ret;
+    }
     // handles that share a stream go to the same worker, in index order
     std::vector<std::vector<int>> groups;
     {

@@ -42,6 +42,13 @@ struct Ctrl {
     int iter_limit;      // the device loop stops after this many accepted iterations
     int use_stop;        // the device loop stops at the stopping rule
     int pad2_;
+    // lambda path in one launch: point index, estimate staging offset (both advanced
+    // by the next point's begin kernel), and the point's start time
+    int path_pt, path_pt_next;
+    int path_k, path_keep;        // points; 1 = resume the current point (after a regrow)
+    long long path_off, path_off_next, path_need;
+    long long t_point;
+    int path_full, pad3_;         // 1 = the estimate staging buffer is full
 };
 
 enum : int {
@@ -135,6 +142,19 @@ struct LoopCond {
 template <typename T> void launch_iter_begin(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s);
 template <typename T> void launch_commit(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s);
 void launch_stamp(Ctrl* ctrl, int end, cudaStream_t s);
+// lambda path in one launch (device loop): per-point set-up and bookkeeping
+struct PathOut {
+    const double* lam1;          // k
+    hpc_path_point* points;      // k
+    int64_t* rp;                 // k*(p+1) or null: estimates' row offsets
+    int32_t* ci;                 // cap
+    float* cv;                   // cap
+    long long cap;
+    int k;
+};
+void launch_point_begin(Ctrl* ctrl, PathOut out, const LoopCond& lc, cudaStream_t s);
+template <typename T> void launch_point_end(const IterBufs<T>& b, PathOut out, cudaGraphConditionalHandle path_cond,
+                                            cudaStream_t s);
 template <typename T> void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s);
 template <typename T> void launch_candidates(const IterBufs<T>& b, cudaStream_t s);
 template <typename T> void launch_ls_window(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s);

@@ -1715,6 +1715,99 @@ void launch_commit(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
 
 void launch_stamp(Ctrl* ctrl, int end, cudaStream_t s) { k_stamp<<<1, 1, 0, s>>>(ctrl, end); }
 
+// ------------------------------------------------------------------ lambda path in one launch
+__device__ __forceinline__ long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+__device__ __forceinline__ int status_of_flags(int f) {
+    if (f & kFlagNaN) return HPC_ERR_NAN;
+    if (f & kFlagLsFail) return HPC_ERR_LS_FAIL;
+    if (f & kFlagTimeout) return HPC_ERR_DEVICE_TIMEOUT;
+    return HPC_ERR_CUDA;
+}
+
+// Start point pt of the path: its lambda1, fresh counters (unless the point resumes
+// after a host-side regrow), and the iteration loop armed.
+__global__ void k_point_begin(Ctrl* ctrl, PathOut out, cudaGraphConditionalHandle iter_cond) {
+    ctrl->path_pt = ctrl->path_pt_next;
+    ctrl->path_off = ctrl->path_off_next;
+    const int pt = ctrl->path_pt;
+    ctrl->lam1 = out.lam1[pt];
+    if (!ctrl->path_keep) {
+        ctrl->iter = 0;
+        ctrl->ls_trials = 0;
+        ctrl->converged = 0;
+        ctrl->t_point = globaltimer_ns();
+    }
+    ctrl->path_keep = 0;
+    cudaGraphSetConditional(iter_cond, ctrl->iter_limit > ctrl->iter ? 1u : 0u);
+}
+
+// End of point pt: its statistics, optionally a copy of the estimate, and the
+// decision to go on.  Every block reads the point index and the staging offset,
+// which only the next k_point_begin advances.  An overflow flag ends the launch
+// without advancing: the host grows the buffers and resumes this point.
+template <typename T>
+__global__ void k_point_end(Csr<T> cu, int p, PathOut out, Ctrl* ctrl, cudaGraphConditionalHandle path_cond) {
+    const int flags = ctrl->flags;
+    const int pt = ctrl->path_pt;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nt = gridDim.x * blockDim.x;
+    const bool overflow = flags & (kFlagEmOverflow | kFlagBucketOverflow | kFlagNnzOverflow);
+    if (overflow) {
+        if (tid == 0) cudaGraphSetConditional(path_cond, 0u);
+        return;
+    }
+    const long long nnz = ctrl->nnz_cur;
+    const long long base = ctrl->path_off;
+    const bool fits = base + nnz <= out.cap;
+    if (out.rp && fits) {
+        int64_t* rp = out.rp + (size_t)pt * (p + 1);
+        for (int i = tid; i <= p; i += nt) rp[i] = cu.rp[i];
+        for (long long q = tid; q < nnz; q += nt) {
+            out.ci[base + q] = cu.ci[q];
+            out.cv[base + q] = (float)cu.cv[q];
+        }
+    }
+    if (tid != 0) return;
+    hpc_path_point r;
+    r.lambda1 = out.lam1[pt];
+    r.iterations = ctrl->iter;
+    r.ls_trials = ctrl->ls_trials;
+    r.nnz = nnz;
+    r.status = flags ? status_of_flags(flags) : (ctrl->converged ? HPC_OK : HPC_NOT_CONVERGED);
+    r.pad_ = 0;
+    r.f = ctrl->f_cur;
+    r.F = ctrl->f_cur + ctrl->pen_cur;
+    r.rel_change = ctrl->rel;
+    r.ms = 1e-6 * (double)(globaltimer_ns() - ctrl->t_point);
+    out.points[pt] = r;
+    bool more = flags == 0 && pt + 1 < out.k;
+    if (out.rp) {
+        if (fits) {
+            ctrl->path_off_next = base + nnz;
+        } else {
+            ctrl->path_need = base + nnz;
+            ctrl->path_full = 1;
+            more = false;
+        }
+    }
+    ctrl->path_pt_next = pt + 1;
+    cudaGraphSetConditional(path_cond, more ? 1u : 0u);
+}
+
+void launch_point_begin(Ctrl* ctrl, PathOut out, const LoopCond& lc, cudaStream_t s) {
+    k_point_begin<<<1, 1, 0, s>>>(ctrl, out, lc.iter);
+}
+
+template <typename T>
+void launch_point_end(const IterBufs<T>& b, PathOut out, cudaGraphConditionalHandle path_cond, cudaStream_t s) {
+    k_point_end<T><<<b.num_sms * 2, 256, 0, s>>>(b.cur, b.p, out, b.ctrl, path_cond);
+}
+
 template <typename T>
 void launch_set_identity(Csr<T> c, int p, cudaStream_t s) {
     k_set_identity<T><<<64, 256, 0, s>>>(c, p);
@@ -1737,6 +1830,7 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
 #define HPC_INSTANTIATE(T)                                                                       \
     template void launch_iter_begin<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);         \
     template void launch_commit<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);             \
+    template void launch_point_end<T>(const IterBufs<T>&, PathOut, cudaGraphConditionalHandle, cudaStream_t); \
     template void launch_grad_screen<T>(const IterBufs<T>&, cudaStream_t);                         \
     template void launch_candidates<T>(const IterBufs<T>&, cudaStream_t);                          \
     template void launch_ls_window<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);          \

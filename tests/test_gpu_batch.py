@@ -14,7 +14,9 @@ def _problem(p, n, seed):
     return sample_x_cpu(omega0_banded(p, 3, seed), n, seed).astype(np.float32)
 
 
-def test_batch_of_uneven_problems_matches_oracle_and_sequential(lib):
+@pytest.mark.parametrize("device_loop", [1, 0])
+def test_batch_of_uneven_problems_matches_oracle_and_sequential(lib, device_loop):
+    """device_loop=1: the whole batch is one graph launch; 0: a host thread pool."""
     import torch
 
     shapes = [(120, 60), (200, 100), (257, 128), (300, 150), (384, 192), (500, 250)]
@@ -22,7 +24,7 @@ def test_batch_of_uneven_problems_matches_oracle_and_sequential(lib):
     lam1, lam2 = 0.15, 0.1
     streams = [torch.cuda.Stream() for _ in shapes]
     solvers = [lib.Solver(torch.as_tensor(X).cuda(), lam1, lam2, stream=st, precision=lib.PREC_FP32, eps=1e-7,
-                          max_iter=20000) for X, st in zip(Xs, streams)]
+                          max_iter=20000, device_loop=device_loop) for X, st in zip(Xs, streams)]
     stats = lib.solve_batch(solvers)
     batch = [s.get_omega() for s in solvers]
     for s in solvers:
@@ -47,11 +49,37 @@ def test_batch_thread_limit_and_errors(lib):
 
     Xs = [_problem(100, 50, 20 + t) for t in range(3)]
     solvers = [lib.Solver(torch.as_tensor(X).cuda(), 0.15, 0.1, stream=torch.cuda.Stream(),
-                          precision=lib.PREC_FP32) for X in Xs]
+                          precision=lib.PREC_FP32, device_loop=0) for X in Xs]
     stats = lib.solve_batch(solvers, threads=2)
     assert len(stats) == 3 and all(st["iterations"] > 0 for st in stats)
     for s in solvers:
         s.close()
+
+
+def test_batch_launch_with_overflow_and_shared_stream(lib):
+    """One graph launch: a handle with a tiny candidate capacity overflows, grows and
+    finishes alone; two handles on one stream; a handle with max_iter = 0.  Every
+    result equals the same handle's plain solve."""
+    import torch
+
+    Xs = [_problem(180, 90, 30 + t) for t in range(4)]
+    st_shared = torch.cuda.Stream()
+    opts = [dict(capacity=200), dict(), dict(), dict(max_iter=0)]
+    streams = [torch.cuda.Stream(), st_shared, st_shared, torch.cuda.Stream()]
+    solvers = [lib.Solver(torch.as_tensor(X).cuda(), 0.08, 0.1, stream=st, precision=lib.PREC_FP32, eps=1e-7, **o)
+               for X, st, o in zip(Xs, streams, opts)]
+    stats = lib.solve_batch(solvers)
+    ests = [s.get_omega() for s in solvers]
+    for s in solvers:
+        s.close()
+    assert stats[0]["capacity_regrows"] >= 1
+    assert stats[3]["status"] == 1 and stats[3]["iterations"] == 0
+    for X, o, est, st in list(zip(Xs, opts, ests, stats))[:3]:
+        with lib.Solver(torch.as_tensor(X).cuda(), 0.08, 0.1, precision=lib.PREC_FP32, eps=1e-7, **o) as s:
+            ref = s.solve().as_dict()
+            seq = s.get_omega()
+        assert st["iterations"] == ref["iterations"] and st["ls_trials"] == ref["ls_trials"]
+        assert np.array_equal(seq.col, est.col) and np.array_equal(seq.val, est.val)
 
 
 @pytest.mark.slow

@@ -44,3 +44,44 @@ def test_path_without_estimates_and_bad_arguments(lib):
         with pytest.raises(lib.HpcError) as e:
             s.solve_path([0.2, -1.0], 0.1)
         assert e.value.status == lib.ERR_ARG
+
+
+def _path(lib, X, grid, lam2, **opt):
+    import torch
+
+    with lib.Solver(torch.as_tensor(X).cuda(), grid[0], lam2, precision=lib.PREC_FP32, eps=1e-7, max_iter=20000,
+                    **opt) as s:
+        return s.solve_path(grid, lam2)
+
+
+def test_path_in_one_launch_matches_the_host_driven_path(lib):
+    """device_loop=1 runs the whole grid as one graph launch (an outer WHILE over the
+    points); it must give the host-driven path's points and estimates bit for bit."""
+    X = small_problem(260, 200, 4.0, 33).astype(np.float32)
+    grid = np.logspace(np.log10(0.5), np.log10(0.06), 9)
+    pd, ed = _path(lib, X, grid, 0.1, device_loop=1)
+    ph, eh = _path(lib, X, grid, 0.1, device_loop=0)
+    for a, b in zip(pd, ph):
+        for key in ("lambda1", "iterations", "ls_trials", "nnz", "status", "F", "rel_change"):
+            assert a[key] == b[key], key
+        assert a["ms"] > 0
+    for a, b in zip(ed, eh):
+        assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+        assert np.array_equal(a.val, b.val)
+
+
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_path_estimate_capacity_and_iteration_limit(lib, device_loop):
+    import torch
+
+    X = small_problem(150, 120, 3.0, 5).astype(np.float32)
+    grid = [0.4, 0.2, 0.1]
+    with lib.Solver(torch.as_tensor(X).cuda(), 0.4, 0.1, precision=lib.PREC_FP32, device_loop=device_loop) as s:
+        with pytest.raises(lib.HpcError) as e:
+            s.solve_path(grid, 0.1, capacity=200)        # less than the first estimate (>= 150 diagonal entries + ...)
+        assert e.value.status == lib.ERR_CAPACITY
+    with lib.Solver(torch.as_tensor(X).cuda(), 0.4, 0.1, precision=lib.PREC_FP32, device_loop=device_loop,
+                    eps=1e-12, max_iter=3) as s:
+        pts, ests = s.solve_path(grid, 0.1)
+        assert [q["status"] for q in pts] == [1, 1, 1]   # HPC_NOT_CONVERGED at every point, the path goes on
+        assert [q["iterations"] for q in pts] == [3, 3, 3]
