@@ -82,6 +82,7 @@ struct hpc_ctx {
     void* em_om = nullptr;
     int* bk_cnt = nullptr; int* bk_off = nullptr; int* bk_cur = nullptr; int* bk_len = nullptr;
     long long* bk_uoff = nullptr;
+    int* bk_long = nullptr;
     int2* bk_mir = nullptr;
     int* col_a = nullptr; void* w_a = nullptr; void* om_a = nullptr; unsigned char* fl_a = nullptr;
     int* col_b = nullptr; void* w_b = nullptr; void* om_b = nullptr; unsigned char* fl_b = nullptr;
@@ -217,6 +218,7 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.bk.col_b = h->col_b; b.bk.w_b = as<T>(h->w_b); b.bk.om_b = as<T>(h->om_b); b.bk.fl_b = h->fl_b;
     b.bk.g = as<T>(h->g_b);
     b.bk.uoff = h->bk_uoff;
+    b.bk.longlist = h->bk_long;
     b.bk.mir = h->bk_mir;
     b.bk.cap = (int)std::min<int64_t>(2 * h->cap, 0x7fffffff);
     b.cnt2 = h->cnt2;
@@ -848,7 +850,7 @@ void destroy(hpc_ctx* h) {
     void* ptrs[] = {h->S, h->rp[0], h->rp[1], h->ci[0], h->ci[1], h->cv[0], h->cv[1], h->bk_cnt, h->bk_off,
                     h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
-                    h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff};
+                    h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -1000,6 +1002,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     CK(cudaMalloc(&h->bk_cur, p * sizeof(int)));
     CK(cudaMalloc(&h->bk_len, p * sizeof(int)));
     CK(cudaMalloc(&h->bk_uoff, (p + 1) * sizeof(long long)));
+    CK(cudaMalloc(&h->bk_long, p * sizeof(int)));
     CK(cudaMalloc(&h->cnt2, p * sizeof(int)));
     h->nblk = (int)std::min<int64_t>((p + 7) / 8, 152 * 16);
     CK(cudaMalloc(&h->part_obj, (size_t)h->nblk * 4 * sizeof(double)));

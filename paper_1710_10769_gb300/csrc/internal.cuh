@@ -49,7 +49,12 @@ struct Ctrl {
     long long path_off, path_off_next, path_need;
     long long t_point;
     int path_full, pad3_;         // 1 = the estimate staging buffer is full
+    int n_long, pad4_;            // rows of the candidate structure with more than kShortRow entries
 };
+
+// Rows with at most this many candidate entries (before de-dup) are handled one
+// lane per row by the candidate, line-search and compaction kernels.
+constexpr int kShortRow = 2;
 
 enum : int {
     kFlagEmOverflow = 1,
@@ -91,7 +96,8 @@ struct Buckets {
     int* col_a; T* w_a; T* om_a; unsigned char* fl_a;    // scattered
     int* col_b; T* w_b; T* om_b; unsigned char* fl_b;    // sorted, de-duplicated
     T* g;         // G_ij of the sorted entries
-    long long* uoff;  // p+1: prefix of line-search work units per row (pairs of 32-entry chunks)
+    long long* uoff;  // nlong+1: prefix of line-search work units over the long rows
+    int* longlist;    // p: rows with more than kShortRow entries before de-dup, ascending
     int2* mir;    // cap: (position, row) of every kept partner entry
     int cap;
 };

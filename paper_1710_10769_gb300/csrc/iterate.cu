@@ -747,26 +747,28 @@ __device__ __forceinline__ long long warp_incl_scan64(long long x, int lane) {
 }
 
 // Single-block exclusive scan of n ints, out[n] = total; if total > cap, sets
-// flag.  With uoff, also the exclusive 64-bit scan of ls_units(in[i]) (uoff[n] =
-// total units).  Thread t owns the contiguous run [t E, t E + E): one pass sums
-// the runs (16-byte loads), one block-wide scan of the 1024 run sums, and a
-// second pass writes the run's prefixes.
+// flag.  With uoff (the bucket scan), also the list of long rows (more than
+// kShortRow entries), in ascending order, into longlist, their count into
+// ctrl->n_long, and the exclusive 64-bit prefix of their ls_units over that list
+// into uoff (uoff[n_long] = total units).  Thread t owns the contiguous run
+// [t E, t E + E): one pass sums the runs (16-byte loads), one block-wide scan of
+// the 1024 run sums, and a second pass writes the run's prefixes.
 __global__ void __launch_bounds__(1024)
 k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
-       int* total_dst, long long* __restrict__ uoff) {
-    __shared__ int wsum[32];
+       int* total_dst, long long* __restrict__ uoff, int* __restrict__ longlist) {
+    __shared__ int wsum[32], wlong[32];
     __shared__ long long usum[32];
     if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) {
         if (threadIdx.x == 0) {
             out[n] = 0;
-            if (uoff) uoff[n] = 0;
+            if (uoff) { uoff[0] = 0; ctrl->n_long = 0; }
         }
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int E = ((n + 1023) / 1024 + 3) & ~3;
     const int b0 = min(n, threadIdx.x * E), b1 = min(n, b0 + E);
-    int s = 0;
+    int s = 0, ls = 0;
     long long us = 0;
     for (int j = b0; j < b1; j += 4) {
         int v[4];
@@ -780,20 +782,28 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             s += v[q];
-            if (uoff && j + q < b1) us += ls_units(v[q]);
+            if (uoff && j + q < b1 && v[q] > kShortRow) {
+                us += ls_units(v[q]);
+                ls += 1;
+            }
         }
     }
     const int x = warp_incl_scan(s, lane);
+    const int lx = uoff ? warp_incl_scan(ls, lane) : 0;
     const long long ux = uoff ? warp_incl_scan64(us, lane) : 0;
-    if (lane == 31) { wsum[warp] = x; usum[warp] = ux; }
+    if (lane == 31) { wsum[warp] = x; usum[warp] = ux; wlong[warp] = lx; }
     __syncthreads();
     if (warp == 0) {
         wsum[lane] = warp_incl_scan(wsum[lane], lane);
-        if (uoff) usum[lane] = warp_incl_scan64(usum[lane], lane);
+        if (uoff) {
+            usum[lane] = warp_incl_scan64(usum[lane], lane);
+            wlong[lane] = warp_incl_scan(wlong[lane], lane);
+        }
     }
     __syncthreads();
     int run = x - s + (warp ? wsum[warp - 1] : 0);
     long long urun = ux - us + (warp ? usum[warp - 1] : 0);
+    int lrun = lx - ls + (warp ? wlong[warp - 1] : 0);
     // second pass over the run, 16 bytes at a time (the loads hit L1/L2)
 #pragma unroll 4
     for (int j = b0; j < b1; j += 4) {
@@ -807,31 +817,30 @@ k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* 
             for (int q = 0; q < 4; ++q) v[q] = j + q < b1 ? in[j + q] : 0;
         }
         int o[4];
-        long long uo[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             o[q] = run;
             run += v[q];
-            uo[q] = urun;
-            if (uoff) urun += ls_units(v[q]);
+            if (uoff && j + q < b1 && v[q] > kShortRow) {
+                longlist[lrun] = j + q;
+                uoff[lrun] = urun;
+                ++lrun;
+                urun += ls_units(v[q]);
+            }
         }
         if (full) {
             *reinterpret_cast<int4*>(out + j) = make_int4(o[0], o[1], o[2], o[3]);
-            if (uoff) {
-                *reinterpret_cast<longlong2*>(uoff + j) = make_longlong2(uo[0], uo[1]);
-                *reinterpret_cast<longlong2*>(uoff + j + 2) = make_longlong2(uo[2], uo[3]);
-            }
         } else {
-            for (int q = 0; q < 4 && j + q < b1; ++q) {
-                out[j + q] = o[q];
-                if (uoff) uoff[j + q] = uo[q];
-            }
+            for (int q = 0; q < 4 && j + q < b1; ++q) out[j + q] = o[q];
         }
     }
     if (threadIdx.x == 1023) {
         const int total = wsum[31];
         out[n] = total;
-        if (uoff) uoff[n] = usum[31];
+        if (uoff) {
+            uoff[wlong[31]] = usum[31];
+            ctrl->n_long = wlong[31];
+        }
         if (total_dst) *total_dst = total;
         if (total > cap) atomicOr(&ctrl->flags, flag);
     }
@@ -884,27 +893,68 @@ constexpr int kSortSmem = 4096;
 constexpr int kSortShort = 32;
 
 // Sort by (column, own-before-partner) into the b arrays, then drop partner
-// requests whose own entry exists (the own entry sorts just before).  Rows of at
-// most 32 entries: one warp each, in registers.  Longer rows: one block each, so a
-// hub row with thousands of candidates does not serialise a warp.
+// requests whose own entry exists (the own entry sorts just before).  Three
+// tiers: rows of at most kShortRow entries one lane each (32 rows per warp);
+// rows of at most 32 entries one warp each, in registers; longer rows (hub
+// rows with thousands of candidates) one block each, so none serialises a warp.
+// The last two tiers take their rows from the long-row list of the bucket scan.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
     __shared__ unsigned long long s_key[kSortSmem];
-    __shared__ int s_long[kThreads];
     __shared__ int s_cnt[kWarps];
-    __shared__ int s_nlong, s_out;
+    __shared__ int s_out;
     if (ctrl->flags) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = gw; i < p; i += nw) {
+    const int nlong = ctrl->n_long;
+
+    // 1. short rows, one lane each
+    for (int base = gw * 32; base < p; base += nw * 32) {
+        const int i = base + lane;
+        const int c = i < p ? bk.cnt[i] : kShortRow + 1;
+        const bool sh = c <= kShortRow;
+        int beg = 0, kept = 0;
+        bool m0 = false, m1 = false;
+        if (sh) {
+            beg = bk.off[i];
+            int e0 = 0, e1 = 1;
+            bool drop1 = false;
+            if (c == 2) {
+                if (sort_key(bk, beg + 1) < sort_key(bk, beg)) { e0 = 1; e1 = 0; }
+                drop1 = (bk.fl_a[beg + e1] & kEntMirror) && bk.col_a[beg + e1] == bk.col_a[beg + e0];
+            }
+            if (c >= 1) {
+                bk.col_b[beg] = bk.col_a[beg + e0];
+                bk.w_b[beg] = bk.w_a[beg + e0];
+                bk.om_b[beg] = bk.om_a[beg + e0];
+                bk.fl_b[beg] = bk.fl_a[beg + e0];
+                m0 = bk.fl_a[beg + e0] & kEntMirror;
+                kept = 1;
+            }
+            if (c == 2 && !drop1) {
+                bk.col_b[beg + 1] = bk.col_a[beg + e1];
+                bk.w_b[beg + 1] = bk.w_a[beg + e1];
+                bk.om_b[beg + 1] = bk.om_a[beg + e1];
+                bk.fl_b[beg + 1] = bk.fl_a[beg + e1];
+                m1 = bk.fl_a[beg + e1] & kEntMirror;
+                kept = 2;
+            }
+            bk.len[i] = kept;
+        }
+        push_mirrors(bk, ctrl, m0, beg, i, lane);
+        push_mirrors(bk, ctrl, m1, beg + 1, i, lane);
+    }
+
+    // 2. rows of kShortRow+1 .. 32 entries, one warp each: rank by shuffles (keys are
+    // distinct), drop a partner request whose predecessor in column order is the own
+    // entry of that column, and write the kept entries in order
+    for (int li = gw; li < nlong; li += nw) {
+        const int i = bk.longlist[li];
         const int beg = bk.off[i];
         const int c = bk.cnt[i];
         if (c > kSortShort) continue;
-        // whole row in registers: rank by shuffles (keys are distinct), drop a partner
-        // request whose predecessor in column order is the own entry of that column,
-        // and write the kept entries in order
         const bool valid = lane < c;
         int col = 0;
         T w = T(0), om = T(0);
@@ -941,106 +991,99 @@ k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
         if (lane == 0) bk.len[i] = __popc(kb);
     }
 
-    // long rows: row i belongs to block i mod gridDim.x
-    for (int base = blockIdx.x; base < p; base += gridDim.x * kThreads) {
+    // 3. rows over 32 entries, one block each
+    for (int li = blockIdx.x; li < nlong; li += gridDim.x) {
+        const int i = bk.longlist[li];
+        const int c = bk.cnt[i];
+        if (c <= kSortShort) continue;
+        const int beg = bk.off[i];
         __syncthreads();
-        if (threadIdx.x == 0) s_nlong = 0;
-        __syncthreads();
-        const int i0 = base + threadIdx.x * gridDim.x;
-        if (i0 < p && bk.cnt[i0] > kSortShort) s_long[atomicAdd(&s_nlong, 1)] = i0;
-        __syncthreads();
-        const int nlong = s_nlong;
-        for (int r = 0; r < nlong; ++r) {
-            const int i = s_long[r];
-            const int beg = bk.off[i];
-            const int c = bk.cnt[i];
-            if (c <= kSortSmem) {
-                int n2 = 1;
-                while (n2 < c) n2 <<= 1;
-                for (int e = threadIdx.x; e < n2; e += kThreads)
-                    s_key[e] = e < c ? ((unsigned long long)sort_key(bk, beg + e) << 32) | (unsigned)e : ~0ull;
-                __syncthreads();
-                for (int k = 2; k <= n2; k <<= 1) {
-                    for (int j = k >> 1; j > 0; j >>= 1) {
-                        for (int t = threadIdx.x; t < n2; t += kThreads) {
-                            const int u = t ^ j;
-                            if (u > t) {
-                                const unsigned long long x = s_key[t], y = s_key[u];
-                                if ((x > y) == ((t & k) == 0)) { s_key[t] = y; s_key[u] = x; }
-                            }
-                        }
-                        __syncthreads();
-                    }
-                }
-                for (int q = threadIdx.x; q < c; q += kThreads) {
-                    const int e = beg + (int)(s_key[q] & 0xffffffffu);
-                    bk.col_b[beg + q] = bk.col_a[e];
-                    bk.w_b[beg + q] = bk.w_a[e];
-                    bk.om_b[beg + q] = bk.om_a[e];
-                    bk.fl_b[beg + q] = bk.fl_a[e];
-                }
-            } else {
-                // rank of each entry against all keys of the row, streamed in tiles
-                unsigned* s_k32 = reinterpret_cast<unsigned*>(s_key);
-                constexpr int kTile = 2 * kSortSmem;
-                for (int e0 = 0; e0 < c; e0 += kThreads) {
-                    const int e = e0 + threadIdx.x;
-                    const unsigned ke = e < c ? sort_key(bk, beg + e) : 0xffffffffu;
-                    int rank = 0;
-                    for (int f0 = 0; f0 < c; f0 += kTile) {
-                        __syncthreads();
-                        for (int f = threadIdx.x; f < kTile; f += kThreads)
-                            s_k32[f] = f0 + f < c ? sort_key(bk, beg + f0 + f) : 0xffffffffu;
-                        __syncthreads();
-                        const int fn = min(kTile, c - f0);
-                        for (int f = 0; f < fn; ++f) rank += (s_k32[f] < ke) ? 1 : 0;
-                    }
-                    if (e < c) {
-                        bk.col_b[beg + rank] = bk.col_a[beg + e];
-                        bk.w_b[beg + rank] = bk.w_a[beg + e];
-                        bk.om_b[beg + rank] = bk.om_a[beg + e];
-                        bk.fl_b[beg + rank] = bk.fl_a[beg + e];
-                    }
-                }
-            }
+        if (c <= kSortSmem) {
+            int n2 = 1;
+            while (n2 < c) n2 <<= 1;
+            for (int e = threadIdx.x; e < n2; e += kThreads)
+                s_key[e] = e < c ? ((unsigned long long)sort_key(bk, beg + e) << 32) | (unsigned)e : ~0ull;
             __syncthreads();
-            // de-dup in place, chunk by chunk (a chunk only writes at or before the
-            // positions it read, and the predecessor it compares with keeps its value)
-            if (threadIdx.x == 0) s_out = 0;
-            for (int c0 = 0; c0 < c; c0 += kThreads) {
-                const int e = c0 + threadIdx.x;
-                int col = 0;
-                T w = T(0), om = T(0);
-                unsigned char fl = 0;
-                bool keep = false;
-                if (e < c) {
-                    col = bk.col_b[beg + e];
-                    w = bk.w_b[beg + e];
-                    om = bk.om_b[beg + e];
-                    fl = bk.fl_b[beg + e];
-                    keep = !((fl & kEntMirror) && e > 0 && bk.col_b[beg + e - 1] == col);
+            for (int k = 2; k <= n2; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int t = threadIdx.x; t < n2; t += kThreads) {
+                        const int u = t ^ j;
+                        if (u > t) {
+                            const unsigned long long x = s_key[t], y = s_key[u];
+                            if ((x > y) == ((t & k) == 0)) { s_key[t] = y; s_key[u] = x; }
+                        }
+                    }
+                    __syncthreads();
                 }
-                const unsigned bal = __ballot_sync(kFull, keep);
-                if (lane == 0) s_cnt[warp] = __popc(bal);
-                __syncthreads();
-                int before = s_out;
-                for (int w2 = 0; w2 < warp; ++w2) before += s_cnt[w2];
-                int total = 0;
-                for (int w2 = 0; w2 < kWarps; ++w2) total += s_cnt[w2];
-                const int q = before + __popc(bal & ((1u << lane) - 1u));
-                if (keep) {
-                    bk.col_b[beg + q] = col;
-                    bk.w_b[beg + q] = w;
-                    bk.om_b[beg + q] = om;
-                    bk.fl_b[beg + q] = fl;
-                }
-                push_mirrors(bk, ctrl, keep && (fl & kEntMirror), beg + q, i, lane);
-                __syncthreads();
-                if (threadIdx.x == 0) s_out += total;
-                __syncthreads();
             }
-            if (threadIdx.x == 0) bk.len[i] = s_out;
+            for (int q = threadIdx.x; q < c; q += kThreads) {
+                const int e = beg + (int)(s_key[q] & 0xffffffffu);
+                bk.col_b[beg + q] = bk.col_a[e];
+                bk.w_b[beg + q] = bk.w_a[e];
+                bk.om_b[beg + q] = bk.om_a[e];
+                bk.fl_b[beg + q] = bk.fl_a[e];
+            }
+        } else {
+            // rank of each entry against all keys of the row, streamed in tiles
+            unsigned* s_k32 = reinterpret_cast<unsigned*>(s_key);
+            constexpr int kTile = 2 * kSortSmem;
+            for (int e0 = 0; e0 < c; e0 += kThreads) {
+                const int e = e0 + threadIdx.x;
+                const unsigned ke = e < c ? sort_key(bk, beg + e) : 0xffffffffu;
+                int rank = 0;
+                for (int f0 = 0; f0 < c; f0 += kTile) {
+                    __syncthreads();
+                    for (int f = threadIdx.x; f < kTile; f += kThreads)
+                        s_k32[f] = f0 + f < c ? sort_key(bk, beg + f0 + f) : 0xffffffffu;
+                    __syncthreads();
+                    const int fn = min(kTile, c - f0);
+                    for (int f = 0; f < fn; ++f) rank += (s_k32[f] < ke) ? 1 : 0;
+                }
+                if (e < c) {
+                    bk.col_b[beg + rank] = bk.col_a[beg + e];
+                    bk.w_b[beg + rank] = bk.w_a[beg + e];
+                    bk.om_b[beg + rank] = bk.om_a[beg + e];
+                    bk.fl_b[beg + rank] = bk.fl_a[beg + e];
+                }
+            }
         }
+        __syncthreads();
+        // de-dup in place, chunk by chunk (a chunk only writes at or before the
+        // positions it read, and the predecessor it compares with keeps its value)
+        if (threadIdx.x == 0) s_out = 0;
+        for (int c0 = 0; c0 < c; c0 += kThreads) {
+            const int e = c0 + threadIdx.x;
+            int col = 0;
+            T w = T(0), om = T(0);
+            unsigned char fl = 0;
+            bool keep = false;
+            if (e < c) {
+                col = bk.col_b[beg + e];
+                w = bk.w_b[beg + e];
+                om = bk.om_b[beg + e];
+                fl = bk.fl_b[beg + e];
+                keep = !((fl & kEntMirror) && e > 0 && bk.col_b[beg + e - 1] == col);
+            }
+            const unsigned bal = __ballot_sync(kFull, keep);
+            if (lane == 0) s_cnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = s_out;
+            for (int w2 = 0; w2 < warp; ++w2) before += s_cnt[w2];
+            int total = 0;
+            for (int w2 = 0; w2 < kWarps; ++w2) total += s_cnt[w2];
+            const int q = before + __popc(bal & ((1u << lane) - 1u));
+            if (keep) {
+                bk.col_b[beg + q] = col;
+                bk.w_b[beg + q] = w;
+                bk.om_b[beg + q] = om;
+                bk.fl_b[beg + q] = fl;
+            }
+            push_mirrors(bk, ctrl, keep && (fl & kEntMirror), beg + q, i, lane);
+            __syncthreads();
+            if (threadIdx.x == 0) s_out += total;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) bk.len[i] = s_out;
     }
 }
 
@@ -1065,7 +1108,41 @@ k_fill_w(const T* __restrict__ S, int64_t ld, Csr<T> om, const int4* __restrict_
     }
 }
 
-// G on the candidates (Alg. 2 steps 5-6) and the objective partials of Omega^k.
+// G_ij of one entry (position q of row i) and its share of the objective partials.
+template <typename T, typename A>
+__device__ __forceinline__ void gradient_entry(const Buckets<T>& bk, int i, int q, T lam1, T lam2, A& s_ow, A& s_o2,
+                                               A& s_log, A& s_abs, int& bad) {
+    const int j = bk.col_b[q];
+    const T wij = bk.w_b[q];
+    const T om = bk.om_b[q];
+    const unsigned char fl = bk.fl_b[q];
+    // W_ji: binary search for column i in row j
+    const int jb = bk.off[j];
+    int lo = 0, hi = bk.len[j] - 1, pos = -1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int cm = bk.col_b[jb + mid];
+        if (cm == i) { pos = mid; break; }
+        if (cm < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (pos < 0) { bad |= kFlagBadStructure; return; }
+    const T wji = bk.w_b[jb + pos];
+    // G_ij = (W_ij + W_ji)/2 + lambda2 w_ij - [i=j]/w_ii, one fixed rounding sequence
+    T g = fmaT(lam2, om, T(0.5) * (wij + wji));
+    if (i == j) g -= T(1) / om;
+    bk.g[q] = g;
+    const bool keep = (fl & kEntSupp) || (i == j) || !(fabs(g) <= lam1);
+    if (keep) bk.fl_b[q] = fl | kEntKeep;
+    if (!(g == g) || isinf((double)g)) bad |= kFlagNaN;
+    if (fl & kEntSupp) {
+        acc_add(s_ow, mulT(om, wij));
+        acc_add(s_o2, mulT(om, om));
+        if (i == j) acc_add(s_log, logT(om)); else acc_add(s_abs, fabs(om));
+    }
+}
+
+// G on the candidates (Alg. 2 steps 5-6) and the objective partials of Omega^k:
+// short rows one lane each, long rows (from the bucket scan's list) one warp each.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
@@ -1076,39 +1153,20 @@ k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const bool skip = ctrl->flags != 0;
     const T lam1 = (T)ctrl->lam1, lam2 = (T)ctrl->lam2;
+    const int nlong = skip ? 0 : ctrl->n_long;
     A s_ow{}, s_o2{}, s_log{}, s_abs{};
     int bad = 0;
-    for (int i = skip ? p : gw; i < p; i += nw) {
-        const int beg = bk.off[i], L = bk.len[i];
-        for (int e = lane; e < L; e += 32) {
-            const int j = bk.col_b[beg + e];
-            const T wij = bk.w_b[beg + e];
-            const T om = bk.om_b[beg + e];
-            const unsigned char fl = bk.fl_b[beg + e];
-            // W_ji: binary search for column i in row j
-            const int jb = bk.off[j];
-            int lo = 0, hi = bk.len[j] - 1, pos = -1;
-            while (lo <= hi) {
-                const int mid = (lo + hi) >> 1;
-                const int cm = bk.col_b[jb + mid];
-                if (cm == i) { pos = mid; break; }
-                if (cm < i) lo = mid + 1; else hi = mid - 1;
-            }
-            if (pos < 0) { bad |= kFlagBadStructure; continue; }
-            const T wji = bk.w_b[jb + pos];
-            // G_ij = (W_ij + W_ji)/2 + lambda2 w_ij - [i=j]/w_ii, one fixed rounding sequence
-            T g = fmaT(lam2, om, T(0.5) * (wij + wji));
-            if (i == j) g -= T(1) / om;
-            bk.g[beg + e] = g;
-            const bool keep = (fl & kEntSupp) || (i == j) || !(fabs(g) <= lam1);
-            if (keep) bk.fl_b[beg + e] = fl | kEntKeep;
-            if (!(g == g) || isinf((double)g)) bad |= kFlagNaN;
-            if (fl & kEntSupp) {
-                acc_add(s_ow, mulT(om, wij));
-                acc_add(s_o2, mulT(om, om));
-                if (i == j) acc_add(s_log, logT(om)); else acc_add(s_abs, fabs(om));
-            }
+    for (int base = skip ? p : gw * 32; base < p; base += nw * 32) {
+        const int i = base + lane;
+        if (i < p && bk.cnt[i] <= kShortRow) {
+            const int beg = bk.off[i], L = bk.len[i];
+            for (int e = 0; e < L; ++e) gradient_entry(bk, i, beg + e, lam1, lam2, s_ow, s_o2, s_log, s_abs, bad);
         }
+    }
+    for (int li = gw; li < nlong; li += nw) {
+        const int i = bk.longlist[li];
+        const int beg = bk.off[i], L = bk.len[i];
+        for (int e = lane; e < L; e += 32) gradient_entry(bk, i, beg + e, lam1, lam2, s_ow, s_o2, s_log, s_abs, bad);
     }
     if (bad) atomicOr(&ctrl->flags, bad);
     s_ow = warp_sum(s_ow); s_o2 = warp_sum(s_o2); s_log = warp_sum(s_log); s_abs = warp_sum(s_abs);
@@ -1191,17 +1249,65 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride,
         s_acc[warp][lane][1] = A{};
         s_nb[warp][lane] = 0;
     }
+    __syncwarp();
     A q[M]{};
 
-    const long long U = skip ? 0 : bk.uoff[p];
+    // 1. short rows (at most kShortRow entries), one lane each: the quadratic form
+    //    of a row with entries e0, e1 is d0^2 S_00 + d1^2 S_11 + 2 d0 d1 S_01
+    for (int base = skip ? p : (int)gw * 32; base < p; base += (int)nw * 32) {
+        const int i = base + lane;
+        int L = 0, beg = 0;
+        if (i < p && bk.cnt[i] <= kShortRow) {
+            L = bk.len[i];
+            beg = bk.off[i];
+        }
+        int j0 = 0, j1 = 0;
+        T om0 = T(1), g0 = T(0), om1 = T(1), g1 = T(0);
+        if (L >= 1) { j0 = bk.col_b[beg]; om0 = bk.om_b[beg]; g0 = bk.g[beg]; }
+        if (L >= 2) { j1 = bk.col_b[beg + 1]; om1 = bk.om_b[beg + 1]; g1 = bk.g[beg + 1]; }
+        const T s00 = L >= 1 ? S[(int64_t)j0 * ld + j0] : T(0);
+        const T s11 = L >= 2 ? S[(int64_t)j1 * ld + j1] : T(0);
+        const T s01 = L >= 2 ? S[(int64_t)j0 * ld + j1] : T(0);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const T tau = tau_pow2<T>(h_base + m);
+            const T n0 = prox_entry(om0, g0, tau, tau * lam1, j0 == i);
+            const T n1 = prox_entry(om1, g1, tau, tau * lam1, j1 == i);
+            const T d0 = L >= 1 ? n0 - om0 : T(0);
+            const T d1 = L >= 2 ? n1 - om1 : T(0);
+            T qf = mulT(mulT(d0, d0), s00);
+            qf = fmaT(mulT(d1, d1), s11, qf);
+            qf = fmaT(T(2) * mulT(d0, d1), s01, qf);
+            acc_add(q[m], qf);
+            A n2 = to_acc(mulT(d0, d0));
+            acc_add(n2, mulT(d1, d1));
+            T ph = T(0);
+            bool bad = false;
+            if (L >= 1 && j0 == i) { if (!(n0 > T(0))) bad = true; else ph = phiT(d0 / om0); }
+            if (L >= 2 && j1 == i) { if (!(n1 > T(0))) bad = true; else ph = phiT(d1 / om1); }
+            const A n2w = warp_sum(n2);
+            const A phw = warp_sum(to_acc(ph));
+            const int nbad = __popc(__ballot_sync(kFull, bad));
+            if (lane == 0) {
+                acc_merge(s_acc[warp][m][0], n2w);
+                acc_merge(s_acc[warp][m][1], phw);
+                s_nb[warp][m] += nbad;
+            }
+        }
+    }
+
+    // 2. long rows: equal ranges of the work units of the long-row list
+    const int nlong = skip ? 0 : ctrl->n_long;
+    const long long U = nlong > 0 ? bk.uoff[nlong] : 0;
     long long u = U * gw / nw;
     const long long u1 = U * (gw + 1) / nw;
-    int i = u < u1 ? find_unit_row(bk.uoff, p, u, lane) : 0;
+    int li = u < u1 ? find_unit_row(bk.uoff, nlong, u, lane) : 0;
     while (u < u1) {
-        while (bk.uoff[i + 1] <= u) ++i;
-        const long long uend = min(bk.uoff[i + 1], u1);
+        while (bk.uoff[li + 1] <= u) ++li;
+        const int i = bk.longlist[li];
+        const long long uend = min(bk.uoff[li + 1], u1);
         const int tc = (bk.cnt[i] + 31) >> 5;
-        int k = (int)(u - bk.uoff[i]);
+        int k = (int)(u - bk.uoff[li]);
         int a = 0;
         while (k >= tc - a) { k -= tc - a; ++a; }
         int cb = a + k;
@@ -1482,6 +1588,9 @@ k_ls_decide(const double* __restrict__ part_ls, int n_ls, const double* __restri
 }
 
 // ------------------------------------------------------------------ 4. accept
+// Entries of the accepted iterate: the diagonal, and every candidate the prox
+// at the accepted tau leaves nonzero.  Short rows one lane each, long rows one
+// warp each.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_compact_count(int p, Buckets<T> bk, int* cnt2, const Ctrl* ctrl) {
@@ -1491,7 +1600,22 @@ k_compact_count(int p, Buckets<T> bk, int* cnt2, const Ctrl* ctrl) {
     if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
     const T tau = (T)ctrl->tau;
     const T tl1 = tau * (T)ctrl->lam1;
-    for (int i = gw; i < p; i += nw) {
+    const int nlong = ctrl->n_long;
+    for (int base = gw * 32; base < p; base += nw * 32) {
+        const int i = base + lane;
+        if (i < p && bk.cnt[i] <= kShortRow) {
+            const int beg = bk.off[i], L = bk.len[i];
+            int c = 0;
+            for (int e = 0; e < L; ++e) {
+                const int j = bk.col_b[beg + e];
+                const T v = prox_entry(bk.om_b[beg + e], bk.g[beg + e], tau, tl1, j == i);
+                c += ((j == i) || (v != T(0))) ? 1 : 0;
+            }
+            cnt2[i] = c;
+        }
+    }
+    for (int li = gw; li < nlong; li += nw) {
+        const int i = bk.longlist[li];
         const int beg = bk.off[i], L = bk.len[i];
         int c = 0;
         for (int base = 0; base < L; base += 32) {
@@ -1517,7 +1641,24 @@ k_compact_write(int p, Buckets<T> bk, Csr<T> nx, int cap, const Ctrl* ctrl) {
     if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
     const T tau = (T)ctrl->tau;
     const T tl1 = tau * (T)ctrl->lam1;
-    for (int i = gw; i < p; i += nw) {
+    const int nlong = ctrl->n_long;
+    for (int base = gw * 32; base < p; base += nw * 32) {
+        const int i = base + lane;
+        if (i < p && bk.cnt[i] <= kShortRow) {
+            const int beg = bk.off[i], L = bk.len[i];
+            int out = nx.rp[i];
+            for (int e = 0; e < L; ++e) {
+                const int j = bk.col_b[beg + e];
+                const T v = prox_entry(bk.om_b[beg + e], bk.g[beg + e], tau, tl1, j == i);
+                if ((j == i) || (v != T(0))) {
+                    if (out < cap) { nx.ci[out] = j; nx.cv[out] = v; }
+                    ++out;
+                }
+            }
+        }
+    }
+    for (int li = gw; li < nlong; li += nw) {
+        const int i = bk.longlist[li];
         const int beg = bk.off[i], L = bk.len[i];
         int out = nx.rp[i];
         for (int base = 0; base < L; base += 32) {
@@ -1636,7 +1777,7 @@ void launch_candidates(const IterBufs<T>& b, cudaStream_t s) {
     const int g = 152 * 4;
     k_bucket_count<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
     k_scan<<<1, 1024, 0, s>>>(b.bk.cnt, b.bk.off, b.p, b.bk.cap, b.ctrl, kFlagBucketOverflow,
-                              &b.ctrl->bucket_total, b.bk.uoff);
+                              &b.ctrl->bucket_total, b.bk.uoff, b.bk.longlist);
     k_bucket_scatter<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
     k_bucket_sort<T><<<b.nblk, kThreads, 0, s>>>(b.bk, b.p, b.ctrl);
     k_fill_w<T><<<b.num_sms * 8, kThreads, 0, s>>>(b.S, b.ld, b.cur, b.rinfo, b.rdv, b.bk, b.ctrl);
@@ -1703,7 +1844,7 @@ void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStre
 template <typename T>
 void launch_accept(const IterBufs<T>& b, cudaStream_t s) {
     k_compact_count<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.cnt2, b.ctrl);
-    k_scan<<<1, 1024, 0, s>>>(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr);
+    k_scan<<<1, 1024, 0, s>>>(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr, nullptr);
     k_compact_write<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.next, b.csr_cap, b.ctrl);
     k_converge<<<1, 1, 0, s>>>(b.next.rp, b.p, b.csr_cap, b.eps, b.ctrl);
 }
