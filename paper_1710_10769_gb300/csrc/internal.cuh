@@ -50,6 +50,7 @@ struct Ctrl {
     long long t_point;
     int path_full, pad3_;         // 1 = the estimate staging buffer is full
     int n_long, pad4_;            // rows of the candidate structure with more than kShortRow entries
+    int n_pairs, pad5_;           // (row, column block) items the bound screening keeps
 };
 
 // Rows with at most this many candidate entries (before de-dup) are handled one
@@ -131,6 +132,13 @@ struct IterBufs {
     int screen_grid;          // screening pass: CTAs
     int ls_blocks_per_sm;     // line-search evaluation: resident blocks per SM (0 = occupancy)
     int rows_ctas_per_sm;     // off-diagonal row kernel: CTAs per SM
+    // bound screening of the pure-diagonal rows
+    const T* m1;              // p x nbm: max |S_ij| over column block jb, j != i (null: stream only)
+    int nbm;                  // column blocks of width BJ
+    void* colmax;             // nbm words: max |w_jj| over the pure rows j of each block (T's bits)
+    int2* pairs;              // kept (row, block) items
+    int pairs_cap;            // above this many items the pass streams the upper triangle instead
+    unsigned* rowmask;        // rows with neighbours: bit (position, jb) = the block can emit (p x nbm bits)
     int num_sms;
     // Obs variant: X^T (p x ldx, FP32) and n
     const float* xt;
@@ -172,13 +180,15 @@ template <typename T> void launch_csr_export(const int* rp, const int* ci, const
 void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int64_t* rows,
                      const int64_t* cols, double* out, cudaStream_t s);
 
-constexpr int kLaunchesScreen = 3;
+constexpr int kLaunchesScreen = 7;
 constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 6;
 constexpr int kLaunchesLsWindow = 2;
 constexpr int kLaunchesAccept = 4;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
+// max |S_ij| per (row, column block of width screen_box_cols), off the diagonal
+template <typename T> void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, T* m1, cudaStream_t s);
 template <typename T> int screen_plan(int p, int num_sms, std::vector<long long>& seqoff);
 void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s);
 

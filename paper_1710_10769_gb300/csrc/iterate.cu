@@ -142,6 +142,7 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl, int use_cond, cud
         ctrl->em_count = 0;
         ctrl->n_offrows = 0;
         ctrl->n_mirror = 0;
+        ctrl->n_pairs = 0;
         ctrl->bucket_total = 0;
         ctrl->flags = 0;
         ctrl->ls_accept = -1;
@@ -361,7 +362,7 @@ template <typename T>
 __global__ void __launch_bounds__(kScreenThreads, 1)
 k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* __restrict__ seqoff,
               const int4* __restrict__ rinfo, const T* __restrict__ rdv, const unsigned* __restrict__ pmask,
-              Emit<T> em, Ctrl* __restrict__ ctrl) {
+              int pairs_cap, Emit<T> em, Ctrl* __restrict__ ctrl) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
     constexpr int BJ = Sc::BJ;
@@ -379,6 +380,7 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* 
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kScreenStages);
 
     if (2 * ctrl->n_offrows > p) return;      // dense rows: k_grad_screen_rows covers every row
+    if (ctrl->n_pairs <= pairs_cap) return;   // the bound screening's items cover the pairs
     const T lam1 = (T)ctrl->lam1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x;
@@ -513,10 +515,8 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* 
                     av[q][v] = mulT(dv, sv[v]);
                     bv[q][v] = mulT(cdv[v], sv[v]);
                     const unsigned bit = 1u << (q * V + v);
-                    if (r < p && j < p && j >= r) {
-                        if (j == r) {
-                            if (rpure) ea |= bit;                       // the diagonal: support
-                        } else {
+                    if (r < p && j < p && j > r) {
+                        {
                             const bool ba = rpure && !(fabs(av[q][v]) <= lam1);
                             const bool bb = cpure && !(fabs(bv[q][v]) <= lam1);
                             if (rpure && cpure) {
@@ -539,10 +539,7 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* 
                         const unsigned bit = 1u << (q * V + v);
                         const int r = r0 + q, j = jl + v;
                         const unsigned pf = (pairbits & bit) ? 0x40000000u : 0u;
-                        if (ea & bit) {
-                            if (j == r) put_entry(em, pos, r, (unsigned)j | 0x80000000u, av[q][v], s_dv[m * R + warp * 8 + q]);
-                            else put_entry(em, pos, r, (unsigned)j | pf, av[q][v], T(0));
-                        }
+                        if (ea & bit) put_entry(em, pos, r, (unsigned)j | pf, av[q][v], T(0));
                         if (eb & bit) put_entry(em, pos, j, (unsigned)r | pf, bv[q][v], T(0));
                     }
                 }
@@ -572,6 +569,232 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* 
     }
 }
 
+// ------------------------------------------------------------------ bound screening
+// Once per data load: m1[i][jb] = max |S_ij| over the column block jb (width BJ),
+// j != i, j < p; NaN if the block holds a NaN.  One warp per row.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rowblock_max(const T* __restrict__ S, int64_t ld, int p, int nbm, T* __restrict__ m1) {
+    using Sc = Screen<T>;
+    constexpr int V = Sc::V;
+    constexpr int BJ = Sc::BJ;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = gw; i < p; i += nw) {
+        const T* row = S + (int64_t)i * ld;
+        for (int jb = 0; jb < nbm; ++jb) {
+            const int jl = jb * BJ + lane * V;
+            T x[V];
+            vload(x, row + jl);
+            T mx = T(0);
+            bool nan = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int j = jl + v;
+                const T a = (j < p && j != i) ? fabs(x[v]) : T(0);
+                nan |= !(a == a);
+                mx = a > mx ? a : mx;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T y = __shfl_xor_sync(kFull, mx, o);
+                mx = y > mx ? y : mx;
+            }
+            nan = __any_sync(kFull, nan);
+            if (lane == 0) m1[(int64_t)i * nbm + jb] = nan ? T(NAN) : mx;
+        }
+    }
+}
+
+// NaN-propagating maximum of two non-negative values.
+template <typename T>
+__device__ __forceinline__ T max_nan(T a, T b) { return (a != a || b != b) ? T(NAN) : (a > b ? a : b); }
+
+// Per iteration, after k_row_info: colmax[jb] = max |w_jj| over the pure rows j of
+// column block jb (NaN if one is NaN); one warp per block.
+template <typename T>
+__global__ void k_colmax(int p, int nbm, const int4* __restrict__ rinfo, const T* __restrict__ rdv, void* colmax_raw) {
+    constexpr int BJ = Screen<T>::BJ;
+    T* colmax = static_cast<T*>(colmax_raw);
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int jb = gw; jb < nbm; jb += nw) {
+        T a = T(0);
+        for (int r = lane; r < BJ; r += 32) {
+            const int j = jb * BJ + r;
+            if (j < p && rinfo[j].w) a = max_nan(a, (T)fabs(rdv[j]));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = max_nan(a, __shfl_xor_sync(kFull, a, o));
+        if (lane == 0) colmax[jb] = a;
+    }
+}
+
+// Selection of the (row i, column block jb) items of the upper triangle (some j > i
+// in the block) that can emit: with m = max(|w_ii| if row i is pure, max |w_jj| over
+// the pure rows j of the block), an item is kept iff fl(m * m1[i][jb]) > lambda1.
+// Rounding is monotone, so a dropped item has no j with fl(|w_ii| |S_ij|) > lambda1
+// or fl(|w_jj| |S_ij|) > lambda1: the emitted set is exactly the full screen's.  The
+// pure rows' diagonals (support) are emitted here.  Nothing happens when the rows
+// with neighbours are the majority (k_grad_screen_rows then screens every row).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const T* __restrict__ m1,
+              const int4* __restrict__ rinfo, const T* __restrict__ rdv, const void* colmax_raw,
+              int2* __restrict__ pairs, int cap, Emit<T> em, Ctrl* __restrict__ ctrl) {
+    constexpr int BJ = Screen<T>::BJ;
+    if (2 * ctrl->n_offrows > p) return;
+    const T* colmax = static_cast<const T*>(colmax_raw);
+    const T lam1 = (T)ctrl->lam1;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    // the pure diagonals, 32 rows per warp
+    for (int base = gw * 32; base < p; base += nw * 32) {
+        const int i = base + lane;
+        const bool d = i < p && rinfo[i].w;
+        T w = T(0), dv = T(0);
+        if (d) {
+            dv = rdv[i];
+            w = mulT(dv, S[(int64_t)i * ld + i]);
+        }
+        int pos = warp_reserve<T>(d ? 1 : 0, ctrl, lane);
+        if (d) put_entry(em, pos, i, (unsigned)i | 0x80000000u, w, dv);
+    }
+    // the items, one warp per row
+    for (int i = m1 ? gw : p; i < p; i += nw) {
+        const int4 ri = rinfo[i];
+        const T rm = ri.w ? fabs(rdv[i]) : T(0);
+        const int jb0 = (i + 1) / BJ;
+        for (int c0 = jb0; c0 < nbm; c0 += 32) {
+            const int jb = c0 + lane;
+            bool keep = false;
+            if (jb < nbm && (i + 1) < min(p, (jb + 1) * BJ)) {
+                const T m = max_nan(rm, colmax[jb]);
+                keep = (m != T(0)) && !(mulT(m, m1[(int64_t)i * nbm + jb]) <= lam1);
+            }
+            const unsigned bal = __ballot_sync(kFull, keep);
+            if (!bal) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ctrl->n_pairs, __popc(bal));
+            base = __shfl_sync(kFull, base, 0);
+            const int q = base + __popc(bal & ((1u << lane) - 1u));
+            if (keep && q < cap) pairs[q] = make_int2(i, jb);
+        }
+    }
+}
+
+// The kept items: for j > i in the block, W_ij = w_ii S_ij (row i pure) and W_ji =
+// w_jj S_ij (row j pure), emitted as in the triangle stream (pairs of pure rows from
+// both sides, flagged as paired).  Idle when the items overflowed their list: the
+// triangle stream then covers every pair.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_pair_screen(const T* __restrict__ S, int64_t ld, int p, const int2* __restrict__ pairs, int cap,
+              const int4* __restrict__ rinfo, const T* __restrict__ rdv, const unsigned* __restrict__ pmask,
+              Emit<T> em, Ctrl* __restrict__ ctrl) {
+    using Sc = Screen<T>;
+    constexpr int V = Sc::V;
+    constexpr int BJ = Sc::BJ;
+    if (2 * ctrl->n_offrows > p) return;
+    const int n = ctrl->n_pairs;
+    if (n > cap) return;
+    const T lam1 = (T)ctrl->lam1;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = gw; t < n; t += nw) {
+        const int2 it = pairs[t];
+        const int i = it.x;
+        const int jl = it.y * BJ + lane * V;
+        T sv[V], cdv[V];
+        vload(sv, S + (int64_t)i * ld + jl);
+        vload(cdv, rdv + jl);
+        const unsigned cbits = (pmask[jl >> 5] >> (jl & 31)) & ((1u << V) - 1u);
+        const bool rpure = rinfo[i].w != 0;
+        const T dv = rdv[i];
+        T av[V], bv[V];
+        unsigned ea = 0, eb = 0, pb = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int j = jl + v;
+            av[v] = mulT(dv, sv[v]);
+            bv[v] = mulT(cdv[v], sv[v]);
+            if (j > i && j < p) {
+                const bool cpure = (cbits >> v) & 1u;
+                const bool ba = rpure && !(fabs(av[v]) <= lam1);
+                const bool bb = cpure && !(fabs(bv[v]) <= lam1);
+                if (rpure && cpure) {
+                    if (ba || bb) { ea |= 1u << v; eb |= 1u << v; pb |= 1u << v; }
+                } else {
+                    if (ba) ea |= 1u << v;
+                    if (bb) eb |= 1u << v;
+                }
+            }
+        }
+        const int cnt = __popc(ea) + __popc(eb);
+        if (!__any_sync(kFull, cnt != 0)) continue;
+        int pos = warp_reserve<T>(cnt, ctrl, lane);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int j = jl + v;
+            const unsigned pf = ((pb >> v) & 1u) ? 0x40000000u : 0u;
+            if ((ea >> v) & 1u) put_entry(em, pos, i, (unsigned)j | pf, av[v], T(0));
+            if ((eb >> v) & 1u) put_entry(em, pos, j, (unsigned)i | pf, bv[v], T(0));
+        }
+    }
+}
+
+// Rows with neighbours: which column blocks can emit.  For row i with terms t
+// (the diagonal w_ii at k = i, then w_ik), W_ij is an FMA chain of m terms, so
+// |fl(W_ij)| <= (1 + gamma_m) sum_t |w_t| |S_{k_t j}| <= (1 + gamma_m) B_jb with
+// B_jb = sum_t |w_t| m1[k_t][jb] (computed in FP64) and gamma_m = m u / (1 - m u).
+// Columns j = k_t are the support (and i), whose blocks are always processed; for
+// the other columns the bound holds because m1 excludes each row's diagonal.  A
+// block is skipped iff it holds no support column and (1 + gamma_m) B_jb <= lambda1
+// (NaN keeps it).  Bit (position, jb) in the row kernel's row order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_mask(int p, int nbm, const T* __restrict__ m1, const int4* __restrict__ rinfo, const T* __restrict__ rdv,
+            const int* __restrict__ offlist, const int* __restrict__ ci, const T* __restrict__ cv,
+            unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
+    constexpr int BJ = Screen<T>::BJ;
+    const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
+    const bool all_rows = 2 * ctrl->n_offrows > p;
+    const int nrows = all_rows ? p : ctrl->n_offrows;
+    const double lam1 = ctrl->lam1;
+    const int nwords = (nbm + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int pos = gw; pos < nrows; pos += nw) {
+        const int i = all_rows ? pos : offlist[pos];
+        const int4 ri = rinfo[i];
+        const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
+        const double g = (double)m * u / (1.0 - (double)m * u);
+        const double di = fabs((double)rdv[i]);
+        for (int w0 = 0; w0 < nwords; ++w0) {
+            const int jb = w0 * 32 + lane;
+            bool keep = false;
+            if (jb < nbm) {
+                double B = di * (double)m1[(int64_t)i * nbm + jb];
+                bool sup = (i / BJ) == jb;
+                for (int q = ri.x; q < ri.y; ++q) {
+                    if (q == ri.z) continue;
+                    const int k = ci[q];
+                    B += fabs((double)cv[q]) * (double)m1[(int64_t)k * nbm + jb];
+                    sup |= (k / BJ) == jb;
+                }
+                keep = sup || !((1.0 + g) * B * (1.0 + 1e-12) <= lam1);
+            }
+            const unsigned word = __ballot_sync(kFull, keep);
+            if (lane == 0) rowmask[(int64_t)pos * nwords + w0] = word;
+        }
+    }
+}
+
 // Rows with off-diagonal entries (or, when they are the majority, every row):
 // persistent warps over items (column block, group of 8 listed rows), column
 // block outermost so that in-flight warps share S[:, J] in L2.  The terms of the
@@ -588,7 +811,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 2)
 k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __restrict__ rinfo,
                    const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
-                   const T* __restrict__ cv, Emit<T> em, Ctrl* __restrict__ ctrl) {
+                   const T* __restrict__ cv, const unsigned* __restrict__ rowmask, int nbm, Emit<T> em,
+                   Ctrl* __restrict__ ctrl) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
     constexpr int BJ = Sc::BJ;
@@ -610,6 +834,14 @@ k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __res
         const int jb = (int)(it / ngroups), grp = (int)(it % ngroups);
         const int j0 = jb * BJ;
         const int nr = min(R, nrows - grp * R);
+        if (rowmask) {
+            // skip the item when no row of the group can emit in this block
+            const int nwords = (nbm + 31) / 32;
+            bool need = false;
+            if (lane < nr)
+                need = (rowmask[(int64_t)(grp * R + lane) * nwords + (jb >> 5)] >> (jb & 31)) & 1u;
+            if (!__any_sync(kFull, need)) continue;
+        }
         // lanes < nr: the row's set-up and the length of its term stream
         int slen = 0;
         __syncwarp();
@@ -1760,11 +1992,27 @@ template <typename T>
 void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     constexpr int smem = screen_smem_bytes<T>();
     set_smem_once((const void*)k_grad_screen<T>, smem, sizeof(T) == 8 ? kSmemSlotScreenD : kSmemSlotScreenF);
+    const int warps_grid = b.num_sms * 4;
     k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.pmask, b.offlist, b.ctrl);
+    if (b.m1) k_colmax<T><<<(b.nbm + 7) / 8, kThreads, 0, s>>>(b.p, b.nbm, b.rinfo, b.rdv, b.colmax);
+    k_pair_select<T><<<warps_grid, kThreads, 0, s>>>(b.S, b.ld, b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.colmax, b.pairs,
+                                                     b.pairs_cap, b.em, b.ctrl);
+    if (b.m1)
+        k_pair_screen<T><<<warps_grid, kThreads, 0, s>>>(b.S, b.ld, b.p, b.pairs, b.pairs_cap, b.rinfo, b.rdv, b.pmask,
+                                                         b.em, b.ctrl);
     k_grad_screen<T><<<b.screen_grid, kScreenThreads, smem, s>>>(*b.smap, b.p, b.seqoff, b.rinfo, b.rdv, b.pmask,
-                                                                 b.em, b.ctrl);
+                                                                 b.m1 ? b.pairs_cap : -1, b.em, b.ctrl);
+    if (b.m1)
+        k_rows_mask<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv,
+                                                       b.rowmask, b.ctrl);
     k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
-        b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.em, b.ctrl);
+        b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.rowmask : nullptr, b.nbm, b.em,
+        b.ctrl);
+}
+
+template <typename T>
+void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, T* m1, cudaStream_t s) {
+    k_rowblock_max<T><<<std::max(1, std::min((p + 7) / 8, 152 * 16)), kThreads, 0, s>>>(S, ld, p, nbm, m1);
 }
 
 template <typename T>
@@ -1978,6 +2226,7 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
     template void launch_accept<T>(const IterBufs<T>&, cudaStream_t);                              \
     template void launch_set_identity<T>(Csr<T>, int, cudaStream_t);                               \
     template void launch_row_info<T>(int, Csr<T>, int4*, T*, cudaStream_t);                        \
+    template void launch_rowblock_max<T>(const T*, int64_t, int, int, T*, cudaStream_t);            \
     template int screen_plan<T>(int, int, std::vector<long long>&);                                 \
     template void launch_csr_export<T>(const int*, const int*, const T*, int, int, int64_t*, int32_t*, \
                                        void*, int, cudaStream_t);
