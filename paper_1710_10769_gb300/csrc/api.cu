@@ -109,6 +109,8 @@ struct hpc_ctx {
     int2* pairs_list = nullptr;
     int pairs_cap = 0;
     unsigned* rowmask = nullptr;
+    int2* row_items = nullptr;
+    int row_items_cap = 0;
     int num_sms = 0;
     // scratch for the tensor-core Gram
     void* gram_scratch = nullptr;
@@ -248,12 +250,14 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.pmask = h->pmask;
     b.seqoff = h->seqoff;
     b.screen_grid = h->screen_grid;
-    b.m1 = as<T>(h->m1);
+    b.m1 = static_cast<const unsigned short*>(h->m1);
     b.nbm = h->nbm;
     b.colmax = h->colmax;
     b.pairs = h->pairs_list;
     b.pairs_cap = h->pairs_cap;
     b.rowmask = h->rowmask;
+    b.row_items = h->row_items;
+    b.row_items_cap = h->row_items_cap;
     b.num_sms = h->num_sms;
     b.xt = h->xt;
     b.ldx = h->ldx;
@@ -843,10 +847,10 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
     if (h->m1) {
         if (h->vdt == HPC_F64)
             hpc::launch_rowblock_max<double>(static_cast<const double*>(h->S), h->ld, (int)h->p, h->nbm,
-                                             static_cast<double*>(h->m1), h->stream);
+                                             static_cast<unsigned short*>(h->m1), h->stream);
         else
             hpc::launch_rowblock_max<float>(static_cast<const float*>(h->S), h->ld, (int)h->p, h->nbm,
-                                            static_cast<float*>(h->m1), h->stream);
+                                            static_cast<unsigned short*>(h->m1), h->stream);
         CUDA_TRY(cudaGetLastError());
     }
     if (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) {
@@ -874,7 +878,7 @@ void destroy(hpc_ctx* h) {
                     h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
                     h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long,
-                    h->m1, h->colmax, h->pairs_list, h->rowmask};
+                    h->m1, h->colmax, h->pairs_list, h->row_items, h->rowmask};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -1017,10 +1021,12 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         h->nbm = (int)((p + bj - 1) / bj);
         const int64_t items = p * (int64_t)h->nbm / 2 + p;
         h->pairs_cap = (int)std::min<int64_t>(std::max<int64_t>(items / 4, 1024), 0x7ffffff0);
-        CK(cudaMalloc(&h->m1, (size_t)p * h->nbm * vs));
+        CK(cudaMalloc(&h->m1, (size_t)p * h->nbm * sizeof(unsigned short)));
         CK(cudaMalloc(&h->colmax, (size_t)h->nbm * vs));
         CK(cudaMalloc(&h->pairs_list, (size_t)h->pairs_cap * sizeof(int2)));
         CK(cudaMalloc(&h->rowmask, (size_t)p * ((h->nbm + 31) / 32) * sizeof(unsigned)));
+        h->row_items_cap = (int)std::min<int64_t>((p + 7) / 8 * (int64_t)h->nbm, 0x7ffffff0);
+        CK(cudaMalloc(&h->row_items, (size_t)h->row_items_cap * sizeof(int2)));
     }
     for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->rp[b], (p + 1) * sizeof(int)));
     const int64_t cap0 = o.capacity > 0 ? o.capacity : std::max<int64_t>(32 * p, 1024);

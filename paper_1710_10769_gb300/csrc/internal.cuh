@@ -50,7 +50,7 @@ struct Ctrl {
     long long t_point;
     int path_full, pad3_;         // 1 = the estimate staging buffer is full
     int n_long, pad4_;            // rows of the candidate structure with more than kShortRow entries
-    int n_pairs, pad5_;           // (row, column block) items the bound screening keeps
+    int n_pairs, n_row_items;     // items the bound screening keeps (pure rows; rows with neighbours)
 };
 
 // Rows with at most this many candidate entries (before de-dup) are handled one
@@ -133,12 +133,15 @@ struct IterBufs {
     int ls_blocks_per_sm;     // line-search evaluation: resident blocks per SM (0 = occupancy)
     int rows_ctas_per_sm;     // off-diagonal row kernel: CTAs per SM
     // bound screening of the pure-diagonal rows
-    const T* m1;              // p x nbm: max |S_ij| over column block jb, j != i (null: stream only)
+    const unsigned short* m1; // p x nbm: max |S_ij| over column block jb, j != i, as BF16 rounded up
+                              // (an upper bound; null: no bound screening)
     int nbm;                  // column blocks of width BJ
     void* colmax;             // nbm words: max |w_jj| over the pure rows j of each block (T's bits)
     int2* pairs;              // kept (row, block) items
     int pairs_cap;            // above this many items the pass streams the upper triangle instead
-    unsigned* rowmask;        // rows with neighbours: bit (position, jb) = the block can emit (p x nbm bits)
+    unsigned* rowmask;        // rows with neighbours: bit (position, jb) = the block can emit
+    int2* row_items;          // rows with neighbours: kept (8-row group, block) items of the row kernel
+    int row_items_cap;
     int num_sms;
     // Obs variant: X^T (p x ldx, FP32) and n
     const float* xt;
@@ -180,7 +183,7 @@ template <typename T> void launch_csr_export(const int* rp, const int* ci, const
 void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int64_t* rows,
                      const int64_t* cols, double* out, cudaStream_t s);
 
-constexpr int kLaunchesScreen = 7;
+constexpr int kLaunchesScreen = 8;
 constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 6;
 constexpr int kLaunchesLsWindow = 2;
@@ -188,7 +191,8 @@ constexpr int kLaunchesAccept = 4;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
 // max |S_ij| per (row, column block of width screen_box_cols), off the diagonal
-template <typename T> void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, T* m1, cudaStream_t s);
+template <typename T> void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, unsigned short* m1,
+                                               cudaStream_t s);
 template <typename T> int screen_plan(int p, int num_sms, std::vector<long long>& seqoff);
 void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s);
 

@@ -143,6 +143,7 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl, int use_cond, cud
         ctrl->n_offrows = 0;
         ctrl->n_mirror = 0;
         ctrl->n_pairs = 0;
+        ctrl->n_row_items = 0;
         ctrl->bucket_total = 0;
         ctrl->flags = 0;
         ctrl->ls_accept = -1;
@@ -570,11 +571,22 @@ k_grad_screen(const __grid_constant__ CUtensorMap smap, int p, const long long* 
 }
 
 // ------------------------------------------------------------------ bound screening
+// Non-negative value rounded up to BF16 (an upper bound: 8 bits of mantissa kept,
+// the rest carried upwards), and its float value.
+__device__ __forceinline__ unsigned short bf16_up(float x) {
+    if (!(x == x)) return 0x7fc0;
+    unsigned u = __float_as_uint(x);
+    if (u & 0xffffu) u += 0x10000u;
+    return (unsigned short)(u >> 16);
+}
+__device__ __forceinline__ unsigned short bf16_up(double x) { return bf16_up(__double2float_ru(x)); }
+__device__ __forceinline__ float bf16_val(unsigned short b) { return __uint_as_float((unsigned)b << 16); }
+
 // Once per data load: m1[i][jb] = max |S_ij| over the column block jb (width BJ),
-// j != i, j < p; NaN if the block holds a NaN.  One warp per row.
+// j != i, j < p, rounded up to BF16; NaN if the block holds a NaN.  One warp per row.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_rowblock_max(const T* __restrict__ S, int64_t ld, int p, int nbm, T* __restrict__ m1) {
+k_rowblock_max(const T* __restrict__ S, int64_t ld, int p, int nbm, unsigned short* __restrict__ m1) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
     constexpr int BJ = Sc::BJ;
@@ -602,7 +614,7 @@ k_rowblock_max(const T* __restrict__ S, int64_t ld, int p, int nbm, T* __restric
                 mx = y > mx ? y : mx;
             }
             nan = __any_sync(kFull, nan);
-            if (lane == 0) m1[(int64_t)i * nbm + jb] = nan ? T(NAN) : mx;
+            if (lane == 0) m1[(int64_t)i * nbm + jb] = nan ? (unsigned short)0x7fc0 : bf16_up(mx);
         }
     }
 }
@@ -641,7 +653,7 @@ __global__ void k_colmax(int p, int nbm, const int4* __restrict__ rinfo, const T
 // with neighbours are the majority (k_grad_screen_rows then screens every row).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const T* __restrict__ m1,
+k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const unsigned short* __restrict__ m1,
               const int4* __restrict__ rinfo, const T* __restrict__ rdv, const void* colmax_raw,
               int2* __restrict__ pairs, int cap, Emit<T> em, Ctrl* __restrict__ ctrl) {
     constexpr int BJ = Screen<T>::BJ;
@@ -663,25 +675,37 @@ k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const T* __re
         int pos = warp_reserve<T>(d ? 1 : 0, ctrl, lane);
         if (d) put_entry(em, pos, i, (unsigned)i | 0x80000000u, w, dv);
     }
-    // the items, one warp per row
+    // the items, one warp per row, four 32-block chunks of loads in flight
     for (int i = m1 ? gw : p; i < p; i += nw) {
         const int4 ri = rinfo[i];
         const T rm = ri.w ? fabs(rdv[i]) : T(0);
         const int jb0 = (i + 1) / BJ;
-        for (int c0 = jb0; c0 < nbm; c0 += 32) {
-            const int jb = c0 + lane;
-            bool keep = false;
-            if (jb < nbm && (i + 1) < min(p, (jb + 1) * BJ)) {
-                const T m = max_nan(rm, colmax[jb]);
-                keep = (m != T(0)) && !(mulT(m, m1[(int64_t)i * nbm + jb]) <= lam1);
+        const unsigned short* mrow = m1 + (int64_t)i * nbm;
+        for (int c0 = jb0; c0 < nbm; c0 += 128) {
+            unsigned short mv[4];
+            T cm[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jb = c0 + 32 * u + lane;
+                mv[u] = jb < nbm ? mrow[jb] : (unsigned short)0;
+                cm[u] = jb < nbm ? colmax[jb] : T(0);
             }
-            const unsigned bal = __ballot_sync(kFull, keep);
-            if (!bal) continue;
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&ctrl->n_pairs, __popc(bal));
-            base = __shfl_sync(kFull, base, 0);
-            const int q = base + __popc(bal & ((1u << lane) - 1u));
-            if (keep && q < cap) pairs[q] = make_int2(i, jb);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jb = c0 + 32 * u + lane;
+                bool keep = false;
+                if (jb < nbm && (i + 1) < min(p, (jb + 1) * BJ)) {
+                    const T m = max_nan(rm, cm[u]);
+                    keep = (m != T(0)) && !(mulT(m, (T)bf16_val(mv[u])) <= lam1);
+                }
+                const unsigned bal = __ballot_sync(kFull, keep);
+                if (!bal) continue;
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&ctrl->n_pairs, __popc(bal));
+                base = __shfl_sync(kFull, base, 0);
+                const int q = base + __popc(bal & ((1u << lane) - 1u));
+                if (keep && q < cap) pairs[q] = make_int2(i, jb);
+            }
         }
     }
 }
@@ -747,51 +771,85 @@ k_pair_screen(const T* __restrict__ S, int64_t ld, int p, const int2* __restrict
     }
 }
 
-// Rows with neighbours: which column blocks can emit.  For row i with terms t
-// (the diagonal w_ii at k = i, then w_ik), W_ij is an FMA chain of m terms, so
+// Rows with neighbours: which column blocks can emit.  For row i with terms t (the
+// diagonal w_ii at k = i, then w_ik), W_ij is an FMA chain of m terms, so
 // |fl(W_ij)| <= (1 + gamma_m) sum_t |w_t| |S_{k_t j}| <= (1 + gamma_m) B_jb with
-// B_jb = sum_t |w_t| m1[k_t][jb] (computed in FP64) and gamma_m = m u / (1 - m u).
-// Columns j = k_t are the support (and i), whose blocks are always processed; for
-// the other columns the bound holds because m1 excludes each row's diagonal.  A
-// block is skipped iff it holds no support column and (1 + gamma_m) B_jb <= lambda1
-// (NaN keeps it).  Bit (position, jb) in the row kernel's row order.
+// B_jb = sum_t |w_t| m1[k_t][jb] (FP64; m1 is an upper bound) and gamma_m =
+// m u / (1 - m u).  Columns j = k_t are the support (and i), whose blocks are always
+// processed; for the other columns the bound holds because m1 excludes each row's
+// diagonal.  Row i needs block jb iff the block holds a support column or
+// !((1 + gamma_m) B_jb <= lambda1) (NaN keeps it).  One warp per (row, 32 blocks):
+// bit (position, jb) in the row kernel's row order.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_rows_mask(int p, int nbm, const T* __restrict__ m1, const int4* __restrict__ rinfo, const T* __restrict__ rdv,
-            const int* __restrict__ offlist, const int* __restrict__ ci, const T* __restrict__ cv,
-            unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
+k_rows_mask(int p, int nbm, const unsigned short* __restrict__ m1, const int4* __restrict__ rinfo,
+            const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
+            const T* __restrict__ cv, unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
     constexpr int BJ = Screen<T>::BJ;
     const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
     const bool all_rows = 2 * ctrl->n_offrows > p;
     const int nrows = all_rows ? p : ctrl->n_offrows;
-    const double lam1 = ctrl->lam1;
     const int nwords = (nbm + 31) / 32;
+    const long long work = (long long)nrows * nwords;
+    const double lam1 = ctrl->lam1;
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int pos = gw; pos < nrows; pos += nw) {
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long it = gw; it < work; it += nw) {
+        const int pos = (int)(it / nwords), w0 = (int)(it % nwords);
         const int i = all_rows ? pos : offlist[pos];
         const int4 ri = rinfo[i];
-        const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
-        const double g = (double)m * u / (1.0 - (double)m * u);
-        const double di = fabs((double)rdv[i]);
-        for (int w0 = 0; w0 < nwords; ++w0) {
-            const int jb = w0 * 32 + lane;
-            bool keep = false;
-            if (jb < nbm) {
-                double B = di * (double)m1[(int64_t)i * nbm + jb];
-                bool sup = (i / BJ) == jb;
-                for (int q = ri.x; q < ri.y; ++q) {
-                    if (q == ri.z) continue;
-                    const int k = ci[q];
-                    B += fabs((double)cv[q]) * (double)m1[(int64_t)k * nbm + jb];
+        const int jb = w0 * 32 + lane;
+        bool keep = false;
+        if (jb < nbm) {
+            const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
+            const double g = (double)m * u / (1.0 - (double)m * u);
+            double B = fabs((double)rdv[i]) * (double)bf16_val(m1[(int64_t)i * nbm + jb]);
+            bool sup = (i / BJ) == jb;
+#pragma unroll 4
+            for (int q = ri.x; q < ri.y; ++q) {
+                const int k = ci[q];
+                const double t = fabs((double)cv[q]) * (double)bf16_val(m1[(int64_t)k * nbm + jb]);
+                if (q != ri.z) {
+                    B += t;
                     sup |= (k / BJ) == jb;
                 }
-                keep = sup || !((1.0 + g) * B * (1.0 + 1e-12) <= lam1);
             }
-            const unsigned word = __ballot_sync(kFull, keep);
-            if (lane == 0) rowmask[(int64_t)pos * nwords + w0] = word;
+            keep = sup || !((1.0 + g) * B * (1.0 + 1e-12) <= lam1);
         }
+        const unsigned word = __ballot_sync(kFull, keep);
+        if (lane == 0) rowmask[(int64_t)pos * nwords + w0] = word;
+    }
+}
+
+// The row kernel's item list: (8-row group, block) items any of whose rows needs the
+// block.  One warp per (group, 32 blocks).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_list(int p, int nbm, const unsigned* __restrict__ rowmask, int2* __restrict__ items, int cap,
+            Ctrl* __restrict__ ctrl) {
+    constexpr int R = 8;
+    const bool all_rows = 2 * ctrl->n_offrows > p;
+    const int nrows = all_rows ? p : ctrl->n_offrows;
+    const int ngroups = (nrows + R - 1) / R;
+    const int nwords = (nbm + 31) / 32;
+    const long long work = (long long)ngroups * nwords;
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long it = gw; it < work; it += nw) {
+        const int grp = (int)(it / nwords), w0 = (int)(it % nwords);
+        const int nr = min(R, nrows - grp * R);
+        unsigned word = lane < nr ? rowmask[(int64_t)(grp * R + lane) * nwords + w0] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) word |= __shfl_xor_sync(kFull, word, o);
+        if (!word) continue;
+        const bool keep = (word >> lane) & 1u;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&ctrl->n_row_items, __popc(word));
+        base = __shfl_sync(kFull, base, 0);
+        const int q = base + __popc(word & ((1u << lane) - 1u));
+        if (keep && q < cap) items[q] = make_int2(grp, w0 * 32 + lane);
     }
 }
 
@@ -811,7 +869,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 2)
 k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __restrict__ rinfo,
                    const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
-                   const T* __restrict__ cv, const unsigned* __restrict__ rowmask, int nbm, Emit<T> em,
+                   const T* __restrict__ cv, const int2* __restrict__ row_items, int row_items_cap, Emit<T> em,
                    Ctrl* __restrict__ ctrl) {
     using Sc = Screen<T>;
     constexpr int V = Sc::V;
@@ -827,21 +885,23 @@ k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __res
     const int nrows = all_rows ? p : ctrl->n_offrows;
     const int ngroups = (nrows + R - 1) / R;
     const int nblocks = (p + BJ - 1) / BJ;
-    const long long items = (long long)ngroups * nblocks;
+    // the bound screening's list of kept items, unless it overflowed; else every item
+    const bool listed = row_items && ctrl->n_row_items <= row_items_cap;
+    const long long items = listed ? (long long)ctrl->n_row_items : (long long)ngroups * nblocks;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long it = gw; it < items; it += nw) {
-        const int jb = (int)(it / ngroups), grp = (int)(it % ngroups);
+        int jb, grp;
+        if (listed) {
+            const int2 x = row_items[it];
+            grp = x.x;
+            jb = x.y;
+        } else {
+            jb = (int)(it / ngroups);
+            grp = (int)(it % ngroups);
+        }
         const int j0 = jb * BJ;
         const int nr = min(R, nrows - grp * R);
-        if (rowmask) {
-            // skip the item when no row of the group can emit in this block
-            const int nwords = (nbm + 31) / 32;
-            bool need = false;
-            if (lane < nr)
-                need = (rowmask[(int64_t)(grp * R + lane) * nwords + (jb >> 5)] >> (jb & 31)) & 1u;
-            if (!__any_sync(kFull, need)) continue;
-        }
         // lanes < nr: the row's set-up and the length of its term stream
         int slen = 0;
         __syncwarp();
@@ -2002,16 +2062,18 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
                                                          b.em, b.ctrl);
     k_grad_screen<T><<<b.screen_grid, kScreenThreads, smem, s>>>(*b.smap, b.p, b.seqoff, b.rinfo, b.rdv, b.pmask,
                                                                  b.m1 ? b.pairs_cap : -1, b.em, b.ctrl);
-    if (b.m1)
+    if (b.m1) {
         k_rows_mask<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv,
                                                        b.rowmask, b.ctrl);
+        k_rows_list<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.rowmask, b.row_items, b.row_items_cap, b.ctrl);
+    }
     k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
-        b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.rowmask : nullptr, b.nbm, b.em,
-        b.ctrl);
+        b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.row_items : nullptr,
+        b.row_items_cap, b.em, b.ctrl);
 }
 
 template <typename T>
-void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, T* m1, cudaStream_t s) {
+void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, unsigned short* m1, cudaStream_t s) {
     k_rowblock_max<T><<<std::max(1, std::min((p + 7) / 8, 152 * 16)), kThreads, 0, s>>>(S, ld, p, nbm, m1);
 }
 
@@ -2226,7 +2288,7 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
     template void launch_accept<T>(const IterBufs<T>&, cudaStream_t);                              \
     template void launch_set_identity<T>(Csr<T>, int, cudaStream_t);                               \
     template void launch_row_info<T>(int, Csr<T>, int4*, T*, cudaStream_t);                        \
-    template void launch_rowblock_max<T>(const T*, int64_t, int, int, T*, cudaStream_t);            \
+    template void launch_rowblock_max<T>(const T*, int64_t, int, int, unsigned short*, cudaStream_t); \
     template int screen_plan<T>(int, int, std::vector<long long>&);                                 \
     template void launch_csr_export<T>(const int*, const int*, const T*, int, int, int64_t*, int32_t*, \
                                        void*, int, cudaStream_t);
