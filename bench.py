@@ -216,11 +216,15 @@ def main(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-sample-p", type=int, default=2048)
-    ap.add_argument("--device-loop", type=int, default=0, choices=[0, 1],
-                    help="1: iterations run as one CUDA-graph launch per solve (the per-pass screening "
-                         "time then comes from device timestamps instead of CUDA events)")
+    ap.add_argument("--device-loop", type=int, default=1, choices=[0, 1],
+                    help="1 (default): iterations run as one CUDA-graph launch per solve, the library's "
+                         "default; the Gram is timed with CUDA events either way, the screening pass with "
+                         "device timestamps in this mode (CUDA events with 0)")
     ap.add_argument("--compare-loops", type=int, default=1, choices=[0, 1],
                     help="also time one solve with the other loop driver")
+    ap.add_argument("--x-dtype", default="workload", choices=["workload", "f32", "bf16"],
+                    help="store X in this dtype instead of the workload's (profiling the one-product BF16 Gram "
+                         "at sizes a full ncu capture allows)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="pick the launch shapes with the library's autotuner before the warm-up")
     args = ap.parse_args(argv)
@@ -245,6 +249,11 @@ def main(argv=None):
     prec = {"auto": hpc.PREC_AUTO, "fp32": hpc.PREC_FP32, "bf16x3": hpc.PREC_BF16X3, "tf32": hpc.PREC_TF32}[
         args.precision]
     X = make_x(w, device="cuda")
+    if args.x_dtype != "workload":
+        import dataclasses
+
+        w = dataclasses.replace(w, x_dtype=args.x_dtype)
+        X = X.to(torch.bfloat16 if args.x_dtype == "bf16" else torch.float32)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     xdt = hpc.BF16 if w.x_dtype == "bf16" else hpc.F32
