@@ -180,7 +180,7 @@ struct Cfg {
     static constexpr int kMmaK = 32 / kElem;                           // K per instruction
     static constexpr int kStageBytes = kPieces * (kABytes + kBBytes);
     static constexpr int kStages = (MODE == kModeBf16x3) ? 2 : 4;
-    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers and flags*/;
 };
 
 template <int MODE>
@@ -321,6 +321,180 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     }
 }
 
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent form: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + grid,
+// ... (the banded order of the tile list, so the tiles running together still
+// share X panels in L2) with three roles:
+//   warp 0      TMA producer, running ahead across tile boundaries;
+//   warp 1      MMA issuer, tile t into TMEM accumulator t & 1 (columns 0 / 256);
+//   warps 2-5   epilogue of tile t while tile t + 1 accumulates in the other
+//               buffer; warp w reads TMEM lanes 32 (w % 4) .. +31.
+// acc_full[b] (one commit) and acc_empty[b] (four epilogue warps) hand the
+// buffers over.  Every wait is bounded; an abort stops all roles, drains the
+// loads in flight and frees TMEM.
+constexpr int kPersistThreads = 192;
+
+template <int MODE>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                  const int2* __restrict__ tiles, int ntiles, int k_tiles, int64_t p, int64_t n,
+                  float* __restrict__ S, int64_t lds, int vec_ok) {
+    using C = Cfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
+    uint64_t* empty = full + C::kStages;
+    uint64_t* acc_full = empty + C::kStages;     // [2]
+    uint64_t* acc_empty = acc_full + 2;          // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
+        if (C::kPieces > 1) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 2 * kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    long long issued = 0;   // stages whose TMA loads were issued (producer thread)
+    if (threadIdx.x == 0) {
+        // ---------------- TMA producer
+        long long g = 0;
+        bool ok = true;
+        for (int lt = 0; lt < my_tiles && ok; ++lt) {
+            const int2 tile = tiles[blockIdx.x + (long long)lt * gridDim.x];
+            const int I0 = tile.x * kBM, J0 = tile.y * kBN;
+            for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+                const int s = (int)(g % C::kStages);
+                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 11)) { ok = false; break; }
+                uint8_t* st = smem + s * C::kStageBytes;
+                mbar_expect_tx(&full[s], C::kStageBytes);
+                const int kc = kt * C::kBK;
+                for (int pc = 0; pc < C::kPieces; ++pc) {
+                    const CUtensorMap* m = pc == 0 ? &map_hi : &map_lo;
+                    uint8_t* a = st + pc * (kABytes + kBBytes);
+                    uint8_t* b = a + kABytes;
+                    tma_load_2d(a, m, &full[s], kc, I0);
+                    tma_load_2d(b, m, &full[s], kc, J0);
+                    tma_load_2d(b + kABytes, m, &full[s], kc, J0 + kBM);
+                }
+                ++issued;
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = instr_desc<MODE>();
+        long long g = 0;
+        bool ok = true;
+        for (int lt = 0; lt < my_tiles && ok; ++lt) {
+            const int b = lt & 1;
+            if (!mbar_wait(&acc_empty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u, abort_flag, 12)) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + (uint32_t)(b * kTmemCols);
+            for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+                const int s = (int)(g % C::kStages);
+                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                if (!mbar_wait(&full[s], ph, abort_flag, 13)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+                const uint32_t a_hi = st, b_hi = st + kABytes;
+                const uint32_t a_lo = st + (kABytes + kBBytes), b_lo = a_lo + kABytes;
+#pragma unroll
+                for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+                    umma<MODE>(acc, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
+                    if constexpr (C::kTerms == 3) {
+                        umma<MODE>(acc, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+                        umma<MODE>(acc, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+                    }
+                }
+                umma_commit(&empty[s]);
+            }
+            umma_commit(&acc_full[b]);
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> registers -> S (owner rule i <= j, plus mirror)
+        const float dn = (float)n;
+        const int q4 = warp & 3;
+        const int r = q4 * 32 + lane;
+        for (int lt = 0; lt < my_tiles; ++lt) {
+            const int b = lt & 1;
+            bool have = mbar_wait(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, 14) && !*abort_flag;
+            have = __all_sync(kFull, have);
+            if (!have) break;
+            tc_fence_after();
+            const int2 tile = tiles[blockIdx.x + (long long)lt * gridDim.x];
+            const int I0 = tile.x * kBM, J0 = tile.y * kBN;
+            const int64_t i = I0 + r;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kBN; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kTmemCols + c0), v);
+                tmem_ld_wait();
+                if (i >= p) continue;
+                const int64_t jb = J0 + c0;
+                float o[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) o[q] = __uint_as_float(v[q]) / dn;
+                if (vec_ok && jb >= i && jb + 31 < p) {
+                    float4* dst = reinterpret_cast<float4*>(S + i * lds + jb);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int64_t j = jb + q;
+                        if (j >= i && j < p) S[i * lds + j] = o[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int64_t j = jb + q;
+                    if (j > i && j < p) S[j * lds + i] = o[q];
+                }
+            }
+            // this warp's lanes of buffer b are read: hand the buffer back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_local(&acc_empty[b]);
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && threadIdx.x == 0) {
+        // drain: bounded waits for the loads this CTA issued, so no copy lands after exit
+        for (long long g = issued > C::kStages ? issued - C::kStages : 0; g < issued; ++g) {
+            const int s = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+            for (long long it = 0; it < (1ll << 22) && !mbar_try_wait(&full[s], ph); ++it) __nanosleep(64);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * kTmemCols);
+    }
+}
+
 // Transpose X (n x p) into K-major panels (p_pad x n_pad) of the MMA input type.
 template <typename TX, int MODE>
 __global__ void __launch_bounds__(256)
@@ -429,7 +603,7 @@ bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
 
 template <int MODE>
 cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles, int64_t n, int64_t p, float* S,
-                        int64_t lds, cudaStream_t s) {
+                        int64_t lds, cudaStream_t s, bool persistent = false) {
     using C = Cfg<MODE>;
     CUtensorMap mh, ml;
     std::memset(&mh, 0, sizeof mh);
@@ -437,11 +611,23 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
     if (!make_map(&mh, hi, MODE, g)) return cudaErrorNotSupported;
     if (C::kPieces > 1 && !make_map(&ml, lo, MODE, g)) return cudaErrorNotSupported;
     if (C::kPieces == 1) ml = mh;
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-    if (e != cudaSuccess) return e;
     const int k_tiles = (int)(g.n_pad / C::kBK);
     // float4 row stores need 16-byte aligned rows: lds % 4 == 0 and an aligned base
     const int vec_ok = (lds % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0) ? 1 : 0;
+    if (persistent) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_gram_tc_persist<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        const int grid = (int)std::min<int64_t>(g.ntiles, sms);
+        k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n,
+                                                                       S, lds, vec_ok);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
     k_gram_tc<MODE><<<(unsigned)g.ntiles, 128, C::kSmem, s>>>(mh, ml, tiles, k_tiles, p, n, S, lds, vec_ok);
     return cudaGetLastError();
 }
@@ -488,9 +674,9 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (launches) *launches += 2;
-    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s);
-    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s);
-    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s);
+    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, true);
+    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, true);
+    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, true);
 }
 
 int gram_tc_take_error() {
