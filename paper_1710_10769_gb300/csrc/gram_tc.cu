@@ -531,6 +531,46 @@ k_prep(const TX* __restrict__ X, int64_t n, int64_t p, void* __restrict__ hi, vo
     }
 }
 
+// BF16 X into the BF16 panel: a plain transpose, 64 x 64 elements per block with
+// 16-byte loads and stores (vec: rows of X start on 16-byte boundaries).  The
+// shared tile's rows are padded to 72 elements (144 bytes, a multiple of 16).
+__global__ void __launch_bounds__(256)
+k_prep_bf16(const uint16_t* __restrict__ X, int64_t n, int64_t p, uint16_t* __restrict__ out, int64_t n_pad,
+            int vec) {
+    __shared__ __align__(16) uint16_t t[64][72];
+    const int64_t k0 = (int64_t)blockIdx.x * 64, i0 = (int64_t)blockIdx.y * 64;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int r = tid / 8 + rr * 32, c = (tid % 8) * 8;
+        const int64_t k = k0 + r, i = i0 + c;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (k < n) {
+            if (vec && i + 8 <= p) {
+                v = *reinterpret_cast<const uint4*>(X + k * p + i);
+            } else {
+                uint16_t e[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e[q] = (i + q < p) ? X[k * p + i + q] : (uint16_t)0;
+                v = make_uint4(e[0] | ((uint32_t)e[1] << 16), e[2] | ((uint32_t)e[3] << 16),
+                               e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
+            }
+        }
+        *reinterpret_cast<uint4*>(&t[r][c]) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int ri = tid / 8 + rr * 32, kc = (tid % 8) * 8;
+        const int64_t i = i0 + ri, k = k0 + kc;
+        if (k >= n_pad) continue;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] = t[kc + 2 * q][ri] | ((uint32_t)t[kc + 2 * q + 1][ri] << 16);
+        *reinterpret_cast<uint4*>(out + i * n_pad + k) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -635,8 +675,18 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
 template <typename TX>
 void launch_prep(const void* X, int mode, int64_t n, int64_t p, void* hi, void* lo, const Geometry& g,
                  cudaStream_t s) {
-    dim3 grid((unsigned)((g.n_pad + 31) / 32), (unsigned)((g.p_pad + 31) / 32));
     const TX* x = static_cast<const TX*>(X);
+    if constexpr (std::is_same<TX, __nv_bfloat16>::value) {
+        if (mode == kModeBf16) {
+            // n_pad and p_pad are multiples of 64: every block's tile is inside the panel
+            const int vec = (p % 8 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0) ? 1 : 0;
+            dim3 g64((unsigned)(g.n_pad / 64), (unsigned)(g.p_pad / 64));
+            k_prep_bf16<<<g64, 256, 0, s>>>(reinterpret_cast<const uint16_t*>(X), n, p, static_cast<uint16_t*>(hi),
+                                            g.n_pad, vec);
+            return;
+        }
+    }
+    dim3 grid((unsigned)((g.n_pad + 31) / 32), (unsigned)((g.p_pad + 31) / 32));
     if (mode == kModeTf32) k_prep<TX, kModeTf32><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
     else if (mode == kModeBf16x3) k_prep<TX, kModeBf16x3><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
     else k_prep<TX, kModeBf16><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);

@@ -49,8 +49,10 @@ def test_bf16x3_on_fp32_x(lib, n, p):
     assert torch.isnan(S[:, p:]).all()
 
 
-@pytest.mark.parametrize("n,p", [(300, 700), (33, 257)])
+@pytest.mark.parametrize("n,p", [(300, 700), (33, 257), (130, 1024), (65, 520)])
 def test_single_product_on_bf16_x(lib, n, p):
+    """p % 8 == 0 takes the 16-byte transpose of X into the panel; the others the
+    element-wise edges; n not a multiple of 64 leaves a zero-padded K tail."""
     import torch
 
     rng = np.random.default_rng(p)
