@@ -109,6 +109,8 @@ typedef struct {
     int64_t kernel_launches;  /* kernels this library launched during the call           */
     int64_t capacity_regrows; /* times the candidate buffers grew                        */
     int64_t candidates;       /* candidate entries of the last gradient pass             */
+    double  ms_gram_kernel;   /* of ms_gram: the tensor-core product kernel alone (without
+                                 the transpose of X into its operand panels)             */
 } hpc_stats;
 
 /* Fill *opt with the defaults listed above. */

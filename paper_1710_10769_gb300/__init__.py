@@ -37,7 +37,8 @@ class Stats(C.Structure):
                 ("status", C.c_int32), ("accepted_halvings", C.c_int32), ("f", C.c_double),
                 ("F", C.c_double), ("rel_change", C.c_double), ("ms_total", C.c_double),
                 ("ms_gram", C.c_double), ("ms_grad_pass", C.c_double), ("grad_pass_launches", C.c_int64),
-                ("kernel_launches", C.c_int64), ("capacity_regrows", C.c_int64), ("candidates", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("capacity_regrows", C.c_int64), ("candidates", C.c_int64),
+                ("ms_gram_kernel", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -120,6 +120,8 @@ struct hpc_ctx {
     cudaEvent_t ev_scr0 = nullptr, ev_scr1 = nullptr;
     int64_t regrows = 0;
     double ms_gram = 0.0;
+    double ms_gram_kernel = 0.0;
+    cudaEvent_t ev_gk = nullptr;     // between the transpose and the tensor-core product
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
     hpc_tuning tune{16, 8, 0, 2};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
@@ -647,6 +649,7 @@ int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s, bool fre
     s->grad_pass_launches = c.iter_attempts;
     s->kernel_launches = c.iter_attempts * loop_launches(h) + 2 * c.ls_windows;
     s->ms_gram = h->ms_gram;
+    s->ms_gram_kernel = h->ms_gram_kernel;
     s->capacity_regrows = h->regrows - regrows0;
     s->status = status;
     return status;
@@ -746,6 +749,7 @@ int solve_batch_device(const std::vector<hpc_ctx*>& hs, std::vector<int>& status
         s.grad_pass_launches = c.iter_attempts;
         s.kernel_launches = c.iter_attempts * loop_launches(h) + 2 * c.ls_windows;
         s.ms_gram = h->ms_gram;
+        s.ms_gram_kernel = h->ms_gram_kernel;
         s.capacity_regrows = h->regrows - regrows0[t];
         s.status = stt;
         status[t] = stt;
@@ -780,6 +784,7 @@ int run_iterations(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* st) {
     s->ls_trials = h->h_ctrl->ls_trials;
     s->nnz = h->nnz;
     s->ms_gram = h->ms_gram;
+    s->ms_gram_kernel = h->ms_gram_kernel;
     s->capacity_regrows = h->regrows - regrows0;
     s->status = status;
     return status;
@@ -821,7 +826,8 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
             h->gram_scratch_bytes = need;
         }
         e = hpc::gram_tc(Xd, xdt, h->n, h->p, static_cast<float*>(h->S), h->ld, prec, h->gram_scratch,
-                         h->gram_scratch_bytes, h->stream, &launches, h->tune.gram_band);
+                         h->gram_scratch_bytes, h->stream, &launches, h->tune.gram_band,
+                         h->opt.timing ? h->ev_gk : nullptr);
         if (e == cudaErrorNotSupported) {
             if (tmp) cudaFree(tmp);
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
@@ -839,6 +845,12 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
         h->ms_gram = ms;
+        h->ms_gram_kernel = ms;
+        if (h->variant == HPC_COV && (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32)) {
+            float mk = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&mk, h->ev_gk, h->ev[3]));
+            h->ms_gram_kernel = mk;
+        }
     }
     if (tmp) {
         CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -883,6 +895,7 @@ void destroy(hpc_ctx* h) {
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     if (h->ev_scr0) cudaEventDestroy(h->ev_scr0);
+    if (h->ev_gk) cudaEventDestroy(h->ev_gk);
     if (h->ev_scr1) cudaEventDestroy(h->ev_scr1);
     delete h;
 }
@@ -1052,6 +1065,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     std::memset(h->h_ctrl, 0, sizeof(hpc::Ctrl));
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&h->ev_scr0));
+    CK(cudaEventCreate(&h->ev_gk));
     CK(cudaEventCreate(&h->ev_scr1));
 #undef CK
     if (X) {

@@ -700,7 +700,8 @@ size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision) {
 }
 
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
-                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band) {
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band,
+                    cudaEvent_t before_kernel) {
     if (band <= 0) band = kBand;
     if (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32) return cudaErrorInvalidValue;
     if (xdt == HPC_F64) return cudaErrorNotSupported;
@@ -724,6 +725,7 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (launches) *launches += 2;
+    if (before_kernel && (e = cudaEventRecord(before_kernel, s)) != cudaSuccess) return e;
     if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, true);
     if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, true);
     return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, true);

@@ -243,8 +243,10 @@ void launch_reduce_parts(const double* part, int nb, double* out, cudaStream_t s
 cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int sdt, int64_t lds,
                       cudaStream_t s, int* launches);
 // band: row blocks per band of the tile order (<= 0: the default, 16).
+// before_kernel (nullable) is recorded on s between the transpose and the product kernel.
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
-                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0);
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0,
+                    cudaEvent_t before_kernel = nullptr);
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();
