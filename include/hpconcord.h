@@ -103,7 +103,9 @@ typedef struct {
     double  F;                /* f + lambda1 * sum_{i!=j} |w_ij| at that iterate          */
     double  rel_change;       /* last ||Omega^{k+1}-Omega^k||_F / ||Omega^k||_F          */
     double  ms_total;         /* device time of the call                                 */
-    double  ms_gram;          /* device time of the dense product that formed S (load)   */
+    double  ms_gram;          /* device time of the data load: the dense product that
+                                 formed S, with its operand transpose and the block
+                                 maxima of the bound screening                          */
     double  ms_grad_pass;     /* device time in the gradient-screening pass (Cov SpMM)   */
     int64_t grad_pass_launches;
     int64_t kernel_launches;  /* kernels this library launched during the call           */
@@ -345,7 +347,18 @@ typedef struct {
     int32_t ls_blocks_per_sm;  /* resident blocks per SM of the line-search
                                   evaluation, 0 = as many as fit (2)               */
     int32_t rows_ctas_per_sm;  /* CTAs per SM of the off-diagonal row kernel, 1..4 (2) */
+    int32_t gram_maxima;       /* 1: the tensor-core Gram's epilogue writes the bound
+                                  screening's block maxima; 0: a pass over S after it (1) */
+    int32_t reserved_;
 } hpc_tuning;
+
+/* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max
+ * |S_ij| over the column block jb (columns 128 jb .. 128 jb + 127, 64 in FP64 mode)
+ * with j != i and j < p, rounded up to BF16 (bit patterns), nb = ceil(p / block).
+ * The tensor-core Gram writes them from its epilogue; the other modes by a pass
+ * over S.  Query with out == NULL (p * nb into *count_inout); HPC_ERR_CAPACITY if
+ * *count_inout is smaller; HPC_ERR_NOT_IMPLEMENTED for the Obs variant. */
+int hpc_get_block_maxima(hpc_handle h, int64_t* count_inout, uint16_t* out);
 
 /* Read / replace a handle's tuning.  HPC_ERR_ARG for a value out of range. */
 int hpc_get_tuning(hpc_handle h, hpc_tuning* t);
@@ -354,9 +367,10 @@ int hpc_set_tuning(hpc_handle h, const hpc_tuning* t);
 #define HPC_TUNE_MAX_TRIALS 48
 typedef struct {
     int32_t knob;              /* 0 gram_band, 1 ls_window, 2 ls_blocks_per_sm,
-                                  3 rows_ctas_per_sm                                */
+                                  3 rows_ctas_per_sm, 4 gram_maxima                 */
     int32_t value;
-    double  ms;                /* Gram: one launch; the others: one iteration        */
+    double  ms;                /* Gram knobs: one data load (transpose, product, block
+                                  maxima); the others: one iteration                */
 } hpc_tune_trial;
 
 typedef struct {

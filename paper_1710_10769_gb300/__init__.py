@@ -73,14 +73,14 @@ class HypergradInfo(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("gram_band", C.c_int32), ("ls_window", C.c_int32), ("ls_blocks_per_sm", C.c_int32),
-                ("rows_ctas_per_sm", C.c_int32)]
+                ("rows_ctas_per_sm", C.c_int32), ("gram_maxima", C.c_int32), ("reserved_", C.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved_"}
 
 
 TUNE_MAX_TRIALS = 48
-TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm")
+TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm", "gram_maxima")
 
 
 class TuneTrial(C.Structure):
@@ -129,6 +129,7 @@ _SIGS = {
     "hpc_gram": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int, C.c_int64, C.c_int, _P]),
     "hpc_gram_noalloc": (C.c_int, [_P, C.c_int, C.c_int64, C.c_int64, _P, C.c_int64, C.c_int, _P]),
     "hpc_get_tuning": (C.c_int, [_P, _P]),
+    "hpc_get_block_maxima": (C.c_int, [_P, C.POINTER(C.c_int64), _P]),
     "hpc_set_tuning": (C.c_int, [_P, _P]),
     "hpc_autotune": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int64, _P, _P]),
 }
@@ -274,6 +275,16 @@ class Solver:
         st = self._lib.hpc_iterate(self._h, int(k), C.byref(self.stats))
         _check(st, "hpc_iterate")
         return self.stats
+
+    def block_maxima(self) -> np.ndarray:
+        """hpc_get_block_maxima: the bound screening's max |S_ij| per (row, column block)
+        as float32 (decoded from the BF16 bit patterns), shape (p, nb)."""
+        c = C.c_int64(0)
+        _check(self._lib.hpc_get_block_maxima(self._h, C.byref(c), None), "hpc_get_block_maxima")
+        out = np.empty(c.value, np.uint16)
+        _check(self._lib.hpc_get_block_maxima(self._h, C.byref(c), out.ctypes.data_as(C.c_void_p)),
+               "hpc_get_block_maxima")
+        return (out.astype(np.uint32) << 16).view(np.float32).reshape(self.p, -1)
 
     def get_tuning(self) -> dict:
         t = Tuning()

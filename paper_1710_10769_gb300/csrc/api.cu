@@ -122,8 +122,9 @@ struct hpc_ctx {
     double ms_gram = 0.0;
     double ms_gram_kernel = 0.0;
     cudaEvent_t ev_gk = nullptr;     // between the transpose and the tensor-core product
+    cudaEvent_t ev_ge = nullptr;     // end of the product (before the block-maxima pass)
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{16, 8, 0, 2};
+    hpc_tuning tune{16, 8, 0, 2, 1, 0};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -827,7 +828,8 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         }
         e = hpc::gram_tc(Xd, xdt, h->n, h->p, static_cast<float*>(h->S), h->ld, prec, h->gram_scratch,
                          h->gram_scratch_bytes, h->stream, &launches, h->tune.gram_band,
-                         h->opt.timing ? h->ev_gk : nullptr);
+                         h->opt.timing ? h->ev_gk : nullptr,
+                         h->tune.gram_maxima ? static_cast<uint16_t*>(h->m1) : nullptr, h->nbm);
         if (e == cudaErrorNotSupported) {
             if (tmp) cudaFree(tmp);
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
@@ -839,24 +841,11 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         if (tmp) cudaFree(tmp);
         return HPC_ERR_CUDA;
     }
-    if (h->opt.timing) {
-        CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
-        CUDA_TRY(cudaEventSynchronize(h->ev[3]));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
-        h->ms_gram = ms;
-        h->ms_gram_kernel = ms;
-        if (h->variant == HPC_COV && (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32)) {
-            float mk = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&mk, h->ev_gk, h->ev[3]));
-            h->ms_gram_kernel = mk;
-        }
-    }
-    if (tmp) {
-        CUDA_TRY(cudaStreamSynchronize(h->stream));
-        cudaFree(tmp);
-    }
-    if (h->m1) {
+    // block maxima of the bound screening: from the Gram's epilogue, or a pass over S
+    const bool maxima_from_gram =
+        h->variant == HPC_COV && (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) && h->tune.gram_maxima;
+    if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_ge, h->stream));
+    if (h->m1 && !maxima_from_gram) {
         if (h->vdt == HPC_F64)
             hpc::launch_rowblock_max<double>(static_cast<const double*>(h->S), h->ld, (int)h->p, h->nbm,
                                              static_cast<unsigned short*>(h->m1), h->stream);
@@ -864,6 +853,21 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
             hpc::launch_rowblock_max<float>(static_cast<const float*>(h->S), h->ld, (int)h->p, h->nbm,
                                             static_cast<unsigned short*>(h->m1), h->stream);
         CUDA_TRY(cudaGetLastError());
+    }
+    if (h->opt.timing) {
+        CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
+        CUDA_TRY(cudaEventSynchronize(h->ev[3]));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]));
+        h->ms_gram = ms;
+        const bool tc = h->variant == HPC_COV && (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32);
+        float mk = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&mk, tc ? h->ev_gk : h->ev[2], h->ev_ge));
+        h->ms_gram_kernel = mk;
+    }
+    if (tmp) {
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        cudaFree(tmp);
     }
     if (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) {
         CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -896,6 +900,7 @@ void destroy(hpc_ctx* h) {
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     if (h->ev_scr0) cudaEventDestroy(h->ev_scr0);
     if (h->ev_gk) cudaEventDestroy(h->ev_gk);
+    if (h->ev_ge) cudaEventDestroy(h->ev_ge);
     if (h->ev_scr1) cudaEventDestroy(h->ev_scr1);
     delete h;
 }
@@ -1066,6 +1071,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
     CK(cudaEventCreate(&h->ev_scr0));
     CK(cudaEventCreate(&h->ev_gk));
+    CK(cudaEventCreate(&h->ev_ge));
     CK(cudaEventCreate(&h->ev_scr1));
 #undef CK
     if (X) {
@@ -1644,7 +1650,8 @@ int hypergrad_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double cg_t
 bool tuning_ok(const hpc_tuning& t) {
     const int w = t.ls_window;
     return t.gram_band >= 1 && t.gram_band <= 256 && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16) &&
-           t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4;
+           t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4 &&
+           (t.gram_maxima == 0 || t.gram_maxima == 1);
 }
 
 void apply_tuning(hpc_ctx* h, const hpc_tuning& t) {
@@ -1740,7 +1747,24 @@ int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, h
             if (ms < best_ms) { best_ms = ms; best_band = b; }
         }
         t.gram_band = best_band;
-        apply_tuning(h, t);
+        // block maxima from the Gram's epilogue or from a pass over S, whole loads timed
+        double best_mx = 1e300;
+        int best_fused = t.gram_maxima;
+        for (int f : {1, 0}) {
+            hpc_tuning u = t;
+            u.gram_maxima = f;
+            apply_tuning(h, u);
+            double ms = 1e300;
+            for (int rep_i = 0; rep_i < 2 && status == HPC_OK; ++rep_i) {
+                status = load_x(h, X, xdt, on_host);
+                ms = std::min(ms, h->ms_gram);
+            }
+            if (status != HPC_OK) break;
+            add_trial(rep, 4, f, ms);
+            if (ms < best_mx) { best_mx = ms; best_fused = f; }
+        }
+        t.gram_maxima = best_fused;
+        apply_tuning(h, t);     // S and the maxima of the last trial are the same either way
     } else if (X) {
         status = load_x(h, X, xdt, on_host);
     }
@@ -1779,6 +1803,18 @@ int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, h
 }  // namespace
 
 extern "C" {
+
+int hpc_get_block_maxima(hpc_handle h, int64_t* count_inout, uint16_t* out) {
+    if (!h || !count_inout) return HPC_ERR_ARG;
+    if (!h->m1 || !h->loaded) return HPC_ERR_NOT_IMPLEMENTED;
+    const int64_t total = h->p * (int64_t)h->nbm;
+    if (!out) { *count_inout = total; return HPC_OK; }
+    if (*count_inout < total) { *count_inout = total; return HPC_ERR_CAPACITY; }
+    CUDA_TRY(cudaMemcpyAsync(out, h->m1, total * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *count_inout = total;
+    return HPC_OK;
+}
 
 int hpc_get_tuning(hpc_handle h, hpc_tuning* t) {
     if (!h || !t) return HPC_ERR_ARG;

@@ -180,7 +180,8 @@ struct Cfg {
     static constexpr int kMmaK = 32 / kElem;                           // K per instruction
     static constexpr int kStageBytes = kPieces * (kABytes + kBBytes);
     static constexpr int kStages = (MODE == kModeBf16x3) ? 2 : 4;
-    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers and flags*/;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers and flags*/
+                                 + kBN * 4 /*column maxima of the persistent epilogue*/;
 };
 
 template <int MODE>
@@ -321,6 +322,13 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     }
 }
 
+// Non-negative float rounded up to BF16 (an upper bound).
+__device__ __forceinline__ uint16_t bf16_up_f(float x) {
+    uint32_t u = __float_as_uint(x);
+    if (u & 0xffffu) u += 0x10000u;
+    return (uint16_t)(u >> 16);
+}
+
 __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -341,7 +349,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                   const int2* __restrict__ tiles, int ntiles, int k_tiles, int64_t p, int64_t n,
-                  float* __restrict__ S, int64_t lds, int vec_ok) {
+                  float* __restrict__ S, int64_t lds, int vec_ok, uint16_t* __restrict__ m1, int nbm) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -351,6 +359,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
     uint64_t* acc_empty = acc_full + 2;          // [2]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    unsigned* s_colmax = reinterpret_cast<unsigned*>(smem + C::kStages * C::kStageBytes + 256);   // [kBN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -432,28 +441,93 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
         }
     } else if (warp >= 2) {
         // ---------------- epilogue: TMEM -> registers -> S (owner rule i <= j, plus mirror)
+        // and, with m1, the block maxima max |S_ij| (128-column blocks, j != i, BF16
+        // rounded up): row maxima for the tile's own row blocks at or right of the
+        // diagonal (this tile holds all 128 columns of them, the diagonal block's
+        // lower part included), column maxima (over the tile's 128 rows, all above j)
+        // for the rows j whose block lies right of the tile's row block.
         const float dn = (float)n;
         const int q4 = warp & 3;
         const int r = q4 * 32 + lane;
+        const int et = threadIdx.x - 64;                    // 0..127 over the epilogue warps
+        // After an abort a warp keeps walking its tiles (every wait then fails at once)
+        // without touching TMEM or memory, so the four epilogue warps always meet at
+        // the named barrier the same number of times.  Column maxima: cleared once
+        // here, accumulated per tile, read after the first barrier of the tile and
+        // cleared again by their readers before the second.
+        if (m1) {
+            for (int c = et; c < kBN; c += 128) s_colmax[c] = 0u;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
         for (int lt = 0; lt < my_tiles; ++lt) {
             const int b = lt & 1;
-            bool have = mbar_wait(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, 14) && !*abort_flag;
+            bool have = !*abort_flag && mbar_wait(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, 14);
             have = __all_sync(kFull, have);
-            if (!have) break;
+            if (!have) {
+                if (m1) {
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                }
+                continue;
+            }
             tc_fence_after();
             const int2 tile = tiles[blockIdx.x + (long long)lt * gridDim.x];
             const int I0 = tile.x * kBM, J0 = tile.y * kBN;
             const int64_t i = I0 + r;
+            const int ib = I0 / 128;                       // the tile's row block in 128-column units
+            float rmax[kBN / 128];
+            bool rnan[kBN / 128];
+#pragma unroll
+            for (int h = 0; h < kBN / 128; ++h) { rmax[h] = 0.f; rnan[h] = false; }
 #pragma unroll 1
             for (int c0 = 0; c0 < kBN; c0 += 32) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kTmemCols + c0), v);
                 tmem_ld_wait();
-                if (i >= p) continue;
                 const int64_t jb = J0 + c0;
                 float o[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q) o[q] = __uint_as_float(v[q]) / dn;
+                if (m1) {
+                    const int h = c0 / 128;
+                    const int cb = (int)(jb / 128);        // this chunk's 128-column block
+                    if (i < p && cb >= ib) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const int64_t j = jb + q;
+                            if (j < p && j != i) {
+                                const float a = fabsf(o[q]);
+                                rnan[h] |= !(a == a);
+                                rmax[h] = a > rmax[h] ? a : rmax[h];
+                            }
+                        }
+                    }
+                    if (cb > ib) {
+                        // max over the tile's rows of column jb + q: reduce-scatter, lane q keeps column q
+                        float a[32];
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const float x = (i < p) ? fabsf(o[q]) : 0.f;
+                            a[q] = (x == x) ? x : __int_as_float(0x7fc00000);
+                        }
+#pragma unroll
+                        for (int w = 16; w >= 1; w >>= 1) {
+                            const bool upper = (lane & w) != 0;
+#pragma unroll
+                            for (int q = 0; q < w; ++q) {
+                                const float mine = upper ? a[q + w] : a[q];
+                                const float send = upper ? a[q] : a[q + w];
+                                const float got = __shfl_xor_sync(kFull, send, w);
+                                a[q] = (mine != mine || got != got) ? __int_as_float(0x7fc00000)
+                                                                   : (mine > got ? mine : got);
+                            }
+                        }
+                        // lane l now holds the warp's maximum of column jb + l
+                        const float x = a[0];
+                        atomicMax(&s_colmax[c0 + lane], (x != x) ? 0x7fc00000u : __float_as_uint(x));
+                    }
+                }
+                if (i >= p) continue;
                 if (vec_ok && jb >= i && jb + 31 < p) {
                     float4* dst = reinterpret_cast<float4*>(S + i * lds + jb);
 #pragma unroll
@@ -470,6 +544,24 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
                     const int64_t j = jb + q;
                     if (j > i && j < p) S[j * lds + i] = o[q];
                 }
+            }
+            if (m1) {
+#pragma unroll
+                for (int h = 0; h < kBN / 128; ++h) {
+                    const int cb = J0 / 128 + h;
+                    if (i < p && cb >= ib && cb < nbm)
+                        m1[i * nbm + cb] = rnan[h] ? (uint16_t)0x7fc0 : bf16_up_f(rmax[h]);
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                for (int c = et; c < kBN; c += 128) {
+                    const int64_t j = J0 + c;
+                    if (j < p && (int)(j / 128) > ib) {
+                        const float x = __uint_as_float(s_colmax[c]);
+                        m1[j * nbm + ib] = (x != x) ? (uint16_t)0x7fc0 : bf16_up_f(x);
+                    }
+                    s_colmax[c] = 0u;
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
             }
             // this warp's lanes of buffer b are read: hand the buffer back
             tc_fence_before();
@@ -643,7 +735,7 @@ bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
 
 template <int MODE>
 cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles, int64_t n, int64_t p, float* S,
-                        int64_t lds, cudaStream_t s, bool persistent = false) {
+                        int64_t lds, cudaStream_t s, bool persistent = false, uint16_t* m1 = nullptr, int nbm = 0) {
     using C = Cfg<MODE>;
     CUtensorMap mh, ml;
     std::memset(&mh, 0, sizeof mh);
@@ -663,7 +755,7 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         const int grid = (int)std::min<int64_t>(g.ntiles, sms);
         k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n,
-                                                                       S, lds, vec_ok);
+                                                                       S, lds, vec_ok, m1, nbm);
         return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
@@ -701,7 +793,7 @@ size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision) {
 
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band,
-                    cudaEvent_t before_kernel) {
+                    cudaEvent_t before_kernel, uint16_t* m1, int nbm) {
     if (band <= 0) band = kBand;
     if (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32) return cudaErrorInvalidValue;
     if (xdt == HPC_F64) return cudaErrorNotSupported;
@@ -726,9 +818,9 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     if (e != cudaSuccess) return e;
     if (launches) *launches += 2;
     if (before_kernel && (e = cudaEventRecord(before_kernel, s)) != cudaSuccess) return e;
-    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, true);
-    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, true);
-    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, true);
+    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, true, m1, nbm);
+    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, true, m1, nbm);
+    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, true, m1, nbm);
 }
 
 int gram_tc_take_error() {

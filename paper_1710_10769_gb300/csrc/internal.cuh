@@ -244,9 +244,11 @@ cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int
                       cudaStream_t s, int* launches);
 // band: row blocks per band of the tile order (<= 0: the default, 16).
 // before_kernel (nullable) is recorded on s between the transpose and the product kernel.
+// m1 (nullable, p x nbm): also write max |S_ij| per (row, 128-column block), j != i,
+// rounded up to BF16, from the product's epilogue.
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0,
-                    cudaEvent_t before_kernel = nullptr);
+                    cudaEvent_t before_kernel = nullptr, uint16_t* m1 = nullptr, int nbm = 0);
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();

@@ -25,7 +25,7 @@ def test_autotune_picks_valid_shapes_and_keeps_results(lib):
     with lib.Solver(X, 0.12, 0.1, precision=lib.PREC_BF16X3, eps=1e-7) as s:
         best, trials = s.autotune(X, iters=2)
         knobs = {t["knob"] for t in trials}
-        assert {"gram_band", "ls_window", "rows_ctas_per_sm", "ls_blocks_per_sm"} <= knobs
+        assert {"gram_band", "gram_maxima", "ls_window", "rows_ctas_per_sm", "ls_blocks_per_sm"} <= knobs
         assert all(t["ms"] > 0 for t in trials)
         assert s.get_tuning() == best
         assert best["ls_window"] in (2, 4, 8, 16) and 1 <= best["rows_ctas_per_sm"] <= 4
@@ -51,7 +51,7 @@ def test_autotune_restores_the_iterate(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(gram_band=0), dict(ls_window=3), dict(rows_ctas_per_sm=5),
-                                 dict(ls_blocks_per_sm=-1)])
+                                 dict(ls_blocks_per_sm=-1), dict(gram_maxima=2)])
 def test_set_tuning_rejects_out_of_range(lib, bad):
     torch = _torch()
     X = torch.as_tensor(small_problem(64, 40, 3.0, seed=1).astype(np.float32)).cuda()
@@ -59,4 +59,6 @@ def test_set_tuning_rejects_out_of_range(lib, bad):
         with pytest.raises(lib.HpcError):
             s.set_tuning(**bad)
         s.set_tuning(gram_band=4, ls_window=2, rows_ctas_per_sm=1, ls_blocks_per_sm=1)
-        assert s.get_tuning() == dict(gram_band=4, ls_window=2, ls_blocks_per_sm=1, rows_ctas_per_sm=1)
+        t = s.get_tuning()
+        assert {k: t[k] for k in ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm")} == \
+            dict(gram_band=4, ls_window=2, ls_blocks_per_sm=1, rows_ctas_per_sm=1)
