@@ -123,6 +123,9 @@ struct hpc_ctx {
     double ms_gram_kernel = 0.0;
     cudaEvent_t ev_gk = nullptr;     // between the transpose and the tensor-core product
     cudaEvent_t ev_ge = nullptr;     // end of the product (before the block-maxima pass)
+    // device staging buffer for X passed from the host (kept between loads)
+    void* x_stage = nullptr;
+    size_t x_stage_bytes = 0;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
     hpc_tuning tune{16, 8, 0, 2, 1, 0};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
@@ -799,12 +802,18 @@ int load_x_obs(hpc_ctx* h, const void* Xd) {
 
 int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
     const void* Xd = X;
-    void* tmp = nullptr;
     const size_t xbytes = (size_t)h->n * h->p * dtype_size(xdt);
     if (on_host) {
-        CUDA_TRY(cudaMalloc(&tmp, xbytes));
-        CUDA_TRY(cudaMemcpyAsync(tmp, X, xbytes, cudaMemcpyHostToDevice, h->stream));
-        Xd = tmp;
+        // the staging buffer is kept for the next load of the same size or smaller
+        if (xbytes > h->x_stage_bytes) {
+            if (h->x_stage) cudaFree(h->x_stage);
+            h->x_stage = nullptr;
+            h->x_stage_bytes = 0;
+            CUDA_TRY(cudaMalloc(&h->x_stage, xbytes));
+            h->x_stage_bytes = xbytes;
+        }
+        CUDA_TRY(cudaMemcpyAsync(h->x_stage, X, xbytes, cudaMemcpyHostToDevice, h->stream));
+        Xd = h->x_stage;
     }
     int launches = 0;
     if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev[2], h->stream));
@@ -831,14 +840,12 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
                          h->opt.timing ? h->ev_gk : nullptr,
                          h->tune.gram_maxima ? static_cast<uint16_t*>(h->m1) : nullptr, h->nbm);
         if (e == cudaErrorNotSupported) {
-            if (tmp) cudaFree(tmp);
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
             return HPC_ERR_NOT_IMPLEMENTED;
         }
     }
     if (e != cudaSuccess) {
         set_cuda_error(e, "gram", __LINE__);
-        if (tmp) cudaFree(tmp);
         return HPC_ERR_CUDA;
     }
     // block maxima of the bound screening: from the Gram's epilogue, or a pass over S
@@ -865,10 +872,7 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         CUDA_TRY(cudaEventElapsedTime(&mk, tc ? h->ev_gk : h->ev[2], h->ev_ge));
         h->ms_gram_kernel = mk;
     }
-    if (tmp) {
-        CUDA_TRY(cudaStreamSynchronize(h->stream));
-        cudaFree(tmp);
-    }
+
     if (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) {
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         const int w = hpc::gram_tc_take_error();
@@ -894,7 +898,7 @@ void destroy(hpc_ctx* h) {
                     h->bk_cur, h->bk_len, h->cnt2, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
                     h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long,
-                    h->m1, h->colmax, h->pairs_list, h->row_items, h->rowmask};
+                    h->m1, h->colmax, h->pairs_list, h->row_items, h->rowmask, h->x_stage};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
