@@ -111,11 +111,11 @@ def reduce_over_ranks(ms, iters, pg, device):
     return float(t[0]), float(u[0])
 
 
-def measured_traffic(kernel, p, n):
+def measured_traffic(kernel, p, n, tag=""):
     """DRAM bytes per launch of `kernel` ("screen_pass" or "gram") from the committed
-    ncu summary (profiles/roofline_traffic.txt, a 1-pass capture at the full
-    workload); None when it was taken on other sizes or another version of the
-    kernel's source."""
+    ncu summary (profiles/roofline_traffic.txt, 1-pass captures at the full
+    workload); None when it was taken on other sizes, another version of the
+    kernel's source, or (tag) another launch configuration of the kernel."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
@@ -127,7 +127,7 @@ def measured_traffic(kernel, p, n):
                 return None
         if int(kv[f"{kernel}.p"]) != p or int(kv[f"{kernel}.n"]) != n:
             return None
-        return float(kv[f"{kernel}.dram_bytes"])
+        return float(kv[f"{kernel}.{tag}dram_bytes" if tag else f"{kernel}.dram_bytes"])
     except Exception:
         return None
 
@@ -317,7 +317,9 @@ def main(argv=None):
         g_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # SIMT FP32 FMA peak at the max SM clock
         g_bound, g_src = "alu", "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
     roof_gram = {"kernel": "gram", "bound": g_bound, "achieved": g_achieved, "peak": g_peak, "unit": "TFLOP/s",
-                 "frac": g_achieved / g_peak, "traffic": measured_traffic("gram", p, n), "peak_source": g_src,
+                 "frac": g_achieved / g_peak, "peak_source": g_src,
+                 # the Gram's traffic depends on its tile-order band and on whether it writes the block maxima
+                 "traffic": measured_traffic("gram", p, n, f"band{tuning['gram_band']}.maxima{tuning['gram_maxima']}."),
                  "ms_per_launch": gram_ms / len(recs),
                  "load_ms_per_step": sum(r["ms_load_step"] for r in recs) / len(recs)}
     per = scr_ms / max(scr_launches, 1) / 1000.0

@@ -383,8 +383,10 @@ typedef struct {
 
 /* The autotuner: times the candidate values of each knob on the handle's own
  * problem and keeps the fastest, one knob after another.
- *  - If X != NULL (same conventions as hpc_load_x) the Gram is timed once per
- *    gram_band candidate; S is rewritten with identical values.
+ *  - If X != NULL (same conventions as hpc_load_x) the whole load is timed for
+ *    each gram_band candidate, then for gram_maxima 1 and 0: three round-robin
+ *    rounds over the candidates, each keeping its fastest load (the SM clock
+ *    drifts under the power cap).  S is rewritten with identical values.
  *  - The iteration knobs are timed over `iters` outer iterations (>= 1) each,
  *    every trial starting from the handle's current iterate, which is restored
  *    afterwards: the call leaves the estimate unchanged.  Start from a

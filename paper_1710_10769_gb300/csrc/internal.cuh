@@ -88,6 +88,13 @@ struct Emit {
 };
 
 // Per-row candidate structure (symmetric pattern, columns ascending after sort).
+// Per-tile sums of the multi-block row-count scan: entries, long rows, their line-search units.
+struct ScanPart {
+    int s;
+    int l;
+    long long u;
+};
+
 template <typename T>
 struct Buckets {
     int* cnt;     // p: entries per row before de-dup
@@ -115,6 +122,7 @@ struct IterBufs {
     Emit<T> em;
     Buckets<T> bk;
     int* cnt2;            // p: per-row entry counts of the accepted iterate
+    ScanPart* scan_part;  // ceil(p / 4096): per-tile sums of the row-count scans
     double* part_obj;     // objective partials   [nblk][4]
     double* part_ls;      // line-search partials [nblk][16][4]
     int nblk;             // blocks of the warp-per-row kernels
@@ -183,11 +191,11 @@ template <typename T> void launch_csr_export(const int* rp, const int* ci, const
 void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int64_t* rows,
                      const int64_t* cols, double* out, cudaStream_t s);
 
-constexpr int kLaunchesScreen = 8;
+constexpr int kLaunchesScreen = 7;
 constexpr int kLaunchesBegin = 1;
-constexpr int kLaunchesCandidates = 6;
+constexpr int kLaunchesCandidates = 7;
 constexpr int kLaunchesLsWindow = 2;
-constexpr int kLaunchesAccept = 4;
+constexpr int kLaunchesAccept = 5;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
 // max |S_ij| per (row, column block of width screen_box_cols), off the diagonal

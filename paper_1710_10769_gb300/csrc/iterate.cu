@@ -239,20 +239,32 @@ constexpr int screen_smem_bytes() {
 
 __host__ __device__ __forceinline__ int screen_seq_chunk(int s, int nc) { return (s & 1) ? nc - 1 - (s >> 1) : (s >> 1); }
 
+// NaN-propagating maximum of two non-negative values.
+template <typename T>
+__device__ __forceinline__ T max_nan(T a, T b) { return (a != a || b != b) ? T(NAN) : (a > b ? a : b); }
+
 // Per row of the iterate: CSR bounds, position of the diagonal (-1 if absent,
 // found by binary search: columns ascend), its value, and the pure-diagonal bit
 // (pmask, one word per 32 rows); rows with off-diagonal entries (or no
 // diagonal) are appended to offlist (any order: the screening output is
-// re-sorted per row downstream).
+// re-sorted per row downstream).  With colmax (the bound screening), also
+// colmax[jb] = max |w_jj| over the pure rows j of column block jb (NaN if one is
+// NaN): the launch gives every thread one row, so the BJ rows of a block are in
+// one CTA (256 is a multiple of BJ) and are reduced in shared memory.
 template <typename T>
-__global__ void k_row_info(int p, Csr<T> om, int4* __restrict__ rinfo, T* __restrict__ rdv,
-                           unsigned* __restrict__ pmask, int* __restrict__ offlist, Ctrl* __restrict__ ctrl) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256)
+k_row_info(int p, Csr<T> om, int4* __restrict__ rinfo, T* __restrict__ rdv, unsigned* __restrict__ pmask,
+           int* __restrict__ offlist, Ctrl* __restrict__ ctrl, T* __restrict__ colmax, int nbm) {
+    constexpr int BJ = 32 * (16 / (int)sizeof(T));
+    __shared__ T s_cm[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    if (lane == 0) s_cm[warp] = T(0);
     for (int base = gw * 32; base < p; base += nw * 32) {
         const int i = base + lane;
         bool pure = false;
+        T dv = T(0);
         if (i < p) {
             const int rb = om.rp[i], re = om.rp[i + 1];
             int lo = rb, hi = re;
@@ -261,7 +273,7 @@ __global__ void k_row_info(int p, Csr<T> om, int4* __restrict__ rinfo, T* __rest
                 if (om.ci[mid] < i) lo = mid + 1; else hi = mid;
             }
             const int pd = (lo < re && om.ci[lo] == i) ? lo : -1;
-            const T dv = pd >= 0 ? om.cv[pd] : T(0);
+            dv = pd >= 0 ? om.cv[pd] : T(0);
             pure = (re - rb == 1) && pd >= 0;
             rinfo[i] = make_int4(rb, re, pd, pure ? 1 : 0);
             rdv[i] = dv;
@@ -269,6 +281,25 @@ __global__ void k_row_info(int p, Csr<T> om, int4* __restrict__ rinfo, T* __rest
         }
         const unsigned word = __ballot_sync(kFull, pure);
         if (pmask && lane == 0) pmask[base >> 5] = word;
+        if (colmax) {
+            T a = pure ? (T)fabs(dv) : T(0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a = max_nan(a, __shfl_xor_sync(kFull, a, o));
+            if (lane == 0) s_cm[warp] = a;
+        }
+    }
+    if (colmax) {
+        __syncthreads();
+        constexpr int kPerBlock = 256 / BJ, kWarpsPerCol = BJ / 32;
+        if (threadIdx.x < kPerBlock) {
+            const int jb = blockIdx.x * kPerBlock + threadIdx.x;
+            if (jb < nbm) {
+                T m = T(0);
+#pragma unroll
+                for (int w = 0; w < kWarpsPerCol; ++w) m = max_nan(m, s_cm[threadIdx.x * kWarpsPerCol + w]);
+                colmax[jb] = m;
+            }
+        }
     }
 }
 
@@ -582,6 +613,18 @@ __device__ __forceinline__ unsigned short bf16_up(float x) {
 __device__ __forceinline__ unsigned short bf16_up(double x) { return bf16_up(__double2float_ru(x)); }
 __device__ __forceinline__ float bf16_val(unsigned short b) { return __uint_as_float((unsigned)b << 16); }
 
+// Eight BF16 block maxima from one 16-byte load (element 0 in the low half of x).
+__device__ __forceinline__ void bf16x8(const uint4 v, float (&f)[8]) {
+    f[0] = __uint_as_float(v.x << 16);
+    f[1] = __uint_as_float(v.x & 0xffff0000u);
+    f[2] = __uint_as_float(v.y << 16);
+    f[3] = __uint_as_float(v.y & 0xffff0000u);
+    f[4] = __uint_as_float(v.z << 16);
+    f[5] = __uint_as_float(v.z & 0xffff0000u);
+    f[6] = __uint_as_float(v.w << 16);
+    f[7] = __uint_as_float(v.w & 0xffff0000u);
+}
+
 // Once per data load: m1[i][jb] = max |S_ij| over the column block jb (width BJ),
 // j != i, j < p, rounded up to BF16; NaN if the block holds a NaN.  One warp per row.
 template <typename T>
@@ -619,31 +662,6 @@ k_rowblock_max(const T* __restrict__ S, int64_t ld, int p, int nbm, unsigned sho
     }
 }
 
-// NaN-propagating maximum of two non-negative values.
-template <typename T>
-__device__ __forceinline__ T max_nan(T a, T b) { return (a != a || b != b) ? T(NAN) : (a > b ? a : b); }
-
-// Per iteration, after k_row_info: colmax[jb] = max |w_jj| over the pure rows j of
-// column block jb (NaN if one is NaN); one warp per block.
-template <typename T>
-__global__ void k_colmax(int p, int nbm, const int4* __restrict__ rinfo, const T* __restrict__ rdv, void* colmax_raw) {
-    constexpr int BJ = Screen<T>::BJ;
-    T* colmax = static_cast<T*>(colmax_raw);
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int jb = gw; jb < nbm; jb += nw) {
-        T a = T(0);
-        for (int r = lane; r < BJ; r += 32) {
-            const int j = jb * BJ + r;
-            if (j < p && rinfo[j].w) a = max_nan(a, (T)fabs(rdv[j]));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a = max_nan(a, __shfl_xor_sync(kFull, a, o));
-        if (lane == 0) colmax[jb] = a;
-    }
-}
-
 // Selection of the (row i, column block jb) items of the upper triangle (some j > i
 // in the block) that can emit: with m = max(|w_ii| if row i is pure, max |w_jj| over
 // the pure rows j of the block), an item is kept iff fl(m * m1[i][jb]) > lambda1.
@@ -674,6 +692,50 @@ k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const unsigne
         }
         int pos = warp_reserve<T>(d ? 1 : 0, ctrl, lane);
         if (d) put_entry(em, pos, i, (unsigned)i | 0x80000000u, w, dv);
+    }
+    if (m1 && nbm % 8 == 0 && (long long)p * (nbm / 8) < 0x7fffffffLL - (long long)gridDim.x * blockDim.x) {
+        // the items, one thread per (row, 8-block group) with one 16-byte load of the
+        // row's maxima (rows 16-byte aligned: nbm % 8 == 0); groups left of the upper
+        // triangle load nothing.  The loop bound is uniform over each block.
+        const int ng = nbm / 8;
+        const int total = p * ng;
+        const int nthreads = gridDim.x * blockDim.x;
+        for (int base = blockIdx.x * blockDim.x; base < total; base += nthreads) {
+            const int it = base + threadIdx.x;
+            unsigned bits = 0;
+            int i = 0, jl = 0;
+            if (it < total) {
+                i = it / ng;
+                jl = (it - i * ng) * 8;
+                const int jb0 = (i + 1) / BJ;
+                if (jl + 8 > jb0) {
+                    const bool pure = rinfo[i].w != 0;
+                    const T rm = pure ? fabs(rdv[i]) : T(0);
+                    float f[8];
+                    bf16x8(*reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + jl), f);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const int jb = jl + v;
+                        if ((i + 1) < min(p, (jb + 1) * BJ)) {
+                            const T m = max_nan(rm, colmax[jb]);
+                            if ((m != T(0)) && !(mulT(m, (T)f[v]) <= lam1)) bits |= 1u << v;
+                        }
+                    }
+                }
+            }
+            const int c = __popc(bits);
+            if (!__any_sync(kFull, c != 0)) continue;
+            const int incl = warp_incl_scan(c, lane);
+            int q = 0;
+            if (lane == 31) q = atomicAdd(&ctrl->n_pairs, incl);
+            q = __shfl_sync(kFull, q, 31) + incl - c;
+            for (int v = 0; bits; ++v, bits >>= 1)
+                if (bits & 1u) {
+                    if (q < cap) pairs[q] = make_int2(i, jl + v);
+                    ++q;
+                }
+        }
+        return;
     }
     // the items, one warp per row, four 32-block chunks of loads in flight
     for (int i = m1 ? gw : p; i < p; i += nw) {
@@ -774,24 +836,33 @@ k_pair_screen(const T* __restrict__ S, int64_t ld, int p, const int2* __restrict
 // Rows with neighbours: which column blocks can emit.  For row i with terms t (the
 // diagonal w_ii at k = i, then w_ik), W_ij is an FMA chain of m terms, so
 // |fl(W_ij)| <= (1 + gamma_m) sum_t |w_t| |S_{k_t j}| <= (1 + gamma_m) B_jb with
-// B_jb = sum_t |w_t| m1[k_t][jb] (FP64; m1 is an upper bound) and gamma_m =
-// m u / (1 - m u).  Columns j = k_t are the support (and i), whose blocks are always
-// processed; for the other columns the bound holds because m1 excludes each row's
-// diagonal.  Row i needs block jb iff the block holds a support column or
-// !((1 + gamma_m) B_jb <= lambda1) (NaN keeps it).  One warp per (row, 32 blocks):
-// bit (position, jb) in the row kernel's row order.
+// B_jb = sum_t |w_t| m1[k_t][jb] (m1 is an upper bound) and gamma_m = m u / (1 - m u).
+// The bound is evaluated in FP32 with every operation rounded towards +inf (the
+// operands are non-negative, so the result is at least the exact value) and
+// compared with the emission threshold in T; for m u <= 2^-10, gamma_m <=
+// m u (1 + 2^-9), and longer chains keep every block.  Columns j = k_t are the
+// support (and i), whose blocks are always processed; for the other columns the
+// bound holds because m1 excludes each row's diagonal.  Row i needs block jb iff
+// the block holds a support column or !(bound <= lambda1) (NaN keeps it).  One warp
+// per (row, 32 blocks): bit (position, jb) in the row kernel's row order.
+template <typename T>
+__device__ __forceinline__ float abs_up(T x) {
+    if constexpr (sizeof(T) == 4) return fabsf(x);
+    else return __double2float_ru(fabs(x));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_rows_mask(int p, int nbm, const unsigned short* __restrict__ m1, const int4* __restrict__ rinfo,
             const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
             const T* __restrict__ cv, unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
     constexpr int BJ = Screen<T>::BJ;
-    const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
+    const float u = sizeof(T) == 4 ? 0x1p-24f : 0x1p-53f;
     const bool all_rows = 2 * ctrl->n_offrows > p;
     const int nrows = all_rows ? p : ctrl->n_offrows;
     const int nwords = (nbm + 31) / 32;
     const long long work = (long long)nrows * nwords;
-    const double lam1 = ctrl->lam1;
+    const T lam1 = (T)ctrl->lam1;
     const int lane = threadIdx.x & 31;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -803,22 +874,101 @@ k_rows_mask(int p, int nbm, const unsigned short* __restrict__ m1, const int4* _
         bool keep = false;
         if (jb < nbm) {
             const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
-            const double g = (double)m * u / (1.0 - (double)m * u);
-            double B = fabs((double)rdv[i]) * (double)bf16_val(m1[(int64_t)i * nbm + jb]);
+            const float mu = (float)m * u;                       // exact: m < 2^24, u a power of 2
+            float B = __fmul_ru(abs_up(rdv[i]), bf16_val(m1[(int64_t)i * nbm + jb]));
             bool sup = (i / BJ) == jb;
 #pragma unroll 4
             for (int q = ri.x; q < ri.y; ++q) {
                 const int k = ci[q];
-                const double t = fabs((double)cv[q]) * (double)bf16_val(m1[(int64_t)k * nbm + jb]);
                 if (q != ri.z) {
-                    B += t;
+                    B = __fadd_ru(B, __fmul_ru(abs_up(cv[q]), bf16_val(m1[(int64_t)k * nbm + jb])));
                     sup |= (k / BJ) == jb;
                 }
             }
-            keep = sup || !((1.0 + g) * B * (1.0 + 1e-12) <= lam1);
+            const float bound = __fmul_ru(__fadd_ru(1.0f, __fmul_ru(mu, 1.001953125f)), B);
+            bool below;
+            if constexpr (sizeof(T) == 4) below = bound <= lam1;
+            else below = (double)bound <= lam1;
+            keep = sup || mu > 0x1p-10f || !below;
         }
         const unsigned word = __ballot_sync(kFull, keep);
         if (lane == 0) rowmask[(int64_t)pos * nwords + w0] = word;
+    }
+}
+
+// k_rows_mask for nbm % 8 == 0, when every m1 row is 16-byte aligned: one warp per
+// row; in each chunk of 256 blocks lane l covers blocks c0 + 8l .. c0 + 8l + 7 with
+// one 16-byte load of m1 per term.  The row's terms are fetched 32 at a time and
+// broadcast; a term that is not one (the diagonal's CSR slot, the tail of the last
+// fetch) becomes the weight 0 on row i itself, which adds 0 (or the NaN that row i's
+// own diagonal term already adds).  Same bound, rounding and word layout as
+// k_rows_mask.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_mask_v(int p, int nbm, const unsigned short* __restrict__ m1, const int4* __restrict__ rinfo,
+              const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
+              const T* __restrict__ cv, unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
+    constexpr int BJ = Screen<T>::BJ;
+    const float u = sizeof(T) == 4 ? 0x1p-24f : 0x1p-53f;
+    const bool all_rows = 2 * ctrl->n_offrows > p;
+    const int nrows = all_rows ? p : ctrl->n_offrows;
+    const int nwords = (nbm + 31) / 32;
+    const T lam1 = (T)ctrl->lam1;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int pos = gw; pos < nrows; pos += nw) {
+        const int i = all_rows ? pos : offlist[pos];
+        const int4 ri = rinfo[i];
+        const float di = abs_up(rdv[i]);
+        const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
+        const float mu = (float)m * u;                           // exact: m < 2^24, u a power of 2
+        const float g1 = __fadd_ru(1.0f, __fmul_ru(mu, 1.001953125f));
+        const bool long_chain = mu > 0x1p-10f;
+        const int ib = i / BJ;
+        for (int c0 = 0; c0 < nbm; c0 += 256) {
+            const int jl = c0 + lane * 8;
+            const bool act = jl < nbm;
+            float B[8], f[8];
+            unsigned sup = (unsigned)(ib - jl) < 8u ? 1u << (ib - jl) : 0u;
+            bf16x8(act ? *reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + jl) : make_uint4(0, 0, 0, 0), f);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) B[v] = __fmul_ru(di, f[v]);
+            for (int q0 = ri.x; q0 < ri.y; q0 += 32) {
+                const int q = q0 + lane;
+                const bool term = q < ri.y && q != ri.z;
+                const int kq = term ? ci[q] : i;
+                const float wq = term ? abs_up(cv[q]) : 0.0f;
+                const int nt = min(32, ri.y - q0);
+#pragma unroll 4
+                for (int t = 0; t < nt; ++t) {
+                    const int k = __shfl_sync(kFull, kq, t);
+                    const float w = __shfl_sync(kFull, wq, t);
+                    bf16x8(act ? *reinterpret_cast<const uint4*>(m1 + (int64_t)k * nbm + jl) : make_uint4(0, 0, 0, 0),
+                           f);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) B[v] = __fadd_ru(B[v], __fmul_ru(w, f[v]));
+                    const int kb = k / BJ;
+                    if ((unsigned)(kb - jl) < 8u) sup |= 1u << (kb - jl);
+                }
+            }
+            unsigned bits = 0;
+            if (act) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const float bound = __fmul_ru(g1, B[v]);
+                    bool below;
+                    if constexpr (sizeof(T) == 4) below = bound <= lam1;
+                    else below = (double)bound <= lam1;
+                    if (((sup >> v) & 1u) || long_chain || !below) bits |= 1u << v;
+                }
+            }
+            unsigned word = bits << (8 * (lane & 3));
+            word |= __shfl_xor_sync(kFull, word, 1);
+            word |= __shfl_xor_sync(kFull, word, 2);
+            const int w = jl / 32;
+            if ((lane & 3) == 0 && w < nwords) rowmask[(int64_t)pos * nwords + w] = word;
+        }
     }
 }
 
@@ -1038,104 +1188,150 @@ __device__ __forceinline__ long long warp_incl_scan64(long long x, int lane) {
     return x;
 }
 
-// Single-block exclusive scan of n ints, out[n] = total; if total > cap, sets
-// flag.  With uoff (the bucket scan), also the list of long rows (more than
-// kShortRow entries), in ascending order, into longlist, their count into
-// ctrl->n_long, and the exclusive 64-bit prefix of their ls_units over that list
-// into uoff (uoff[n_long] = total units).  Thread t owns the contiguous run
-// [t E, t E + E): one pass sums the runs (16-byte loads), one block-wide scan of
-// the 1024 run sums, and a second pass writes the run's prefixes.
-__global__ void __launch_bounds__(1024)
-k_scan(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
-       int* total_dst, long long* __restrict__ uoff, int* __restrict__ longlist) {
-    __shared__ int wsum[32], wlong[32];
-    __shared__ long long usum[32];
+// Multi-block exclusive scan of n ints, out[n] = total; if total > cap, sets flag.
+// With uoff (the bucket scan), also the list of long rows (more than kShortRow
+// entries), in ascending order, into longlist, their count into ctrl->n_long, and
+// the exclusive 64-bit prefix of their ls_units over that list into uoff
+// (uoff[n_long] = total units).  Two kernels over tiles of kScanTile inputs (thread
+// t of a tile owns 16 consecutive inputs, four 16-byte loads): k_scan_reduce writes
+// each tile's sums, k_scan_apply adds the sums of the tiles before its own and
+// writes the tile's prefixes.  No block waits on another.
+constexpr int kScanThreads = 256;
+constexpr int kScanPerThread = 16;
+constexpr int kScanTile = kScanThreads * kScanPerThread;
+
+// The 16 inputs of thread t (zero past n); in + base is 16-byte aligned.
+__device__ __forceinline__ void scan_load16(const int* __restrict__ in, int n, int base, int (&v)[kScanPerThread]) {
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; q += 4) {
+        const int j = base + q;
+        if (j + 4 <= n) {
+            const int4 x = *reinterpret_cast<const int4*>(in + j);
+            v[q] = x.x; v[q + 1] = x.y; v[q + 2] = x.z; v[q + 3] = x.w;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[q + r] = j + r < n ? in[j + r] : 0;
+        }
+    }
+}
+
+// Block-wide sums (with_long: also the long-row count and units) of the thread values.
+template <bool INCL>
+__device__ __forceinline__ void scan_block3(int& s, int& l, long long& u, bool with_long, int* ws, int* wl,
+                                            long long* wu) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s0 = s, l0 = l;
+    const long long u0 = u;
+    s = warp_incl_scan(s, lane);
+    if (with_long) { l = warp_incl_scan(l, lane); u = warp_incl_scan64(u, lane); }
+    if (lane == 31) { ws[warp] = s; wl[warp] = l; wu[warp] = u; }
+    __syncthreads();
+    int ps = 0, pl = 0;
+    long long pu = 0;
+    for (int w = 0; w < warp; ++w) { ps += ws[w]; pl += wl[w]; pu += wu[w]; }
+    s += ps; l += pl; u += pu;
+    if (!INCL) { s -= s0; l -= l0; u -= u0; }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const int* __restrict__ in, int n, const Ctrl* __restrict__ ctrl, bool with_long,
+              ScanPart* __restrict__ part) {
+    __shared__ int ws[kScanThreads / 32], wl[kScanThreads / 32];
+    __shared__ long long wu[kScanThreads / 32];
+    if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) return;
+    int v[kScanPerThread];
+    scan_load16(in, n, blockIdx.x * kScanTile + threadIdx.x * kScanPerThread, v);
+    int s = 0, l = 0;
+    long long u = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+        s += v[q];
+        if (with_long && v[q] > kShortRow) { ++l; u += ls_units(v[q]); }
+    }
+    scan_block3<true>(s, l, u, with_long, ws, wl, wu);
+    if (threadIdx.x == kScanThreads - 1) part[blockIdx.x] = ScanPart{s, l, u};
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
+             int* total_dst, long long* __restrict__ uoff, int* __restrict__ longlist,
+             const ScanPart* __restrict__ part) {
+    __shared__ int ws[kScanThreads / 32], wl[kScanThreads / 32];
+    __shared__ long long wu[kScanThreads / 32];
+    __shared__ int s_ps, s_pl;
+    __shared__ long long s_pu;
     if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) {
-        if (threadIdx.x == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
             out[n] = 0;
             if (uoff) { uoff[0] = 0; ctrl->n_long = 0; }
         }
         return;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int E = ((n + 1023) / 1024 + 3) & ~3;
-    const int b0 = min(n, threadIdx.x * E), b1 = min(n, b0 + E);
-    int s = 0, ls = 0;
-    long long us = 0;
-    for (int j = b0; j < b1; j += 4) {
-        int v[4];
-        if (j + 4 <= b1) {
-            const int4 x = *reinterpret_cast<const int4*>(in + j);
-            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = j + q < b1 ? in[j + q] : 0;
+    const bool with_long = uoff != nullptr;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+    int v[kScanPerThread];
+    scan_load16(in, n, base, v);
+    // the sums of the tiles before this one
+    {
+        int ps = 0, pl = 0;
+        long long pu = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) {
+            const ScanPart q = part[b];
+            ps += q.s; pl += q.l; pu += q.u;
         }
+        scan_block3<true>(ps, pl, pu, with_long, ws, wl, wu);
+        if (threadIdx.x == kScanThreads - 1) { s_ps = ps; s_pl = pl; s_pu = pu; }
+        __syncthreads();
+    }
+    int s = 0, l = 0;
+    long long u = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            s += v[q];
-            if (uoff && j + q < b1 && v[q] > kShortRow) {
-                us += ls_units(v[q]);
-                ls += 1;
-            }
+    for (int q = 0; q < kScanPerThread; ++q) {
+        s += v[q];
+        if (with_long && v[q] > kShortRow) { ++l; u += ls_units(v[q]); }
+    }
+    scan_block3<false>(s, l, u, with_long, ws, wl, wu);
+    int run = s + s_ps, lrun = l + s_pl;
+    long long urun = u + s_pu;
+    int o[kScanPerThread];
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; ++q) {
+        o[q] = run;
+        run += v[q];
+        if (with_long && v[q] > kShortRow) {
+            longlist[lrun] = base + q;
+            uoff[lrun] = urun;
+            ++lrun;
+            urun += ls_units(v[q]);
         }
     }
-    const int x = warp_incl_scan(s, lane);
-    const int lx = uoff ? warp_incl_scan(ls, lane) : 0;
-    const long long ux = uoff ? warp_incl_scan64(us, lane) : 0;
-    if (lane == 31) { wsum[warp] = x; usum[warp] = ux; wlong[warp] = lx; }
-    __syncthreads();
-    if (warp == 0) {
-        wsum[lane] = warp_incl_scan(wsum[lane], lane);
-        if (uoff) {
-            usum[lane] = warp_incl_scan64(usum[lane], lane);
-            wlong[lane] = warp_incl_scan(wlong[lane], lane);
+#pragma unroll
+    for (int q = 0; q < kScanPerThread; q += 4) {
+        const int j = base + q;
+        if (j + 4 <= n) {
+            *reinterpret_cast<int4*>(out + j) = make_int4(o[q], o[q + 1], o[q + 2], o[q + 3]);
+        } else {
+            for (int r = 0; r < 4 && j + r < n; ++r) out[j + r] = o[q + r];
         }
     }
-    __syncthreads();
-    int run = x - s + (warp ? wsum[warp - 1] : 0);
-    long long urun = ux - us + (warp ? usum[warp - 1] : 0);
-    int lrun = lx - ls + (warp ? wlong[warp - 1] : 0);
-    // second pass over the run, 16 bytes at a time (the loads hit L1/L2)
-#pragma unroll 4
-    for (int j = b0; j < b1; j += 4) {
-        int v[4];
-        const bool full = j + 4 <= b1;
-        if (full) {
-            const int4 x4 = *reinterpret_cast<const int4*>(in + j);
-            v[0] = x4.x; v[1] = x4.y; v[2] = x4.z; v[3] = x4.w;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = j + q < b1 ? in[j + q] : 0;
-        }
-        int o[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            o[q] = run;
-            run += v[q];
-            if (uoff && j + q < b1 && v[q] > kShortRow) {
-                longlist[lrun] = j + q;
-                uoff[lrun] = urun;
-                ++lrun;
-                urun += ls_units(v[q]);
-            }
-        }
-        if (full) {
-            *reinterpret_cast<int4*>(out + j) = make_int4(o[0], o[1], o[2], o[3]);
-        } else {
-            for (int q = 0; q < 4 && j + q < b1; ++q) out[j + q] = o[q];
-        }
-    }
-    if (threadIdx.x == 1023) {
-        const int total = wsum[31];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
+        // the inputs past n are zero, so this thread's running values are the totals
+        const int total = run;
         out[n] = total;
-        if (uoff) {
-            uoff[wlong[31]] = usum[31];
-            ctrl->n_long = wlong[31];
+        if (with_long) {
+            uoff[lrun] = urun;
+            ctrl->n_long = lrun;
         }
         if (total_dst) *total_dst = total;
         if (total > cap) atomicOr(&ctrl->flags, flag);
     }
+}
+
+void launch_scan(const int* in, int* out, int n, int cap, Ctrl* ctrl, int flag, int* total_dst, long long* uoff,
+                 int* longlist, ScanPart* part, cudaStream_t s) {
+    const int tiles = (int)std::max<int64_t>(1, ((int64_t)n + kScanTile - 1) / kScanTile);
+    k_scan_reduce<<<tiles, kScanThreads, 0, s>>>(in, n, ctrl, uoff != nullptr, part);
+    k_scan_apply<<<tiles, kScanThreads, 0, s>>>(in, out, n, cap, ctrl, flag, total_dst, uoff, longlist, part);
 }
 
 template <typename T>
@@ -1861,9 +2057,12 @@ k_ls_decide(const double* __restrict__ part_ls, int n_ls, const double* __restri
     const int nq = M * 4 + (first ? 4 : 0);
     for (int q = warp; q < nq; q += 32) {
         double a = 0.0;
+        // eight loads in flight per lane; the additions keep their order
         if (q < M * 4) {
+#pragma unroll 8
             for (int b = lane; b < n_ls; b += 32) a += part_ls[(size_t)q * stride + b];
         } else {
+#pragma unroll 8
             for (int b = lane; b < n_obj; b += 32) a += part_obj[(size_t)(q - M * 4) * stride + b];
         }
         a = warp_sum(a);
@@ -2053,9 +2252,10 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     constexpr int smem = screen_smem_bytes<T>();
     set_smem_once((const void*)k_grad_screen<T>, smem, sizeof(T) == 8 ? kSmemSlotScreenD : kSmemSlotScreenF);
     const int warps_grid = b.num_sms * 4;
-    k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.pmask, b.offlist, b.ctrl);
-    if (b.m1) k_colmax<T><<<(b.nbm + 7) / 8, kThreads, 0, s>>>(b.p, b.nbm, b.rinfo, b.rdv, b.colmax);
-    k_pair_select<T><<<warps_grid, kThreads, 0, s>>>(b.S, b.ld, b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.colmax, b.pairs,
+    // one row per thread (the column maxima need every row of a block in one CTA)
+    k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.pmask, b.offlist, b.ctrl,
+                                                     b.m1 ? static_cast<T*>(b.colmax) : nullptr, b.nbm);
+    k_pair_select<T><<<b.num_sms * 8, kThreads, 0, s>>>(b.S, b.ld, b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.colmax, b.pairs,
                                                      b.pairs_cap, b.em, b.ctrl);
     if (b.m1)
         k_pair_screen<T><<<warps_grid, kThreads, 0, s>>>(b.S, b.ld, b.p, b.pairs, b.pairs_cap, b.rinfo, b.rdv, b.pmask,
@@ -2063,8 +2263,12 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     k_grad_screen<T><<<b.screen_grid, kScreenThreads, smem, s>>>(*b.smap, b.p, b.seqoff, b.rinfo, b.rdv, b.pmask,
                                                                  b.m1 ? b.pairs_cap : -1, b.em, b.ctrl);
     if (b.m1) {
-        k_rows_mask<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv,
-                                                       b.rowmask, b.ctrl);
+        if (b.nbm % 8 == 0)
+            k_rows_mask_v<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci,
+                                                             b.cur.cv, b.rowmask, b.ctrl);
+        else
+            k_rows_mask<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci,
+                                                           b.cur.cv, b.rowmask, b.ctrl);
         k_rows_list<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.rowmask, b.row_items, b.row_items_cap, b.ctrl);
     }
     k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
@@ -2079,19 +2283,25 @@ void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, unsigned short*
 
 template <typename T>
 void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s) {
-    k_row_info<T><<<(p + 255) / 256, 256, 0, s>>>(p, om, rinfo, rdv, nullptr, nullptr, nullptr);
+    k_row_info<T><<<(p + 255) / 256, 256, 0, s>>>(p, om, rinfo, rdv, nullptr, nullptr, nullptr, nullptr, 0);
+}
+
+// Blocks of k_gradient: one objective partial each (read back by k_ls_decide).
+template <typename T>
+static int gradient_grid(const IterBufs<T>& b) {
+    return std::max(1, std::min(b.nblk, b.num_sms * 4));
 }
 
 template <typename T>
 void launch_candidates(const IterBufs<T>& b, cudaStream_t s) {
     const int g = 152 * 4;
     k_bucket_count<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
-    k_scan<<<1, 1024, 0, s>>>(b.bk.cnt, b.bk.off, b.p, b.bk.cap, b.ctrl, kFlagBucketOverflow,
-                              &b.ctrl->bucket_total, b.bk.uoff, b.bk.longlist);
+    launch_scan(b.bk.cnt, b.bk.off, b.p, b.bk.cap, b.ctrl, kFlagBucketOverflow, &b.ctrl->bucket_total, b.bk.uoff,
+                b.bk.longlist, b.scan_part, s);
     k_bucket_scatter<T><<<g, 256, 0, s>>>(b.em, b.bk, b.ctrl);
     k_bucket_sort<T><<<b.nblk, kThreads, 0, s>>>(b.bk, b.p, b.ctrl);
     k_fill_w<T><<<b.num_sms * 8, kThreads, 0, s>>>(b.S, b.ld, b.cur, b.rinfo, b.rdv, b.bk, b.ctrl);
-    k_gradient<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.nblk, b.part_obj, b.ctrl);
+    k_gradient<T><<<gradient_grid(b), kThreads, 0, s>>>(b.p, b.bk, b.nblk, b.part_obj, b.ctrl);
 }
 
 // Persistent grid of the line-search evaluation: resident blocks x SMs (at most
@@ -2129,8 +2339,8 @@ void launch_ls_window(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) 
         case 8: g = ls_eval_m<T, 8>(b, s); break;
         default: g = ls_eval_m<T, 16>(b, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, g, b.part_obj, b.nblk, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls,
-                                  b.ctrl);
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, g, b.part_obj, gradient_grid(b), b.nblk, M, b.max_halvings, 1.0,
+                                   lc.use, lc.ls, b.ctrl);
 }
 
 template <int M>
@@ -2147,14 +2357,14 @@ void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStre
         case 8: ls_eval_obs_m<8>(b, s); break;
         default: ls_eval_obs_m<16>(b, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.nblk, b.part_obj, b.nblk, b.nblk, M, b.max_halvings, 1.0, lc.use, lc.ls,
-                                   b.ctrl);
+    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.nblk, b.part_obj, gradient_grid(b), b.nblk, M, b.max_halvings, 1.0,
+                                   lc.use, lc.ls, b.ctrl);
 }
 
 template <typename T>
 void launch_accept(const IterBufs<T>& b, cudaStream_t s) {
     k_compact_count<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.cnt2, b.ctrl);
-    k_scan<<<1, 1024, 0, s>>>(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr, nullptr);
+    launch_scan(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr, nullptr, b.scan_part, s);
     k_compact_write<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.next, b.csr_cap, b.ctrl);
     k_converge<<<1, 1, 0, s>>>(b.next.rp, b.p, b.csr_cap, b.eps, b.ctrl);
 }

@@ -152,19 +152,25 @@ def test_fp32_first_iterations_follow_oracle(lib):
             Om, W = step.omega, step.W
 
 
-def test_screened_gradient_matches_oracle(lib):
+@pytest.mark.parametrize("p,n,f64", [
+    (600, 400, False),      # 5 column blocks: the per-block mask and selection
+    (1024, 500, False),     # 8 blocks of 128: the 16-byte (8-block) vector forms
+    (512, 300, True),       # FP64, 8 blocks of 64: the vector forms in double
+])
+def test_screened_gradient_matches_oracle(lib, p, n, f64):
     """After a few iterations: G on every reported candidate equals the oracle's G, and every
-    entry outside the candidate set has w_ij = 0 and |G_ij| <= lambda1."""
+    entry outside the candidate set has w_ij = 0 and |G_ij| <= lambda1 (the bound screening
+    skipped no block that can emit)."""
     torch = _torch()
-    p, n = 600, 400
-    X = small_problem(p, n, 5.0, 8).astype(np.float32)
+    X = small_problem(p, n, 5.0, 8).astype(np.float64 if f64 else np.float32)
     S = oracle.gram(X)
     lam1, lam2 = 0.08, 0.1
-    with lib.Solver(torch.as_tensor(X).cuda(), lam1, lam2, precision=lib.PREC_FP32) as s:
+    opt = dict(value_dtype=lib.F64, precision=lib.PREC_FP64) if f64 else dict(precision=lib.PREC_FP32)
+    with lib.Solver(torch.as_tensor(X).cuda(), lam1, lam2, **opt) as s:
         s.iterate(4)
         om_before = None
         # candidates belong to the gradient pass at the iterate *before* the last accept
-        s2 = lib.Solver(torch.as_tensor(X).cuda(), lam1, lam2, precision=lib.PREC_FP32)
+        s2 = lib.Solver(torch.as_tensor(X).cuda(), lam1, lam2, **opt)
         s2.iterate(3)
         om_before = s2.omega_dense()
         s2.close()
