@@ -351,7 +351,10 @@ typedef struct {
     int32_t rows_ctas_per_sm;  /* CTAs per SM of the off-diagonal row kernel, 1..4 (2) */
     int32_t gram_maxima;       /* 1: the tensor-core Gram's epilogue writes the bound
                                   screening's block maxima; 0: a pass over S after it (1) */
-    int32_t reserved_;
+    int32_t screen_bounds;     /* 1: the screening pass reads only the segments of S
+                                  whose block-maxima bound can emit; 0: it streams the
+                                  whole upper triangle and every block of the rows with
+                                  neighbours.  Both emit the same entries (1)       */
 } hpc_tuning;
 
 /* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max

@@ -105,6 +105,8 @@ struct hpc_ctx {
     // bound screening: max |S_ij| per (row, column block), the column maxima of the
     // pure diagonals, and the kept (row, block) items
     void* m1 = nullptr;
+    void* m1g = nullptr;
+    int ngl = 0;
     int nbm = 0;
     void* colmax = nullptr;
     int2* pairs_list = nullptr;
@@ -128,7 +130,7 @@ struct hpc_ctx {
     void* x_stage = nullptr;
     size_t x_stage_bytes = 0;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{16, 8, 0, 2, 1, 0};
+    hpc_tuning tune{16, 8, 0, 2, 1, 1};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -258,7 +260,10 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.pmask = h->pmask;
     b.seqoff = h->seqoff;
     b.screen_grid = h->screen_grid;
-    b.m1 = static_cast<const unsigned short*>(h->m1);
+    const bool bounds = h->tune.screen_bounds != 0;
+    b.m1 = bounds ? static_cast<const unsigned short*>(h->m1) : nullptr;
+    b.m1g = bounds ? static_cast<const unsigned short*>(h->m1g) : nullptr;
+    b.ngl = h->ngl;
     b.nbm = h->nbm;
     b.colmax = h->colmax;
     b.pairs = h->pairs_list;
@@ -863,6 +868,11 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
                                             static_cast<unsigned short*>(h->m1), h->stream);
         CUDA_TRY(cudaGetLastError());
     }
+    if (h->m1g) {
+        hpc::launch_group_max(static_cast<const unsigned short*>(h->m1), (int)h->p, h->nbm,
+                              static_cast<unsigned short*>(h->m1g), h->ngl, h->stream);
+        CUDA_TRY(cudaGetLastError());
+    }
     if (h->opt.timing) {
         CUDA_TRY(cudaEventRecord(h->ev[3], h->stream));
         CUDA_TRY(cudaEventSynchronize(h->ev[3]));
@@ -900,7 +910,7 @@ void destroy(hpc_ctx* h) {
                     h->bk_cur, h->bk_len, h->cnt2, h->scan_part, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
                     h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long,
-                    h->m1, h->colmax, h->pairs_list, h->row_items, h->rowmask, h->x_stage};
+                    h->m1, h->m1g, h->colmax, h->pairs_list, h->row_items, h->rowmask, h->x_stage};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -1046,6 +1056,10 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         const int64_t items = p * (int64_t)h->nbm / 2 + p;
         h->pairs_cap = (int)std::min<int64_t>(std::max<int64_t>(items / 4, 1024), 0x7ffffff0);
         CK(cudaMalloc(&h->m1, (size_t)p * h->nbm * sizeof(unsigned short)));
+        if (h->nbm % 8 == 0) {
+            h->ngl = (h->nbm / 8 + 7) / 8 * 8;
+            CK(cudaMalloc(&h->m1g, (size_t)p * h->ngl * sizeof(unsigned short)));
+        }
         CK(cudaMalloc(&h->colmax, (size_t)h->nbm * vs));
         CK(cudaMalloc(&h->pairs_list, (size_t)h->pairs_cap * sizeof(int2)));
         CK(cudaMalloc(&h->rowmask, (size_t)p * ((h->nbm + 31) / 32) * sizeof(unsigned)));
@@ -1658,7 +1672,7 @@ bool tuning_ok(const hpc_tuning& t) {
     const int w = t.ls_window;
     return t.gram_band >= 1 && t.gram_band <= 256 && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16) &&
            t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4 &&
-           (t.gram_maxima == 0 || t.gram_maxima == 1);
+           (t.gram_maxima == 0 || t.gram_maxima == 1) && (t.screen_bounds == 0 || t.screen_bounds == 1);
 }
 
 void apply_tuning(hpc_ctx* h, const hpc_tuning& t) {

@@ -144,6 +144,9 @@ struct IterBufs {
     const unsigned short* m1; // p x nbm: max |S_ij| over column block jb, j != i, as BF16 rounded up
                               // (an upper bound; null: no bound screening)
     int nbm;                  // column blocks of width BJ
+    const unsigned short* m1g;  // p x ngl (nbm % 8 == 0, else null): m1's maximum over each group of
+                                // 8 blocks
+    int ngl;                  // row stride of m1g: nbm / 8 rounded up to a multiple of 8
     void* colmax;             // nbm words: max |w_jj| over the pure rows j of each block (T's bits)
     int2* pairs;              // kept (row, block) items
     int pairs_cap;            // above this many items the pass streams the upper triangle instead
@@ -201,6 +204,8 @@ template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv
 // max |S_ij| per (row, column block of width screen_box_cols), off the diagonal
 template <typename T> void launch_rowblock_max(const T* S, int64_t ld, int p, int nbm, unsigned short* m1,
                                                cudaStream_t s);
+// m1g[i][g] = max over blocks 8g .. 8g+7 of m1[i][.] (nbm % 8 == 0), once per data load.
+void launch_group_max(const unsigned short* m1, int p, int nbm, unsigned short* m1g, int ngl, cudaStream_t s);
 template <typename T> int screen_plan(int p, int num_sms, std::vector<long long>& seqoff);
 void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s);
 

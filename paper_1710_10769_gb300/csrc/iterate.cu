@@ -672,8 +672,9 @@ k_rowblock_max(const T* __restrict__ S, int64_t ld, int p, int nbm, unsigned sho
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const unsigned short* __restrict__ m1,
-              const int4* __restrict__ rinfo, const T* __restrict__ rdv, const void* colmax_raw,
-              int2* __restrict__ pairs, int cap, Emit<T> em, Ctrl* __restrict__ ctrl) {
+              const unsigned short* __restrict__ m1g, int ngl, const int4* __restrict__ rinfo,
+              const T* __restrict__ rdv, const void* colmax_raw, int2* __restrict__ pairs, int cap, Emit<T> em,
+              Ctrl* __restrict__ ctrl) {
     constexpr int BJ = Screen<T>::BJ;
     if (2 * ctrl->n_offrows > p) return;
     const T* colmax = static_cast<const T*>(colmax_raw);
@@ -693,47 +694,70 @@ k_pair_select(const T* __restrict__ S, int64_t ld, int p, int nbm, const unsigne
         int pos = warp_reserve<T>(d ? 1 : 0, ctrl, lane);
         if (d) put_entry(em, pos, i, (unsigned)i | 0x80000000u, w, dv);
     }
-    if (m1 && nbm % 8 == 0 && (long long)p * (nbm / 8) < 0x7fffffffLL - (long long)gridDim.x * blockDim.x) {
-        // the items, one thread per (row, 8-block group) with one 16-byte load of the
-        // row's maxima (rows 16-byte aligned: nbm % 8 == 0); groups left of the upper
-        // triangle load nothing.  The loop bound is uniform over each block.
+    if (m1g) {
+        // the items, two-level: the column maxima and their group maxima (8 blocks) in
+        // shared memory (the launch sizes it); one thread per (row, span of 8 groups).
+        // A group is dropped when fl(max(|w_ii|, max colmax over the group) * m1g) <=
+        // lambda1: both factors bound each block's, so no block of it could be kept.
+        // Only the groups that pass load their 8 block maxima for the per-block test.
+        extern __shared__ __align__(16) unsigned char ps_smem[];
+        T* s_cm = reinterpret_cast<T*>(ps_smem);
         const int ng = nbm / 8;
-        const int total = p * ng;
-        const int nthreads = gridDim.x * blockDim.x;
-        for (int base = blockIdx.x * blockDim.x; base < total; base += nthreads) {
-            const int it = base + threadIdx.x;
-            unsigned bits = 0;
-            int i = 0, jl = 0;
-            if (it < total) {
-                i = it / ng;
-                jl = (it - i * ng) * 8;
-                const int jb0 = (i + 1) / BJ;
-                if (jl + 8 > jb0) {
-                    const bool pure = rinfo[i].w != 0;
-                    const T rm = pure ? fabs(rdv[i]) : T(0);
-                    float f[8];
-                    bf16x8(*reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + jl), f);
+        T* s_cg = s_cm + nbm;
+        for (int t = threadIdx.x; t < nbm; t += blockDim.x) s_cm[t] = colmax[t];
+        __syncthreads();
+        for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+            T m = T(0);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        const int jb = jl + v;
-                        if ((i + 1) < min(p, (jb + 1) * BJ)) {
-                            const T m = max_nan(rm, colmax[jb]);
-                            if ((m != T(0)) && !(mulT(m, (T)f[v]) <= lam1)) bits |= 1u << v;
+            for (int v = 0; v < 8; ++v) m = max_nan(m, s_cm[8 * g + v]);
+            s_cg[g] = m;
+        }
+        __syncthreads();
+        const int nsp = (ng + 7) / 8;
+        const int total = p * nsp;          // the launch checks that this fits an int
+        for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
+            const int it = base + threadIdx.x;
+            unsigned long long bits = 0;
+            int i = 0, g0 = 0;
+            if (it < total) {
+                i = it / nsp;
+                g0 = (it - i * nsp) * 8;
+                const int jb0 = (i + 1) / BJ;
+                if (8 * (g0 + 8) > jb0) {
+                    const T rm = rinfo[i].w ? fabs(rdv[i]) : T(0);
+                    float gf[8];
+                    bf16x8(*reinterpret_cast<const uint4*>(m1g + (int64_t)i * ngl + g0), gf);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int g = g0 + q;
+                        if (g >= ng || 8 * (g + 1) <= jb0) continue;
+                        const T mg = max_nan(rm, s_cg[g]);
+                        if (mg == T(0) || mulT(mg, (T)gf[q]) <= lam1) continue;
+                        float f[8];
+                        bf16x8(*reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + 8 * g), f);
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) {
+                            const int jb = 8 * g + v;
+                            if ((i + 1) < min(p, (jb + 1) * BJ)) {
+                                const T m = max_nan(rm, s_cm[jb]);
+                                if ((m != T(0)) && !(mulT(m, (T)f[v]) <= lam1)) bits |= 1ull << (8 * q + v);
+                            }
                         }
                     }
                 }
             }
-            const int c = __popc(bits);
+            const int c = __popcll(bits);
             if (!__any_sync(kFull, c != 0)) continue;
             const int incl = warp_incl_scan(c, lane);
             int q = 0;
             if (lane == 31) q = atomicAdd(&ctrl->n_pairs, incl);
             q = __shfl_sync(kFull, q, 31) + incl - c;
-            for (int v = 0; bits; ++v, bits >>= 1)
-                if (bits & 1u) {
-                    if (q < cap) pairs[q] = make_int2(i, jl + v);
-                    ++q;
-                }
+            while (bits) {
+                const int b = __ffsll((long long)bits) - 1;
+                bits &= bits - 1;
+                if (q < cap) pairs[q] = make_int2(i, 8 * g0 + b);
+                ++q;
+            }
         }
         return;
     }
@@ -2255,8 +2279,14 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     // one row per thread (the column maxima need every row of a block in one CTA)
     k_row_info<T><<<(b.p + 255) / 256, 256, 0, s>>>(b.p, b.cur, b.rinfo, b.rdv, b.pmask, b.offlist, b.ctrl,
                                                      b.m1 ? static_cast<T*>(b.colmax) : nullptr, b.nbm);
-    k_pair_select<T><<<b.num_sms * 8, kThreads, 0, s>>>(b.S, b.ld, b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.colmax, b.pairs,
-                                                     b.pairs_cap, b.em, b.ctrl);
+    // two-level item selection when the group maxima exist and the column maxima fit
+    // in shared memory (and the item count fits an int)
+    const int ngr = b.nbm / 8;
+    const size_t ps_smem = (size_t)(b.nbm + ngr) * sizeof(T);
+    const bool grp = b.m1 && b.m1g && ps_smem <= 48 * 1024 && (long long)b.p * ((ngr + 7) / 8) < (1ll << 30);
+    k_pair_select<T><<<b.num_sms * 8, kThreads, grp ? ps_smem : 0, s>>>(
+        b.S, b.ld, b.p, b.nbm, b.m1, grp ? b.m1g : nullptr, b.ngl, b.rinfo, b.rdv, b.colmax, b.pairs, b.pairs_cap,
+        b.em, b.ctrl);
     if (b.m1)
         k_pair_screen<T><<<warps_grid, kThreads, 0, s>>>(b.S, b.ld, b.p, b.pairs, b.pairs_cap, b.rinfo, b.rdv, b.pmask,
                                                          b.em, b.ctrl);
@@ -2274,6 +2304,30 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
         b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.row_items : nullptr,
         b.row_items_cap, b.em, b.ctrl);
+}
+
+// Group maxima of the block maxima: m1g[i][g] = max over the blocks 8g .. 8g+7 of
+// m1[i][.].  For non-negative BF16 values (and the NaN pattern 0x7fc0, above +inf)
+// the order of the bit patterns is the order of the values, so an unsigned maximum
+// is exact and keeps NaN.  One thread per (row, group): one 16-byte load.
+__global__ void k_group_max(const unsigned short* __restrict__ m1, int p, int nbm, unsigned short* __restrict__ m1g,
+                            int ngl) {
+    const int ng = nbm / 8;
+    const long long total = (long long)p * ng;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / ng), g = (int)(t - (long long)i * ng);
+        const uint4 v = *reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + 8 * g);
+        const unsigned m = max(max(max(v.x & 0xffffu, v.x >> 16), max(v.y & 0xffffu, v.y >> 16)),
+                               max(max(v.z & 0xffffu, v.z >> 16), max(v.w & 0xffffu, v.w >> 16)));
+        m1g[(int64_t)i * ngl + g] = (unsigned short)m;
+    }
+}
+
+void launch_group_max(const unsigned short* m1, int p, int nbm, unsigned short* m1g, int ngl, cudaStream_t s) {
+    const long long total = (long long)p * (nbm / 8);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 152 * 32));
+    k_group_max<<<blocks, 256, 0, s>>>(m1, p, nbm, m1g, ngl);
 }
 
 template <typename T>

@@ -51,7 +51,7 @@ def test_autotune_restores_the_iterate(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(gram_band=0), dict(ls_window=3), dict(rows_ctas_per_sm=5),
-                                 dict(ls_blocks_per_sm=-1), dict(gram_maxima=2)])
+                                 dict(ls_blocks_per_sm=-1), dict(gram_maxima=2), dict(screen_bounds=2)])
 def test_set_tuning_rejects_out_of_range(lib, bad):
     torch = _torch()
     X = torch.as_tensor(small_problem(64, 40, 3.0, seed=1).astype(np.float32)).cuda()

@@ -69,3 +69,36 @@ def test_block_maxima_equal_the_rounded_up_exact_maxima(lib, case):
     want = _bf16_up(_f32_up(m) if kind == "fp64" else m.astype(np.float32))
     assert got.shape == want.shape
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("p,n,f64,lam1", [
+    (1024, 500, False, 0.08),     # 8 blocks: group maxima, two-level item selection, vector row masks
+    (1100, 600, False, 0.06),     # 9 blocks: the per-block selection and row masks
+    (512, 300, True, 0.08),       # FP64 (blocks of 64 columns)
+    (2048, 700, False, 0.03),     # rows with many neighbours (the row kernel covers more blocks)
+])
+def test_bound_screening_changes_no_bit(lib, p, n, f64, lam1):
+    """The bounds only decide which segments of S are read: a solve with them equals,
+    bit for bit, the solve that streams the whole upper triangle and every block of
+    the rows with neighbours."""
+    import torch
+
+    from workloads import small_problem
+
+    X = small_problem(p, n, 5.0, p + 3).astype(np.float64 if f64 else np.float32)
+    opt = dict(value_dtype=lib.F64, precision=lib.PREC_FP64, eps=1e-9) if f64 else \
+        dict(precision=lib.PREC_FP32, eps=1e-7)
+    out = []
+    for bounds in (1, 0):
+        with lib.Solver(torch.as_tensor(X).cuda(), lam1, 0.1, max_iter=20000, **opt) as s:
+            s.set_tuning(screen_bounds=bounds)
+            st = s.solve().as_dict()
+            out.append((s.get_omega(np.float64), st))
+    (a, sa), (b, sb) = out
+    assert sa["status"] == 0 and sb["status"] == 0
+    for key in ("iterations", "ls_trials", "nnz", "F", "rel_change"):
+        assert sa[key] == sb[key], key
+    assert np.array_equal(a.row_ptr, b.row_ptr)
+    assert np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val, b.val)
+    assert sa["nnz"] > p                  # off-diagonal entries survive
