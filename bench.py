@@ -225,6 +225,8 @@ def main(argv=None):
     ap.add_argument("--x-dtype", default="workload", choices=["workload", "f32", "bf16"],
                     help="store X in this dtype instead of the workload's (profiling the one-product BF16 Gram "
                          "at sizes a full ncu capture allows)")
+    ap.add_argument("--screen-bounds", type=int, default=1, choices=[0, 1],
+                    help="0: screen without the block-maxima bounds (same result; for comparison)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="pick the launch shapes with the library's autotuner before the warm-up")
     args = ap.parse_args(argv)
@@ -267,6 +269,9 @@ def main(argv=None):
         solver.iterate(8)
         tuning, tr1 = solver.autotune(None, iters=3)
         tune_trials = tr0 + tr1
+    if not args.screen_bounds:
+        solver.set_tuning(screen_bounds=0)
+        tuning = solver.get_tuning()
 
     def step(Xsrc):
         solver.load_x(Xsrc)
@@ -331,7 +336,9 @@ def main(argv=None):
     roof_scr = {"kernel": "screen_pass", "bound": "hbm (bound-pruned reads)", "ms_per_launch": per * 1000.0,
                 "full_triangle_read_ms_at_peak": uniq / (hbm * 1e9) * 1000.0,
                 "speedup_vs_full_triangle_read_at_peak": (uniq / (hbm * 1e9)) / per,
-                "traffic": measured_traffic("screen_pass", p, n), "peak_source": peak_src}
+                # captured with the bounds on
+                "traffic": measured_traffic("screen_pass", p, n) if args.screen_bounds else None,
+                "peak_source": peak_src}
     roof = roof_gram if gram_ms >= scr_ms else roof_scr
 
     # end to end through the C ABI with host buffers: H2D of X inside the timed region,

@@ -83,9 +83,13 @@ typedef struct {
     int32_t ls_window;      /* tau values tested per line-search launch, 1..16 (8)     */
     int64_t capacity;       /* initial candidate capacity in entries (0 = 32 p)        */
     int64_t max_capacity;   /* growth limit in entries (0 = p*p)                       */
-    int32_t x_on_host;      /* X passed to hpc_create / hpc_load_x is a host pointer;
-                               the handle then keeps a device staging buffer of X's
-                               size between loads (freed by hpc_destroy)              */
+    int32_t x_on_host;      /* X passed to hpc_create / hpc_load_x is a host pointer.
+                               Page-locked (pinned) memory and the tensor-core Gram:
+                               the kernels read X where it is, through its device
+                               mapping.  Otherwise the handle copies X into a device
+                               staging buffer, kept between loads (freed by
+                               hpc_destroy).  The host buffer is not used after the
+                               call returns.                                          */
     int32_t timing;         /* time the phases into hpc_stats (1): CUDA events around
                                each screening pass, or device timestamps in the device
                                loop                                                    */

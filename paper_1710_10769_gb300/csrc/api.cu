@@ -111,7 +111,6 @@ struct hpc_ctx {
     void* colmax = nullptr;
     int2* pairs_list = nullptr;
     int pairs_cap = 0;
-    unsigned* rowmask = nullptr;
     int2* row_items = nullptr;
     int row_items_cap = 0;
     int num_sms = 0;
@@ -268,7 +267,6 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.colmax = h->colmax;
     b.pairs = h->pairs_list;
     b.pairs_cap = h->pairs_cap;
-    b.rowmask = h->rowmask;
     b.row_items = h->row_items;
     b.row_items_cap = h->row_items_cap;
     b.num_sms = h->num_sms;
@@ -810,6 +808,19 @@ int load_x_obs(hpc_ctx* h, const void* Xd) {
 int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
     const void* Xd = X;
     const size_t xbytes = (size_t)h->n * h->p * dtype_size(xdt);
+    const bool tc_cov = h->variant == HPC_COV && (h->precision == HPC_PREC_BF16X3 || h->precision == HPC_PREC_TF32);
+    if (on_host && tc_cov) {
+        // Page-locked host memory is mapped into the device's address space: the
+        // tensor-core Gram's panel preparation, which reads X once, then reads it
+        // there directly (the host-to-device transfer and the transpose in one pass).
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, X) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+            Xd = a.devicePointer;
+            on_host = 0;
+        } else {
+            cudaGetLastError();     // pageable memory: the query's error is not sticky; stage it
+        }
+    }
     if (on_host) {
         // the staging buffer is kept for the next load of the same size or smaller
         if (xbytes > h->x_stage_bytes) {
@@ -910,7 +921,7 @@ void destroy(hpc_ctx* h) {
                     h->bk_cur, h->bk_len, h->cnt2, h->scan_part, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
                     h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long,
-                    h->m1, h->m1g, h->colmax, h->pairs_list, h->row_items, h->rowmask, h->x_stage};
+                    h->m1, h->m1g, h->colmax, h->pairs_list, h->row_items, h->x_stage};
     for (void* q : ptrs) if (q) cudaFree(q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -1062,7 +1073,6 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         }
         CK(cudaMalloc(&h->colmax, (size_t)h->nbm * vs));
         CK(cudaMalloc(&h->pairs_list, (size_t)h->pairs_cap * sizeof(int2)));
-        CK(cudaMalloc(&h->rowmask, (size_t)p * ((h->nbm + 31) / 32) * sizeof(unsigned)));
         h->row_items_cap = (int)std::min<int64_t>((p + 7) / 8 * (int64_t)h->nbm, 0x7ffffff0);
         CK(cudaMalloc(&h->row_items, (size_t)h->row_items_cap * sizeof(int2)));
     }

@@ -150,7 +150,6 @@ struct IterBufs {
     void* colmax;             // nbm words: max |w_jj| over the pure rows j of each block (T's bits)
     int2* pairs;              // kept (row, block) items
     int pairs_cap;            // above this many items the pass streams the upper triangle instead
-    unsigned* rowmask;        // rows with neighbours: bit (position, jb) = the block can emit
     int2* row_items;          // rows with neighbours: kept (8-row group, block) items of the row kernel
     int row_items_cap;
     int num_sms;
@@ -194,11 +193,11 @@ template <typename T> void launch_csr_export(const int* rp, const int* ci, const
 void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int64_t* rows,
                      const int64_t* cols, double* out, cudaStream_t s);
 
-constexpr int kLaunchesScreen = 7;
+constexpr int kLaunchesScreen = 6;
 constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 7;
 constexpr int kLaunchesLsWindow = 2;
-constexpr int kLaunchesAccept = 5;
+constexpr int kLaunchesAccept = 4;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
 // max |S_ij| per (row, column block of width screen_box_cols), off the diagonal

@@ -867,8 +867,7 @@ k_pair_screen(const T* __restrict__ S, int64_t ld, int p, const int2* __restrict
 // m u (1 + 2^-9), and longer chains keep every block.  Columns j = k_t are the
 // support (and i), whose blocks are always processed; for the other columns the
 // bound holds because m1 excludes each row's diagonal.  Row i needs block jb iff
-// the block holds a support column or !(bound <= lambda1) (NaN keeps it).  One warp
-// per (row, 32 blocks): bit (position, jb) in the row kernel's row order.
+// the block holds a support column or !(bound <= lambda1) (NaN keeps it).
 template <typename T>
 __device__ __forceinline__ float abs_up(T x) {
     if constexpr (sizeof(T) == 4) return fabsf(x);
@@ -876,154 +875,131 @@ __device__ __forceinline__ float abs_up(T x) {
 }
 
 template <typename T>
+__device__ __forceinline__ bool bound_keeps(float g1, float B, bool long_chain, T lam1) {
+    const float bound = __fmul_ru(g1, B);
+    bool below;
+    if constexpr (sizeof(T) == 4) below = bound <= lam1;
+    else below = (double)bound <= lam1;
+    return long_chain || !below;
+}
+
+// The row kernel's item list: (8-row group, column block) items any of whose rows
+// needs the block.  One CTA per group of 8 listed rows, warp w on the group's row w;
+// the rows' block words (bit jb % 32 of word jb / 32) meet in shared memory and are
+// ORed there.  VEC (nbm % 8 == 0, m1 rows 16-byte aligned): in each chunk of 256
+// blocks lane l covers blocks c0 + 8l .. c0 + 8l + 7 with one 16-byte load of m1 per
+// term, the row's terms fetched 32 at a time and broadcast (a slot that is not a
+// term -- the diagonal's CSR position, the tail of the last fetch -- is the weight 0
+// on row i itself, which adds 0, or the NaN that row i's own diagonal term already
+// adds).  Otherwise lane l takes block 32 w + l of word w.
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kThreads)
-k_rows_mask(int p, int nbm, const unsigned short* __restrict__ m1, const int4* __restrict__ rinfo,
-            const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
-            const T* __restrict__ cv, unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
+k_rows_items(int p, int nbm, const unsigned short* __restrict__ m1, const int4* __restrict__ rinfo,
+             const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
+             const T* __restrict__ cv, int2* __restrict__ items, int cap, Ctrl* __restrict__ ctrl) {
     constexpr int BJ = Screen<T>::BJ;
+    static_assert(kWarps == 8, "one warp per row of an 8-row group");
+    extern __shared__ unsigned ri_words[];          // [kWarps][nwords]
     const float u = sizeof(T) == 4 ? 0x1p-24f : 0x1p-53f;
     const bool all_rows = 2 * ctrl->n_offrows > p;
     const int nrows = all_rows ? p : ctrl->n_offrows;
+    const int ngroups = (nrows + 7) / 8;
     const int nwords = (nbm + 31) / 32;
-    const long long work = (long long)nrows * nwords;
     const T lam1 = (T)ctrl->lam1;
-    const int lane = threadIdx.x & 31;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long it = gw; it < work; it += nw) {
-        const int pos = (int)(it / nwords), w0 = (int)(it % nwords);
-        const int i = all_rows ? pos : offlist[pos];
-        const int4 ri = rinfo[i];
-        const int jb = w0 * 32 + lane;
-        bool keep = false;
-        if (jb < nbm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned* my = ri_words + warp * nwords;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int pos = grp * 8 + warp;
+        if (pos >= nrows) {
+            for (int w = lane; w < nwords; w += 32) my[w] = 0u;
+        } else {
+            const int i = all_rows ? pos : offlist[pos];
+            const int4 ri = rinfo[i];
+            const float di = abs_up(rdv[i]);
             const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
             const float mu = (float)m * u;                       // exact: m < 2^24, u a power of 2
-            float B = __fmul_ru(abs_up(rdv[i]), bf16_val(m1[(int64_t)i * nbm + jb]));
-            bool sup = (i / BJ) == jb;
-#pragma unroll 4
-            for (int q = ri.x; q < ri.y; ++q) {
-                const int k = ci[q];
-                if (q != ri.z) {
-                    B = __fadd_ru(B, __fmul_ru(abs_up(cv[q]), bf16_val(m1[(int64_t)k * nbm + jb])));
-                    sup |= (k / BJ) == jb;
-                }
-            }
-            const float bound = __fmul_ru(__fadd_ru(1.0f, __fmul_ru(mu, 1.001953125f)), B);
-            bool below;
-            if constexpr (sizeof(T) == 4) below = bound <= lam1;
-            else below = (double)bound <= lam1;
-            keep = sup || mu > 0x1p-10f || !below;
-        }
-        const unsigned word = __ballot_sync(kFull, keep);
-        if (lane == 0) rowmask[(int64_t)pos * nwords + w0] = word;
-    }
-}
-
-// k_rows_mask for nbm % 8 == 0, when every m1 row is 16-byte aligned: one warp per
-// row; in each chunk of 256 blocks lane l covers blocks c0 + 8l .. c0 + 8l + 7 with
-// one 16-byte load of m1 per term.  The row's terms are fetched 32 at a time and
-// broadcast; a term that is not one (the diagonal's CSR slot, the tail of the last
-// fetch) becomes the weight 0 on row i itself, which adds 0 (or the NaN that row i's
-// own diagonal term already adds).  Same bound, rounding and word layout as
-// k_rows_mask.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_rows_mask_v(int p, int nbm, const unsigned short* __restrict__ m1, const int4* __restrict__ rinfo,
-              const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
-              const T* __restrict__ cv, unsigned* __restrict__ rowmask, Ctrl* __restrict__ ctrl) {
-    constexpr int BJ = Screen<T>::BJ;
-    const float u = sizeof(T) == 4 ? 0x1p-24f : 0x1p-53f;
-    const bool all_rows = 2 * ctrl->n_offrows > p;
-    const int nrows = all_rows ? p : ctrl->n_offrows;
-    const int nwords = (nbm + 31) / 32;
-    const T lam1 = (T)ctrl->lam1;
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int pos = gw; pos < nrows; pos += nw) {
-        const int i = all_rows ? pos : offlist[pos];
-        const int4 ri = rinfo[i];
-        const float di = abs_up(rdv[i]);
-        const int m = 1 + (ri.y - ri.x) - (ri.z >= 0 ? 1 : 0);
-        const float mu = (float)m * u;                           // exact: m < 2^24, u a power of 2
-        const float g1 = __fadd_ru(1.0f, __fmul_ru(mu, 1.001953125f));
-        const bool long_chain = mu > 0x1p-10f;
-        const int ib = i / BJ;
-        for (int c0 = 0; c0 < nbm; c0 += 256) {
-            const int jl = c0 + lane * 8;
-            const bool act = jl < nbm;
-            float B[8], f[8];
-            unsigned sup = (unsigned)(ib - jl) < 8u ? 1u << (ib - jl) : 0u;
-            bf16x8(act ? *reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + jl) : make_uint4(0, 0, 0, 0), f);
-#pragma unroll
-            for (int v = 0; v < 8; ++v) B[v] = __fmul_ru(di, f[v]);
-            for (int q0 = ri.x; q0 < ri.y; q0 += 32) {
-                const int q = q0 + lane;
-                const bool term = q < ri.y && q != ri.z;
-                const int kq = term ? ci[q] : i;
-                const float wq = term ? abs_up(cv[q]) : 0.0f;
-                const int nt = min(32, ri.y - q0);
-#pragma unroll 4
-                for (int t = 0; t < nt; ++t) {
-                    const int k = __shfl_sync(kFull, kq, t);
-                    const float w = __shfl_sync(kFull, wq, t);
-                    bf16x8(act ? *reinterpret_cast<const uint4*>(m1 + (int64_t)k * nbm + jl) : make_uint4(0, 0, 0, 0),
+            const float g1 = __fadd_ru(1.0f, __fmul_ru(mu, 1.001953125f));
+            const bool long_chain = mu > 0x1p-10f;
+            const int ib = i / BJ;
+            if constexpr (VEC) {
+                for (int c0 = 0; c0 < nbm; c0 += 256) {
+                    const int jl = c0 + lane * 8;
+                    const bool act = jl < nbm;
+                    float B[8], f[8];
+                    unsigned sup = (unsigned)(ib - jl) < 8u ? 1u << (ib - jl) : 0u;
+                    bf16x8(act ? *reinterpret_cast<const uint4*>(m1 + (int64_t)i * nbm + jl) : make_uint4(0, 0, 0, 0),
                            f);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) B[v] = __fadd_ru(B[v], __fmul_ru(w, f[v]));
-                    const int kb = k / BJ;
-                    if ((unsigned)(kb - jl) < 8u) sup |= 1u << (kb - jl);
-                }
-            }
-            unsigned bits = 0;
-            if (act) {
+                    for (int v = 0; v < 8; ++v) B[v] = __fmul_ru(di, f[v]);
+                    for (int q0 = ri.x; q0 < ri.y; q0 += 32) {
+                        const int q = q0 + lane;
+                        const bool term = q < ri.y && q != ri.z;
+                        const int kq = term ? ci[q] : i;
+                        const float wq = term ? abs_up(cv[q]) : 0.0f;
+                        const int nt = min(32, ri.y - q0);
+#pragma unroll 4
+                        for (int t = 0; t < nt; ++t) {
+                            const int k = __shfl_sync(kFull, kq, t);
+                            const float w = __shfl_sync(kFull, wq, t);
+                            bf16x8(act ? *reinterpret_cast<const uint4*>(m1 + (int64_t)k * nbm + jl)
+                                       : make_uint4(0, 0, 0, 0),
+                                   f);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const float bound = __fmul_ru(g1, B[v]);
-                    bool below;
-                    if constexpr (sizeof(T) == 4) below = bound <= lam1;
-                    else below = (double)bound <= lam1;
-                    if (((sup >> v) & 1u) || long_chain || !below) bits |= 1u << v;
+                            for (int v = 0; v < 8; ++v) B[v] = __fadd_ru(B[v], __fmul_ru(w, f[v]));
+                            const int kb = k / BJ;
+                            if ((unsigned)(kb - jl) < 8u) sup |= 1u << (kb - jl);
+                        }
+                    }
+                    unsigned bits = 0;
+                    if (act) {
+#pragma unroll
+                        for (int v = 0; v < 8; ++v)
+                            if (((sup >> v) & 1u) || bound_keeps<T>(g1, B[v], long_chain, lam1)) bits |= 1u << v;
+                    }
+                    unsigned word = bits << (8 * (lane & 3));
+                    word |= __shfl_xor_sync(kFull, word, 1);
+                    word |= __shfl_xor_sync(kFull, word, 2);
+                    const int w = jl / 32;
+                    if ((lane & 3) == 0 && w < nwords) my[w] = word;
+                }
+            } else {
+                for (int w0 = 0; w0 < nwords; ++w0) {
+                    const int jb = w0 * 32 + lane;
+                    bool keep = false;
+                    if (jb < nbm) {
+                        float B = __fmul_ru(di, bf16_val(m1[(int64_t)i * nbm + jb]));
+                        bool sup = ib == jb;
+#pragma unroll 4
+                        for (int q = ri.x; q < ri.y; ++q) {
+                            const int k = ci[q];
+                            if (q != ri.z) {
+                                B = __fadd_ru(B, __fmul_ru(abs_up(cv[q]), bf16_val(m1[(int64_t)k * nbm + jb])));
+                                sup |= (k / BJ) == jb;
+                            }
+                        }
+                        keep = sup || bound_keeps<T>(g1, B, long_chain, lam1);
+                    }
+                    const unsigned word = __ballot_sync(kFull, keep);
+                    if (lane == 0) my[w0] = word;
                 }
             }
-            unsigned word = bits << (8 * (lane & 3));
-            word |= __shfl_xor_sync(kFull, word, 1);
-            word |= __shfl_xor_sync(kFull, word, 2);
-            const int w = jl / 32;
-            if ((lane & 3) == 0 && w < nwords) rowmask[(int64_t)pos * nwords + w] = word;
         }
-    }
-}
-
-// The row kernel's item list: (8-row group, block) items any of whose rows needs the
-// block.  One warp per (group, 32 blocks).
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_rows_list(int p, int nbm, const unsigned* __restrict__ rowmask, int2* __restrict__ items, int cap,
-            Ctrl* __restrict__ ctrl) {
-    constexpr int R = 8;
-    const bool all_rows = 2 * ctrl->n_offrows > p;
-    const int nrows = all_rows ? p : ctrl->n_offrows;
-    const int ngroups = (nrows + R - 1) / R;
-    const int nwords = (nbm + 31) / 32;
-    const long long work = (long long)ngroups * nwords;
-    const int lane = threadIdx.x & 31;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long it = gw; it < work; it += nw) {
-        const int grp = (int)(it / nwords), w0 = (int)(it % nwords);
-        const int nr = min(R, nrows - grp * R);
-        unsigned word = lane < nr ? rowmask[(int64_t)(grp * R + lane) * nwords + w0] : 0u;
+        __syncthreads();
+        // the group's items: warps take words w0 = warp, warp + 8, ...
+        for (int w0 = warp; w0 < nwords; w0 += kWarps) {
+            unsigned word = lane < 8 ? ri_words[lane * nwords + w0] : 0u;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) word |= __shfl_xor_sync(kFull, word, o);
-        if (!word) continue;
-        const bool keep = (word >> lane) & 1u;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&ctrl->n_row_items, __popc(word));
-        base = __shfl_sync(kFull, base, 0);
-        const int q = base + __popc(word & ((1u << lane) - 1u));
-        if (keep && q < cap) items[q] = make_int2(grp, w0 * 32 + lane);
+            for (int o = 4; o > 0; o >>= 1) word |= __shfl_xor_sync(kFull, word, o);
+            word = __shfl_sync(kFull, word, 0);
+            if (!word) continue;
+            const bool keep = (word >> lane) & 1u;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&ctrl->n_row_items, __popc(word));
+            base = __shfl_sync(kFull, base, 0);
+            const int q = base + __popc(word & ((1u << lane) - 1u));
+            if (keep && q < cap) items[q] = make_int2(grp, w0 * 32 + lane);
+        }
+        __syncthreads();
     }
 }
 
@@ -1279,7 +1255,7 @@ k_scan_reduce(const int* __restrict__ in, int n, const Ctrl* __restrict__ ctrl, 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
              int* total_dst, long long* __restrict__ uoff, int* __restrict__ longlist,
-             const ScanPart* __restrict__ part) {
+             const ScanPart* __restrict__ part, int conv_cap, double eps) {
     __shared__ int ws[kScanThreads / 32], wl[kScanThreads / 32];
     __shared__ long long wu[kScanThreads / 32];
     __shared__ int s_ps, s_pl;
@@ -1348,14 +1324,29 @@ k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, 
         }
         if (total_dst) *total_dst = total;
         if (total > cap) atomicOr(&ctrl->flags, flag);
+        // the compaction's scan (conv_cap >= 0) also takes the stopping-rule step once
+        // a step is accepted: the new entry count against the CSR capacity, and the
+        // relative change ||dOmega||_F / ||Omega||_F, both known before the write-out
+        if (conv_cap >= 0 && ctrl->flags == 0 && ctrl->ls_accept >= 0) {
+            ctrl->nnz_next = total;
+            if (total > conv_cap) {
+                ctrl->flags |= kFlagNnzOverflow;
+            } else {
+                const double rel = sqrt(ctrl->delta2) / sqrt(ctrl->norm2_cur);
+                ctrl->rel = rel;
+                ctrl->converged = rel < eps ? 1 : 0;
+                ctrl->iter += 1;
+            }
+        }
     }
 }
 
 void launch_scan(const int* in, int* out, int n, int cap, Ctrl* ctrl, int flag, int* total_dst, long long* uoff,
-                 int* longlist, ScanPart* part, cudaStream_t s) {
+                 int* longlist, ScanPart* part, cudaStream_t s, int conv_cap = -1, double eps = 0.0) {
     const int tiles = (int)std::max<int64_t>(1, ((int64_t)n + kScanTile - 1) / kScanTile);
     k_scan_reduce<<<tiles, kScanThreads, 0, s>>>(in, n, ctrl, uoff != nullptr, part);
-    k_scan_apply<<<tiles, kScanThreads, 0, s>>>(in, out, n, cap, ctrl, flag, total_dst, uoff, longlist, part);
+    k_scan_apply<<<tiles, kScanThreads, 0, s>>>(in, out, n, cap, ctrl, flag, total_dst, uoff, longlist, part, conv_cap,
+                                                eps);
 }
 
 template <typename T>
@@ -2196,17 +2187,6 @@ k_compact_write(int p, Buckets<T> bk, Csr<T> nx, int cap, const Ctrl* ctrl) {
     }
 }
 
-__global__ void k_converge(const int* rp_next, int p, int cap, double eps, Ctrl* ctrl) {
-    if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
-    const int nnz = rp_next[p];
-    ctrl->nnz_next = nnz;
-    if (nnz > cap) { ctrl->flags |= kFlagNnzOverflow; return; }
-    const double rel = sqrt(ctrl->delta2) / sqrt(ctrl->norm2_cur);
-    ctrl->rel = rel;
-    ctrl->converged = rel < eps ? 1 : 0;
-    ctrl->iter += 1;
-}
-
 template <typename T>
 __global__ void k_set_identity(Csr<T> c, int p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= p; i += gridDim.x * blockDim.x) {
@@ -2293,13 +2273,16 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
     k_grad_screen<T><<<b.screen_grid, kScreenThreads, smem, s>>>(*b.smap, b.p, b.seqoff, b.rinfo, b.rdv, b.pmask,
                                                                  b.m1 ? b.pairs_cap : -1, b.em, b.ctrl);
     if (b.m1) {
+        const int ngroups_max = (b.p + 7) / 8;
+        const int grid = std::max(1, std::min(ngroups_max, b.num_sms * 4));
+        const size_t words = (size_t)kWarps * ((b.nbm + 31) / 32) * sizeof(unsigned);
         if (b.nbm % 8 == 0)
-            k_rows_mask_v<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci,
-                                                             b.cur.cv, b.rowmask, b.ctrl);
+            k_rows_items<T, true><<<grid, kThreads, words, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci,
+                                                                b.cur.cv, b.row_items, b.row_items_cap, b.ctrl);
         else
-            k_rows_mask<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist, b.cur.ci,
-                                                           b.cur.cv, b.rowmask, b.ctrl);
-        k_rows_list<T><<<warps_grid, kThreads, 0, s>>>(b.p, b.nbm, b.rowmask, b.row_items, b.row_items_cap, b.ctrl);
+            k_rows_items<T, false><<<grid, kThreads, words, s>>>(b.p, b.nbm, b.m1, b.rinfo, b.rdv, b.offlist,
+                                                                 b.cur.ci, b.cur.cv, b.row_items, b.row_items_cap,
+                                                                 b.ctrl);
     }
     k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
         b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.row_items : nullptr,
@@ -2418,9 +2401,9 @@ void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStre
 template <typename T>
 void launch_accept(const IterBufs<T>& b, cudaStream_t s) {
     k_compact_count<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.cnt2, b.ctrl);
-    launch_scan(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr, nullptr, b.scan_part, s);
+    launch_scan(b.cnt2, b.next.rp, b.p, 0x7fffffff, b.ctrl, 0, nullptr, nullptr, nullptr, b.scan_part, s, b.csr_cap,
+                b.eps);
     k_compact_write<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.next, b.csr_cap, b.ctrl);
-    k_converge<<<1, 1, 0, s>>>(b.next.rp, b.p, b.csr_cap, b.eps, b.ctrl);
 }
 
 template <typename T>

@@ -97,3 +97,34 @@ def test_solver_with_tensor_core_gram_matches_oracle(lib):
         s.solve()
         om = s.omega_dense()
     assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-5
+
+
+@pytest.mark.parametrize("bf16", [True, False])
+def test_host_x_pinned_or_pageable_gives_the_device_result(lib, bf16):
+    """X from device memory, from pinned host memory (read in place through its device
+    mapping) and from pageable host memory (staged): the same S, maxima and estimate."""
+    import torch
+
+    from workloads import small_problem
+
+    n, p = 500, 700
+    X = torch.as_tensor(small_problem(p, n, 5.0, 21).astype(np.float32))
+    if bf16:
+        X = X.to(torch.bfloat16)
+    rng = np.random.default_rng(3)
+    r, c = rng.integers(0, p, 200), rng.integers(0, p, 200)
+    out = []
+    for src in (X.cuda(), X.pin_memory(), X.clone()):
+        with lib.Solver(None, 0.15, 0.1, n=n, p=p, xdtype=lib.BF16 if bf16 else lib.F32,
+                        precision=lib.PREC_BF16X3, eps=1e-7) as s:
+            s.load_x(src)
+            m = s.block_maxima()
+            e = s.s_entries(r, c)
+            st = s.solve().as_dict()
+            out.append((m, e, s.get_omega(np.float64), st["iterations"]))
+    m0, e0, om0, it0 = out[0]
+    for m, e, om, it in out[1:]:
+        assert np.array_equal(m, m0)
+        assert np.array_equal(e, e0)
+        assert it == it0
+        assert np.array_equal(om.col, om0.col) and np.array_equal(om.val, om0.val)
