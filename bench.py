@@ -168,6 +168,234 @@ def cpu_baseline_run(workload, X_host_cols, p_sample, max_seconds=25.0):
             "seconds": dt, "iterations": res.iterations}
 
 
+def _oracle_cores():
+    try:
+        from threadpoolctl import threadpool_info
+
+        return int(max([d.get("num_threads", 1) for d in threadpool_info()] + [1]))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _line(metric, value, unit, ms, args, higher, dtype, config, roofline, clocks, launches, cpu, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded generator)", "config": config, "roofline": roofline, "clocks": clocks,
+            "e2e": None, "gpu_launches": launches, "cpu_baseline": cpu}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_row(args):
+    """One line per further row of the hot path, on its own workload:
+    path    -- the 32-point lambda1 path of path_p8192 (warm starts, one graph launch);
+    batch   -- the 16 uneven problems p = 1024 k, solved as one graph launch;
+    adjoint -- dL/dOmega, dL/dX and the hypergradient at p = 16384 after a solve;
+    obs     -- the Obs variant (Z = Y^T X / n on tensor cores) on fp32_p16384.
+    Each carries the FP64 oracle timed on a bounded sample of the same workload."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1710_10769_gb300 as hpc
+    from workloads import (BATCH_PROBLEMS, PATH_LAMBDA1, PATH_LAMBDA2, WORKLOADS, make_x, omega0_for,
+                           sample_x_cpu, sample_x_cuda)
+
+    hbm, bf16, bf16_sus, peak_src = _peaks()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    if args.row == "path":
+        w = WORKLOADS["path_p8192"]
+        lam = sorted(PATH_LAMBDA1, reverse=True)
+        X = make_x(w, device="cuda")
+        s = hpc.Solver(X, lam[0], PATH_LAMBDA2, eps=w.eps, max_iter=100000)
+        for _ in range(args.warmup):
+            s.load_x(X)
+            s.solve_path(lam, PATH_LAMBDA2, return_estimates=False)
+        ms, its, it_ms = 0.0, 0, 0.0
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.load_x(X)
+                pts, _ = s.solve_path(lam, PATH_LAMBDA2, return_estimates=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                its += sum(q["iterations"] for q in pts)
+                it_ms += sum(q["ms"] for q in pts)
+        p = w.p
+        t_it = it_ms / its / 1000.0
+        alg = 4.0 * p * p / t_it / 1e9
+        roof = {"kernel": "path iteration", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
+                "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
+                "note": "algorithmic 4p^2 bytes per iteration / measured iteration time"}
+        # the oracle: warm-started path on the leading 1024 x 1024 sub-problem, first points
+        ps = min(1024, p)
+        Xs = sample_x_cpu(omega0_for(w)[:ps, :ps], w.n, w.seed).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        S = oracle.gram(Xs)
+        om, oits, npts = None, 0, 0
+        for l1 in lam:
+            r = oracle.solve(S, l1, PATH_LAMBDA2, eps=w.eps, max_iter=100000, omega0=om)
+            om, oits, npts = r.omega, oits + r.iterations, npts + 1
+            if time.perf_counter() - t0 > 20.0:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": oits / dt * (ps / p) ** 2, "unit": "iters/s", "cores": _oracle_cores(), "kind": "oracle",
+               "sample": f"FP64 oracle path over the first {npts} lambda1 points (warm starts, {oits} iterations, "
+                         f"{dt:.1f} s) of the leading {ps}x{ps} sub-problem, rate scaled by ({ps}/{p})^2"}
+        _line("lambda1 path iters/s, 32 points on p=8192 n=4096 (ms_per_step = load + whole path)", its / (ms / 1000),
+              "iters/s", ms / args.steps, args, True, "f32",
+              {"workload": "path_p8192", "p": p, "n": w.n, "points": len(lam), "lambda2": PATH_LAMBDA2,
+               "gram_precision": s.precision_name(), "loop": "one graph launch per path"},
+              roof, clk.summary(), None, cpu, iterations_per_step=its // args.steps,
+              iteration_ms=t_it * 1000)
+        s.close()
+        return 0
+
+    if args.row == "batch":
+        Xs = [make_x(wk, device="cuda") for wk in BATCH_PROBLEMS]
+        streams = [torch.cuda.Stream() for _ in BATCH_PROBLEMS]
+        sv = [hpc.Solver(X, wk.lambda1, wk.lambda2, stream=st, eps=wk.eps, max_iter=100000)
+              for X, wk, st in zip(Xs, BATCH_PROBLEMS, streams)]
+        torch.cuda.synchronize()
+        ms, its, per = 0.0, 0, None
+        with ClockSampler(0) as clk:
+            for k in range(args.warmup + args.steps):
+                for sk, X in zip(sv, Xs):
+                    sk.load_x(X)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = hpc.solve_batch(sv)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                if k >= args.warmup:
+                    ms += 1000 * (t1 - t0)
+                    its += sum(q["iterations"] for q in st)
+                    per = [q["iterations"] for q in st]
+        byt = sum(4.0 * wk.p * wk.p * it for wk, it in zip(BATCH_PROBLEMS, per)) * args.steps
+        alg = byt / (ms / 1000) / 1e9
+        roof = {"kernel": "batched solves", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
+                "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
+                "note": "algorithmic 4p^2 bytes per iteration of every problem / batch time"}
+        # the oracle: full solves of the two smallest problems; seconds per iteration
+        # scale as p^2 (Gram included), applied to every problem's iteration count
+        t_it = []
+        for wk in BATCH_PROBLEMS[:2]:
+            Xc = make_x(wk, device="cpu").astype(np.float64)
+            t0 = time.perf_counter()
+            r = oracle.solve(oracle.gram(Xc), wk.lambda1, wk.lambda2, eps=wk.eps, max_iter=100000)
+            t_it.append((time.perf_counter() - t0) / r.iterations / (wk.p / BATCH_PROBLEMS[0].p) ** 2)
+        unit_t = sum(t_it) / len(t_it)
+        t_all = sum(unit_t * (wk.p / BATCH_PROBLEMS[0].p) ** 2 * it for wk, it in zip(BATCH_PROBLEMS, per))
+        cpu = {"value": sum(per) / t_all, "unit": "iters/s", "cores": _oracle_cores(), "kind": "oracle",
+               "sample": "FP64 oracle full solves of the p = 1024 and 2048 problems; seconds per iteration scaled "
+                         "by (p/1024)^2 over the 16 problems' iteration counts"}
+        _line("batched solve iters/s, 16 problems p=1024..16384 (ms_per_step = the batch, Gram excluded)",
+              its / (ms / 1000), "iters/s", ms / args.steps, args, True, "f32",
+              {"workload": "batch16", "p": [wk.p for wk in BATCH_PROBLEMS], "n": "p/2",
+               "loop": "one graph, a branch per problem", "timing": "host clock, device synchronised"},
+              roof, clk.summary(), None, cpu, iterations_per_problem=per)
+        for sk in sv:
+            sk.close()
+        return 0
+
+    if args.row == "adjoint":
+        w = WORKLOADS["adjoint_p16384"]
+        om0 = omega0_for(w)
+        Xtr = sample_x_cuda(om0, w.n, w.seed)
+        Xva = sample_x_cuda(om0, 2048, w.seed + 7919)
+        s = hpc.Solver(Xtr, w.lambda1, w.lambda2, precision=hpc.PREC_FP32, eps=w.eps, max_iter=100000)
+        s.solve()
+        for _ in range(args.warmup):
+            s.backward(Xtr)
+            s.hypergrad(Xva, tol=1e-10)
+        mb, mh = 0.0, 0.0
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                s.backward(Xtr)
+                e1.record(stream)
+                d1, d2, info = s.hypergrad(Xva, tol=1e-10)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                mb += e0.elapsed_time(e1)
+                mh += e1.elapsed_time(e2)
+        p, n = w.p, w.n
+        # backward writes dL/dOmega (p x p) and dL/dX (n x p) and reads X twice
+        byt = 4.0 * p * p + 4.0 * n * p * 3
+        alg = byt / (mb / args.steps / 1000) / 1e9
+        roof = {"kernel": "backward", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
+                "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
+                "note": "dense dL/dOmega and dL/dX written, X read twice"}
+        csr = s.get_omega().to_scipy(p)
+        Xh, Xvh = Xtr.cpu().numpy(), Xva.cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.hypergrad_sparse(Xh, Xvh, csr, w.lambda1, w.lambda2)
+        dt = time.perf_counter() - t0
+        cpu = {"value": dt * 1000, "unit": "ms", "cores": _oracle_cores(), "kind": "oracle",
+               "sample": f"FP64 sparse hypergradient at full size on the GPU's support ({csr.nnz} entries)"}
+        _line("adjoint + hypergradient ms per step at p=16384 (n=4096 train, 2048 held out)",
+              (mb + mh) / args.steps, "ms", (mb + mh) / args.steps, args, False, "f32",
+              {"workload": "adjoint_p16384", "p": p, "n": n, "n_val": 2048, "lambda1": w.lambda1,
+               "lambda2": w.lambda2},
+              roof, clk.summary(), None, cpu, backward_ms=mb / args.steps, hypergrad_ms=mh / args.steps,
+              cg_iterations=info["cg_iterations"])
+        s.close()
+        return 0
+
+    if args.row == "obs":
+        w = WORKLOADS["fp32_p16384"]
+        X = make_x(w, device="cuda")
+        s = hpc.Solver(X, w.lambda1, w.lambda2, variant=hpc.OBS, eps=w.eps, max_iter=100000)
+        for _ in range(args.warmup):
+            s.load_x(X)
+            s.solve()
+        ms, its, gp, gpl, launches = 0.0, 0, 0.0, 0, 0
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.load_x(X)
+                st = s.solve().as_dict()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                its += st["iterations"]
+                gp += st["ms_grad_pass"]
+                gpl += st["grad_pass_launches"]
+                launches += st["kernel_launches"]
+        p, n = w.p, w.n
+        # one gradient pass forms Z = Y^T X / n over the symmetric half: n p (p+1) flop,
+        # three BF16 products per element (BF16X3): a third of the bf16 peak
+        per = gp / max(gpl, 1) / 1000.0
+        tf = n * p * (p + 1) / per / 1e12
+        pk = (bf16_sus if bf16_sus else bf16) / 3.0
+        roof = {"kernel": "obs gradient pass (Z GEMM)", "bound": "tensor", "achieved": tf, "peak": pk,
+                "unit": "TFLOP/s", "frac": tf / pk, "traffic": None,
+                "peak_source": f"{peak_src} (bf16 sustained / 3, BF16X3)", "ms_per_launch": per * 1000}
+        ps = min(1024, p)
+        Xs = sample_x_cpu(omega0_for(w)[:ps, :ps], n, w.seed).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        r = oracle.solve_obs(Xs, w.lambda1, w.lambda2, eps=w.eps, max_iter=100000)
+        dt = time.perf_counter() - t0
+        cpu = {"value": r.iterations / dt * (ps / p) ** 2, "unit": "iters/s", "cores": _oracle_cores(),
+               "kind": "oracle",
+               "sample": f"FP64 oracle Obs solve ({r.iterations} iterations, {dt:.1f} s) of the leading {ps}x{ps} "
+                         f"sub-problem (same n), rate scaled by ({ps}/{p})^2"}
+        _line("Obs prox-grad iters/s at p=16384 n=8192 (ms_per_step = load + solve)", its / (ms / 1000), "iters/s",
+              ms / args.steps, args, True, "f32",
+              {"workload": "fp32_p16384", "variant": "obs", "p": p, "n": n, "lambda1": w.lambda1,
+               "lambda2": w.lambda2, "z_precision": s.precision_name()},
+              roof, clk.summary(), launches, cpu, iterations_per_step=its // args.steps)
+        s.close()
+        return 0
+    raise SystemExit(f"unknown row {args.row}")
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -191,7 +419,8 @@ def run_reference(args):
             secs.append(r["seconds"])
             its.append(r["iterations"])
     value = sum(its) / sum(secs) * (ps / w.p) ** 2
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC.replace("p=65536 n=32768", f"p={w.p} n={w.n}"), "value": value,
+            "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs) / (ps / w.p) ** 2,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded generator, leading sub-problem of the workload)",
@@ -225,6 +454,8 @@ def main(argv=None):
     ap.add_argument("--x-dtype", default="workload", choices=["workload", "f32", "bf16"],
                     help="store X in this dtype instead of the workload's (profiling the one-product BF16 Gram "
                          "at sizes a full ncu capture allows)")
+    ap.add_argument("--row", default=None, choices=["path", "batch", "adjoint", "obs"],
+                    help="time a further row of the hot path instead of the headline solve")
     ap.add_argument("--screen-bounds", type=int, default=1, choices=[0, 1],
                     help="0: screen without the block-maxima bounds (same result; for comparison)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
@@ -232,6 +463,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.row:
+        return run_row(args)
 
     import numpy as np
     import torch
@@ -258,9 +491,14 @@ def main(argv=None):
         X = X.to(torch.bfloat16 if args.x_dtype == "bf16" else torch.float32)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    xdt = hpc.BF16 if w.x_dtype == "bf16" else hpc.F32
+    xdt = {"bf16": hpc.BF16, "f32": hpc.F32, "f64": hpc.F64}[w.x_dtype]
+    f64 = w.x_dtype == "f64"
+    # FP64 workloads solve in FP64 values with the FP64 Gram
+    vopt = dict(value_dtype=hpc.F64) if f64 else {}
+    if f64 and args.precision == "auto":
+        prec = hpc.PREC_FP64
     solver = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=prec, eps=w.eps,
-                        max_iter=100000, device_loop=args.device_loop)
+                        max_iter=100000, device_loop=args.device_loop, **vopt)
 
     tuning, tune_trials = solver.get_tuning(), []
     if args.autotune:
@@ -368,7 +606,7 @@ def main(argv=None):
     other = None
     if args.compare_loops and rank == 0:
         alt = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=prec, eps=w.eps,
-                         max_iter=100000, device_loop=1 - args.device_loop)
+                         max_iter=100000, device_loop=1 - args.device_loop, **vopt)
         alt.set_tuning(**tuning)
         alt.load_x(X)
         alt.solve()
@@ -384,7 +622,7 @@ def main(argv=None):
         alt.close()
 
     plain = None
-    if not args.no_plain and solver.precision_used() != hpc.PREC_FP32 and rank == 0:
+    if not args.no_plain and solver.precision_used() not in (hpc.PREC_FP32, hpc.PREC_FP64) and rank == 0:
         ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=hpc.PREC_FP32, eps=w.eps,
                         max_iter=100000, device_loop=args.device_loop)
         ps.set_tuning(**tuning)
@@ -408,27 +646,30 @@ def main(argv=None):
     if not args.no_cpu and rank == 0:
         from workloads import omega0_for, round_to_bf16, sample_x_cpu
 
-        om0 = omega0_for(w)[: args.cpu_sample_p, : args.cpu_sample_p]
+        ps = min(args.cpu_sample_p, w.p)
+        om0 = omega0_for(w)[:ps, :ps]
         Xs = sample_x_cpu(om0, w.n, w.seed)
         if w.x_dtype == "bf16":
             Xs = round_to_bf16(Xs.astype(np.float32)).astype(np.float64)
-        c = cpu_baseline_run(w, Xs, args.cpu_sample_p)
+        c = cpu_baseline_run(w, Xs, ps)
         cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
         gpu_launches = sum(r["kernel_launches"] for r in recs) + sum(1 for _ in recs)
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC.replace("p=65536 n=32768", f"p={p} n={n}"), "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if (w.x_dtype == "bf16" and tensor_gram) else "f32",
-            "data": "synthetic (seeded: random SDD Omega0 with ~8 nnz/row, X = Z L^-T)",
+            "dtype": "f64" if f64 else ("bf16" if (w.x_dtype == "bf16" and tensor_gram) else "f32"),
+            "data": f"synthetic (seeded: {w.graph} SDD Omega0, X = Z L^-T)",
             "config": {"workload": w.name, "p": p, "n": n, "lambda1": w.lambda1, "lambda2": w.lambda2,
-                       "eps": w.eps, "x_dtype": w.x_dtype, "s_dtype": "f32",
+                       "eps": w.eps, "x_dtype": w.x_dtype, "s_dtype": "f64" if f64 else "f32",
                        "gram_precision": solver.precision_name(), "parallelism": f"replicas x{ws}",
                        "loop": "device (one CUDA graph per solve)" if args.device_loop else "host-driven",
                        "tuning": tuning, "autotuned": bool(args.autotune),
-                       "l2": "inputs > L2 (X 4.3 GB, S 17.2 GB); no flush"},
+                       "l2": (f"inputs > L2 (X {X.numel() * X.element_size() / 1e9:.2f} GB, S {4 * (1 + f64) * p * p / 1e9:.2f} GB); no flush"
+                              if (1 + f64) * 4 * p * p > 129e6 else "S fits in L2 (small latency-bound case); no flush")},
             "iterations_per_step": [r["iterations"] for r in recs],
             "ls_trials_per_step": [r["ls_trials"] for r in recs],
             "time_to_converge_ms": ms_all / args.steps,
