@@ -340,19 +340,22 @@ int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* 
                      int precision, void* cuda_stream);
 
 /* ---------------------------------------------------------------- tuning */
-/* Launch shapes of a handle's kernels.  None of them changes a result bit: the
- * Gram's tiles are summed in the same order whatever their schedule, and the
- * iterations run the same kernels on the same data.  The paper tunes its
- * replication factors and grid shapes per machine (Section 4); these are the
- * single-GPU counterparts. */
+/* Launch shapes of a handle's kernels.  The Gram's tiles are summed in the same
+ * order whatever their schedule, and the candidates are sorted per row whatever
+ * their emission order, so S and the candidate values do not depend on them.
+ * The line-search grid (ls_blocks_per_sm) regroups the FP64 partial sums of the
+ * sufficient-decrease test, which can move their last bits; a step changes only
+ * if that decides an exact tie.  The paper tunes its replication factors and grid
+ * shapes per machine (Section 4); these are the single-GPU counterparts. */
 typedef struct {
     int32_t gram_band;         /* row blocks of 128 per band of the tensor-core Gram's
-                                  tile order, 1..256 (16): sets which X panels the
+                                  tile order, 1..256 (32): sets which X panels the
                                   tiles running together share in L2               */
     int32_t ls_window;         /* tau values per line-search launch: 1, 2, 4, 8, 16 */
     int32_t ls_blocks_per_sm;  /* resident blocks per SM of the line-search
                                   evaluation, 0 = as many as fit (2)               */
-    int32_t rows_ctas_per_sm;  /* CTAs per SM of the off-diagonal row kernel, 1..4 (2) */
+    int32_t rows_ctas_per_sm;  /* CTAs per SM of the off-diagonal row kernel, 1..4 (2);
+                                  3 and 4 run a form sized for 3 resident CTAs  */
     int32_t gram_maxima;       /* 1: the tensor-core Gram's epilogue writes the bound
                                   screening's block maxima; 0: a pass over S after it (1) */
     int32_t screen_bounds;     /* 1: the screening pass reads only the segments of S

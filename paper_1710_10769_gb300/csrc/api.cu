@@ -129,7 +129,7 @@ struct hpc_ctx {
     void* x_stage = nullptr;
     size_t x_stage_bytes = 0;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{16, 8, 0, 2, 1, 1};
+    hpc_tuning tune{32, 8, 0, 2, 1, 1};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -1807,7 +1807,7 @@ int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, h
         IterateCopy c;
         status = save_iterate(h, c);
         struct Knob { int id; std::vector<int> vals; };
-        const Knob knobs[] = {{1, {2, 4, 8, 16}}, {3, {1, 2, 3, 4}}, {2, {1, 2}}};
+        const Knob knobs[] = {{1, {2, 4, 8, 16}}, {3, {1, 2, 3, 4}}, {2, {1, 2, 3}}};
         for (const Knob& k : knobs) {
             if (status != HPC_OK) break;
             if (k.id == 3 && h->variant == HPC_OBS) continue;       // Obs has no row kernel

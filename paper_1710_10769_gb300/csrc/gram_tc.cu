@@ -11,17 +11,21 @@
 //   BF16 X           : one panel, one product (bf16 x bf16 is exact in FP32);
 //   TF32             : FP32 panel rounded to TF32, kind::tf32 products.
 //
-// Tiles.  One CTA computes a 128 x 256 tile S[I, J] (UMMA M = 128, N = 256,
-// 256 TMEM columns) over the whole K = n, for the tiles that touch the upper
-// triangle, visited in bands of 16 row blocks so that CTAs in flight share A
-// and B panels in L2.  Each entry with i <= j is written together with its
+// Tiles.  A 128 x 256 tile S[I, J] (UMMA M = 128, N = 256) is accumulated over
+// the whole K = n in 256 TMEM columns.  Only the tiles that touch the upper
+// triangle run, in bands of row blocks (a tuning knob) so that the tiles in flight
+// share A and B panels in L2.  Each entry with i <= j is written together with its
 // mirror S[j, i]: S is bitwise symmetric by construction.
 //
-// Roles (128 threads): thread 0 issues TMA loads, thread 32 issues MMAs and
-// commits, warp 1 owns the TMEM allocation, and all four warps drain the
-// accumulator (warp w reads TMEM lanes 32w..32w+31).  Every mbarrier wait is
-// bounded; on timeout the CTA records an error word, stops issuing, waits
-// (bounded) for its own copies and MMAs, frees its TMEM and returns.
+// Persistent kernel (192 threads, one CTA per SM, CTA g takes tiles g, g + grid,
+// ...): warp 0 issues TMA loads into a ring of stages, warp 1 issues MMAs from
+// one lane and owns the TMEM allocation (two 256-column accumulators, so the
+// epilogue of one tile overlaps the MMAs of the next), warps 2-5 drain the
+// accumulator (TMEM lanes 32 (w % 4) .. + 31), scale by 1/n, store the tile and
+// its mirror, and optionally write the block maxima of |S| for the bound
+// screening.  Every mbarrier wait is bounded; on timeout the CTA records an error
+// word, stops issuing, waits (bounded) for its own copies and MMAs, frees its
+// TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -183,144 +187,6 @@ struct Cfg {
     static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers and flags*/
                                  + kBN * 4 /*column maxima of the persistent epilogue*/;
 };
-
-template <int MODE>
-__global__ void __launch_bounds__(128, 1)
-k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-          const int2* __restrict__ tiles, int k_tiles, int64_t p, int64_t n, float* __restrict__ S, int64_t lds,
-          int vec_ok) {
-    using C = Cfg<MODE>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes);
-    uint64_t* empty = full + C::kStages;
-    uint64_t* accum = empty + C::kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 tile = tiles[blockIdx.x];
-    const int I0 = tile.x * kBM, J0 = tile.y * kBN;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < C::kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(accum, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
-        if (C::kPieces > 1) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
-    }
-    if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    int issued = 0;   // stages whose TMA loads were issued (producer thread)
-    if (threadIdx.x == 0) {
-        // ---------------- TMA producer
-        for (int kt = 0; kt < k_tiles; ++kt) {
-            const int s = kt % C::kStages;
-            const uint32_t ph = (uint32_t)(kt / C::kStages) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 1)) break;
-            uint8_t* st = smem + s * C::kStageBytes;
-            mbar_expect_tx(&full[s], C::kStageBytes);
-            const int kc = kt * C::kBK;
-            for (int pc = 0; pc < C::kPieces; ++pc) {
-                const CUtensorMap* m = pc == 0 ? &map_hi : &map_lo;
-                uint8_t* a = st + pc * (kABytes + kBBytes);
-                uint8_t* b = a + kABytes;
-                tma_load_2d(a, m, &full[s], kc, I0);
-                tma_load_2d(b, m, &full[s], kc, J0);
-                tma_load_2d(b + kABytes, m, &full[s], kc, J0 + kBM);
-            }
-            ++issued;
-        }
-    } else if (threadIdx.x == 32) {
-        // ---------------- MMA issuer
-        constexpr uint32_t idesc = instr_desc<MODE>();
-        bool ok = true;
-        for (int kt = 0; kt < k_tiles && ok; ++kt) {
-            const int s = kt % C::kStages;
-            const uint32_t ph = (uint32_t)(kt / C::kStages) & 1u;
-            if (!mbar_wait(&full[s], ph, abort_flag, 2)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t st = smem_u32(smem + s * C::kStageBytes);
-            const uint32_t a_hi = st, b_hi = st + kABytes;
-            const uint32_t a_lo = st + (kABytes + kBBytes), b_lo = a_lo + kABytes;
-#pragma unroll
-            for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
-                const uint32_t off = kk * 32;   // bytes along the swizzled K row
-                const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-                umma<MODE>(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
-                if constexpr (C::kTerms == 3) {
-                    umma<MODE>(tmem, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
-                    umma<MODE>(tmem, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
-                }
-            }
-            umma_commit(&empty[s]);    // frees the stage once these MMAs have read it
-        }
-        umma_commit(accum);            // accumulator complete (or all issued MMAs done)
-    }
-    __syncwarp();
-
-    // ---------------- epilogue: TMEM -> registers -> S (owner rule i <= j, plus mirror)
-    bool have = mbar_wait(accum, 0, abort_flag, 3) && !*abort_flag;
-    have = __all_sync(kFull, have);     // tcgen05.ld is warp-collective
-    tc_fence_after();
-    if (have) {
-        const float dn = (float)n;
-        const int r = warp * 32 + lane;
-        const int64_t i = I0 + r;
-#pragma unroll 1
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            tmem_ld_wait();
-            if (i >= p) continue;
-            const int64_t jb = J0 + c0;
-            float o[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) o[q] = __uint_as_float(v[q]) / dn;
-            // direct row segment S[i, jb .. jb+31]
-            if (vec_ok && jb >= i && jb + 31 < p) {     // 16-byte aligned rows only
-                float4* dst = reinterpret_cast<float4*>(S + i * lds + jb);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int64_t j = jb + q;
-                    if (j >= i && j < p) S[i * lds + j] = o[q];
-                }
-            }
-            // mirror S[j, i] for j > i: for fixed q the warp writes 32 consecutive floats
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int64_t j = jb + q;
-                if (j > i && j < p) S[j * lds + i] = o[q];
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_flag && threadIdx.x == 0) {
-        // drain: bounded waits for the loads this CTA issued, so no copy lands after exit
-        for (int kt = max(0, issued - C::kStages); kt < issued; ++kt) {
-            const int s = kt % C::kStages;
-            const uint32_t ph = (uint32_t)(kt / C::kStages) & 1u;
-            for (long long it = 0; it < (1ll << 22) && !mbar_try_wait(&full[s], ph); ++it) __nanosleep(64);
-        }
-    }
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
-    }
-}
 
 // Non-negative float rounded up to BF16 (an upper bound).
 __device__ __forceinline__ uint16_t bf16_up_f(float x) {
@@ -623,19 +489,24 @@ k_prep(const TX* __restrict__ X, int64_t n, int64_t p, void* __restrict__ hi, vo
     }
 }
 
-// BF16 X into the BF16 panel: a plain transpose, 64 x 64 elements per block with
-// 16-byte loads and stores (vec: rows of X start on 16-byte boundaries).  The
-// shared tile's rows are padded to 72 elements (144 bytes, a multiple of 16).
+// BF16 X into the BF16 panel: a transpose of 64 (k) x 128 (i) tiles with 16-byte
+// global loads and stores (vec: rows of X start on 16-byte boundaries).  In the
+// shared tile the 16-byte chunks of row r sit XOR-swizzled by (r / 8) % 8, so the
+// column reads of the store phase -- the 8 k-groups of a warp at the same columns --
+// fall on 8 different chunks, all 32 banks.  A thread reads 32-bit words (two
+// adjacent i) and writes the two output rows.
+__device__ __forceinline__ int prep_col(int r, int col) { return (((col >> 3) ^ ((r >> 3) & 7)) << 3) | (col & 7); }
+
 __global__ void __launch_bounds__(256)
 k_prep_bf16(const uint16_t* __restrict__ X, int64_t n, int64_t p, uint16_t* __restrict__ out, int64_t n_pad,
             int vec) {
-    __shared__ __align__(16) uint16_t t[64][72];
-    const int64_t k0 = (int64_t)blockIdx.x * 64, i0 = (int64_t)blockIdx.y * 64;
+    __shared__ __align__(16) uint16_t t[64][128];
+    const int64_t k0 = (int64_t)blockIdx.x * 64, i0 = (int64_t)blockIdx.y * 128;
     const int tid = threadIdx.x;
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const int r = tid / 8 + rr * 32, c = (tid % 8) * 8;
-        const int64_t k = k0 + r, i = i0 + c;
+    for (int rr = 0; rr < 4; ++rr) {
+        const int r = tid / 16 + rr * 16, ch = tid % 16;
+        const int64_t k = k0 + r, i = i0 + ch * 8;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (k < n) {
             if (vec && i + 8 <= p) {
@@ -648,18 +519,26 @@ k_prep_bf16(const uint16_t* __restrict__ X, int64_t n, int64_t p, uint16_t* __re
                                e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
             }
         }
-        *reinterpret_cast<uint4*>(&t[r][c]) = v;
+        *reinterpret_cast<uint4*>(&t[r][prep_col(r, ch * 8)]) = v;
     }
     __syncthreads();
+    // 64 row pairs x 8 k-groups, two per thread; n_pad and p_pad are multiples of 64
+    // and 128, so every output row and k-group of the tile is inside the panel
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-        const int ri = tid / 8 + rr * 32, kc = (tid % 8) * 8;
-        const int64_t i = i0 + ri, k = k0 + kc;
-        if (k >= n_pad) continue;
-        uint32_t w[4];
+        const int kg = tid % 8, il = 2 * (tid / 8 + rr * 32);
+        uint32_t a[4], b[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = t[kc + 2 * q][ri] | ((uint32_t)t[kc + 2 * q + 1][ri] << 16);
-        *reinterpret_cast<uint4*>(out + i * n_pad + k) = make_uint4(w[0], w[1], w[2], w[3]);
+        for (int q = 0; q < 4; ++q) {
+            const int r0 = 8 * kg + 2 * q, r1 = r0 + 1;
+            const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&t[r0][prep_col(r0, il)]);
+            const uint32_t w1 = *reinterpret_cast<const uint32_t*>(&t[r1][prep_col(r1, il)]);
+            a[q] = (w0 & 0xffffu) | (w1 << 16);               // row il:     k = r0, r1
+            b[q] = (w0 >> 16) | (w1 & 0xffff0000u);           // row il + 1: k = r0, r1
+        }
+        const int64_t i = i0 + il, k = k0 + 8 * kg;
+        *reinterpret_cast<uint4*>(out + i * n_pad + k) = make_uint4(a[0], a[1], a[2], a[3]);
+        *reinterpret_cast<uint4*>(out + (i + 1) * n_pad + k) = make_uint4(b[0], b[1], b[2], b[3]);
     }
 }
 
@@ -735,7 +614,7 @@ bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
 
 template <int MODE>
 cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles, int64_t n, int64_t p, float* S,
-                        int64_t lds, cudaStream_t s, bool persistent = false, uint16_t* m1 = nullptr, int nbm = 0) {
+                        int64_t lds, cudaStream_t s, uint16_t* m1 = nullptr, int nbm = 0) {
     using C = Cfg<MODE>;
     CUtensorMap mh, ml;
     std::memset(&mh, 0, sizeof mh);
@@ -746,21 +625,15 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
     const int k_tiles = (int)(g.n_pad / C::kBK);
     // float4 row stores need 16-byte aligned rows: lds % 4 == 0 and an aligned base
     const int vec_ok = (lds % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0) ? 1 : 0;
-    if (persistent) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_gram_tc_persist<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-        if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        const int grid = (int)std::min<int64_t>(g.ntiles, sms);
-        k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n,
-                                                                       S, lds, vec_ok, m1, nbm);
-        return cudaGetLastError();
-    }
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gram_tc_persist<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return e;
-    k_gram_tc<MODE><<<(unsigned)g.ntiles, 128, C::kSmem, s>>>(mh, ml, tiles, k_tiles, p, n, S, lds, vec_ok);
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(g.ntiles, sms);
+    k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n, S,
+                                                                   lds, vec_ok, m1, nbm);
     return cudaGetLastError();
 }
 
@@ -770,11 +643,11 @@ void launch_prep(const void* X, int mode, int64_t n, int64_t p, void* hi, void* 
     const TX* x = static_cast<const TX*>(X);
     if constexpr (std::is_same<TX, __nv_bfloat16>::value) {
         if (mode == kModeBf16) {
-            // n_pad and p_pad are multiples of 64: every block's tile is inside the panel
+            // n_pad is a multiple of 64 and p_pad of 256: every block's tile is inside the panel
             const int vec = (p % 8 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0) ? 1 : 0;
-            dim3 g64((unsigned)(g.n_pad / 64), (unsigned)(g.p_pad / 64));
-            k_prep_bf16<<<g64, 256, 0, s>>>(reinterpret_cast<const uint16_t*>(X), n, p, static_cast<uint16_t*>(hi),
-                                            g.n_pad, vec);
+            dim3 grid((unsigned)(g.n_pad / 64), (unsigned)(g.p_pad / 128));
+            k_prep_bf16<<<grid, 256, 0, s>>>(reinterpret_cast<const uint16_t*>(X), n, p, static_cast<uint16_t*>(hi),
+                                             g.n_pad, vec);
             return;
         }
     }
@@ -818,9 +691,9 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     if (e != cudaSuccess) return e;
     if (launches) *launches += 2;
     if (before_kernel && (e = cudaEventRecord(before_kernel, s)) != cudaSuccess) return e;
-    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, true, m1, nbm);
-    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, true, m1, nbm);
-    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, true, m1, nbm);
+    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
+    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
+    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
 }
 
 int gram_tc_take_error() {

@@ -1015,8 +1015,10 @@ k_rows_items(int p, int nbm, const unsigned short* __restrict__ m1, const int4* 
 constexpr int kRowsPerItem = 8;
 constexpr int kTermBatch = 8;
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 2)
+// MINB: resident CTAs per SM the registers are sized for (2: 128 registers; 3: 80,
+// with a small spill); the tuning knob rows_ctas_per_sm >= 3 selects the second.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __restrict__ rinfo,
                    const T* __restrict__ rdv, const int* __restrict__ offlist, const int* __restrict__ ci,
                    const T* __restrict__ cv, const int2* __restrict__ row_items, int row_items_cap, Emit<T> em,
@@ -1730,9 +1732,10 @@ __device__ __forceinline__ void acc_merge(double& a, double b) { a += b; }
 // rows (prefix uoff), so rows with thousands of candidates spread over many warps.
 // Terms [1]-[3] are per entry: each diagonal unit (a = b) warp-reduces them into
 // the warp's shared accumulators, which keeps the register count (and so the
-// number of resident warps on a persistent grid) where the gathers need it.
+// number of resident warps on a persistent grid) where the gathers need it: three
+// CTAs per SM for windows of up to 4 step sizes, two for wider ones.
 template <typename T, int M>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, (M <= 4) ? 3 : 2)
 k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride, double* part_ls,
           const Ctrl* ctrl) {
     using A = typename AccOf<T>::type;
@@ -2284,9 +2287,15 @@ void launch_grad_screen(const IterBufs<T>& b, cudaStream_t s) {
                                                                  b.cur.ci, b.cur.cv, b.row_items, b.row_items_cap,
                                                                  b.ctrl);
     }
-    k_grad_screen_rows<T><<<b.num_sms * std::max(1, std::min(4, b.rows_ctas_per_sm)), kThreads, 0, s>>>(
-        b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.row_items : nullptr,
-        b.row_items_cap, b.em, b.ctrl);
+    const int rows_ctas = std::max(1, std::min(4, b.rows_ctas_per_sm));
+    if (rows_ctas >= 3)
+        k_grad_screen_rows<T, 3><<<b.num_sms * rows_ctas, kThreads, 0, s>>>(
+            b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.row_items : nullptr,
+            b.row_items_cap, b.em, b.ctrl);
+    else
+        k_grad_screen_rows<T, 2><<<b.num_sms * rows_ctas, kThreads, 0, s>>>(
+            b.S, b.ld, b.p, b.rinfo, b.rdv, b.offlist, b.cur.ci, b.cur.cv, b.m1 ? b.row_items : nullptr,
+            b.row_items_cap, b.em, b.ctrl);
 }
 
 // Group maxima of the block maxima: m1g[i][g] = max over the blocks 8g .. 8g+7 of
