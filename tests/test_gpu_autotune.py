@@ -1,5 +1,5 @@
-"""hpc_autotune / hpc_set_tuning: launch shapes are chosen by timing, never change a
-result bit, and the autotuner leaves the iterate as it found it."""
+"""hpc_autotune / hpc_set_tuning: launch shapes are chosen by timing, leave the
+iterates unchanged, and the autotuner leaves the iterate as it found it."""
 import numpy as np
 import pytest
 
@@ -33,6 +33,29 @@ def test_autotune_picks_valid_shapes_and_keeps_results(lib):
         om = s.omega_dense()
     assert np.array_equal(om, om_ref)
     assert st["iterations"] == st_ref["iterations"] and st["ls_trials"] == st_ref["ls_trials"]
+
+
+@pytest.mark.parametrize("shape", [
+    dict(rows_ctas_per_sm=3, ls_blocks_per_sm=3, ls_window=4),     # the 3-CTA forms
+    dict(rows_ctas_per_sm=1, ls_blocks_per_sm=1, ls_window=2),
+    dict(rows_ctas_per_sm=4, ls_blocks_per_sm=0, ls_window=16, gram_band=2, gram_maxima=0),
+])
+def test_launch_shapes_give_the_default_iterates(lib, shape):
+    """Every form the knobs select reaches the default shapes' estimate, iteration for
+    iteration, including the row kernel's and line-search kernel's 3-CTA forms."""
+    torch = _torch()
+    X = torch.as_tensor(small_problem(1024, 400, 5.0, seed=17).astype(np.float32)).cuda()
+    out = []
+    for kw in ({}, shape):
+        with lib.Solver(X, 0.08, 0.1, precision=lib.PREC_BF16X3, eps=1e-7) as s:
+            if kw:
+                s.set_tuning(**kw)
+                s.load_x(X)
+            st = s.solve().as_dict()
+            out.append((s.omega_dense(), st))
+    (a, sa), (b, sb) = out
+    assert np.array_equal(a, b)
+    assert sa["iterations"] == sb["iterations"] and sa["ls_trials"] == sb["ls_trials"]
 
 
 def test_autotune_restores_the_iterate(lib):
