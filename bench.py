@@ -441,7 +441,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bf16_p65536")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3", "tf32"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-sample-p", type=int, default=2048)
@@ -579,27 +579,37 @@ def main(argv=None):
                 "peak_source": peak_src}
     roof = roof_gram if gram_ms >= scr_ms else roof_scr
 
-    # end to end through the C ABI with host buffers: H2D of X inside the timed region,
-    # D2H of the CSR result
+    # end to end through the C ABI with host buffers: each step reads its X from pinned
+    # host memory and copies the CSR result back.  Steps alternate between two pinned
+    # buffers (same contents), as a pipeline over successive data sets would: the next
+    # step's X is staged (hpc_prefetch_x: a copy-engine transfer during this step's
+    # Gram, its panel transpose during this step's solve).  Step 0 reads its own X and
+    # the last step stages nothing, so the region holds one transfer per step.  One
+    # timed region over all steps, after an untimed step that sizes the buffers.
     e2e = None
     if args.e2e_steps > 0:
-        Xh = X.cpu().pin_memory()
-        e2e_ms, e2e_its, d2h = 0.0, 0, 0
-        for k in range(args.e2e_steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            solver.load_x(Xh)
+        bufs = [X.cpu().pin_memory(), X.cpu().pin_memory()]
+        solver.load_x(bufs[0])
+        solver.solve()
+        solver.get_omega(np.float32)
+        torch.cuda.synchronize()
+        e2e_its, d2h = 0, 0
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            if k + 1 < args.e2e_steps:
+                solver.prefetch_x(bufs[(k + 1) % 2])
+            solver.load_x(bufs[k % 2])
             st = solver.solve().as_dict()
             csr = solver.get_omega(np.float32)
-            t1 = time.perf_counter()
-            if k >= 1:
-                e2e_ms += (t1 - t0) * 1000
-                e2e_its += st["iterations"]
-                d2h += csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes
+            e2e_its += st["iterations"]
+            d2h += csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1000
         e2e = {"value": e2e_its / (e2e_ms / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
-               "d2h_bytes_per_step": int(d2h // max(args.e2e_steps, 1))}
-        del Xh
+               "h2d_bytes_per_step": int(bufs[0].numel() * bufs[0].element_size()),
+               "d2h_bytes_per_step": int(d2h // args.e2e_steps), "steps": args.e2e_steps,
+               "overlap": "next step's X staged during this step (hpc_prefetch_x), two pinned buffers"}
+        del bufs
 
     # the same step with the other loop driver (host-driven iterations vs one CUDA-graph
     # launch per solve), for comparison

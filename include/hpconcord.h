@@ -148,6 +148,28 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
  * set-up cost of a solve: a time-to-converge is hpc_load_x + hpc_solve. */
 int hpc_load_x(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host);
 
+/* Stage the next data set while the handle works on the current one.  The
+ * paper's data arrives once per problem (Alg. 1 step 2 builds S from it).  A
+ * caller that solves a sequence of data sets can overlap the next one's arrival
+ * with the current load and solve.
+ *  - Host X is copied into the handle's staging buffer by the copy engine, on a
+ *    second stream, starting at once. It needs no SM, so the copy runs alongside
+ *    the Gram of the next hpc_load_x. Device X needs no copy.
+ *  - That next hpc_load_x (of another X) then queues the staged X's panel
+ *    preparation (the tensor-core Gram's transpose) on the second stream, behind
+ *    its own Gram, so the preparation overlaps the solve.
+ *  - A later hpc_load_x of the staged X (same pointer and type) uses the prepared
+ *    panels, or the staged copy if no Gram came in between.
+ *  - Pipeline over data sets X_0, X_1, ...: hpc_prefetch_x(X_{k+1}),
+ *    hpc_load_x(X_k), hpc_solve, for k = 0, 1, ...  The buffers of consecutive
+ *    data sets must differ.
+ *  - Arguments as hpc_load_x. X must keep its contents until it has been loaded.
+ *  - A load that stages pageable host memory, and hpc_hypergrad, first wait for
+ *    the staging and discard it.
+ *  - A no-op (HPC_OK) on the other paths (Obs, FP32/FP64 Gram), and before the
+ *    first hpc_load_x has sized the handle's buffers. */
+int hpc_prefetch_x(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host);
+
 /* Run Alg. 1 from the current iterate until the stopping rule holds (HPC_OK),
  * max_iter is reached (HPC_NOT_CONVERGED) or an error occurs.  stats may be NULL. */
 int hpc_solve(hpc_handle h, hpc_stats* stats);

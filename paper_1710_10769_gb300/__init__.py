@@ -111,6 +111,7 @@ _SIGS = {
     "hpc_create": (C.c_int, [C.POINTER(_P), _P, C.c_int, C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_int,
                              C.POINTER(Options), _P]),
     "hpc_load_x": (C.c_int, [_P, _P, C.c_int, C.c_int]),
+    "hpc_prefetch_x": (C.c_int, [_P, _P, C.c_int, C.c_int]),
     "hpc_solve": (C.c_int, [_P, C.POINTER(Stats)]),
     "hpc_iterate": (C.c_int, [_P, C.c_int64, C.POINTER(Stats)]),
     "hpc_get_omega": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.c_int, C.c_int]),
@@ -265,6 +266,18 @@ class Solver:
         else:
             st = self._lib.hpc_load_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 0)
         return _check(st, "hpc_load_x")
+
+    def prefetch_x(self, X):
+        """hpc_prefetch_x: stage the next data set on a second stream (a copy-engine
+        transfer now, its Gram panels after the next load's Gram).  Pipeline:
+        prefetch_x(X_next); load_x(X_cur); solve() -- with distinct buffers."""
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X)
+            st = self._lib.hpc_prefetch_x(self._h, X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1)
+        else:
+            assert X.is_contiguous()
+            st = self._lib.hpc_prefetch_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 0 if X.is_cuda else 1)
+        return _check(st, "hpc_prefetch_x")
 
     def solve(self, allow_not_converged=True) -> Stats:
         st = self._lib.hpc_solve(self._h, C.byref(self.stats))

@@ -499,46 +499,52 @@ __device__ __forceinline__ int prep_col(int r, int col) { return (((col >> 3) ^ 
 
 __global__ void __launch_bounds__(256)
 k_prep_bf16(const uint16_t* __restrict__ X, int64_t n, int64_t p, uint16_t* __restrict__ out, int64_t n_pad,
-            int vec) {
+            int64_t p_pad, int vec) {
     __shared__ __align__(16) uint16_t t[64][128];
-    const int64_t k0 = (int64_t)blockIdx.x * 64, i0 = (int64_t)blockIdx.y * 128;
     const int tid = threadIdx.x;
+    const int64_t nkt = n_pad / 64, ntiles = nkt * (p_pad / 128);
+    // one tile per block, or a grid-stride loop when the grid is smaller (a staging
+    // that shares the GPU with a solve)
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t k0 = (tile % nkt) * 64, i0 = (tile / nkt) * 128;
+        __syncthreads();        // the previous tile's reads of t are done
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-        const int r = tid / 16 + rr * 16, ch = tid % 16;
-        const int64_t k = k0 + r, i = i0 + ch * 8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (k < n) {
-            if (vec && i + 8 <= p) {
-                v = *reinterpret_cast<const uint4*>(X + k * p + i);
-            } else {
-                uint16_t e[8];
+        for (int rr = 0; rr < 4; ++rr) {
+            const int r = tid / 16 + rr * 16, ch = tid % 16;
+            const int64_t k = k0 + r, i = i0 + ch * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k < n) {
+                if (vec && i + 8 <= p) {
+                    v = *reinterpret_cast<const uint4*>(X + k * p + i);
+                } else {
+                    uint16_t e[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) e[q] = (i + q < p) ? X[k * p + i + q] : (uint16_t)0;
-                v = make_uint4(e[0] | ((uint32_t)e[1] << 16), e[2] | ((uint32_t)e[3] << 16),
-                               e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
+                    for (int q = 0; q < 8; ++q) e[q] = (i + q < p) ? X[k * p + i + q] : (uint16_t)0;
+                    v = make_uint4(e[0] | ((uint32_t)e[1] << 16), e[2] | ((uint32_t)e[3] << 16),
+                                   e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
+                }
             }
+            *reinterpret_cast<uint4*>(&t[r][prep_col(r, ch * 8)]) = v;
         }
-        *reinterpret_cast<uint4*>(&t[r][prep_col(r, ch * 8)]) = v;
-    }
-    __syncthreads();
-    // 64 row pairs x 8 k-groups, two per thread; n_pad and p_pad are multiples of 64
-    // and 128, so every output row and k-group of the tile is inside the panel
+        __syncthreads();
+        // 64 row pairs x 8 k-groups, two per thread; n_pad and p_pad are multiples of 64
+        // and 128, so every output row and k-group of the tile is inside the panel
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const int kg = tid % 8, il = 2 * (tid / 8 + rr * 32);
-        uint32_t a[4], b[4];
+        for (int rr = 0; rr < 2; ++rr) {
+            const int kg = tid % 8, il = 2 * (tid / 8 + rr * 32);
+            uint32_t a[4], b[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int r0 = 8 * kg + 2 * q, r1 = r0 + 1;
-            const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&t[r0][prep_col(r0, il)]);
-            const uint32_t w1 = *reinterpret_cast<const uint32_t*>(&t[r1][prep_col(r1, il)]);
-            a[q] = (w0 & 0xffffu) | (w1 << 16);               // row il:     k = r0, r1
-            b[q] = (w0 >> 16) | (w1 & 0xffff0000u);           // row il + 1: k = r0, r1
+            for (int q = 0; q < 4; ++q) {
+                const int r0 = 8 * kg + 2 * q, r1 = r0 + 1;
+                const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&t[r0][prep_col(r0, il)]);
+                const uint32_t w1 = *reinterpret_cast<const uint32_t*>(&t[r1][prep_col(r1, il)]);
+                a[q] = (w0 & 0xffffu) | (w1 << 16);               // row il:     k = r0, r1
+                b[q] = (w0 >> 16) | (w1 & 0xffff0000u);           // row il + 1: k = r0, r1
+            }
+            const int64_t i = i0 + il, k = k0 + 8 * kg;
+            *reinterpret_cast<uint4*>(out + i * n_pad + k) = make_uint4(a[0], a[1], a[2], a[3]);
+            *reinterpret_cast<uint4*>(out + (i + 1) * n_pad + k) = make_uint4(b[0], b[1], b[2], b[3]);
         }
-        const int64_t i = i0 + il, k = k0 + 8 * kg;
-        *reinterpret_cast<uint4*>(out + i * n_pad + k) = make_uint4(a[0], a[1], a[2], a[3]);
-        *reinterpret_cast<uint4*>(out + (i + 1) * n_pad + k) = make_uint4(b[0], b[1], b[2], b[3]);
     }
 }
 
@@ -637,17 +643,26 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
     return cudaGetLastError();
 }
 
+// max_blocks > 0 bounds the BF16 transpose's grid (it then loops over its tiles).
 template <typename TX>
 void launch_prep(const void* X, int mode, int64_t n, int64_t p, void* hi, void* lo, const Geometry& g,
-                 cudaStream_t s) {
+                 cudaStream_t s, int max_blocks = 0) {
     const TX* x = static_cast<const TX*>(X);
     if constexpr (std::is_same<TX, __nv_bfloat16>::value) {
         if (mode == kModeBf16) {
-            // n_pad is a multiple of 64 and p_pad of 256: every block's tile is inside the panel
+            // n_pad is a multiple of 64 and p_pad of 256: every tile is inside the panel
             const int vec = (p % 8 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0) ? 1 : 0;
-            dim3 grid((unsigned)(g.n_pad / 64), (unsigned)(g.p_pad / 128));
-            k_prep_bf16<<<grid, 256, 0, s>>>(reinterpret_cast<const uint16_t*>(X), n, p, static_cast<uint16_t*>(hi),
-                                             g.n_pad, vec);
+            const int64_t ntiles = (g.n_pad / 64) * (g.p_pad / 128);
+            const int64_t grid = max_blocks > 0 ? std::min<int64_t>(ntiles, max_blocks) : ntiles;
+            // the shared-memory configuration of the large-shared-memory kernels, so that a
+            // staging transpose can share SMs with the solve's kernels
+            static std::once_flag carve;
+            std::call_once(carve, [] {
+                cudaFuncSetAttribute(k_prep_bf16, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+            });
+            k_prep_bf16<<<(unsigned)grid, 256, 0, s>>>(reinterpret_cast<const uint16_t*>(X), n, p,
+                                                      static_cast<uint16_t*>(hi), g.n_pad, g.p_pad, vec);
             return;
         }
     }
@@ -664,32 +679,62 @@ size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision) {
     return g.pieces * g.panel_bytes + (size_t)g.ntiles * sizeof(int2) + 1024;
 }
 
-cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
-                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band,
-                    cudaEvent_t before_kernel, uint16_t* m1, int nbm) {
-    if (band <= 0) band = kBand;
+static cudaError_t check_shape(int xdt, int64_t n, int64_t p, int precision, size_t scratch_bytes) {
     if (precision != HPC_PREC_BF16X3 && precision != HPC_PREC_TF32) return cudaErrorInvalidValue;
     if (xdt == HPC_F64) return cudaErrorNotSupported;
     if (!encode_fn()) return cudaErrorNotSupported;
-    const int mode = mode_of(xdt, precision);
     const Geometry g = geometry(xdt, n, p, precision);
     if (g.ntiles > 0x7fffffff || g.n_pad / 64 > 0x7fffffff || g.p_pad > 0x7fffffff) return cudaErrorNotSupported;
     if (scratch_bytes < gram_tc_scratch_bytes(xdt, n, p, precision)) return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+cudaError_t gram_tc_prepare(const void* X, int xdt, int64_t n, int64_t p, int precision, void* scratch,
+                            size_t scratch_bytes, cudaStream_t s, int max_blocks) {
+    cudaError_t e = check_shape(xdt, n, p, precision, scratch_bytes);
+    if (e != cudaSuccess) return e;
+    const int mode = mode_of(xdt, precision);
+    const Geometry g = geometry(xdt, n, p, precision);
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    void* hi = base;
+    void* lo = g.pieces > 1 ? base + g.panel_bytes : nullptr;
+    if (xdt == HPC_BF16) launch_prep<__nv_bfloat16>(X, mode, n, p, hi, lo, g, s, max_blocks);
+    else launch_prep<float>(X, mode, n, p, hi, lo, g, s, max_blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
+                    void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band,
+                    cudaEvent_t before_kernel, uint16_t* m1, int nbm, int prepared, uint64_t* tiles_sig) {
+    if (band <= 0) band = kBand;
+    cudaError_t e = check_shape(xdt, n, p, precision, scratch_bytes);
+    if (e != cudaSuccess) return e;
+    const int mode = mode_of(xdt, precision);
+    const Geometry g = geometry(xdt, n, p, precision);
     uint8_t* base = static_cast<uint8_t*>(scratch);
     void* hi = base;
     void* lo = g.pieces > 1 ? base + g.panel_bytes : nullptr;
     int2* tiles = reinterpret_cast<int2*>(base + g.pieces * g.panel_bytes);
-    const std::vector<int2> order = tile_order(g.p_pad, band);
-    cudaError_t e = cudaMemcpyAsync(tiles, order.data(), order.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    // the host vector must outlive the copy
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    if (xdt == HPC_BF16) launch_prep<__nv_bfloat16>(X, mode, n, p, hi, lo, g, s);
-    else launch_prep<float>(X, mode, n, p, hi, lo, g, s);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (launches) *launches += 2;
+    // the tile order depends on p_pad and the band only: with tiles_sig the caller keeps
+    // it on the device between calls (no copy queued behind other transfers)
+    const uint64_t sig = (reinterpret_cast<uintptr_t>(tiles) * 1000003ull) ^ ((uint64_t)g.p_pad << 20) ^ (uint64_t)band;
+    if (!tiles_sig || *tiles_sig != sig) {
+        const std::vector<int2> order = tile_order(g.p_pad, band);
+        e = cudaMemcpyAsync(tiles, order.data(), order.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        // the host vector must outlive the copy
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        if (tiles_sig) *tiles_sig = sig;
+    }
+    if (!prepared) {
+        if (xdt == HPC_BF16) launch_prep<__nv_bfloat16>(X, mode, n, p, hi, lo, g, s);
+        else launch_prep<float>(X, mode, n, p, hi, lo, g, s);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (launches) *launches += 1;
+    }
+    if (launches) *launches += 1;
     if (before_kernel && (e = cudaEventRecord(before_kernel, s)) != cudaSuccess) return e;
     if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
     if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);

@@ -258,9 +258,16 @@ cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int
 // before_kernel (nullable) is recorded on s between the transpose and the product kernel.
 // m1 (nullable, p x nbm): also write max |S_ij| per (row, 128-column block), j != i,
 // rounded up to BF16, from the product's epilogue.
+// prepared: the panels in scratch already hold X's preparation (gram_tc_prepare).
+// tiles_sig: the caller's record of the tile order already in scratch (null: upload it).
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0,
-                    cudaEvent_t before_kernel = nullptr, uint16_t* m1 = nullptr, int nbm = 0);
+                    cudaEvent_t before_kernel = nullptr, uint16_t* m1 = nullptr, int nbm = 0, int prepared = 0,
+                    uint64_t* tiles_sig = nullptr);
+// Only the panel preparation of gram_tc (transpose / split of X into scratch);
+// max_blocks > 0 bounds the BF16 transpose's grid, so that it shares the GPU with a solve.
+cudaError_t gram_tc_prepare(const void* X, int xdt, int64_t n, int64_t p, int precision, void* scratch,
+                            size_t scratch_bytes, cudaStream_t s, int max_blocks = 0);
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();

@@ -128,3 +128,49 @@ def test_host_x_pinned_or_pageable_gives_the_device_result(lib, bf16):
         assert np.array_equal(e, e0)
         assert it == it0
         assert np.array_equal(om.col, om0.col) and np.array_equal(om.val, om0.val)
+
+
+@pytest.mark.parametrize("src", ["device", "pinned", "pageable"])
+def test_prefetch_gives_the_load_result(lib, src):
+    """hpc_prefetch_x stages the next X's panels while the current data solves; the next
+    load_x of that X gives the same S, maxima and estimate as a plain load.  A prefetch
+    of one X followed by the load of another is discarded."""
+    import torch
+
+    from workloads import small_problem
+
+    n, p = 400, 1024
+    mk = lambda seed: torch.as_tensor(small_problem(p, n, 5.0, seed).astype(np.float32)).to(torch.bfloat16)
+    X1, X2 = mk(31), mk(32)
+    if src == "device":
+        X1, X2 = X1.cuda(), X2.cuda()
+    elif src == "pinned":
+        X1, X2 = X1.pin_memory(), X2.pin_memory()
+    rng = np.random.default_rng(5)
+    r, c = rng.integers(0, p, 300), rng.integers(0, p, 300)
+
+    def run(steps):
+        with lib.Solver(None, 0.1, 0.1, n=n, p=p, xdtype=lib.BF16, precision=lib.PREC_BF16X3, eps=1e-7) as s:
+            for act, X in steps:
+                if act == "load":
+                    s.load_x(X)
+                elif act == "prefetch":
+                    s.prefetch_x(X)
+                else:
+                    s.solve()
+            return s.block_maxima(), s.s_entries(r, c), s.solve().as_dict()["iterations"], s.omega_dense()
+
+    ref2 = run([("load", X2)])
+    # staged, then loaded directly (the staged copy)
+    got2 = run([("load", X1), ("prefetch", X2), ("solve", None), ("load", X2)])
+    # pipelined: staged before the current load, prepared after its Gram, loaded next
+    pip2 = run([("load", X1), ("solve", None), ("prefetch", X2), ("load", X1), ("solve", None), ("load", X2)])
+    ref1 = run([("load", X1)])
+    # a staged X that is not loaded next: the load of another X is not affected
+    got1 = run([("load", X2), ("prefetch", X2), ("solve", None), ("load", X1)])
+    pip1 = run([("prefetch", X2), ("load", X2), ("prefetch", X2), ("load", X1)])
+    for got, ref in ((got2, ref2), (pip2, ref2), (got1, ref1), (pip1, ref1)):
+        assert np.array_equal(got[0], ref[0])
+        assert np.array_equal(got[1], ref[1])
+        assert got[2] == ref[2]
+        assert np.array_equal(got[3], ref[3])
