@@ -593,7 +593,7 @@ def main(argv=None):
         solver.solve()
         solver.get_omega(np.float32)
         torch.cuda.synchronize()
-        e2e_its, d2h = 0, 0
+        e2e_its, d2h, marks = 0, 0, []
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             if k + 1 < args.e2e_steps:
@@ -603,12 +603,14 @@ def main(argv=None):
             csr = solver.get_omega(np.float32)
             e2e_its += st["iterations"]
             d2h += csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1000
         e2e = {"value": e2e_its / (e2e_ms / 1000.0), "unit": UNIT,
                "h2d_bytes_per_step": int(bufs[0].numel() * bufs[0].element_size()),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps), "steps": args.e2e_steps,
-               "overlap": "next step's X staged during this step (hpc_prefetch_x), two pinned buffers"}
+               "overlap": "next step's X staged during this step (hpc_prefetch_x), two pinned buffers",
+               "step_ms": [round(1000 * (b - a), 1) for a, b in zip([t0] + marks[:-1], marks)]}
         del bufs
 
     # the same step with the other loop driver (host-driven iterations vs one CUDA-graph
