@@ -453,38 +453,44 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
     }
 }
 
-// Transpose X (n x p) into K-major panels (p_pad x n_pad) of the MMA input type.
+// Transpose X (n x p) into K-major panels (p_pad x n_pad) of the MMA input type,
+// 32 x 32 tiles: one per block, or a grid-stride loop over them when the grid is
+// smaller (a staging that shares the GPU with a solve).
 template <typename TX, int MODE>
 __global__ void __launch_bounds__(256)
 k_prep(const TX* __restrict__ X, int64_t n, int64_t p, void* __restrict__ hi, void* __restrict__ lo,
        int64_t n_pad, int64_t p_pad) {
     __shared__ float tile[32][33];
-    const int64_t k0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t k = k0 + r, i = i0 + tx;
-        float v = 0.f;
-        if (k < n && i < p) {
-            if constexpr (std::is_same<TX, __nv_bfloat16>::value) v = __bfloat162float(X[k * p + i]);
-            else v = (float)X[k * p + i];
+    const int64_t nkt = (n_pad + 31) / 32, ntiles = nkt * ((p_pad + 31) / 32);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t k0 = (t % nkt) * 32, i0 = (t / nkt) * 32;
+        __syncthreads();        // the previous tile's reads of the shared tile are done
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t k = k0 + r, i = i0 + tx;
+            float v = 0.f;
+            if (k < n && i < p) {
+                if constexpr (std::is_same<TX, __nv_bfloat16>::value) v = __bfloat162float(X[k * p + i]);
+                else v = (float)X[k * p + i];
+            }
+            tile[r][tx] = v;
         }
-        tile[r][tx] = v;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t i = i0 + r, k = k0 + tx;
-        if (i >= p_pad || k >= n_pad) continue;
-        const float x = tile[tx][r];
-        const int64_t o = i * n_pad + k;
-        if constexpr (MODE == kModeTf32) {
-            uint32_t t;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(x));
-            static_cast<float*>(hi)[o] = __uint_as_float(t);
-        } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            static_cast<__nv_bfloat16*>(hi)[o] = h;
-            if constexpr (MODE == kModeBf16x3)
-                static_cast<__nv_bfloat16*>(lo)[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t i = i0 + r, k = k0 + tx;
+            if (i >= p_pad || k >= n_pad) continue;
+            const float x = tile[tx][r];
+            const int64_t o = i * n_pad + k;
+            if constexpr (MODE == kModeTf32) {
+                uint32_t tf;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tf) : "f"(x));
+                static_cast<float*>(hi)[o] = __uint_as_float(tf);
+            } else {
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                static_cast<__nv_bfloat16*>(hi)[o] = h;
+                if constexpr (MODE == kModeBf16x3)
+                    static_cast<__nv_bfloat16*>(lo)[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+            }
         }
     }
 }
@@ -666,7 +672,8 @@ void launch_prep(const void* X, int mode, int64_t n, int64_t p, void* hi, void* 
             return;
         }
     }
-    dim3 grid((unsigned)((g.n_pad + 31) / 32), (unsigned)((g.p_pad + 31) / 32));
+    const int64_t ntiles = ((g.n_pad + 31) / 32) * ((g.p_pad + 31) / 32);
+    const unsigned grid = (unsigned)(max_blocks > 0 ? std::min<int64_t>(ntiles, max_blocks) : ntiles);
     if (mode == kModeTf32) k_prep<TX, kModeTf32><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
     else if (mode == kModeBf16x3) k_prep<TX, kModeBf16x3><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);
     else k_prep<TX, kModeBf16><<<grid, 256, 0, s>>>(x, n, p, hi, lo, g.n_pad, g.p_pad);

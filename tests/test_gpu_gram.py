@@ -130,8 +130,9 @@ def test_host_x_pinned_or_pageable_gives_the_device_result(lib, bf16):
         assert np.array_equal(om.col, om0.col) and np.array_equal(om.val, om0.val)
 
 
-@pytest.mark.parametrize("src", ["device", "pinned", "pageable"])
-def test_prefetch_gives_the_load_result(lib, src):
+@pytest.mark.parametrize("src,dt", [("device", "bf16"), ("pinned", "bf16"), ("pageable", "bf16"),
+                                    ("pinned", "f32"), ("device", "f32")])
+def test_prefetch_gives_the_load_result(lib, src, dt):
     """hpc_prefetch_x stages the next X's panels while the current data solves; the next
     load_x of that X gives the same S, maxima and estimate as a plain load.  A prefetch
     of one X followed by the load of another is discarded."""
@@ -140,7 +141,8 @@ def test_prefetch_gives_the_load_result(lib, src):
     from workloads import small_problem
 
     n, p = 400, 1024
-    mk = lambda seed: torch.as_tensor(small_problem(p, n, 5.0, seed).astype(np.float32)).to(torch.bfloat16)
+    tdt = torch.bfloat16 if dt == "bf16" else torch.float32
+    mk = lambda seed: torch.as_tensor(small_problem(p, n, 5.0, seed).astype(np.float32)).to(tdt)
     X1, X2 = mk(31), mk(32)
     if src == "device":
         X1, X2 = X1.cuda(), X2.cuda()
@@ -150,7 +152,8 @@ def test_prefetch_gives_the_load_result(lib, src):
     r, c = rng.integers(0, p, 300), rng.integers(0, p, 300)
 
     def run(steps):
-        with lib.Solver(None, 0.1, 0.1, n=n, p=p, xdtype=lib.BF16, precision=lib.PREC_BF16X3, eps=1e-7) as s:
+        with lib.Solver(None, 0.1, 0.1, n=n, p=p, xdtype=lib.BF16 if dt == "bf16" else lib.F32,
+                        precision=lib.PREC_BF16X3, eps=1e-7) as s:
             for act, X in steps:
                 if act == "load":
                     s.load_x(X)
