@@ -562,7 +562,8 @@ def main(argv=None):
     roof_gram = {"kernel": "gram", "bound": g_bound, "achieved": g_achieved, "peak": g_peak, "unit": "TFLOP/s",
                  "frac": g_achieved / g_peak, "peak_source": g_src,
                  # the Gram's traffic depends on its tile-order band and on whether it writes the block maxima
-                 "traffic": measured_traffic("gram", p, n, f"band{tuning['gram_band']}.maxima{tuning['gram_maxima']}."),
+                 "traffic": measured_traffic("gram", p, n, f"band{tuning['gram_band']}.maxima{tuning['gram_maxima']}."
+                                                           f"sched{tuning['gram_schedule']}."),
                  "ms_per_launch": gram_ms / len(recs),
                  "load_ms_per_step": sum(r["ms_load_step"] for r in recs) / len(recs)}
     per = scr_ms / max(scr_launches, 1) / 1000.0

@@ -384,6 +384,10 @@ typedef struct {
                                   whose block-maxima bound can emit; 0: it streams the
                                   whole upper triangle and every block of the rows with
                                   neighbours.  Both emit the same entries (1)       */
+    int32_t gram_schedule;     /* tensor-core Gram tiles: 1, taken by the persistent
+                                  CTAs from a shared counter (the tiles in flight stay
+                                  together in the band order); 0, CTA g takes tiles g,
+                                  g + grid, ... (1)                                 */
 } hpc_tuning;
 
 /* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max
@@ -401,7 +405,7 @@ int hpc_set_tuning(hpc_handle h, const hpc_tuning* t);
 #define HPC_TUNE_MAX_TRIALS 48
 typedef struct {
     int32_t knob;              /* 0 gram_band, 1 ls_window, 2 ls_blocks_per_sm,
-                                  3 rows_ctas_per_sm, 4 gram_maxima                 */
+                                  3 rows_ctas_per_sm, 4 gram_maxima, 5 gram_schedule */
     int32_t value;
     double  ms;                /* Gram knobs: one data load (transpose, product, block
                                   maxima); the others: one iteration                */

@@ -146,7 +146,7 @@ struct hpc_ctx {
     const void* pf_ptr = nullptr;
     int pf_xdt = -1;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{32, 8, 0, 2, 1, 1};
+    hpc_tuning tune{32, 8, 0, 2, 1, 1, 1};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -911,7 +911,7 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
                          h->gram_scratch_bytes, h->stream, &launches, h->tune.gram_band,
                          h->opt.timing ? h->ev_gk : nullptr,
                          h->tune.gram_maxima ? static_cast<uint16_t*>(h->m1) : nullptr, h->nbm, prepared ? 1 : 0,
-                         &h->tiles_sig);
+                         &h->tiles_sig, h->tune.gram_schedule);
         if (e == cudaErrorNotSupported) {
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
             return HPC_ERR_NOT_IMPLEMENTED;
@@ -1803,7 +1803,8 @@ bool tuning_ok(const hpc_tuning& t) {
     const int w = t.ls_window;
     return t.gram_band >= 1 && t.gram_band <= 256 && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16) &&
            t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4 &&
-           (t.gram_maxima == 0 || t.gram_maxima == 1) && (t.screen_bounds == 0 || t.screen_bounds == 1);
+           (t.gram_maxima == 0 || t.gram_maxima == 1) && (t.screen_bounds == 0 || t.screen_bounds == 1) &&
+           (t.gram_schedule == 0 || t.gram_schedule == 1);
 }
 
 void apply_tuning(hpc_ctx* h, const hpc_tuning& t) {
@@ -1903,6 +1904,21 @@ int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, h
                 if (band_ms[q] < band_ms[best]) best = q;
             }
             t.gram_band = bands[best];
+        }
+        // the tile schedule at that band: shared counter or static round-robin
+        const int sched[2] = {1, 0};
+        double sc_ms[2] = {1e300, 1e300};
+        for (int r = 0; r < kRounds && status == HPC_OK; ++r)
+            for (int q = 0; q < 2 && status == HPC_OK; ++q) {
+                hpc_tuning u = t;
+                u.gram_schedule = sched[q];
+                apply_tuning(h, u);
+                status = load_x(h, X, xdt, on_host);
+                sc_ms[q] = std::min(sc_ms[q], h->ms_gram);
+            }
+        if (status == HPC_OK) {
+            for (int q = 0; q < 2; ++q) add_trial(rep, 5, sched[q], sc_ms[q]);
+            t.gram_schedule = sc_ms[1] < sc_ms[0] ? sched[1] : sched[0];
         }
         // block maxima from the Gram's epilogue or from a pass over S, whole loads timed
         const int fused[2] = {1, 0};

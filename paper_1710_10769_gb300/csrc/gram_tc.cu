@@ -199,23 +199,32 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Persistent form: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + grid,
-// ... (the banded order of the tile list, so the tiles running together still
-// share X panels in L2) with three roles:
-//   warp 0      TMA producer, running ahead across tile boundaries;
-//   warp 1      MMA issuer, tile t into TMEM accumulator t & 1 (columns 0 / 256);
+// Persistent form: one CTA per SM walks the banded order of the tile list, so the
+// tiles running together share X panels in L2.  Dynamic: the CTAs take tiles from a
+// counter they share, so the tiles in flight stay a contiguous window of the order
+// however the CTAs drift; static: CTA g takes tiles g, g + grid, ...  Roles:
+//   warp 0      TMA producer: takes the next tile, publishes its index in a ring of
+//               kTileRing slots (tid_full / tid_empty), loads its K slices ahead;
+//   warp 1      MMA issuer, the CTA's tile t into TMEM accumulator t & 1 (columns
+//               0 / 256);
 //   warps 2-5   epilogue of tile t while tile t + 1 accumulates in the other
 //               buffer; warp w reads TMEM lanes 32 (w % 4) .. +31.
 // acc_full[b] (one commit) and acc_empty[b] (four epilogue warps) hand the
 // buffers over.  Every wait is bounded; an abort stops all roles, drains the
 // loads in flight and frees TMEM.
 constexpr int kPersistThreads = 192;
+constexpr int kTileRing = 4;
+
+// The tile counter of k_gram_tc_persist, reset before each launch (a kernel, so the
+// reset is not queued behind copies on a copy engine).
+__global__ void k_zero_counter(unsigned* ctr) { *ctr = 0u; }
 
 template <int MODE>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                   const int2* __restrict__ tiles, int ntiles, int k_tiles, int64_t p, int64_t n,
-                  float* __restrict__ S, int64_t lds, int vec_ok, uint16_t* __restrict__ m1, int nbm) {
+                  float* __restrict__ S, int64_t lds, int vec_ok, uint16_t* __restrict__ m1, int nbm,
+                  unsigned* __restrict__ tile_ctr, int dynamic) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -223,16 +232,21 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
     uint64_t* empty = full + C::kStages;
     uint64_t* acc_full = empty + C::kStages;     // [2]
     uint64_t* acc_empty = acc_full + 2;          // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    uint64_t* tid_full = acc_empty + 2;          // [kTileRing]
+    uint64_t* tid_empty = tid_full + kTileRing;  // [kTileRing]: MMA thread + one epilogue thread
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tid_empty + kTileRing);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* s_tid = reinterpret_cast<volatile int*>(tmem_slot + 2);      // [kTileRing]
+    volatile int* s_epi = s_tid + kTileRing;                                    // [2]
     unsigned* s_colmax = reinterpret_cast<unsigned*>(smem + C::kStages * C::kStageBytes + 256);   // [kBN]
+    static_assert(8 * (2 * C::kStages + 4 + 2 * kTileRing) + 4 * (2 + kTileRing + 2) <= 256, "barrier area");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
+        for (int r = 0; r < kTileRing; ++r) { mbar_init(&tid_full[r], 1); mbar_init(&tid_empty[r], 2); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
@@ -252,8 +266,18 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
         // ---------------- TMA producer
         long long g = 0;
         bool ok = true;
-        for (int lt = 0; lt < my_tiles && ok; ++lt) {
-            const int2 tile = tiles[blockIdx.x + (long long)lt * gridDim.x];
+        for (int lt = 0; ok; ++lt) {
+            // the next tile of the shared order, published to the MMA and epilogue roles
+            const int slot = lt % kTileRing;
+            if (!mbar_wait(&tid_empty[slot], ((uint32_t)(lt / kTileRing) & 1u) ^ 1u, abort_flag, 15)) break;
+            // dynamic: the counter shared by the CTAs; static: tiles blockIdx.x + lt * grid
+            const unsigned t = dynamic ? atomicAdd(tile_ctr, 1u)
+                                       : (unsigned)blockIdx.x + (unsigned)lt * (unsigned)gridDim.x;
+            const int tt = t < (unsigned)ntiles ? (int)t : -1;
+            s_tid[slot] = tt;
+            mbar_arrive_local(&tid_full[slot]);
+            if (tt < 0) break;
+            const int2 tile = tiles[tt];
             const int I0 = tile.x * kBM, J0 = tile.y * kBN;
             for (int kt = 0; kt < k_tiles; ++kt, ++g) {
                 const int s = (int)(g % C::kStages);
@@ -278,7 +302,12 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
         constexpr uint32_t idesc = instr_desc<MODE>();
         long long g = 0;
         bool ok = true;
-        for (int lt = 0; lt < my_tiles && ok; ++lt) {
+        for (int lt = 0; ok; ++lt) {
+            const int slot = lt % kTileRing;
+            if (!mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 16)) break;
+            const int tt = s_tid[slot];
+            mbar_arrive_local(&tid_empty[slot]);
+            if (tt < 0) break;
             const int b = lt & 1;
             if (!mbar_wait(&acc_empty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u, abort_flag, 12)) break;
             tc_fence_after();
@@ -325,7 +354,23 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
             for (int c = et; c < kBN; c += 128) s_colmax[c] = 0u;
             asm volatile("bar.sync 1, 128;" ::: "memory");
         }
-        for (int lt = 0; lt < my_tiles; ++lt) {
+        for (int lt = 0;; ++lt) {
+            // the round's tile: one thread takes it from the ring, all four warps read it
+            // after the barrier (double-buffered, so the next round's write cannot race
+            // this round's reads); -1 (no tile left, or an abort) ends every warp's loop
+            // at the same round
+            if (et == 0) {
+                const int slot = lt % kTileRing;
+                int tt = -1;
+                if (!*abort_flag && mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 17)) {
+                    tt = s_tid[slot];
+                    mbar_arrive_local(&tid_empty[slot]);
+                }
+                s_epi[lt & 1] = tt;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int tt = s_epi[lt & 1];
+            if (tt < 0) break;
             const int b = lt & 1;
             bool have = !*abort_flag && mbar_wait(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, 14);
             have = __all_sync(kFull, have);
@@ -337,7 +382,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
                 continue;
             }
             tc_fence_after();
-            const int2 tile = tiles[blockIdx.x + (long long)lt * gridDim.x];
+            const int2 tile = tiles[tt];
             const int I0 = tile.x * kBM, J0 = tile.y * kBN;
             const int64_t i = I0 + r;
             const int ib = I0 / 128;                       // the tile's row block in 128-column units
@@ -626,7 +671,7 @@ bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
 
 template <int MODE>
 cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles, int64_t n, int64_t p, float* S,
-                        int64_t lds, cudaStream_t s, uint16_t* m1 = nullptr, int nbm = 0) {
+                        int64_t lds, cudaStream_t s, uint16_t* m1 = nullptr, int nbm = 0, int dynamic = 1) {
     using C = Cfg<MODE>;
     CUtensorMap mh, ml;
     std::memset(&mh, 0, sizeof mh);
@@ -644,8 +689,12 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(g.ntiles, sms);
+    // the shared tile counter sits after the tile list, in the scratch's slack
+    unsigned* ctr = reinterpret_cast<unsigned*>(
+        (reinterpret_cast<uintptr_t>(tiles + g.ntiles) + 255) & ~uintptr_t(255));
+    if (dynamic) k_zero_counter<<<1, 1, 0, s>>>(ctr);
     k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n, S,
-                                                                   lds, vec_ok, m1, nbm);
+                                                                   lds, vec_ok, m1, nbm, ctr, dynamic);
     return cudaGetLastError();
 }
 
@@ -712,7 +761,8 @@ cudaError_t gram_tc_prepare(const void* X, int xdt, int64_t n, int64_t p, int pr
 
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band,
-                    cudaEvent_t before_kernel, uint16_t* m1, int nbm, int prepared, uint64_t* tiles_sig) {
+                    cudaEvent_t before_kernel, uint16_t* m1, int nbm, int prepared, uint64_t* tiles_sig,
+                    int schedule) {
     if (band <= 0) band = kBand;
     cudaError_t e = check_shape(xdt, n, p, precision, scratch_bytes);
     if (e != cudaSuccess) return e;
@@ -743,9 +793,9 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     }
     if (launches) *launches += 1;
     if (before_kernel && (e = cudaEventRecord(before_kernel, s)) != cudaSuccess) return e;
-    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
-    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
-    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm);
+    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule);
+    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule);
+    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule);
 }
 
 int gram_tc_take_error() {

@@ -263,7 +263,7 @@ cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0,
                     cudaEvent_t before_kernel = nullptr, uint16_t* m1 = nullptr, int nbm = 0, int prepared = 0,
-                    uint64_t* tiles_sig = nullptr);
+                    uint64_t* tiles_sig = nullptr, int schedule = 1);
 // Only the panel preparation of gram_tc (transpose / split of X into scratch);
 // max_blocks > 0 bounds the BF16 transpose's grid, so that it shares the GPU with a solve.
 cudaError_t gram_tc_prepare(const void* X, int xdt, int64_t n, int64_t p, int precision, void* scratch,
