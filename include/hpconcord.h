@@ -371,7 +371,7 @@ int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* 
  * shapes per machine (Section 4); these are the single-GPU counterparts. */
 typedef struct {
     int32_t gram_band;         /* row blocks of 128 per band of the tensor-core Gram's
-                                  tile order, 1..256 (32): sets which X panels the
+                                  tile order, 1..256 (16): sets which X panels the
                                   tiles running together share in L2               */
     int32_t ls_window;         /* tau values per line-search launch: 1, 2, 4, 8, 16 */
     int32_t ls_blocks_per_sm;  /* resident blocks per SM of the line-search

@@ -146,7 +146,7 @@ struct hpc_ctx {
     const void* pf_ptr = nullptr;
     int pf_xdt = -1;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{32, 8, 0, 2, 1, 1, 1};
+    hpc_tuning tune{16, 8, 0, 2, 1, 1, 1};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
