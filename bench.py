@@ -231,21 +231,23 @@ def run_row(args):
         roof = {"kernel": "path iteration", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
                 "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
                 "note": "algorithmic 4p^2 bytes per iteration / measured iteration time"}
-        # the oracle: warm-started path on the leading 1024 x 1024 sub-problem, first points
-        ps = min(1024, p)
-        Xs = sample_x_cpu(omega0_for(w)[:ps, :ps], w.n, w.seed).astype(np.float32).astype(np.float64)
-        t0 = time.perf_counter()
-        S = oracle.gram(Xs)
-        om, oits, npts = None, 0, 0
-        for l1 in lam:
-            r = oracle.solve(S, l1, PATH_LAMBDA2, eps=w.eps, max_iter=100000, omega0=om)
-            om, oits, npts = r.omega, oits + r.iterations, npts + 1
-            if time.perf_counter() - t0 > 20.0:
-                break
-        dt = time.perf_counter() - t0
-        cpu = {"value": oits / dt * (ps / p) ** 2, "unit": "iters/s", "cores": _oracle_cores(), "kind": "oracle",
-               "sample": f"FP64 oracle path over the first {npts} lambda1 points (warm starts, {oits} iterations, "
-                         f"{dt:.1f} s) of the leading {ps}x{ps} sub-problem, rate scaled by ({ps}/{p})^2"}
+        cpu = None
+        if not args.no_cpu:
+            # the oracle: warm-started path on the leading 1024 x 1024 sub-problem, first points
+            ps = min(1024, p)
+            Xs = sample_x_cpu(omega0_for(w)[:ps, :ps], w.n, w.seed).astype(np.float32).astype(np.float64)
+            t0 = time.perf_counter()
+            S = oracle.gram(Xs)
+            om, oits, npts = None, 0, 0
+            for l1 in lam:
+                r = oracle.solve(S, l1, PATH_LAMBDA2, eps=w.eps, max_iter=100000, omega0=om)
+                om, oits, npts = r.omega, oits + r.iterations, npts + 1
+                if time.perf_counter() - t0 > 20.0:
+                    break
+            dt = time.perf_counter() - t0
+            cpu = {"value": oits / dt * (ps / p) ** 2, "unit": "iters/s", "cores": _oracle_cores(), "kind": "oracle",
+                   "sample": f"FP64 oracle path over the first {npts} lambda1 points (warm starts, {oits} iterations, "
+                             f"{dt:.1f} s) of the leading {ps}x{ps} sub-problem, rate scaled by ({ps}/{p})^2"}
         _line("lambda1 path iters/s, 32 points on p=8192 n=4096 (ms_per_step = load + whole path)", its / (ms / 1000),
               "iters/s", ms / args.steps, args, True, "f32",
               {"workload": "path_p8192", "p": p, "n": w.n, "points": len(lam), "lambda2": PATH_LAMBDA2,
@@ -280,19 +282,21 @@ def run_row(args):
         roof = {"kernel": "batched solves", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
                 "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
                 "note": "algorithmic 4p^2 bytes per iteration of every problem / batch time"}
-        # the oracle: full solves of the two smallest problems; seconds per iteration
-        # scale as p^2 (Gram included), applied to every problem's iteration count
-        t_it = []
-        for wk in BATCH_PROBLEMS[:2]:
-            Xc = make_x(wk, device="cpu").astype(np.float64)
-            t0 = time.perf_counter()
-            r = oracle.solve(oracle.gram(Xc), wk.lambda1, wk.lambda2, eps=wk.eps, max_iter=100000)
-            t_it.append((time.perf_counter() - t0) / r.iterations / (wk.p / BATCH_PROBLEMS[0].p) ** 2)
-        unit_t = sum(t_it) / len(t_it)
-        t_all = sum(unit_t * (wk.p / BATCH_PROBLEMS[0].p) ** 2 * it for wk, it in zip(BATCH_PROBLEMS, per))
-        cpu = {"value": sum(per) / t_all, "unit": "iters/s", "cores": _oracle_cores(), "kind": "oracle",
-               "sample": "FP64 oracle full solves of the p = 1024 and 2048 problems; seconds per iteration scaled "
-                         "by (p/1024)^2 over the 16 problems' iteration counts"}
+        cpu = None
+        if not args.no_cpu:
+            # the oracle: full solves of the two smallest problems; seconds per iteration
+            # scale as p^2 (Gram included), applied to every problem's iteration count
+            t_it = []
+            for wk in BATCH_PROBLEMS[:2]:
+                Xc = make_x(wk, device="cpu").astype(np.float64)
+                t0 = time.perf_counter()
+                r = oracle.solve(oracle.gram(Xc), wk.lambda1, wk.lambda2, eps=wk.eps, max_iter=100000)
+                t_it.append((time.perf_counter() - t0) / r.iterations / (wk.p / BATCH_PROBLEMS[0].p) ** 2)
+            unit_t = sum(t_it) / len(t_it)
+            t_all = sum(unit_t * (wk.p / BATCH_PROBLEMS[0].p) ** 2 * it for wk, it in zip(BATCH_PROBLEMS, per))
+            cpu = {"value": sum(per) / t_all, "unit": "iters/s", "cores": _oracle_cores(), "kind": "oracle",
+                   "sample": "FP64 oracle full solves of the p = 1024 and 2048 problems; seconds per iteration scaled "
+                             "by (p/1024)^2 over the 16 problems' iteration counts"}
         _line("batched solve iters/s, 16 problems p=1024..16384 (ms_per_step = the batch, Gram excluded)",
               its / (ms / 1000), "iters/s", ms / args.steps, args, True, "f32",
               {"workload": "batch16", "p": [wk.p for wk in BATCH_PROBLEMS], "n": "p/2",
@@ -331,13 +335,15 @@ def run_row(args):
         roof = {"kernel": "backward", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
                 "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
                 "note": "dense dL/dOmega and dL/dX written, X read twice"}
-        csr = s.get_omega().to_scipy(p)
-        Xh, Xvh = Xtr.cpu().numpy(), Xva.cpu().numpy()
-        t0 = time.perf_counter()
-        oracle.hypergrad_sparse(Xh, Xvh, csr, w.lambda1, w.lambda2)
-        dt = time.perf_counter() - t0
-        cpu = {"value": dt * 1000, "unit": "ms", "cores": _oracle_cores(), "kind": "oracle",
-               "sample": f"FP64 sparse hypergradient at full size on the GPU's support ({csr.nnz} entries)"}
+        cpu = None
+        if not args.no_cpu:
+            csr = s.get_omega().to_scipy(p)
+            Xh, Xvh = Xtr.cpu().numpy(), Xva.cpu().numpy()
+            t0 = time.perf_counter()
+            oracle.hypergrad_sparse(Xh, Xvh, csr, w.lambda1, w.lambda2)
+            dt = time.perf_counter() - t0
+            cpu = {"value": dt * 1000, "unit": "ms", "cores": _oracle_cores(), "kind": "oracle",
+                   "sample": f"FP64 sparse hypergradient at full size on the GPU's support ({csr.nnz} entries)"}
         _line("adjoint + hypergradient ms per step at p=16384 (n=4096 train, 2048 held out)",
               (mb + mh) / args.steps, "ms", (mb + mh) / args.steps, args, False, "f32",
               {"workload": "adjoint_p16384", "p": p, "n": n, "n_val": 2048, "lambda1": w.lambda1,
@@ -377,15 +383,17 @@ def run_row(args):
         roof = {"kernel": "obs gradient pass (Z GEMM)", "bound": "tensor", "achieved": tf, "peak": pk,
                 "unit": "TFLOP/s", "frac": tf / pk, "traffic": None,
                 "peak_source": f"{peak_src} (bf16 sustained / 3, BF16X3)", "ms_per_launch": per * 1000}
-        ps = min(1024, p)
-        Xs = sample_x_cpu(omega0_for(w)[:ps, :ps], n, w.seed).astype(np.float32).astype(np.float64)
-        t0 = time.perf_counter()
-        r = oracle.solve_obs(Xs, w.lambda1, w.lambda2, eps=w.eps, max_iter=100000)
-        dt = time.perf_counter() - t0
-        cpu = {"value": r.iterations / dt * (ps / p) ** 2, "unit": "iters/s", "cores": _oracle_cores(),
-               "kind": "oracle",
-               "sample": f"FP64 oracle Obs solve ({r.iterations} iterations, {dt:.1f} s) of the leading {ps}x{ps} "
-                         f"sub-problem (same n), rate scaled by ({ps}/{p})^2"}
+        cpu = None
+        if not args.no_cpu:
+            ps = min(1024, p)
+            Xs = sample_x_cpu(omega0_for(w)[:ps, :ps], n, w.seed).astype(np.float32).astype(np.float64)
+            t0 = time.perf_counter()
+            r = oracle.solve_obs(Xs, w.lambda1, w.lambda2, eps=w.eps, max_iter=100000)
+            dt = time.perf_counter() - t0
+            cpu = {"value": r.iterations / dt * (ps / p) ** 2, "unit": "iters/s", "cores": _oracle_cores(),
+                   "kind": "oracle",
+                   "sample": f"FP64 oracle Obs solve ({r.iterations} iterations, {dt:.1f} s) of the leading {ps}x{ps} "
+                             f"sub-problem (same n), rate scaled by ({ps}/{p})^2"}
         _line("Obs prox-grad iters/s at p=16384 n=8192 (ms_per_step = load + solve)", its / (ms / 1000), "iters/s",
               ms / args.steps, args, True, "f32",
               {"workload": "fp32_p16384", "variant": "obs", "p": p, "n": n, "lambda1": w.lambda1,
