@@ -356,7 +356,8 @@ def run_row(args):
     if args.row == "obs":
         w = WORKLOADS["fp32_p16384"]
         X = make_x(w, device="cuda")
-        s = hpc.Solver(X, w.lambda1, w.lambda2, variant=hpc.OBS, eps=w.eps, max_iter=100000)
+        s = hpc.Solver(X, w.lambda1, w.lambda2, variant=hpc.OBS, eps=w.eps, max_iter=100000,
+                       device_loop=args.device_loop)
         for _ in range(args.warmup):
             s.load_x(X)
             s.solve()
