@@ -376,10 +376,11 @@ def run_row(args):
                 gpl += st["grad_pass_launches"]
                 launches += st["kernel_launches"]
         p, n = w.p, w.n
-        # one gradient pass forms Z = Y^T X / n over the symmetric half: n p (p+1) flop,
-        # three BF16 products per element (BF16X3): a third of the bf16 peak
+        # one gradient pass forms Z = Y^T X / n = Omega S, which is not symmetric: both
+        # Z[I, J] and Z[J, I] of every block pair, 2 n p^2 flop; three BF16 products per
+        # element (BF16X3): a third of the bf16 peak
         per = gp / max(gpl, 1) / 1000.0
-        tf = n * p * (p + 1) / per / 1e12
+        tf = 2.0 * n * p * p / per / 1e12
         pk = (bf16_sus if bf16_sus else bf16) / 3.0
         roof = {"kernel": "obs gradient pass (Z GEMM)", "bound": "tensor", "achieved": tf, "peak": pk,
                 "unit": "TFLOP/s", "frac": tf / pk, "traffic": None,
