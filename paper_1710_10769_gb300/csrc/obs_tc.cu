@@ -5,12 +5,13 @@
 //
 // Z equals W = Omega S, so the screening rule of the Cov pass applies: an entry
 // can enter a prox step only if it is in the support or |G_ij| > lambda1, and
-// |G_ij| > lambda1 needs max(|Z_ij|, |Z_ji|) > lambda1.  One CTA computes the
-// tile pair Z[I, J] and Z[J, I] (I <= J, 128 x 128 tiles) into two TMEM
-// accumulators, transposes the second through shared memory, and emits both
-// (i, j) and (j, i) -- flagged as paired, so no partner request follows -- for
-// every pair in the support or above the threshold (Alg. 3 steps 4-6 with the
-// transpose done inside the CTA).  Z is never stored.
+// |G_ij| > lambda1 needs max(|Z_ij|, |Z_ji|) > lambda1.  Persistent CTAs walk the
+// tile pairs Z[I, J] and Z[J, I] (I <= J, 128 x 128 tiles), each into one of two
+// TMEM accumulator pairs; the epilogue warps transpose the second tile through
+// shared memory and emit both (i, j) and (j, i) -- flagged as paired, so no
+// partner request follows -- for every pair in the support or above the
+// threshold (Alg. 3 steps 4-6 with the transpose done inside the CTA), while the
+// next pair accumulates.  Z is never stored.
 //
 // Operands are BF16 hi/lo panels (BF16X3: hi*hi + hi*lo + lo*hi) or TF32
 // panels, K-major, zero padded; loaded by TMA (128-byte swizzle) through an
@@ -30,7 +31,7 @@ namespace {
 constexpr int kT = 128;                    // tile edge (UMMA M = N = 128)
 constexpr int kRowB = 128;                 // bytes per swizzle row
 constexpr int kPanelTile = kT * kRowB;     // 16 KB
-constexpr uint32_t kTmemCols = 256;        // two 128-column FP32 accumulators
+constexpr uint32_t kTmemCols = 256;        // one accumulator pair: two 128-column FP32 accumulators
 constexpr long long kWaitLimit = 1ll << 26;
 
 enum : int { kObsBf16x3 = 0, kObsTf32 = 1 };
@@ -45,6 +46,9 @@ __device__ __forceinline__ void tmem_relinquish() {
 }
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void ptx_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -105,47 +109,59 @@ struct ObsCfg {
     static constexpr int kMmaK = 32 / kElem;
     static constexpr int kStageBytes = kPieces * 2 * kPanelTile;    // A and B tiles, each piece
     static constexpr int kStages = MODE == kObsBf16x3 ? 3 : 5;
-    static constexpr int kTransBytes = kT * (kT + 1) * 4;           // Z[J, I] staged for the transpose
-    static constexpr int kSmem = (kStages * kStageBytes > kTransBytes ? kStages * kStageBytes : kTransBytes) + 1024 +
-                                 256;
+    static constexpr int kTransBytes = (kT / 2) * (kT + 1) * 4;     // half of Z[J, I], staged for the transpose
+    static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
 };
+
+constexpr int kObsThreads = 192;
 
 __device__ int g_obs_error = 0;
 
-// Pair (bi, bj), bi <= bj, of 128-row blocks; Z[I, J] = Y^T[I] X^T[J]^T / n and
-// Z[J, I] = Y^T[J] X^T[I]^T / n; emission of both sides.
+// Persistent pair kernel: one CTA per SM walks the pairs blockIdx.x, blockIdx.x +
+// grid, ... of the pair list (bi <= bj, bands of row blocks).  For pair (I, J)
+// it forms Z[I, J] = Y^T[I] X^T[J]^T / n and Z[J, I] = Y^T[J] X^T[I]^T / n and emits
+// both sides.  Roles:
+//   warp 0      TMA producer (thread 0), running ahead across pairs;
+//   warp 1      MMA issuer (thread 32) and TMEM owner: pair t into accumulator pair
+//               t & 1 (columns 256 (t & 1) + {0, 128} for Z[I, J], Z[J, I]);
+//   warps 2-5   epilogue of pair t while pair t + 1 accumulates: stage Z[J, I]
+//               through shared memory (a buffer of its own, half the tile at a
+//               time), then emit row by row; warp w reads TMEM lanes 32 (w % 4) .. + 31.
+// acc_full[b] (one commit) and acc_empty[b] (four epilogue warps) hand the
+// accumulator pairs over.  Every wait is bounded; after an abort every role stops,
+// the epilogue warps keep meeting at their barriers, the loads in flight drain and
+// TMEM is freed.
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kObsThreads, 1)
 k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUtensorMap yb,
            const __grid_constant__ CUtensorMap xa, const __grid_constant__ CUtensorMap xb, const int2* __restrict__ pairs,
-           int k_tiles, int p, int64_t n, const int* __restrict__ rp, const int* __restrict__ ci,
+           int npairs, int k_tiles, int p, int64_t n, const int* __restrict__ rp, const int* __restrict__ ci,
            const float* __restrict__ cv, Emit<float> em, Ctrl* __restrict__ ctrl) {
     using C = ObsCfg<MODE>;
     const float lam1 = (float)ctrl->lam1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int region = C::kStages * C::kStageBytes > C::kTransBytes ? C::kStages * C::kStageBytes : C::kTransBytes;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + region);
+    float* zt = reinterpret_cast<float*>(smem + C::kStages * C::kStageBytes);        // [kT / 2][kT + 1]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + C::kTransBytes);
     uint64_t* empty = full + C::kStages;
-    uint64_t* accum = empty + C::kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    uint64_t* acc_full = empty + C::kStages;     // [2]
+    uint64_t* acc_empty = acc_full + 2;          // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    static_assert(8 * (2 * C::kStages + 4) + 8 <= 256, "barrier area");
+    static_assert(C::kSmem <= 232448, "shared memory per block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 pr = pairs[blockIdx.x];
-    const int I0 = pr.x * kT, J0 = pr.y * kT;
-    const bool diag_pair = pr.x == pr.y;
-    const int phases = diag_pair ? 1 : 2;
-    const int items = phases * k_tiles;
+    const int my_pairs = (int)blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], 1); }
-        ptx::mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) { ptx::mbar_init(&acc_full[b], 1); ptx::mbar_init(&acc_empty[b], 4); }
         *abort_flag = 0;
         ptx::mbar_init_fence();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, kTmemCols);
+        tmem_alloc(tmem_slot, 2 * kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -153,131 +169,170 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    int issued = 0;
+    long long issued = 0;
     if (threadIdx.x == 0) {
-        // producer: phase 0 streams (Y^T[I], X^T[J]), phase 1 (Y^T[J], X^T[I])
-        for (int t = 0; t < items; ++t) {
-            const int s = t % C::kStages;
-            const uint32_t ph = (uint32_t)(t / C::kStages) & 1u;
-            if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, kWaitLimit)) {
-                atomicCAS(&g_obs_error, 0, 1);
-                break;
+        // ---------------- producer: per pair, phase 0 streams (Y^T[I], X^T[J]), phase 1 (Y^T[J], X^T[I])
+        long long g = 0;
+        bool ok = true;
+        for (int lt = 0; lt < my_pairs && ok; ++lt) {
+            const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+            const int I0 = pr.x * kT, J0 = pr.y * kT;
+            const int items = (pr.x == pr.y ? 1 : 2) * k_tiles;
+            for (int t = 0; t < items; ++t, ++g) {
+                const int s = (int)(g % C::kStages);
+                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, kWaitLimit)) {
+                    atomicCAS(&g_obs_error, 0, 1);
+                    ok = false;
+                    break;
+                }
+                const int phase = t / k_tiles, kt = t % k_tiles;
+                const int ra = phase == 0 ? I0 : J0, rb = phase == 0 ? J0 : I0;
+                uint8_t* st = smem + s * C::kStageBytes;
+                ptx::mbar_expect_tx(&full[s], C::kStageBytes);
+                const int kc = kt * C::kBK;
+                ptx::tma_load_2d(st, &ya, &full[s], kc, ra);
+                ptx::tma_load_2d(st + kPanelTile, &xa, &full[s], kc, rb);
+                if (C::kPieces > 1) {
+                    ptx::tma_load_2d(st + 2 * kPanelTile, &yb, &full[s], kc, ra);
+                    ptx::tma_load_2d(st + 3 * kPanelTile, &xb, &full[s], kc, rb);
+                }
+                ++issued;
             }
-            const int phase = t / k_tiles, kt = t % k_tiles;
-            const int ra = phase == 0 ? I0 : J0, rb = phase == 0 ? J0 : I0;
-            uint8_t* st = smem + s * C::kStageBytes;
-            ptx::mbar_expect_tx(&full[s], C::kStageBytes);
-            const int kc = kt * C::kBK;
-            ptx::tma_load_2d(st, &ya, &full[s], kc, ra);
-            ptx::tma_load_2d(st + kPanelTile, &xa, &full[s], kc, rb);
-            if (C::kPieces > 1) {
-                ptx::tma_load_2d(st + 2 * kPanelTile, &yb, &full[s], kc, ra);
-                ptx::tma_load_2d(st + 3 * kPanelTile, &xb, &full[s], kc, rb);
-            }
-            ++issued;
         }
     } else if (threadIdx.x == 32) {
+        // ---------------- MMA issuer
         constexpr uint32_t idesc = instr_desc<MODE>();
-        for (int t = 0; t < items; ++t) {
-            const int s = t % C::kStages;
-            const uint32_t ph = (uint32_t)(t / C::kStages) & 1u;
-            if (!ptx::mbar_wait_bounded(&full[s], ph, abort_flag, kWaitLimit)) {
-                atomicCAS(&g_obs_error, 0, 2);
+        long long g = 0;
+        bool ok = true;
+        for (int lt = 0; lt < my_pairs && ok; ++lt) {
+            const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+            const int items = (pr.x == pr.y ? 1 : 2) * k_tiles;
+            const int b = lt & 1;
+            if (!ptx::mbar_wait_bounded(&acc_empty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
+                atomicCAS(&g_obs_error, 0, 3);
                 break;
             }
             tc_fence_after();
-            const int phase = t / k_tiles, kt = t % k_tiles;
-            const uint32_t d = tmem + (uint32_t)(phase * kT);
-            const uint32_t st = ptx::smem_u32(smem + s * C::kStageBytes);
-            const uint32_t a_hi = st, b_hi = st + kPanelTile, a_lo = st + 2 * kPanelTile, b_lo = st + 3 * kPanelTile;
-#pragma unroll
-            for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
-                const uint32_t off = kk * 32;
-                const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-                umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
-                if constexpr (C::kTerms == 3) {
-                    umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
-                    umma<MODE>(d, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+            for (int t = 0; t < items; ++t, ++g) {
+                const int s = (int)(g % C::kStages);
+                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                if (!ptx::mbar_wait_bounded(&full[s], ph, abort_flag, kWaitLimit)) {
+                    atomicCAS(&g_obs_error, 0, 2);
+                    ok = false;
+                    break;
                 }
+                tc_fence_after();
+                const int phase = t / k_tiles, kt = t % k_tiles;
+                const uint32_t d = tmem + (uint32_t)(b * 2 * kT + phase * kT);
+                const uint32_t st = ptx::smem_u32(smem + s * C::kStageBytes);
+                const uint32_t a_hi = st, b_hi = st + kPanelTile, a_lo = st + 2 * kPanelTile, b_lo = st + 3 * kPanelTile;
+#pragma unroll
+                for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
+                    umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
+                    if constexpr (C::kTerms == 3) {
+                        umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+                        umma<MODE>(d, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+                    }
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            if (ok) umma_commit(&acc_full[b]);
         }
-        umma_commit(accum);
+    } else if (warp >= 2) {
+        // ---------------- epilogue
+        const int q4 = warp & 3;
+        const int r = q4 * 32 + lane;                // TMEM lane = local row
+        const float dn = (float)n;
+        for (int lt = 0; lt < my_pairs; ++lt) {
+            const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+            const int I0 = pr.x * kT, J0 = pr.y * kT;
+            const bool diag_pair = pr.x == pr.y;
+            const int b = lt & 1;
+            bool have = !*abort_flag &&
+                        ptx::mbar_wait_bounded(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, kWaitLimit);
+            have = __all_sync(kFull, have);
+            tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 2 * kT);
+            // Z[J, I] (Z[I, I] for a diagonal pair) is staged in two halves of 64 rows:
+            // the warps holding TMEM lanes 64 h .. 64 h + 63 write them, then every
+            // thread emits its row's columns 64 h .. 64 h + 63 (the support merge
+            // carries over between the halves)
+            const uint32_t src = diag_pair ? 0u : (uint32_t)kT;
+            const int i = I0 + r;
+            int q = 0, qe = 0;
+            if (have && i < p) {
+                q = rp[i];
+                qe = rp[i + 1];
+                while (q < qe && ci[q] < J0) ++q;
+            }
+            for (int h = 0; h < 2; ++h) {
+                if (have && (q4 >> 1) == h) {
+                    const int cl = (q4 - 2 * h) * 32 + lane;            // staged row, 0..63
+                    for (int c0 = 0; c0 < kT; c0 += 32) {
+                        uint32_t v[32];
+                        tmem_ld32(base + src + (uint32_t)c0, v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int qq = 0; qq < 32; ++qq) zt[cl * (kT + 1) + c0 + qq] = __uint_as_float(v[qq]) / dn;
+                    }
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");      // the staged half is complete
+                if (have) {
+                    for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 32) {
+                        uint32_t v[32];
+                        tmem_ld32(base + (uint32_t)c0, v);
+                        tmem_ld_wait();
+                        if (i >= p) continue;
+                        for (int cc = 0; cc < 32; ++cc) {
+                            const int c = c0 + cc;
+                            const int j = J0 + c;
+                            if (j >= p) break;
+                            while (q < qe && ci[q] < j) ++q;             // support merge, column order
+                            if (diag_pair && j < i) continue;            // the (j, i) thread emits this pair
+                            const float a = __uint_as_float(v[cc]) / dn; // Z_ij
+                            const float bz = zt[(c - 64 * h) * (kT + 1) + r];   // Z_ji
+                            const bool sup = q < qe && ci[q] == j;
+                            const float om = sup ? cv[q] : 0.f;
+                            const bool big = !(fabsf(a) <= lam1) || !(fabsf(bz) <= lam1);
+                            if (!(sup || big || i == j)) continue;
+                            const int cnt = (i == j) ? 1 : 2;
+                            const int pos = atomicAdd(&ctrl->em_count, cnt);
+                            const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);   // paired, support
+                            if (pos < em.cap) {
+                                em.row[pos] = i;
+                                em.col[pos] = (int)((unsigned)j | fl);
+                                em.w[pos] = a;
+                                em.om[pos] = om;
+                            }
+                            if (i != j && pos + 1 < em.cap) {
+                                em.row[pos + 1] = j;
+                                em.col[pos + 1] = (int)((unsigned)i | fl);
+                                em.w[pos + 1] = bz;
+                                em.om[pos + 1] = om;
+                            }
+                        }
+                    }
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");      // the staged half is free again
+            }
+            // this warp's lanes of the accumulator pair are read: hand it back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx_arrive(&acc_empty[b]);
+        }
     }
     __syncwarp();
-
-    // ---------------- epilogue
-    bool have = ptx::mbar_wait_bounded(accum, 0, abort_flag, kWaitLimit) && !*abort_flag;
-    have = __all_sync(kFull, have);
-    tc_fence_after();
-    __syncthreads();      // every stage consumed: the ring's memory now holds the transpose tile
-    float* zt = reinterpret_cast<float*>(smem);      // [kT][kT + 1]
-    const int r = warp * 32 + lane;                   // TMEM lane = local row
-    const float dn = (float)n;
-    if (have) {
-        // stage the second accumulator (Z[J, I], or Z[I, I] for a diagonal pair) row by row
-        const uint32_t src = diag_pair ? 0u : (uint32_t)kT;
-        for (int c0 = 0; c0 < kT; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + src + (uint32_t)c0, v);
-            tmem_ld_wait();
-#pragma unroll
-            for (int q = 0; q < 32; ++q) zt[r * (kT + 1) + c0 + q] = __uint_as_float(v[q]) / dn;
-        }
-    }
-    __syncthreads();
-    if (have) {
-        const int i = I0 + r;
-        // this row's support entries in columns [J0, J0 + kT), consumed in column order
-        int q = 0, qe = 0;
-        if (i < p) {
-            q = rp[i];
-            qe = rp[i + 1];
-            while (q < qe && ci[q] < J0) ++q;
-        }
-        for (int c0 = 0; c0 < kT; c0 += 32) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            tmem_ld_wait();
-            if (i >= p) continue;
-            for (int cc = 0; cc < 32; ++cc) {
-                const int c = c0 + cc;
-                const int j = J0 + c;
-                if (j >= p) break;
-                while (q < qe && ci[q] < j) ++q;             // support merge, column order
-                if (diag_pair && j < i) continue;            // the (j, i) thread emits this pair
-                const float a = __uint_as_float(v[cc]) / dn; // Z_ij
-                const float b = zt[c * (kT + 1) + r];         // Z_ji
-                const bool sup = q < qe && ci[q] == j;
-                const float om = sup ? cv[q] : 0.f;
-                const bool big = !(fabsf(a) <= lam1) || !(fabsf(b) <= lam1);
-                if (!(sup || big || i == j)) continue;
-                const int cnt = (i == j) ? 1 : 2;
-                const int pos = atomicAdd(&ctrl->em_count, cnt);
-                const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);   // paired, support
-                if (pos < em.cap) {
-                    em.row[pos] = i;
-                    em.col[pos] = (int)((unsigned)j | fl);
-                    em.w[pos] = a;
-                    em.om[pos] = om;
-                }
-                if (i != j && pos + 1 < em.cap) {
-                    em.row[pos + 1] = j;
-                    em.col[pos + 1] = (int)((unsigned)i | fl);
-                    em.w[pos + 1] = b;
-                    em.om[pos + 1] = om;
-                }
-            }
-        }
-    }
     tc_fence_before();
     __syncthreads();
     if (*abort_flag) {
         if (threadIdx.x == 0) {
             atomicOr(&ctrl->flags, kFlagTimeout);
-            for (int t = max(0, issued - C::kStages); t < issued; ++t) {
-                const int s = t % C::kStages;
-                const uint32_t ph = (uint32_t)(t / C::kStages) & 1u;
+            for (long long g = issued > C::kStages ? issued - C::kStages : 0; g < issued; ++g) {
+                const int s = (int)(g % C::kStages);
+                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
                 for (long long it = 0; it < (1ll << 22) && !ptx::mbar_try_wait(&full[s], ph); ++it) __nanosleep(64);
             }
         }
@@ -285,7 +340,7 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
     }
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc(tmem, 2 * kTmemCols);
     }
 }
 
@@ -361,20 +416,28 @@ cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2*
                              int p, const int* rp, const int* ci, const float* cv, Emit<float> em,
                              Ctrl* ctrl, cudaStream_t s) {
     const int64_t n_pad = (n + 63) / 64 * 64;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(npairs, sms));   // one CTA per SM
     if (precision == HPC_PREC_TF32) {
         using C = ObsCfg<kObsTf32>;
         cudaError_t e = set_smem_once((const void*)k_obs_pair<kObsTf32>, C::kSmem, kSmemSlotObsTf32);
         if (e != cudaSuccess) return e;
-        k_obs_pair<kObsTf32><<<(unsigned)npairs, 128, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
-                                                                     (int)(n_pad / C::kBK), p, n, rp, ci, cv,
-                                                                     em, ctrl);
+        k_obs_pair<kObsTf32><<<grid, kObsThreads, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
+                                                                 (int)npairs, (int)(n_pad / C::kBK), p, n, rp, ci,
+                                                                 cv, em, ctrl);
     } else {
         using C = ObsCfg<kObsBf16x3>;
         cudaError_t e = set_smem_once((const void*)k_obs_pair<kObsBf16x3>, C::kSmem, kSmemSlotObsBf16x3);
         if (e != cudaSuccess) return e;
-        k_obs_pair<kObsBf16x3><<<(unsigned)npairs, 128, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
-                                                                       (int)(n_pad / C::kBK), p, n, rp, ci, cv,
-                                                                       em, ctrl);
+        k_obs_pair<kObsBf16x3><<<grid, kObsThreads, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
+                                                                   (int)npairs, (int)(n_pad / C::kBK), p, n, rp, ci,
+                                                                   cv, em, ctrl);
     }
     return cudaGetLastError();
 }
