@@ -69,6 +69,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_ready(self, timeout=5.0):
+        """Block until nvidia-smi has printed its first sample, so that a short timed
+        region starts with the sampler running."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+
     def __exit__(self, *a):
         if self.proc:
             self.proc.terminate()
@@ -112,14 +119,14 @@ def reduce_over_ranks(ms, iters, pg, device):
 
 
 def measured_traffic(kernel, p, n, tag=""):
-    """DRAM bytes per launch of `kernel` ("screen_pass" or "gram") from the committed
+    """DRAM bytes per launch of `kernel` ("screen_pass", "gram" or "dense_grad") from the committed
     ncu summary (profiles/roofline_traffic.txt, 1-pass captures at the full
     workload); None when it was taken on other sizes, another version of the
     kernel's source, or (tag) another launch configuration of the kernel."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
-    srcs = {"screen_pass": "iterate.cu", "gram": "gram_tc.cu"}
+    srcs = {"screen_pass": "iterate.cu", "gram": "gram_tc.cu", "dense_grad": "adjoint.cu"}
     try:
         kv = dict(line.strip().split("=", 1) for line in open(path) if "=" in line and not line.startswith("#"))
         with open(os.path.join(ROOT, "paper_1710_10769_gb300", "csrc", srcs[kernel]), "rb") as fh:
@@ -316,9 +323,14 @@ def run_row(args):
         for _ in range(args.warmup):
             s.backward(Xtr)
             s.hypergrad(Xva, tol=1e-10)
-        mb, mh = 0.0, 0.0
+        # A step is ~2-3 ms: time at least args.steps of them and at least 0.4 s, so that
+        # the clock sampler (200 ms period) sees the timed region.
+        mb, mh, steps = 0.0, 0.0, 0
         with ClockSampler(0) as clk:
-            for _ in range(args.steps):
+            clk.wait_ready()
+            t_start = time.perf_counter()
+            while steps < args.steps or time.perf_counter() - t_start < 0.4:
+                steps += 1
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record(stream)
                 s.backward(Xtr)
@@ -328,13 +340,28 @@ def run_row(args):
                 torch.cuda.synchronize()
                 mb += e0.elapsed_time(e1)
                 mh += e1.elapsed_time(e2)
+        args = argparse.Namespace(**{**vars(args), "steps": steps})
         p, n = w.p, w.n
-        # backward writes dL/dOmega (p x p) and dL/dX (n x p) and reads X twice
-        byt = 4.0 * p * p + 4.0 * n * p * 3
-        alg = byt / (mb / args.steps / 1000) / 1e9
-        roof = {"kernel": "backward", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
-                "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
-                "note": "dense dL/dOmega and dL/dX written, X read twice"}
+        # The dominant kernel, k_dense_grad_pair (dL/dOmega), timed on its own: one
+        # backward call with dL/dX off is the row-info kernel plus that kernel.  It must
+        # read the p (p + 1) / 2 distinct FP32 elements of S once and write the p x p
+        # FP32 G once: 4 p^2 + 2 p (p + 1) bytes.
+        md = 0.0
+        for _ in range(args.steps):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            s.backward(Xtr, dx=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            md += e0.elapsed_time(e1)
+        md /= args.steps
+        byt = 4.0 * p * p + 2.0 * p * (p + 1)
+        alg = byt / (md / 1000) / 1e9
+        roof = {"kernel": "k_dense_grad_pair", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
+                "frac": alg / hbm, "traffic": measured_traffic("dense_grad", p, n), "peak_source": peak_src,
+                "ms": md, "algorithmic_bytes": byt,
+                "note": "distinct S elements read once, G written once; the gathered S rows of the few "
+                        "off-diagonal support entries are not counted"}
         cpu = None
         if not args.no_cpu:
             csr = s.get_omega().to_scipy(p)

@@ -307,7 +307,9 @@ typedef struct {
  *   dL_val/dlambda1 = -<v, sign_off(Omega_A)>,  dL_val/dlambda2 = -<v, Omega_A>,
  *   H_A v = grad_A L_val,  H[E] = (E S + S E)/2 + lambda2 E + diag(E_ii / w_ii^2),
  * solved by conjugate gradients (FP64 vectors, relative residual cg_tol, at
- * most cg_max_iter iterations).  Xval: device, nval x p.  Returns HPC_OK, or
+ * most cg_max_iter iterations).  Xval: device, nval x p, row-major, caller-owned;
+ * S_val is not formed: its term (Omega S_val)_ij on A is read from X_val Omega
+ * and X_val (scratch 2 p nval values of the handle's type).  Returns HPC_OK, or
  * HPC_NOT_CONVERGED when cg_max_iter was reached (results still written). */
 int hpc_hypergrad(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double cg_tol, int64_t cg_max_iter,
                   double* dlambda1, double* dlambda2, hpc_hypergrad_info* info);

@@ -891,7 +891,7 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
     int prec = h->precision;
     if (h->variant == HPC_OBS) {
         STATUS_TRY(load_x_obs(h, Xd));
-        hpc::launch_transpose(Xd, xdt, h->n, h->p, h->p, h->xt, HPC_F32, h->ldx, 1.0f, h->stream);
+        hpc::launch_transpose(Xd, xdt, h->n, h->p, h->p, h->xt, HPC_F32, h->ldx, 1.0, h->stream);
         hpc::launch_obs_split(prec, h->xt, h->p, h->ldx, h->ldx, h->xp[0], h->xp[1], h->n, h->p, h->stream);
         e = cudaGetLastError();
     } else if (prec == HPC_PREC_FP64 || prec == HPC_PREC_FP32) {
@@ -1677,10 +1677,11 @@ int backward_t(hpc_ctx* h, const void* X, int xdt, double grad_loss, void* dOmeg
         T* xt = static_cast<T*>(h->adj_buf);
         T* yt = reinterpret_cast<T*>(static_cast<uint8_t*>(h->adj_buf) + plane);
         const int tdt = sizeof(T) == 8 ? HPC_F64 : HPC_F32;
-        hpc::launch_transpose(X, xdt, n, p, p, xt, tdt, n, 1.0f, h->stream);                 // X^T (p x n)
+        hpc::launch_transpose(X, xdt, n, p, p, xt, tdt, n, 1.0, h->stream);                  // X^T (p x n)
         hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), xt, n, n, yt, n, h->stream);  // Y^T = Omega X^T
-        hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), yt, n, n, xt, n, h->stream);  // Omega Y^T
-        hpc::launch_transpose(xt, tdt, p, n, n, dX, tdt, p, (float)(grad_loss / (double)n), h->stream);
+        // dX = (Omega Y^T)^T grad_loss / n, transposed as it is written
+        hpc::launch_spmm_dense_t<T>(p, om, h->rinfo, as<T>(h->rdv), yt, n, n, static_cast<T*>(dX), p,
+                                    (T)(grad_loss / (double)n), h->stream);
     }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -1693,85 +1694,106 @@ int hypergrad_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double cg_t
     const int p = (int)h->p;
     const int64_t nnz = h->nnz;
     const size_t vs = sizeof(T);
-    const size_t b_s = align256((size_t)p * h->ld * vs);
+    const size_t b_x = align256((size_t)p * nval * vs);
     const size_t b_v = align256(nnz * sizeof(double));
     const size_t b_i = align256(nnz * sizeof(int));
     const size_t b_p = align256(1024 * sizeof(double));
-    STATUS_TRY(adj_reserve(h, b_s + 8 * b_v + b_i + b_p + 4 * 256));
+    STATUS_TRY(adj_reserve(h, 2 * b_x + 9 * b_v + 2 * b_i + b_p + 4 * 256));
     uint8_t* q = static_cast<uint8_t*>(h->adj_buf);
-    T* Sv = reinterpret_cast<T*>(q); q += b_s;
+    T* xtv = reinterpret_cast<T*>(q); q += b_x;
+    T* ytv = reinterpret_cast<T*>(q); q += b_x;
     double* om_d = reinterpret_cast<double*>(q); q += b_v;
     double* sgn = reinterpret_cast<double*>(q); q += b_v;
     double* Tv = reinterpret_cast<double*>(q); q += b_v;
     double* bvec = reinterpret_cast<double*>(q); q += b_v;
     double* x = reinterpret_cast<double*>(q); q += b_v;
     double* r = reinterpret_cast<double*>(q); q += b_v;
-    double* pv = reinterpret_cast<double*>(q); q += b_v;
+    double* pbuf[2];
+    pbuf[0] = reinterpret_cast<double*>(q); q += b_v;
+    pbuf[1] = reinterpret_cast<double*>(q); q += b_v;
     double* Ap = reinterpret_cast<double*>(q); q += b_v;
     int* tr = reinterpret_cast<int*>(q); q += b_i;
+    int* rowid = reinterpret_cast<int*>(q); q += b_i;
     double* part = reinterpret_cast<double*>(q); q += b_p;
     void* cg = q; q += 256;
     double* out = reinterpret_cast<double*>(q);
     cudaStream_t s = h->stream;
     hpc::Csr<T> om = cur_csr<T>(h);
 
-    // S_val = X_val^T X_val / n_val in the handle's precision
-    CUDA_TRY(cudaMemsetAsync(Sv, 0, b_s, s));
-    cudaError_t e;
-    if (h->precision == HPC_PREC_FP64 || h->precision == HPC_PREC_FP32) {
-        e = hpc::gram_simt(Xval, xdt, nval, p, Sv, h->vdt, h->ld, s, nullptr);
-    } else {
-        const size_t need = hpc::gram_tc_scratch_bytes(xdt, nval, p, h->precision);
-        STATUS_TRY(drop_prefetch(h));
-        if (need > h->gram_scratch_bytes) {
-            if (h->pf_issued) CUDA_TRY(cudaEventSynchronize(h->ev_pf));
-            if (h->gram_scratch) cudaFree(h->gram_scratch);
-            h->gram_scratch = nullptr;
-            h->tiles_sig = 0;     // a new buffer may reuse the old address
-            h->gram_scratch_bytes = 0;
-            CUDA_TRY(cudaMalloc(&h->gram_scratch, need));
-            h->gram_scratch_bytes = need;
-        }
-        e = hpc::gram_tc(Xval, xdt, nval, p, reinterpret_cast<float*>(Sv), h->ld, h->precision, h->gram_scratch,
-                         h->gram_scratch_bytes, s, nullptr);
-        h->tiles_sig = 0;       // its panels may cover the handle's tile order
-    }
-    if (e != cudaSuccess) { set_cuda_error(e, "held-out Gram", __LINE__); return HPC_ERR_CUDA; }
-
     hpc::launch_row_info<T>(p, om, h->rinfo, as<T>(h->rdv), s);
-    hpc::launch_transpose_index<T>(p, om, tr, s);
+    hpc::launch_transpose_index<T>(p, om, tr, rowid, s);
     hpc::launch_support_vectors<T>(p, nnz, om, om_d, sgn, s);
-    // b = gradient of the held-out loss on the support
-    hpc::launch_support_product<T>(p, om, h->rinfo, om_d, Sv, h->ld, Tv, s);
-    hpc::launch_support_combine<T>(p, om, tr, Tv, om_d, h->lam2, 1, bvec, s);
+    // b = gradient of the held-out loss on the support.  Its term (Omega S_val)_ij is
+    // (1/n_val) <(X_val Omega)_{:,i}, X_val_{:,j}>: Y^T = Omega X_val^T, then one row
+    // pair per support entry; S_val itself is never formed.
+    const int tdt = sizeof(T) == 8 ? HPC_F64 : HPC_F32;
+    hpc::launch_transpose(Xval, xdt, nval, p, p, xtv, tdt, nval, 1.0, s);
+    hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), xtv, nval, nval, ytv, nval, s);
+    hpc::launch_support_sddmm<T>(p, om, ytv, xtv, nval, nval, Tv, s);
+    hpc::launch_support_combine<T>(nnz, rowid, om, tr, Tv, om_d, h->lam2, 1, bvec, nullptr, 0.0, cg, s);
     // CG on H_A v = b
     CUDA_TRY(cudaMemsetAsync(x, 0, nnz * sizeof(double), s));
     CUDA_TRY(cudaMemcpyAsync(r, bvec, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(pv, bvec, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(pbuf[0], bvec, nnz * sizeof(double), cudaMemcpyDeviceToDevice, s));
     const int nb = hpc::cg_part_blocks(nnz);
     const double tol2 = cg_tol * cg_tol;
+    CUDA_TRY(cudaMemsetAsync(cg, 0, hpc::cg_state_bytes(), s));      // the fused reductions' ticket starts at 0
     hpc::launch_dot_part(nnz, r, r, part, s);
     hpc::launch_cg_scalar(part, nb, 0, tol2, cg, s);
+    // One CG iteration k is three kernels: the direction p = r + beta p_old (beta = 0 at
+    // first, so p = r = b) with its S gathers, Ap = H_A p with alpha, then x, r, beta and
+    // the stopping test.  Directions alternate between two buffers.
+    const hpc::Csr<T> omc = om;
+    auto iteration = [&](int64_t k, cudaStream_t st) {
+        double* p_old = pbuf[k & 1];
+        double* p_new = pbuf[(k + 1) & 1];
+        hpc::launch_support_product_p<T>(nnz, rowid, omc, h->rinfo, r, p_old, p_new, cg, static_cast<const T*>(h->S),
+                                         h->ld, Tv, st);
+        hpc::launch_support_combine<T>(nnz, rowid, omc, tr, Tv, p_new, h->lam2, 0, Ap, part, tol2, cg, st);
+        hpc::launch_cg_xr(nnz, cg, p_new, Ap, x, r, part, tol2, st);
+    };
+    // Chunks of kChunk iterations run as one captured graph (an even count, so every
+    // chunk starts on buffer 0); the host reads the stop flag between chunks.
+    constexpr int kChunk = 8;
+    cudaGraphExec_t chunk = nullptr;
+    if (cg_max >= kChunk) {
+        STATUS_TRY(ensure_cap_stream(h));
+        cudaStream_t cs = h->cap_stream;
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < kChunk; ++k) iteration(k, cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            set_cuda_error(ec != cudaSuccess ? ec : cudaErrorUnknown, "CG chunk capture", __LINE__);
+            return HPC_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&chunk, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) { set_cuda_error(ei, "CG chunk instantiate", __LINE__); return HPC_ERR_CUDA; }
+    }
     int64_t it = 0;
     int done = 0;
-    for (; it < cg_max; ++it) {
-        hpc::launch_support_product<T>(p, om, h->rinfo, pv, static_cast<const T*>(h->S), h->ld, Tv, s);
-        hpc::launch_support_combine<T>(p, om, tr, Tv, pv, h->lam2, 0, Ap, s);
-        hpc::launch_dot_part(nnz, pv, Ap, part, s);
-        hpc::launch_cg_scalar(part, nb, 1, tol2, cg, s);
-        hpc::launch_cg_xr(nnz, cg, pv, Ap, x, r, s);
-        hpc::launch_dot_part(nnz, r, r, part, s);
-        hpc::launch_cg_scalar(part, nb, 2, tol2, cg, s);
-        hpc::launch_cg_p(nnz, cg, r, pv, s);
-        if ((it & 7) == 7 || it + 1 == cg_max) {
-            CUDA_TRY(cudaGetLastError());
-            int dd = 0;
-            CUDA_TRY(cudaMemcpyAsync(&dd, reinterpret_cast<uint8_t*>(cg) + 5 * sizeof(double), sizeof(int),
-                                     cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            if (dd) { done = dd; ++it; break; }
+    int status = HPC_OK;
+    while (it < cg_max && status == HPC_OK) {
+        cudaError_t e2 = cudaSuccess;
+        if (chunk && it + kChunk <= cg_max) {
+            e2 = cudaGraphLaunch(chunk, s);
+            it += kChunk;
+        } else {
+            for (; it < cg_max; ++it) iteration(it, s);     // the tail (it is even here)
+            e2 = cudaGetLastError();
         }
+        int dd = 0;
+        if (e2 == cudaSuccess)
+            e2 = cudaMemcpyAsync(&dd, reinterpret_cast<uint8_t*>(cg) + 5 * sizeof(double), sizeof(int),
+                                 cudaMemcpyDeviceToHost, s);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+        if (e2 != cudaSuccess) { set_cuda_error(e2, "CG", __LINE__); status = HPC_ERR_CUDA; }
+        if (dd) { done = dd; break; }
     }
+    if (chunk) cudaGraphExecDestroy(chunk);
+    if (status != HPC_OK) return status;
     // dL_val/dlambda1 = -<v, sgn_off>, dL_val/dlambda2 = -<v, Omega_A>
     hpc::launch_dot_part(nnz, x, sgn, part, s);
     hpc::launch_reduce_parts(part, nb, out, s);

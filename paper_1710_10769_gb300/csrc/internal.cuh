@@ -229,22 +229,32 @@ void launch_dense_grad(int p, Csr<T> om, const int4* rinfo, const T* rdv, const 
 template <typename T>
 void launch_spmm_dense(int p, Csr<T> om, const int4* rinfo, const T* rdv, const T* B, int64_t ldb, int64_t m, T* C,
                        int64_t ldc, cudaStream_t s);
+template <typename T>
+void launch_spmm_dense_t(int p, Csr<T> om, const int4* rinfo, const T* rdv, const T* B, int64_t ldb, int64_t m,
+                         T* Ct, int64_t ldt, T scale, cudaStream_t s);
 void launch_transpose(const void* in, int in_dt, int64_t rows, int64_t cols, int64_t ldi, void* out, int out_dt,
-                      int64_t ldo, float scale, cudaStream_t s);
-template <typename T> void launch_transpose_index(int p, Csr<T> om, int* tr, cudaStream_t s);
+                      int64_t ldo, double scale, cudaStream_t s);
+template <typename T> void launch_transpose_index(int p, Csr<T> om, int* tr, int* row, cudaStream_t s);
 template <typename T>
 void launch_support_product(int p, Csr<T> om, const int4* rinfo, const double* v, const T* S, int64_t lds,
                             double* out, cudaStream_t s);
 template <typename T>
-void launch_support_combine(int p, Csr<T> om, const int* tr, const double* Tv, const double* v, double lam2, int mode,
-                            double* out, cudaStream_t s);
+void launch_support_sddmm(int p, Csr<T> om, const T* yt, const T* xt, int64_t ld, int64_t n, double* out,
+                          cudaStream_t s);
+template <typename T>
+void launch_support_product_p(int64_t nnz, const int* row, Csr<T> om, const int4* rinfo, const double* r,
+                              const double* p_old, double* p_new, const void* cg, const T* S, int64_t lds,
+                              double* out, cudaStream_t s);
+template <typename T>
+void launch_support_combine(int64_t nnz, const int* row, Csr<T> om, const int* tr, const double* Tv, const double* v,
+                            double lam2, int mode, double* out, double* part, double tol2, void* cg, cudaStream_t s);
 template <typename T>
 void launch_support_vectors(int p, int64_t nnz, Csr<T> om, double* omega_d, double* sign_off, cudaStream_t s);
 int cg_part_blocks(int64_t n);
 void launch_dot_part(int64_t n, const double* a, const double* b, double* part, cudaStream_t s);
 void launch_cg_scalar(const double* part, int nb, int stage, double tol2, void* cg, cudaStream_t s);
-void launch_cg_xr(int64_t n, const void* cg, const double* p, const double* Ap, double* x, double* r, cudaStream_t s);
-void launch_cg_p(int64_t n, const void* cg, const double* r, double* p, cudaStream_t s);
+void launch_cg_xr(int64_t n, void* cg, const double* p, const double* Ap, double* x, double* r, double* part,
+                  double tol2, cudaStream_t s);
 size_t cg_state_bytes();
 template <typename T>
 int launch_smooth_parts(int p, Csr<T> om, const double* Tv, double* part, double* out3, cudaStream_t s);

@@ -47,6 +47,26 @@ def test_backward_matches_oracle_gradients(lib):
     s.close()
 
 
+def test_backward_fp64_handle_keeps_fp64(lib):
+    """An FP64 handle: dL/dOmega and dL/dX (its transposes included) carry FP64 through,
+    so both agree with the FP64 oracle far below FP32 rounding."""
+    import torch
+
+    X = small_problem(120, 90, 3.0, 43)
+    lam1, lam2 = 0.12, 0.1
+    Xt = torch.as_tensor(X).cuda()
+    s = lib.Solver(Xt, lam1, lam2, value_dtype=lib.F64, precision=lib.PREC_FP64, eps=1e-10, max_iter=100000)
+    s.solve()
+    Om = s.omega_dense()
+    dO, dX = s.backward(Xt, grad_loss=-1.5)
+    assert dO.dtype == torch.float64 and dX.dtype == torch.float64
+    rO, rX = oracle.smooth_loss_grads(X, Om, lam2)
+    dO, dX = dO.cpu().numpy(), dX.cpu().numpy()
+    assert np.max(np.abs(dO + 1.5 * rO)) <= 1e-12 * np.max(np.abs(rO))
+    assert np.max(np.abs(dX + 1.5 * rX)) <= 1e-12 * np.max(np.abs(rX))
+    s.close()
+
+
 def test_backward_domega_is_the_solvers_gradient_bitwise(lib):
     X = small_problem(300, 200, 4.0, 42).astype(np.float32)
     s, Xt = _solved(lib, X, 0.15, 0.1, eps=1e-4)
@@ -115,6 +135,60 @@ def test_hypergrad_matches_dense_oracle(lib):
     assert np.array_equal(ref_om != 0, Om != 0)
     e1, e2 = oracle.hypergrad(oracle.gram(Xtr), oracle.gram(Xva), ref_om, lam1, lam2)
     assert d1 == pytest.approx(e1, rel=1e-3) and d2 == pytest.approx(e2, rel=1e-3)
+    s.close()
+
+
+@pytest.mark.parametrize("handle,xdt", [("f64", "f64"), ("f64", "f32"), ("f64", "bf16"), ("f32", "bf16")])
+def test_hypergrad_handle_and_xval_dtypes(lib, handle, xdt):
+    """The held-out term (Omega S_val on the support) from X_val of each dtype. The
+    held-out values are BF16-representable, so every dtype carries the same numbers; an
+    FP64 handle (FP64 values, FP64 products) must then agree with the dense FP64 oracle
+    to CG accuracy, an FP32 handle to the FP32 tolerance."""
+    import torch
+
+    p = 60
+    Xtr = small_problem(p, 90, 3.0, 45)
+    Xva = torch.as_tensor(small_problem(p, 50, 3.0, 46)).to(torch.bfloat16).double()
+    lam1, lam2 = 0.1, 0.15
+    if handle == "f64":
+        Xt = torch.as_tensor(Xtr).cuda()
+        s = lib.Solver(Xt, lam1, lam2, value_dtype=lib.F64, precision=lib.PREC_FP64, eps=1e-10, max_iter=100000)
+        s.solve()
+        rel, tol = 1e-8, 1e-13
+    else:
+        s, Xt = _solved(lib, Xtr.astype(np.float32), lam1, lam2)
+        rel, tol = REL, 1e-10
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[xdt]
+    d1, d2, info = s.hypergrad(Xva.to(tdt).cuda(), tol=tol)
+    assert info["converged"] == 1
+    Om = s.omega_dense()
+    Xtr_used = Xtr if handle == "f64" else Xtr.astype(np.float32).astype(np.float64)
+    r1, r2 = oracle.hypergrad(oracle.gram(Xtr_used), oracle.gram(Xva.numpy()), Om, lam1, lam2)
+    assert d1 == pytest.approx(r1, rel=rel)
+    assert d2 == pytest.approx(r2, rel=rel)
+    s.close()
+
+
+def test_hypergrad_iteration_cap(lib):
+    """CG runs in captured chunks of eight iterations plus a directly launched tail:
+    the cap is honoured exactly below, at and above one chunk, a capped run reports
+    NOT_CONVERGED, repeats bitwise, and more iterations approach the converged value."""
+    import torch
+
+    p = 60
+    Xtr = small_problem(p, 90, 3.0, 45).astype(np.float32)
+    Xva = torch.as_tensor(small_problem(p, 50, 3.0, 46).astype(np.float32)).cuda()
+    s, _ = _solved(lib, Xtr, 0.1, 0.15)
+    ref1, ref2, info = s.hypergrad(Xva, tol=1e-12)
+    assert info["converged"] == 1
+    errs = []
+    for cap in (5, 8, 13):
+        d1, d2, info = s.hypergrad(Xva, tol=1e-30, max_iter=cap)
+        assert info["converged"] == 0 and info["cg_iterations"] == cap
+        e1, e2, _ = s.hypergrad(Xva, tol=1e-30, max_iter=cap)
+        assert (d1, d2) == (e1, e2)
+        errs.append(abs(d1 - ref1) + abs(d2 - ref2))
+    assert errs[2] <= errs[0]
     s.close()
 
 
