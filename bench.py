@@ -216,7 +216,7 @@ def run_row(args):
         w = WORKLOADS["path_p8192"]
         lam = sorted(PATH_LAMBDA1, reverse=True)
         X = make_x(w, device="cuda")
-        s = hpc.Solver(X, lam[0], PATH_LAMBDA2, eps=w.eps, max_iter=100000)
+        s = hpc.Solver(X, lam[0], PATH_LAMBDA2, eps=w.eps, max_iter=100000, device_loop=args.device_loop)
         for _ in range(args.warmup):
             s.load_x(X)
             s.solve_path(lam, PATH_LAMBDA2, return_estimates=False)
@@ -258,7 +258,8 @@ def run_row(args):
         _line("lambda1 path iters/s, 32 points on p=8192 n=4096 (ms_per_step = load + whole path)", its / (ms / 1000),
               "iters/s", ms / args.steps, args, True, "f32",
               {"workload": "path_p8192", "p": p, "n": w.n, "points": len(lam), "lambda2": PATH_LAMBDA2,
-               "gram_precision": s.precision_name(), "loop": "one graph launch per path"},
+               "gram_precision": s.precision_name(),
+               "loop": "one graph launch per path" if args.device_loop else "host-driven"},
               roof, clk.summary(), None, cpu, iterations_per_step=its // args.steps,
               iteration_ms=t_it * 1000)
         s.close()
