@@ -184,6 +184,37 @@ def _dtype_code(t) -> int:
     return {torch.float32: F32, torch.float64: F64, torch.bfloat16: BF16}[t.dtype]
 
 
+def _matrix(X, rows, cols, what, cuda=None, dtypes=None):
+    """Check a row-major matrix argument before its pointer crosses the C ABI, which
+    cannot see shapes: a 2-D torch tensor (or numpy array, on the host) of shape (rows,
+    cols) (None: any), contiguous, of a supported dtype, on the device when cuda is
+    True and on the host when False.  Raises TypeError / ValueError; returns X."""
+    import torch
+
+    if isinstance(X, np.ndarray):
+        if cuda:
+            raise ValueError(f"{what}: a CUDA tensor is required, got a numpy array")
+        ok = {np.dtype(np.float32), np.dtype(np.float64)}
+        if X.dtype not in ok:
+            raise TypeError(f"{what}: dtype {X.dtype} is not float32 or float64")
+    elif isinstance(X, torch.Tensor):
+        if cuda is not None and X.is_cuda != cuda:
+            raise ValueError(f"{what}: must be on the {'GPU' if cuda else 'host'}, got {X.device}")
+        if not X.is_contiguous():
+            raise ValueError(f"{what}: must be contiguous (row-major)")
+        ok = dtypes or (torch.float32, torch.float64, torch.bfloat16)
+        if X.dtype not in ok:
+            raise TypeError(f"{what}: dtype {X.dtype} is not one of {ok}")
+    else:
+        raise TypeError(f"{what}: expected a torch tensor or numpy array, got {type(X).__name__}")
+    if X.ndim != 2:
+        raise ValueError(f"{what}: expected a 2-D matrix, got shape {tuple(X.shape)}")
+    if (rows is not None and X.shape[0] != rows) or (cols is not None and X.shape[1] != cols):
+        raise ValueError(f"{what}: expected shape ({rows if rows is not None else 'any'}, "
+                         f"{cols if cols is not None else 'any'}), got {tuple(X.shape)}")
+    return X
+
+
 def _stream_ptr(stream):
     import torch
 
@@ -218,7 +249,7 @@ class Solver:
             n, p = X.shape
             xdt = _dtype_code(X)
         elif X is not None and not X.is_cuda:
-            assert X.is_contiguous() and X.dim() == 2
+            _matrix(X, None, None, "X", cuda=False)
             self.options.x_on_host = 1
             ptr = C.c_void_p(X.data_ptr())
             n, p = X.shape
@@ -227,7 +258,7 @@ class Solver:
             ptr = None
             xdt = F32 if xdtype is None else xdtype
         else:
-            assert X.is_cuda and X.is_contiguous() and X.dim() == 2
+            _matrix(X, None, None, "X", cuda=True)
             ptr = C.c_void_p(X.data_ptr())
             n, p = X.shape
             xdt = _dtype_code(X)
@@ -259,10 +290,9 @@ class Solver:
 
     def load_x(self, X):
         if isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X)
+            X = _matrix(np.ascontiguousarray(X), self.n, self.p, "X")
             st = self._lib.hpc_load_x(self._h, X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1)
-        elif not X.is_cuda:
-            assert X.is_contiguous()
+        elif not _matrix(X, self.n, self.p, "X").is_cuda:
             st = self._lib.hpc_load_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 1)
         else:
             st = self._lib.hpc_load_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 0)
@@ -273,10 +303,10 @@ class Solver:
         transfer now, its Gram panels after the next load's Gram).  Pipeline:
         prefetch_x(X_next); load_x(X_cur); solve() -- with distinct buffers."""
         if isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X)
+            X = _matrix(np.ascontiguousarray(X), self.n, self.p, "X")
             st = self._lib.hpc_prefetch_x(self._h, X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1)
         else:
-            assert X.is_contiguous()
+            _matrix(X, self.n, self.p, "X")
             st = self._lib.hpc_prefetch_x(self._h, C.c_void_p(X.data_ptr()), _dtype_code(X), 0 if X.is_cuda else 1)
         return _check(st, "hpc_prefetch_x")
 
@@ -321,10 +351,10 @@ class Solver:
         if X is None:
             ptr, xdt, host = None, F32, 0
         elif isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X)
+            X = _matrix(np.ascontiguousarray(X), self.n, self.p, "X")
             ptr, xdt, host = X.ctypes.data_as(C.c_void_p), _dtype_code(X), 1
         else:
-            assert X.is_contiguous() and X.dim() == 2
+            _matrix(X, self.n, self.p, "X")
             ptr, xdt, host = C.c_void_p(X.data_ptr()), _dtype_code(X), 0 if X.is_cuda else 1
         _check(self._lib.hpc_autotune(self._h, ptr, xdt, host, int(iters), C.byref(t), C.byref(rep)), "hpc_autotune")
         return t.as_dict(), rep.as_list()
@@ -421,6 +451,7 @@ class Solver:
         (``hpc_backward``); X is the device data the solver was loaded with."""
         import torch
 
+        _matrix(X, self.n, self.p, "X", cuda=True)
         dt = torch.float64 if self.info().value_dtype == F64 else torch.float32
         dO = torch.empty((self.p, self.p), dtype=dt, device=X.device) if domega else None
         dX = torch.empty((self.n, self.p), dtype=dt, device=X.device) if dx else None
@@ -433,6 +464,7 @@ class Solver:
 
     def hypergrad(self, Xval, tol=1e-8, max_iter=20000):
         """(dL_val/dlambda1, dL_val/dlambda2, info) at the current estimate (``hpc_hypergrad``)."""
+        _matrix(Xval, None, self.p, "Xval", cuda=True)
         d1, d2 = C.c_double(0.0), C.c_double(0.0)
         inf = HypergradInfo()
         st = self._lib.hpc_hypergrad(self._h, C.c_void_p(Xval.data_ptr()), _dtype_code(Xval), Xval.shape[0],
@@ -475,9 +507,25 @@ class Solver:
         return r[:k], c[:k], o[:k], g[:k]
 
 
+def _check_s(S, p, dtypes):
+    """S for hpc_gram*: a CUDA (p, lds) tensor with lds >= p and unit column stride."""
+    import torch
+
+    if not isinstance(S, torch.Tensor) or not S.is_cuda or S.dim() != 2:
+        raise ValueError("S: expected a 2-D CUDA tensor")
+    if S.dtype not in dtypes:
+        raise TypeError(f"S: dtype {S.dtype} is not one of {dtypes}")
+    if S.shape[0] != p or S.shape[1] < p or S.stride(1) != 1 or S.stride(0) < p:
+        raise ValueError(f"S: expected ({p}, >= {p}) rows of unit stride, got shape {tuple(S.shape)} "
+                         f"strides {S.stride()}")
+
+
 def gram(X, S, precision=PREC_AUTO, stream=None):
     """S = X^T X / n on the device (``hpc_gram``); S is a (p, lds) tensor, lds >= p."""
-    n, p = X.shape
+    import torch
+
+    n, p = _matrix(X, None, None, "X", cuda=True).shape
+    _check_s(S, p, (torch.float32, torch.float64))
     st = load().hpc_gram(C.c_void_p(X.data_ptr()), _dtype_code(X), n, p, C.c_void_p(S.data_ptr()),
                          _dtype_code(S), S.stride(0), precision, _stream_ptr(stream))
     return _check(st, "hpc_gram")
@@ -490,7 +538,10 @@ def gram_noalloc(X, S, precision=PREC_AUTO, stream=None):
     """S = X^T X / n through ``hpc_gram_noalloc``: the tensor-core Gram with its scratch in a
     static device array, for callers that must not allocate device memory; S is a float32
     (p, lds) tensor."""
-    n, p = X.shape
+    import torch
+
+    n, p = _matrix(X, None, None, "X", cuda=True).shape
+    _check_s(S, p, (torch.float32,))
     st = load().hpc_gram_noalloc(C.c_void_p(X.data_ptr()), _dtype_code(X), n, p, C.c_void_p(S.data_ptr()),
                                  S.stride(0), precision, _stream_ptr(stream))
     return _check(st, "hpc_gram_noalloc")

@@ -56,3 +56,38 @@ def test_struct_layouts_match_the_header(lib):
     assert ctypes.sizeof(lib.Stats) == 13 * 8 + 2 * 4 + 8
     assert ctypes.sizeof(lib.Tuning) == 28
     assert ctypes.sizeof(lib.TuneReport) == 8 + lib.TUNE_MAX_TRIALS * 16
+
+
+def test_binding_checks_matrix_arguments_before_the_abi(lib):
+    """The C ABI takes bare pointers and sizes, so the binding checks every matrix it
+    passes: shape against the handle's (n, p), row-major contiguity, dtype, and device.
+    A mismatch raises before any pointer crosses the boundary."""
+    import numpy as np
+    import torch
+
+    m = lib._matrix
+    X = torch.zeros(3, 4)
+    assert m(X, 3, 4, "X") is X
+    assert m(X, None, 4, "X") is X
+    with pytest.raises(ValueError, match="shape"):
+        m(X, 3, 5, "X")
+    with pytest.raises(ValueError, match="shape"):
+        m(X, 2, None, "X")
+    with pytest.raises(ValueError, match="contiguous"):
+        m(torch.zeros(4, 3).t(), 3, 4, "X")
+    with pytest.raises(ValueError, match="2-D"):
+        m(torch.zeros(12), None, None, "X")
+    with pytest.raises(TypeError, match="dtype"):
+        m(torch.zeros(3, 4, dtype=torch.int32), 3, 4, "X")
+    with pytest.raises(ValueError, match="GPU"):
+        m(X, 3, 4, "X", cuda=True)
+    with pytest.raises(ValueError, match="CUDA"):
+        m(np.zeros((3, 4)), 3, 4, "X", cuda=True)
+    with pytest.raises(TypeError, match="dtype"):
+        m(np.zeros((3, 4), np.int64), 3, 4, "X")
+    with pytest.raises(TypeError):
+        m([[0.0]], 1, 1, "X")
+    assert m(torch.zeros(3, 4, dtype=torch.bfloat16), 3, 4, "X").dtype == torch.bfloat16
+    # S for the stateless Gram: (p, lds >= p) rows of unit stride, on the device
+    with pytest.raises(ValueError):
+        lib._check_s(torch.zeros(4, 4), 4, (torch.float32,))
