@@ -138,7 +138,8 @@ const char* hpc_last_error(void);
  * The iterate starts at Omega = I (Alg. 1 step 1).  cuda_stream is a
  * cudaStream_t (NULL = default stream).  X may be NULL: then call hpc_load_x
  * before solving.  Errors: HPC_ERR_ARG (n,p < 1; lambda < 0; eps <= 0; bad
- * enum), HPC_ERR_OOM, HPC_ERR_CUDA, HPC_ERR_NOT_IMPLEMENTED. */
+ * enum; Obs with n > 2097120, the rows its transpose of X takes), HPC_ERR_OOM,
+ * HPC_ERR_CUDA, HPC_ERR_NOT_IMPLEMENTED. */
 int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t p,
                double lambda1, double lambda2, hpc_variant variant,
                const hpc_options* opt, void* cuda_stream);
@@ -285,7 +286,8 @@ int hpc_smooth_value(hpc_handle h, double* f);
  * (X Omega Omega + X Omega^T Omega^T)/(2n); the iterate is always symmetric.
  * X: the device data (n x p, dtype xdt) the handle was loaded with; needed only
  * for dX.  dOmega, dX: device buffers in the handle's value dtype (FP32, or
- * FP64 for FP64 handles); either may be NULL.  Allocates scratch on first use. */
+ * FP64 for FP64 handles); either may be NULL.  Allocates scratch on first use.
+ * HPC_ERR_ARG when dX is asked for with n > 2097120 (the rows of X's transpose). */
 int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, void* dOmega, int64_t ld_domega,
                  void* dX);
 
@@ -307,7 +309,8 @@ typedef struct {
  *   dL_val/dlambda1 = -<v, sign_off(Omega_A)>,  dL_val/dlambda2 = -<v, Omega_A>,
  *   H_A v = grad_A L_val,  H[E] = (E S + S E)/2 + lambda2 E + diag(E_ii / w_ii^2),
  * solved by conjugate gradients (FP64 vectors, relative residual cg_tol, at
- * most cg_max_iter iterations).  Xval: device, nval x p, row-major, caller-owned;
+ * most cg_max_iter iterations).  Xval: device, nval x p (nval <= 2097120),
+ * row-major, caller-owned;
  * S_val is not formed: its term (Omega S_val)_ij on A is read from X_val Omega
  * and X_val (scratch 2 p nval values of the handle's type).  Returns HPC_OK, or
  * HPC_NOT_CONVERGED when cg_max_iter was reached (results still written). */

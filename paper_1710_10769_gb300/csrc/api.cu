@@ -1053,6 +1053,11 @@ const char* hpc_last_error(void) { return g_last_error; }
 int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t p, double lambda1,
                double lambda2, hpc_variant variant, const hpc_options* opt, void* cuda_stream) {
     if (!out) return HPC_ERR_ARG;
+    if (variant == HPC_OBS && n > hpc::kTransposeMaxRows) {
+        std::snprintf(g_last_error, sizeof g_last_error, "the Obs variant transposes X: n <= %lld",
+                      (long long)hpc::kTransposeMaxRows);
+        return HPC_ERR_ARG;
+    }
     *out = nullptr;
     hpc_options o;
     if (opt) o = *opt; else hpc_default_options(&o);
@@ -2044,6 +2049,11 @@ int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, v
         !std::isfinite(grad_loss))
         return HPC_ERR_ARG;
     if (!h->S) return HPC_ERR_NOT_IMPLEMENTED;      // needs S (Cov variant)
+    if (dX && h->n > hpc::kTransposeMaxRows) {
+        std::snprintf(g_last_error, sizeof g_last_error, "dL/dX transposes X: n <= %lld",
+                      (long long)hpc::kTransposeMaxRows);
+        return HPC_ERR_ARG;
+    }
     return h->vdt == HPC_F64 ? backward_t<double>(h, X, xdt, grad_loss, dOmega, ld_domega, dX)
                              : backward_t<float>(h, X, xdt, grad_loss, dOmega, ld_domega, dX);
 }
@@ -2054,6 +2064,11 @@ int hpc_hypergrad(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, d
         !dlambda1 || !dlambda2)
         return HPC_ERR_ARG;
     if (!h->S) return HPC_ERR_NOT_IMPLEMENTED;      // needs S (Cov variant)
+    if (nval > hpc::kTransposeMaxRows) {
+        std::snprintf(g_last_error, sizeof g_last_error, "hpc_hypergrad transposes X_val: nval <= %lld",
+                      (long long)hpc::kTransposeMaxRows);
+        return HPC_ERR_ARG;
+    }
     return h->vdt == HPC_F64 ? hypergrad_t<double>(h, Xval, xdt, nval, cg_tol, cg_max_iter, dlambda1, dlambda2, info)
                              : hypergrad_t<float>(h, Xval, xdt, nval, cg_tol, cg_max_iter, dlambda1, dlambda2, info);
 }

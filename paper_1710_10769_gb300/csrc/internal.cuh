@@ -232,6 +232,8 @@ void launch_spmm_dense(int p, Csr<T> om, const int4* rinfo, const T* rdv, const 
 template <typename T>
 void launch_spmm_dense_t(int p, Csr<T> om, const int4* rinfo, const T* rdv, const T* B, int64_t ldb, int64_t m,
                          T* Ct, int64_t ldt, T scale, cudaStream_t s);
+// launch_transpose puts rows / 32 in gridDim.y (at most 65535)
+constexpr int64_t kTransposeMaxRows = 65535ll * 32;
 void launch_transpose(const void* in, int in_dt, int64_t rows, int64_t cols, int64_t ldi, void* out, int out_dt,
                       int64_t ldo, double scale, cudaStream_t s);
 template <typename T> void launch_transpose_index(int p, Csr<T> om, int* tr, int* row, cudaStream_t s);
