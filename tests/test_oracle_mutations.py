@@ -107,3 +107,98 @@ def test_threshold_without_tau_is_caught(monkeypatch):
 
 def test_unmutated_oracle_passes_every_pin():
     assert not _some_pin_fails()
+
+
+# ------------------------------------------------------------- differentiation and entry helpers
+# The differentiation oracle and the sampled-entry helpers (used by the full-size parity
+# tests) carry their own pins; each mistake below must make one of those fail.
+
+_real = {name: getattr(oracle, name) for name in
+         ("smooth_loss_grads", "hypergrad", "hypergrad_sparse", "gram_entries", "gradient_entries")}
+
+
+def _dx_without_transpose_term(X, Omega, lam2):
+    dOm, _ = _real["smooth_loss_grads"](X, Omega, lam2)
+    X = np.asarray(X, dtype=np.float64)
+    return dOm, X @ Omega @ Omega / X.shape[0]
+
+
+def _domega_without_half(X, Omega, lam2):
+    dOm, dX = _real["smooth_loss_grads"](X, Omega, lam2)
+    S = oracle.gram(X)
+    return dOm + 0.5 * (Omega.T @ S + S @ Omega.T), dX
+
+
+def _hypergrad_without_diag_hessian(S, S_val, Omega, lam1, lam2):
+    p = S.shape[0]
+    iu, ju = np.nonzero(np.triu(Omega != 0.0))
+    d = np.diag(Omega)
+    Hm = np.zeros((iu.size, iu.size))
+    for t, (a, b) in enumerate(zip(iu, ju)):
+        E = np.zeros((p, p))
+        E[a, b] = E[b, a] = 1.0
+        Hm[:, t] = (0.5 * (E @ S + S @ E) + lam2 * E)[iu, ju]
+    gval = 0.5 * (Omega @ S_val + S_val @ Omega)
+    gval[np.diag_indices(p)] -= 1.0 / d
+    v = np.linalg.solve(Hm, gval[iu, ju])
+    w = np.where(iu == ju, 1.0, 2.0)
+    s = np.where(iu == ju, 0.0, np.sign(Omega[iu, ju]))
+    return float(-np.sum(w * v * s)), float(-np.sum(w * v * Omega[iu, ju]))
+
+
+def _hypergrad_lambda1_sign(S, S_val, Omega, lam1, lam2):
+    g1, g2 = _real["hypergrad"](S, S_val, Omega, lam1, lam2)
+    return -g1, g2
+
+
+def _sparse_hypergrad_training_data_held_out(X, Xval, omega_csr, lam1, lam2):
+    return _real["hypergrad_sparse"](X, X, omega_csr, lam1, lam2)
+
+
+def _gram_entries_unbiased(X, rows, cols):
+    n = X.shape[0]
+    return _real["gram_entries"](X, rows, cols) * n / (n - 1)
+
+
+def _gradient_entries_without_lam2(X, omega_csr, lam2, rows, cols):
+    return _real["gradient_entries"](X, omega_csr, 0.0, rows, cols)
+
+
+DIFF_MUTATIONS = {
+    "dX_drops_transpose_term": ("smooth_loss_grads", _dx_without_transpose_term),
+    "dOmega_drops_half": ("smooth_loss_grads", _domega_without_half),
+    "hypergrad_drops_diag_hessian": ("hypergrad", _hypergrad_without_diag_hessian),
+    "hypergrad_lambda1_sign": ("hypergrad", _hypergrad_lambda1_sign),
+    "sparse_hypergrad_wrong_held_out_operand": ("hypergrad_sparse", _sparse_hypergrad_training_data_held_out),
+    "gram_entries_divides_by_n_minus_1": ("gram_entries", _gram_entries_unbiased),
+    "gradient_entries_drops_lam2": ("gradient_entries", _gradient_entries_without_lam2),
+}
+
+DIFF_PINS = [
+    lambda: pins.test_entry_helpers_match_dense(),
+    lambda: pins.test_smooth_loss_grads_by_central_differences(),
+    lambda: pins.test_smooth_loss_grads_reduce_to_G_and_Y_Omega_at_symmetric_omega(),
+    lambda: pins.test_hypergrad_by_central_differences_of_resolved_estimates(0),
+    lambda: pins.test_sparse_hypergrad_equals_dense_hypergrad(),
+]
+
+
+def _some_diff_pin_fails():
+    for pin in DIFF_PINS:
+        try:
+            pin()
+        except (AssertionError, FloatingPointError, ValueError, IndexError, np.linalg.LinAlgError):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(DIFF_MUTATIONS))
+def test_planted_differentiation_mistake_is_caught(name, monkeypatch):
+    attr, fn = DIFF_MUTATIONS[name]
+    monkeypatch.setattr(oracle, attr, fn)
+    with np.errstate(all="ignore"):
+        assert _some_diff_pin_fails(), f"no pin catches mutation {name}"
+
+
+def test_unmutated_differentiation_oracle_passes_its_pins():
+    assert not _some_diff_pin_fails()
