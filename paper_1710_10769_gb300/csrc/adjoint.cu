@@ -421,7 +421,10 @@ struct CgState {
     unsigned ticket;      // blocks of the running fused reduction that have stored their partial
 };
 
-// stage 0: rr = rr0 = <r, r> (initial); stage 1: alpha = rr / <p, Ap>; stage 2: beta = rr_new / rr, done test
+// stage 0: rr = rr0 = <r, r> (initial); stage 1: alpha = rr / <p, Ap>; stage 2: beta = rr_new / rr, done test.
+// The stop flag is set once: iterations that run on after a stop (up to the host's next
+// check) leave x and r alone and must not turn "converged" into "non-positive
+// curvature" (b = 0 gives p = 0) or the reverse.
 __device__ void cg_update(int stage, double v, double tol2, CgState* cg) {
     if (stage == 0) {
         cg->rr = v;
@@ -431,11 +434,11 @@ __device__ void cg_update(int stage, double v, double tol2, CgState* cg) {
     } else if (stage == 1) {
         cg->pap = v;
         cg->alpha = (v > 0.0) ? cg->rr / v : 0.0;
-        if (!(v > 0.0)) cg->done = 2;      // H not positive definite along p: stop
+        if (!(v > 0.0) && cg->done == 0) cg->done = 2;      // H not positive definite along p: stop
     } else {
         cg->beta = (cg->rr > 0.0) ? v / cg->rr : 0.0;
         cg->rr = v;
-        if (v <= tol2 * cg->rr0) cg->done = 1;
+        if (cg->done == 0 && v <= tol2 * cg->rr0) cg->done = 1;
     }
 }
 
