@@ -43,3 +43,56 @@ def test_single_rank_is_identity():
     import bench
 
     assert bench.reduce_over_ranks(12.5, 7, None, "cpu") == (12.5, 7.0)
+
+
+def test_clock_summary_reads_nvidia_smi_lines():
+    """The clocks object of a bench line: median SM clock under load, the maximum, and the
+    throttle reasons seen Active in any sample (the ones that void a measurement)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "0, 1590, 2070, 1380.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2025, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1300.0, 0x0, Not Active, Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s["samples"] == 3
+    assert s["sm_mhz"] == 1980.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                                               "samples": 0}
+
+
+def test_measured_traffic_is_keyed_on_source_size_and_setting(tmp_path, monkeypatch):
+    """A traffic figure from profiles/roofline_traffic.txt is used only for the kernel
+    source it was captured on (sha256), the captured sizes and, for the Gram, the
+    captured launch setting; anything else gives None (the line's traffic is null)."""
+    import hashlib
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    csrc = tmp_path / "paper_1710_10769_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "adjoint.cu").write_text("// kernel v1\n")
+    (csrc / "gram_tc.cu").write_text("// gram v1\n")
+    sha = lambda name: hashlib.sha256((csrc / name).read_bytes()).hexdigest()
+    (tmp_path / "profiles" / "roofline_traffic.txt").write_text(
+        "# comment = ignored\n"
+        f"dense_grad.src_sha256={sha('adjoint.cu')}\ndense_grad.p=16384\ndense_grad.n=4096\n"
+        "dense_grad.dram_bytes=1755441824\n"
+        f"gram.src_sha256={sha('gram_tc.cu')}\ngram.p=65536\ngram.n=32768\n"
+        "gram.band16.maxima1.sched1.dram_bytes=163673027072\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("dense_grad", 16384, 4096) == 1755441824.0
+    assert bench.measured_traffic("dense_grad", 8192, 4096) is None
+    assert bench.measured_traffic("gram", 65536, 32768, "band16.maxima1.sched1.") == 163673027072.0
+    assert bench.measured_traffic("gram", 65536, 32768, "band32.maxima1.sched1.") is None
+    assert bench.measured_traffic("screen_pass", 65536, 32768) is None       # no entry, no source
+    (csrc / "adjoint.cu").write_text("// kernel v2\n")                      # the kernel changed
+    assert bench.measured_traffic("dense_grad", 16384, 4096) is None
