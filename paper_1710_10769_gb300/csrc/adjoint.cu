@@ -4,10 +4,11 @@
 //    + lambda2/2 ||Omega||_F^2, S = X^T X / n, at the (symmetric) iterate:
 //      dL/dOmega = -diag(1/w_ii) + (Omega S + S Omega)/2 + lambda2 Omega   (Alg. 1 step 4's G, dense)
 //      dL/dX     = X Omega^2 / n = Y Omega / n,  Y = X Omega.
-//    Dense W = Omega S comes from a row-split SpMM in the screening pass's
-//    canonical FMA order (so G agrees bitwise with the solver's G on its
-//    candidates), then an in-place tile-pair symmetrisation and the support
-//    terms.  X Omega^2 / n is two row-split SpMMs on X^T.
+//    dL/dOmega is one kernel over pairs of tiles (I <= J): W[I, J] and W[J, I] in
+//    the screening pass's canonical FMA order (so G agrees bitwise with the solver's
+//    G on its candidates), symmetrised, with the support terms, written once.
+//    X Omega^2 / n is two row-split SpMMs on X^T, the second writing its result
+//    transposed.
 //  * The implicit lambda-gradient of a held-out loss on the support A: the
 //    support-restricted products (E S)_ij by gathers, the Hessian-vector product
 //      H[E]_ij = ((E S)_ij + (E S)_ji)/2 + lambda2 E_ij + [i=j] E_ii / w_ii^2,
