@@ -249,26 +249,35 @@ def gram_entries(X, rows, cols) -> np.ndarray:
 def gradient_entries(X, omega_csr: sp.csr_matrix, lam2, rows, cols) -> np.ndarray:
     """G_ij of Alg. 1 step 4 at the listed pairs for a sparse symmetric Omega, from X.
 
-    W_ij = sum_k w_ik S_kj and W_ji = sum_k w_jk S_ki with every S entry formed
-    from X in FP64.
+    W_ij = sum_k w_ik S_kj (Alg. 2 step 3) with S = X^T X / n, summed in FP64 as
+    <X w_i, x_j> / n: the column X w_i = sum_k w_ik x_k is formed once per row i that the
+    pairs name, and W_ji = <X w_j, x_i> / n likewise.
     """
     om = sp.csr_matrix(omega_csr, dtype=np.float64)
     om.sort_indices()
     n = X.shape[0]
+    X = np.asfortranarray(X)                 # columns contiguous: x_k is one slice
+    w_pairs = np.asarray(om[np.asarray(rows), np.asarray(cols)], dtype=np.float64).ravel()
+    diag = om.diagonal()
+    xw = {}
+
+    def x_omega(i):
+        if i not in xw:
+            ki = om.indices[om.indptr[i]:om.indptr[i + 1]]
+            vi = om.data[om.indptr[i]:om.indptr[i + 1]]
+            xw[i] = _columns(X, ki) @ vi if ki.size else np.zeros(n)
+        return xw[i]
+
     out = np.empty(len(rows))
     for t, (i, j) in enumerate(zip(rows, cols)):
         i, j = int(i), int(j)
-        ki = om.indices[om.indptr[i]:om.indptr[i + 1]]
-        vi = om.data[om.indptr[i]:om.indptr[i + 1]]
-        kj = om.indices[om.indptr[j]:om.indptr[j + 1]]
-        vj = om.data[om.indptr[j]:om.indptr[j + 1]]
-        xi = _columns(X, [i])[:, 0]
-        xj = _columns(X, [j])[:, 0]
-        w_ij = vi @ ((_columns(X, ki).T @ xj) / n) if ki.size else 0.0
-        w_ji = vj @ ((_columns(X, kj).T @ xi) / n) if kj.size else 0.0
-        g = 0.5 * (w_ij + w_ji) + lam2 * om[i, j]
+        xi = np.asarray(X[:, i], dtype=np.float64)
+        xj = np.asarray(X[:, j], dtype=np.float64)
+        w_ij = (x_omega(i) @ xj) / n
+        w_ji = (x_omega(j) @ xi) / n
+        g = 0.5 * (w_ij + w_ji) + lam2 * w_pairs[t]
         if i == j:
-            g -= 1.0 / om[i, i]
+            g -= 1.0 / diag[i]
         out[t] = g
     return out
 
