@@ -154,7 +154,8 @@ def round_to_bf16(a: np.ndarray) -> np.ndarray:
 
 
 def sample_x_cpu(omega0: sp.csr_matrix, n: int, seed: int) -> np.ndarray:
-    """X = Z L^-T in float64 on the CPU (dense Cholesky; fine up to p ~ 8192)."""
+    """X = Z L^-T in float64 on the CPU (dense Cholesky; fine up to p ~ 8192), where
+    Omega0 = L L^T: rows of X have covariance L^-1 L^-T = (L^T L)^-1 (not Omega0^-1)."""
     import scipy.linalg as sla
 
     p = omega0.shape[0]
@@ -166,7 +167,8 @@ def sample_x_cpu(omega0: sp.csr_matrix, n: int, seed: int) -> np.ndarray:
 
 
 def sample_x_cuda(omega0: sp.csr_matrix, n: int, seed: int, device: str = "cuda"):
-    """X = Z L^-T on a CUDA device with torch (FP32 factor), returned as a float32 tensor."""
+    """X = Z L^-T on a CUDA device with torch (FP32 factor), returned as a float32 tensor;
+    the same law as sample_x_cpu (row covariance (L^T L)^-1)."""
     import torch
 
     p = omega0.shape[0]
