@@ -139,6 +139,20 @@ def measured_traffic(kernel, p, n, tag=""):
         return None
 
 
+def lemma31_flops(n, p, s, t, d):
+    """Lemma 3.1's dominant flop counts of the paper's formulation (Sec. 3), with s
+    prox-gradient iterations, t line-search trials per iteration and d nonzeros per row
+    of the iterate:
+      F_Cov = 2 n p^2 + 2 d p^2 (s t + 1)   (S once, then Omega S per trial),
+      F_Obs = 2 n p^2 s + 2 d n p (s t + 1) (Z = Y X per iteration, Y = Omega X^T per trial),
+    and the lemma's condition for Cov to be the cheaper, d/p < n / ((p - n) t) (its large-s
+    limit; always true for p <= n)."""
+    cov = 2.0 * n * p * p + 2.0 * d * p * p * (s * t + 1)
+    obs = 2.0 * n * p * p * s + 2.0 * d * n * p * (s * t + 1)
+    cheaper = True if p <= n else d / p < n / ((p - n) * t)
+    return {"flops_cov": cov, "flops_obs": obs, "cov_cheaper": cheaper}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -729,6 +743,13 @@ def main(argv=None):
             "iteration_loop_its": iters / (sum(r["ms_total"] for r in recs) / 1000.0),
             "grad_pass_ms": scr_ms / max(scr_launches, 1),
             "final_nnz": recs[-1]["nnz"], "final_F": recs[-1]["F"],
+            # the paper's cost model (Lemma 3.1) for this solve, for context: s and t are the
+            # solve's own counts, d the final estimate's nonzeros per row (the lemma averages
+            # d over every trial's iterate)
+            "paper_model": dict(lemma31_flops(n, p, recs[-1]["iterations"],
+                                              recs[-1]["ls_trials"] / max(recs[-1]["iterations"], 1),
+                                              recs[-1]["nnz"] / p),
+                                s=recs[-1]["iterations"], d="final nnz / p"),
             "roofline": roof, "roofline_kernels": [roof_gram, roof_scr], "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
             "cpu_baseline": cpu, "plain_fp32": plain, "other_loop": other,
             "autotune_trials": [(t["knob"], t["value"], round(t["ms"], 4)) for t in tune_trials],

@@ -96,3 +96,20 @@ def test_measured_traffic_is_keyed_on_source_size_and_setting(tmp_path, monkeypa
     assert bench.measured_traffic("screen_pass", 65536, 32768) is None       # no entry, no source
     (csrc / "adjoint.cu").write_text("// kernel v2\n")                      # the kernel changed
     assert bench.measured_traffic("dense_grad", 16384, 4096) is None
+
+
+def test_lemma31_flop_counts():
+    """The bench's statement of Lemma 3.1: F_Cov = 2np^2 + 2dp^2(st+1) and
+    F_Obs = 2np^2 s + 2dnp(st+1), hand-evaluated; and its Cov-is-cheaper condition
+    d/p < n/((p-n)t) agrees with comparing the two counts once s is large."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    m = bench.lemma31_flops(n=100, p=400, s=10, t=3, d=5)
+    assert m["flops_cov"] == 2 * 100 * 400 ** 2 + 2 * 5 * 400 ** 2 * 31
+    assert m["flops_obs"] == 2 * 100 * 400 ** 2 * 10 + 2 * 5 * 100 * 400 * 31
+    for n, p, t, d in [(100, 400, 3, 5), (100, 40000, 2.9, 8), (8192, 16384, 3, 1.2), (500, 520, 4, 40),
+                       (12800, 40000, 3, 200), (100, 40000, 3, 0.5)]:
+        big = bench.lemma31_flops(n, p, 1e9, t, d)
+        assert big["cov_cheaper"] == (big["flops_cov"] < big["flops_obs"]), (n, p, t, d)
+    assert bench.lemma31_flops(n=500, p=400, s=3, t=2, d=9)["cov_cheaper"] is True     # p <= n
