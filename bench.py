@@ -220,7 +220,7 @@ def run_row(args):
     import oracle
     import paper_1710_10769_gb300 as hpc
     from workloads import (BATCH_PROBLEMS, PATH_LAMBDA1, PATH_LAMBDA2, WORKLOADS, make_x, omega0_for,
-                           sample_x_cpu, sample_x_cuda)
+                           sample_x_cpu, sample_x_cuda, cast_x, HELDOUT_STREAM)
 
     hbm, bf16, bf16_sus, peak_src = _peaks()
     torch.cuda.set_device(0)
@@ -331,8 +331,8 @@ def run_row(args):
     if args.row == "adjoint":
         w = WORKLOADS["adjoint_p16384"]
         om0 = omega0_for(w)
-        Xtr = sample_x_cuda(om0, w.n, w.seed)
-        Xva = sample_x_cuda(om0, 2048, w.seed + 7919)
+        Xtr = cast_x(sample_x_cuda(om0, w.n, w.seed), "f32")
+        Xva = cast_x(sample_x_cuda(om0, 2048, w.seed, stream=HELDOUT_STREAM), "f32")
         s = hpc.Solver(Xtr, w.lambda1, w.lambda2, precision=hpc.PREC_FP32, eps=w.eps, max_iter=100000)
         s.solve()
         for _ in range(args.warmup):

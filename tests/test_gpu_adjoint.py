@@ -200,10 +200,10 @@ def test_differentiation_workload_full_size(lib):
 
     w = WORKLOADS["adjoint_p16384"]
     om0 = omega0_for(w)
-    from workloads import sample_x_cuda
+    from workloads import HELDOUT_STREAM, cast_x, sample_x_cuda
 
-    Xtr = sample_x_cuda(om0, w.n, w.seed)
-    Xva = sample_x_cuda(om0, 2048, w.seed + 7919)
+    Xtr = cast_x(sample_x_cuda(om0, w.n, w.seed), "f32")
+    Xva = cast_x(sample_x_cuda(om0, 2048, w.seed, stream=HELDOUT_STREAM), "f32")
     s = lib.Solver(Xtr, w.lambda1, w.lambda2, precision=lib.PREC_FP32, eps=1e-6, max_iter=20000)
     s.solve()
     d1, d2, info = s.hypergrad(Xva, tol=1e-10)

@@ -5,7 +5,12 @@
 - banded graphs: every pair with 0 < |i - j| <= b; tridiagonal: 1.0 and -0.4;
 - the same seed gives the same matrix, another seed another one;
 - BF16 rounding is round-to-nearest-even, the conversion torch does;
-- X = Z L^-T, with covariance (L^T L)^-1 where Omega0 = L L^T;
+- the normals come from Philox4x32-10, which reproduces its published known-answer
+  vectors, and the numpy and torch forms of the draw give the same integers;
+- Omega0 = B^T B for the sparse factor the sampler builds, and the rows of X follow
+  N(0, Omega0^-1);
+- a row of X depends on its index only (not on how the rows are chunked), and the
+  torch form of the draw agrees with the numpy form to FP64 rounding;
 - the workload table holds the shapes the benchmark and the tests name.
 """
 import math
@@ -13,8 +18,13 @@ import math
 import numpy as np
 import pytest
 
-from workloads import (BATCH_PROBLEMS, PATH_LAMBDA1, PATH_LAMBDA2, WORKLOADS, omega0_banded, omega0_random,
-                       omega0_tridiagonal, round_to_bf16, sample_x_cpu)
+import os
+
+from workloads import (BATCH_PROBLEMS, PATH_LAMBDA1, PATH_LAMBDA2, WORKLOADS, normal_pairs, omega0_banded,
+                       omega0_random, omega0_tridiagonal, philox4x32, round_to_bf16, sample_factor, sample_rows_cpu,
+                       sample_x_cpu, sample_x_cuda)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _check_dominant(om, lo, hi):
@@ -73,23 +83,62 @@ def test_bf16_rounding_is_nearest_even():
     assert np.array_equal(round_to_bf16(x), ref)
 
 
-def test_samples_follow_the_stated_law():
-    """X = Z L^-T with Omega0 = L L^T: rows of X have covariance L^-1 L^-T = (L^T L)^-1, so
-    the data's precision matrix is L^T L (Omega0's pattern plus Cholesky fill) and not
-    Omega0 itself. Parity does not depend on it, because the oracle and the GPU read the
-    same X. The inputs' structure does, and that deviation is recorded with the recipe."""
-    p, n = 12, 40000
-    om = omega0_random(p, 3.0, 5)
-    X = sample_x_cpu(om, n, 5)
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for ln in fh:
+            if ln.strip() and not ln.startswith("#"):
+                rows.append([int(t, 16) for t in ln.split()])
+    assert len(rows) == 3
+    for r in rows:
+        c = [np.array([v], dtype=np.int64) for v in r[:4]]
+        out = philox4x32(*c, r[4], r[5])
+        assert [int(o[0]) for o in out] == r[6:10]
+
+
+def test_numpy_and_torch_draws_agree():
+    import torch
+
+    z_np = normal_pairs(np, 11, 0, np.arange(7), 300)
+    z_t = normal_pairs(torch, 11, 0, np.arange(7), 300, device="cpu").numpy()
+    # the same Philox integers; Box-Muller's log and cos may differ in the last bit
+    assert np.max(np.abs(z_np - z_t)) <= 4 * np.finfo(np.float64).eps * np.max(np.abs(z_np))
+    assert 0.3 < np.mean(np.abs(z_np)) < 1.3 and abs(np.mean(z_np)) < 0.1
+    om = omega0_random(300, 5.0, 3)
+    X = sample_x_cpu(om, 200, 3)
+    Xt = sample_x_cuda(om, 200, 3, device="cpu", chunk=64).numpy()
+    assert np.max(np.abs(X - Xt)) <= 1e-13 * np.max(np.abs(X))
+
+
+def test_sparse_factor_and_rows():
+    for om in (omega0_random(150, 6.0, 2), omega0_banded(90, 3, 4), omega0_tridiagonal(40)):
+        f = sample_factor(om)
+        assert f.m == om.shape[0] + (om.nnz - om.shape[0]) // 2
+        assert abs(f.Bt @ f.Bt.T - om).max() <= 1e-14
+    om = omega0_random(150, 6.0, 2)
+    X = sample_x_cpu(om, 70, 9, chunk=64)
+    assert np.array_equal(X, sample_x_cpu(om, 70, 9, chunk=16))
+    assert np.array_equal(X[[3, 69, 40]], sample_rows_cpu(om, [3, 69, 40], 9))
+    assert not np.array_equal(X, sample_x_cpu(om, 70, 10))
+    assert not np.array_equal(X, sample_x_cpu(om, 70, 9, stream=1))
+
+
+@pytest.mark.parametrize("graph", ["random", "tridiagonal"])
+def test_samples_follow_the_stated_law(graph):
+    """Rows of X follow N(0, Omega0^-1): the sample covariance of many draws is within
+    five standard errors of Omega0^-1 in every entry."""
+    p, n = 12, 200000
+    om = omega0_random(p, 3.0, 5) if graph == "random" else omega0_tridiagonal(p)
+    X = sample_x_cpu(om, n, 5, chunk=20000)
     S = X.T @ X / n
-    L = np.linalg.cholesky(om.toarray())
-    Sigma = np.linalg.inv(L.T @ L)
+    Sigma = np.linalg.inv(om.toarray())
     # each entry's sampling error is about sqrt((Sigma_ii Sigma_jj + Sigma_ij^2) / n)
     sd = np.sqrt((np.outer(np.diag(Sigma), np.diag(Sigma)) + Sigma ** 2) / n)
     assert np.all(np.abs(S - Sigma) <= 5 * sd)
-    # and not Omega0^-1: the two laws are told apart by far more than the sampling error
-    assert np.max(np.abs(S - np.linalg.inv(om.toarray())) / sd) > 20
-    assert np.array_equal(sample_x_cpu(om, 100, 5), sample_x_cpu(om, 100, 5))
+    # and not the law of X = Z L^-T with Omega0 = L L^T, (L^T L)^-1
+    if graph == "random":
+        L = np.linalg.cholesky(om.toarray())
+        assert np.max(np.abs(S - np.linalg.inv(L.T @ L)) / sd) > 20
 
 
 def test_workload_table():
