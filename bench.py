@@ -189,6 +189,19 @@ def cpu_baseline_run(workload, X_host_cols, p_sample, max_seconds=25.0):
             "seconds": dt, "iterations": res.iterations}
 
 
+def sample_subproblem(w, ps):
+    """X (float64, the workload's storage values) of the leading ps x ps sub-problem of the
+    workload's law: n samples of N(0, B^-1) with B = Omega0's leading ps x ps block (itself
+    diagonally dominant), drawn on the CPU with the workload's seed."""
+    import numpy as np
+
+    from workloads import omega0_for, sample_x_cpu
+
+    om = omega0_for(w)[:ps, :ps]
+    workers = max(1, min(8, os.cpu_count() or 1))
+    return sample_x_cpu(om, w.n, w.seed, workers=workers, chunk=256, x_dtype=w.x_dtype).astype(np.float64)
+
+
 def _oracle_cores():
     try:
         from threadpoolctl import threadpool_info
@@ -454,15 +467,11 @@ def run_reference(args):
         return 0
     import numpy as np
 
-    from workloads import WORKLOADS, omega0_for, round_to_bf16, sample_x_cpu
+    from workloads import WORKLOADS
 
     w = WORKLOADS[args.workload]
     ps = args.cpu_sample_p
-    # the leading principal sub-problem of the workload's law: Omega0's leading block
-    om = omega0_for(w)[:ps, :ps]
-    X = sample_x_cpu(om, w.n, w.seed)
-    if w.x_dtype == "bf16":
-        X = round_to_bf16(X.astype(np.float32)).astype(np.float64)
+    X = sample_subproblem(w, ps)
     vals, secs, its = [], [], []
     for k in range(args.warmup + args.steps):
         r = cpu_baseline_run(w, X, ps)
@@ -709,14 +718,8 @@ def main(argv=None):
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        from workloads import omega0_for, round_to_bf16, sample_x_cpu
-
         ps = min(args.cpu_sample_p, w.p)
-        om0 = omega0_for(w)[:ps, :ps]
-        Xs = sample_x_cpu(om0, w.n, w.seed)
-        if w.x_dtype == "bf16":
-            Xs = round_to_bf16(Xs.astype(np.float32)).astype(np.float64)
-        c = cpu_baseline_run(w, Xs, ps)
+        c = cpu_baseline_run(w, sample_subproblem(w, ps), ps)
         cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:
@@ -727,7 +730,7 @@ def main(argv=None):
             "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if f64 else ("bf16" if (w.x_dtype == "bf16" and tensor_gram) else "f32"),
-            "data": f"synthetic (seeded: {w.graph} SDD Omega0, X = Z L^-T)",
+            "data": f"synthetic (seeded: {w.graph} SDD Omega0, rows of X ~ N(0, Omega0^-1))",
             "config": {"workload": w.name, "p": p, "n": n, "lambda1": w.lambda1, "lambda2": w.lambda2,
                        "eps": w.eps, "x_dtype": w.x_dtype, "s_dtype": "f64" if f64 else "f32",
                        "gram_precision": solver.precision_name(), "parallelism": f"replicas x{ws}",

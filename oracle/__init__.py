@@ -415,3 +415,312 @@ def hypergrad_sparse(X, Xval, omega_csr: sp.csr_matrix, lam1, lam2):
     om_u = np.array([om[i, j] for i, j in U])
     s_u = np.where(np.array([i == j for i, j in U]), 0.0, np.sign(om_u))
     return float(-np.sum(wgt * v * s_u)), float(-np.sum(wgt * v * om_u))
+
+
+# ----------------------------------------------------------------- CSR iterate form (large p)
+#
+# The same Alg. 2 / Alg. 3 with the iterate Omega and every trial Omega+ held as CSR, so
+# that p = 16384 and p = 65536 fit in host memory next to a dense FP64 S.  The steps and
+# their order are those of ``solve`` / ``solve_obs``; three things change only the storage:
+#
+# * W = Omega S (step 3) and G (steps 5-6) are formed in blocks of rows, and G is kept on
+#   K = supp(Omega) + diagonal + {(i, j): |G_ij| > lambda1}.  Outside K an entry of
+#   Omega - tau G is -tau G_ij with |tau G_ij| <= tau lambda1 (tau is a power of two, so
+#   the scaling is exact), which eq. (2) maps to 0 for every tau of the line search; such
+#   entries add nothing to Omega+, to <Omega - Omega+, G> or to ||Omega+ - Omega||^2.
+# * tr(W+ Omega+) in g(Omega+) (steps 10-11) needs W+ = Omega+ S only on supp(Omega+):
+#   W+_ij = sum_k w+_ik S_kj over the row's support.
+# * S = X^T X / n is summed over chunks of observations (the definition's sum over k of
+#   x_k x_k^T), with a symmetric rank-k update per chunk.
+
+def gram_chunked(X, chunk=4096, dtype_in=None) -> np.ndarray:
+    """S = (1/n) sum_k x_k x_k^T in FP64 (Alg. 2 step 2), accumulated over chunks of rows of X.
+
+    Returns a C-ordered, exactly symmetric p x p float64 array."""
+    from scipy.linalg import blas
+
+    n, p = X.shape
+    S = np.zeros((p, p), dtype=np.float64, order="F")
+    for r0 in range(0, n, chunk):
+        Xc = np.asarray(X[r0:r0 + chunk], dtype=np.float64)
+        # C := 1 * A A^T + 1 * C on the upper triangle, A = Xc^T (p x c, Fortran view of Xc)
+        S = blas.dsyrk(1.0, Xc.T, beta=1.0, c=S, trans=0, lower=0, overwrite_c=1)
+    S /= n
+    # mirror the upper triangle, in blocks, then view as C order (symmetric: same values)
+    b = 2048
+    for j0 in range(0, p, b):
+        for i0 in range(j0 + b, p, b):
+            S[i0:i0 + b, j0:j0 + b] = S[j0:j0 + b, i0:i0 + b].T
+        blk = S[j0:j0 + b, j0:j0 + b]
+        S[j0:j0 + b, j0:j0 + b] = np.triu(blk) + np.triu(blk, 1).T
+    return S.T          # S^T = S; the transpose of a Fortran array is C-ordered
+
+
+def _csr_identity(p):
+    I = sp.identity(p, format="csr", dtype=np.float64)
+    I.sort_indices()
+    return I
+
+
+def _blocks(p, block):
+    return [(r0, min(p, r0 + block)) for r0 in range(0, p, block)]
+
+
+def gradient_candidates_cov(S, omega: sp.csr_matrix, lam1, lam2, block=512, threads=8):
+    """Steps 3 and 5-6 of Alg. 2 for a CSR iterate: W = Omega S and
+    G = (W + W^T)/2 + lam2 Omega - diag(1/w_ii), formed in row blocks.
+
+    Returns (Gk, Wsupp): G on K = supp(Omega) + diagonal + {|G_ij| > lam1} as CSR, and
+    W on supp(Omega) as a CSR with Omega's pattern."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    p = S.shape[0]
+    om = omega
+    dinv = 1.0 / om.diagonal()
+
+    def one(rb):
+        r0, r1 = rb
+        WI = np.asarray(om[r0:r1] @ S)                                  # rows r0..r1 of W
+        WtI = np.asarray(om @ np.ascontiguousarray(S[:, r0:r1])).T      # rows r0..r1 of W^T
+        OI = om[r0:r1].toarray()
+        GI = 0.5 * (WtI + WI) + lam2 * OI
+        rr = np.arange(r1 - r0)
+        GI[rr, r0 + rr] -= dinv[r0:r1]
+        keep = (np.abs(GI) > lam1) | (OI != 0.0)
+        keep[rr, r0 + rr] = True
+        i, j = np.nonzero(keep)
+        si, sj = np.nonzero(OI != 0.0)
+        return (i + r0, j, GI[i, j]), (si + r0, sj, WI[si, sj])
+
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(one, _blocks(p, block)))
+    gi = np.concatenate([a[0][0] for a in parts])
+    gj = np.concatenate([a[0][1] for a in parts])
+    gv = np.concatenate([a[0][2] for a in parts])
+    wi = np.concatenate([a[1][0] for a in parts])
+    wj = np.concatenate([a[1][1] for a in parts])
+    wv = np.concatenate([a[1][2] for a in parts])
+    Gk = sp.csr_matrix((gv, (gi, gj)), shape=(p, p))
+    Gk.sort_indices()
+    Wsupp = sp.csr_matrix((wv, (wi, wj)), shape=(p, p))
+    Wsupp.sort_indices()
+    return Gk, Wsupp
+
+
+def w_on_support(S, omega: sp.csr_matrix) -> np.ndarray:
+    """W = Omega S at the entries of supp(Omega), in CSR order: W_ij = sum_k w_ik S_kj over
+    the row's support (step 10, restricted to the entries step 11 reads)."""
+    om = omega
+    L = np.diff(om.indptr)
+    row = np.repeat(np.arange(om.shape[0]), L)
+    rep = L[row]                                   # each entry pairs with every entry of its row
+    u = np.repeat(np.arange(om.nnz), rep)
+    start = np.repeat(np.cumsum(rep) - rep, rep)
+    v = om.indptr[row][u] + (np.arange(u.size) - start)
+    # entry v = (i, j) receives w_ik S_kj from entry u = (i, k)
+    return np.bincount(v, weights=om.data[u] * S[om.indices[u], om.indices[v]], minlength=om.nnz)
+
+
+def smooth_csr(omega: sp.csr_matrix, w_supp, lam2) -> float:
+    """g(Omega) = -sum log w_ii + tr(W Omega)/2 + lam2/2 ||Omega||^2 with W given on supp(Omega)
+    (an array in Omega's CSR order)."""
+    d = omega.diagonal()
+    if np.any(d <= 0.0):
+        return np.inf
+    return -float(np.sum(np.log(d))) + 0.5 * float(np.sum(w_supp * omega.data)) + \
+        0.5 * lam2 * float(np.sum(omega.data * omega.data))
+
+
+def penalty_csr(omega: sp.csr_matrix, lam1) -> float:
+    a = np.abs(omega.data)
+    return lam1 * (float(a.sum()) - float(np.sum(np.abs(omega.diagonal()))))
+
+
+def _on_pattern(A: sp.csr_matrix, pattern: sp.csr_matrix) -> np.ndarray:
+    """Values of A at the entries of ``pattern`` (0 where A has none), in pattern's CSR order."""
+    rows = np.repeat(np.arange(pattern.shape[0]), np.diff(pattern.indptr))
+    return np.asarray(A[rows, pattern.indices]).ravel()
+
+
+def prox_csr(Zk: sp.csr_matrix, alpha) -> sp.csr_matrix:
+    """eq. (2) on the off-diagonal entries of a CSR matrix, diagonal kept; zeros dropped."""
+    rows = np.repeat(np.arange(Zk.shape[0]), np.diff(Zk.indptr))
+    off = rows != Zk.indices
+    v = Zk.data.copy()
+    v[off] = soft_threshold(v[off], alpha)
+    out = sp.csr_matrix((v, Zk.indices.copy(), Zk.indptr.copy()), shape=Zk.shape)
+    out.eliminate_zeros()
+    out.sort_indices()
+    return out
+
+
+@dataclasses.dataclass
+class SparseResult:
+    omega: sp.csr_matrix
+    iterations: int
+    trials: list
+    taus: list
+    F: list
+    rel_change: float
+    status: str
+
+
+def solve_sparse(S, lam1, lam2, eps=1e-6, max_iter=1000, tau0=1.0, shrink=0.5, max_halvings=60,
+                 block=512, threads=8, log=None) -> SparseResult:
+    """Alg. 2 with a CSR iterate: the same steps and the same line-search rule as ``solve``."""
+    p = S.shape[0]
+    Omega = _csr_identity(p)
+    rel = np.inf
+    status = "max_iter"
+    trials, taus, F = [], [], []
+    for it in range(max_iter):
+        Gk, Wsupp = gradient_candidates_cov(S, Omega, lam1, lam2, block, threads)   # steps 3, 5-6
+        g = smooth_csr(Omega, _on_pattern(Wsupp, Omega), lam2)                      # step 7
+        if it == 0:
+            F.append(g + penalty_csr(Omega, lam1))
+        Ok = _on_pattern(Omega, Gk)                # Omega on K (K holds supp(Omega))
+        Gv = Gk.data
+        tau, accepted = tau0, False
+        for h in range(max_halvings + 1):
+            Zk = sp.csr_matrix((Ok - tau * Gv, Gk.indices, Gk.indptr), shape=(p, p))
+            Op = prox_csr(Zk, tau * lam1)                                           # step 9
+            if np.all(Op.diagonal() > 0.0):
+                wp = w_on_support(S, Op)                                            # step 10
+                gp = smooth_csr(Op, wp, lam2)                                       # step 11
+                Dk = _on_pattern(Op, Gk) - Ok
+                # step 12: g(O+) <= g(O) - <O - O+, G> + ||O+ - O||^2 / (2 tau)
+                rhs = g - float(np.sum(-Dk * Gv)) + float(np.sum(Dk * Dk)) / (2.0 * tau)
+                if gp <= rhs:
+                    accepted = True
+                    break
+            tau *= shrink
+        if not accepted:
+            status = "floor" if rel < 1e-8 else "ls_fail"
+            break
+        rel = float(np.sqrt(np.sum(Dk * Dk)) / np.sqrt(np.sum(Omega.data * Omega.data)))
+        Omega = Op
+        trials.append(h + 1)
+        taus.append(tau)
+        F.append(gp + penalty_csr(Omega, lam1))
+        if log:
+            log(f"it {it + 1}: tau {tau:g} trials {h + 1} nnz {Omega.nnz} rel {rel:.3e} F {F[-1]:.12g}")
+        if rel < eps:
+            status = "converged"
+            break
+    return SparseResult(Omega, len(trials), trials, taus, F, rel, status)
+
+
+def kkt_residual_csr(Gk: sp.csr_matrix, omega: sp.csr_matrix, lam1) -> np.ndarray:
+    """The smallest element of the subdifferential of F at Omega, on the entries of K, given G
+    on K (``gradient_candidates_*``): G_ii on the diagonal, G_ij + lam1 sign(w_ij) on the
+    off-diagonal support, max(|G_ij| - lam1, 0) elsewhere (0 outside K, where |G_ij| <= lam1).
+
+    The smooth part is lam2-strongly convex on symmetric matrices, so an estimate with
+    residual r lies within ||r||_F / lam2 of the minimiser in Frobenius norm."""
+    rows = np.repeat(np.arange(Gk.shape[0]), np.diff(Gk.indptr))
+    w = _on_pattern(omega, Gk)
+    g = Gk.data
+    diag = rows == Gk.indices
+    on = (w != 0.0) & ~diag
+    r = np.where(diag, g, np.where(on, g + lam1 * np.sign(w), np.maximum(np.abs(g) - lam1, 0.0)))
+    return r
+
+
+def gradient_candidates_obs(X, Y, omega: sp.csr_matrix, lam1, lam2, block=512):
+    """Steps 4-6 of Alg. 3 for a CSR iterate: Z = Y X / n with Y = Omega X^T, and
+    G = (Z + Z^T)/2 + lam2 Omega - diag(1/w_ii), formed in row blocks; G kept on K as in
+    ``gradient_candidates_cov``.  Returns G on K as CSR."""
+    n, p = X.shape
+    om = omega
+    dinv = 1.0 / om.diagonal()
+    gi, gj, gv = [], [], []
+    for r0, r1 in _blocks(p, block):
+        ZI = (Y[r0:r1] @ X) / n                                     # rows r0..r1 of Z
+        ZtI = ((Y @ np.ascontiguousarray(X[:, r0:r1])) / n).T       # rows r0..r1 of Z^T
+        OI = om[r0:r1].toarray()
+        GI = 0.5 * (ZtI + ZI) + lam2 * OI
+        rr = np.arange(r1 - r0)
+        GI[rr, r0 + rr] -= dinv[r0:r1]
+        keep = (np.abs(GI) > lam1) | (OI != 0.0)
+        keep[rr, r0 + rr] = True
+        i, j = np.nonzero(keep)
+        gi.append(i + r0)
+        gj.append(j)
+        gv.append(GI[i, j])
+    Gk = sp.csr_matrix((np.concatenate(gv), (np.concatenate(gi), np.concatenate(gj))), shape=(p, p))
+    Gk.sort_indices()
+    return Gk
+
+
+def solve_obs_sparse(X, lam1, lam2, eps=1e-6, max_iter=1000, tau0=1.0, shrink=0.5, max_halvings=60,
+                     block=512, log=None) -> SparseResult:
+    """Alg. 3 with a CSR iterate: Y = Omega X^T (steps 2, 10), Z = Y X / n (step 4),
+    g from ||Y||_F^2 / n (steps 7, 11); the line-search rule of ``solve_obs``."""
+    X = np.asarray(X, dtype=np.float64)
+    n, p = X.shape
+    Xt = np.ascontiguousarray(X.T)
+
+    def g_of(Om, Y):
+        d = Om.diagonal()
+        if np.any(d <= 0.0):
+            return np.inf
+        return -float(np.sum(np.log(d))) + 0.5 * float(np.sum(Y * Y)) / n + \
+            0.5 * lam2 * float(np.sum(Om.data * Om.data))
+
+    Omega = _csr_identity(p)
+    Y = np.asarray(Omega @ Xt)                                                  # step 2
+    rel = np.inf
+    status = "max_iter"
+    trials, taus = [], []
+    F = [g_of(Omega, Y) + penalty_csr(Omega, lam1)]
+    for it in range(max_iter):
+        Gk = gradient_candidates_obs(X, Y, Omega, lam1, lam2, block)            # steps 4-6
+        g = g_of(Omega, Y)                                                      # step 7
+        Ok = _on_pattern(Omega, Gk)
+        Gv = Gk.data
+        tau, accepted = tau0, False
+        for h in range(max_halvings + 1):
+            Zk = sp.csr_matrix((Ok - tau * Gv, Gk.indices, Gk.indptr), shape=(p, p))
+            Op = prox_csr(Zk, tau * lam1)                                       # step 9
+            if np.all(Op.diagonal() > 0.0):
+                Yp = np.asarray(Op @ Xt)                                        # step 10
+                gp = g_of(Op, Yp)                                               # step 11
+                Dk = _on_pattern(Op, Gk) - Ok
+                rhs = g - float(np.sum(-Dk * Gv)) + float(np.sum(Dk * Dk)) / (2.0 * tau)
+                if gp <= rhs:
+                    accepted = True
+                    break
+            tau *= shrink
+        if not accepted:
+            status = "floor" if rel < 1e-8 else "ls_fail"
+            break
+        rel = float(np.sqrt(np.sum(Dk * Dk)) / np.sqrt(np.sum(Omega.data * Omega.data)))
+        Omega, Y = Op, Yp
+        trials.append(h + 1)
+        taus.append(tau)
+        F.append(gp + penalty_csr(Omega, lam1))
+        if log:
+            log(f"it {it + 1}: tau {tau:g} trials {h + 1} nnz {Omega.nnz} rel {rel:.3e} F {F[-1]:.12g}")
+        if rel < eps:
+            status = "converged"
+            break
+    return SparseResult(Omega, len(trials), trials, taus, F, rel, status)
+
+
+def objective_from_x(X, omega: sp.csr_matrix, lam1, lam2, chunk=4096) -> float:
+    """F(Omega) = -sum log w_ii + ||X Omega||_F^2 / (2n) + lam2/2 ||Omega||_F^2 + lam1 ||Omega_X||_1
+    in FP64 for a sparse symmetric Omega, with tr(Omega S Omega) = ||X Omega||_F^2 / n as in
+    Alg. 3 step 7, summed over chunks of observations (rows of X)."""
+    n = X.shape[0]
+    om = sp.csr_matrix(omega, dtype=np.float64)
+    d = om.diagonal()
+    if np.any(d <= 0.0):
+        return np.inf
+    omt = om.T.tocsr()
+    q = 0.0
+    for r0 in range(0, n, chunk):
+        Xc = np.asarray(X[r0:r0 + chunk], dtype=np.float64)
+        Yc = np.asarray(omt @ Xc.T)              # (X Omega)^T for these rows
+        q += float(np.sum(Yc * Yc))
+    return -float(np.sum(np.log(d))) + 0.5 * q / n + 0.5 * lam2 * float(np.sum(om.data ** 2)) + \
+        penalty_csr(om, lam1)

@@ -318,28 +318,28 @@ def _rows_numpy(f: SampleFactor, seed: int, rows: np.ndarray, stream: int) -> np
 
 
 def _rows_worker(args):
-    om, seed, r0, r1, stream = args
+    om, seed, r0, r1, stream, x_dtype = args
     f = sample_factor(om)
-    return r0, _rows_numpy(f, seed, np.arange(r0, r1, dtype=np.int64), stream)
+    return r0, cast_x(_rows_numpy(f, seed, np.arange(r0, r1, dtype=np.int64), stream), x_dtype)
 
 
 def sample_x_cpu(omega0: sp.csr_matrix, n: int, seed: int, stream: int = 0, workers: int = 1,
-                 chunk: int = 64, out_dtype=np.float64) -> np.ndarray:
+                 chunk: int = 64, x_dtype: str = "f64") -> np.ndarray:
     """n samples of N(0, Omega0^-1) as the rows of an n x p array, on the CPU.
 
-    Row s is a pure function of (Omega0, seed, stream, s), computed in FP64 and stored
-    as ``out_dtype``.  ``workers`` > 1 spreads the rows over processes started with
-    spawn; the result does not depend on it."""
+    Row s is a pure function of (Omega0, seed, stream, s), computed in FP64 and stored in
+    the storage type ``x_dtype`` (cast_x).  ``workers`` > 1 spreads the rows over
+    processes started with spawn; the result does not depend on it."""
     f = sample_factor(omega0)
-    out = np.empty((n, f.p), dtype=out_dtype)
+    out = np.empty((n, f.p), dtype=np.float64 if x_dtype == "f64" else np.float32)
     if workers <= 1 or n <= chunk:
         for r0 in range(0, n, chunk):
             r1 = min(n, r0 + chunk)
-            out[r0:r1] = _rows_numpy(f, seed, np.arange(r0, r1, dtype=np.int64), stream)
+            out[r0:r1] = cast_x(_rows_numpy(f, seed, np.arange(r0, r1, dtype=np.int64), stream), x_dtype)
         return out
     import multiprocessing as mp
 
-    jobs = [(f.omega, seed, r0, min(n, r0 + chunk), stream) for r0 in range(0, n, chunk)]
+    jobs = [(f.omega, seed, r0, min(n, r0 + chunk), stream, x_dtype) for r0 in range(0, n, chunk)]
     with mp.get_context("spawn").Pool(workers) as pool:
         for r0, rows in pool.imap_unordered(_rows_worker, jobs):
             out[r0:r0 + rows.shape[0]] = rows
@@ -428,7 +428,7 @@ def make_x(w: Workload, device: str = "cpu", workers: int = 1, stream: int = 0):
     values as float32) or a torch tensor on a CUDA device."""
     om = omega0_for(w)
     if device == "cpu":
-        return cast_x(sample_x_cpu(om, w.n, w.seed, stream=stream, workers=workers), w.x_dtype)
+        return sample_x_cpu(om, w.n, w.seed, stream=stream, workers=workers, x_dtype=w.x_dtype)
     x = sample_x_cuda(om, w.n, w.seed, stream=stream, device=device)
     out = cast_x(x, w.x_dtype)
     del x
