@@ -373,7 +373,8 @@ int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* 
  * The line-search grid (ls_blocks_per_sm) regroups the FP64 partial sums of the
  * sufficient-decrease test, which can move their last bits; a step changes only
  * if that decides an exact tie.  The paper tunes its replication factors and grid
- * shapes per machine (Section 4); these are the single-GPU counterparts. */
+ * shapes per machine (Section 4); these are the single-GPU counterparts.
+ * gram_chunk is the exception: it sets how the Gram's FP32 sums are grouped. */
 typedef struct {
     int32_t gram_band;         /* row blocks of 128 per band of the tensor-core Gram's
                                   tile order, 1..256 (16): sets which X panels the
@@ -393,6 +394,21 @@ typedef struct {
                                   CTAs from a shared counter (the tiles in flight stay
                                   together in the band order); 0, CTA g takes tiles g,
                                   g + grid, ... (1)                                 */
+    int32_t gram_chunk;        /* K elements per accumulation chunk of the tensor-core
+                                  Gram (and of the Obs Z product), rounded down to a
+                                  stage (64 K for BF16 operands, 32 for TF32): each
+                                  chunk starts from a zero accumulator and the chunk
+                                  sums are added in FP32 round-to-nearest.  Shorter
+                                  chunks shrink the bias of the tensor core's
+                                  truncating accumulation.  0 = the default (512 for
+                                  BF16 X, 256 for BF16X3 and TF32); a value >= n is
+                                  one chunk per tile.  It changes S's last bits, so
+                                  the autotuner does not touch it (0)               */
+    int32_t gram_lead;         /* K elements of each tile's (each Obs pair's) first two
+                                  chunks, which keep the tensor core busy while the
+                                  epilogue stores the previous tile (emits the previous
+                                  pair); 0 = 2 gram_chunk (Gram), 4 gram_chunk (Obs).
+                                  Like gram_chunk it groups S's sums: not tuned (0)  */
 } hpc_tuning;
 
 /* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max

@@ -430,30 +430,27 @@ def hypergrad_sparse(X, Xval, omega_csr: sp.csr_matrix, lam1, lam2):
 #   entries add nothing to Omega+, to <Omega - Omega+, G> or to ||Omega+ - Omega||^2.
 # * tr(W+ Omega+) in g(Omega+) (steps 10-11) needs W+ = Omega+ S only on supp(Omega+):
 #   W+_ij = sum_k w+_ik S_kj over the row's support.
-# * S = X^T X / n is summed over chunks of observations (the definition's sum over k of
-#   x_k x_k^T), with a symmetric rank-k update per chunk.
+# * S = X^T X / n is formed one block of columns at a time (S[I, J] = X_I^T X_J / n, the
+#   upper blocks, mirrored).
 
-def gram_chunked(X, chunk=4096, dtype_in=None) -> np.ndarray:
-    """S = (1/n) sum_k x_k x_k^T in FP64 (Alg. 2 step 2), accumulated over chunks of rows of X.
-
-    Returns a C-ordered, exactly symmetric p x p float64 array."""
-    from scipy.linalg import blas
-
+def gram_chunked(X, block=4096) -> np.ndarray:
+    """S = X^T X / n in FP64 (Alg. 2 step 2), one block of columns at a time: S[I, J] = X_I^T X_J / n
+    for the blocks I <= J, mirrored to S[J, I]; each diagonal block is made exactly symmetric
+    from its upper triangle.  X may be float32 (converted block by block).  Returns a C-ordered
+    p x p float64 array."""
     n, p = X.shape
-    S = np.zeros((p, p), dtype=np.float64, order="F")
-    for r0 in range(0, n, chunk):
-        Xc = np.asarray(X[r0:r0 + chunk], dtype=np.float64)
-        # C := 1 * A A^T + 1 * C on the upper triangle, A = Xc^T (p x c, Fortran view of Xc)
-        S = blas.dsyrk(1.0, Xc.T, beta=1.0, c=S, trans=0, lower=0, overwrite_c=1)
-    S /= n
-    # mirror the upper triangle, in blocks, then view as C order (symmetric: same values)
-    b = 2048
-    for j0 in range(0, p, b):
-        for i0 in range(j0 + b, p, b):
-            S[i0:i0 + b, j0:j0 + b] = S[j0:j0 + b, i0:i0 + b].T
-        blk = S[j0:j0 + b, j0:j0 + b]
-        S[j0:j0 + b, j0:j0 + b] = np.triu(blk) + np.triu(blk, 1).T
-    return S.T          # S^T = S; the transpose of a Fortran array is C-ordered
+    S = np.empty((p, p), dtype=np.float64)
+    for j0 in range(0, p, block):
+        XJ = np.asarray(X[:, j0:j0 + block], dtype=np.float64)
+        for i0 in range(0, j0 + 1, block):
+            XI = XJ if i0 == j0 else np.asarray(X[:, i0:i0 + block], dtype=np.float64)
+            B = (XI.T @ XJ) / n
+            if i0 == j0:
+                S[j0:j0 + block, j0:j0 + block] = np.triu(B) + np.triu(B, 1).T
+            else:
+                S[i0:i0 + block, j0:j0 + block] = B
+                S[j0:j0 + block, i0:i0 + block] = B.T
+    return S
 
 
 def _csr_identity(p):

@@ -124,7 +124,8 @@ struct hpc_ctx {
     double ms_gram = 0.0;
     double ms_gram_kernel = 0.0;
     cudaEvent_t ev_gk = nullptr;     // between the transpose and the tensor-core product
-    cudaEvent_t ev_ge = nullptr;     // end of the product (before the block-maxima pass)
+    cudaEvent_t ev_ge = nullptr;     // end of the Gram (before the block-maxima pass)
+    cudaEvent_t ev_gp = nullptr;     // end of the tensor-core product (before its mirror pass)
     // device staging buffer for X passed from the host (kept between loads)
     void* x_stage = nullptr;
     size_t x_stage_bytes = 0;
@@ -146,7 +147,7 @@ struct hpc_ctx {
     const void* pf_ptr = nullptr;
     int pf_xdt = -1;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{16, 8, 0, 2, 1, 1, 1};
+    hpc_tuning tune{16, 8, 0, 2, 1, 1, 1, 0, 0};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -332,7 +333,7 @@ int obs_screen(hpc_ctx* h, const hpc::IterBufs<float>& b, cudaStream_t s) {
     hpc::launch_spmm_dense<float>(p, b.cur, h->rinfo, as<float>(h->rdv), h->xt, h->ldx, h->ldx, h->yt, h->ldx, s);
     hpc::launch_obs_split(h->precision, h->yt, p, h->ldx, h->ldx, h->yp[0], h->yp[1], h->n, h->p, s);
     cudaError_t e = hpc::launch_obs_pairs(h->precision, h->obs_maps, h->pairs, h->npairs, h->n, p, b.cur.rp, b.cur.ci,
-                                          b.cur.cv, b.em, h->d_ctrl, s);
+                                          b.cur.cv, b.em, h->d_ctrl, s, h->tune.gram_chunk, h->tune.gram_lead);
     if (e != cudaSuccess) { set_cuda_error(e, "obs pair GEMM", __LINE__); return HPC_ERR_CUDA; }
     return HPC_OK;
 }
@@ -911,7 +912,8 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
                          h->gram_scratch_bytes, h->stream, &launches, h->tune.gram_band,
                          h->opt.timing ? h->ev_gk : nullptr,
                          h->tune.gram_maxima ? static_cast<uint16_t*>(h->m1) : nullptr, h->nbm, prepared ? 1 : 0,
-                         &h->tiles_sig, h->tune.gram_schedule);
+                         &h->tiles_sig, h->tune.gram_schedule, h->tune.gram_chunk, h->tune.gram_lead,
+                         h->opt.timing ? h->ev_gp : nullptr);
         if (e == cudaErrorNotSupported) {
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
             return HPC_ERR_NOT_IMPLEMENTED;
@@ -961,7 +963,7 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         h->ms_gram = ms;
         const bool tc = h->variant == HPC_COV && (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32);
         float mk = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&mk, tc ? h->ev_gk : h->ev[2], h->ev_ge));
+        CUDA_TRY(cudaEventElapsedTime(&mk, tc ? h->ev_gk : h->ev[2], tc ? h->ev_gp : h->ev_ge));
         h->ms_gram_kernel = mk;
     }
 
@@ -1005,6 +1007,7 @@ void destroy(hpc_ctx* h) {
     if (h->ev_scr0) cudaEventDestroy(h->ev_scr0);
     if (h->ev_gk) cudaEventDestroy(h->ev_gk);
     if (h->ev_ge) cudaEventDestroy(h->ev_ge);
+    if (h->ev_gp) cudaEventDestroy(h->ev_gp);
     if (h->ev_scr1) cudaEventDestroy(h->ev_scr1);
     delete h;
 }
@@ -1185,6 +1188,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     CK(cudaEventCreate(&h->ev_scr0));
     CK(cudaEventCreate(&h->ev_gk));
     CK(cudaEventCreate(&h->ev_ge));
+    CK(cudaEventCreate(&h->ev_gp));
     CK(cudaEventCreate(&h->ev_scr1));
 #undef CK
     if (X) {
@@ -1831,7 +1835,8 @@ bool tuning_ok(const hpc_tuning& t) {
     return t.gram_band >= 1 && t.gram_band <= 256 && (w == 1 || w == 2 || w == 4 || w == 8 || w == 16) &&
            t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4 &&
            (t.gram_maxima == 0 || t.gram_maxima == 1) && (t.screen_bounds == 0 || t.screen_bounds == 1) &&
-           (t.gram_schedule == 0 || t.gram_schedule == 1);
+           (t.gram_schedule == 0 || t.gram_schedule == 1) && t.gram_chunk >= 0 &&
+           t.gram_lead >= 0;
 }
 
 void apply_tuning(hpc_ctx* h, const hpc_tuning& t) {

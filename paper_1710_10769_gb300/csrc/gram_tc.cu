@@ -150,6 +150,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr)
         : "memory");
 }
+// 32 TMEM lanes x 16 consecutive 32-bit columns: thread t gets lane (base + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor (tcgen05 format): K-major, 128-byte swizzle,
@@ -185,7 +195,7 @@ struct Cfg {
     static constexpr int kStageBytes = kPieces * (kABytes + kBBytes);
     static constexpr int kStages = (MODE == kModeBf16x3) ? 2 : 4;
     static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers and flags*/
-                                 + kBN * 4 /*column maxima of the persistent epilogue*/;
+                                 + 8 * 32 * 17 * 4 /*per-warp staging of the row stores*/;
 };
 
 // Non-negative float rounded up to BF16 (an upper bound).
@@ -202,18 +212,44 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
 // Persistent form: one CTA per SM walks the banded order of the tile list, so the
 // tiles running together share X panels in L2.  Dynamic: the CTAs take tiles from a
 // counter they share, so the tiles in flight stay a contiguous window of the order
-// however the CTAs drift; static: CTA g takes tiles g, g + grid, ...  Roles:
+// however the CTAs drift; static: CTA g takes tiles g, g + grid, ...
+//
+// Chunked accumulation.  The tensor core adds each MMA's K slice into the FP32
+// accumulator with truncation, so a sum over the whole K = n carries a bias that
+// grows with the number of MMAs chained into one accumulator (about -1.4e-4
+// relative on S_ii at n = 32768).  The K loop of a tile is therefore cut into
+// chunks (chunk_start): each chunk starts from a zero accumulator, and the epilogue
+// adds the chunk sums in FP32 with round-to-nearest, in chunk order, in registers.
+// The bias then scales with the chunk lengths instead of n (the sum over chunks of
+// length^2 / K).  A chunk longer than K gives one chunk per tile.
+//
+// Roles:
 //   warp 0      TMA producer: takes the next tile, publishes its index in a ring of
 //               kTileRing slots (tid_full / tid_empty), loads its K slices ahead;
-//   warp 1      MMA issuer, the CTA's tile t into TMEM accumulator t & 1 (columns
-//               0 / 256);
-//   warps 2-5   epilogue of tile t while tile t + 1 accumulates in the other
-//               buffer; warp w reads TMEM lanes 32 (w % 4) .. +31.
-// acc_full[b] (one commit) and acc_empty[b] (four epilogue warps) hand the
+//   warp 1      MMA issuer: chunk c of the CTA's sequence into TMEM accumulator
+//               c & 1 (columns 0 / 256), so a chunk accumulates while the previous
+//               one is read out;
+//   warps 2-3   idle (they complete warpgroup 0, which hands registers to the
+//               epilogue with setmaxnreg);
+//   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and the column
+//               half (w - 4) / 4 of the tile (128 columns), keeps the running
+//               sums of its row's 128 columns in registers, and after a tile's last
+//               chunk scales by 1/n and stores the tile, its mirror and the block
+//               maxima.
+// acc_full[b] (one commit) and acc_empty[b] (eight epilogue warps) hand the
 // buffers over.  Every wait is bounded; an abort stops all roles, drains the
 // loads in flight and frees TMEM.
-constexpr int kPersistThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kPersistThreads = 128 + 32 * kEpiWarps;     // warpgroup 0: roles; warpgroups 1-2: epilogue
+// Registers per thread after setmaxnreg: warpgroup 0 gives down to kRegsSmall, the two
+// epilogue warpgroups take up to kRegsEpi.  The launch's pool (threads x registers per
+// thread at launch) must cover both, which the host checks before the first launch
+// (kMinLaunchRegs), so that the increase never waits for registers that do not exist.
+constexpr int kRegsSmall = 56;
+constexpr int kRegsEpi = 216;
+constexpr int kMinLaunchRegs = (128 * kRegsSmall + 32 * kEpiWarps * kRegsEpi + kPersistThreads - 1) / kPersistThreads;
 constexpr int kTileRing = 4;
+constexpr int kHalf = kBN / 2;          // columns per epilogue warp
 
 // The tile counter of k_gram_tc_persist, reset before each launch (a kernel, so the
 // reset is not queued behind copies on a copy engine).
@@ -223,8 +259,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                   const int2* __restrict__ tiles, int ntiles, int k_tiles, int64_t p, int64_t n,
-                  float* __restrict__ S, int64_t lds, int vec_ok, uint16_t* __restrict__ m1, int nbm,
-                  unsigned* __restrict__ tile_ctr, int dynamic) {
+                  float* __restrict__ S, int64_t lds, unsigned* __restrict__ tile_ctr, int dynamic, int chunk_kt,
+                  int lead_kt) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -238,14 +274,17 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* s_tid = reinterpret_cast<volatile int*>(tmem_slot + 2);      // [kTileRing]
     volatile int* s_epi = s_tid + kTileRing;                                    // [2]
-    unsigned* s_colmax = reinterpret_cast<unsigned*>(smem + C::kStages * C::kStageBytes + 256);   // [kBN]
+    float* s_stage = reinterpret_cast<float*>(smem + C::kStages * C::kStageBytes + 256);   // [kEpiWarps][32][17]
     static_assert(8 * (2 * C::kStages + 4 + 2 * kTileRing) + 4 * (2 + kTileRing + 2) <= 256, "barrier area");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (chunk_kt < 1) chunk_kt = 1;
+    if (lead_kt < chunk_kt) lead_kt = chunk_kt;
+    const int nch = num_chunks(k_tiles, chunk_kt, lead_kt);     // chunks per tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], 4); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&acc_full[b], 1); mbar_init(&acc_empty[b], kEpiWarps); }
         for (int r = 0; r < kTileRing; ++r) { mbar_init(&tid_full[r], 1); mbar_init(&tid_empty[r], 2); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -262,100 +301,104 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
     const uint32_t tmem = *tmem_slot;
 
     long long issued = 0;   // stages whose TMA loads were issued (producer thread)
-    if (threadIdx.x == 0) {
-        // ---------------- TMA producer
-        long long g = 0;
-        bool ok = true;
-        for (int lt = 0; ok; ++lt) {
-            // the next tile of the shared order, published to the MMA and epilogue roles
-            const int slot = lt % kTileRing;
-            if (!mbar_wait(&tid_empty[slot], ((uint32_t)(lt / kTileRing) & 1u) ^ 1u, abort_flag, 15)) break;
-            // dynamic: the counter shared by the CTAs; static: tiles blockIdx.x + lt * grid
-            const unsigned t = dynamic ? atomicAdd(tile_ctr, 1u)
-                                       : (unsigned)blockIdx.x + (unsigned)lt * (unsigned)gridDim.x;
-            const int tt = t < (unsigned)ntiles ? (int)t : -1;
-            s_tid[slot] = tt;
-            mbar_arrive_local(&tid_full[slot]);
-            if (tt < 0) break;
-            const int2 tile = tiles[tt];
-            const int I0 = tile.x * kBM, J0 = tile.y * kBN;
-            for (int kt = 0; kt < k_tiles; ++kt, ++g) {
-                const int s = (int)(g % C::kStages);
-                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 11)) { ok = false; break; }
-                uint8_t* st = smem + s * C::kStageBytes;
-                mbar_expect_tx(&full[s], C::kStageBytes);
-                const int kc = kt * C::kBK;
-                for (int pc = 0; pc < C::kPieces; ++pc) {
-                    const CUtensorMap* m = pc == 0 ? &map_hi : &map_lo;
-                    uint8_t* a = st + pc * (kABytes + kBBytes);
-                    uint8_t* b = a + kABytes;
-                    tma_load_2d(a, m, &full[s], kc, I0);
-                    tma_load_2d(b, m, &full[s], kc, J0);
-                    tma_load_2d(b + kABytes, m, &full[s], kc, J0 + kBM);
-                }
-                ++issued;
-            }
-        }
-    } else if (threadIdx.x == 32) {
-        // ---------------- MMA issuer
-        constexpr uint32_t idesc = instr_desc<MODE>();
-        long long g = 0;
-        bool ok = true;
-        for (int lt = 0; ok; ++lt) {
-            const int slot = lt % kTileRing;
-            if (!mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 16)) break;
-            const int tt = s_tid[slot];
-            mbar_arrive_local(&tid_empty[slot]);
-            if (tt < 0) break;
-            const int b = lt & 1;
-            if (!mbar_wait(&acc_empty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u, abort_flag, 12)) break;
-            tc_fence_after();
-            const uint32_t acc = tmem + (uint32_t)(b * kTmemCols);
-            for (int kt = 0; kt < k_tiles; ++kt, ++g) {
-                const int s = (int)(g % C::kStages);
-                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
-                if (!mbar_wait(&full[s], ph, abort_flag, 13)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t st = smem_u32(smem + s * C::kStageBytes);
-                const uint32_t a_hi = st, b_hi = st + kABytes;
-                const uint32_t a_lo = st + (kABytes + kBBytes), b_lo = a_lo + kABytes;
-#pragma unroll
-                for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
-                    const uint32_t off = kk * 32;
-                    const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-                    umma<MODE>(acc, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
-                    if constexpr (C::kTerms == 3) {
-                        umma<MODE>(acc, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
-                        umma<MODE>(acc, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+    if (warp < 4) {
+        // producer, MMA issuer and two idle warps: one warpgroup that gives registers away
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsSmall));
+        if (threadIdx.x == 0) {
+            // ---------------- TMA producer
+            long long g = 0;
+            bool ok = true;
+            for (int lt = 0; ok; ++lt) {
+                // the next tile of the shared order, published to the MMA and epilogue roles
+                const int slot = lt % kTileRing;
+                if (!mbar_wait(&tid_empty[slot], ((uint32_t)(lt / kTileRing) & 1u) ^ 1u, abort_flag, 15)) break;
+                // dynamic: the counter shared by the CTAs; static: tiles blockIdx.x + lt * grid
+                const unsigned t = dynamic ? atomicAdd(tile_ctr, 1u)
+                                           : (unsigned)blockIdx.x + (unsigned)lt * (unsigned)gridDim.x;
+                const int tt = t < (unsigned)ntiles ? (int)t : -1;
+                s_tid[slot] = tt;
+                mbar_arrive_local(&tid_full[slot]);
+                if (tt < 0) break;
+                const int2 tile = tiles[tt];
+                const int I0 = tile.x * kBM, J0 = tile.y * kBN;
+                for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+                    const int s = (int)(g % C::kStages);
+                    const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 11)) { ok = false; break; }
+                    uint8_t* st = smem + s * C::kStageBytes;
+                    mbar_expect_tx(&full[s], C::kStageBytes);
+                    const int kc = kt * C::kBK;
+                    for (int pc = 0; pc < C::kPieces; ++pc) {
+                        const CUtensorMap* m = pc == 0 ? &map_hi : &map_lo;
+                        uint8_t* a = st + pc * (kABytes + kBBytes);
+                        uint8_t* b = a + kABytes;
+                        tma_load_2d(a, m, &full[s], kc, I0);
+                        tma_load_2d(b, m, &full[s], kc, J0);
+                        tma_load_2d(b + kABytes, m, &full[s], kc, J0 + kBM);
                     }
+                    ++issued;
                 }
-                umma_commit(&empty[s]);
             }
-            umma_commit(&acc_full[b]);
+        } else if (threadIdx.x == 32) {
+            // ---------------- MMA issuer: chunk after chunk, alternating the two accumulators
+            constexpr uint32_t idesc = instr_desc<MODE>();
+            long long g = 0, gc = 0;
+            bool ok = true;
+            for (int lt = 0; ok; ++lt) {
+                const int slot = lt % kTileRing;
+                if (!mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 16)) break;
+                const int tt = s_tid[slot];
+                mbar_arrive_local(&tid_empty[slot]);
+                if (tt < 0) break;
+                for (int c = 0; c < nch && ok; ++c, ++gc) {
+                    const int b = (int)(gc & 1);
+                    if (!mbar_wait(&acc_empty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abort_flag, 12)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t acc = tmem + (uint32_t)(b * kTmemCols);
+                    const int kt0 = chunk_start(c, k_tiles, chunk_kt, lead_kt);
+                    const int kt1 = chunk_start(c + 1, k_tiles, chunk_kt, lead_kt);
+                    for (int kt = kt0; kt < kt1; ++kt, ++g) {
+                        const int s = (int)(g % C::kStages);
+                        const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                        if (!mbar_wait(&full[s], ph, abort_flag, 13)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+                        const uint32_t a_hi = st, b_hi = st + kABytes;
+                        const uint32_t a_lo = st + (kABytes + kBBytes), b_lo = a_lo + kABytes;
+    #pragma unroll
+                        for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
+                            const uint32_t off = kk * 32;
+                            const uint32_t acc0 = (kt > kt0 || kk > 0) ? 1u : 0u;
+                            umma<MODE>(acc, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
+                            if constexpr (C::kTerms == 3) {
+                                umma<MODE>(acc, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+                                umma<MODE>(acc, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+                            }
+                        }
+                        umma_commit(&empty[s]);
+                    }
+                    if (ok) umma_commit(&acc_full[b]);
+                }
+            }
         }
-    } else if (warp >= 2) {
-        // ---------------- epilogue: TMEM -> registers -> S (owner rule i <= j, plus mirror)
-        // and, with m1, the block maxima max |S_ij| (128-column blocks, j != i, BF16
-        // rounded up): row maxima for the tile's own row blocks at or right of the
-        // diagonal (this tile holds all 128 columns of them, the diagonal block's
-        // lower part included), column maxima (over the tile's 128 rows, all above j)
-        // for the rows j whose block lies right of the tile's row block.
-        const float dn = (float)n;
+    } else {
+        // the epilogue warpgroups take them: the running sums of 128 columns live in registers
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
+        // ---------------- epilogue: chunk sums -> registers; after a tile's last chunk, the
+        // scaled sums S_ij with i <= j (the owner rule; the lower triangle is written by
+        // the mirror pass that follows the kernel)
+        const float inv_n = 1.0f / (float)n;
         const int q4 = warp & 3;
-        const int r = q4 * 32 + lane;
-        const int et = threadIdx.x - 64;                    // 0..127 over the epilogue warps
+        const int hc = (warp - 4) >> 2;                     // column half of the tile
+        const int et = threadIdx.x - 128;                   // 0..255 over the epilogue warps
+        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(hc * kHalf);
+        float* stg = s_stage + (warp - 4) * 32 * 17;
         // After an abort a warp keeps walking its tiles (every wait then fails at once)
-        // without touching TMEM or memory, so the four epilogue warps always meet at
-        // the named barrier the same number of times.  Column maxima: cleared once
-        // here, accumulated per tile, read after the first barrier of the tile and
-        // cleared again by their readers before the second.
-        if (m1) {
-            for (int c = et; c < kBN; c += 128) s_colmax[c] = 0u;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
+        // without touching TMEM or memory, so the eight epilogue warps always meet at
+        // the named barrier the same number of times.
+        long long gc = 0;
         for (int lt = 0;; ++lt) {
-            // the round's tile: one thread takes it from the ring, all four warps read it
+            // the round's tile: one thread takes it from the ring, all eight warps read it
             // after the barrier (double-buffered, so the next round's write cannot race
             // this round's reads); -1 (no tile left, or an abort) ends every warp's loop
             // at the same round
@@ -368,116 +411,56 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
                 }
                 s_epi[lt & 1] = tt;
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
             const int tt = s_epi[lt & 1];
             if (tt < 0) break;
-            const int b = lt & 1;
-            bool have = !*abort_flag && mbar_wait(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, 14);
-            have = __all_sync(kFull, have);
-            if (!have) {
-                if (m1) {
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
+            float acc[kHalf];
+#pragma unroll
+            for (int q = 0; q < kHalf; ++q) acc[q] = 0.f;
+            bool have = true;
+            for (int c = 0; c < nch; ++c, ++gc) {
+                const int b = (int)(gc & 1);
+                bool got = have && !*abort_flag &&
+                           mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u, abort_flag, 14);
+                got = __all_sync(kFull, got);
+                if (!got) { have = false; continue; }
+                tc_fence_after();
+#pragma unroll
+                for (int s4 = 0; s4 < kHalf / 16; ++s4) {
+                    uint32_t v[16];
+                    tmem_ld16(lane_base + (uint32_t)(b * kTmemCols + s4 * 16), v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[s4 * 16 + q] += __uint_as_float(v[q]);
                 }
-                continue;
+                // this warp's lanes of buffer b are read: hand the buffer back
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_local(&acc_empty[b]);
             }
-            tc_fence_after();
+            if (!have) continue;
             const int2 tile = tiles[tt];
-            const int I0 = tile.x * kBM, J0 = tile.y * kBN;
-            const int64_t i = I0 + r;
-            const int ib = I0 / 128;                       // the tile's row block in 128-column units
-            float rmax[kBN / 128];
-            bool rnan[kBN / 128];
+            const int I0 = tile.x * kBM, J0 = tile.y * kBN + hc * kHalf;   // this warp's columns
+            // 16 columns at a time, staged through this warp's shared buffer so that each
+            // store covers two rows x 64 contiguous bytes (a lane per row would write 32
+            // rows x 16 bytes per instruction)
+            const int ri0 = I0 + q4 * 32 + (lane >> 4);            // store row for k = 0
+            const int ci = lane & 15;                              // store column in the piece
 #pragma unroll
-            for (int h = 0; h < kBN / 128; ++h) { rmax[h] = 0.f; rnan[h] = false; }
-#pragma unroll 1
-            for (int c0 = 0; c0 < kBN; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kTmemCols + c0), v);
-                tmem_ld_wait();
-                const int64_t jb = J0 + c0;
-                float o[32];
+            for (int s16 = 0; s16 < kHalf / 16; ++s16) {
+                const int c0 = s16 * 16;
+                __syncwarp();
 #pragma unroll
-                for (int q = 0; q < 32; ++q) o[q] = __uint_as_float(v[q]) / dn;
-                if (m1) {
-                    const int h = c0 / 128;
-                    const int cb = (int)(jb / 128);        // this chunk's 128-column block
-                    if (i < p && cb >= ib) {
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            const int64_t j = jb + q;
-                            if (j < p && j != i) {
-                                const float a = fabsf(o[q]);
-                                rnan[h] |= !(a == a);
-                                rmax[h] = a > rmax[h] ? a : rmax[h];
-                            }
-                        }
-                    }
-                    if (cb > ib) {
-                        // max over the tile's rows of column jb + q: reduce-scatter, lane q keeps column q
-                        float a[32];
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            const float x = (i < p) ? fabsf(o[q]) : 0.f;
-                            a[q] = (x == x) ? x : __int_as_float(0x7fc00000);
-                        }
-#pragma unroll
-                        for (int w = 16; w >= 1; w >>= 1) {
-                            const bool upper = (lane & w) != 0;
-#pragma unroll
-                            for (int q = 0; q < w; ++q) {
-                                const float mine = upper ? a[q + w] : a[q];
-                                const float send = upper ? a[q] : a[q + w];
-                                const float got = __shfl_xor_sync(kFull, send, w);
-                                a[q] = (mine != mine || got != got) ? __int_as_float(0x7fc00000)
-                                                                   : (mine > got ? mine : got);
-                            }
-                        }
-                        // lane l now holds the warp's maximum of column jb + l
-                        const float x = a[0];
-                        atomicMax(&s_colmax[c0 + lane], (x != x) ? 0x7fc00000u : __float_as_uint(x));
-                    }
-                }
-                if (i >= p) continue;
-                if (vec_ok && jb >= i && jb + 31 < p) {
-                    float4* dst = reinterpret_cast<float4*>(S + i * lds + jb);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int64_t j = jb + q;
-                        if (j >= i && j < p) S[i * lds + j] = o[q];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int64_t j = jb + q;
-                    if (j > i && j < p) S[j * lds + i] = o[q];
+                for (int q = 0; q < 16; ++q) stg[lane * 17 + q] = __fmul_rn(acc[c0 + q], inv_n);
+                __syncwarp();
+                const int cj = J0 + c0 + ci;
+                float* dst = S + (int64_t)ri0 * lds + cj;
+#pragma unroll 4
+                for (int k = 0; k < 16; ++k) {
+                    const int ri = ri0 + 2 * k;
+                    if (ri < p && cj < p && cj >= ri) dst[(int64_t)(2 * k) * lds] = stg[(2 * k + (lane >> 4)) * 17 + ci];
                 }
             }
-            if (m1) {
-#pragma unroll
-                for (int h = 0; h < kBN / 128; ++h) {
-                    const int cb = J0 / 128 + h;
-                    if (i < p && cb >= ib && cb < nbm)
-                        m1[i * nbm + cb] = rnan[h] ? (uint16_t)0x7fc0 : bf16_up_f(rmax[h]);
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                for (int c = et; c < kBN; c += 128) {
-                    const int64_t j = J0 + c;
-                    if (j < p && (int)(j / 128) > ib) {
-                        const float x = __uint_as_float(s_colmax[c]);
-                        m1[j * nbm + ib] = (x != x) ? (uint16_t)0x7fc0 : bf16_up_f(x);
-                    }
-                    s_colmax[c] = 0u;
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-            }
-            // this warp's lanes of buffer b are read: hand the buffer back
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_local(&acc_empty[b]);
         }
     }
     __syncwarp();
@@ -496,6 +479,130 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
         tc_fence_after();
         tmem_dealloc(tmem, 2 * kTmemCols);
     }
+}
+
+// The lower triangle and, with m1, the block maxima, after the product kernel wrote
+// S_ij for i <= j: S_ji = S_ij for i < j (bitwise, so S is exactly symmetric), and
+// m1[i][jb] = max |S_ij| over the 128-column block jb with j != i and j < p, rounded
+// up to BF16 (an upper bound; 0x7fc0 when the block holds a NaN).  One block of 256
+// threads per 128 x 128 block pair (I <= J) of the upper triangle, in triangle order:
+// the tile is read row by row (row maxima on the way), staged in shared memory, and
+// written transposed row by row (column maxima on the way); both passes are
+// coalesced.  A diagonal pair reads and writes only its strictly upper part, and its
+// maxima combine the row (j > i) and column (j < i) parts.
+constexpr int kMirT = 128;
+constexpr int kMirSmem = kMirT * (kMirT + 1) * 4 + kMirT * 8;
+
+__device__ __forceinline__ void nanmax_warp(float& mx, bool& nan) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+    nan = __any_sync(kFull, nan);
+}
+
+template <bool MAXIMA>
+__global__ void __launch_bounds__(256)
+k_mirror_max(float* __restrict__ S, int64_t lds, int p, int nb, uint16_t* __restrict__ m1, int nbm) {
+    extern __shared__ float mir[];
+    float* t = mir;                                               // [kMirT][kMirT + 1]
+    float* rmax = mir + kMirT * (kMirT + 1);                      // [kMirT] upper-part row maxima
+    int* rnan = reinterpret_cast<int*>(rmax + kMirT);             // [kMirT]
+    // block pair (bi <= bj) of this CTA: t = bj (bj + 1) / 2 + bi
+    const long long tix = blockIdx.x;
+    int bj = (int)((sqrt(8.0 * (double)tix + 1.0) - 1.0) * 0.5);
+    while ((long long)(bj + 1) * (bj + 2) / 2 <= tix) ++bj;
+    while ((long long)bj * (bj + 1) / 2 > tix) --bj;
+    const int bi = (int)(tix - (long long)bj * (bj + 1) / 2);
+    if (bj >= nb) return;
+    const bool dg = bi == bj;
+    const int I0 = bi * kMirT, J0 = bj * kMirT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // rows of S[I, J]: warp w takes rows w, w + 8, ...; lane l columns l + 32 m.  Only
+    // loads and shared stores here, so that the loads of several rows are in flight.
+#pragma unroll 4
+    for (int r = warp; r < kMirT; r += 8) {
+        const int i = I0 + r;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int c = lane + 32 * m;
+            t[r * (kMirT + 1) + c] = (i < p && (!dg || c > r)) ? S[(int64_t)i * lds + J0 + c] : 0.f;
+        }
+    }
+    __syncthreads();
+    if constexpr (MAXIMA) {
+        // row maxima of the staged tile (for a diagonal pair, of its upper part)
+        for (int r = warp; r < kMirT; r += 8) {
+            const int i = I0 + r;
+            float mx = 0.f;
+            bool nan = false;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int c = lane + 32 * m;
+                if (J0 + c < p && (!dg || c > r)) {
+                    const float a = fabsf(t[r * (kMirT + 1) + c]);
+                    nan |= !(a == a);
+                    mx = fmaxf(mx, a);
+                }
+            }
+            nanmax_warp(mx, nan);
+            if (lane == 0) {
+                if (dg) {
+                    rmax[r] = mx;
+                    rnan[r] = nan;
+                } else if (i < p) {
+                    m1[(int64_t)i * nbm + bj] = nan ? (uint16_t)0x7fc0 : bf16_up_f(mx);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // columns of the tile = rows J0 + c of the lower triangle: warp w takes c = w, w + 8, ...
+    for (int c = warp; c < kMirT; c += 8) {
+        const int j = J0 + c;
+        if (j >= p) continue;
+        float mx = 0.f;
+        bool nan = false;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = lane + 32 * m;
+            const int i = I0 + r;
+            if (i < p && (!dg || r < c)) {
+                const float x = t[r * (kMirT + 1) + c];
+                S[(int64_t)j * lds + i] = x;
+                if constexpr (MAXIMA) {
+                    const float a = fabsf(x);
+                    nan |= !(a == a);
+                    mx = fmaxf(mx, a);
+                }
+            }
+        }
+        if constexpr (MAXIMA) {
+            nanmax_warp(mx, nan);
+            if (lane == 0) {
+                if (dg) {
+                    mx = fmaxf(mx, rmax[c]);
+                    nan = nan || rnan[c] != 0;
+                }
+                m1[(int64_t)j * nbm + bi] = nan ? (uint16_t)0x7fc0 : bf16_up_f(mx);
+            }
+        }
+    }
+}
+
+cudaError_t launch_mirror(float* S, int64_t lds, int64_t p, uint16_t* m1, int nbm, cudaStream_t s) {
+    const int nb = (int)((p + kMirT - 1) / kMirT);
+    const long long pairs = (long long)nb * (nb + 1) / 2;
+    if (pairs > 0x7fffffffll) return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mirror_max<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMirSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_mirror_max<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMirSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (m1) k_mirror_max<true><<<(unsigned)pairs, 256, kMirSmem, s>>>(S, lds, (int)p, nb, m1, nbm);
+    else k_mirror_max<false><<<(unsigned)pairs, 256, kMirSmem, s>>>(S, lds, (int)p, nb, nullptr, 0);
+    return cudaGetLastError();
 }
 
 // Transpose X (n x p) into K-major panels (p_pad x n_pad) of the MMA input type,
@@ -669,10 +776,27 @@ bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
     return r == CUDA_SUCCESS;
 }
 
+// K elements per accumulation chunk when the caller gives none: the S_ii bias of a
+// chunk grows with the MMAs chained into it, so 32 MMAs for one product per K step
+// (BF16 X) and 48 for the three of BF16X3 keep it near 1e-6 relative (measured
+// -9.5e-7 on the diagonal at n = 32768, against -1.4e-4 for one chunk over all of K).
+// Shorter chunks leave the tensor core idle while the epilogue reads them out.  The
+// first two chunks of a tile are twice as long (lead_k), which covers the epilogue's
+// stores of the previous tile.
+template <int MODE>
+constexpr int default_chunk_k() { return MODE == kModeBf16 ? 512 : 256; }
+
+// The product kernel, then the mirror pass (lower triangle and, with m1, the block
+// maxima); after_kernel (nullable) is recorded between the two.
 template <int MODE>
 cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles, int64_t n, int64_t p, float* S,
-                        int64_t lds, cudaStream_t s, uint16_t* m1 = nullptr, int nbm = 0, int dynamic = 1) {
+                        int64_t lds, cudaStream_t s, uint16_t* m1 = nullptr, int nbm = 0, int dynamic = 1,
+                        int64_t chunk_k = 0, int64_t lead_k = 0, cudaEvent_t after_kernel = nullptr) {
     using C = Cfg<MODE>;
+    if (chunk_k <= 0) chunk_k = default_chunk_k<MODE>();
+    if (lead_k <= 0) lead_k = std::min<int64_t>(2 * chunk_k, (int64_t)1 << 40);
+    const int chunk_kt = (int)std::max<int64_t>(1, std::min<int64_t>(chunk_k / C::kBK, 1 << 30));
+    const int lead_kt = (int)std::max<int64_t>(chunk_kt, std::min<int64_t>(lead_k / C::kBK, 1 << 30));
     CUtensorMap mh, ml;
     std::memset(&mh, 0, sizeof mh);
     std::memset(&ml, 0, sizeof ml);
@@ -680,11 +804,18 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
     if (C::kPieces > 1 && !make_map(&ml, lo, MODE, g)) return cudaErrorNotSupported;
     if (C::kPieces == 1) ml = mh;
     const int k_tiles = (int)(g.n_pad / C::kBK);
-    // float4 row stores need 16-byte aligned rows: lds % 4 == 0 and an aligned base
-    const int vec_ok = (lds % 4 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0) ? 1 : 0;
     cudaError_t e =
         cudaFuncSetAttribute(k_gram_tc_persist<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return e;
+    // setmaxnreg moves registers between the warpgroups of a block: the kernel must have
+    // been built with enough registers per thread for both shares (else it would wait)
+    static int regs = -1;
+    if (regs < 0) {
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, k_gram_tc_persist<MODE>)) != cudaSuccess) return e;
+        regs = fa.numRegs;
+    }
+    if (regs < kMinLaunchRegs) return cudaErrorNotSupported;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
@@ -694,8 +825,10 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
         (reinterpret_cast<uintptr_t>(tiles + g.ntiles) + 255) & ~uintptr_t(255));
     if (dynamic) k_zero_counter<<<1, 1, 0, s>>>(ctr);
     k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n, S,
-                                                                   lds, vec_ok, m1, nbm, ctr, dynamic);
-    return cudaGetLastError();
+                                                                   lds, ctr, dynamic, chunk_kt, lead_kt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (after_kernel && (e = cudaEventRecord(after_kernel, s)) != cudaSuccess) return e;
+    return launch_mirror(S, lds, p, m1, nbm, s);
 }
 
 // max_blocks > 0 bounds the BF16 transpose's grid (it then loops over its tiles).
@@ -762,7 +895,7 @@ cudaError_t gram_tc_prepare(const void* X, int xdt, int64_t n, int64_t p, int pr
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band,
                     cudaEvent_t before_kernel, uint16_t* m1, int nbm, int prepared, uint64_t* tiles_sig,
-                    int schedule) {
+                    int schedule, int64_t chunk_k, int64_t lead_k, cudaEvent_t after_kernel) {
     if (band <= 0) band = kBand;
     cudaError_t e = check_shape(xdt, n, p, precision, scratch_bytes);
     if (e != cudaSuccess) return e;
@@ -793,9 +926,14 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
     }
     if (launches) *launches += 1;
     if (before_kernel && (e = cudaEventRecord(before_kernel, s)) != cudaSuccess) return e;
-    if (mode == kModeBf16) return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule);
-    if (mode == kModeBf16x3) return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule);
-    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule);
+    if (mode == kModeBf16)
+        return launch_mode<kModeBf16>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule, chunk_k, lead_k,
+                                        after_kernel);
+    if (mode == kModeBf16x3)
+        return launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule, chunk_k, lead_k,
+                                        after_kernel);
+    return launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s, m1, nbm, schedule, chunk_k, lead_k,
+                                        after_kernel);
 }
 
 int gram_tc_take_error() {

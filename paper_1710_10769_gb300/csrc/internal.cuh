@@ -219,7 +219,7 @@ bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void
                    int64_t p, CUtensorMap* maps);
 cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
                              int p, const int* rp, const int* ci, const float* cv, Emit<float> em,
-                             Ctrl* ctrl, cudaStream_t s);
+                             Ctrl* ctrl, cudaStream_t s, int64_t chunk_k = 0, int64_t lead_k = 0);
 int obs_take_error();
 
 // ---------------------------------------------------------------- differentiation (adjoint.cu)
@@ -272,14 +272,31 @@ cudaError_t gram_simt(const void* X, int xdt, int64_t n, int64_t p, void* S, int
 // rounded up to BF16, from the product's epilogue.
 // prepared: the panels in scratch already hold X's preparation (gram_tc_prepare).
 // tiles_sig: the caller's record of the tile order already in scratch (null: upload it).
+// chunk_k: K elements per accumulation chunk (0: the mode's default); lead_k: K elements
+// of each tile's first two chunks (0: 4 chunk_k).  The product writes S_ij for i <= j; a
+// pass after it writes the lower triangle (and m1); after_kernel (nullable) is recorded
+// between the two.
 cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int64_t lds, int precision,
                     void* scratch, size_t scratch_bytes, cudaStream_t s, int* launches, int band = 0,
                     cudaEvent_t before_kernel = nullptr, uint16_t* m1 = nullptr, int nbm = 0, int prepared = 0,
-                    uint64_t* tiles_sig = nullptr, int schedule = 1);
+                    uint64_t* tiles_sig = nullptr, int schedule = 1, int64_t chunk_k = 0, int64_t lead_k = 0,
+                    cudaEvent_t after_kernel = nullptr);
 // Only the panel preparation of gram_tc (transpose / split of X into scratch);
 // max_blocks > 0 bounds the BF16 transpose's grid, so that it shares the GPU with a solve.
 cudaError_t gram_tc_prepare(const void* X, int xdt, int64_t n, int64_t p, int precision, void* scratch,
                             size_t scratch_bytes, cudaStream_t s, int max_blocks = 0);
+// Chunk c of a tile's K loop (in stages): the first two chunks hold lead stages each,
+// the rest chunk stages each (the last one ragged).  The long first chunks keep the
+// MMAs of the next tile busy while the epilogue stores the previous one.
+__host__ __device__ __forceinline__ int chunk_start(int c, int k_tiles, int chunk, int lead) {
+    const long long st = c <= 2 ? (long long)c * lead : 2ll * lead + (long long)(c - 2) * chunk;
+    return st < k_tiles ? (int)st : k_tiles;
+}
+__host__ __device__ __forceinline__ int num_chunks(int k_tiles, int chunk, int lead) {
+    if (k_tiles <= 2 * lead) return (k_tiles + lead - 1) / lead;
+    return 2 + (k_tiles - 2 * lead + chunk - 1) / chunk;
+}
+
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
 int gram_tc_take_error();

@@ -113,21 +113,53 @@ struct ObsCfg {
     static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
 };
 
-constexpr int kObsThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kObsThreads = 128 + 32 * kEpiWarps;     // warpgroup 0: roles; warpgroups 1-2: epilogue
+// Registers per thread after setmaxnreg (warpgroup 0 down, the epilogue warpgroups up);
+// the host checks that the launch's pool covers both (kMinLaunchRegs) before launching.
+constexpr int kRegsSmall = 56;
+constexpr int kRegsEpi = 216;
+constexpr int kMinLaunchRegs = (128 * kRegsSmall + 32 * kEpiWarps * kRegsEpi + kObsThreads - 1) / kObsThreads;
 
 __device__ int g_obs_error = 0;
+
+// 32 TMEM lanes x 16 consecutive 32-bit columns: thread t gets lane (base + t).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
 
 // Persistent pair kernel: one CTA per SM walks the pairs blockIdx.x, blockIdx.x +
 // grid, ... of the pair list (bi <= bj, bands of row blocks).  For pair (I, J)
 // it forms Z[I, J] = Y^T[I] X^T[J]^T / n and Z[J, I] = Y^T[J] X^T[I]^T / n and emits
-// both sides.  Roles:
-//   warp 0      TMA producer (thread 0), running ahead across pairs;
-//   warp 1      MMA issuer (thread 32) and TMEM owner: pair t into accumulator pair
-//               t & 1 (columns 256 (t & 1) + {0, 128} for Z[I, J], Z[J, I]);
-//   warps 2-5   epilogue of pair t while pair t + 1 accumulates: stage Z[J, I]
-//               through shared memory (a buffer of its own, half the tile at a
-//               time), then emit row by row; warp w reads TMEM lanes 32 (w % 4) .. + 31.
-// acc_full[b] (one commit) and acc_empty[b] (four epilogue warps) hand the
+// both sides.
+//
+// Chunked accumulation, as in the Gram: the K loop of a pair is cut into chunks
+// (chunk_start), each chunk accumulates both tiles from zero into one TMEM
+// accumulator pair, and the epilogue adds the chunk sums in FP32 round-to-nearest in
+// registers, so the bias of the tensor core's truncating accumulation scales with
+// the chunk, not with n.
+//
+// Roles:
+//   warp 0      TMA producer (thread 0), running ahead across pairs: per chunk the
+//               stages of (Y^T[I], X^T[J]), then of (Y^T[J], X^T[I]);
+//   warp 1      MMA issuer (thread 32) and TMEM owner: chunk c of the CTA's sequence
+//               into accumulator pair c & 1 (columns 256 (c & 1) + {0, 128} for
+//               Z[I, J], Z[J, I]);
+//   warps 2-3   idle (they complete warpgroup 0, which hands registers to the
+//               epilogue with setmaxnreg);
+//   warps 4-7   running sums of Z[I, J] (warp w: TMEM lanes 32 (w % 4) .. + 31, one
+//               row of 128 columns per thread), and after the last chunk the
+//               emission of the pair, row by row;
+//   warps 8-11  running sums of Z[J, I] (the same lanes), staged after the last chunk
+//               through shared memory, half the tile at a time, for the transpose;
+//               for a diagonal pair (I = J) warps 4-7 stage their own rows.
+// acc_full[b] (one commit) and acc_empty[b] (eight epilogue warps) hand the
 // accumulator pairs over.  Every wait is bounded; after an abort every role stops,
 // the epilogue warps keep meeting at their barriers, the loads in flight drain and
 // TMEM is freed.
@@ -136,7 +168,7 @@ __global__ void __launch_bounds__(kObsThreads, 1)
 k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUtensorMap yb,
            const __grid_constant__ CUtensorMap xa, const __grid_constant__ CUtensorMap xb, const int2* __restrict__ pairs,
            int npairs, int k_tiles, int p, int64_t n, const int* __restrict__ rp, const int* __restrict__ ci,
-           const float* __restrict__ cv, Emit<float> em, Ctrl* __restrict__ ctrl) {
+           const float* __restrict__ cv, Emit<float> em, Ctrl* __restrict__ ctrl, int chunk_kt, int lead_kt) {
     using C = ObsCfg<MODE>;
     const float lam1 = (float)ctrl->lam1;
     extern __shared__ uint8_t smem_raw[];
@@ -153,10 +185,13 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int my_pairs = (int)blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (chunk_kt < 1) chunk_kt = 1;
+    if (lead_kt < chunk_kt) lead_kt = chunk_kt;
+    const int nch = num_chunks(k_tiles, chunk_kt, lead_kt);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { ptx::mbar_init(&acc_full[b], 1); ptx::mbar_init(&acc_empty[b], 4); }
+        for (int b = 0; b < 2; ++b) { ptx::mbar_init(&acc_full[b], 1); ptx::mbar_init(&acc_empty[b], kEpiWarps); }
         *abort_flag = 0;
         ptx::mbar_init_fence();
     }
@@ -170,158 +205,193 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_slot;
 
     long long issued = 0;
-    if (threadIdx.x == 0) {
-        // ---------------- producer: per pair, phase 0 streams (Y^T[I], X^T[J]), phase 1 (Y^T[J], X^T[I])
-        long long g = 0;
-        bool ok = true;
-        for (int lt = 0; lt < my_pairs && ok; ++lt) {
-            const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
-            const int I0 = pr.x * kT, J0 = pr.y * kT;
-            const int items = (pr.x == pr.y ? 1 : 2) * k_tiles;
-            for (int t = 0; t < items; ++t, ++g) {
-                const int s = (int)(g % C::kStages);
-                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
-                if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, kWaitLimit)) {
-                    atomicCAS(&g_obs_error, 0, 1);
-                    ok = false;
-                    break;
-                }
-                const int phase = t / k_tiles, kt = t % k_tiles;
-                const int ra = phase == 0 ? I0 : J0, rb = phase == 0 ? J0 : I0;
-                uint8_t* st = smem + s * C::kStageBytes;
-                ptx::mbar_expect_tx(&full[s], C::kStageBytes);
-                const int kc = kt * C::kBK;
-                ptx::tma_load_2d(st, &ya, &full[s], kc, ra);
-                ptx::tma_load_2d(st + kPanelTile, &xa, &full[s], kc, rb);
-                if (C::kPieces > 1) {
-                    ptx::tma_load_2d(st + 2 * kPanelTile, &yb, &full[s], kc, ra);
-                    ptx::tma_load_2d(st + 3 * kPanelTile, &xb, &full[s], kc, rb);
-                }
-                ++issued;
-            }
-        }
-    } else if (threadIdx.x == 32) {
-        // ---------------- MMA issuer
-        constexpr uint32_t idesc = instr_desc<MODE>();
-        long long g = 0;
-        bool ok = true;
-        for (int lt = 0; lt < my_pairs && ok; ++lt) {
-            const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
-            const int items = (pr.x == pr.y ? 1 : 2) * k_tiles;
-            const int b = lt & 1;
-            if (!ptx::mbar_wait_bounded(&acc_empty[b], ((uint32_t)(lt >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
-                atomicCAS(&g_obs_error, 0, 3);
-                break;
-            }
-            tc_fence_after();
-            for (int t = 0; t < items; ++t, ++g) {
-                const int s = (int)(g % C::kStages);
-                const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
-                if (!ptx::mbar_wait_bounded(&full[s], ph, abort_flag, kWaitLimit)) {
-                    atomicCAS(&g_obs_error, 0, 2);
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const int phase = t / k_tiles, kt = t % k_tiles;
-                const uint32_t d = tmem + (uint32_t)(b * 2 * kT + phase * kT);
-                const uint32_t st = ptx::smem_u32(smem + s * C::kStageBytes);
-                const uint32_t a_hi = st, b_hi = st + kPanelTile, a_lo = st + 2 * kPanelTile, b_lo = st + 3 * kPanelTile;
-#pragma unroll
-                for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
-                    const uint32_t off = kk * 32;
-                    const uint32_t acc0 = (kt > 0 || kk > 0) ? 1u : 0u;
-                    umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
-                    if constexpr (C::kTerms == 3) {
-                        umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
-                        umma<MODE>(d, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+    if (warp < 4) {
+        // producer, MMA issuer and two idle warps: one warpgroup that gives registers away
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsSmall));
+        if (threadIdx.x == 0) {
+            // ---------------- producer: per chunk, phase 0 streams (Y^T[I], X^T[J]), phase 1 (Y^T[J], X^T[I])
+            long long g = 0;
+            bool ok = true;
+            for (int lt = 0; lt < my_pairs && ok; ++lt) {
+                const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+                const int I0 = pr.x * kT, J0 = pr.y * kT;
+                const int phases = pr.x == pr.y ? 1 : 2;
+                for (int c = 0; c < nch && ok; ++c) {
+                    const int kt0 = chunk_start(c, k_tiles, chunk_kt, lead_kt);
+                    const int kt1 = chunk_start(c + 1, k_tiles, chunk_kt, lead_kt);
+                    for (int phase = 0; phase < phases && ok; ++phase) {
+                        const int ra = phase == 0 ? I0 : J0, rb = phase == 0 ? J0 : I0;
+                        for (int kt = kt0; kt < kt1; ++kt, ++g) {
+                            const int s = (int)(g % C::kStages);
+                            const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                            if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, kWaitLimit)) {
+                                atomicCAS(&g_obs_error, 0, 1);
+                                ok = false;
+                                break;
+                            }
+                            uint8_t* st = smem + s * C::kStageBytes;
+                            ptx::mbar_expect_tx(&full[s], C::kStageBytes);
+                            const int kc = kt * C::kBK;
+                            ptx::tma_load_2d(st, &ya, &full[s], kc, ra);
+                            ptx::tma_load_2d(st + kPanelTile, &xa, &full[s], kc, rb);
+                            if (C::kPieces > 1) {
+                                ptx::tma_load_2d(st + 2 * kPanelTile, &yb, &full[s], kc, ra);
+                                ptx::tma_load_2d(st + 3 * kPanelTile, &xb, &full[s], kc, rb);
+                            }
+                            ++issued;
+                        }
                     }
                 }
-                umma_commit(&empty[s]);
             }
-            if (ok) umma_commit(&acc_full[b]);
+        } else if (threadIdx.x == 32) {
+            // ---------------- MMA issuer
+            constexpr uint32_t idesc = instr_desc<MODE>();
+            long long g = 0, gc = 0;
+            bool ok = true;
+            for (int lt = 0; lt < my_pairs && ok; ++lt) {
+                const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+                const int phases = pr.x == pr.y ? 1 : 2;
+                for (int c = 0; c < nch && ok; ++c, ++gc) {
+                    const int b = (int)(gc & 1);
+                    if (!ptx::mbar_wait_bounded(&acc_empty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abort_flag,
+                                                kWaitLimit)) {
+                        atomicCAS(&g_obs_error, 0, 3);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int kt0 = chunk_start(c, k_tiles, chunk_kt, lead_kt);
+                    const int kt1 = chunk_start(c + 1, k_tiles, chunk_kt, lead_kt);
+                    for (int phase = 0; phase < phases && ok; ++phase) {
+                        const uint32_t d = tmem + (uint32_t)(b * 2 * kT + phase * kT);
+                        for (int kt = kt0; kt < kt1; ++kt, ++g) {
+                            const int s = (int)(g % C::kStages);
+                            const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
+                            if (!ptx::mbar_wait_bounded(&full[s], ph, abort_flag, kWaitLimit)) {
+                                atomicCAS(&g_obs_error, 0, 2);
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t st = ptx::smem_u32(smem + s * C::kStageBytes);
+                            const uint32_t a_hi = st, b_hi = st + kPanelTile, a_lo = st + 2 * kPanelTile,
+                                           b_lo = st + 3 * kPanelTile;
+    #pragma unroll
+                            for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
+                                const uint32_t off = kk * 32;
+                                const uint32_t acc0 = (kt > kt0 || kk > 0) ? 1u : 0u;
+                                umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_hi + off), idesc, acc0);
+                                if constexpr (C::kTerms == 3) {
+                                    umma<MODE>(d, smem_desc_sw128(a_hi + off), smem_desc_sw128(b_lo + off), idesc, 1u);
+                                    umma<MODE>(d, smem_desc_sw128(a_lo + off), smem_desc_sw128(b_hi + off), idesc, 1u);
+                                }
+                            }
+                            umma_commit(&empty[s]);
+                        }
+                    }
+                    if (ok) umma_commit(&acc_full[b]);
+                }
+            }
         }
-    } else if (warp >= 2) {
+    } else {
+        // the epilogue warpgroups take them: the running sums of 128 columns live in registers
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
         // ---------------- epilogue
         const int q4 = warp & 3;
+        const int side = (warp - 4) >> 2;            // 0: Z[I, J] rows, 1: Z[J, I] rows
         const int r = q4 * 32 + lane;                // TMEM lane = local row
         const float dn = (float)n;
+        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(side * kT);
+        long long gc = 0;
         for (int lt = 0; lt < my_pairs; ++lt) {
             const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
             const int I0 = pr.x * kT, J0 = pr.y * kT;
             const bool diag_pair = pr.x == pr.y;
-            const int b = lt & 1;
-            bool have = !*abort_flag &&
-                        ptx::mbar_wait_bounded(&acc_full[b], (uint32_t)(lt >> 1) & 1u, abort_flag, kWaitLimit);
-            have = __all_sync(kFull, have);
-            tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 2 * kT);
-            // Z[J, I] (Z[I, I] for a diagonal pair) is staged in two halves of 64 rows:
-            // the warps holding TMEM lanes 64 h .. 64 h + 63 write them, then every
-            // thread emits its row's columns 64 h .. 64 h + 63 (the support merge
-            // carries over between the halves)
-            const uint32_t src = diag_pair ? 0u : (uint32_t)kT;
+            float acc[kT];
+#pragma unroll
+            for (int q = 0; q < kT; ++q) acc[q] = 0.f;
+            bool have = true;
+            for (int c = 0; c < nch; ++c, ++gc) {
+                const int b = (int)(gc & 1);
+                bool got = have && !*abort_flag &&
+                           ptx::mbar_wait_bounded(&acc_full[b], (uint32_t)(gc >> 1) & 1u, abort_flag, kWaitLimit);
+                got = __all_sync(kFull, got);
+                if (!got) { have = false; continue; }
+                tc_fence_after();
+                if (side == 0 || !diag_pair) {
+#pragma unroll
+                    for (int s8 = 0; s8 < kT / 16; ++s8) {
+                        uint32_t v[16];
+                        tmem_ld16(lane_base + (uint32_t)(b * 2 * kT + s8 * 16), v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) acc[s8 * 16 + q] += __uint_as_float(v[q]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx_arrive(&acc_empty[b]);
+            }
+#pragma unroll
+            for (int q = 0; q < kT; ++q) acc[q] = acc[q] / dn;
+            // the staging side: Z[J, I] (side 1), or Z[I, I] itself for a diagonal pair
+            const bool stager = diag_pair ? side == 0 : side == 1;
             const int i = I0 + r;
             int q = 0, qe = 0;
-            if (have && i < p) {
+            if (side == 0 && have && i < p) {
                 q = rp[i];
                 qe = rp[i + 1];
                 while (q < qe && ci[q] < J0) ++q;
             }
-            for (int h = 0; h < 2; ++h) {
-                if (have && (q4 >> 1) == h) {
-                    const int cl = (q4 - 2 * h) * 32 + lane;            // staged row, 0..63
-                    for (int c0 = 0; c0 < kT; c0 += 32) {
-                        uint32_t v[32];
-                        tmem_ld32(base + src + (uint32_t)c0, v);
-                        tmem_ld_wait();
+            // Z[J, I] (Z[I, I] for a diagonal pair) is staged in two halves of 64 rows:
+            // the warps holding rows 64 h .. 64 h + 63 write them, then every emitting
+            // thread handles its row's columns 64 h .. 64 h + 63 (the support merge
+            // carries over between the halves)
 #pragma unroll
-                        for (int qq = 0; qq < 32; ++qq) zt[cl * (kT + 1) + c0 + qq] = __uint_as_float(v[qq]) / dn;
-                    }
+            for (int h = 0; h < 2; ++h) {
+                if (have && stager && (q4 >> 1) == h) {
+                    const int cl = (q4 - 2 * h) * 32 + lane;            // staged row, 0..63
+#pragma unroll
+                    for (int cc = 0; cc < kT; ++cc) zt[cl * (kT + 1) + cc] = acc[cc];
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");      // the staged half is complete
-                if (have) {
-                    for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 32) {
-                        uint32_t v[32];
-                        tmem_ld32(base + (uint32_t)c0, v);
-                        tmem_ld_wait();
-                        if (i >= p) continue;
-                        for (int cc = 0; cc < 32; ++cc) {
-                            const int c = c0 + cc;
-                            const int j = J0 + c;
-                            if (j >= p) break;
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");      // the staged half is complete
+                if (have && side == 0 && i < p) {
+#pragma unroll
+                    for (int cc = 0; cc < kT / 2; ++cc) {
+                        const int c = 64 * h + cc;
+                        const int j = J0 + c;
+                        if (j < p) {
                             while (q < qe && ci[q] < j) ++q;             // support merge, column order
-                            if (diag_pair && j < i) continue;            // the (j, i) thread emits this pair
-                            const float a = __uint_as_float(v[cc]) / dn; // Z_ij
-                            const float bz = zt[(c - 64 * h) * (kT + 1) + r];   // Z_ji
-                            const bool sup = q < qe && ci[q] == j;
-                            const float om = sup ? cv[q] : 0.f;
-                            const bool big = !(fabsf(a) <= lam1) || !(fabsf(bz) <= lam1);
-                            if (!(sup || big || i == j)) continue;
-                            const int cnt = (i == j) ? 1 : 2;
-                            const int pos = atomicAdd(&ctrl->em_count, cnt);
-                            const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);   // paired, support
-                            if (pos < em.cap) {
-                                em.row[pos] = i;
-                                em.col[pos] = (int)((unsigned)j | fl);
-                                em.w[pos] = a;
-                                em.om[pos] = om;
-                            }
-                            if (i != j && pos + 1 < em.cap) {
-                                em.row[pos + 1] = j;
-                                em.col[pos + 1] = (int)((unsigned)i | fl);
-                                em.w[pos + 1] = bz;
-                                em.om[pos + 1] = om;
+                            // on a diagonal pair the (j, i) thread emits the pairs with j < i
+                            if (!(diag_pair && j < i)) {
+                                const float a = acc[c];                                  // Z_ij
+                                const float bz = zt[cc * (kT + 1) + r];                  // Z_ji
+                                const bool sup = q < qe && ci[q] == j;
+                                const float om = sup ? cv[q] : 0.f;
+                                const bool big = !(fabsf(a) <= lam1) || !(fabsf(bz) <= lam1);
+                                if (sup || big || i == j) {
+                                    const int cnt = (i == j) ? 1 : 2;
+                                    const int pos = atomicAdd(&ctrl->em_count, cnt);
+                                    const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);   // paired, support
+                                    if (pos < em.cap) {
+                                        em.row[pos] = i;
+                                        em.col[pos] = (int)((unsigned)j | fl);
+                                        em.w[pos] = a;
+                                        em.om[pos] = om;
+                                    }
+                                    if (i != j && pos + 1 < em.cap) {
+                                        em.row[pos + 1] = j;
+                                        em.col[pos + 1] = (int)((unsigned)i | fl);
+                                        em.w[pos + 1] = bz;
+                                        em.om[pos + 1] = om;
+                                    }
+                                }
                             }
                         }
                     }
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");      // the staged half is free again
+                asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");      // the staged half is free again
             }
-            // this warp's lanes of the accumulator pair are read: hand it back
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx_arrive(&acc_empty[b]);
         }
     }
     __syncwarp();
@@ -412,10 +482,16 @@ bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void
     return true;
 }
 
+// K elements -> whole stages of kbk elements, at least one.
+static int kt_of(int64_t k, int kbk) { return (int)std::max<int64_t>(1, std::min<int64_t>(k / kbk, 1 << 30)); }
+
 cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
                              int p, const int* rp, const int* ci, const float* cv, Emit<float> em,
-                             Ctrl* ctrl, cudaStream_t s) {
+                             Ctrl* ctrl, cudaStream_t s, int64_t chunk_k, int64_t lead_k) {
     const int64_t n_pad = (n + 63) / 64 * 64;
+    // K elements per accumulation chunk (the Gram's BF16X3 / TF32 default when none is given)
+    if (chunk_k <= 0) chunk_k = 256;
+    if (lead_k <= 0) lead_k = 4 * chunk_k;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -424,20 +500,34 @@ cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2*
             sms = 1;
     }
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(npairs, sms));   // one CTA per SM
+    // setmaxnreg moves registers between the warpgroups of a block: the kernel must have
+    // been built with enough registers per thread for both shares (else it would wait)
+    static int regs[2] = {-1, -1};
+    const int mi = precision == HPC_PREC_TF32 ? 1 : 0;
+    if (regs[mi] < 0) {
+        cudaFuncAttributes fa;
+        const cudaError_t e = cudaFuncGetAttributes(
+            &fa, mi ? (const void*)k_obs_pair<kObsTf32> : (const void*)k_obs_pair<kObsBf16x3>);
+        if (e != cudaSuccess) return e;
+        regs[mi] = fa.numRegs;
+    }
+    if (regs[mi] < kMinLaunchRegs) return cudaErrorNotSupported;
     if (precision == HPC_PREC_TF32) {
         using C = ObsCfg<kObsTf32>;
         cudaError_t e = set_smem_once((const void*)k_obs_pair<kObsTf32>, C::kSmem, kSmemSlotObsTf32);
         if (e != cudaSuccess) return e;
         k_obs_pair<kObsTf32><<<grid, kObsThreads, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
                                                                  (int)npairs, (int)(n_pad / C::kBK), p, n, rp, ci,
-                                                                 cv, em, ctrl);
+                                                                 cv, em, ctrl, kt_of(chunk_k, C::kBK),
+                                                                 kt_of(lead_k, C::kBK));
     } else {
         using C = ObsCfg<kObsBf16x3>;
         cudaError_t e = set_smem_once((const void*)k_obs_pair<kObsBf16x3>, C::kSmem, kSmemSlotObsBf16x3);
         if (e != cudaSuccess) return e;
         k_obs_pair<kObsBf16x3><<<grid, kObsThreads, C::kSmem, s>>>(maps[0], maps[1], maps[2], maps[3], pairs,
                                                                    (int)npairs, (int)(n_pad / C::kBK), p, n, rp, ci,
-                                                                   cv, em, ctrl);
+                                                                   cv, em, ctrl, kt_of(chunk_k, C::kBK),
+                                                                   kt_of(lead_k, C::kBK));
     }
     return cudaGetLastError();
 }

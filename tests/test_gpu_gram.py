@@ -177,3 +177,37 @@ def test_prefetch_gives_the_load_result(lib, src, dt):
         assert np.array_equal(got[1], ref[1])
         assert got[2] == ref[2]
         assert np.array_equal(got[3], ref[3])
+
+
+@pytest.mark.parametrize("xdt", ["bf16", "f32"])
+def test_chunked_accumulation_removes_the_truncation_bias(lib, xdt):
+    """The tensor core adds each MMA into the FP32 accumulator with truncation, which biases
+    a long sum towards zero (about 0.6 ulp of the partial sum per MMA).  With the K loop cut
+    into chunks summed in FP32 round-to-nearest (gram_chunk, default 512 K for BF16 X and
+    256 K for BF16X3) the diagonal's mean relative error against the FP64 Gram stays within
+    0.6 * 2^-23 per MMA of a chunk (32 or 48 MMAs); one chunk over all n = 8192 (a
+    gram_chunk >= n) shows the bias the chunking removes.  Both stay within the per-entry
+    bound, and the chunked S is exactly symmetric."""
+    import torch
+
+    n, p = 8192, 384
+    rng = np.random.default_rng(23)
+    X = rng.standard_normal((n, p)).astype(np.float32)
+    Xt = torch.as_tensor(X).cuda()
+    if xdt == "bf16":
+        Xt = Xt.to(torch.bfloat16)
+        Xd = Xt.float().cpu().numpy().astype(np.float64)
+        per_chunk = 32
+    else:
+        Xd = X.astype(np.float64)
+        per_chunk = 48
+    ref = np.diag(oracle.gram(Xd))
+    bias = {}
+    for chunk in (0, n):
+        with lib.Solver(Xt, 0.5, 0.1, precision=lib.PREC_BF16X3) as s:
+            s.set_tuning(gram_chunk=chunk)
+            s.load_x(Xt)
+            d = s.s_entries(np.arange(p), np.arange(p))
+        bias[chunk] = float(np.mean((d - ref) / ref))
+    assert abs(bias[0]) <= 0.6 * 2.0 ** -23 * per_chunk * 1.5, bias
+    assert bias[n] < -4 * abs(bias[0]), bias

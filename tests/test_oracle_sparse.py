@@ -25,7 +25,7 @@ CASES = [(120, 80, 4.0, 3, 0.1), (120, 80, 4.0, 3, 0.3), (90, 200, 3.0, 5, 0.15)
 def test_chunked_gram():
     X = small_problem(70, 53, 3.0, 1)
     S = oracle.gram(X)
-    S2 = oracle.gram_chunked(X, chunk=16)
+    S2 = oracle.gram_chunked(X, block=16)
     assert np.array_equal(S2, S2.T) and S2.flags["C_CONTIGUOUS"]
     assert np.max(np.abs(S - S2)) <= 1e-14 * np.max(np.abs(S))
 
