@@ -63,7 +63,11 @@ typedef enum { HPC_COV = 0, HPC_OBS = 1 } hpc_variant;          /* Alg. 2 / Alg.
 typedef enum { HPC_F32 = 0, HPC_F64 = 1, HPC_BF16 = 2 } hpc_dtype;
 
 /* Arithmetic of the dense products S = X^T X / n (Alg. 2 step 2) and
- * Z = Y X / n (Alg. 3 step 4).  Everything else follows value_dtype. */
+ * Z = Y X / n (Alg. 3 step 4).  Everything else follows value_dtype.
+ * The tensor-core modes sum K in chunks (hpc_tuning.gram_chunk), so their
+ * accumulation error does not grow with n: BF16X3 is FP32-class.  For the Obs
+ * variant HPC_PREC_FP32 selects that BF16X3 Z product (hpc_get_info then
+ * reports HPC_PREC_BF16X3); FP64 and the SIMT modes are Cov only. */
 typedef enum {
     HPC_PREC_AUTO   = -1,  /* FP64 for FP64 iterates, BF16X3 otherwise            */
     HPC_PREC_FP64   = 0,   /* SIMT FP64 fused multiply-adds                        */
@@ -291,6 +295,16 @@ int hpc_smooth_value(hpc_handle h, double* f);
 int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, void* dOmega, int64_t ld_domega,
                  void* dX);
 
+/* The same gradients with dL/dOmega restricted to the entries of the current
+ * iterate: dOmega_vals[e] = grad_loss * G_ij for the e-th entry (i, j) in the
+ * order hpc_get_omega returns them (row_ptr / col), FP64 on the device, nnz
+ * values; G as in hpc_backward (Alg. 1 step 4), formed without a p x p buffer:
+ * (Omega S)_ij from gathers of S (Cov) or from Y^T = Omega X^T and the handle's
+ * copy of X^T (Obs).  dX as hpc_backward (Cov only).  Either output may be NULL.
+ * Synchronises the handle's stream. */
+int hpc_backward_support(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, double* dOmega_vals,
+                         void* dX);
+
 typedef struct {
     int64_t cg_iterations;
     double  rel_residual;     /* ||r|| / ||b|| of the CG solve                     */
@@ -356,11 +370,16 @@ int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dt
  *
  * The first call on a device looks up the array's device address there (with
  * that device current), so make the first call on each device before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents (each call writes everything it reads); calls that overlap on the
- * GPU -- on other streams or from other host threads -- race on it.  The call
- * synchronises the stream before returning (to check the kernel's error word).
- * Errors as hpc_gram; HPC_ERR_NOT_IMPLEMENTED if TMA descriptors are
+ * stream capture.  Under CUDA's default lazy module loading that first call is
+ * also when the device code is loaded and the 64 MiB array is reserved: a
+ * caller with a fixed budget should make it at start-up (or set
+ * CUDA_MODULE_LOADING=EAGER, which reserves it when the library is loaded).
+ * All calls share the array and it keeps the last call's contents (each call
+ * writes everything it reads); calls that overlap on the GPU -- on other
+ * streams or from other host threads -- race on it, including on the kernel's
+ * error word, which also sits in the array.  The call synchronises the stream
+ * before returning (to read that word).  Errors as hpc_gram;
+ * HPC_ERR_NOT_IMPLEMENTED (with hpc_last_error() set) if TMA descriptors are
  * unavailable. */
 #define HPC_GRAM_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t p, float* S, int64_t lds,

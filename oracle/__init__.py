@@ -721,3 +721,10 @@ def objective_from_x(X, omega: sp.csr_matrix, lam1, lam2, chunk=4096) -> float:
         q += float(np.sum(Yc * Yc))
     return -float(np.sum(np.log(d))) + 0.5 * q / n + 0.5 * lam2 * float(np.sum(om.data ** 2)) + \
         penalty_csr(om, lam1)
+
+
+def heldout_loss_from_x(Xval, omega: sp.csr_matrix, chunk=4096) -> float:
+    """L_val(Omega) = -sum log w_ii + ||X_val Omega||_F^2 / (2 n_val): the unpenalised held-out
+    pseudolikelihood loss (heldout_loss) with tr(Omega S_val Omega) = ||X_val Omega||^2 / n_val,
+    for a sparse Omega at large p."""
+    return objective_from_x(Xval, omega, 0.0, 0.0, chunk)

@@ -126,6 +126,7 @@ _SIGS = {
     "hpc_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "hpc_smooth_value": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "hpc_backward": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, C.c_int64, _P]),
+    "hpc_backward_support": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, _P]),
     "hpc_hypergrad": (C.c_int, [_P, _P, C.c_int, C.c_int64, C.c_double, C.c_int64, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(HypergradInfo)]),
     "hpc_destroy": (C.c_int, [_P]),
@@ -463,6 +464,37 @@ class Solver:
         _check(st, "hpc_backward")
         return dO, dX
 
+    def backward_support(self, X=None, grad_loss=1.0, dx=False):
+        """(dL/dOmega at the estimate's entries in CSR order as an FP64 (nnz,) device tensor,
+        dL/dX (n, p) or None) times grad_loss (``hpc_backward_support``)."""
+        import torch
+
+        dev = X.device if X is not None else torch.device("cuda")
+        if X is not None:
+            _matrix(X, self.n, self.p, "X", cuda=True)
+        elif dx:
+            raise ValueError("dx needs X")
+        m = self.nnz()
+        dv = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+        dX = None
+        if dx:
+            dt = torch.float64 if self.info().value_dtype == F64 else torch.float32
+            dX = torch.empty((self.n, self.p), dtype=dt, device=dev)
+        st = self._lib.hpc_backward_support(self._h, C.c_void_p(X.data_ptr()) if X is not None else None,
+                                            _dtype_code(X) if X is not None else F32, float(grad_loss),
+                                            C.c_void_p(dv.data_ptr()),
+                                            C.c_void_p(dX.data_ptr()) if dX is not None else None)
+        _check(st, "hpc_backward_support")
+        return dv[:m], dX
+
+    def set_omega_device(self, row_ptr, col, val):
+        """hpc_set_omega from device tensors: row_ptr (p+1,) int64, col (nnz,) int32, val (nnz,)
+        float32 or float64; a symmetric pattern with every diagonal entry present and positive."""
+        code = F64 if str(val.dtype) == "torch.float64" else F32
+        return _check(self._lib.hpc_set_omega(self._h, int(col.numel()), C.c_void_p(row_ptr.data_ptr()),
+                                              C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()), code, 1),
+                      "hpc_set_omega")
+
     def hypergrad(self, Xval, tol=1e-8, max_iter=20000):
         """(dL_val/dlambda1, dL_val/dlambda2, info) at the current estimate (``hpc_hypergrad``)."""
         _matrix(Xval, None, self.p, "Xval", cuda=True)
@@ -553,36 +585,60 @@ def _make_smooth_loss():
 
     class ConcordSmoothLoss(torch.autograd.Function):
         """L(Omega, X) = -sum log w_ii + tr(Omega S Omega)/2 + lambda2/2 ||Omega||_F^2, S = X^T X / n,
-        at a solver's current estimate, with the library's adjoint as backward.
+        evaluated at the Omega it is given, with the library's adjoint as backward.
 
-        Inputs: X (n, p) device tensor the solver was loaded with; omega, the estimate as either its
-        CSR values (nnz,) from Solver.omega_values() or a dense (p, p) tensor; the solver.  The
-        forward value is computed by the library at the solver's estimate (omega only carries the
-        gradient).  Backward returns dL/dX and dL/dOmega (dense, or gathered on the support for the
-        CSR-values form), both from hpc_backward."""
+        Inputs: X (n, p), the device data the solver was loaded with; omega, either
+        - the values (nnz,) of a matrix with the solver's current CSR pattern
+          (Solver.omega_values() gives the estimate's), or
+        - a dense symmetric (p, p) tensor with a positive diagonal;
+        and the solver.  forward loads omega into the solver as its iterate (hpc_set_omega:
+        it replaces the solver's estimate) and returns f there (hpc_smooth_value); backward
+        returns dL/dX (hpc_backward) and dL/dOmega at the same omega: dense from
+        hpc_backward for the dense form, on the pattern from hpc_backward_support (no p x p
+        buffer) for the values form."""
 
         @staticmethod
         def forward(ctx, X, omega, solver):
+            p = solver.p
+            dev = X.device
+            if tuple(omega.shape) == (p, p):
+                if not torch.equal(omega, omega.t()):
+                    raise ValueError("omega: the smooth loss is defined here for symmetric matrices")
+                nz = omega != 0
+                nz.fill_diagonal_(True)
+                rows, cols = nz.nonzero(as_tuple=True)               # row-major: columns ascending
+                counts = torch.bincount(rows, minlength=p)
+                rp = torch.zeros(p + 1, dtype=torch.int64, device=dev)
+                rp[1:] = torch.cumsum(counts, 0)
+                vals = omega[rows, cols].to(torch.float64)
+                solver.set_omega_device(rp, cols.to(torch.int32).contiguous(), vals.contiguous())
+                ctx.form = "dense"
+            else:
+                rp, ci, cur = solver.omega_values(device=dev)
+                if omega.dim() != 1 or omega.numel() != ci.numel():
+                    raise ValueError(f"omega: expected ({p}, {p}) or the ({ci.numel()},) values of the solver's "
+                                     f"pattern, got {tuple(omega.shape)}")
+                solver.set_omega_device(rp, ci, omega.detach().to(cur.dtype).contiguous())
+                ctx.form = "values"
             ctx.solver = solver
             ctx.save_for_backward(X)
-            ctx.omega_shape = tuple(omega.shape)
             ctx.omega_dtype = omega.dtype
-            return torch.tensor(solver.smooth_value(), dtype=torch.float64, device=X.device)
+            return torch.tensor(solver.smooth_value(), dtype=torch.float64, device=dev)
 
         @staticmethod
         def backward(ctx, gL):
             (X,) = ctx.saved_tensors
             s = ctx.solver
             want_o, want_x = ctx.needs_input_grad[1], ctx.needs_input_grad[0]
-            dO, dX = s.backward(X, float(gL), domega=want_o, dx=want_x)
-            g_om = None
-            if want_o:
-                if ctx.omega_shape == (s.p, s.p):
+            g_om, dX = None, None
+            if ctx.form == "dense":
+                dO, dX = s.backward(X, float(gL), domega=want_o, dx=want_x)
+                if want_o:
                     g_om = dO.to(ctx.omega_dtype)
-                else:
-                    rp, ci, _ = s.omega_values(device=X.device)
-                    rows = torch.repeat_interleave(torch.arange(s.p, device=X.device), rp[1:] - rp[:-1])
-                    g_om = dO[rows, ci.long()].to(ctx.omega_dtype)
+            else:
+                dv, dX = s.backward_support(X, float(gL), dx=want_x)
+                if want_o:
+                    g_om = dv.to(ctx.omega_dtype)
             if want_x:
                 dX = dX.to(X.dtype)
             return dX, g_om, None

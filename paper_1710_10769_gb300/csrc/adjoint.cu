@@ -541,6 +541,23 @@ k_support_combine(int64_t nnz, const int* __restrict__ row, const int* __restric
     if (part) partial_then_scalar(s, part, 1, tol2, cg);
 }
 
+// dL/dOmega on the support, one thread per entry e = (i, j):
+//   out_e = scale ((T_e + T_tr(e))/2 + lambda2 w_e - [i = j] / w_ii),  T = Omega S on the
+// support (Alg. 1 step 4's G restricted to the entries of the iterate).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_support_grad(int64_t nnz, const int* __restrict__ row, const int* __restrict__ ci, const T* __restrict__ cv,
+               const int* __restrict__ tr, const double* __restrict__ Tv, double lam2, double scale,
+               double* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int te = tr[e] >= 0 ? tr[e] : (int)e;
+        const double w = (double)cv[e];
+        double o = 0.5 * (Tv[e] + Tv[te]) + lam2 * w;
+        if (ci[e] == row[e]) o -= 1.0 / w;
+        out[e] = scale * o;
+    }
+}
+
 // block partials of <a, b> (fixed grid-stride order)
 __global__ void __launch_bounds__(256) k_dot_part(int64_t n, const double* a, const double* b, double* part) {
     __shared__ double red[8];
@@ -735,6 +752,12 @@ void launch_support_combine(int64_t nnz, const int* row, Csr<T> om, const int* t
 }
 
 template <typename T>
+void launch_support_grad(int64_t nnz, const int* row, Csr<T> om, const int* tr, const double* Tv, double lam2,
+                         double scale, double* out, cudaStream_t s) {
+    k_support_grad<T><<<cg_part_blocks(nnz), 256, 0, s>>>(nnz, row, om.ci, om.cv, tr, Tv, lam2, scale, out);
+}
+
+template <typename T>
 void launch_support_vectors(int p, int64_t nnz, Csr<T> om, double* omega_d, double* sign_off, cudaStream_t s) {
     k_support_values<T><<<256, 256, 0, s>>>(nnz, om.cv, omega_d);
     k_sign_off<T><<<(p + kW - 1) / kW, 256, 0, s>>>(p, om, sign_off);
@@ -784,6 +807,8 @@ size_t cg_state_bytes() { return sizeof(CgState); }
                                               const double*, double*, const void*, const T*, int64_t, double*,   \
                                               cudaStream_t);                                                     \
     template void launch_support_vectors<T>(int, int64_t, Csr<T>, double*, double*, cudaStream_t);          \
+    template void launch_support_grad<T>(int64_t, const int*, Csr<T>, const int*, const double*, double,      \
+                                         double, double*, cudaStream_t);                                        \
     template int launch_smooth_parts<T>(int, Csr<T>, const double*, double*, double*, cudaStream_t);
 
 HPC_ADJ_INSTANTIATE(float)

@@ -969,7 +969,7 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
 
     if (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) {
         CUDA_TRY(cudaStreamSynchronize(h->stream));
-        const int w = hpc::gram_tc_take_error();
+        const int w = hpc::gram_tc_take_error(h->gram_scratch, xdt, h->n, h->p, prec, h->stream);
         if (w != 0) {
             std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram: bounded wait %d gave up", w);
             return HPC_ERR_DEVICE_TIMEOUT;
@@ -1073,6 +1073,9 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     if (variant != HPC_COV && variant != HPC_OBS) return HPC_ERR_ARG;
     int prec = o.precision;
     if (prec == HPC_PREC_AUTO) prec = (o.value_dtype == HPC_F64) ? HPC_PREC_FP64 : HPC_PREC_BF16X3;
+    // the Obs variant's FP32-class Z product is the chunked BF16X3 split (the SIMT FP32
+    // product would repeat a 2 n p^2 flop GEMM every iteration)
+    if (variant == HPC_OBS && prec == HPC_PREC_FP32 && o.value_dtype == HPC_F32) prec = HPC_PREC_BF16X3;
     if (variant == HPC_OBS && (o.value_dtype != HPC_F32 || (prec != HPC_PREC_BF16X3 && prec != HPC_PREC_TF32))) {
         std::snprintf(g_last_error, sizeof g_last_error,
                       "the Obs variant runs its Z product on tensor cores: FP32 values with BF16X3 or TF32");
@@ -1697,6 +1700,42 @@ int backward_t(hpc_ctx* h, const void* X, int xdt, double grad_loss, void* dOmeg
     return HPC_OK;
 }
 
+// dL/dOmega at the support entries (FP64, CSR order) and optionally dL/dX, at the current
+// iterate.  Cov: (Omega S)_ij by gathers of S; Obs: from Y^T = Omega X^T and the resident X^T.
+template <typename T>
+int backward_support_t(hpc_ctx* h, const void* X, int xdt, double grad_loss, double* dvals, void* dX) {
+    const int p = (int)h->p;
+    const int64_t nnz = h->nnz;
+    if (dvals) {
+        const size_t b_v = align256(nnz * sizeof(double));
+        const size_t b_i = align256(nnz * sizeof(int));
+        const size_t b_y = h->S ? 0 : align256((size_t)p * h->ldx * sizeof(T));
+        STATUS_TRY(adj_reserve(h, 2 * b_v + 2 * b_i + b_y));
+        uint8_t* q = static_cast<uint8_t*>(h->adj_buf);
+        double* om_d = reinterpret_cast<double*>(q); q += b_v;
+        double* Tv = reinterpret_cast<double*>(q); q += b_v;
+        int* tr = reinterpret_cast<int*>(q); q += b_i;
+        int* rowid = reinterpret_cast<int*>(q); q += b_i;
+        hpc::Csr<T> om = cur_csr<T>(h);
+        hpc::launch_row_info<T>(p, om, h->rinfo, as<T>(h->rdv), h->stream);
+        hpc::launch_transpose_index<T>(p, om, tr, rowid, h->stream);
+        hpc::launch_support_vectors<T>(p, nnz, om, om_d, Tv, h->stream);      // Tv: scratch for the signs
+        if (h->S) {
+            hpc::launch_support_product<T>(p, om, h->rinfo, om_d, static_cast<const T*>(h->S), h->ld, Tv, h->stream);
+        } else {
+            T* yt = reinterpret_cast<T*>(q);
+            const T* xt = reinterpret_cast<const T*>(h->xt);
+            hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), xt, h->ldx, h->ldx, yt, h->ldx, h->stream);
+            hpc::launch_support_sddmm<T>(p, om, yt, xt, h->ldx, h->n, Tv, h->stream);
+        }
+        hpc::launch_support_grad<T>(nnz, rowid, om, tr, Tv, h->lam2, grad_loss, dvals, h->stream);
+        CUDA_TRY(cudaGetLastError());
+    }
+    if (dX) return backward_t<T>(h, X, xdt, grad_loss, nullptr, h->p, dX);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return HPC_OK;
+}
+
 template <typename T>
 int hypergrad_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double cg_tol, int64_t cg_max, double* dl1,
                 double* dl2, hpc_hypergrad_info* info) {
@@ -2063,6 +2102,19 @@ int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, v
                              : backward_t<float>(h, X, xdt, grad_loss, dOmega, ld_domega, dX);
 }
 
+int hpc_backward_support(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, double* dOmega_vals,
+                         void* dX) {
+    if (!h || !h->loaded || (dX && !X) || !valid_dtype(xdt) || !std::isfinite(grad_loss)) return HPC_ERR_ARG;
+    if (dX && !h->S) return HPC_ERR_NOT_IMPLEMENTED;     // dL/dX: Cov variant (as hpc_backward)
+    if (dX && h->n > hpc::kTransposeMaxRows) {
+        std::snprintf(g_last_error, sizeof g_last_error, "dL/dX transposes X: n <= %lld",
+                      (long long)hpc::kTransposeMaxRows);
+        return HPC_ERR_ARG;
+    }
+    return h->vdt == HPC_F64 ? backward_support_t<double>(h, X, xdt, grad_loss, dOmega_vals, dX)
+                             : backward_support_t<float>(h, X, xdt, grad_loss, dOmega_vals, dX);
+}
+
 int hpc_hypergrad(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double cg_tol, int64_t cg_max_iter,
                   double* dlambda1, double* dlambda2, hpc_hypergrad_info* info) {
     if (!h || !h->loaded || !Xval || nval < 1 || !valid_dtype(xdt) || !(cg_tol > 0.0) || cg_max_iter < 1 ||
@@ -2119,11 +2171,19 @@ int hpc_gram(const void* X, hpc_dtype xdt, int64_t n, int64_t p, void* S, hpc_dt
     void* scratch = nullptr;
     if (need) CUDA_TRY(cudaMallocAsync(&scratch, need, s));
     cudaError_t e = hpc::gram_tc(X, xdt, n, p, static_cast<float*>(S), lds, precision, scratch, need, s, nullptr);
+    // the launch's error word sits in this call's scratch: read it before the scratch is freed
+    const int w = e == cudaSuccess ? hpc::gram_tc_take_error(scratch, xdt, n, p, precision, s) : 0;
     if (scratch) cudaFreeAsync(scratch, s);
-    if (e == cudaErrorNotSupported) return HPC_ERR_NOT_IMPLEMENTED;
+    if (e == cudaErrorNotSupported) {
+        std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram not available for this shape");
+        return HPC_ERR_NOT_IMPLEMENTED;
+    }
     if (e != cudaSuccess) { set_cuda_error(e, "gram_tc", __LINE__); return HPC_ERR_CUDA; }
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (hpc::gram_tc_take_error() != 0) return HPC_ERR_DEVICE_TIMEOUT;
+    if (w < 0) { set_cuda_error(cudaGetLastError(), "gram_tc error word", __LINE__); return HPC_ERR_CUDA; }
+    if (w != 0) {
+        std::snprintf(g_last_error, sizeof g_last_error, "tensor-core Gram: bounded wait %d gave up", w);
+        return HPC_ERR_DEVICE_TIMEOUT;
+    }
     return HPC_OK;
 }
 

@@ -52,7 +52,6 @@ constexpr long long kWaitLimit = 1ll << 26;
 
 enum : int { kModeBf16 = 0, kModeBf16x3 = 1, kModeTf32 = 2 };
 
-__device__ int g_gram_error = 0;   // first error word recorded by any CTA
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -80,7 +79,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: false on timeout or when another role raised the abort flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int code) {
+// The first wait to give up records its code in the launch's error word.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int code,
+                                          int* err) {
     for (long long it = 0; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255) == 255) {
@@ -89,7 +90,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
         }
     }
     *abort_flag = 1;
-    atomicCAS(&g_gram_error, 0, code);
+    atomicCAS(err, 0, code);
     return false;
 }
 
@@ -251,16 +252,18 @@ constexpr int kMinLaunchRegs = (128 * kRegsSmall + 32 * kEpiWarps * kRegsEpi + k
 constexpr int kTileRing = 4;
 constexpr int kHalf = kBN / 2;          // columns per epilogue warp
 
-// The tile counter of k_gram_tc_persist, reset before each launch (a kernel, so the
-// reset is not queued behind copies on a copy engine).
-__global__ void k_zero_counter(unsigned* ctr) { *ctr = 0u; }
+// The launch's control words in the scratch's slack: the shared tile counter and the
+// error word of the bounded waits, reset before each launch (by a kernel, so the reset
+// is not queued behind copies on a copy engine).  Each scratch has its own, so an error
+// is reported by the call whose launch hit it.
+__global__ void k_zero_ctl(unsigned* ctl) { ctl[0] = 0u; ctl[1] = 0u; }
 
 template <int MODE>
 __global__ void __launch_bounds__(kPersistThreads, 1)
 k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                   const int2* __restrict__ tiles, int ntiles, int k_tiles, int64_t p, int64_t n,
-                  float* __restrict__ S, int64_t lds, unsigned* __restrict__ tile_ctr, int dynamic, int chunk_kt,
-                  int lead_kt) {
+                  float* __restrict__ S, int64_t lds, unsigned* __restrict__ tile_ctr, int* __restrict__ err,
+                  int dynamic, int chunk_kt, int lead_kt) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -311,7 +314,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
             for (int lt = 0; ok; ++lt) {
                 // the next tile of the shared order, published to the MMA and epilogue roles
                 const int slot = lt % kTileRing;
-                if (!mbar_wait(&tid_empty[slot], ((uint32_t)(lt / kTileRing) & 1u) ^ 1u, abort_flag, 15)) break;
+                if (!mbar_wait(&tid_empty[slot], ((uint32_t)(lt / kTileRing) & 1u) ^ 1u, abort_flag, 15, err)) break;
                 // dynamic: the counter shared by the CTAs; static: tiles blockIdx.x + lt * grid
                 const unsigned t = dynamic ? atomicAdd(tile_ctr, 1u)
                                            : (unsigned)blockIdx.x + (unsigned)lt * (unsigned)gridDim.x;
@@ -324,7 +327,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
                 for (int kt = 0; kt < k_tiles; ++kt, ++g) {
                     const int s = (int)(g % C::kStages);
                     const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 11)) { ok = false; break; }
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, 11, err)) { ok = false; break; }
                     uint8_t* st = smem + s * C::kStageBytes;
                     mbar_expect_tx(&full[s], C::kStageBytes);
                     const int kc = kt * C::kBK;
@@ -346,13 +349,13 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
             bool ok = true;
             for (int lt = 0; ok; ++lt) {
                 const int slot = lt % kTileRing;
-                if (!mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 16)) break;
+                if (!mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 16, err)) break;
                 const int tt = s_tid[slot];
                 mbar_arrive_local(&tid_empty[slot]);
                 if (tt < 0) break;
                 for (int c = 0; c < nch && ok; ++c, ++gc) {
                     const int b = (int)(gc & 1);
-                    if (!mbar_wait(&acc_empty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abort_flag, 12)) { ok = false; break; }
+                    if (!mbar_wait(&acc_empty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abort_flag, 12, err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t acc = tmem + (uint32_t)(b * kTmemCols);
                     const int kt0 = chunk_start(c, k_tiles, chunk_kt, lead_kt);
@@ -360,7 +363,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
                     for (int kt = kt0; kt < kt1; ++kt, ++g) {
                         const int s = (int)(g % C::kStages);
                         const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
-                        if (!mbar_wait(&full[s], ph, abort_flag, 13)) { ok = false; break; }
+                        if (!mbar_wait(&full[s], ph, abort_flag, 13, err)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t st = smem_u32(smem + s * C::kStageBytes);
                         const uint32_t a_hi = st, b_hi = st + kABytes;
@@ -405,7 +408,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
             if (et == 0) {
                 const int slot = lt % kTileRing;
                 int tt = -1;
-                if (!*abort_flag && mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 17)) {
+                if (!*abort_flag && mbar_wait(&tid_full[slot], (uint32_t)(lt / kTileRing) & 1u, abort_flag, 17, err)) {
                     tt = s_tid[slot];
                     mbar_arrive_local(&tid_empty[slot]);
                 }
@@ -421,7 +424,7 @@ k_gram_tc_persist(const __grid_constant__ CUtensorMap map_hi, const __grid_const
             for (int c = 0; c < nch; ++c, ++gc) {
                 const int b = (int)(gc & 1);
                 bool got = have && !*abort_flag &&
-                           mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u, abort_flag, 14);
+                           mbar_wait(&acc_full[b], (uint32_t)(gc >> 1) & 1u, abort_flag, 14, err);
                 got = __all_sync(kFull, got);
                 if (!got) { have = false; continue; }
                 tc_fence_after();
@@ -762,6 +765,11 @@ std::vector<int2> tile_order(int64_t p_pad, int band) {
     return t;
 }
 
+// The tile counter and the error word: after the tile list, in the scratch's slack.
+unsigned* ctl_words(const int2* tiles, const Geometry& g) {
+    return reinterpret_cast<unsigned*>((reinterpret_cast<uintptr_t>(tiles + g.ntiles) + 255) & ~uintptr_t(255));
+}
+
 bool make_map(CUtensorMap* m, void* base, int mode, const Geometry& g) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -820,12 +828,11 @@ cudaError_t launch_mode(const Geometry& g, void* hi, void* lo, const int2* tiles
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const int grid = (int)std::min<int64_t>(g.ntiles, sms);
-    // the shared tile counter sits after the tile list, in the scratch's slack
-    unsigned* ctr = reinterpret_cast<unsigned*>(
-        (reinterpret_cast<uintptr_t>(tiles + g.ntiles) + 255) & ~uintptr_t(255));
-    if (dynamic) k_zero_counter<<<1, 1, 0, s>>>(ctr);
+    unsigned* ctl = ctl_words(tiles, g);
+    k_zero_ctl<<<1, 1, 0, s>>>(ctl);
     k_gram_tc_persist<MODE><<<grid, kPersistThreads, C::kSmem, s>>>(mh, ml, tiles, (int)g.ntiles, k_tiles, p, n, S,
-                                                                   lds, ctr, dynamic, chunk_kt, lead_kt);
+                                                                   lds, ctl, reinterpret_cast<int*>(ctl + 1),
+                                                                   dynamic, chunk_kt, lead_kt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (after_kernel && (e = cudaEventRecord(after_kernel, s)) != cudaSuccess) return e;
     return launch_mirror(S, lds, p, m1, nbm, s);
@@ -936,13 +943,13 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
                                         after_kernel);
 }
 
-int gram_tc_take_error() {
+int gram_tc_take_error(const void* scratch, int xdt, int64_t n, int64_t p, int precision, cudaStream_t s) {
+    const Geometry g = geometry(xdt, n, p, precision);
+    const int2* tiles = reinterpret_cast<const int2*>(static_cast<const uint8_t*>(scratch) + g.pieces * g.panel_bytes);
+    const int* err = reinterpret_cast<const int*>(ctl_words(tiles, g) + 1);
     int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_gram_error, sizeof v) != cudaSuccess) return -1;
-    if (v != 0) {
-        const int zero = 0;
-        cudaMemcpyToSymbol(g_gram_error, &zero, sizeof zero);
-    }
+    if (cudaMemcpyAsync(&v, err, sizeof v, cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
     return v;
 }
 
@@ -958,7 +965,10 @@ int gram_tc_take_error() {
 // cudaMalloc/cudaFree would synchronise the device.
 //
 // The array costs kNoAllocScratchBytes of memory on every GPU that loads the
-// library, held until the process exits.  All calls share it and it keeps the
+// library's device code, held until the process exits.  Under CUDA's default lazy
+// module loading that happens at the first call on each device (the symbol lookup
+// loads the module), so that first call reserves the 64 MiB: make it at start-up,
+// or load modules eagerly (CUDA_MODULE_LOADING=EAGER).  All calls share it and it keeps the
 // last call's contents: every byte a call reads is first written by that call
 // (the panels, padding included, and the tile list), and calls that overlap on
 // the GPU (other streams, other host threads) race on it.
@@ -1019,7 +1029,10 @@ extern "C" int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t
         set_last_error(msg);
         return HPC_ERR_ARG;
     }
-    if (!encode_fn()) return HPC_ERR_NOT_IMPLEMENTED;
+    if (!encode_fn()) {
+        set_last_error("hpc_gram_noalloc: the driver's TMA descriptor encoder is not available");
+        return HPC_ERR_NOT_IMPLEMENTED;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     void* base_v = nullptr;
     cudaError_t e = noalloc_base(&base_v);
@@ -1042,14 +1055,24 @@ extern "C" int hpc_gram_noalloc(const void* X, hpc_dtype xdt, int64_t n, int64_t
         else if (mode == kModeBf16x3) e = launch_mode<kModeBf16x3>(g, hi, lo, tiles, n, p, S, lds, s);
         else e = launch_mode<kModeTf32>(g, hi, lo, tiles, n, p, S, lds, s);
     }
-    if (e == cudaErrorNotSupported) return HPC_ERR_NOT_IMPLEMENTED;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaErrorNotSupported) {
+        set_last_error("hpc_gram_noalloc: the tensor-core Gram is not available for this shape or build");
+        return HPC_ERR_NOT_IMPLEMENTED;
+    }
+    // the launch's error word sits in the static scratch (shared by overlapping calls)
+    const int w = e == cudaSuccess ? gram_tc_take_error(base_v, xdt, n, p, precision, s) : 0;
+    if (e == cudaSuccess && w < 0) e = cudaGetLastError();
     if (e != cudaSuccess) {
         char msg[256];
         std::snprintf(msg, sizeof msg, "hpc_gram_noalloc: %s", cudaGetErrorString(e));
         set_last_error(msg);
         return HPC_ERR_CUDA;
     }
-    if (gram_tc_take_error() != 0) return HPC_ERR_DEVICE_TIMEOUT;
+    if (w != 0) {
+        char msg[128];
+        std::snprintf(msg, sizeof msg, "hpc_gram_noalloc: bounded wait %d gave up", w);
+        set_last_error(msg);
+        return HPC_ERR_DEVICE_TIMEOUT;
+    }
     return HPC_OK;
 }

@@ -220,7 +220,6 @@ bool obs_make_maps(int precision, const void* y_hi, const void* y_lo, const void
 cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2* pairs, int64_t npairs, int64_t n,
                              int p, const int* rp, const int* ci, const float* cv, Emit<float> em,
                              Ctrl* ctrl, cudaStream_t s, int64_t chunk_k = 0, int64_t lead_k = 0);
-int obs_take_error();
 
 // ---------------------------------------------------------------- differentiation (adjoint.cu)
 template <typename T>
@@ -252,6 +251,10 @@ void launch_support_combine(int64_t nnz, const int* row, Csr<T> om, const int* t
                             double lam2, int mode, double* out, double* part, double tol2, void* cg, cudaStream_t s);
 template <typename T>
 void launch_support_vectors(int p, int64_t nnz, Csr<T> om, double* omega_d, double* sign_off, cudaStream_t s);
+// scale ((T_e + T_tr(e))/2 + lambda2 w_e - [i=j]/w_ii) per support entry (dL/dOmega on the support)
+template <typename T>
+void launch_support_grad(int64_t nnz, const int* row, Csr<T> om, const int* tr, const double* Tv, double lam2,
+                         double scale, double* out, cudaStream_t s);
 int cg_part_blocks(int64_t n);
 void launch_dot_part(int64_t n, const double* a, const double* b, double* part, cudaStream_t s);
 void launch_cg_scalar(const double* part, int nb, int stage, double tol2, void* cg, cudaStream_t s);
@@ -299,7 +302,9 @@ __host__ __device__ __forceinline__ int num_chunks(int k_tiles, int chunk, int l
 
 size_t gram_tc_scratch_bytes(int xdt, int64_t n, int64_t p, int precision);
 // Error word of the tensor-core Gram's bounded waits (0 = none); reading it resets it.
-int gram_tc_take_error();
+// The error word of the last tensor-core Gram launched on this scratch (0: none; else the
+// code of the bounded wait that gave up); synchronises s.
+int gram_tc_take_error(const void* scratch, int xdt, int64_t n, int64_t p, int precision, cudaStream_t s);
 
 // Raise a kernel's dynamic shared-memory limit once per device (the attribute call
 // is a host round trip that must stay out of the iteration loop).

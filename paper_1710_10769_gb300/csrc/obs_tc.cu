@@ -121,7 +121,6 @@ constexpr int kRegsSmall = 56;
 constexpr int kRegsEpi = 216;
 constexpr int kMinLaunchRegs = (128 * kRegsSmall + 32 * kEpiWarps * kRegsEpi + kObsThreads - 1) / kObsThreads;
 
-__device__ int g_obs_error = 0;
 
 // 32 TMEM lanes x 16 consecutive 32-bit columns: thread t gets lane (base + t).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -225,7 +224,6 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                             const int s = (int)(g % C::kStages);
                             const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
                             if (!ptx::mbar_wait_bounded(&empty[s], ph ^ 1u, abort_flag, kWaitLimit)) {
-                                atomicCAS(&g_obs_error, 0, 1);
                                 ok = false;
                                 break;
                             }
@@ -255,7 +253,6 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                     const int b = (int)(gc & 1);
                     if (!ptx::mbar_wait_bounded(&acc_empty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abort_flag,
                                                 kWaitLimit)) {
-                        atomicCAS(&g_obs_error, 0, 3);
                         ok = false;
                         break;
                     }
@@ -268,7 +265,6 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                             const int s = (int)(g % C::kStages);
                             const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
                             if (!ptx::mbar_wait_bounded(&full[s], ph, abort_flag, kWaitLimit)) {
-                                atomicCAS(&g_obs_error, 0, 2);
                                 ok = false;
                                 break;
                             }
@@ -532,14 +528,5 @@ cudaError_t launch_obs_pairs(int precision, const CUtensorMap* maps, const int2*
     return cudaGetLastError();
 }
 
-int obs_take_error() {
-    int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_obs_error, sizeof v) != cudaSuccess) return -1;
-    if (v) {
-        const int z = 0;
-        cudaMemcpyToSymbol(g_obs_error, &z, sizeof z);
-    }
-    return v;
-}
 
 }  // namespace hpc

@@ -116,6 +116,66 @@ def test_autograd_function(lib, form):
     s.close()
 
 
+@pytest.mark.parametrize("form", ["values", "dense"])
+def test_autograd_evaluates_at_the_given_omega(lib, form):
+    """A perturbed omega (symmetric, on the estimate's pattern) changes the loss and its
+    gradients to the oracle's at that omega: forward loads omega into the solver."""
+    import torch
+
+    X = small_problem(150, 100, 3.0, 47).astype(np.float32)
+    lam2 = 0.1
+    s, Xt = _solved(lib, X, 0.12, lam2)
+    Om = s.omega_dense()
+    f0 = s.smooth_value()
+    rng = np.random.default_rng(3)
+    P = np.where(Om != 0, rng.uniform(-0.05, 0.05, Om.shape), 0.0)
+    Om2 = (Om + (P + P.T) / 2).astype(np.float32).astype(np.float64)
+    Xg = Xt.clone().requires_grad_(True)
+    rp, ci, _ = s.omega_values()
+    rows = np.repeat(np.arange(150), np.diff(rp.cpu().numpy()))
+    cols = ci.cpu().numpy()
+    if form == "values":
+        om = torch.as_tensor(Om2[rows, cols], dtype=torch.float32, device="cuda").requires_grad_(True)
+    else:
+        om = torch.as_tensor(Om2, dtype=torch.float32, device="cuda").requires_grad_(True)
+    loss = lib.concord_smooth_loss(Xg, om, s)
+    X64 = X.astype(np.float64)
+    ref = oracle.smooth_loss(X64, Om2, lam2)
+    assert float(loss.detach()) == pytest.approx(ref, rel=1e-6)
+    assert abs(float(loss.detach()) - f0) > 1e-3 * abs(f0)
+    loss.backward()
+    rO, rX = oracle.smooth_loss_grads(X64, Om2, lam2)
+    go = om.grad.double().cpu().numpy()
+    refo = rO[rows, cols] if form == "values" else rO
+    assert np.max(np.abs(go - refo)) <= REL * np.max(np.abs(refo))
+    gx = Xg.grad.double().cpu().numpy()
+    assert np.max(np.abs(gx - rX)) <= REL * np.max(np.abs(rX))
+    with pytest.raises(ValueError):
+        A = torch.as_tensor(Om2, dtype=torch.float32, device="cuda")
+        A[0, 1] += 0.5
+        lib.concord_smooth_loss(Xt, A, s)
+    s.close()
+
+
+def test_support_gradient_of_the_obs_variant(lib):
+    """hpc_backward_support on an Obs handle (no S): dL/dOmega on the support from
+    Y^T = Omega X^T and the resident X^T, against the oracle's dense gradient."""
+    import torch
+
+    X = small_problem(140, 90, 3.0, 48).astype(np.float32)
+    lam2 = 0.1
+    with lib.Solver(torch.as_tensor(X).cuda(), 0.12, lam2, variant=lib.OBS, precision=lib.PREC_FP32, eps=3e-7,
+                    max_iter=3000) as s:
+        s.solve()
+        Om = s.omega_dense()
+        dv, _ = s.backward_support(None, 2.0)
+        rp, ci, _ = s.omega_values()
+    rows = np.repeat(np.arange(140), np.diff(rp.cpu().numpy()))
+    rO, _ = oracle.smooth_loss_grads(X.astype(np.float64), Om, lam2)
+    ref = 2.0 * rO[rows, ci.cpu().numpy()]
+    assert np.max(np.abs(dv.cpu().numpy() - ref)) <= REL * max(np.max(np.abs(ref)), 1.0)
+
+
 def test_hypergrad_matches_dense_oracle(lib):
     import torch
 
@@ -225,4 +285,71 @@ def test_differentiation_workload_full_size(lib):
     dx_ref = (Y @ csr) / w.n
     dx_got = dX[torch.as_tensor(rr).cuda()].double().cpu().numpy()
     assert np.max(np.abs(dx_got - dx_ref)) <= REL * np.max(np.abs(dx_ref))
+    s.close()
+
+
+@pytest.mark.slow
+def test_hypergrad_central_differences_full_size(lib):
+    """p = 16384, n = 4096 train + 2048 held-out: hpc_hypergrad against central differences
+    (h = 1e-3) of the held-out loss at GPU re-solves with lambda1 +- h and lambda2 +- h,
+    warm-started from the estimate.  The implicit-function gradient holds while the support
+    stays fixed, so a direction counts only if the four re-solves keep the support; dL/dX
+    (exactly quadratic in X) against central differences of the oracle's loss at three
+    entries.  The held-out loss is evaluated by the oracle from X_val."""
+    import json
+    import os
+
+    import scipy.sparse as sp
+
+    from workloads import HELDOUT_STREAM, cast_x, sample_x_cuda
+
+    w = WORKLOADS["adjoint_p16384"]
+    om0 = omega0_for(w)
+    Xtr = cast_x(sample_x_cuda(om0, w.n, w.seed), "f32")
+    Xva = cast_x(sample_x_cuda(om0, 2048, w.seed, stream=HELDOUT_STREAM), "f32")
+    Xvh = Xva.cpu().numpy()
+    eps = 1e-8
+    s = lib.Solver(Xtr, w.lambda1, w.lambda2, precision=lib.PREC_FP32, eps=eps, max_iter=20000)
+    s.solve()
+    d1, d2, info = s.hypergrad(Xva, tol=1e-12)
+    base = s.get_omega()
+    base_sp = base.to_scipy(w.p)
+    pattern = (base_sp != 0)
+    h = 1e-3
+    fd, same = {}, {}
+    for name, (l1, l2) in {"l1+": (w.lambda1 + h, w.lambda2), "l1-": (w.lambda1 - h, w.lambda2),
+                           "l2+": (w.lambda1, w.lambda2 + h), "l2-": (w.lambda1, w.lambda2 - h)}.items():
+        s.set_omega(base)
+        s.set_lambda(l1, l2)
+        s.solve()
+        est = s.get_omega().to_scipy(w.p)
+        same[name] = bool(((est != 0) != pattern).nnz == 0)
+        fd[name] = oracle.heldout_loss_from_x(Xvh, est)
+    g1 = (fd["l1+"] - fd["l1-"]) / (2 * h)
+    g2 = (fd["l2+"] - fd["l2-"]) / (2 * h)
+    rec = {"workload": w.name, "hypergrad": [d1, d2], "central_differences": [g1, g2],
+           "support_constant": same, "cg_iterations": info["cg_iterations"]}
+    if os.environ.get("HPC_REPORT_DIR"):
+        with open(os.path.join(os.environ["HPC_REPORT_DIR"], "hypergrad_fd.json"), "w") as fh:
+            json.dump(rec, fh, default=float)
+    if same["l1+"] and same["l1-"]:
+        assert d1 == pytest.approx(g1, rel=1e-4, abs=1e-4 * abs(d2)), rec
+    if same["l2+"] and same["l2-"]:
+        assert d2 == pytest.approx(g2, rel=1e-4, abs=1e-4 * abs(d1)), rec
+    assert any(same.values()), rec
+    # dL/dX at the base estimate against central differences of the oracle's loss (lambda1 = 0
+    # in objective_from_x leaves the smooth part)
+    s.set_omega(base)
+    s.set_lambda(w.lambda1, w.lambda2)
+    _, dX = s.backward(Xtr, domega=False)
+    Xh = Xtr.cpu().numpy().astype(np.float64)
+    for (k, j) in [(0, 0), (17, 9001), (4095, 16383)]:
+        vals = []
+        for sgn in (1, -1):
+            Xp = Xh.copy()
+            Xp[k, j] += sgn * h
+            vals.append(oracle.objective_from_x(Xp, base_sp, 0.0, w.lambda2))
+        fdx = (vals[0] - vals[1]) / (2 * h)
+        got = float(dX[k, j])
+        assert got == pytest.approx(fdx, rel=1e-4, abs=1e-6), (k, j, got, fdx)
     s.close()

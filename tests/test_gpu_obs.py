@@ -59,12 +59,15 @@ def test_obs_tf32_runs_and_is_close(lib):
     assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-2
 
 
-def test_obs_rejects_unsupported_modes(lib):
+def test_obs_modes(lib):
+    """PREC_FP32 selects the chunked BF16X3 Z product (FP32-class); FP64 values are Cov only."""
     import torch
 
     X = torch.zeros((8, 16), device="cuda")
+    with lib.Solver(X, 0.1, 0.1, variant=lib.OBS, precision=lib.PREC_FP32) as s:
+        assert s.precision_used() == lib.PREC_BF16X3
     with pytest.raises(lib.HpcError) as e:
-        lib.Solver(X, 0.1, 0.1, variant=lib.OBS, precision=lib.PREC_FP32)
+        lib.Solver(X.double(), 0.1, 0.1, variant=lib.OBS, precision=lib.PREC_FP64, value_dtype=lib.F64)
     assert e.value.status == lib.ERR_NOT_IMPLEMENTED
 
 

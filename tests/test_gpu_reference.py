@@ -42,7 +42,7 @@ def fp32_case(lib):
 
 
 @pytest.mark.parametrize("variant,precision,eps", [("cov", "fp32", 1e-7), ("cov", "bf16x3", 1e-7),
-                                                   ("obs", "bf16x3", 3e-7)])
+                                                   ("obs", "fp32", 3e-7)])
 def test_fp32_workload_against_fp64_reference(lib, fp32_case, variant, precision, eps):
     w, ref = fp32_case["w"], fp32_case["ref"]
     v = lib.COV if variant == "cov" else lib.OBS
