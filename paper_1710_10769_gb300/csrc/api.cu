@@ -967,7 +967,8 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         h->ms_gram_kernel = mk;
     }
 
-    if (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32) {
+    if (h->variant == HPC_COV && (prec == HPC_PREC_BF16X3 || prec == HPC_PREC_TF32)) {
+        // the tensor-core Gram's error word, in the scratch it ran on (the Obs variant has no Gram)
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         const int w = hpc::gram_tc_take_error(h->gram_scratch, xdt, h->n, h->p, prec, h->stream);
         if (w != 0) {

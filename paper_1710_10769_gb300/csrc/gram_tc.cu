@@ -944,6 +944,7 @@ cudaError_t gram_tc(const void* X, int xdt, int64_t n, int64_t p, float* S, int6
 }
 
 int gram_tc_take_error(const void* scratch, int xdt, int64_t n, int64_t p, int precision, cudaStream_t s) {
+    if (!scratch) return 0;                 // no Gram ran on this scratch
     const Geometry g = geometry(xdt, n, p, precision);
     const int2* tiles = reinterpret_cast<const int2*>(static_cast<const uint8_t*>(scratch) + g.pieces * g.panel_bytes);
     const int* err = reinterpret_cast<const int*>(ctl_words(tiles, g) + 1);
