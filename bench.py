@@ -292,6 +292,98 @@ def run_row(args):
         s.close()
         return 0
 
+    if args.row == "select":
+        # model selection over the 32-point lambda1 grid of the path workload: the path, the
+        # held-out loss of every point on the device, support recovery against Omega0
+        from paper_1710_10769_gb300.selection import select_lambda1
+
+        w = WORKLOADS["path_p8192"]
+        lam = sorted(PATH_LAMBDA1, reverse=True)
+        om0 = omega0_for(w)
+        X = make_x(w, device="cuda")
+        Xv = cast_x(sample_x_cuda(om0, w.n // 2, w.seed, stream=HELDOUT_STREAM), "f32")
+        s = hpc.Solver(X, lam[0], PATH_LAMBDA2, eps=w.eps, max_iter=100000)
+        for _ in range(args.warmup):
+            s.load_x(X)
+            select_lambda1(s, Xv, lam, PATH_LAMBDA2)
+        ms = 0.0
+        with ClockSampler(0) as clk:
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.load_x(X)
+                sel = select_lambda1(s, Xv, lam, PATH_LAMBDA2)
+                torch.cuda.synchronize()
+                ms += (time.perf_counter() - t0) * 1000.0
+        from paper_1710_10769_gb300.selection import support_recovery
+
+        s.load_x(X)
+        sel = select_lambda1(s, Xv, lam, PATH_LAMBDA2, truth=om0)
+        table = [{"lambda1": l1, "heldout": hl, "nnz": pt["nnz"], "iterations": pt["iterations"],
+                  "ppv": rc["ppv"], "fdr": rc["fdr"], "tpr": rc["tpr"], "pairs": rc["pairs"]}
+                 for l1, hl, pt, rc in zip(sel["lambda1"], sel["heldout"], sel["points"], sel["recovery"])]
+        best_ppv = max(table, key=lambda r: (r["ppv"] if r["tpr"] > 0 else 0, r["tpr"]))
+        _line("model selection over 32 lambda1 on p=8192 n=4096 (held-out n=2048): ms per selection", ms / args.steps,
+              "ms", ms / args.steps, args, False, "f32",
+              {"workload": "path_p8192", "p": w.p, "n": w.n, "n_val": w.n // 2, "points": len(lam),
+               "lambda2": PATH_LAMBDA2, "timing": "host clock around load + path + held-out losses"},
+              None, clk.summary(), None, None, selected={"lambda1": sel["lambda1"][sel["best"]], **table[sel["best"]]},
+              best_ppv_point=best_ppv, table=table)
+        s.close()
+        return 0
+
+    if args.row == "crossover":
+        # One GPU's Fig. 2 (Section 4): p = 40000, n = 100 ... 12800, chain and random graphs,
+        # time to converge of Cov (Gram + iterations) and Obs (Z every iteration), with
+        # lambda1 = sqrt(2 log p / n) (the noise level of S's off-diagonal entries), lambda2 = 0.1.
+        from workloads import omega0_banded, omega0_random
+
+        p = 40000
+        ns = [100, 200, 400, 800, 1600, 3200, 6400, 12800]
+        rows = []
+        with ClockSampler(0) as clk:
+            for graph in ("chain", "random"):
+                om0 = omega0_banded(p, 1, 5) if graph == "chain" else omega0_random(p, 8.0, 5)
+                for n in ns:
+                    X = cast_x(sample_x_cuda(om0, n, 5), "f32")
+                    lam1 = math.sqrt(2.0 * math.log(p) / n)
+                    rec = {"graph": graph, "n": n, "lambda1": lam1}
+                    for vname, v in (("cov", hpc.COV), ("obs", hpc.OBS)):
+                        s = hpc.Solver(None, lam1, 0.1, variant=v, n=n, p=p, xdtype=hpc.F32, eps=1e-6,
+                                       max_iter=20000, precision=hpc.PREC_FP32 if v == hpc.OBS else hpc.PREC_BF16X3)
+                        for rep in range(2):            # the first is a warm-up (graph capture, first-use costs)
+                            torch.cuda.synchronize()
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            e0.record(stream)
+                            s.load_x(X)
+                            st = s.solve().as_dict()
+                            e1.record(stream)
+                            torch.cuda.synchronize()
+                        rec[vname] = {"ms": e0.elapsed_time(e1), "iterations": st["iterations"],
+                                      "trials": st["ls_trials"], "nnz": st["nnz"], "status": st["status"]}
+                        s.close()
+                    sc = rec["cov"]["iterations"]
+                    tc = rec["cov"]["trials"] / max(sc, 1)
+                    dc = rec["cov"]["nnz"] / p
+                    auto, _, _ = hpc.choose_variant(n, p)
+                    meas, cc, co = hpc.choose_variant(n, p, sc, tc, dc, 0.0)
+                    rec["faster"] = "cov" if rec["cov"]["ms"] < rec["obs"]["ms"] else "obs"
+                    rec["auto"] = "cov" if auto == hpc.COV else "obs"
+                    rec["lemma_with_measured_s_t_d"] = "cov" if meas == hpc.COV else "obs"
+                    rec["lemma_flops"] = lemma31_flops(n, p, sc, tc, dc)
+                    rows.append(rec)
+                    print(json.dumps(rec), file=sys.stderr, flush=True)
+                    del X
+                    torch.cuda.empty_cache()
+        agree = sum(r["auto"] == r["faster"] for r in rows)
+        total_ms = sum(min(r["cov"]["ms"], r["obs"]["ms"]) for r in rows)
+        _line("Cov vs Obs crossover at p=40000, n=100..12800 (ms of the AUTO choice summed over the sweep)",
+              sum(r[r["auto"]]["ms"] for r in rows), "ms", total_ms, args, False, "f32",
+              {"workload": "crossover_p40000", "p": p, "n": ns, "graphs": ["chain (bandwidth 1)", "random (d = 8)"],
+               "lambda1": "sqrt(2 log p / n)", "lambda2": 0.1, "timing": "CUDA events around load + solve"},
+              None, clk.summary(), None, None, auto_picks_faster=f"{agree}/{len(rows)}", sweep=rows)
+        return 0
+
     if args.row == "batch":
         Xs = [make_x(wk, device="cuda") for wk in BATCH_PROBLEMS]
         streams = [torch.cuda.Stream() for _ in BATCH_PROBLEMS]
@@ -515,7 +607,7 @@ def main(argv=None):
     ap.add_argument("--x-dtype", default="workload", choices=["workload", "f32", "bf16"],
                     help="store X in this dtype instead of the workload's (profiling the one-product BF16 Gram "
                          "at sizes a full ncu capture allows)")
-    ap.add_argument("--row", default=None, choices=["path", "batch", "adjoint", "obs"],
+    ap.add_argument("--row", default=None, choices=["path", "batch", "adjoint", "obs", "select", "crossover"],
                     help="time a further row of the hot path instead of the headline solve")
     ap.add_argument("--screen-bounds", type=int, default=1, choices=[0, 1],
                     help="0: screen without the block-maxima bounds (same result; for comparison)")

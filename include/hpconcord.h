@@ -58,7 +58,9 @@ extern "C" {
 /* ---------------------------------------------------------------- enums */
 typedef struct hpc_ctx* hpc_handle;         /* opaque, owned by the library */
 
-typedef enum { HPC_COV = 0, HPC_OBS = 1 } hpc_variant;          /* Alg. 2 / Alg. 3 */
+/* Alg. 2 (Cov: S formed once) / Alg. 3 (Obs: Z = Y X / n every iteration);
+ * HPC_AUTO picks one at hpc_create by hpc_choose_variant. */
+typedef enum { HPC_COV = 0, HPC_OBS = 1, HPC_AUTO = 2 } hpc_variant;
 
 typedef enum { HPC_F32 = 0, HPC_F64 = 1, HPC_BF16 = 2 } hpc_dtype;
 
@@ -76,6 +78,23 @@ typedef enum {
                               lo*hi accumulated in FP32; one term when X is BF16  */
     HPC_PREC_TF32   = 3    /* tensor cores, TF32 inputs, FP32 accumulation        */
 } hpc_precision;
+
+/* Lemma 3.1's choice between the variants.  With s outer iterations, t line-search
+ * trials per iteration and d nonzeros per row of the iterate, Cov costs
+ * 2np^2 + 2dp^2(st+1) flops and Obs 2np^2 s + 2dnp(st+1); weighting the dense
+ * products (the Gram, Z) by gamma_dense and the sparse-dense work by gamma_sparse
+ * (time per flop of each on this GPU), Cov is chosen when
+ *   gamma_dense 2np^2 + gamma_sparse 2dp^2(st+1) < gamma_dense 2np^2 s + gamma_sparse 2dnp(st+1).
+ * s, t, d and the ratio gamma_sparse / gamma_dense are the arguments; a value <= 0
+ * takes the default: s = 40, t = 3, d = 2 and ratio HPC_GAMMA_RATIO, the medians
+ * measured on GB300 over a sweep of p = 40000, n = 100 ... 12800 on chain and random
+ * graphs (gamma_sparse: the Cov iteration's time per flop the lemma counts for it;
+ * gamma_dense: the Obs Z product's time per flop).  The two modelled costs (in
+ * gamma_dense units) go to *cost_cov and *cost_obs (nullable).  Returns HPC_COV or
+ * HPC_OBS; HPC_ERR_ARG for n < 1 or p < 1. */
+#define HPC_GAMMA_RATIO 8.0
+int hpc_choose_variant(int64_t n, int64_t p, double s, double t, double d, double gamma_ratio,
+                       double* cost_cov, double* cost_obs);
 
 /* ---------------------------------------------------------------- options / stats */
 typedef struct {
@@ -304,6 +323,17 @@ int hpc_backward(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, v
  * Synchronises the handle's stream. */
 int hpc_backward_support(hpc_handle h, const void* X, hpc_dtype xdt, double grad_loss, double* dOmega_vals,
                          void* dX);
+
+/* The held-out loss of model selection at the current iterate:
+ *   L_val(Omega) = -sum_i log w_ii + tr(Omega S_val Omega) / 2,  S_val = X_val^T X_val / n_val,
+ * the unpenalised smooth part of the objective (Section 2, eq. (1) under this library's
+ * scaling) on data the estimate was not fitted to.  The paper motivates grids of tuning
+ * parameters for cross-validation; this is the criterion evaluated at each point.
+ * tr(Omega S_val Omega) = sum over the support of w_ij (Omega S_val)_ij, with
+ * (Omega S_val)_ij = <(X_val Omega)_{:,i}, X_val_{:,j}> / n_val: S_val is never formed.
+ * Xval: device, nval x p row-major, dtype xdt.  Cov and Obs handles.  Synchronises the
+ * handle's stream; the FP64 result goes to *loss (host). */
+int hpc_heldout_loss(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double* loss);
 
 typedef struct {
     int64_t cg_iterations;

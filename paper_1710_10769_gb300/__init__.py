@@ -20,7 +20,7 @@ _LIB = None
 OK, NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OOM, ERR_CAPACITY, ERR_NONPOS_DIAG, ERR_NAN, ERR_LS_FAIL, ERR_CUDA, ERR_NOT_IMPLEMENTED, \
     ERR_DEVICE_TIMEOUT = -1, -2, -3, -4, -5, -6, -7, -8, -9
-COV, OBS = 0, 1
+COV, OBS, AUTO = 0, 1, 2
 F32, F64, BF16 = 0, 1, 2
 PREC_AUTO, PREC_FP64, PREC_FP32, PREC_BF16X3, PREC_TF32 = -1, 0, 1, 2, 3
 
@@ -127,6 +127,9 @@ _SIGS = {
     "hpc_smooth_value": (C.c_int, [_P, C.POINTER(C.c_double)]),
     "hpc_backward": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, C.c_int64, _P]),
     "hpc_backward_support": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, _P]),
+    "hpc_heldout_loss": (C.c_int, [_P, _P, C.c_int, C.c_int64, C.POINTER(C.c_double)]),
+    "hpc_choose_variant": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hpc_hypergrad": (C.c_int, [_P, _P, C.c_int, C.c_int64, C.c_double, C.c_int64, C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(HypergradInfo)]),
     "hpc_destroy": (C.c_int, [_P]),
@@ -495,6 +498,14 @@ class Solver:
                                               C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()), code, 1),
                       "hpc_set_omega")
 
+    def heldout_loss(self, Xval) -> float:
+        """L_val = -sum log w_ii + tr(Omega S_val Omega)/2 at the current estimate (``hpc_heldout_loss``)."""
+        _matrix(Xval, None, self.p, "Xval", cuda=True)
+        out = C.c_double(0.0)
+        _check(self._lib.hpc_heldout_loss(self._h, C.c_void_p(Xval.data_ptr()), _dtype_code(Xval), Xval.shape[0],
+                                          C.byref(out)), "hpc_heldout_loss")
+        return out.value
+
     def hypergrad(self, Xval, tol=1e-8, max_iter=20000):
         """(dL_val/dlambda1, dL_val/dlambda2, info) at the current estimate (``hpc_hypergrad``)."""
         _matrix(Xval, None, self.p, "Xval", cuda=True)
@@ -655,6 +666,17 @@ def concord_smooth_loss(X, omega, solver):
     if _SMOOTH_LOSS is None:
         _SMOOTH_LOSS = _make_smooth_loss()
     return _SMOOTH_LOSS.apply(X, omega, solver)
+
+
+def choose_variant(n, p, s=0.0, t=0.0, d=0.0, gamma_ratio=0.0):
+    """Lemma 3.1's choice (``hpc_choose_variant``): (COV or OBS, modelled Cov cost, modelled Obs cost)."""
+    lib = load()
+    cc, co = C.c_double(0.0), C.c_double(0.0)
+    v = lib.hpc_choose_variant(int(n), int(p), float(s), float(t), float(d), float(gamma_ratio), C.byref(cc),
+                               C.byref(co))
+    if v < 0:
+        raise HpcError(v, "hpc_choose_variant")
+    return v, cc.value, co.value
 
 
 def solve_batch(solvers, threads=0):

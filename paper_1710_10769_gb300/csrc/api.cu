@@ -1054,6 +1054,22 @@ const char* hpc_status_string(int s) {
 
 const char* hpc_last_error(void) { return g_last_error; }
 
+int hpc_choose_variant(int64_t n, int64_t p, double s, double t, double d, double gamma_ratio, double* cost_cov,
+                       double* cost_obs) {
+    if (n < 1 || p < 1) return HPC_ERR_ARG;
+    if (!(s > 0.0)) s = 40.0;
+    if (!(t > 0.0)) t = 3.0;
+    if (!(d > 0.0)) d = 2.0;
+    if (!(gamma_ratio > 0.0)) gamma_ratio = HPC_GAMMA_RATIO;
+    const double N = (double)n, P = (double)p;
+    // Lemma 3.1's flop counts, the sparse-dense terms weighted by gamma_sparse / gamma_dense
+    const double cov = 2.0 * N * P * P + gamma_ratio * 2.0 * d * P * P * (s * t + 1.0);
+    const double obs = 2.0 * N * P * P * s + gamma_ratio * 2.0 * d * N * P * (s * t + 1.0);
+    if (cost_cov) *cost_cov = cov;
+    if (cost_obs) *cost_obs = obs;
+    return cov < obs ? HPC_COV : HPC_OBS;
+}
+
 int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t p, double lambda1,
                double lambda2, hpc_variant variant, const hpc_options* opt, void* cuda_stream) {
     if (!out) return HPC_ERR_ARG;
@@ -1071,6 +1087,8 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         !(o.ls_window == 1 || o.ls_window == 2 || o.ls_window == 4 || o.ls_window == 8 || o.ls_window == 16) ||
         o.precision < HPC_PREC_AUTO || o.precision > HPC_PREC_TF32)
         return HPC_ERR_ARG;
+    if (variant == HPC_AUTO)
+        variant = (hpc_variant)hpc_choose_variant(n, p, 0.0, 0.0, 0.0, 0.0, nullptr, nullptr);
     if (variant != HPC_COV && variant != HPC_OBS) return HPC_ERR_ARG;
     int prec = o.precision;
     if (prec == HPC_PREC_AUTO) prec = (o.value_dtype == HPC_F64) ? HPC_PREC_FP64 : HPC_PREC_BF16X3;
@@ -1737,6 +1755,39 @@ int backward_support_t(hpc_ctx* h, const void* X, int xdt, double grad_loss, dou
     return HPC_OK;
 }
 
+// L_val(Omega) = -sum log w_ii + tr(Omega S_val Omega) / 2 at the current iterate, with
+// tr(Omega S_val Omega) = sum_e w_e (Omega S_val)_e over the support and (Omega S_val)_ij =
+// <(X_val Omega)_{:,i}, X_val_{:,j}> / n_val (S_val is never formed).
+template <typename T>
+int heldout_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double* loss) {
+    const int p = (int)h->p;
+    const int64_t nnz = h->nnz;
+    const size_t b_x = align256((size_t)p * nval * sizeof(T));
+    const size_t b_v = align256(nnz * sizeof(double));
+    const size_t b_p = align256(1024 * 3 * sizeof(double));
+    STATUS_TRY(adj_reserve(h, 2 * b_x + b_v + b_p + 256));
+    uint8_t* q = static_cast<uint8_t*>(h->adj_buf);
+    T* xtv = reinterpret_cast<T*>(q); q += b_x;
+    T* ytv = reinterpret_cast<T*>(q); q += b_x;
+    double* Tv = reinterpret_cast<double*>(q); q += b_v;
+    double* part = reinterpret_cast<double*>(q); q += b_p;
+    double* out3 = reinterpret_cast<double*>(q);
+    cudaStream_t s = h->stream;
+    hpc::Csr<T> om = cur_csr<T>(h);
+    hpc::launch_row_info<T>(p, om, h->rinfo, as<T>(h->rdv), s);
+    const int tdt = sizeof(T) == 8 ? HPC_F64 : HPC_F32;
+    hpc::launch_transpose(Xval, xdt, nval, p, p, xtv, tdt, nval, 1.0, s);
+    hpc::launch_spmm_dense<T>(p, om, h->rinfo, as<T>(h->rdv), xtv, nval, nval, ytv, nval, s);
+    hpc::launch_support_sddmm<T>(p, om, ytv, xtv, nval, nval, Tv, s);
+    hpc::launch_smooth_parts<T>(p, om, Tv, part, out3, s);
+    CUDA_TRY(cudaGetLastError());
+    double o[3];
+    CUDA_TRY(cudaMemcpyAsync(o, out3, sizeof o, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *loss = -o[2] + 0.5 * o[0];
+    return HPC_OK;
+}
+
 template <typename T>
 int hypergrad_t(hpc_ctx* h, const void* Xval, int xdt, int64_t nval, double cg_tol, int64_t cg_max, double* dl1,
                 double* dl2, hpc_hypergrad_info* info) {
@@ -2114,6 +2165,16 @@ int hpc_backward_support(hpc_handle h, const void* X, hpc_dtype xdt, double grad
     }
     return h->vdt == HPC_F64 ? backward_support_t<double>(h, X, xdt, grad_loss, dOmega_vals, dX)
                              : backward_support_t<float>(h, X, xdt, grad_loss, dOmega_vals, dX);
+}
+
+int hpc_heldout_loss(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double* loss) {
+    if (!h || !h->loaded || !Xval || nval < 1 || !valid_dtype(xdt) || !loss) return HPC_ERR_ARG;
+    if (nval > hpc::kTransposeMaxRows) {
+        std::snprintf(g_last_error, sizeof g_last_error, "hpc_heldout_loss transposes X_val: nval <= %lld",
+                      (long long)hpc::kTransposeMaxRows);
+        return HPC_ERR_ARG;
+    }
+    return h->vdt == HPC_F64 ? heldout_t<double>(h, Xval, xdt, nval, loss) : heldout_t<float>(h, Xval, xdt, nval, loss);
 }
 
 int hpc_hypergrad(hpc_handle h, const void* Xval, hpc_dtype xdt, int64_t nval, double cg_tol, int64_t cg_max_iter,

@@ -84,3 +84,20 @@ def test_obs_equals_cov_on_the_fp32_workload(lib):
     a, b = ests
     d = a - b
     assert np.sqrt(d.multiply(d).sum()) / np.sqrt(a.multiply(a).sum()) < 1e-5
+
+
+@pytest.mark.parametrize("n,p", [(200, 150), (40, 300)])
+def test_auto_variant_matches_oracle(lib, n, p):
+    """variant = AUTO resolves by Lemma 3.1 (hpc_choose_variant) and reaches the oracle's estimate."""
+    import torch
+
+    X = small_problem(p, n, 3.0, 80 + n).astype(np.float32)
+    want, _, _ = lib.choose_variant(n, p)
+    with lib.Solver(torch.as_tensor(X).cuda(), 0.15, 0.1, variant=lib.AUTO, precision=lib.PREC_FP32, eps=3e-7,
+                    max_iter=5000) as s:
+        assert s.info().variant == want
+        st = s.solve().as_dict()
+        om = s.omega_dense()
+    assert _stopped_ok(st), st
+    ref = oracle.solve(oracle.gram(X), 0.15, 0.1, eps=1e-9, max_iter=20000)
+    assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-5
