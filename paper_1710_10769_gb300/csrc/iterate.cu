@@ -221,7 +221,7 @@ constexpr int kScreenTileRows = 64;
 constexpr int kScreenStages = 5;
 constexpr int kScreenMaxChunks = 32;              // row chunks per CTA (shared-memory row cache)
 constexpr int kScreenThreads = kThreads + 32;     // 8 consumer warps + 1 producer warp
-constexpr long long kScreenWaitLimit = 1ll << 26;
+constexpr long long kScreenWaitLimit = 1ll << 22;     // polls of at most 1 us each
 
 // Column side of a tile, loaded with it: the BJ diagonal values and 16 bytes of the
 // purity bitmask around the block.

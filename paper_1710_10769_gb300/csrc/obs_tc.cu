@@ -32,7 +32,7 @@ constexpr int kT = 128;                    // tile edge (UMMA M = N = 128)
 constexpr int kRowB = 128;                 // bytes per swizzle row
 constexpr int kPanelTile = kT * kRowB;     // 16 KB
 constexpr uint32_t kTmemCols = 256;        // one accumulator pair: two 128-column FP32 accumulators
-constexpr long long kWaitLimit = 1ll << 26;
+constexpr long long kWaitLimit = 1ll << 22;     // polls of at most 1 us each
 
 enum : int { kObsBf16x3 = 0, kObsTf32 = 1 };
 
@@ -109,7 +109,7 @@ struct ObsCfg {
     static constexpr int kMmaK = 32 / kElem;
     static constexpr int kStageBytes = kPieces * 2 * kPanelTile;    // A and B tiles, each piece
     static constexpr int kStages = MODE == kObsBf16x3 ? 3 : 5;
-    static constexpr int kTransBytes = (kT / 2) * (kT + 1) * 4;     // half of Z[J, I], staged for the transpose
+    static constexpr int kTransBytes = 2 * 2 * kT * 4 * 4;          // threshold bits, transposed: [side][buffer][kT][4]
     static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
 };
 
@@ -172,7 +172,7 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
     const float lam1 = (float)ctrl->lam1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* zt = reinterpret_cast<float*>(smem + C::kStages * C::kStageBytes);        // [kT / 2][kT + 1]
+    uint32_t* tbits = reinterpret_cast<uint32_t*>(smem + C::kStages * C::kStageBytes);   // [2][2][kT][4]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + C::kTransBytes);
     uint64_t* empty = full + C::kStages;
     uint64_t* acc_full = empty + C::kStages;     // [2]
@@ -293,16 +293,48 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
         // the epilogue warpgroups take them: the running sums of 128 columns live in registers
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
         // ---------------- epilogue
+        // Thread (side, row-local r) owns row g = (side ? J0 : I0) + r of its tile and the
+        // tile's columns c = 0..127 of the other block (column k0 + c).  The entry pair
+        // {(i, j), (j, i)} is emitted when it is in the support, on the diagonal, or when
+        // n |Z_ij| or n |Z_ji| exceeds lambda1 n; each side emits its own entry with its own
+        // value, flagged as paired (the other side emits the partner).  A side's threshold
+        // bits reach the other side transposed: per column, a warp ballot over its 32 rows
+        // (tbits), so no value crosses between the warps.  A diagonal pair is one tile,
+        // held by side 0, whose bits meet their own transpose.
         const int q4 = warp & 3;
         const int side = (warp - 4) >> 2;            // 0: Z[I, J] rows, 1: Z[J, I] rows
         const int r = q4 * 32 + lane;                // TMEM lane = local row
-        const float dn = (float)n;
         const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(side * kT);
+        // Z = (Y X) / n: the sums are tested against lambda1 n and only the emitted entries
+        // are scaled.  The threshold is lowered by 2^-20 relative, so that the entries
+        // emitted include every one whose scaled value exceeds lambda1 in FP32; an extra
+        // entry at the threshold is harmless (its prox step leaves it at zero).
+        const float inv_n = 1.0f / (float)n;
+        const float thr = (float)((double)lam1 * (double)n * (1.0 - 0x1p-20));
         long long gc = 0;
         for (int lt = 0; lt < my_pairs; ++lt) {
             const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
             const int I0 = pr.x * kT, J0 = pr.y * kT;
             const bool diag_pair = pr.x == pr.y;
+            const bool active = side == 0 || !diag_pair;
+            const int g = (side ? J0 : I0) + r;          // this thread's row
+            const int k0 = side ? I0 : J0;               // its tile's first column
+            // the row's support in the columns k0 .. k0 + 127: a 128-bit mask, and the CSR
+            // position of its first entry there (columns ascend, so entry k of the mask sits
+            // at qs + k); read before the accumulator is waited for, so that the loads'
+            // latency overlaps it
+            uint32_t smask[4] = {0u, 0u, 0u, 0u};
+            int qs = 0;
+            if (active && g < p) {
+                int q = rp[g];
+                const int qe = rp[g + 1];
+                while (q < qe && ci[q] < k0) ++q;
+                qs = q;
+                for (; q < qe && ci[q] < k0 + kT; ++q) {
+                    const int c = ci[q] - k0;
+                    smask[c >> 5] |= 1u << (c & 31);
+                }
+            }
             float acc[kT];
 #pragma unroll
             for (int q = 0; q < kT; ++q) acc[q] = 0.f;
@@ -314,7 +346,7 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                 got = __all_sync(kFull, got);
                 if (!got) { have = false; continue; }
                 tc_fence_after();
-                if (side == 0 || !diag_pair) {
+                if (active) {
 #pragma unroll
                     for (int s8 = 0; s8 < kT / 16; ++s8) {
                         uint32_t v[16];
@@ -328,65 +360,72 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                 __syncwarp();
                 if (lane == 0) ptx_arrive(&acc_empty[b]);
             }
+            // own threshold bits, and their transpose by ballots: column c's word (bit l = row
+            // 32 q4 + l of this warp) is kept by lane c % 32
+            uint32_t own[4] = {0u, 0u, 0u, 0u}, tw[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int q = 0; q < kT; ++q) acc[q] = acc[q] / dn;
-            // the staging side: Z[J, I] (side 1), or Z[I, I] itself for a diagonal pair
-            const bool stager = diag_pair ? side == 0 : side == 1;
-            const int i = I0 + r;
-            int q = 0, qe = 0;
-            if (side == 0 && have && i < p) {
-                q = rp[i];
-                qe = rp[i + 1];
-                while (q < qe && ci[q] < J0) ++q;
+            for (int c = 0; c < kT; ++c) {
+                const bool big = active && have && g < p && !(fabsf(acc[c]) <= thr);
+                own[c >> 5] |= (uint32_t)big << (c & 31);
+                const uint32_t word = __ballot_sync(kFull, big);
+                if ((c & 31) == lane) tw[c >> 5] = word;
             }
-            // Z[J, I] (Z[I, I] for a diagonal pair) is staged in two halves of 64 rows:
-            // the warps holding rows 64 h .. 64 h + 63 write them, then every emitting
-            // thread handles its row's columns 64 h .. 64 h + 63 (the support merge
-            // carries over between the halves)
+            // layout [side][buffer][column][warp]; the buffer alternates by pair, so the next
+            // pair's words cannot overwrite words another thread still reads
+            uint32_t* tb = tbits + (size_t)(lt & 1) * kT * 4;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (have && stager && (q4 >> 1) == h) {
-                    const int cl = (q4 - 2 * h) * 32 + lane;            // staged row, 0..63
+            for (int k = 0; k < 4; ++k) tb[((side * 2) * kT + 32 * k + lane) * 4 + q4] = tw[k];
+            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");     // every side's bits are in
+            const bool mine = active && have && g < p;
+            // the other side's bits for this row: its words for column r (a diagonal pair: this side's)
+            const int other = diag_pair ? 0 : 1 - side;
+            uint32_t emb[4];
+            int cnt = 0;
 #pragma unroll
-                    for (int cc = 0; cc < kT; ++cc) zt[cl * (kT + 1) + cc] = acc[cc];
-                }
-                asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");      // the staged half is complete
-                if (have && side == 0 && i < p) {
+            for (int k = 0; k < 4; ++k) {
+                uint32_t e = own[k] | tb[((other * 2) * kT + r) * 4 + k] | smask[k];
+                const int lim = p - (k0 + 32 * k);              // columns k0 + 32 k + b < p
+                if (lim < 32) e &= lim > 0 ? (1u << lim) - 1u : 0u;
+                if (diag_pair && (r >> 5) == k) e |= 1u << (r & 31);      // the diagonal
+                emb[k] = mine ? e : 0u;
+                cnt += __popc(emb[k]);
+            }
+            // one atomic per warp: an inclusive scan of the lanes' counts, the last lane takes
+            // the warp's total from the emission counter and every lane writes from its offset
+            int incl = cnt;
 #pragma unroll
-                    for (int cc = 0; cc < kT / 2; ++cc) {
-                        const int c = 64 * h + cc;
-                        const int j = J0 + c;
-                        if (j < p) {
-                            while (q < qe && ci[q] < j) ++q;             // support merge, column order
-                            // on a diagonal pair the (j, i) thread emits the pairs with j < i
-                            if (!(diag_pair && j < i)) {
-                                const float a = acc[c];                                  // Z_ij
-                                const float bz = zt[cc * (kT + 1) + r];                  // Z_ji
-                                const bool sup = q < qe && ci[q] == j;
-                                const float om = sup ? cv[q] : 0.f;
-                                const bool big = !(fabsf(a) <= lam1) || !(fabsf(bz) <= lam1);
-                                if (sup || big || i == j) {
-                                    const int cnt = (i == j) ? 1 : 2;
-                                    const int pos = atomicAdd(&ctrl->em_count, cnt);
-                                    const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);   // paired, support
-                                    if (pos < em.cap) {
-                                        em.row[pos] = i;
-                                        em.col[pos] = (int)((unsigned)j | fl);
-                                        em.w[pos] = a;
-                                        em.om[pos] = om;
-                                    }
-                                    if (i != j && pos + 1 < em.cap) {
-                                        em.row[pos + 1] = j;
-                                        em.col[pos + 1] = (int)((unsigned)i | fl);
-                                        em.w[pos + 1] = bz;
-                                        em.om[pos + 1] = om;
-                                    }
-                                }
-                            }
-                        }
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int base = 0;
+            if (lane == 31 && incl > 0) base = atomicAdd(&ctrl->em_count, incl);
+            base = __shfl_sync(kFull, base, 31);
+            if (!mine) continue;
+            int pos = base + incl - cnt;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t em_bits = emb[k];
+                while (em_bits) {
+                    const int b = __ffs(em_bits) - 1;
+                    em_bits &= em_bits - 1u;
+                    const int c = 32 * k + b;
+                    float a = 0.f;                              // acc[32 k + b] without dynamic indexing
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) a = (t == b) ? acc[32 * k + t] : a;
+                    const uint32_t sw = smask[k];
+                    const bool sup = (sw >> b) & 1u;
+                    int before = __popc(sw & ((1u << b) - 1u));
+#pragma unroll
+                    for (int t = 0; t < k; ++t) before += __popc(smask[t]);
+                    if (pos < em.cap) {
+                        em.row[pos] = g;
+                        em.col[pos] = (int)((unsigned)(k0 + c) | 0x40000000u | (sup ? 0x80000000u : 0u));
+                        em.w[pos] = __fmul_rn(a, inv_n);
+                        em.om[pos] = sup ? cv[qs + before] : 0.f;
                     }
+                    ++pos;
                 }
-                asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");      // the staged half is free again
             }
         }
     }

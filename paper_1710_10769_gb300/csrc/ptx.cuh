@@ -41,16 +41,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread may sleep in the instruction (up to
+// `ns` nanoseconds) until the phase completes, instead of polling.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on the phase of `parity`: false after `limit` polls or once
-// *abort_flag is raised by another role (which this call then also sees).
+// *abort_flag is raised by another role (which this call then also sees).  Each
+// poll may sleep in the wait instruction for up to 1 us.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                                   long long limit) {
     for (long long it = 0; it < limit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255) == 255) {
-            if (*abort_flag) return false;
-            __nanosleep(64);
-        }
+        if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
+        if ((it & 255) == 255 && *abort_flag) return false;
     }
     *abort_flag = 1;
     return false;
