@@ -384,6 +384,72 @@ def run_row(args):
               None, clk.summary(), None, None, auto_picks_faster=f"{agree}/{len(rows)}", sweep=rows)
         return 0
 
+    if args.row == "chain":
+        # The paper's headline shape on one GPU (Abstract; Section 4, Fig. 4a; Table 1): chain
+        # graph (bandwidth 1), n = 100, p up to 1.28 million, Obs variant (Z = Y X / n on the
+        # tensor cores every iteration, no p x p array anywhere).  lambda1 makes the null
+        # off-diagonal |S_ij| exceed it for about p of the p^2 / 2 pairs (lambda1 =
+        # z_{1 - 1/p} / sqrt(n)), so that the estimate's average degree is near the chain's 2,
+        # the paper's rule for comparing equally sparse estimates; the degree reached is reported.
+        from statistics import NormalDist
+
+        from paper_1710_10769_gb300.selection import support_recovery
+        from workloads import omega0_banded
+
+        n, lam2, seed = 100, 0.1, 5
+        ps = [int(v) for v in args.chain_p.split(",")]
+        rows = []
+        with ClockSampler(0) as clk:
+            for i, p in enumerate(ps):
+                om0 = omega0_banded(p, 1, seed)
+                X = cast_x(sample_x_cuda(om0, n, seed), "f32")
+                lam1 = NormalDist().inv_cdf(1.0 - 1.0 / p) / math.sqrt(n)
+                s = hpc.Solver(None, lam1, lam2, variant=hpc.OBS, n=n, p=p, xdtype=hpc.F32,
+                               precision=hpc.PREC_FP32, eps=1e-6, max_iter=5000, timing=1)
+                if i == 0:                      # first use of the kernels and the graph capture
+                    s.load_x(X)
+                    s.solve()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.load_x(X)
+                st = s.solve().as_dict()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                est = s.get_omega().to_scipy(p)
+                rec = support_recovery(est, om0)
+                info = s.info()
+                npairs = ((p + 127) // 128) * ((p + 127) // 128 + 1) // 2
+                per = st["ms_grad_pass"] / max(st["grad_pass_launches"], 1)
+                kdim = (n + 63) // 64 * 64
+                # tensor work of one Z pass: both tiles of every block pair at the padded K, three
+                # BF16 products each (BF16X3)
+                tf = 2.0 * 2 * npairs * 128 * 128 * kdim * 3 / (per / 1000.0) / 1e12
+                r = {"p": p, "n": n, "lambda1": lam1, "lambda2": lam2, "ms_to_converge": ms,
+                     "iterations": st["iterations"], "ls_trials": st["ls_trials"], "status": st["status"],
+                     "nnz": st["nnz"], "avg_degree": (st["nnz"] - p) / p, "ppv": rec["ppv"], "tpr": rec["tpr"],
+                     "ms_z_pass": per, "z_pass_share": st["ms_grad_pass"] / ms,
+                     "z_pass_tflops_bf16_equiv": tf, "z_pass_frac_of_bf16": tf / (bf16_sus if bf16_sus else bf16),
+                     "device_bytes": info.device_bytes, "p_squared_fp32_bytes": 4 * p * p,
+                     "parameters": p * (p + 1) // 2, "z_precision": s.precision_name()}
+                rows.append(r)
+                print(json.dumps(r), file=sys.stderr, flush=True)
+                s.close()
+                del X
+                torch.cuda.empty_cache()
+        big = rows[-1]
+        roof = {"kernel": "k_obs_pair (Z pass)", "bound": "tensor", "achieved": big["z_pass_tflops_bf16_equiv"],
+                "peak": bf16_sus if bf16_sus else bf16, "unit": "TFLOP/s", "frac": big["z_pass_frac_of_bf16"],
+                "traffic": None, "peak_source": f"{peak_src} (bf16 sustained; 3 BF16 products per element counted)"}
+        _line(f"Obs time to converge, chain graph, n=100, p={big['p']}", big["ms_to_converge"] / 1000.0, "s",
+              big["ms_to_converge"], args, False, "f32",
+              {"workload": f"chain_n100_p{big['p']}", "variant": "obs", "graph": "chain (bandwidth 1)", "n": n,
+               "p": ps, "lambda1": "z_{1-1/p} / sqrt(n)", "lambda2": lam2, "eps": 1e-6,
+               "timing": "CUDA events around load_x + solve, one cold solve per p"},
+              roof, clk.summary(), None, None, sweep=rows)
+        return 0
+
     if args.row == "batch":
         Xs = [make_x(wk, device="cuda") for wk in BATCH_PROBLEMS]
         streams = [torch.cuda.Stream() for _ in BATCH_PROBLEMS]
@@ -607,8 +673,11 @@ def main(argv=None):
     ap.add_argument("--x-dtype", default="workload", choices=["workload", "f32", "bf16"],
                     help="store X in this dtype instead of the workload's (profiling the one-product BF16 Gram "
                          "at sizes a full ncu capture allows)")
-    ap.add_argument("--row", default=None, choices=["path", "batch", "adjoint", "obs", "select", "crossover"],
+    ap.add_argument("--row", default=None,
+                    choices=["path", "batch", "adjoint", "obs", "select", "crossover", "chain"],
                     help="time a further row of the hot path instead of the headline solve")
+    ap.add_argument("--chain-p", default="80000,160000,320000,640000,1280000",
+                    help="dimensions of the chain row (comma separated)")
     ap.add_argument("--screen-bounds", type=int, default=1, choices=[0, 1],
                     help="0: screen without the block-maxima bounds (same result; for comparison)")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],

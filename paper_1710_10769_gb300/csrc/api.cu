@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.cuh"
@@ -169,14 +170,40 @@ struct hpc_ctx {
     int2* pairs = nullptr;
     int64_t npairs = 0;
     CUtensorMap obs_maps[4];
+    // device buffers the handle holds (address -> bytes), for hpc_get_info
+    std::unordered_map<void*, size_t> held;
+    size_t held_bytes = 0;
 };
 
 namespace {
 
+// cudaMalloc of a buffer the handle keeps, recorded in its ledger.
+template <typename T>
+cudaError_t hold(hpc_ctx* h, T** q, size_t bytes) {
+    void* v = nullptr;
+    const cudaError_t e = cudaMalloc(&v, bytes);
+    if (e == cudaSuccess) {
+        *q = static_cast<T*>(v);
+        h->held[v] = bytes;
+        h->held_bytes += bytes;
+    }
+    return e;
+}
+
+void release(hpc_ctx* h, void* q) {
+    if (!q) return;
+    auto it = h->held.find(q);
+    if (it != h->held.end()) {
+        h->held_bytes -= it->second;
+        h->held.erase(it);
+    }
+    cudaFree(q);
+}
+
 void free_candidates(hpc_ctx* h) {
     void* ptrs[] = {h->em_row, h->em_col, h->em_w, h->em_om, h->col_a, h->w_a, h->om_a, h->fl_a,
                     h->col_b, h->w_b, h->om_b, h->fl_b, h->g_b, h->bk_mir};
-    for (void* q : ptrs) if (q) cudaFree(q);
+    for (void* q : ptrs) release(h, q);
     h->em_row = h->em_col = nullptr; h->em_w = h->em_om = nullptr;
     h->col_a = h->col_b = nullptr; h->w_a = h->om_a = h->w_b = h->om_b = h->g_b = nullptr;
     h->fl_a = h->fl_b = nullptr;
@@ -187,20 +214,20 @@ int alloc_candidates(hpc_ctx* h, int64_t cap) {
     const size_t vs = dtype_size(h->vdt);
     const int64_t bcap = 2 * cap;
     free_candidates(h);
-    CUDA_TRY(cudaMalloc(&h->em_row, cap * sizeof(int)));
-    CUDA_TRY(cudaMalloc(&h->em_col, cap * sizeof(int)));
-    CUDA_TRY(cudaMalloc(&h->em_w, cap * vs));
-    CUDA_TRY(cudaMalloc(&h->em_om, cap * vs));
-    CUDA_TRY(cudaMalloc(&h->col_a, bcap * sizeof(int)));
-    CUDA_TRY(cudaMalloc(&h->w_a, bcap * vs));
-    CUDA_TRY(cudaMalloc(&h->om_a, bcap * vs));
-    CUDA_TRY(cudaMalloc(&h->fl_a, bcap));
-    CUDA_TRY(cudaMalloc(&h->col_b, bcap * sizeof(int)));
-    CUDA_TRY(cudaMalloc(&h->w_b, bcap * vs));
-    CUDA_TRY(cudaMalloc(&h->om_b, bcap * vs));
-    CUDA_TRY(cudaMalloc(&h->fl_b, bcap));
-    CUDA_TRY(cudaMalloc(&h->g_b, bcap * vs));
-    CUDA_TRY(cudaMalloc(&h->bk_mir, bcap * sizeof(int2)));
+    CUDA_TRY(hold(h, &h->em_row, cap * sizeof(int)));
+    CUDA_TRY(hold(h, &h->em_col, cap * sizeof(int)));
+    CUDA_TRY(hold(h, &h->em_w, cap * vs));
+    CUDA_TRY(hold(h, &h->em_om, cap * vs));
+    CUDA_TRY(hold(h, &h->col_a, bcap * sizeof(int)));
+    CUDA_TRY(hold(h, &h->w_a, bcap * vs));
+    CUDA_TRY(hold(h, &h->om_a, bcap * vs));
+    CUDA_TRY(hold(h, &h->fl_a, bcap));
+    CUDA_TRY(hold(h, &h->col_b, bcap * sizeof(int)));
+    CUDA_TRY(hold(h, &h->w_b, bcap * vs));
+    CUDA_TRY(hold(h, &h->om_b, bcap * vs));
+    CUDA_TRY(hold(h, &h->fl_b, bcap));
+    CUDA_TRY(hold(h, &h->g_b, bcap * vs));
+    CUDA_TRY(hold(h, &h->bk_mir, bcap * sizeof(int2)));
     h->cap = cap;
     h->epoch += 1;
     return HPC_OK;
@@ -212,15 +239,15 @@ int grow_csr(hpc_ctx* h, int64_t newcap) {
     for (int b = 0; b < 2; ++b) {
         int* ci = nullptr;
         void* cv = nullptr;
-        CUDA_TRY(cudaMalloc(&ci, newcap * sizeof(int)));
-        CUDA_TRY(cudaMalloc(&cv, newcap * vs));
+        CUDA_TRY(hold(h, &ci, newcap * sizeof(int)));
+        CUDA_TRY(hold(h, &cv, newcap * vs));
         if (b == h->cur && h->ci[b] && h->nnz > 0) {
             CUDA_TRY(cudaMemcpyAsync(ci, h->ci[b], h->nnz * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
             CUDA_TRY(cudaMemcpyAsync(cv, h->cv[b], h->nnz * vs, cudaMemcpyDeviceToDevice, h->stream));
             CUDA_TRY(cudaStreamSynchronize(h->stream));
         }
-        if (h->ci[b]) cudaFree(h->ci[b]);
-        if (h->cv[b]) cudaFree(h->cv[b]);
+        if (h->ci[b]) release(h, h->ci[b]);
+        if (h->cv[b]) release(h, h->cv[b]);
         h->ci[b] = ci;
         h->cv[b] = cv;
     }
@@ -877,10 +904,10 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         }
         if (xbytes > h->x_stage_bytes) {
             if (h->pf_issued) CUDA_TRY(cudaEventSynchronize(h->ev_pf));
-            if (h->x_stage) cudaFree(h->x_stage);
+            if (h->x_stage) release(h, h->x_stage);
             h->x_stage = nullptr;
             h->x_stage_bytes = 0;
-            CUDA_TRY(cudaMalloc(&h->x_stage, xbytes));
+            CUDA_TRY(hold(h, &h->x_stage, xbytes));
             h->x_stage_bytes = xbytes;
         }
         CUDA_TRY(cudaMemcpyAsync(h->x_stage, X, xbytes, cudaMemcpyHostToDevice, h->stream));
@@ -901,11 +928,11 @@ int load_x(hpc_ctx* h, const void* X, int xdt, int on_host) {
         const size_t need = hpc::gram_tc_scratch_bytes(xdt, h->n, h->p, prec);
         if (need > h->gram_scratch_bytes) {
             if (h->pf_issued) CUDA_TRY(cudaEventSynchronize(h->ev_pf));
-            if (h->gram_scratch) cudaFree(h->gram_scratch);
+            if (h->gram_scratch) release(h, h->gram_scratch);
             h->gram_scratch = nullptr;
             h->tiles_sig = 0;     // a new buffer may reuse the old address
             h->gram_scratch_bytes = 0;
-            CUDA_TRY(cudaMalloc(&h->gram_scratch, need));
+            CUDA_TRY(hold(h, &h->gram_scratch, need));
             h->gram_scratch_bytes = need;
         }
         e = hpc::gram_tc(Xd, xdt, h->n, h->p, static_cast<float*>(h->S), h->ld, prec, h->gram_scratch,
@@ -1002,7 +1029,7 @@ void destroy(hpc_ctx* h) {
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
                     h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long,
                     h->m1, h->m1g, h->colmax, h->pairs_list, h->row_items, h->x_stage};
-    for (void* q : ptrs) if (q) cudaFree(q);
+    for (void* q : ptrs) release(h, q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
     if (h->ev_scr0) cudaEventDestroy(h->ev_scr0);
@@ -1126,17 +1153,17 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     }
     if (variant == HPC_OBS) {
         h->ldx = (n + 63) / 64 * 64;
-        CK(cudaMalloc(&h->xt, (size_t)p * h->ldx * sizeof(float)));
-        CK(cudaMalloc(&h->yt, (size_t)p * h->ldx * sizeof(float)));
+        CK(hold(h, &h->xt, (size_t)p * h->ldx * sizeof(float)));
+        CK(hold(h, &h->yt, (size_t)p * h->ldx * sizeof(float)));
         const size_t pb = hpc::obs_panel_bytes(prec, n, p);
         for (int t = 0; t < hpc::obs_pieces(prec); ++t) {
-            CK(cudaMalloc(&h->xp[t], pb));
-            CK(cudaMalloc(&h->yp[t], pb));
+            CK(hold(h, &h->xp[t], pb));
+            CK(hold(h, &h->yp[t], pb));
         }
         std::vector<int2> pl;
         hpc::obs_pair_list(p, pl);
         h->npairs = (int64_t)pl.size();
-        CK(cudaMalloc(&h->pairs, pl.size() * sizeof(int2)));
+        CK(hold(h, &h->pairs, pl.size() * sizeof(int2)));
         CK(cudaMemcpy(h->pairs, pl.data(), pl.size() * sizeof(int2), cudaMemcpyHostToDevice));
         if (!hpc::obs_make_maps(prec, h->yp[0], h->yp[1], h->xp[0], h->xp[1], n, p, h->obs_maps)) {
             std::snprintf(g_last_error, sizeof g_last_error, "TMA descriptors of the Obs panels could not be encoded");
@@ -1144,7 +1171,7 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         }
     }
     if (variant == HPC_COV) {
-    CK(cudaMalloc(&h->S, (size_t)p * h->ld * vs));
+    CK(hold(h, &h->S, (size_t)p * h->ld * vs));
     CK(cudaMemsetAsync(h->S, 0, (size_t)p * h->ld * vs, h->stream));
     }
     if (variant == HPC_COV) {
@@ -1156,34 +1183,34 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
             return fail(HPC_ERR_NOT_IMPLEMENTED);
         }
     }
-    CK(cudaMalloc(&h->rinfo, p * sizeof(int4)));
-    CK(cudaMalloc(&h->offlist, p * sizeof(int)));
-    CK(cudaMalloc(&h->rdv, h->ld * vs));
+    CK(hold(h, &h->rinfo, p * sizeof(int4)));
+    CK(hold(h, &h->offlist, p * sizeof(int)));
+    CK(hold(h, &h->rdv, h->ld * vs));
     CK(cudaMemsetAsync(h->rdv, 0, h->ld * vs, h->stream));
-    CK(cudaMalloc(&h->pmask, (h->ld / 32) * sizeof(unsigned)));
+    CK(hold(h, &h->pmask, (h->ld / 32) * sizeof(unsigned)));
     CK(cudaMemsetAsync(h->pmask, 0, (h->ld / 32) * sizeof(unsigned), h->stream));
     if (variant == HPC_COV) {
         std::vector<long long> so;
         h->screen_grid = h->vdt == HPC_F64 ? hpc::screen_plan<double>((int)p, h->num_sms, so)
                                            : hpc::screen_plan<float>((int)p, h->num_sms, so);
-        CK(cudaMalloc(&h->seqoff, so.size() * sizeof(long long)));
+        CK(hold(h, &h->seqoff, so.size() * sizeof(long long)));
         CK(cudaMemcpy(h->seqoff, so.data(), so.size() * sizeof(long long), cudaMemcpyHostToDevice));
         // bound screening (the grid is filled after each Gram)
         const int bj = h->vdt == HPC_F64 ? hpc::screen_box_cols<double>() : hpc::screen_box_cols<float>();
         h->nbm = (int)((p + bj - 1) / bj);
         const int64_t items = p * (int64_t)h->nbm / 2 + p;
         h->pairs_cap = (int)std::min<int64_t>(std::max<int64_t>(items / 4, 1024), 0x7ffffff0);
-        CK(cudaMalloc(&h->m1, (size_t)p * h->nbm * sizeof(unsigned short)));
+        CK(hold(h, &h->m1, (size_t)p * h->nbm * sizeof(unsigned short)));
         if (h->nbm % 8 == 0) {
             h->ngl = (h->nbm / 8 + 7) / 8 * 8;
-            CK(cudaMalloc(&h->m1g, (size_t)p * h->ngl * sizeof(unsigned short)));
+            CK(hold(h, &h->m1g, (size_t)p * h->ngl * sizeof(unsigned short)));
         }
-        CK(cudaMalloc(&h->colmax, (size_t)h->nbm * vs));
-        CK(cudaMalloc(&h->pairs_list, (size_t)h->pairs_cap * sizeof(int2)));
+        CK(hold(h, &h->colmax, (size_t)h->nbm * vs));
+        CK(hold(h, &h->pairs_list, (size_t)h->pairs_cap * sizeof(int2)));
         h->row_items_cap = (int)std::min<int64_t>((p + 7) / 8 * (int64_t)h->nbm, 0x7ffffff0);
-        CK(cudaMalloc(&h->row_items, (size_t)h->row_items_cap * sizeof(int2)));
+        CK(hold(h, &h->row_items, (size_t)h->row_items_cap * sizeof(int2)));
     }
-    for (int b = 0; b < 2; ++b) CK(cudaMalloc(&h->rp[b], (p + 1) * sizeof(int)));
+    for (int b = 0; b < 2; ++b) CK(hold(h, &h->rp[b], (p + 1) * sizeof(int)));
     const int64_t cap0 = o.capacity > 0 ? o.capacity : std::max<int64_t>(32 * p, 1024);
     {
         const int s = alloc_candidates(h, cap0);
@@ -1191,18 +1218,18 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
         const int s2 = grow_csr(h, 2 * cap0);
         if (s2 != HPC_OK) return fail(s2);
     }
-    CK(cudaMalloc(&h->bk_cnt, p * sizeof(int)));
-    CK(cudaMalloc(&h->bk_off, (p + 1) * sizeof(int)));
-    CK(cudaMalloc(&h->bk_cur, p * sizeof(int)));
-    CK(cudaMalloc(&h->bk_len, p * sizeof(int)));
-    CK(cudaMalloc(&h->bk_uoff, (p + 1) * sizeof(long long)));
-    CK(cudaMalloc(&h->bk_long, p * sizeof(int)));
-    CK(cudaMalloc(&h->cnt2, p * sizeof(int)));
-    CK(cudaMalloc(&h->scan_part, std::max<int64_t>(1, (p + 4095) / 4096) * sizeof(hpc::ScanPart)));
+    CK(hold(h, &h->bk_cnt, p * sizeof(int)));
+    CK(hold(h, &h->bk_off, (p + 1) * sizeof(int)));
+    CK(hold(h, &h->bk_cur, p * sizeof(int)));
+    CK(hold(h, &h->bk_len, p * sizeof(int)));
+    CK(hold(h, &h->bk_uoff, (p + 1) * sizeof(long long)));
+    CK(hold(h, &h->bk_long, p * sizeof(int)));
+    CK(hold(h, &h->cnt2, p * sizeof(int)));
+    CK(hold(h, &h->scan_part, std::max<int64_t>(1, (p + 4095) / 4096) * sizeof(hpc::ScanPart)));
     h->nblk = (int)std::min<int64_t>((p + 7) / 8, 152 * 16);
-    CK(cudaMalloc(&h->part_obj, (size_t)h->nblk * 4 * sizeof(double)));
-    CK(cudaMalloc(&h->part_ls, (size_t)h->nblk * 16 * 4 * sizeof(double)));
-    CK(cudaMalloc(&h->d_ctrl, sizeof(hpc::Ctrl)));
+    CK(hold(h, &h->part_obj, (size_t)h->nblk * 4 * sizeof(double)));
+    CK(hold(h, &h->part_ls, (size_t)h->nblk * 16 * 4 * sizeof(double)));
+    CK(hold(h, &h->d_ctrl, sizeof(hpc::Ctrl)));
     CK(cudaMemsetAsync(h->d_ctrl, 0, sizeof(hpc::Ctrl), h->stream));
     CK(cudaMallocHost(&h->h_ctrl, sizeof(hpc::Ctrl)));
     std::memset(h->h_ctrl, 0, sizeof(hpc::Ctrl));
@@ -1247,10 +1274,10 @@ int hpc_prefetch_x(hpc_handle h, const void* X, hpc_dtype xdt, int x_on_host) {
         const size_t xbytes = (size_t)h->n * h->p * dtype_size(xdt);
         if (xbytes > h->x_stage_bytes) {
             if (h->pf_issued) CUDA_TRY(cudaEventSynchronize(h->ev_pf));
-            if (h->x_stage) cudaFree(h->x_stage);
+            if (h->x_stage) release(h, h->x_stage);
             h->x_stage = nullptr;
             h->x_stage_bytes = 0;
-            CUDA_TRY(cudaMalloc(&h->x_stage, xbytes));
+            CUDA_TRY(hold(h, &h->x_stage, xbytes));
             h->x_stage_bytes = xbytes;
         }
         CUDA_TRY(cudaMemcpyAsync(h->x_stage, X, xbytes, cudaMemcpyHostToDevice, h->pf_stream));
@@ -1656,10 +1683,10 @@ namespace {
 
 int adj_reserve(hpc_ctx* h, size_t bytes) {
     if (bytes <= h->adj_bytes) return HPC_OK;
-    if (h->adj_buf) cudaFree(h->adj_buf);
+    if (h->adj_buf) release(h, h->adj_buf);
     h->adj_buf = nullptr;
     h->adj_bytes = 0;
-    CUDA_TRY(cudaMalloc(&h->adj_buf, bytes));
+    CUDA_TRY(hold(h, &h->adj_buf, bytes));
     h->adj_bytes = bytes;
     return HPC_OK;
 }
@@ -2202,10 +2229,7 @@ int hpc_get_info(hpc_handle h, hpc_info* info) {
     info->precision = h->precision;
     info->value_dtype = h->vdt;
     info->capacity = h->cap;
-    const size_t vs = dtype_size(h->vdt);
-    info->device_bytes = (int64_t)((size_t)h->p * h->ld * vs + h->cap * (8 + 2 * vs) +
-                                   2 * h->cap * (2 * 4 + 5 * vs + 2) + 2 * h->csr_cap * (4 + vs) +
-                                   (size_t)h->p * 32 + h->gram_scratch_bytes);
+    info->device_bytes = (int64_t)h->held_bytes;
     info->lambda1 = h->lam1;
     info->lambda2 = h->lam2;
     return HPC_OK;

@@ -41,7 +41,7 @@ struct Ctrl {
     int nnz_cur;         // entries of the current iterate (device loop)
     int iter_limit;      // the device loop stops after this many accepted iterations
     int use_stop;        // the device loop stops at the stopping rule
-    int pad2_;
+    int obs_next;        // next block pair of the Obs pair kernel (shared tile counter)
     // lambda path in one launch: point index, estimate staging offset (both advanced
     // by the next point's begin kernel), and the point's start time
     int path_pt, path_pt_next;

@@ -140,6 +140,7 @@ __global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl, int use_cond, cud
     }
     if (tid == 0) {
         ctrl->em_count = 0;
+        ctrl->obs_next = 0;
         ctrl->n_offrows = 0;
         ctrl->n_mirror = 0;
         ctrl->n_pairs = 0;
@@ -1380,6 +1381,11 @@ __device__ __forceinline__ unsigned sort_key(const Buckets<T>& bk, int pos) {
     return (unsigned)bk.col_a[pos] * 2u + ((bk.fl_a[pos] & kEntMirror) ? 1u : 0u);
 }
 
+template <typename T>
+__device__ __forceinline__ unsigned sort_key_b(const Buckets<T>& bk, int pos) {
+    return (unsigned)bk.col_b[pos] * 2u + ((bk.fl_b[pos] & kEntMirror) ? 1u : 0u);
+}
+
 // Append the kept partner entries of this warp (flag `mir`, final position pos in
 // row i) to the fill list.
 template <typename T>
@@ -1393,7 +1399,8 @@ __device__ __forceinline__ void push_mirrors(const Buckets<T>& bk, Ctrl* ctrl, b
 }
 
 // Rows longer than one warp are sorted by a whole block in shared memory (bitonic
-// on 64-bit (key, index) words) up to this many entries; beyond it, by ranks.
+// on 64-bit (key, index) words) up to this many entries; beyond it, in chunks of
+// this many that are then merged by ranks (binary searches in the other chunks).
 constexpr int kSortSmem = 4096;
 constexpr int kSortShort = 32;
 
@@ -1529,27 +1536,66 @@ k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
                 bk.fl_b[beg + q] = bk.fl_a[e];
             }
         } else {
-            // rank of each entry against all keys of the row, streamed in tiles
-            unsigned* s_k32 = reinterpret_cast<unsigned*>(s_key);
-            constexpr int kTile = 2 * kSortSmem;
-            for (int e0 = 0; e0 < c; e0 += kThreads) {
-                const int e = e0 + threadIdx.x;
-                const unsigned ke = e < c ? sort_key(bk, beg + e) : 0xffffffffu;
-                int rank = 0;
-                for (int f0 = 0; f0 < c; f0 += kTile) {
-                    __syncthreads();
-                    for (int f = threadIdx.x; f < kTile; f += kThreads)
-                        s_k32[f] = f0 + f < c ? sort_key(bk, beg + f0 + f) : 0xffffffffu;
-                    __syncthreads();
-                    const int fn = min(kTile, c - f0);
-                    for (int f = 0; f < fn; ++f) rank += (s_k32[f] < ke) ? 1 : 0;
+            // (a) every chunk of kSortSmem entries sorted in shared memory into the b arrays
+            for (int q0 = 0; q0 < c; q0 += kSortSmem) {
+                const int cn = min(kSortSmem, c - q0);
+                int n2 = 1;
+                while (n2 < cn) n2 <<= 1;
+                __syncthreads();
+                for (int e = threadIdx.x; e < n2; e += kThreads)
+                    s_key[e] = e < cn ? ((unsigned long long)sort_key(bk, beg + q0 + e) << 32) | (unsigned)e : ~0ull;
+                __syncthreads();
+                for (int k = 2; k <= n2; k <<= 1) {
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        for (int t = threadIdx.x; t < n2; t += kThreads) {
+                            const int u = t ^ j;
+                            if (u > t) {
+                                const unsigned long long x = s_key[t], y = s_key[u];
+                                if ((x > y) == ((t & k) == 0)) { s_key[t] = y; s_key[u] = x; }
+                            }
+                        }
+                        __syncthreads();
+                    }
                 }
-                if (e < c) {
-                    bk.col_b[beg + rank] = bk.col_a[beg + e];
-                    bk.w_b[beg + rank] = bk.w_a[beg + e];
-                    bk.om_b[beg + rank] = bk.om_a[beg + e];
-                    bk.fl_b[beg + rank] = bk.fl_a[beg + e];
+                for (int q = threadIdx.x; q < cn; q += kThreads) {
+                    const int e = beg + q0 + (int)(s_key[q] & 0xffffffffu);
+                    bk.col_b[beg + q0 + q] = bk.col_a[e];
+                    bk.w_b[beg + q0 + q] = bk.w_a[e];
+                    bk.om_b[beg + q0 + q] = bk.om_a[e];
+                    bk.fl_b[beg + q0 + q] = bk.fl_a[e];
                 }
+            }
+            __syncthreads();
+            // (b) the rank of each entry in the row: its place in its own chunk plus, in every
+            // other chunk, the number of keys below its own (a binary search; the keys are
+            // distinct); the entry moves to that place in the a arrays (no longer needed)
+            const int nck = (c + kSortSmem - 1) / kSortSmem;
+            for (int e = threadIdx.x; e < c; e += kThreads) {
+                const int qc = e / kSortSmem;
+                const unsigned ke = sort_key_b(bk, beg + e);
+                int rank = e - qc * kSortSmem;
+                for (int r = 0; r < nck; ++r) {
+                    if (r == qc) continue;
+                    int lo = r * kSortSmem, hi = min(c, lo + kSortSmem);
+                    const int first = lo;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sort_key_b(bk, beg + mid) < ke) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    rank += lo - first;
+                }
+                bk.col_a[beg + rank] = bk.col_b[beg + e];
+                bk.w_a[beg + rank] = bk.w_b[beg + e];
+                bk.om_a[beg + rank] = bk.om_b[beg + e];
+                bk.fl_a[beg + rank] = bk.fl_b[beg + e];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < c; e += kThreads) {
+                bk.col_b[beg + e] = bk.col_a[beg + e];
+                bk.w_b[beg + e] = bk.w_a[beg + e];
+                bk.om_b[beg + e] = bk.om_a[beg + e];
+                bk.fl_b[beg + e] = bk.fl_a[beg + e];
             }
         }
         __syncthreads();

@@ -74,18 +74,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                      ptx::smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // K-major, 128-byte swizzle, 8-row groups 1024 bytes apart, descriptor version 1.
@@ -109,12 +97,16 @@ struct ObsCfg {
     static constexpr int kMmaK = 32 / kElem;
     static constexpr int kStageBytes = kPieces * 2 * kPanelTile;    // A and B tiles, each piece
     static constexpr int kStages = MODE == kObsBf16x3 ? 3 : 5;
-    static constexpr int kTransBytes = 2 * 2 * kT * 4 * 4;          // threshold bits, transposed: [side][buffer][kT][4]
-    static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
+    static constexpr int kRing = 8;                                  // pair slots between the roles
+    static constexpr int kLook = 4;                                  // pairs published ahead of the loads
+    static constexpr int kSupBytes = kRing * kT * (16 + 4);          // support masks (uint4) and CSR starts
+    static constexpr int kCtlBytes = 512;                            // barriers, pair slots, TMEM address
+    static constexpr int kSmem = kStages * kStageBytes + kSupBytes + kCtlBytes + 1024;
 };
 
 constexpr int kEpiWarps = 8;
 constexpr int kObsThreads = 128 + 32 * kEpiWarps;     // warpgroup 0: roles; warpgroups 1-2: epilogue
+constexpr int kHelpThreads = 64;                      // warps 2-3: support masks
 // Registers per thread after setmaxnreg (warpgroup 0 down, the epilogue warpgroups up);
 // the host checks that the launch's pool covers both (kMinLaunchRegs) before launching.
 constexpr int kRegsSmall = 56;
@@ -133,10 +125,72 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 
-// Persistent pair kernel: one CTA per SM walks the pairs blockIdx.x, blockIdx.x +
-// grid, ... of the pair list (bi <= bj, bands of row blocks).  For pair (I, J)
-// it forms Z[I, J] = Y^T[I] X^T[J]^T / n and Z[J, I] = Y^T[J] X^T[I]^T / n and emits
-// both sides.
+// v[O + b] for a run-time b in 0..31 without indexing registers dynamically: a
+// five-level tree of selects on the bits of b.
+template <int O>
+__device__ __forceinline__ float pick32(const float (&v)[64], int b) {
+    float t16[16], t8[8], t4[4], t2[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t16[i] = (b & 16) ? v[O + 16 + i] : v[O + i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t8[i] = (b & 8) ? t16[8 + i] : t16[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t4[i] = (b & 4) ? t8[4 + i] : t8[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) t2[i] = (b & 2) ? t4[2 + i] : t4[i];
+    return (b & 1) ? t2[1] : t2[0];
+}
+
+// Support of row g in the columns j0 .. j0 + 127: a 128-bit mask and the CSR position
+// of the row's first entry at or after column j0 (columns ascend, so the k-th set bit
+// of the mask is entry qs + k).  A binary search narrows long rows; the entries are
+// then read eight at a time with independent loads.
+__device__ __forceinline__ void row_tile_support(const int* __restrict__ rp, const int* __restrict__ ci, int g, int j0,
+                                                 uint4& mask, int& qs) {
+    uint32_t m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+    int lo = rp[g];
+    const int e = rp[g + 1];
+    int hi = e;
+    while (hi - lo > 8) {
+        const int mid = (lo + hi) >> 1;
+        if (ci[mid] < j0) lo = mid + 1;
+        else hi = mid;
+    }
+    // lower_bound lies in [lo, hi]; entries before lo are < j0
+    int q = lo;
+    bool more = true;
+    int first = -1;
+    while (more) {
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = q + u < e ? ci[q + u] : 0x7fffffff;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = v[u] - j0;
+            if (first < 0 && v[u] >= j0) first = q + u;
+            const uint32_t bit = (c >= 0 && c < kT) ? 1u << (c & 31) : 0u;
+            const int w = c >> 5;
+            m0 |= w == 0 ? bit : 0u;
+            m1 |= w == 1 ? bit : 0u;
+            m2 |= w == 2 ? bit : 0u;
+            m3 |= w == 3 ? bit : 0u;
+        }
+        more = q + 8 < e && v[7] < j0 + kT;
+        q += 8;
+    }
+    qs = first < 0 ? e : first;
+    mask = make_uint4(m0, m1, m2, m3);
+}
+
+// Persistent pair kernel: one CTA per SM takes block pairs (I <= J) from a shared
+// counter, in the pair list's order (bands of row blocks, so the pairs in flight
+// across the GPU share their panels in L2).  For pair (I, J) it forms, in TMEM,
+//   phase 0:  Y^T[I] X^T[J]^T = n Z[I, J]          (row r, column c: n Z_{I0+r, J0+c})
+//   phase 1:  X^T[I] Y^T[J]^T = n Z[J, I]^T        (row r, column c: n Z_{J0+c, I0+r})
+// so that the thread holding row r of the tile has both n Z_ij and n Z_ji of every
+// pair (i, j) = (I0 + r, J0 + c) in its registers: the transpose of Alg. 3 step 6
+// costs nothing, and the screening test and the emission of both (i, j) and (j, i)
+// happen in one thread.
 //
 // Chunked accumulation, as in the Gram: the K loop of a pair is cut into chunks
 // (chunk_start), each chunk accumulates both tiles from zero into one TMEM
@@ -145,23 +199,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 // the chunk, not with n.
 //
 // Roles:
-//   warp 0      TMA producer (thread 0), running ahead across pairs: per chunk the
-//               stages of (Y^T[I], X^T[J]), then of (Y^T[J], X^T[I]);
+//   warp 0      thread 0: takes the CTA's next pair from the counter, publishes it in
+//               a ring of kRing pair slots, and streams per chunk the stages of
+//               (Y^T[I], X^T[J]), then of (X^T[I], Y^T[J]) through TMA;
 //   warp 1      MMA issuer (thread 32) and TMEM owner: chunk c of the CTA's sequence
-//               into accumulator pair c & 1 (columns 256 (c & 1) + {0, 128} for
-//               Z[I, J], Z[J, I]);
-//   warps 2-3   idle (they complete warpgroup 0, which hands registers to the
-//               epilogue with setmaxnreg);
-//   warps 4-7   running sums of Z[I, J] (warp w: TMEM lanes 32 (w % 4) .. + 31, one
-//               row of 128 columns per thread), and after the last chunk the
-//               emission of the pair, row by row;
-//   warps 8-11  running sums of Z[J, I] (the same lanes), staged after the last chunk
-//               through shared memory, half the tile at a time, for the transpose;
-//               for a diagonal pair (I = J) warps 4-7 stage their own rows.
-// acc_full[b] (one commit) and acc_empty[b] (eight epilogue warps) hand the
-// accumulator pairs over.  Every wait is bounded; after an abort every role stops,
-// the epilogue warps keep meeting at their barriers, the loads in flight drain and
-// TMEM is freed.
+//               into accumulator pair c & 1 (columns 256 (c & 1) + {0, 128});
+//   warps 2-3   the support of the pair's rows in its columns (row_tile_support),
+//               into the slot's masks, ahead of the epilogue;
+//   warps 4-11  running sums (warp w: TMEM lanes 32 (w % 4) .. + 31, one row per
+//               thread; warps 4-7 columns 0-63, warps 8-11 columns 64-127 of both
+//               tiles), then the screening test and the emission.
+// pair_full / pair_empty hand the pair slots around, sup_full the masks, acc_full /
+// acc_empty the accumulator pairs.  Every wait is bounded; after an abort every
+// role stops, the loads in flight drain and TMEM is freed.
 template <int MODE>
 __global__ void __launch_bounds__(kObsThreads, 1)
 k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUtensorMap yb,
@@ -169,21 +219,26 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
            int npairs, int k_tiles, int p, int64_t n, const int* __restrict__ rp, const int* __restrict__ ci,
            const float* __restrict__ cv, Emit<float> em, Ctrl* __restrict__ ctrl, int chunk_kt, int lead_kt) {
     using C = ObsCfg<MODE>;
+    constexpr int R = C::kRing;
     const float lam1 = (float)ctrl->lam1;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint32_t* tbits = reinterpret_cast<uint32_t*>(smem + C::kStages * C::kStageBytes);   // [2][2][kT][4]
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + C::kTransBytes);
+    uint4* s_mask = reinterpret_cast<uint4*>(smem + C::kStages * C::kStageBytes);           // [R][kT]
+    int* s_qs = reinterpret_cast<int*>(s_mask + R * kT);                                   // [R][kT]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStageBytes + C::kSupBytes);
     uint64_t* empty = full + C::kStages;
     uint64_t* acc_full = empty + C::kStages;     // [2]
     uint64_t* acc_empty = acc_full + 2;          // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    uint64_t* pair_full = acc_empty + 2;         // [R]
+    uint64_t* pair_empty = pair_full + R;        // [R]
+    uint64_t* sup_full = pair_empty + R;         // [R]
+    int2* s_pair = reinterpret_cast<int2*>(sup_full + R);                                  // [R]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(s_pair + R);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    static_assert(8 * (2 * C::kStages + 4) + 8 <= 256, "barrier area");
+    static_assert(8 * (2 * C::kStages + 4 + 3 * R) + 8 * R + 8 <= C::kCtlBytes, "control area");
     static_assert(C::kSmem <= 232448, "shared memory per block");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int my_pairs = (int)blockIdx.x < npairs ? (npairs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (chunk_kt < 1) chunk_kt = 1;
     if (lead_kt < chunk_kt) lead_kt = chunk_kt;
     const int nch = num_chunks(k_tiles, chunk_kt, lead_kt);
@@ -191,6 +246,11 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) { ptx::mbar_init(&full[s], 1); ptx::mbar_init(&empty[s], 1); }
         for (int b = 0; b < 2; ++b) { ptx::mbar_init(&acc_full[b], 1); ptx::mbar_init(&acc_empty[b], kEpiWarps); }
+        for (int s = 0; s < R; ++s) {
+            ptx::mbar_init(&pair_full[s], 1);
+            ptx::mbar_init(&pair_empty[s], 1 + 2 + kEpiWarps);      // MMA issuer, helper warps, epilogue warps
+            ptx::mbar_init(&sup_full[s], kHelpThreads);
+        }
         *abort_flag = 0;
         ptx::mbar_init_fence();
     }
@@ -205,21 +265,45 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
 
     long long issued = 0;
     if (warp < 4) {
-        // producer, MMA issuer and two idle warps: one warpgroup that gives registers away
+        // producer, MMA issuer and the helpers: one warpgroup that gives registers away
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsSmall));
         if (threadIdx.x == 0) {
-            // ---------------- producer: per chunk, phase 0 streams (Y^T[I], X^T[J]), phase 1 (Y^T[J], X^T[I])
+            // ---------------- scheduler and producer
+            // Pairs are published kLook ahead of the loads, so that the counter's and the
+            // pair list's latency, and the helpers' mask work, stay off the MMA's path.
             long long g = 0;
-            bool ok = true;
-            for (int lt = 0; lt < my_pairs && ok; ++lt) {
-                const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+            bool ok = true, pub_done = false;
+            int pub = 0;
+            int nxt = atomicAdd(&ctrl->obs_next, 1);
+            auto publish = [&]() -> bool {
+                const int slot = pub % R;
+                if (!ptx::mbar_wait_bounded(&pair_empty[slot], ((uint32_t)(pub / R) & 1u) ^ 1u, abort_flag,
+                                            kWaitLimit))
+                    return false;
+                const int idx = nxt;
+                const int2 pr = idx < npairs ? pairs[idx] : make_int2(-1, -1);
+                if (idx < npairs) nxt = atomicAdd(&ctrl->obs_next, 1);
+                s_pair[slot] = pr;
+                ptx::mbar_arrive(&pair_full[slot]);
+                ++pub;
+                pub_done = pr.x < 0;
+                return true;
+            };
+            for (int q = 0; q < C::kLook && ok && !pub_done; ++q) ok = publish();
+            for (int t = 0; ok && t < pub; ++t) {
+                const int2 pr = s_pair[t % R];
+                if (pr.x < 0) break;
+                if (!pub_done && !publish()) break;            // pair t + kLook
                 const int I0 = pr.x * kT, J0 = pr.y * kT;
-                const int phases = pr.x == pr.y ? 1 : 2;
                 for (int c = 0; c < nch && ok; ++c) {
                     const int kt0 = chunk_start(c, k_tiles, chunk_kt, lead_kt);
                     const int kt1 = chunk_start(c + 1, k_tiles, chunk_kt, lead_kt);
-                    for (int phase = 0; phase < phases && ok; ++phase) {
-                        const int ra = phase == 0 ? I0 : J0, rb = phase == 0 ? J0 : I0;
+                    for (int phase = 0; phase < 2 && ok; ++phase) {
+                        // phase 0: A = Y^T[I], B = X^T[J]; phase 1: A = X^T[I], B = Y^T[J]
+                        const CUtensorMap* ma = phase == 0 ? &ya : &xa;
+                        const CUtensorMap* mb = phase == 0 ? &xa : &ya;
+                        const CUtensorMap* la = phase == 0 ? &yb : &xb;
+                        const CUtensorMap* lb = phase == 0 ? &xb : &yb;
                         for (int kt = kt0; kt < kt1; ++kt, ++g) {
                             const int s = (int)(g % C::kStages);
                             const uint32_t ph = (uint32_t)(g / C::kStages) & 1u;
@@ -230,11 +314,11 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                             uint8_t* st = smem + s * C::kStageBytes;
                             ptx::mbar_expect_tx(&full[s], C::kStageBytes);
                             const int kc = kt * C::kBK;
-                            ptx::tma_load_2d(st, &ya, &full[s], kc, ra);
-                            ptx::tma_load_2d(st + kPanelTile, &xa, &full[s], kc, rb);
+                            ptx::tma_load_2d(st, ma, &full[s], kc, I0);
+                            ptx::tma_load_2d(st + kPanelTile, mb, &full[s], kc, J0);
                             if (C::kPieces > 1) {
-                                ptx::tma_load_2d(st + 2 * kPanelTile, &yb, &full[s], kc, ra);
-                                ptx::tma_load_2d(st + 3 * kPanelTile, &xb, &full[s], kc, rb);
+                                ptx::tma_load_2d(st + 2 * kPanelTile, la, &full[s], kc, I0);
+                                ptx::tma_load_2d(st + 3 * kPanelTile, lb, &full[s], kc, J0);
                             }
                             ++issued;
                         }
@@ -246,9 +330,12 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
             constexpr uint32_t idesc = instr_desc<MODE>();
             long long g = 0, gc = 0;
             bool ok = true;
-            for (int lt = 0; lt < my_pairs && ok; ++lt) {
-                const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
-                const int phases = pr.x == pr.y ? 1 : 2;
+            for (int t = 0; ok; ++t) {
+                const int slot = t % R;
+                if (!ptx::mbar_wait_bounded(&pair_full[slot], (uint32_t)(t / R) & 1u, abort_flag, kWaitLimit)) break;
+                const int2 pr = s_pair[slot];
+                ptx::mbar_arrive(&pair_empty[slot]);
+                if (pr.x < 0) break;
                 for (int c = 0; c < nch && ok; ++c, ++gc) {
                     const int b = (int)(gc & 1);
                     if (!ptx::mbar_wait_bounded(&acc_empty[b], ((uint32_t)(gc >> 1) & 1u) ^ 1u, abort_flag,
@@ -259,7 +346,7 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                     tc_fence_after();
                     const int kt0 = chunk_start(c, k_tiles, chunk_kt, lead_kt);
                     const int kt1 = chunk_start(c + 1, k_tiles, chunk_kt, lead_kt);
-                    for (int phase = 0; phase < phases && ok; ++phase) {
+                    for (int phase = 0; phase < 2 && ok; ++phase) {
                         const uint32_t d = tmem + (uint32_t)(b * 2 * kT + phase * kT);
                         for (int kt = kt0; kt < kt1; ++kt, ++g) {
                             const int s = (int)(g % C::kStages);
@@ -272,7 +359,7 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                             const uint32_t st = ptx::smem_u32(smem + s * C::kStageBytes);
                             const uint32_t a_hi = st, b_hi = st + kPanelTile, a_lo = st + 2 * kPanelTile,
                                            b_lo = st + 3 * kPanelTile;
-    #pragma unroll
+#pragma unroll
                             for (int kk = 0; kk < C::kBK / C::kMmaK; ++kk) {
                                 const uint32_t off = kk * 32;
                                 const uint32_t acc0 = (kt > kt0 || kk > 0) ? 1u : 0u;
@@ -288,23 +375,47 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
                     if (ok) umma_commit(&acc_full[b]);
                 }
             }
+        } else if (warp >= 2) {
+            // ---------------- support masks of the pair's rows (two rows per thread)
+            const int ht = threadIdx.x - 64;
+            for (int t = 0;; ++t) {
+                const int slot = t % R;
+                if (!ptx::mbar_wait_bounded(&pair_full[slot], (uint32_t)(t / R) & 1u, abort_flag, kWaitLimit)) break;
+                const int2 pr = s_pair[slot];
+                if (pr.x < 0) break;
+                const int I0 = pr.x * kT, J0 = pr.y * kT;
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int rr = ht + kHelpThreads * h2;
+                    const int g = I0 + rr;
+                    uint4 m = make_uint4(0u, 0u, 0u, 0u);
+                    int qs = 0;
+                    if (g < p) row_tile_support(rp, ci, g, J0, m, qs);
+                    s_mask[slot * kT + rr] = m;
+                    s_qs[slot * kT + rr] = qs;
+                }
+                ptx::mbar_arrive(&sup_full[slot]);
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&pair_empty[slot]);
+            }
         }
     } else {
-        // the epilogue warpgroups take them: the running sums of 128 columns live in registers
+        // the epilogue warpgroups take them: 2 x 64 running sums live in registers
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsEpi));
         // ---------------- epilogue
-        // Thread (side, row-local r) owns row g = (side ? J0 : I0) + r of its tile and the
-        // tile's columns c = 0..127 of the other block (column k0 + c).  The entry pair
-        // {(i, j), (j, i)} is emitted when it is in the support, on the diagonal, or when
-        // n |Z_ij| or n |Z_ji| exceeds lambda1 n; each side emits its own entry with its own
-        // value, flagged as paired (the other side emits the partner).  A side's threshold
-        // bits reach the other side transposed: per column, a warp ballot over its 32 rows
-        // (tbits), so no value crosses between the warps.  A diagonal pair is one tile,
-        // held by side 0, whose bits meet their own transpose.
+        // Thread (q4, lane) of warp w owns row r = 32 q4 + lane of the tile (g = I0 + r)
+        // and the columns c0 .. c0 + 63 (c0 = 64 half).  For each column it holds
+        // a = n Z_ij and b = n Z_ji (j = J0 + c).  The pair {(i, j), (j, i)} is emitted
+        // when it is in the support, on the diagonal, or when |a| or |b| exceeds lambda1 n;
+        // (i, j) carries a / n and (j, i) carries b / n, both flagged as paired (each is the
+        // other's partner) and both with w_ij (the iterate is symmetric).  In a diagonal
+        // pair (I = J) each thread emits only its own row's entry: (j, i) is the row of
+        // another thread of the same tile.
         const int q4 = warp & 3;
-        const int side = (warp - 4) >> 2;            // 0: Z[I, J] rows, 1: Z[J, I] rows
-        const int r = q4 * 32 + lane;                // TMEM lane = local row
-        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(side * kT);
+        const int half = (warp - 4) >> 2;
+        const int r = q4 * 32 + lane;
+        const int c0 = half * 64;
+        const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c0;
         // Z = (Y X) / n: the sums are tested against lambda1 n and only the emitted entries
         // are scaled.  The threshold is lowered by 2^-20 relative, so that the entries
         // emitted include every one whose scaled value exceeds lambda1 in FP32; an extra
@@ -312,84 +423,77 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
         const float inv_n = 1.0f / (float)n;
         const float thr = (float)((double)lam1 * (double)n * (1.0 - 0x1p-20));
         long long gc = 0;
-        for (int lt = 0; lt < my_pairs; ++lt) {
-            const int2 pr = pairs[blockIdx.x + (long long)lt * gridDim.x];
+        for (int t = 0;; ++t) {
+            const int slot = t % R;
+            const uint32_t rph = (uint32_t)(t / R) & 1u;
+            bool got = !*abort_flag && ptx::mbar_wait_bounded(&pair_full[slot], rph, abort_flag, kWaitLimit);
+            got = __all_sync(kFull, got);
+            if (!got) break;
+            const int2 pr = s_pair[slot];
+            if (pr.x < 0) break;
             const int I0 = pr.x * kT, J0 = pr.y * kT;
             const bool diag_pair = pr.x == pr.y;
-            const bool active = side == 0 || !diag_pair;
-            const int g = (side ? J0 : I0) + r;          // this thread's row
-            const int k0 = side ? I0 : J0;               // its tile's first column
-            // the row's support in the columns k0 .. k0 + 127: a 128-bit mask, and the CSR
-            // position of its first entry there (columns ascend, so entry k of the mask sits
-            // at qs + k); read before the accumulator is waited for, so that the loads'
-            // latency overlaps it
-            uint32_t smask[4] = {0u, 0u, 0u, 0u};
-            int qs = 0;
-            if (active && g < p) {
-                int q = rp[g];
-                const int qe = rp[g + 1];
-                while (q < qe && ci[q] < k0) ++q;
-                qs = q;
-                for (; q < qe && ci[q] < k0 + kT; ++q) {
-                    const int c = ci[q] - k0;
-                    smask[c >> 5] |= 1u << (c & 31);
-                }
-            }
-            float acc[kT];
-#pragma unroll
-            for (int q = 0; q < kT; ++q) acc[q] = 0.f;
+            const int g = I0 + r;
+            float za[64], zb[64];
             bool have = true;
             for (int c = 0; c < nch; ++c, ++gc) {
                 const int b = (int)(gc & 1);
-                bool got = have && !*abort_flag &&
-                           ptx::mbar_wait_bounded(&acc_full[b], (uint32_t)(gc >> 1) & 1u, abort_flag, kWaitLimit);
-                got = __all_sync(kFull, got);
-                if (!got) { have = false; continue; }
+                bool ok = have && !*abort_flag &&
+                          ptx::mbar_wait_bounded(&acc_full[b], (uint32_t)(gc >> 1) & 1u, abort_flag, kWaitLimit);
+                ok = __all_sync(kFull, ok);
+                if (!ok) { have = false; continue; }
                 tc_fence_after();
-                if (active) {
 #pragma unroll
-                    for (int s8 = 0; s8 < kT / 16; ++s8) {
-                        uint32_t v[16];
-                        tmem_ld16(lane_base + (uint32_t)(b * 2 * kT + s8 * 16), v);
-                        tmem_ld_wait();
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    uint32_t va[16], vb[16];
+                    tmem_ld16(lane_base + (uint32_t)(b * 2 * kT + s4 * 16), va);
+                    tmem_ld16(lane_base + (uint32_t)(b * 2 * kT + kT + s4 * 16), vb);
+                    tmem_ld_wait();
+                    if (c == 0) {
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) acc[s8 * 16 + q] += __uint_as_float(v[q]);
+                        for (int q = 0; q < 16; ++q) {
+                            za[s4 * 16 + q] = __uint_as_float(va[q]);
+                            zb[s4 * 16 + q] = __uint_as_float(vb[q]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            za[s4 * 16 + q] += __uint_as_float(va[q]);
+                            zb[s4 * 16 + q] += __uint_as_float(vb[q]);
+                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx_arrive(&acc_empty[b]);
             }
-            // own threshold bits, and their transpose by ballots: column c's word (bit l = row
-            // 32 q4 + l of this warp) is kept by lane c % 32
-            uint32_t own[4] = {0u, 0u, 0u, 0u}, tw[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int c = 0; c < kT; ++c) {
-                const bool big = active && have && g < p && !(fabsf(acc[c]) <= thr);
-                own[c >> 5] |= (uint32_t)big << (c & 31);
-                const uint32_t word = __ballot_sync(kFull, big);
-                if ((c & 31) == lane) tw[c >> 5] = word;
-            }
-            // layout [side][buffer][column][warp]; the buffer alternates by pair, so the next
-            // pair's words cannot overwrite words another thread still reads
-            uint32_t* tb = tbits + (size_t)(lt & 1) * kT * 4;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tb[((side * 2) * kT + 32 * k + lane) * 4 + q4] = tw[k];
-            asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");     // every side's bits are in
-            const bool mine = active && have && g < p;
-            // the other side's bits for this row: its words for column r (a diagonal pair: this side's)
-            const int other = diag_pair ? 0 : 1 - side;
-            uint32_t emb[4];
+            if (!have) break;
+            bool sok = ptx::mbar_wait_bounded(&sup_full[slot], rph, abort_flag, kWaitLimit);
+            sok = __all_sync(kFull, sok);
+            if (!sok) break;
+            const uint4 m4 = s_mask[slot * kT + r];
+            const int qs = s_qs[slot * kT + r];
+            const uint32_t sm[2] = {half ? m4.z : m4.x, half ? m4.w : m4.y};
+            const int before0 = half ? __popc(m4.x) + __popc(m4.y) : 0;
+            const bool mine = g < p;
+            uint32_t eb[2];
             int cnt = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t e = own[k] | tb[((other * 2) * kT + r) * 4 + k] | smask[k];
-                const int lim = p - (k0 + 32 * k);              // columns k0 + 32 k + b < p
-                if (lim < 32) e &= lim > 0 ? (1u << lim) - 1u : 0u;
-                if (diag_pair && (r >> 5) == k) e |= 1u << (r & 31);      // the diagonal
-                emb[k] = mine ? e : 0u;
-                cnt += __popc(emb[k]);
+            for (int k = 0; k < 2; ++k) {
+                uint32_t w = 0u;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const bool big = !(fabsf(za[32 * k + q]) <= thr) || !(fabsf(zb[32 * k + q]) <= thr);
+                    w |= (uint32_t)big << q;
+                }
+                w |= sm[k];
+                const int lim = p - (J0 + c0 + 32 * k);                 // columns J0 + c0 + 32 k + q < p
+                if (lim < 32) w &= lim > 0 ? (1u << lim) - 1u : 0u;
+                if (diag_pair && (r >> 5) == 2 * half + k) w |= 1u << (r & 31);      // the diagonal
+                eb[k] = mine ? w : 0u;
+                cnt += __popc(eb[k]);
             }
+            if (!diag_pair) cnt *= 2;
             // one atomic per warp: an inclusive scan of the lanes' counts, the last lane takes
             // the warp's total from the emission counter and every lane writes from its offset
             int incl = cnt;
@@ -401,32 +505,39 @@ k_obs_pair(const __grid_constant__ CUtensorMap ya, const __grid_constant__ CUten
             int base = 0;
             if (lane == 31 && incl > 0) base = atomicAdd(&ctrl->em_count, incl);
             base = __shfl_sync(kFull, base, 31);
-            if (!mine) continue;
             int pos = base + incl - cnt;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t em_bits = emb[k];
-                while (em_bits) {
-                    const int b = __ffs(em_bits) - 1;
-                    em_bits &= em_bits - 1u;
-                    const int c = 32 * k + b;
-                    float a = 0.f;                              // acc[32 k + b] without dynamic indexing
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) a = (t == b) ? acc[32 * k + t] : a;
-                    const uint32_t sw = smask[k];
-                    const bool sup = (sw >> b) & 1u;
-                    int before = __popc(sw & ((1u << b) - 1u));
-#pragma unroll
-                    for (int t = 0; t < k; ++t) before += __popc(smask[t]);
+            for (int k = 0; k < 2; ++k) {
+                uint32_t bits = eb[k];
+                const uint32_t sw = sm[k];
+                const int before = before0 + (k ? __popc(sm[0]) : 0);
+                while (bits) {
+                    const int q = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const int j = J0 + c0 + 32 * k + q;
+                    const bool sup = (sw >> q) & 1u;
+                    const float om = sup ? cv[qs + before + __popc(sw & ((1u << q) - 1u))] : 0.f;
+                    const unsigned fl = 0x40000000u | (sup ? 0x80000000u : 0u);
                     if (pos < em.cap) {
                         em.row[pos] = g;
-                        em.col[pos] = (int)((unsigned)(k0 + c) | 0x40000000u | (sup ? 0x80000000u : 0u));
-                        em.w[pos] = __fmul_rn(a, inv_n);
-                        em.om[pos] = sup ? cv[qs + before] : 0.f;
+                        em.col[pos] = (int)((unsigned)j | fl);
+                        em.w[pos] = __fmul_rn(k ? pick32<32>(za, q) : pick32<0>(za, q), inv_n);
+                        em.om[pos] = om;
                     }
                     ++pos;
+                    if (!diag_pair) {
+                        if (pos < em.cap) {
+                            em.row[pos] = j;
+                            em.col[pos] = (int)((unsigned)g | fl);
+                            em.w[pos] = __fmul_rn(k ? pick32<32>(zb, q) : pick32<0>(zb, q), inv_n);
+                            em.om[pos] = om;
+                        }
+                        ++pos;
+                    }
                 }
             }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&pair_empty[slot]);
         }
     }
     __syncwarp();

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.support import support_diff_ok
 from workloads import BATCH_PROBLEMS, omega0_banded, make_x, sample_x_cpu
 
 pytestmark = pytest.mark.gpu
@@ -31,9 +32,12 @@ def test_batch_of_uneven_problems_matches_oracle_and_sequential(lib, device_loop
         s.close()
     assert all(st["status"] == 0 for st in stats)
     for (p, n), X, est in zip(shapes, Xs, batch):
-        ref = oracle.solve(oracle.gram(X), lam1, lam2, eps=1e-9, max_iter=20000)
+        S = oracle.gram(X)
+        ref = oracle.solve(S, lam1, lam2, eps=1e-9, max_iter=20000)
         om = est.to_scipy(p).toarray()
         assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-5
+        ok, detail = support_diff_ok(om, ref.omega, lam1, lam2, S=S)
+        assert ok, (p, detail)
     # sequential, default stream
     for X, est in zip(Xs, batch):
         with lib.Solver(torch.as_tensor(X).cuda(), lam1, lam2, precision=lib.PREC_FP32, eps=1e-7,
@@ -99,9 +103,12 @@ def test_sixteen_problem_workload(lib):
         s.close()
     assert all(st["status"] == 0 for st in stats)
     for X, w, est in list(zip(Xs, BATCH_PROBLEMS, ests))[:2]:
-        ref = oracle.solve(oracle.gram(X.cpu().numpy()), w.lambda1, w.lambda2, eps=1e-9, max_iter=20000)
+        S = oracle.gram(X.cpu().numpy())
+        ref = oracle.solve(S, w.lambda1, w.lambda2, eps=1e-9, max_iter=20000)
         om = est.to_scipy(w.p).toarray()
         assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-5
+        ok, detail = support_diff_ok(om, ref.omega, w.lambda1, w.lambda2, S=S)
+        assert ok, (w.p, detail)
     for X, w, est in list(zip(Xs, BATCH_PROBLEMS, ests))[::5]:
         with lib.Solver(X, w.lambda1, w.lambda2, precision=lib.PREC_BF16X3, eps=w.eps, max_iter=20000) as s:
             s.solve()

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.support import support_diff_ok
 from workloads import WORKLOADS, make_x, small_problem
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +39,8 @@ def test_obs_matches_oracle(lib, p, n, seed, lam1):
     assert _stopped_ok(st), st
     err = np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega)
     assert err < 1e-5, err
+    ok, detail = support_diff_ok(om, ref.omega, lam1, lam2, X=X)
+    assert ok, detail
     assert np.array_equal(om, om.T)
 
 
@@ -101,3 +104,5 @@ def test_auto_variant_matches_oracle(lib, n, p):
     assert _stopped_ok(st), st
     ref = oracle.solve(oracle.gram(X), 0.15, 0.1, eps=1e-9, max_iter=20000)
     assert np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega) < 1e-5
+    ok, detail = support_diff_ok(om, ref.omega, 0.15, 0.1, X=X)
+    assert ok, detail

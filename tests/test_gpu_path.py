@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.support import support_diff_ok
 from workloads import small_problem
 
 pytestmark = pytest.mark.gpu
@@ -29,6 +30,8 @@ def test_path_points_match_cold_oracle_solves(lib):
         assert pts[t]["nnz"] == ests[t].col.size
         err = np.linalg.norm(om - ref.omega) / np.linalg.norm(ref.omega)
         assert err < 1e-5, (t, lam1, err)
+        ok, detail = support_diff_ok(om, ref.omega, lam1, lam2, S=S)
+        assert ok, (t, lam1, detail)
     # the path gets denser as lambda1 decreases
     nnz = [q["nnz"] for q in pts]
     assert nnz == sorted(nnz)

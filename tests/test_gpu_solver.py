@@ -9,6 +9,7 @@ import pytest
 import scipy.sparse as sp
 
 import oracle
+from tests.support import support_diff_ok
 from workloads import WORKLOADS, make_x, small_problem
 
 pytestmark = pytest.mark.gpu
@@ -27,15 +28,7 @@ def _torch():
 
 def _support_diff_ok(om_gpu, om_ref, S, lam1, lam2):
     """Support identical except entries of the reference within THRESH_BAND of the threshold."""
-    G = oracle.gradient(om_ref, oracle.times_S(om_ref, S), lam2)
-    a = om_gpu != 0
-    b = om_ref != 0
-    diff = np.argwhere(a != b)
-    for i, j in diff:
-        near = abs(om_ref[i, j]) <= THRESH_BAND or abs(abs(G[i, j]) - lam1) <= THRESH_BAND
-        if not near:
-            return False, (i, j, om_gpu[i, j], om_ref[i, j], G[i, j])
-    return True, len(diff)
+    return support_diff_ok(om_gpu, om_ref, lam1, lam2, S=S, band=THRESH_BAND)
 
 
 def _solve_gpu(lib, X, lam1, lam2, **opt):

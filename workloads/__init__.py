@@ -449,3 +449,17 @@ def small_problem(p: int, n: int, degree: float, seed: int, graph: str = "random
     else:
         om = omega0_tridiagonal(p)
     return sample_x_cpu(om, n, seed)
+
+
+def hub_factor_problem(p: int, n: int, seed: int, loading: float = 0.5) -> np.ndarray:
+    """A one-factor X (float64, n x p) with a hub column: x_0 = z and x_j = loading z + e_j
+    (z, e_j iid N(0, 1)), so that S_0j is near loading for every j while the other
+    off-diagonal entries of S stay near loading^2.  Its precision matrix is a star centred
+    on column 0; at lambda1 between loading^2 and loading the hub row's candidate list
+    holds about p entries at every iteration (an edge case of the candidate sort)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = rng.standard_normal(n)
+    X = rng.standard_normal((n, p))
+    X[:, 0] = z
+    X[:, 1:] += loading * z[:, None]
+    return X
