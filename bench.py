@@ -161,32 +161,38 @@ def _dist():
 
 
 def cpu_baseline_run(workload, X_host_cols, p_sample, max_seconds=25.0):
-    """Time the FP64 oracle (as it stands) on the leading p_sample x p_sample sub-problem.
+    """Time the FP64 oracle (as it stands: its CSR-iterate form of Alg. 2) on the leading
+    p_sample x p_sample sub-problem of the workload: Gram, then the solve to the
+    workload's stopping rule.
 
-    The oracle's cost per iteration and of its Gram both grow as p^2 at fixed n and
-    row density, so its rate at p is rate(p_sample) * (p_sample / p)^2.
+    Its Gram costs n p^2 and each of its iterations d p^2 (the candidate gradient over the
+    whole matrix; d = nonzeros per row), so its rate at the full p is projected as
+    rate(p_sample) * (p_sample / p)^2 -- a projection from a timed sample, labelled so.
     """
     import numpy as np
 
     import oracle
 
     t0 = time.perf_counter()
-    S = oracle.gram(X_host_cols)
-    res = oracle.solve(S, workload.lambda1, workload.lambda2, eps=workload.eps, max_iter=100000)
+    S = oracle.gram_chunked(X_host_cols)
+    threads = max(1, min(16, os.cpu_count() or 1))
+    res = oracle.solve_sparse(S, workload.lambda1, workload.lambda2, eps=workload.eps, max_iter=100000,
+                              block=512, threads=threads)
     dt = time.perf_counter() - t0
     rate_sample = res.iterations / dt
     scale = (p_sample / workload.p) ** 2
     try:
         from threadpoolctl import threadpool_info
 
-        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [threads])
     except Exception:
         cores = os.cpu_count() or 1
     return {"value": rate_sample * scale, "unit": UNIT, "cores": int(cores), "kind": "oracle",
-            "sample": (f"full FP64 oracle solve (Gram + {res.iterations} iterations, {dt:.1f} s) of the leading "
-                       f"{p_sample}x{p_sample} sub-problem (same n={X_host_cols.shape[0]}, lambda), "
-                       f"rate scaled by ({p_sample}/{workload.p})^2"),
-            "seconds": dt, "iterations": res.iterations}
+            "sample": (f"FP64 oracle (CSR form of Alg. 2) timed on the leading {p_sample}x{p_sample} sub-problem "
+                       f"(same n={X_host_cols.shape[0]}, lambda, eps): Gram + {res.iterations} iterations in "
+                       f"{dt:.1f} s = {rate_sample:.3f} iters/s; projected to p={workload.p} by "
+                       f"({p_sample}/{workload.p})^2"),
+            "seconds": dt, "iterations": res.iterations, "rate_sample": rate_sample}
 
 
 def sample_subproblem(w, ps):
@@ -618,33 +624,39 @@ def run_row(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.  Each step is a
+    bounded sample of the workload (its leading cpu_sample_p x cpu_sample_p sub-problem,
+    Gram + solve); ms_per_step is that step's measured wall time, and value the rate
+    projected to the full workload (cpu_baseline_run), on this arm's metric and unit."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import numpy as np
-
     from workloads import WORKLOADS
 
     w = WORKLOADS[args.workload]
-    ps = args.cpu_sample_p
+    ps = min(args.cpu_sample_p, w.p)
     X = sample_subproblem(w, ps)
-    vals, secs, its = [], [], []
+    recs = []
     for k in range(args.warmup + args.steps):
         r = cpu_baseline_run(w, X, ps)
         if k >= args.warmup:
-            vals.append(r["value"])
-            secs.append(r["seconds"])
-            its.append(r["iterations"])
-    value = sum(its) / sum(secs) * (ps / w.p) ** 2
+            recs.append(r)
+    secs = sum(r["seconds"] for r in recs)
+    its = sum(r["iterations"] for r in recs)
+    value = its / secs * (ps / w.p) ** 2
     line = {"impl": "reference", "metric": METRIC.replace("p=65536 n=32768", f"p={w.p} n={w.n}"), "value": value,
-            "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs) / (ps / w.p) ** 2,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded generator, leading sub-problem of the workload)",
+            "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * secs / len(recs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64",
+            "data": f"synthetic (seeded: {w.graph} SDD Omega0, rows of X ~ N(0, Omega0^-1))",
             "config": {"workload": w.name, "p": w.p, "n": w.n, "lambda1": w.lambda1, "lambda2": w.lambda2,
-                       "eps": w.eps, "sample_p": ps},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                       "eps": w.eps, "x_dtype": w.x_dtype},
+            "projection": {"measured_on_p": ps, "measured_iters_per_s": its / secs,
+                           "scale": (ps / w.p) ** 2,
+                           "rule": "Gram n p^2 and iterations d p^2: rate(p) = rate(sample) (sample / p)^2",
+                           "ms_per_step": "measured wall time of one sample step (Gram + solve)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": recs[-1]["cores"], "kind": "oracle",
+                             "sample": recs[-1]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -779,8 +791,12 @@ def main(argv=None):
     else:
         g_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # SIMT FP32 FMA peak at the max SM clock
         g_bound, g_src = "alu", "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    # the nominal dense bf16 rate of the part (2.25 PFLOP/s; TF32 half of it), for the
+    # fraction of the tensor pipe's own peak beside the fraction of the measured figure
+    g_nominal = (2250.0 / (2.0 if solver.precision_used() == hpc.PREC_TF32 else 1.0)) if tensor_gram else g_peak
     roof_gram = {"kernel": "gram", "bound": g_bound, "achieved": g_achieved, "peak": g_peak, "unit": "TFLOP/s",
                  "frac": g_achieved / g_peak, "peak_source": g_src,
+                 "nominal_peak": g_nominal, "frac_of_nominal": g_achieved / g_nominal,
                  # the Gram's traffic depends on its tile-order band and on whether it writes the block maxima
                  "traffic": measured_traffic("gram", p, n, f"band{tuning['gram_band']}.maxima{tuning['gram_maxima']}."
                                                            f"sched{tuning['gram_schedule']}."),
@@ -854,7 +870,7 @@ def main(argv=None):
                  "value": ast["iterations"] / (e0.elapsed_time(e1) / 1000.0), "iterations": ast["iterations"]}
         alt.close()
 
-    plain = None
+    plain, plain_est = None, None
     if not args.no_plain and solver.precision_used() not in (hpc.PREC_FP32, hpc.PREC_FP64) and rank == 0:
         ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=hpc.PREC_FP32, eps=w.eps,
                         max_iter=100000, device_loop=args.device_loop)
@@ -873,8 +889,32 @@ def main(argv=None):
         plain = {"time_to_converge_ms": e0.elapsed_time(e1), "iterations": pst["iterations"],
                  "gram_ms": pst["ms_gram"], "rel_diff_vs_mixed": float(
                      math.sqrt((A - B).multiply(A - B).sum()) / math.sqrt(A.multiply(A).sum()))}
+        plain_est = om_plain
         ps.close()
 
+    # error against the cached FP64 reference of this workload (written once by
+    # tests/golden/make_fullsize_refs.py from the oracle), when the repository holds one
+    accuracy = None
+    ref_file = os.path.join(ROOT, "tests", "golden", f"ref_{w.name}.npz")
+    if rank == 0 and os.path.exists(ref_file):
+        import scipy.sparse as sp
+
+        z = np.load(ref_file, allow_pickle=False)
+        R = sp.csr_matrix((z["data"], z["indices"], z["indptr"]), shape=(p, p))
+        rn = math.sqrt(R.multiply(R).sum())
+
+        def err(est):
+            E = est.to_scipy(p).astype(np.float64)
+            D = E - R
+            pe, pr = (E != 0), (R != 0)
+            return {"rel_fro": math.sqrt(D.multiply(D).sum()) / rn,
+                    "support_differences": int((pe != pr).nnz), "nnz": int(E.nnz)}
+
+        accuracy = {"reference": f"FP64 oracle fixed point (eps {float(z['eps']):g}, {int(z['iterations'])} iterations, "
+                                 f"certified within {float(z['distance_bound_rel']):.2e} relative of the minimiser)",
+                    "nnz_ref": int(R.nnz), "mixed": err(solver.get_omega())}
+        if plain is not None:
+            accuracy["plain_fp32"] = err(plain_est)
     cpu = None
     if not args.no_cpu and rank == 0:
         ps = min(args.cpu_sample_p, w.p)
@@ -913,7 +953,7 @@ def main(argv=None):
                                               recs[-1]["nnz"] / p),
                                 s=recs[-1]["iterations"], d="final nnz / p"),
             "roofline": roof, "roofline_kernels": [roof_gram, roof_scr], "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
-            "cpu_baseline": cpu, "plain_fp32": plain, "other_loop": other,
+            "cpu_baseline": cpu, "plain_fp32": plain, "accuracy_vs_fp64_reference": accuracy, "other_loop": other,
             "autotune_trials": [(t["knob"], t["value"], round(t["ms"], 4)) for t in tune_trials],
         }
         print(json.dumps(line), flush=True)
