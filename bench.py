@@ -454,6 +454,44 @@ def run_row(args):
               roof, clk.summary(), None, None, sweep=rows)
         return 0
 
+    if args.row == "gram":
+        # The tensor-core Gram of the headline workload under every tile order the autotuner
+        # chooses from (band of row blocks x tile schedule), block maxima on: one load per
+        # setting, in a fixed order, after one warm-up load.  Timed with the library's CUDA
+        # events around the Gram kernel; launch k of k_gram_tc_persist (after the warm-up)
+        # is setting k of the list.
+        w = WORKLOADS[args.workload]
+        X = make_x(w, device="cuda")
+        s = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p,
+                       xdtype={"bf16": hpc.BF16, "f32": hpc.F32}[w.x_dtype], precision=hpc.PREC_AUTO,
+                       eps=w.eps, max_iter=10, timing=1)
+        s.load_x(X)
+        flops = float(w.n) * w.p * (w.p + 1)
+        peak = bf16_sus if bf16_sus else bf16
+        sweep = []
+        with ClockSampler(0) as clk:
+            for band in (2, 4, 8, 16, 32, 64):
+                for sched in (1, 0):
+                    s.set_tuning(gram_band=band, gram_schedule=sched, gram_maxima=1)
+                    s.load_x(X)
+                    st = s.iterate(0).as_dict()
+                    ms = st["ms_gram_kernel"]
+                    sweep.append({"band": band, "schedule": sched, "ms": ms,
+                                  "tflops": flops / (ms / 1000.0) / 1e12,
+                                  "traffic": measured_traffic("gram", w.p, w.n, f"band{band}.maxima1.sched{sched}.")})
+        best = min(sweep, key=lambda r: r["ms"])
+        roof = {"kernel": "gram", "bound": "tensor", "achieved": best["tflops"], "peak": peak, "unit": "TFLOP/s",
+                "frac": best["tflops"] / peak, "traffic": best["traffic"],
+                "peak_source": f"{peak_src} (bf16 sustained)", "nominal_peak": 2250.0,
+                "frac_of_nominal": best["tflops"] / 2250.0}
+        _line(f"tensor-core Gram TFLOP/s at p={w.p} n={w.n}, best tile order", best["tflops"], "TFLOP/s",
+              best["ms"], args, True, w.x_dtype,
+              {"workload": w.name, "p": w.p, "n": w.n, "gram_precision": s.precision_name(),
+               "best": {"band": best["band"], "schedule": best["schedule"]}},
+              roof, clk.summary(), len(sweep), None, sweep=sweep)
+        s.close()
+        return 0
+
     if args.row == "batch":
         Xs = [make_x(wk, device="cuda") for wk in BATCH_PROBLEMS]
         streams = [torch.cuda.Stream() for _ in BATCH_PROBLEMS]
@@ -684,7 +722,7 @@ def main(argv=None):
                     help="store X in this dtype instead of the workload's (profiling the one-product BF16 Gram "
                          "at sizes a full ncu capture allows)")
     ap.add_argument("--row", default=None,
-                    choices=["path", "batch", "adjoint", "obs", "select", "crossover", "chain"],
+                    choices=["path", "batch", "adjoint", "obs", "select", "crossover", "chain", "gram"],
                     help="time a further row of the hot path instead of the headline solve")
     ap.add_argument("--chain-p", default="80000,160000,320000,640000,1280000",
                     help="dimensions of the chain row (comma separated)")

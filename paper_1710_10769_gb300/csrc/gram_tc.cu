@@ -502,9 +502,76 @@ __device__ __forceinline__ void nanmax_warp(float& mx, bool& nan) {
     nan = __any_sync(kFull, nan);
 }
 
+// max that returns NaN when either operand is NaN (so a block's maximum flags a NaN)
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+__device__ __forceinline__ float warp_max_nan(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max_nan(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// An interior block pair (I < J, both blocks whole; rows 16-byte aligned): rows read as float4 (lane l takes
+// columns 4 l .. 4 l + 3), their maxima taken from the registers, and staged in shared
+// memory with column c at c + c / 32 of a 131-float row, so that both the row stores
+// (eight lanes per 128-byte phase) and the column reads (32 rows of one column) hit 32
+// different banks.
+constexpr int kMirRow = 131;
+static_assert(kMirT * kMirRow * 4 <= kMirSmem, "interior staging fits the block's shared memory");
+
+template <bool MAXIMA>
+__device__ __forceinline__ void mirror_interior(float* __restrict__ S, int64_t lds, int I0, int J0, int bi, int bj,
+                                                uint16_t* __restrict__ m1, int nbm, float* t) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cs = 4 * lane + (lane >> 3);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = warp + 8 * (8 * h + q);
+            v[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I0 + r) * lds + J0 + 4 * lane);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int r = warp + 8 * (8 * h + q);
+            float* row = t + r * kMirRow + cs;
+            row[0] = v[q].x;
+            row[1] = v[q].y;
+            row[2] = v[q].z;
+            row[3] = v[q].w;
+            if constexpr (MAXIMA) {
+                float mx = max_nan(max_nan(fabsf(v[q].x), fabsf(v[q].y)), max_nan(fabsf(v[q].z), fabsf(v[q].w)));
+                mx = warp_max_nan(mx);
+                if (lane == 0) m1[(int64_t)(I0 + r) * nbm + bj] = mx != mx ? (uint16_t)0x7fc0 : bf16_up_f(mx);
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = warp; c < kMirT; c += 8) {
+        const int pc = c + (c >> 5);
+        float mx = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = lane + 32 * m;
+            const float x = t[r * kMirRow + pc];
+            S[(int64_t)(J0 + c) * lds + I0 + r] = x;
+            if constexpr (MAXIMA) mx = max_nan(mx, fabsf(x));
+        }
+        if constexpr (MAXIMA) {
+            mx = warp_max_nan(mx);
+            if (lane == 0) m1[(int64_t)(J0 + c) * nbm + bi] = mx != mx ? (uint16_t)0x7fc0 : bf16_up_f(mx);
+        }
+    }
+}
+
 template <bool MAXIMA>
 __global__ void __launch_bounds__(256)
-k_mirror_max(float* __restrict__ S, int64_t lds, int p, int nb, uint16_t* __restrict__ m1, int nbm) {
+k_mirror_max(float* __restrict__ S, int64_t lds, int p, int nb, uint16_t* __restrict__ m1, int nbm, int vec) {
     extern __shared__ float mir[];
     float* t = mir;                                               // [kMirT][kMirT + 1]
     float* rmax = mir + kMirT * (kMirT + 1);                      // [kMirT] upper-part row maxima
@@ -518,8 +585,12 @@ k_mirror_max(float* __restrict__ S, int64_t lds, int p, int nb, uint16_t* __rest
     if (bj >= nb) return;
     const bool dg = bi == bj;
     const int I0 = bi * kMirT, J0 = bj * kMirT;
+    if (vec && !dg && J0 + kMirT <= p) {
+        mirror_interior<MAXIMA>(S, lds, I0, J0, bi, bj, m1, nbm, t);
+        return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // rows of S[I, J]: warp w takes rows w, w + 8, ...; lane l columns l + 32 m.  Only
+    // a diagonal or ragged block pair: rows of S[I, J]: warp w takes rows w, w + 8, ...; lane l columns l + 32 m.  Only
     // loads and shared stores here, so that the loads of several rows are in flight.
 #pragma unroll 4
     for (int r = warp; r < kMirT; r += 8) {
@@ -603,8 +674,10 @@ cudaError_t launch_mirror(float* S, int64_t lds, int64_t p, uint16_t* m1, int nb
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (m1) k_mirror_max<true><<<(unsigned)pairs, 256, kMirSmem, s>>>(S, lds, (int)p, nb, m1, nbm);
-    else k_mirror_max<false><<<(unsigned)pairs, 256, kMirSmem, s>>>(S, lds, (int)p, nb, nullptr, 0);
+    // the interior blocks' float4 rows need 16-byte aligned rows: S aligned and lds a multiple of 4
+    const int vec = (lds % 4 == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0) ? 1 : 0;
+    if (m1) k_mirror_max<true><<<(unsigned)pairs, 256, kMirSmem, s>>>(S, lds, (int)p, nb, m1, nbm, vec);
+    else k_mirror_max<false><<<(unsigned)pairs, 256, kMirSmem, s>>>(S, lds, (int)p, nb, nullptr, 0, vec);
     return cudaGetLastError();
 }
 
