@@ -11,21 +11,22 @@
 //   BF16 X           : one panel, one product (bf16 x bf16 is exact in FP32);
 //   TF32             : FP32 panel rounded to TF32, kind::tf32 products.
 //
-// Tiles.  A 128 x 256 tile S[I, J] (UMMA M = 128, N = 256) is accumulated over
-// the whole K = n in 256 TMEM columns.  Only the tiles that touch the upper
-// triangle run, in bands of row blocks (a tuning knob) so that the tiles in flight
-// share A and B panels in L2.  Each entry with i <= j is written together with its
-// mirror S[j, i]: S is bitwise symmetric by construction.
+// Tiles.  A 128 x 256 tile S[I, J] (UMMA M = 128, N = 256) is accumulated in
+// chunks of K (each from a zero TMEM accumulator, the chunk sums added in FP32
+// round-to-nearest in registers).  Only the tiles that touch the upper triangle
+// run, in bands of row blocks (a tuning knob) so that the tiles in flight share A
+// and B panels in L2.  The product kernel writes S_ij for i <= j; a second pass
+// (k_mirror_max) writes S_ji = S_ij, so S is bitwise symmetric by construction, and
+// optionally the block maxima of |S| for the bound screening.
 //
-// Persistent kernel (192 threads, one CTA per SM, CTA g takes tiles g, g + grid,
-// ...): warp 0 issues TMA loads into a ring of stages, warp 1 issues MMAs from
-// one lane and owns the TMEM allocation (two 256-column accumulators, so the
-// epilogue of one tile overlaps the MMAs of the next), warps 2-5 drain the
-// accumulator (TMEM lanes 32 (w % 4) .. + 31), scale by 1/n, store the tile and
-// its mirror, and optionally write the block maxima of |S| for the bound
-// screening.  Every mbarrier wait is bounded; on timeout the CTA records an error
-// word, stops issuing, waits (bounded) for its own copies and MMAs, frees its
-// TMEM and returns.
+// Persistent kernel (384 threads, one CTA per SM): warp 0 takes tiles and issues
+// TMA loads into a ring of stages, warp 1 issues MMAs from one lane and owns the
+// TMEM allocation (two 256-column accumulators, so the epilogue of one chunk
+// overlaps the MMAs of the next), warps 4-11 drain the accumulators (TMEM lanes
+// 32 (w % 4) .. + 31, one column half each), sum the chunks, scale by 1/n and store
+// the upper part of the tile.  Every mbarrier wait is bounded; on timeout the CTA
+// records an error word, stops issuing, waits (bounded) for its own copies and
+// MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -235,8 +236,8 @@ __device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
 //   warps 4-11  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and the column
 //               half (w - 4) / 4 of the tile (128 columns), keeps the running
 //               sums of its row's 128 columns in registers, and after a tile's last
-//               chunk scales by 1/n and stores the tile, its mirror and the block
-//               maxima.
+//               chunk scales by 1/n and stores the entries with i <= j (the lower
+//               triangle and the block maxima come from the mirror pass).
 // acc_full[b] (one commit) and acc_empty[b] (eight epilogue warps) hand the
 // buffers over.  Every wait is bounded; an abort stops all roles, drains the
 // loads in flight and frees TMEM.
