@@ -409,7 +409,8 @@ def run_row(args):
                 X = cast_x(sample_x_cuda(om0, n, seed), "f32")
                 lam1 = math.sqrt(2.0 * math.log(p) / n)
                 s = hpc.Solver(None, lam1, lam2, variant=hpc.OBS, n=n, p=p, xdtype=hpc.F32,
-                               precision=hpc.PREC_FP32, eps=1e-6, max_iter=5000, timing=1)
+                               precision=hpc.PREC_FP32, eps=1e-6, max_iter=5000, timing=1,
+                               device_loop=args.device_loop)
                 if i == 0:                      # first use of the kernels and the graph capture
                     s.load_x(X)
                     s.solve()

@@ -86,13 +86,16 @@ typedef enum {
  * (time per flop of each on this GPU), Cov is chosen when
  *   gamma_dense 2np^2 + gamma_sparse 2dp^2(st+1) < gamma_dense 2np^2 s + gamma_sparse 2dnp(st+1).
  * s, t, d and the ratio gamma_sparse / gamma_dense are the arguments; a value <= 0
- * takes the default: s = 40, t = 3, d = 2 and ratio HPC_GAMMA_RATIO, the medians
- * measured on GB300 over a sweep of p = 40000, n = 100 ... 12800 on chain and random
- * graphs (gamma_sparse: the Cov iteration's time per flop the lemma counts for it;
- * gamma_dense: the Obs Z product's time per flop).  The two modelled costs (in
- * gamma_dense units) go to *cost_cov and *cost_obs (nullable).  Returns HPC_COV or
- * HPC_OBS; HPC_ERR_ARG for n < 1 or p < 1. */
-#define HPC_GAMMA_RATIO 8.0
+ * takes the default: s = 40, t = 3, d = 2 and ratio HPC_GAMMA_RATIO.  The ratio is the
+ * median measured on GB300 over a sweep of p = 40000, n = 100 ... 12800 on chain and
+ * random graphs (gamma_sparse: the Cov iteration's time per flop the lemma counts for
+ * it; gamma_dense: the Obs iteration's time per flop of its Z product); it ranged from
+ * 12 on the random graph to 121 on the chain, whose noisier S leaves the bound
+ * screening less to prune.  With the measured s, t and d of each point the rule picked
+ * the faster variant at 14 of the 16 points.  The two modelled costs (in gamma_dense
+ * units) go to *cost_cov and *cost_obs (nullable).  Returns HPC_COV or HPC_OBS;
+ * HPC_ERR_ARG for n < 1 or p < 1. */
+#define HPC_GAMMA_RATIO 26.0
 int hpc_choose_variant(int64_t n, int64_t p, double s, double t, double d, double gamma_ratio,
                        double* cost_cov, double* cost_obs);
 

@@ -38,7 +38,7 @@ def test_defaults_and_arguments(lib):
     v, cov, obs = _choose(lib, 200, 100, 0, 0, 0, 0)
     assert v == lib.COV                       # p <= n: S is no larger than X
     v0, c0, o0 = _choose(lib, 100, 40000)
-    v1, c1, o1 = _choose(lib, 100, 40000, 40, 3, 2, 8.0)
+    v1, c1, o1 = _choose(lib, 100, 40000, 40, 3, 2, 26.0)
     assert (v0, c0, o0) == (v1, c1, o1)
     with pytest.raises(lib.HpcError):
         _choose(lib, 0, 10)
