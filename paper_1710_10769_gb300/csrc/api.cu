@@ -535,7 +535,7 @@ void capture_window(hpc_ctx* h, const hpc::IterBufs<T>& b, const hpc::LoopCond& 
 //       WHILE (line-search condition) { window evaluation, decision }
 //       compaction, stopping rule, commit of the accepted iterate
 //   }
-// k_iter_begin arms the line-search loop, k_ls_decide ends it, and the commit
+// k_iter_begin arms the line-search loop, the last block of k_ls_eval ends it, and the commit
 // kernel continues or ends the iteration loop.
 // Capture the iteration loop as a WHILE node of graph g (after dep, if any) on
 // the handle lc.iter, which the caller created for g:
@@ -544,7 +544,7 @@ void capture_window(hpc_ctx* h, const hpc::IterBufs<T>& b, const hpc::LoopCond& 
 //       WHILE (line-search condition) { window evaluation, decision }
 //       compaction, stopping rule, commit of the accepted iterate
 //   }
-// k_iter_begin arms the line-search loop, k_ls_decide ends it, and the commit
+// k_iter_begin arms the line-search loop, the last block of k_ls_eval ends it, and the commit
 // kernel continues or ends the iteration loop.
 template <typename T>
 int capture_iteration_loop(hpc_ctx* h, cudaGraph_t g, const cudaGraphNode_t* dep, hpc::LoopCond& lc,
@@ -701,7 +701,7 @@ int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s, bool fre
     s->rel_change = c.rel;
     s->candidates = c.em_count;
     s->grad_pass_launches = c.iter_attempts;
-    s->kernel_launches = c.iter_attempts * loop_launches(h) + 2 * c.ls_windows;
+    s->kernel_launches = c.iter_attempts * loop_launches(h) + hpc::kLaunchesLsWindow * c.ls_windows;
     s->ms_gram = h->ms_gram;
     s->ms_gram_kernel = h->ms_gram_kernel;
     s->capacity_regrows = h->regrows - regrows0;
@@ -801,7 +801,7 @@ int solve_batch_device(const std::vector<hpc_ctx*>& hs, std::vector<int>& status
         s.ms_total = batch_ms;
         s.ms_grad_pass = h->opt.timing ? (double)c.screen_ns * 1e-6 : 0.0;
         s.grad_pass_launches = c.iter_attempts;
-        s.kernel_launches = c.iter_attempts * loop_launches(h) + 2 * c.ls_windows;
+        s.kernel_launches = c.iter_attempts * loop_launches(h) + hpc::kLaunchesLsWindow * c.ls_windows;
         s.ms_gram = h->ms_gram;
         s.ms_gram_kernel = h->ms_gram_kernel;
         s.capacity_regrows = h->regrows - regrows0[t];

@@ -48,7 +48,8 @@ struct Ctrl {
     int path_k, path_keep;        // points; 1 = resume the current point (after a regrow)
     long long path_off, path_off_next, path_need;
     long long t_point;
-    int path_full, pad3_;         // 1 = the estimate staging buffer is full
+    int path_full;                // 1 = the estimate staging buffer is full
+    int ls_done;                  // blocks of the running line-search launch that wrote their partials
     int n_long, pad4_;            // rows of the candidate structure with more than kShortRow entries
     int n_pairs, n_row_items;     // items the bound screening keeps (pure rows; rows with neighbours)
 };
@@ -196,7 +197,7 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
 constexpr int kLaunchesScreen = 6;
 constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 7;
-constexpr int kLaunchesLsWindow = 2;
+constexpr int kLaunchesLsWindow = 1;     // k_ls_eval (its last block decides)
 constexpr int kLaunchesAccept = 4;
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);

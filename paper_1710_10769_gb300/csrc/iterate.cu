@@ -1736,6 +1736,19 @@ k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
 // ------------------------------------------------------------------ 3. line search
 constexpr int kMaxWindow = 16;
 
+// What the last block of a line-search launch needs for the decision.
+struct LsDecide {
+    const double* part_obj;     // objective partials of the current iterate (k_gradient)
+    int n_obj;                  // their count per quantity
+    int stride;                 // quantity stride of both partial arrays
+    int max_halvings;
+    double tau0;
+    int use_cond;               // 1: set the line-search loop's graph condition
+    cudaGraphConditionalHandle cond;
+};
+template <int M>
+__device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const LsDecide& d, Ctrl* ctrl);
+
 // Row i of the unit-offset prefix containing unit u (uoff[i] <= u < uoff[i+1]): a
 // 32-way search by the whole warp (each step narrows the range 32-fold).
 __device__ __forceinline__ int find_unit_row(const long long* __restrict__ uoff, int p, long long u, int lane) {
@@ -1783,7 +1796,7 @@ __device__ __forceinline__ void acc_merge(double& a, double b) { a += b; }
 template <typename T, int M>
 __global__ void __launch_bounds__(kThreads, (M <= 4) ? 3 : 2)
 k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride, double* part_ls,
-          const Ctrl* ctrl) {
+          Ctrl* ctrl, LsDecide dec) {
     using A = typename AccOf<T>::type;
     __shared__ int s_col[kWarps][32];
     __shared__ T s_del[kWarps][M][32];
@@ -1972,6 +1985,7 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride,
         for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
         part_ls[(size_t)(m * 4 + k) * stride + blockIdx.x] = a;
     }
+    ls_finish<M>(part_ls, (int)gridDim.x, dec, ctrl);
 }
 
 // Obs form of the line-search partials (Alg. 3 step 11): tr(D S D) restricted to
@@ -1980,7 +1994,8 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride,
 template <int M>
 __global__ void __launch_bounds__(kThreads)
 k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, double tau0,
-              int stride, double* part_ls, const Ctrl* ctrl) {
+              int stride, double* part_ls, Ctrl* ctrl,
+              LsDecide dec) {
     __shared__ double red[kWarps][M][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -2072,9 +2087,10 @@ k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Bucke
         for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
         part_ls[(size_t)(m * 4 + k) * stride + blockIdx.x] = a;
     }
+    ls_finish<M>(part_ls, (int)gridDim.x, dec, ctrl);
 }
 
-// The sufficient-decrease decision of one window (thread 0 of k_ls_decide).
+// The sufficient-decrease decision of one window (thread 0 of the last block of k_ls_eval).
 __device__ void decide_window(const double* sums, const double* obj, int M, int h_base, int max_halvings,
                               double tau0, double lam1, double lam2, int first, Ctrl* ctrl) {
     if (first) {
@@ -2103,31 +2119,42 @@ __device__ void decide_window(const double* sums, const double* obj, int M, int 
     if (h_base + M > max_halvings) ctrl->flags |= kFlagLsFail;
 }
 
-// Reduce the partials in a fixed order (one warp per quantity, lanes over strided
-// blocks, then a butterfly) and take the decision of Alg. 1 step 9.
-__global__ void __launch_bounds__(1024)
-k_ls_decide(const double* __restrict__ part_ls, int n_ls, const double* __restrict__ part_obj, int n_obj, int stride,
-            int M, int max_halvings, double tau0, int use_cond, cudaGraphConditionalHandle cond, Ctrl* ctrl) {
-    __shared__ double sums[kMaxWindow * 4];
+// The last block of a line-search launch to finish (every block has written its
+// partials) reduces them in a fixed order -- one warp per quantity, lanes over
+// strided blocks, then a butterfly -- and takes the decision of Alg. 1 step 9; the
+// other blocks return.  The order does not depend on which block is last.
+template <int M>
+__device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const LsDecide& d, Ctrl* ctrl) {
+    __shared__ int s_last;
+    __shared__ double sums[M * 4];
     __shared__ double obj[4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->ls_done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
     if (ctrl->flags != 0 || ctrl->ls_accept >= 0) {
-        if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+        if (threadIdx.x == 0) {
+            ctrl->ls_done = 0;
+            if (d.use_cond) cudaGraphSetConditional(d.cond, 0);
+        }
         return;
     }
     const int h_base = ctrl->ls_base;
     const int first = h_base == 0;
     const double lam1 = ctrl->lam1, lam2 = ctrl->lam2;
     const int nq = M * 4 + (first ? 4 : 0);
-    for (int q = warp; q < nq; q += 32) {
+    for (int q = warp; q < nq; q += nwarps) {
         double a = 0.0;
         // eight loads in flight per lane; the additions keep their order
         if (q < M * 4) {
 #pragma unroll 8
-            for (int b = lane; b < n_ls; b += 32) a += part_ls[(size_t)q * stride + b];
+            for (int b = lane; b < n_ls; b += 32) a += __ldcg(part_ls + (size_t)q * d.stride + b);
         } else {
 #pragma unroll 8
-            for (int b = lane; b < n_obj; b += 32) a += part_obj[(size_t)(q - M * 4) * stride + b];
+            for (int b = lane; b < d.n_obj; b += 32) a += __ldcg(d.part_obj + (size_t)(q - M * 4) * d.stride + b);
         }
         a = warp_sum(a);
         if (lane == 0) {
@@ -2136,10 +2163,11 @@ k_ls_decide(const double* __restrict__ part_ls, int n_ls, const double* __restri
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    ctrl->ls_done = 0;
     ctrl->ls_windows += 1;
-    decide_window(sums, obj, M, h_base, max_halvings, tau0, lam1, lam2, first, ctrl);
+    decide_window(sums, obj, M, h_base, d.max_halvings, d.tau0, lam1, lam2, first, ctrl);
     // another window while nothing is accepted and nothing went wrong
-    if (use_cond) cudaGraphSetConditional(cond, (ctrl->flags == 0 && ctrl->ls_accept < 0) ? 1u : 0u);
+    if (d.use_cond) cudaGraphSetConditional(d.cond, (ctrl->flags == 0 && ctrl->ls_accept < 0) ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ 4. accept
@@ -2378,7 +2406,7 @@ void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s) {
     k_row_info<T><<<(p + 255) / 256, 256, 0, s>>>(p, om, rinfo, rdv, nullptr, nullptr, nullptr, nullptr, 0);
 }
 
-// Blocks of k_gradient: one objective partial each (read back by k_ls_decide).
+// Blocks of k_gradient: one objective partial each (read back by ls_finish).
 template <typename T>
 static int gradient_grid(const IterBufs<T>& b) {
     return std::max(1, std::min(b.nblk, b.num_sms * 4));
@@ -2411,10 +2439,15 @@ static int ls_eval_grid(const IterBufs<T>& b) {
     return std::max(1, std::min(b.nblk, want * b.num_sms));
 }
 
+template <typename T>
+static LsDecide ls_decide_args(const IterBufs<T>& b, const LoopCond& lc) {
+    return LsDecide{b.part_obj, gradient_grid(b), b.nblk, b.max_halvings, 1.0, lc.use, lc.ls};
+}
+
 template <typename T, int M>
-static int ls_eval_m(const IterBufs<T>& b, cudaStream_t s) {
+static int ls_eval_m(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
     const int g = ls_eval_grid<T, M>(b);
-    k_ls_eval<T, M><<<g, kThreads, 0, s>>>(b.S, b.ld, b.p, b.bk, b.nblk, b.part_ls, b.ctrl);
+    k_ls_eval<T, M><<<g, kThreads, 0, s>>>(b.S, b.ld, b.p, b.bk, b.nblk, b.part_ls, b.ctrl, ls_decide_args(b, lc));
     return g;
 }
 
@@ -2423,34 +2456,31 @@ static int window_m(int M) { return M == 1 || M == 2 || M == 4 || M == 8 ? M : 1
 template <typename T>
 void launch_ls_window(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
     const int M = window_m(b.ls_window);
-    int g = 0;
+    // one launch per window: its last block to finish takes the decision (ls_finish)
     switch (M) {
-        case 1: g = ls_eval_m<T, 1>(b, s); break;
-        case 2: g = ls_eval_m<T, 2>(b, s); break;
-        case 4: g = ls_eval_m<T, 4>(b, s); break;
-        case 8: g = ls_eval_m<T, 8>(b, s); break;
-        default: g = ls_eval_m<T, 16>(b, s); break;
+        case 1: ls_eval_m<T, 1>(b, lc, s); break;
+        case 2: ls_eval_m<T, 2>(b, lc, s); break;
+        case 4: ls_eval_m<T, 4>(b, lc, s); break;
+        case 8: ls_eval_m<T, 8>(b, lc, s); break;
+        default: ls_eval_m<T, 16>(b, lc, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, g, b.part_obj, gradient_grid(b), b.nblk, M, b.max_halvings, 1.0,
-                                   lc.use, lc.ls, b.ctrl);
 }
 
 template <int M>
-static void ls_eval_obs_m(const IterBufs<float>& b, cudaStream_t s) {
-    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, 1.0, b.nblk, b.part_ls, b.ctrl);
+static void ls_eval_obs_m(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s) {
+    k_ls_eval_obs<M><<<b.nblk, kThreads, 0, s>>>(b.xt, b.ldx, b.n, b.p, b.bk, 1.0, b.nblk, b.part_ls, b.ctrl,
+                                                 ls_decide_args(b, lc));
 }
 
 void launch_ls_window_obs(const IterBufs<float>& b, const LoopCond& lc, cudaStream_t s) {
     const int M = window_m(b.ls_window);
     switch (M) {
-        case 1: ls_eval_obs_m<1>(b, s); break;
-        case 2: ls_eval_obs_m<2>(b, s); break;
-        case 4: ls_eval_obs_m<4>(b, s); break;
-        case 8: ls_eval_obs_m<8>(b, s); break;
-        default: ls_eval_obs_m<16>(b, s); break;
+        case 1: ls_eval_obs_m<1>(b, lc, s); break;
+        case 2: ls_eval_obs_m<2>(b, lc, s); break;
+        case 4: ls_eval_obs_m<4>(b, lc, s); break;
+        case 8: ls_eval_obs_m<8>(b, lc, s); break;
+        default: ls_eval_obs_m<16>(b, lc, s); break;
     }
-    k_ls_decide<<<1, 1024, 0, s>>>(b.part_ls, b.nblk, b.part_obj, gradient_grid(b), b.nblk, M, b.max_halvings, 1.0,
-                                   lc.use, lc.ls, b.ctrl);
 }
 
 template <typename T>
