@@ -729,6 +729,11 @@ def main(argv=None):
                     help="dimensions of the chain row (comma separated)")
     ap.add_argument("--screen-bounds", type=int, default=1, choices=[0, 1],
                     help="0: screen without the block-maxima bounds (same result; for comparison)")
+    ap.add_argument("--fused-tail", type=int, default=None, choices=[0, 1],
+                    help="form of each iteration's steps after the screening pass: 0, the chain of kernels; "
+                         "1, one cooperative kernel (default: the library's)")
+    ap.add_argument("--compare-tail", type=int, default=1, choices=[0, 1],
+                    help="also time the iteration loop with the other form of the tail")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
                     help="pick the launch shapes with the library's autotuner before the warm-up")
     args = ap.parse_args(argv)
@@ -780,6 +785,9 @@ def main(argv=None):
         tune_trials = tr0 + tr1
     if not args.screen_bounds:
         solver.set_tuning(screen_bounds=0)
+        tuning = solver.get_tuning()
+    if args.fused_tail is not None:
+        solver.set_tuning(fused_tail=args.fused_tail)
         tuning = solver.get_tuning()
 
     def step(Xsrc):
@@ -909,6 +917,27 @@ def main(argv=None):
                  "value": ast["iterations"] / (e0.elapsed_time(e1) / 1000.0), "iterations": ast["iterations"]}
         alt.close()
 
+    # the iteration loop with the other form of the tail (the chain of kernels or the
+    # one cooperative kernel), same data, best of three solves
+    other_tail = None
+    if args.compare_tail and rank == 0:
+        flip = 1 - int(tuning.get("fused_tail", 0))
+        solver.set_tuning(fused_tail=flip)
+        runs = []
+        for _ in range(4):
+            solver.load_x(X)
+            runs.append(solver.solve().as_dict())
+        solver.set_tuning(fused_tail=1 - flip)
+        best = min(runs[1:], key=lambda r: r["ms_total"])
+        mine = min(recs, key=lambda r: r["ms_total"])
+        other_tail = {"fused_tail": flip, "iterations": best["iterations"],
+                      "iteration_loop_its": best["iterations"] / (best["ms_total"] / 1000.0),
+                      "kernel_launches_per_iteration": best["kernel_launches"] / max(best["iterations"], 1),
+                      "this_line": {"fused_tail": int(tuning.get("fused_tail", 0)),
+                                    "iteration_loop_its_best_step": mine["iterations"] / (mine["ms_total"] / 1000.0),
+                                    "kernel_launches_per_iteration": mine["kernel_launches"] /
+                                    max(mine["iterations"], 1)}}
+
     plain, plain_est = None, None
     if not args.no_plain and solver.precision_used() not in (hpc.PREC_FP32, hpc.PREC_FP64) and rank == 0:
         ps = hpc.Solver(None, w.lambda1, w.lambda2, n=w.n, p=w.p, xdtype=xdt, precision=hpc.PREC_FP32, eps=w.eps,
@@ -993,6 +1022,7 @@ def main(argv=None):
                                 s=recs[-1]["iterations"], d="final nnz / p"),
             "roofline": roof, "roofline_kernels": [roof_gram, roof_scr], "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches,
             "cpu_baseline": cpu, "plain_fp32": plain, "accuracy_vs_fp64_reference": accuracy, "other_loop": other,
+            "other_tail": other_tail,
             "autotune_trials": [(t["knob"], t["value"], round(t["ms"], 4)) for t in tune_trials],
         }
         print(json.dumps(line), flush=True)

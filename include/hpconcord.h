@@ -461,6 +461,20 @@ typedef struct {
                                   epilogue stores the previous tile (emits the previous
                                   pair); 0 = 2 gram_chunk (Gram), 4 gram_chunk (Obs).
                                   Like gram_chunk it groups S's sums: not tuned (0)  */
+    int32_t fused_tail;        /* 1: an iteration's steps after the screening pass --
+                                  candidate structure, gradient, every line-search
+                                  window with its decision, compaction and stopping
+                                  rule -- run as one cooperative kernel, grid-wide
+                                  barriers between the steps; 0: as the chain of
+                                  separate kernels.  The same entries and decisions
+                                  either way (the windows' partial sums are grouped
+                                  by the line-search grid in both).  On GB300 the two
+                                  take the same time to within a few percent (a
+                                  barrier costs about a kernel boundary inside the
+                                  solve's CUDA graph); the chain is faster where the
+                                  candidate structure is large.  hpc_solve_batch
+                                  runs its problems' iterations concurrently,
+                                  always on the chain (0)                           */
 } hpc_tuning;
 
 /* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max
@@ -478,7 +492,8 @@ int hpc_set_tuning(hpc_handle h, const hpc_tuning* t);
 #define HPC_TUNE_MAX_TRIALS 48
 typedef struct {
     int32_t knob;              /* 0 gram_band, 1 ls_window, 2 ls_blocks_per_sm,
-                                  3 rows_ctas_per_sm, 4 gram_maxima, 5 gram_schedule */
+                                  3 rows_ctas_per_sm, 4 gram_maxima, 5 gram_schedule,
+                                  6 fused_tail */
     int32_t value;
     double  ms;                /* Gram knobs: one data load (transpose, product, block
                                   maxima); the others: one iteration                */
@@ -496,7 +511,8 @@ typedef struct {
  *    each gram_band candidate, then for gram_maxima 1 and 0: three round-robin
  *    rounds over the candidates, each keeping its fastest load (the SM clock
  *    drifts under the power cap).  S is rewritten with identical values.
- *  - The iteration knobs are timed over `iters` outer iterations (>= 1) each,
+ *  - The iteration knobs (ls_window, rows_ctas_per_sm, ls_blocks_per_sm, then
+ *    fused_tail) are timed over `iters` outer iterations (>= 1) each,
  *    every trial starting from the handle's current iterate, which is restored
  *    afterwards: the call leaves the estimate unchanged.  Start from a
  *    representative iterate (for example after a few hpc_iterate calls) for

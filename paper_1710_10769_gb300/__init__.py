@@ -75,14 +75,15 @@ class Tuning(C.Structure):
     _fields_ = [("gram_band", C.c_int32), ("ls_window", C.c_int32), ("ls_blocks_per_sm", C.c_int32),
                 ("rows_ctas_per_sm", C.c_int32), ("gram_maxima", C.c_int32), ("screen_bounds", C.c_int32),
                 ("gram_schedule", C.c_int32), ("gram_chunk", C.c_int32),
-                ("gram_lead", C.c_int32)]
+                ("gram_lead", C.c_int32), ("fused_tail", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 TUNE_MAX_TRIALS = 48
-TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm", "gram_maxima", "gram_schedule")
+TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm", "gram_maxima", "gram_schedule",
+              "fused_tail")
 
 
 class TuneTrial(C.Structure):

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <thread>
 #include <cmath>
 #include <cstdio>
@@ -84,6 +85,7 @@ struct hpc_ctx {
     int* bk_cnt = nullptr; int* bk_off = nullptr; int* bk_cur = nullptr; int* bk_len = nullptr;
     long long* bk_uoff = nullptr;
     int* bk_long = nullptr;
+    unsigned* bar = nullptr;      // arrival counters of the cooperative tail kernels' grid barriers
     int2* bk_mir = nullptr;
     int* col_a = nullptr; void* w_a = nullptr; void* om_a = nullptr; unsigned char* fl_a = nullptr;
     int* col_b = nullptr; void* w_b = nullptr; void* om_b = nullptr; unsigned char* fl_b = nullptr;
@@ -148,7 +150,7 @@ struct hpc_ctx {
     const void* pf_ptr = nullptr;
     int pf_xdt = -1;
     // launch shapes (hpc_set_tuning / hpc_autotune); ls_window starts from the options
-    hpc_tuning tune{16, 8, 0, 2, 1, 1, 1, 0, 0};
+    hpc_tuning tune{16, 8, 0, 2, 1, 1, 1, 0, 0, 0};
     // device loop: one CUDA graph (outer iteration WHILE node, inner line-search
     // WHILE node) captured on a private stream; rebuilt when a buffer it captured
     // is reallocated (epoch), when the current CSR buffer changes, or with timing
@@ -158,6 +160,7 @@ struct hpc_ctx {
     int64_t epoch = 0;
     int64_t g_epoch = -1;
     int g_cur = -1, g_timing = -1;
+    int g_fused = 0;              // tail form of the device-loop graph (tuning fused_tail)
     // differentiation scratch (grown on demand)
     void* adj_buf = nullptr;
     size_t adj_bytes = 0;
@@ -268,7 +271,7 @@ int set_identity(hpc_ctx* h) {
 
 template <typename T>
 hpc::IterBufs<T> bufs(hpc_ctx* h) {
-    hpc::IterBufs<T> b;
+    hpc::IterBufs<T> b{};
     b.S = static_cast<const T*>(h->S);
     b.ld = h->ld;
     b.p = (int)h->p;
@@ -286,6 +289,7 @@ hpc::IterBufs<T> bufs(hpc_ctx* h) {
     b.bk.cap = (int)std::min<int64_t>(2 * h->cap, 0x7fffffff);
     b.cnt2 = h->cnt2;
     b.scan_part = h->scan_part;
+    b.bar = h->bar;
     b.part_obj = h->part_obj;
     b.part_ls = h->part_ls;
     b.nblk = h->nblk;
@@ -365,6 +369,8 @@ int obs_screen(hpc_ctx* h, const hpc::IterBufs<float>& b, cudaStream_t s) {
     return HPC_OK;
 }
 
+int tail_mode(const hpc_ctx* h);
+
 // One outer iteration.  *done is set when the stopping rule holds.
 template <typename T>
 int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
@@ -380,11 +386,27 @@ int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
             hpc::launch_grad_screen<T>(b, h->stream);
         }
         if (h->opt.timing) CUDA_TRY(cudaEventRecord(h->ev_scr1, h->stream));
-        hpc::launch_candidates<T>(b, h->stream);
-        CUDA_TRY(cudaGetLastError());
-        int launches = hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesCandidates;
+        const bool fused = tail_mode(h) == 1;
+        int launches = hpc::kLaunchesBegin + hpc::kLaunchesScreen;
         bool accepted = false, overflow = false;
-        for (int hb = 0; hb <= h->opt.max_halvings; hb += h->tune.ls_window) {
+        if (fused) {
+            // candidates, gradient, every window and the accept in one launch
+            const cudaError_t e = hpc::launch_tail<T>(b, h->variant == HPC_OBS, h->stream);
+            if (e != cudaSuccess) {
+                set_cuda_error(e, "fused iteration tail", __LINE__);
+                return HPC_ERR_CUDA;
+            }
+            launches += hpc::kLaunchesTail;
+            STATUS_TRY(read_ctrl(h));
+            const hpc::Ctrl& c = *h->h_ctrl;
+            if (c.flags & (hpc::kFlagEmOverflow | hpc::kFlagBucketOverflow)) overflow = true;
+            else if (c.ls_accept >= 0 && (c.flags & ~hpc::kFlagNnzOverflow) == 0) accepted = true;
+        } else {
+            hpc::launch_candidates<T>(b, h->stream);
+            CUDA_TRY(cudaGetLastError());
+            launches += hpc::kLaunchesCandidates;
+        }
+        for (int hb = 0; !fused && hb <= h->opt.max_halvings; hb += h->tune.ls_window) {
             if constexpr (std::is_same<T, float>::value) {
                 if (h->variant == HPC_OBS) hpc::launch_ls_window_obs(b, host_loop, h->stream);
                 else hpc::launch_ls_window<T>(b, host_loop, h->stream);
@@ -421,10 +443,12 @@ int one_iteration(hpc_ctx* h, hpc_stats* st, bool use_stop, bool* done) {
             const int s = flags_to_status(c.flags);
             return s != HPC_OK ? s : HPC_ERR_LS_FAIL;
         }
-        hpc::launch_accept<T>(b, h->stream);
-        CUDA_TRY(cudaGetLastError());
-        if (st) st->kernel_launches += hpc::kLaunchesAccept;
-        STATUS_TRY(read_ctrl(h));
+        if (!fused) {
+            hpc::launch_accept<T>(b, h->stream);
+            CUDA_TRY(cudaGetLastError());
+            if (st) st->kernel_launches += hpc::kLaunchesAccept;
+            STATUS_TRY(read_ctrl(h));
+        }
         const hpc::Ctrl& c2 = *h->h_ctrl;
         if (c2.flags & hpc::kFlagNnzOverflow) {
             STATUS_TRY(grow_csr(h, std::max<int64_t>(2 * h->csr_cap, (int64_t)c2.nnz_next + 1)));
@@ -512,6 +536,58 @@ int add_while(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHan
     return HPC_OK;
 }
 
+// Whether a cooperative kernel runs inside a conditional WHILE node's body on the
+// current device: checked once per device, before any capture, by a graph whose
+// loop body is one cooperative launch of a one-block kernel that ends the loop.
+bool tail_in_graph_supported() {
+    static std::mutex mu;
+    static int state[64] = {};     // 0 unknown, 1 supported, 2 not
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (state[dev]) return state[dev] == 1;
+    bool ok = false;
+    int* d = nullptr;
+    cudaStream_t s = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int coop = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaMalloc(&d, sizeof(int)) == cudaSuccess &&
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaMemsetAsync(d, 0, sizeof(int), s) == cudaSuccess && cudaGraphCreate(&g, 0) == cudaSuccess) {
+        cudaGraphConditionalHandle hnd;
+        cudaGraphNode_t node;
+        cudaGraph_t body;
+        if (cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
+            add_while(g, nullptr, hnd, &node, &body) == HPC_OK &&
+            cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+            const cudaError_t le = hpc::launch_tail_probe(d, hnd, s);
+            cudaGraph_t out = body;
+            const cudaError_t ce = cudaStreamEndCapture(s, &out);
+            int ran = 0;
+            if (le == cudaSuccess && ce == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess &&
+                cudaGraphLaunch(ge, s) == cudaSuccess &&
+                cudaMemcpyAsync(&ran, d, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                cudaStreamSynchronize(s) == cudaSuccess)
+                ok = ran == 1;
+        }
+    }
+    (void)cudaGetLastError();   // a refused capture leaves its error here
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (s) cudaStreamDestroy(s);
+    if (d) cudaFree(d);
+    state[dev] = ok ? 1 : 2;
+    return ok;
+}
+
+// Form of the iteration tail: the tuning's fused_tail (0 the chain of kernels, 1
+// the one cooperative kernel) where the device runs cooperative kernels in graph
+// loops, else the chain (the host-driven loop needs only the cooperative launch
+// itself, which the same check covers).
+int tail_mode(const hpc_ctx* h) { return h->tune.fused_tail != 0 && tail_in_graph_supported() ? h->tune.fused_tail : 0; }
+
 template <typename T>
 int capture_screen(hpc_ctx* h, const hpc::IterBufs<T>& b, cudaStream_t cs) {
     if constexpr (std::is_same<T, float>::value) {
@@ -546,16 +622,38 @@ void capture_window(hpc_ctx* h, const hpc::IterBufs<T>& b, const hpc::LoopCond& 
 //   }
 // k_iter_begin arms the line-search loop, the last block of k_ls_eval ends it, and the commit
 // kernel continues or ends the iteration loop.
+//
+// With the fused tail (mode 1) the body is
+//       begin, [stamp], screening pass, [stamp], k_iter_tail, commit
+// with no inner loop: the tail runs the windows itself.
 template <typename T>
 int capture_iteration_loop(hpc_ctx* h, cudaGraph_t g, const cudaGraphNode_t* dep, hpc::LoopCond& lc,
-                           cudaGraphNode_t* node) {
+                           cudaGraphNode_t* node, int mode) {
     cudaStream_t cs = h->cap_stream;
     const hpc::IterBufs<T> b = bufs<T>(h);
+    const bool fused = mode == 1;
     const bool timing = h->opt.timing != 0;
     lc.use = 1;
     cudaGraphNode_t inner, leaf;
     cudaGraph_t body, ls_body;
     STATUS_TRY(add_while(g, dep, lc.iter, node, &body));
+    if (fused) {
+        CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        int st = HPC_OK;
+        hpc::launch_iter_begin<T>(b, hpc::LoopCond{}, cs);
+        if (timing) hpc::launch_stamp(h->d_ctrl, 0, cs);
+        st = capture_screen<T>(h, b, cs);
+        if (st == HPC_OK) {
+            if (timing) hpc::launch_stamp(h->d_ctrl, 1, cs);
+            const cudaError_t e = hpc::launch_tail<T>(b, h->variant == HPC_OBS, cs);
+            if (e != cudaSuccess) {
+                set_cuda_error(e, "fused iteration tail", __LINE__);
+                st = HPC_ERR_CUDA;
+            }
+        }
+        if (st == HPC_OK) hpc::launch_commit<T>(b, lc, cs);
+        return end_capture(cs, body, st);
+    }
     // the line-search handle lives in the body that holds its node
     CUDA_TRY(cudaGraphConditionalHandleCreate(&lc.ls, body, 1, cudaGraphCondAssignDefault));
     {
@@ -600,8 +698,10 @@ int build_graph(hpc_ctx* h) {
     hpc::LoopCond lc;
     CUDA_TRY(cudaGraphConditionalHandleCreate(&lc.iter, h->graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNode_t loop;
-    STATUS_TRY(capture_iteration_loop<T>(h, h->graph, nullptr, lc, &loop));
+    const int mode = tail_mode(h);
+    STATUS_TRY(capture_iteration_loop<T>(h, h->graph, nullptr, lc, &loop, mode));
     CUDA_TRY(cudaGraphInstantiate(&h->gexec, h->graph, 0));
+    h->g_fused = mode;
     h->g_epoch = h->epoch;
     h->g_cur = h->cur;
     h->g_timing = h->opt.timing ? 1 : 0;
@@ -613,6 +713,7 @@ template <typename T>
 int build_path_graph(hpc_ctx* h, const hpc::PathOut& out, cudaGraph_t* graph, cudaGraphExec_t* exec) {
     STATUS_TRY(ensure_cap_stream(h));
     cudaStream_t cs = h->cap_stream;
+    const int mode = tail_mode(h);
     CUDA_TRY(cudaGraphCreate(graph, 0));
     cudaGraphConditionalHandle path_cond;
     CUDA_TRY(cudaGraphConditionalHandleCreate(&path_cond, *graph, 1, cudaGraphCondAssignDefault));
@@ -627,7 +728,7 @@ int build_path_graph(hpc_ctx* h, const hpc::PathOut& out, cudaGraph_t* graph, cu
         const int st = capture_leaf(cs, &begin_leaf);
         STATUS_TRY(end_capture(cs, body, st));
     }
-    STATUS_TRY(capture_iteration_loop<T>(h, body, &begin_leaf, lc, &loop));
+    STATUS_TRY(capture_iteration_loop<T>(h, body, &begin_leaf, lc, &loop, mode));
     {
         const hpc::IterBufs<T> b = bufs<T>(h);
         CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, &loop, nullptr, 1, cudaStreamCaptureModeRelaxed));
@@ -640,9 +741,15 @@ int build_path_graph(hpc_ctx* h, const hpc::PathOut& out, cudaGraph_t* graph, cu
 
 // Launches of one outer iteration of the device loop besides its line-search
 // windows (two each).
-int loop_launches(const hpc_ctx* h) {
+int loop_launches(const hpc_ctx* h, int mode) {
+    if (mode == 1) return hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesTail + 1 + (h->opt.timing ? 2 : 0);
     return hpc::kLaunchesBegin + hpc::kLaunchesScreen + hpc::kLaunchesCandidates + hpc::kLaunchesAccept + 1 +
            (h->opt.timing ? 2 : 0);
+}
+
+// Window launches of the device loop (none with the fused tail: it runs them).
+int64_t window_launches(int mode, long long windows) {
+    return mode == 1 ? 0 : (int64_t)hpc::kLaunchesLsWindow * windows;
 }
 
 // The device loop: one graph launch runs iterations until the stopping rule, the
@@ -701,7 +808,7 @@ int run_device_loop(hpc_ctx* h, int64_t k, bool use_stop, hpc_stats* s, bool fre
     s->rel_change = c.rel;
     s->candidates = c.em_count;
     s->grad_pass_launches = c.iter_attempts;
-    s->kernel_launches = c.iter_attempts * loop_launches(h) + hpc::kLaunchesLsWindow * c.ls_windows;
+    s->kernel_launches = c.iter_attempts * loop_launches(h, h->g_fused) + window_launches(h->g_fused, c.ls_windows);
     s->ms_gram = h->ms_gram;
     s->ms_gram_kernel = h->ms_gram_kernel;
     s->capacity_regrows = h->regrows - regrows0;
@@ -739,8 +846,10 @@ int solve_batch_device(const std::vector<hpc_ctx*>& hs, std::vector<int>& status
             break;
         }
         cudaGraphNode_t node;
-        r = h->vdt == HPC_F64 ? capture_iteration_loop<double>(h, g, nullptr, lc, &node)
-                              : capture_iteration_loop<float>(h, g, nullptr, lc, &node);
+        // the problems' loops run concurrently: the chain of separate kernels, whose
+        // blocks never wait on one another
+        r = h->vdt == HPC_F64 ? capture_iteration_loop<double>(h, g, nullptr, lc, &node, 0)
+                              : capture_iteration_loop<float>(h, g, nullptr, lc, &node, 0);
     }
     if (r == HPC_OK && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) r = HPC_ERR_CUDA;
     // order the launch after every handle's pending work (its control-block upload)
@@ -801,7 +910,7 @@ int solve_batch_device(const std::vector<hpc_ctx*>& hs, std::vector<int>& status
         s.ms_total = batch_ms;
         s.ms_grad_pass = h->opt.timing ? (double)c.screen_ns * 1e-6 : 0.0;
         s.grad_pass_launches = c.iter_attempts;
-        s.kernel_launches = c.iter_attempts * loop_launches(h) + hpc::kLaunchesLsWindow * c.ls_windows;
+        s.kernel_launches = c.iter_attempts * loop_launches(h, 0) + window_launches(0, c.ls_windows);
         s.ms_gram = h->ms_gram;
         s.ms_gram_kernel = h->ms_gram_kernel;
         s.capacity_regrows = h->regrows - regrows0[t];
@@ -1028,7 +1137,7 @@ void destroy(hpc_ctx* h) {
                     h->bk_cur, h->bk_len, h->cnt2, h->scan_part, h->part_obj, h->part_ls, h->d_ctrl, h->gram_scratch,
                     h->rinfo, h->rdv, h->adj_buf, h->offlist, h->xt, h->yt, h->xp[0], h->xp[1],
                     h->yp[0], h->yp[1], h->pairs, h->bk_uoff, h->pmask, h->seqoff, h->bk_long,
-                    h->m1, h->m1g, h->colmax, h->pairs_list, h->row_items, h->x_stage};
+                    h->m1, h->m1g, h->colmax, h->pairs_list, h->row_items, h->x_stage, h->bar};
     for (void* q : ptrs) release(h, q);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     for (auto& e : h->ev) if (e) cudaEventDestroy(e);
@@ -1231,6 +1340,8 @@ int hpc_create(hpc_handle* out, const void* X, hpc_dtype xdt, int64_t n, int64_t
     CK(hold(h, &h->part_ls, (size_t)h->nblk * 16 * 4 * sizeof(double)));
     CK(hold(h, &h->d_ctrl, sizeof(hpc::Ctrl)));
     CK(cudaMemsetAsync(h->d_ctrl, 0, sizeof(hpc::Ctrl), h->stream));
+    CK(hold(h, &h->bar, hpc::kBarWords * sizeof(unsigned)));
+    CK(cudaMemsetAsync(h->bar, 0, hpc::kBarWords * sizeof(unsigned), h->stream));
     CK(cudaMallocHost(&h->h_ctrl, sizeof(hpc::Ctrl)));
     std::memset(h->h_ctrl, 0, sizeof(hpc::Ctrl));
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
@@ -1954,7 +2065,7 @@ bool tuning_ok(const hpc_tuning& t) {
            t.ls_blocks_per_sm >= 0 && t.ls_blocks_per_sm <= 8 && t.rows_ctas_per_sm >= 1 && t.rows_ctas_per_sm <= 4 &&
            (t.gram_maxima == 0 || t.gram_maxima == 1) && (t.screen_bounds == 0 || t.screen_bounds == 1) &&
            (t.gram_schedule == 0 || t.gram_schedule == 1) && t.gram_chunk >= 0 &&
-           t.gram_lead >= 0;
+           t.gram_lead >= 0 && (t.fused_tail == 0 || t.fused_tail == 1);
 }
 
 void apply_tuning(hpc_ctx* h, const hpc_tuning& t) {
@@ -2096,15 +2207,21 @@ int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, h
         IterateCopy c;
         status = save_iterate(h, c);
         struct Knob { int id; std::vector<int> vals; };
-        const Knob knobs[] = {{1, {2, 4, 8, 16}}, {3, {1, 2, 3, 4}}, {2, {1, 2, 3}}};
+        // the tail's form last: it runs the windows with the shapes chosen before it
+        const bool coop = tail_in_graph_supported();
+        const Knob knobs[] = {{1, {2, 4, 8, 16}}, {3, {1, 2, 3, 4}}, {2, {1, 2, 3}}, {6, {0, 1}}};
         for (const Knob& k : knobs) {
             if (status != HPC_OK) break;
             if (k.id == 3 && h->variant == HPC_OBS) continue;       // Obs has no row kernel
+            if (k.id == 6 && !coop) continue;
             double best_ms = 1e300;
             int best_v = 0;
             for (int v : k.vals) {
                 hpc_tuning u = t;
-                if (k.id == 1) u.ls_window = v; else if (k.id == 2) u.ls_blocks_per_sm = v; else u.rows_ctas_per_sm = v;
+                if (k.id == 1) u.ls_window = v;
+                else if (k.id == 2) u.ls_blocks_per_sm = v;
+                else if (k.id == 3) u.rows_ctas_per_sm = v;
+                else u.fused_tail = v;
                 double ms = 0;
                 status = time_iterations<T>(h, c, u, iters, &ms);
                 if (status != HPC_OK) break;
@@ -2112,7 +2229,10 @@ int autotune_t(hpc_ctx* h, const void* X, int xdt, int on_host, int64_t iters, h
                 if (ms < best_ms) { best_ms = ms; best_v = v; }
             }
             if (status != HPC_OK) break;
-            if (k.id == 1) t.ls_window = best_v; else if (k.id == 2) t.ls_blocks_per_sm = best_v; else t.rows_ctas_per_sm = best_v;
+            if (k.id == 1) t.ls_window = best_v;
+            else if (k.id == 2) t.ls_blocks_per_sm = best_v;
+            else if (k.id == 3) t.rows_ctas_per_sm = best_v;
+            else t.fused_tail = best_v;
         }
         if (status == HPC_OK) status = restore_iterate(h, c);
         if (status == HPC_OK) status = cudaStreamSynchronize(h->stream) == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;

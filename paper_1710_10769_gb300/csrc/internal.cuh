@@ -52,6 +52,7 @@ struct Ctrl {
     int ls_done;                  // blocks of the running line-search launch that wrote their partials
     int n_long, pad4_;            // rows of the candidate structure with more than kShortRow entries
     int n_pairs, n_row_items;     // items the bound screening keeps (pure rows; rows with neighbours)
+    int pad5_, pad6_;
 };
 
 // Rows with at most this many candidate entries (before de-dup) are handled one
@@ -158,6 +159,7 @@ struct IterBufs {
     const float* xt;
     int64_t ldx;
     int64_t n;
+    unsigned* bar;            // kBarWords: arrival counter of the fused tail's grid barriers
 };
 
 // Device-side loop control (CUDA graph conditional nodes); use = 0 outside a graph.
@@ -199,6 +201,20 @@ constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 7;
 constexpr int kLaunchesLsWindow = 1;     // k_ls_eval (its last block decides)
 constexpr int kLaunchesAccept = 4;
+constexpr int kLaunchesTail = 1;
+// Words of the fused tail's barrier buffer: the arrival counter on a 128-byte line
+// of its own (k_iter_begin zeroes it).
+constexpr int kBarWords = 32;         // k_iter_tail: candidates, gradient, every window, accept
+
+// The fused iteration tail (candidates, gradient, line-search windows with their
+// decisions, compaction and stopping rule) as one cooperative launch.  obs selects
+// the Obs form of the window evaluation.  Returns the launch's error code.
+template <typename T> cudaError_t launch_tail(const IterBufs<T>& b, bool obs, cudaStream_t s);
+// Blocks of that launch for these buffers (resident blocks per SM x SMs, at most nblk).
+template <typename T> int tail_grid(const IterBufs<T>& b, bool obs);
+
+// One cooperative launch of a one-block kernel that adds 1 to *out and sets cond to 0.
+cudaError_t launch_tail_probe(int* out, cudaGraphConditionalHandle cond, cudaStream_t s);
 
 template <typename T> void launch_row_info(int p, Csr<T> om, int4* rinfo, T* rdv, cudaStream_t s);
 // max |S_ij| per (row, column block of width screen_box_cols), off the diagonal

@@ -24,6 +24,7 @@
 //  4. accept          compaction of the accepted Omega+ into CSR (ballot/popc row
 //                     counts, scan, ordered write) and the stopping rule.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <vector>
 
@@ -132,12 +133,14 @@ __device__ __forceinline__ T prox_entry(T om, T g, T tau, T tl1, bool diag) {
 
 // ------------------------------------------------------------------ 0. reset
 template <typename T>
-__global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl, int use_cond, cudaGraphConditionalHandle ls_cond) {
+__global__ void k_iter_begin(Buckets<T> bk, int p, Ctrl* ctrl, int use_cond, cudaGraphConditionalHandle ls_cond,
+                             unsigned* bar) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     for (int i = tid; i < p; i += gridDim.x * blockDim.x) {
         bk.cnt[i] = 0;
         bk.cur[i] = 0;
     }
+    if (bar && tid == 0) *bar = 0u;   // arrival counter of the fused tail's grid barriers
     if (tid == 0) {
         ctrl->em_count = 0;
         ctrl->obs_next = 0;
@@ -1159,20 +1162,30 @@ k_grad_screen_rows(const T* __restrict__ S, int64_t ld, int p, const int4* __res
 }
 
 // ------------------------------------------------------------------ 2. candidates
+// Each step of the candidate, line-search and accept chain is a device function
+// over a grid of nb blocks of kThreads threads, this block being bid, so that the
+// same code runs as a kernel of its own (bid = blockIdx.x, nb = gridDim.x) or as a
+// phase of the fused iteration kernel k_iter_tail.  flags0 is the control block's
+// flag word as the step sees it at its start.
 template <typename T>
-__global__ void k_bucket_count(Emit<T> em, Buckets<T> bk, Ctrl* ctrl) {
+__device__ void bucket_count_body(const Emit<T>& em, const Buckets<T>& bk, Ctrl* ctrl, int bid, int nb) {
     const int total = ctrl->em_count;
     if (total > em.cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctrl->flags, kFlagEmOverflow);
+        if (bid == 0 && threadIdx.x == 0) atomicOr(&ctrl->flags, kFlagEmOverflow);
         return;
     }
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    for (int e = bid * kThreads + threadIdx.x; e < total; e += nb * kThreads) {
         const int i = em.row[e];
         const int cj = em.col[e];
         atomicAdd(&bk.cnt[i], 1);
         // off the support and not emitted from both sides: partner request in row j
         if (cj >= 0 && !(cj & 0x40000000)) atomicAdd(&bk.cnt[cj], 1);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bucket_count(Emit<T> em, Buckets<T> bk, Ctrl* ctrl) {
+    bucket_count_body(em, bk, ctrl, blockIdx.x, gridDim.x);
 }
 
 // Line-search work units of a row with c candidate entries before de-dup: the
@@ -1203,8 +1216,10 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPerThread = 16;
 constexpr int kScanTile = kScanThreads * kScanPerThread;
 
-// The 16 inputs of thread t (zero past n); in + base is 16-byte aligned.
-__device__ __forceinline__ void scan_load16(const int* __restrict__ in, int n, int base, int (&v)[kScanPerThread]) {
+// The 16 inputs of thread t (zero past n); in + base is 16-byte aligned.  The
+// input is read through the coherent path: inside the fused iteration kernel it was
+// written by the same launch.
+__device__ __forceinline__ void scan_load16(const int* in, int n, int base, int (&v)[kScanPerThread]) {
 #pragma unroll
     for (int q = 0; q < kScanPerThread; q += 4) {
         const int j = base + q;
@@ -1217,6 +1232,14 @@ __device__ __forceinline__ void scan_load16(const int* __restrict__ in, int n, i
         }
     }
 }
+
+// Shared memory of one scan tile.
+struct ScanSmem {
+    int ws[kScanThreads / 32], wl[kScanThreads / 32];
+    long long wu[kScanThreads / 32];
+    int ps, pl;
+    long long pu;
+};
 
 // Block-wide sums (with_long: also the long-row count and units) of the thread values.
 template <bool INCL>
@@ -1236,14 +1259,12 @@ __device__ __forceinline__ void scan_block3(int& s, int& l, long long& u, bool w
     if (!INCL) { s -= s0; l -= l0; u -= u0; }
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const int* __restrict__ in, int n, const Ctrl* __restrict__ ctrl, bool with_long,
-              ScanPart* __restrict__ part) {
-    __shared__ int ws[kScanThreads / 32], wl[kScanThreads / 32];
-    __shared__ long long wu[kScanThreads / 32];
-    if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) return;
+// Tile t of the first scan kernel: the tile's sums into part[t].
+__device__ void scan_reduce_tile(const int* in, int n, int flags0, bool with_long, ScanPart* part, int t,
+                                 ScanSmem& sm) {
+    if (flags0 & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) return;
     int v[kScanPerThread];
-    scan_load16(in, n, blockIdx.x * kScanTile + threadIdx.x * kScanPerThread, v);
+    scan_load16(in, n, t * kScanTile + threadIdx.x * kScanPerThread, v);
     int s = 0, l = 0;
     long long u = 0;
 #pragma unroll
@@ -1251,39 +1272,43 @@ k_scan_reduce(const int* __restrict__ in, int n, const Ctrl* __restrict__ ctrl, 
         s += v[q];
         if (with_long && v[q] > kShortRow) { ++l; u += ls_units(v[q]); }
     }
-    scan_block3<true>(s, l, u, with_long, ws, wl, wu);
-    if (threadIdx.x == kScanThreads - 1) part[blockIdx.x] = ScanPart{s, l, u};
+    scan_block3<true>(s, l, u, with_long, sm.ws, sm.wl, sm.wu);
+    if (threadIdx.x == kScanThreads - 1) part[t] = ScanPart{s, l, u};
+    __syncthreads();   // sm is reused by the next tile of this block
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag,
-             int* total_dst, long long* __restrict__ uoff, int* __restrict__ longlist,
-             const ScanPart* __restrict__ part, int conv_cap, double eps) {
-    __shared__ int ws[kScanThreads / 32], wl[kScanThreads / 32];
-    __shared__ long long wu[kScanThreads / 32];
-    __shared__ int s_ps, s_pl;
-    __shared__ long long s_pu;
-    if (ctrl->flags & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+k_scan_reduce(const int* in, int n, const Ctrl* __restrict__ ctrl, bool with_long, ScanPart* __restrict__ part) {
+    __shared__ ScanSmem sm;
+    scan_reduce_tile(in, n, ctrl->flags, with_long, part, blockIdx.x, sm);
+}
+
+// Tile t of ntiles of the second scan kernel: the tile's exclusive prefixes, and in
+// the last tile the totals (and the stopping rule, for the compaction's scan).
+__device__ void scan_apply_tile(const int* in, int* out, int n, int cap, Ctrl* ctrl, int flags0, int flag,
+                                int* total_dst, long long* uoff, int* longlist, const ScanPart* part, int conv_cap,
+                                double eps, int t, int ntiles, ScanSmem& sm) {
+    if (flags0 & ~kFlagLsFail & (kFlagEmOverflow | kFlagBucketOverflow)) {
+        if (t == 0 && threadIdx.x == 0) {
             out[n] = 0;
             if (uoff) { uoff[0] = 0; ctrl->n_long = 0; }
         }
         return;
     }
     const bool with_long = uoff != nullptr;
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanPerThread;
+    const int base = t * kScanTile + threadIdx.x * kScanPerThread;
     int v[kScanPerThread];
     scan_load16(in, n, base, v);
     // the sums of the tiles before this one
     {
         int ps = 0, pl = 0;
         long long pu = 0;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kScanThreads) {
+        for (int b = threadIdx.x; b < t; b += kScanThreads) {
             const ScanPart q = part[b];
             ps += q.s; pl += q.l; pu += q.u;
         }
-        scan_block3<true>(ps, pl, pu, with_long, ws, wl, wu);
-        if (threadIdx.x == kScanThreads - 1) { s_ps = ps; s_pl = pl; s_pu = pu; }
+        scan_block3<true>(ps, pl, pu, with_long, sm.ws, sm.wl, sm.wu);
+        if (threadIdx.x == kScanThreads - 1) { sm.ps = ps; sm.pl = pl; sm.pu = pu; }
         __syncthreads();
     }
     int s = 0, l = 0;
@@ -1293,9 +1318,10 @@ k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, 
         s += v[q];
         if (with_long && v[q] > kShortRow) { ++l; u += ls_units(v[q]); }
     }
-    scan_block3<false>(s, l, u, with_long, ws, wl, wu);
-    int run = s + s_ps, lrun = l + s_pl;
-    long long urun = u + s_pu;
+    scan_block3<false>(s, l, u, with_long, sm.ws, sm.wl, sm.wu);
+    int run = s + sm.ps, lrun = l + sm.pl;
+    long long urun = u + sm.pu;
+    __syncthreads();   // sm is reused by the next tile of this block
     int o[kScanPerThread];
 #pragma unroll
     for (int q = 0; q < kScanPerThread; ++q) {
@@ -1317,7 +1343,7 @@ k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, 
             for (int r = 0; r < 4 && j + r < n; ++r) out[j + r] = o[q + r];
         }
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
+    if (t == ntiles - 1 && threadIdx.x == kScanThreads - 1) {
         // the inputs past n are zero, so this thread's running values are the totals
         const int total = run;
         out[n] = total;
@@ -1344,6 +1370,15 @@ k_scan_apply(const int* __restrict__ in, int* __restrict__ out, int n, int cap, 
     }
 }
 
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const int* in, int* __restrict__ out, int n, int cap, Ctrl* ctrl, int flag, int* total_dst,
+             long long* __restrict__ uoff, int* __restrict__ longlist, const ScanPart* __restrict__ part,
+             int conv_cap, double eps) {
+    __shared__ ScanSmem sm;
+    scan_apply_tile(in, out, n, cap, ctrl, ctrl->flags, flag, total_dst, uoff, longlist, part, conv_cap, eps,
+                    blockIdx.x, gridDim.x, sm);
+}
+
 void launch_scan(const int* in, int* out, int n, int cap, Ctrl* ctrl, int flag, int* total_dst, long long* uoff,
                  int* longlist, ScanPart* part, cudaStream_t s, int conv_cap = -1, double eps = 0.0) {
     const int tiles = (int)std::max<int64_t>(1, ((int64_t)n + kScanTile - 1) / kScanTile);
@@ -1353,10 +1388,11 @@ void launch_scan(const int* in, int* out, int n, int cap, Ctrl* ctrl, int flag, 
 }
 
 template <typename T>
-__global__ void k_bucket_scatter(Emit<T> em, Buckets<T> bk, const Ctrl* ctrl) {
-    if (ctrl->flags) return;
+__device__ void bucket_scatter_body(const Emit<T>& em, const Buckets<T>& bk, const Ctrl* ctrl, int flags0, int bid,
+                                    int nb) {
+    if (flags0) return;
     const int total = ctrl->em_count;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    for (int e = bid * kThreads + threadIdx.x; e < total; e += nb * kThreads) {
         const int i = em.row[e];
         const int cj = em.col[e];
         const int j = cj & 0x3fffffff;
@@ -1373,6 +1409,11 @@ __global__ void k_bucket_scatter(Emit<T> em, Buckets<T> bk, const Ctrl* ctrl) {
             bk.fl_a[q] = kEntMirror;
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bucket_scatter(Emit<T> em, Buckets<T> bk, const Ctrl* ctrl) {
+    bucket_scatter_body(em, bk, ctrl, ctrl->flags, blockIdx.x, gridDim.x);
 }
 
 // Sort key of a scattered entry: column, own entry before the partner request.
@@ -1410,16 +1451,22 @@ constexpr int kSortShort = 32;
 // rows of at most 32 entries one warp each, in registers; longer rows (hub
 // rows with thousands of candidates) one block each, so none serialises a warp.
 // The last two tiers take their rows from the long-row list of the bucket scan.
+struct SortSmem {
+    unsigned long long key[kSortSmem];
+    int cnt[kWarps];
+    int out;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
-    __shared__ unsigned long long s_key[kSortSmem];
-    __shared__ int s_cnt[kWarps];
-    __shared__ int s_out;
-    if (ctrl->flags) return;
+__device__ void bucket_sort_body(const Buckets<T>& bk, int p, Ctrl* ctrl, int flags0, int bid, int nb,
+                                 SortSmem& sm) {
+    unsigned long long* s_key = sm.key;
+    int* s_cnt = sm.cnt;
+    int& s_out = sm.out;
+    if (flags0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (bid * kThreads + threadIdx.x) >> 5;
+    const int nw = (nb * kThreads) >> 5;
     const int nlong = ctrl->n_long;
 
     // 1. short rows, one lane each
@@ -1504,7 +1551,7 @@ k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
     }
 
     // 3. rows over 32 entries, one block each
-    for (int li = blockIdx.x; li < nlong; li += gridDim.x) {
+    for (int li = bid; li < nlong; li += nb) {
         const int i = bk.longlist[li];
         const int c = bk.cnt[i];
         if (c <= kSortShort) continue;
@@ -1636,18 +1683,25 @@ k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
         }
         if (threadIdx.x == 0) bk.len[i] = s_out;
     }
+    __syncthreads();   // sm is reused by what follows in a fused launch
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bucket_sort(Buckets<T> bk, int p, Ctrl* ctrl) {
+    __shared__ SortSmem sm;
+    bucket_sort_body(bk, p, ctrl, ctrl->flags, blockIdx.x, gridDim.x, sm);
 }
 
 // W_ij for partner entries, one thread per entry of the fill list, by gathers in
 // the CSR order of row i: diagonal term first, then the off-diagonals ascending
 // (bitwise equal to the value the screening pass computes for that entry).
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_fill_w(const T* __restrict__ S, int64_t ld, Csr<T> om, const int4* __restrict__ rinfo, const T* __restrict__ rdv,
-         Buckets<T> bk, const Ctrl* ctrl) {
-    if (ctrl->flags) return;
+__device__ void fill_w_body(const T* __restrict__ S, int64_t ld, const Csr<T>& om, const int4* __restrict__ rinfo,
+                            const T* __restrict__ rdv, const Buckets<T>& bk, const Ctrl* ctrl, int flags0, int bid,
+                            int nb) {
+    if (flags0) return;
     const int nm = ctrl->n_mirror;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nm; k += gridDim.x * blockDim.x) {
+    for (int k = bid * kThreads + threadIdx.x; k < nm; k += nb * kThreads) {
         const int2 m = bk.mir[k];
         const int i = m.y;
         const int j = bk.col_b[m.x];
@@ -1657,6 +1711,13 @@ k_fill_w(const T* __restrict__ S, int64_t ld, Csr<T> om, const int4* __restrict_
             if (q != ri.z) acc = fmaT(om.cv[q], S[(int64_t)om.ci[q] * ld + j], acc);
         bk.w_b[m.x] = acc;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_fill_w(const T* __restrict__ S, int64_t ld, Csr<T> om, const int4* __restrict__ rinfo, const T* __restrict__ rdv,
+         Buckets<T> bk, const Ctrl* ctrl) {
+    fill_w_body(S, ld, om, rinfo, rdv, bk, ctrl, ctrl->flags, blockIdx.x, gridDim.x);
 }
 
 // G_ij of one entry (position q of row i) and its share of the objective partials.
@@ -1695,14 +1756,13 @@ __device__ __forceinline__ void gradient_entry(const Buckets<T>& bk, int i, int 
 // G on the candidates (Alg. 2 steps 5-6) and the objective partials of Omega^k:
 // short rows one lane each, long rows (from the bucket scan's list) one warp each.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
+__device__ void gradient_body(int p, const Buckets<T>& bk, int stride, double* part_obj, Ctrl* ctrl, int flags0,
+                              int bid, int nb, double (&red)[kWarps][4]) {
     using A = typename AccOf<T>::type;
-    __shared__ double red[kWarps][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const bool skip = ctrl->flags != 0;
+    const int gw = (bid * kThreads + threadIdx.x) >> 5;
+    const int nw = (nb * kThreads) >> 5;
+    const bool skip = flags0 != 0;
     const T lam1 = (T)ctrl->lam1, lam2 = (T)ctrl->lam2;
     const int nlong = skip ? 0 : ctrl->n_long;
     A s_ow{}, s_o2{}, s_log{}, s_abs{};
@@ -1729,8 +1789,16 @@ k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
     if (threadIdx.x < 4) {
         double a = 0.0;
         for (int w = 0; w < kWarps; ++w) a += red[w][threadIdx.x];
-        part_obj[(size_t)threadIdx.x * stride + blockIdx.x] = a;
+        part_obj[(size_t)threadIdx.x * stride + bid] = a;
     }
+    __syncthreads();   // red is reused by what follows in a fused launch
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gradient(int p, Buckets<T> bk, int stride, double* part_obj, Ctrl* ctrl) {
+    __shared__ double red[kWarps][4];
+    gradient_body(p, bk, stride, part_obj, ctrl, ctrl->flags, blockIdx.x, gridDim.x, red);
 }
 
 // ------------------------------------------------------------------ 3. line search
@@ -1751,7 +1819,7 @@ __device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const Ls
 
 // Row i of the unit-offset prefix containing unit u (uoff[i] <= u < uoff[i+1]): a
 // 32-way search by the whole warp (each step narrows the range 32-fold).
-__device__ __forceinline__ int find_unit_row(const long long* __restrict__ uoff, int p, long long u, int lane) {
+__device__ __forceinline__ int find_unit_row(const long long* uoff, int p, long long u, int lane) {
     int lo = 0, hi = p;
     while (hi - lo > 1) {
         const int span = hi - lo;
@@ -1794,19 +1862,28 @@ __device__ __forceinline__ void acc_merge(double& a, double b) { a += b; }
 // number of resident warps on a persistent grid) where the gathers need it: three
 // CTAs per SM for windows of up to 4 step sizes, two for wider ones.
 template <typename T, int M>
-__global__ void __launch_bounds__(kThreads, (M <= 4) ? 3 : 2)
-k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride, double* part_ls,
-          Ctrl* ctrl, LsDecide dec) {
+struct LsSmem {
     using A = typename AccOf<T>::type;
-    __shared__ int s_col[kWarps][32];
-    __shared__ T s_del[kWarps][M][32];
-    __shared__ A s_acc[kWarps][M][2];
-    __shared__ int s_nb[kWarps][M];
-    __shared__ double red[kWarps][M][4];
+    int col[kWarps][32];
+    T del[kWarps][M][32];
+    A acc[kWarps][M][2];
+    int nb[kWarps][M];
+    double red[kWarps][M][4];
+};
+
+template <typename T, int M>
+__device__ void ls_eval_body(const T* __restrict__ S, int64_t ld, int p, const Buckets<T>& bk, int stride,
+                             double* part_ls, Ctrl* ctrl, int flags0, int bid, int nblocks, LsSmem<T, M>& sm) {
+    using A = typename AccOf<T>::type;
+    auto& s_col = sm.col;
+    auto& s_del = sm.del;
+    auto& s_acc = sm.acc;
+    auto& s_nb = sm.nb;
+    auto& red = sm.red;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const bool skip = (ctrl->flags != 0) || (ctrl->ls_accept >= 0);
+    const long long gw = (bid * (long long)kThreads + threadIdx.x) >> 5;
+    const long long nw = ((long long)nblocks * kThreads) >> 5;
+    const bool skip = (flags0 != 0) || (ctrl->ls_accept >= 0);
     const T lam1 = (T)ctrl->lam1;
     const int h_base = ctrl->ls_base;
     if (lane < M) {
@@ -1983,8 +2060,17 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride,
         const int m = threadIdx.x / 4, k = threadIdx.x % 4;
         double a = 0.0;
         for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
-        part_ls[(size_t)(m * 4 + k) * stride + blockIdx.x] = a;
+        part_ls[(size_t)(m * 4 + k) * stride + bid] = a;
     }
+    __syncthreads();   // sm is reused by what follows in a fused launch
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kThreads, (M <= 4) ? 3 : 2)
+k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride, double* part_ls,
+          Ctrl* ctrl, LsDecide dec) {
+    __shared__ LsSmem<T, M> sm;
+    ls_eval_body<T, M>(S, ld, p, bk, stride, part_ls, ctrl, ctrl->flags, blockIdx.x, gridDim.x, sm);
     ls_finish<M>(part_ls, (int)gridDim.x, dec, ctrl);
 }
 
@@ -1992,15 +2078,13 @@ k_ls_eval(const T* __restrict__ S, int64_t ld, int p, Buckets<T> bk, int stride,
 // row i is ||X D_i||^2 / n with X D_i = sum_e D_e X^T[j_e, :]; lanes hold 4
 // consecutive samples of each 128-sample chunk of n.  [1]-[3] as in k_ls_eval.
 template <int M>
-__global__ void __launch_bounds__(kThreads)
-k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, double tau0,
-              int stride, double* part_ls, Ctrl* ctrl,
-              LsDecide dec) {
-    __shared__ double red[kWarps][M][4];
+__device__ void ls_eval_obs_body(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p,
+                                 const Buckets<float>& bk, double tau0, int stride, double* part_ls, Ctrl* ctrl,
+                                 int flags0, int bid, int nblocks, double (&red)[kWarps][M][4]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const bool skip = (ctrl->flags != 0) || (ctrl->ls_accept >= 0);
+    const int gw = (bid * kThreads + threadIdx.x) >> 5;
+    const int nw = (nblocks * kThreads) >> 5;
+    const bool skip = (flags0 != 0) || (ctrl->ls_accept >= 0);
     const float lam1 = (float)ctrl->lam1;
     const int h_base = ctrl->ls_base;
     float tau[M], tl1[M];
@@ -2085,8 +2169,17 @@ k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Bucke
         const int m = threadIdx.x / 4, k = threadIdx.x % 4;
         double a = 0.0;
         for (int w = 0; w < kWarps; ++w) a += red[w][m][k];
-        part_ls[(size_t)(m * 4 + k) * stride + blockIdx.x] = a;
+        part_ls[(size_t)(m * 4 + k) * stride + bid] = a;
     }
+    __syncthreads();   // red is reused by what follows in a fused launch
+}
+
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+k_ls_eval_obs(const float* __restrict__ Xt, int64_t ldx, int64_t n, int p, Buckets<float> bk, double tau0,
+              int stride, double* part_ls, Ctrl* ctrl, LsDecide dec) {
+    __shared__ double red[kWarps][M][4];
+    ls_eval_obs_body<M>(Xt, ldx, n, p, bk, tau0, stride, part_ls, ctrl, ctrl->flags, blockIdx.x, gridDim.x, red);
     ls_finish<M>(part_ls, (int)gridDim.x, dec, ctrl);
 }
 
@@ -2124,24 +2217,19 @@ __device__ void decide_window(const double* sums, const double* obj, int M, int 
 // strided blocks, then a butterfly -- and takes the decision of Alg. 1 step 9; the
 // other blocks return.  The order does not depend on which block is last.
 template <int M>
-__device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const LsDecide& d, Ctrl* ctrl) {
-    __shared__ int s_last;
-    __shared__ double sums[M * 4];
-    __shared__ double obj[4];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->ls_done, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
-    if (ctrl->flags != 0 || ctrl->ls_accept >= 0) {
-        if (threadIdx.x == 0) {
-            ctrl->ls_done = 0;
-            if (d.use_cond) cudaGraphSetConditional(d.cond, 0);
-        }
-        return;
-    }
+struct FinSmem {
+    double sums[M * 4];
+    double obj[4];
+};
+
+// Whole block: the window's partials (and, in the first window, the objective
+// partials) reduced in the fixed order into sm; thread 0 then takes the decision
+// (decide_window).  Called with no flag raised and nothing accepted yet.
+template <int M>
+__device__ void ls_reduce_decide(const double* part_ls, int n_ls, const LsDecide& d, Ctrl* ctrl, FinSmem<M>& sm) {
+    double* sums = sm.sums;
+    double* obj = sm.obj;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = kWarps;
     const int h_base = ctrl->ls_base;
     const int first = h_base == 0;
     const double lam1 = ctrl->lam1, lam2 = ctrl->lam2;
@@ -2162,10 +2250,33 @@ __device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const Ls
         }
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        ctrl->ls_windows += 1;
+        decide_window(sums, obj, M, h_base, d.max_halvings, d.tau0, lam1, lam2, first, ctrl);
+    }
+    __syncthreads();
+}
+
+template <int M>
+__device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const LsDecide& d, Ctrl* ctrl) {
+    __shared__ int s_last;
+    __shared__ FinSmem<M> sm;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctrl->ls_done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (ctrl->flags != 0 || ctrl->ls_accept >= 0) {
+        if (threadIdx.x == 0) {
+            ctrl->ls_done = 0;
+            if (d.use_cond) cudaGraphSetConditional(d.cond, 0);
+        }
+        return;
+    }
+    ls_reduce_decide<M>(part_ls, n_ls, d, ctrl, sm);
     if (threadIdx.x != 0) return;
     ctrl->ls_done = 0;
-    ctrl->ls_windows += 1;
-    decide_window(sums, obj, M, h_base, d.max_halvings, d.tau0, lam1, lam2, first, ctrl);
     // another window while nothing is accepted and nothing went wrong
     if (d.use_cond) cudaGraphSetConditional(d.cond, (ctrl->flags == 0 && ctrl->ls_accept < 0) ? 1u : 0u);
 }
@@ -2175,12 +2286,12 @@ __device__ void ls_finish(const double* __restrict__ part_ls, int n_ls, const Ls
 // at the accepted tau leaves nonzero.  Short rows one lane each, long rows one
 // warp each.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_compact_count(int p, Buckets<T> bk, int* cnt2, const Ctrl* ctrl) {
+__device__ void compact_count_body(int p, const Buckets<T>& bk, int* cnt2, const Ctrl* ctrl, int flags0, int bid,
+                                   int nb) {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
+    const int gw = (bid * kThreads + threadIdx.x) >> 5;
+    const int nw = (nb * kThreads) >> 5;
+    if (flags0 != 0 || ctrl->ls_accept < 0) return;
     const T tau = (T)ctrl->tau;
     const T tl1 = tau * (T)ctrl->lam1;
     const int nlong = ctrl->n_long;
@@ -2216,12 +2327,17 @@ k_compact_count(int p, Buckets<T> bk, int* cnt2, const Ctrl* ctrl) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_compact_write(int p, Buckets<T> bk, Csr<T> nx, int cap, const Ctrl* ctrl) {
+__global__ void __launch_bounds__(kThreads) k_compact_count(int p, Buckets<T> bk, int* cnt2, const Ctrl* ctrl) {
+    compact_count_body(p, bk, cnt2, ctrl, ctrl->flags, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+__device__ void compact_write_body(int p, const Buckets<T>& bk, const Csr<T>& nx, int cap, const Ctrl* ctrl,
+                                   int flags0, int bid, int nb) {
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    if (ctrl->flags != 0 || ctrl->ls_accept < 0) return;
+    const int gw = (bid * kThreads + threadIdx.x) >> 5;
+    const int nw = (nb * kThreads) >> 5;
+    if (flags0 != 0 || ctrl->ls_accept < 0) return;
     const T tau = (T)ctrl->tau;
     const T tl1 = tau * (T)ctrl->lam1;
     const int nlong = ctrl->n_long;
@@ -2265,6 +2381,12 @@ k_compact_write(int p, Buckets<T> bk, Csr<T> nx, int cap, const Ctrl* ctrl) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_compact_write(int p, Buckets<T> bk, Csr<T> nx, int cap, const Ctrl* ctrl) {
+    compact_write_body(p, bk, nx, cap, ctrl, ctrl->flags, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
 __global__ void k_set_identity(Csr<T> c, int p) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= p; i += gridDim.x * blockDim.x) {
         c.rp[i] = i;
@@ -2289,12 +2411,216 @@ __global__ void k_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, con
     }
 }
 
+// ------------------------------------------------------------------ 5. the fused iteration tail
+// One cooperative launch runs steps 2-4 of an outer iteration: the candidate
+// structure (count, scan, scatter, sort, partner fill), the gradient G on it
+// (Alg. 2 steps 5-6), the line-search windows -- prox of eq. (2), the objective
+// partials and the sufficient-decrease decision of Alg. 1 step 9 -- until a step
+// is accepted, then the compaction of the accepted iterate into CSR and the
+// stopping rule.  Every phase is the device function the separate kernels of
+// the chain run, so each entry gets the same bits; grid-wide barriers stand where
+// the chain has kernel boundaries.  The cooperative launch keeps every block of
+// the grid resident, and every wait is bounded: a barrier that waits longer than
+// kBarrierWaitNs raises kFlagTimeout, after which every block skips the remaining
+// phases.
+
+__device__ __forceinline__ long long tail_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *static_cast<const volatile int*>(p); }
+
+constexpr long long kBarrierWaitNs = 4000000000ll;   // 4 s
+
+// Barrier bookkeeping of one block, and the control block's state after a barrier.
+struct TailSync {
+    unsigned* count;             // the launch's arrival counter
+    unsigned target;             // arrivals that complete this block's current barrier
+    int last;
+    int pre_flags, pre_accept;   // as the last block to arrive sees them
+    int flags, accept;           // after the release
+};
+struct TailState {
+    int flags;
+    int accept;
+};
+
+__device__ __forceinline__ void tail_sync_init(TailSync& ss, unsigned* bar) {
+    if (threadIdx.x != 0) return;
+    ss.count = bar;
+    ss.target = 0u;
+}
+
+// Grid-wide barrier over the launch's nb blocks on one arrival counter that only
+// grows within the launch (k_iter_begin zeroes it before each iteration): the
+// barrier is complete when the counter reaches the block's target, which grows
+// by nb per barrier.  With a hook, the last block to arrive runs at_last (the
+// whole block, with the state it read) and then adds one more arrival, which is
+// what the others wait for.  Ordering: the arrival is an acq_rel atomic after the
+// block's writes (CTA barrier first) and the waits are acquire loads, so every
+// block leaves with the writes of every block before the barrier (and of the
+// hook) visible.  A wait longer than kBarrierWaitNs, or a timeout raised
+// elsewhere, raises kFlagTimeout and ends the wait.  (Measured on GB300: one such
+// barrier over 304 blocks costs about what a kernel boundary inside a CUDA graph
+// does; a two-level form with 16 group counters was slower.)
+template <bool HOOK, typename F>
+__device__ TailState grid_barrier_impl(Ctrl* ctrl, int nb, TailSync& ss, F&& at_last) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ss.target += (unsigned)nb;
+        const unsigned target = ss.target + (HOOK ? 1u : 0u);
+        const unsigned prev = atom_add_acq_rel_gpu(ss.count, 1u);
+        ss.last = prev + 1u == ss.target;
+        if (ss.last && HOOK) {
+            ss.pre_flags = ld_volatile_int(&ctrl->flags);
+            ss.pre_accept = ld_volatile_int(&ctrl->ls_accept);
+        } else if (!ss.last) {
+            const long long t0 = tail_clock_ns();
+            unsigned polls = 0;
+            while ((int)(ld_acquire_gpu(ss.count) - target) < 0) {
+                if ((++polls & 63u) == 0u &&
+                    ((ld_volatile_int(&ctrl->flags) & kFlagTimeout) || tail_clock_ns() - t0 > kBarrierWaitNs)) {
+                    atomicOr(&ctrl->flags, kFlagTimeout);
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        if (HOOK) ss.target += 1u;
+    }
+    __syncthreads();
+    if (HOOK && ss.last) {
+        at_last(ss.pre_flags, ss.pre_accept);
+        __syncthreads();
+        if (threadIdx.x == 0) atom_add_acq_rel_gpu(ss.count, 1u);
+    }
+    if (threadIdx.x == 0) {
+        ss.flags = ld_volatile_int(&ctrl->flags);
+        ss.accept = ld_volatile_int(&ctrl->ls_accept);
+    }
+    __syncthreads();
+    return TailState{ss.flags, ss.accept};
+}
+
+template <typename F>
+__device__ __forceinline__ TailState grid_barrier(Ctrl* ctrl, int nb, TailSync& ss, F&& at_last) {
+    return grid_barrier_impl<true>(ctrl, nb, ss, at_last);
+}
+
+__device__ __forceinline__ TailState grid_barrier(Ctrl* ctrl, int nb, TailSync& ss) {
+    return grid_barrier_impl<false>(ctrl, nb, ss, [](int, int) {});
+}
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
+// Shared memory of the fused kernel: one phase at a time uses it.
+template <typename T, int M, bool OBS>
+constexpr size_t tail_smem_bytes() {
+    return cmax(cmax(sizeof(ScanSmem), sizeof(SortSmem)),
+                cmax(cmax(sizeof(double) * kWarps * 4, sizeof(FinSmem<M>)),
+                     OBS ? sizeof(double) * kWarps * M * 4 : sizeof(LsSmem<T, M>)));
+}
+
+// Steps of the tail, each over the whole grid of the launch that runs it.
+// 2. candidates and the gradient (ends with the objective partials written, one
+//    per block of this grid).
+template <typename T>
+__device__ TailState tail_candidates(const IterBufs<T>& b, TailSync& ss, unsigned char* smem) {
+    Ctrl* ctrl = b.ctrl;
+    const int bid = blockIdx.x, nb = gridDim.x;
+    const int p = b.p;
+    const int ntiles = (int)(((int64_t)p + kScanTile - 1) / kScanTile);
+    auto& scan_sm = *reinterpret_cast<ScanSmem*>(smem);
+    const Buckets<T>& bk = b.bk;
+    bucket_count_body(b.em, bk, ctrl, bid, nb);
+    TailState st = grid_barrier(ctrl, nb, ss);
+    if (!(st.flags & kFlagTimeout))
+        for (int t = bid; t < ntiles; t += nb) scan_reduce_tile(bk.cnt, p, st.flags, true, b.scan_part, t, scan_sm);
+    st = grid_barrier(ctrl, nb, ss);
+    if (!(st.flags & kFlagTimeout))
+        for (int t = bid; t < ntiles; t += nb)
+            scan_apply_tile(bk.cnt, bk.off, p, bk.cap, ctrl, st.flags, kFlagBucketOverflow, &ctrl->bucket_total,
+                            bk.uoff, bk.longlist, b.scan_part, -1, 0.0, t, ntiles, scan_sm);
+    st = grid_barrier(ctrl, nb, ss);
+    bucket_scatter_body(b.em, bk, ctrl, st.flags, bid, nb);
+    st = grid_barrier(ctrl, nb, ss);
+    bucket_sort_body(bk, p, ctrl, st.flags, bid, nb, *reinterpret_cast<SortSmem*>(smem));
+    st = grid_barrier(ctrl, nb, ss);
+    fill_w_body(b.S, b.ld, b.cur, b.rinfo, b.rdv, bk, ctrl, st.flags, bid, nb);
+    st = grid_barrier(ctrl, nb, ss);
+    gradient_body(p, bk, b.nblk, b.part_obj, ctrl, st.flags, bid, nb, *reinterpret_cast<double(*)[kWarps][4]>(smem));
+    return st;
+}
+
+// 4. the accepted iterate into CSR (count, scan with the stopping rule, write),
+//    entered with no flag raised and a step accepted.
+template <typename T>
+__device__ void tail_accept(const IterBufs<T>& b, TailSync& ss, unsigned char* smem, TailState st) {
+    Ctrl* ctrl = b.ctrl;
+    const int bid = blockIdx.x, nb = gridDim.x;
+    const int p = b.p;
+    const int ntiles = (int)(((int64_t)p + kScanTile - 1) / kScanTile);
+    auto& scan_sm = *reinterpret_cast<ScanSmem*>(smem);
+    compact_count_body(p, b.bk, b.cnt2, ctrl, st.flags, bid, nb);
+    st = grid_barrier(ctrl, nb, ss);
+    if (!(st.flags & kFlagTimeout))
+        for (int t = bid; t < ntiles; t += nb) scan_reduce_tile(b.cnt2, p, st.flags, false, b.scan_part, t, scan_sm);
+    st = grid_barrier(ctrl, nb, ss);
+    if (!(st.flags & kFlagTimeout))
+        for (int t = bid; t < ntiles; t += nb)
+            scan_apply_tile(b.cnt2, b.next.rp, p, 0x7fffffff, ctrl, st.flags, 0, nullptr, nullptr, nullptr,
+                            b.scan_part, b.csr_cap, b.eps, t, ntiles, scan_sm);
+    st = grid_barrier(ctrl, nb, ss);
+    compact_write_body(p, b.bk, b.next, b.csr_cap, ctrl, st.flags, bid, nb);
+}
+
+// The whole tail in one launch: candidates, gradient, every window (the last
+// block at a window's barrier reduces the partials and decides), accept.
+template <typename T, int M, bool OBS>
+__global__ void __launch_bounds__(kThreads, OBS ? 1 : 2)
+k_iter_tail(IterBufs<T> b) {
+    __shared__ __align__(16) unsigned char smem[tail_smem_bytes<T, M, OBS>()];
+    __shared__ TailSync ss;
+    tail_sync_init(ss, b.bar);
+    Ctrl* ctrl = b.ctrl;
+    const int bid = blockIdx.x, nb = gridDim.x;
+    TailState st = tail_candidates<T>(b, ss, smem);
+    st = grid_barrier(ctrl, nb, ss);
+    // 3. line-search windows until a step is accepted or a flag is raised
+    const LsDecide dec{b.part_obj, nb, b.nblk, b.max_halvings, 1.0, 0, 0};
+    while (st.flags == 0 && st.accept < 0) {
+        if constexpr (OBS) {
+            ls_eval_obs_body<M>(b.xt, b.ldx, b.n, b.p, b.bk, 1.0, b.nblk, b.part_ls, ctrl, st.flags, bid, nb,
+                                *reinterpret_cast<double(*)[kWarps][M][4]>(smem));
+        } else {
+            ls_eval_body<T, M>(b.S, b.ld, b.p, b.bk, b.nblk, b.part_ls, ctrl, st.flags, bid, nb,
+                               *reinterpret_cast<LsSmem<T, M>*>(smem));
+        }
+        st = grid_barrier(ctrl, nb, ss, [&](int f, int acc) {
+            if (f == 0 && acc < 0) ls_reduce_decide<M>(b.part_ls, nb, dec, ctrl, *reinterpret_cast<FinSmem<M>*>(smem));
+        });
+    }
+    if (st.flags != 0 || st.accept < 0) return;
+    tail_accept<T>(b, ss, smem, st);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
 template <typename T>
 void launch_iter_begin(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
-    k_iter_begin<T><<<64, 256, 0, s>>>(b.bk, b.p, b.ctrl, lc.use, lc.ls);
+    k_iter_begin<T><<<64, 256, 0, s>>>(b.bk, b.p, b.ctrl, lc.use, lc.ls, b.bar);
 }
 
 // Prefix of the folded tile sequence of the screening pass (seqoff, nc+1 entries)
@@ -2491,6 +2817,95 @@ void launch_accept(const IterBufs<T>& b, cudaStream_t s) {
     k_compact_write<T><<<b.nblk, kThreads, 0, s>>>(b.p, b.bk, b.next, b.csr_cap, b.ctrl);
 }
 
+// The fused tail's grid: resident blocks per SM (capped by the tuning's
+// ls_blocks_per_sm, as for the window kernel) x SMs, at most nblk (the stride of
+// the partial arrays).  0 if the kernel cannot be resident at all.
+template <typename T, int M, bool OBS>
+static int tail_grid_m(const IterBufs<T>& b) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_iter_tail<T, M, OBS>, kThreads, 0) != cudaSuccess)
+            v = 0;
+        per_sm = std::max(0, v);
+    }
+    if (per_sm < 1) return 0;
+    const int want = b.ls_blocks_per_sm > 0 ? std::min(b.ls_blocks_per_sm, per_sm) : per_sm;
+    return std::max(1, std::min(b.nblk, want * b.num_sms));
+}
+
+template <typename T, int M, bool OBS>
+static cudaError_t tail_m(const IterBufs<T>& b, cudaStream_t s) {
+    const int g = tail_grid_m<T, M, OBS>(b);
+    if (g < 1) return cudaErrorInvalidConfiguration;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_iter_tail<T, M, OBS>, b);
+}
+
+template <typename T, bool OBS>
+static cudaError_t tail_window(const IterBufs<T>& b, cudaStream_t s, int* grid) {
+    switch (window_m(b.ls_window)) {
+        case 1: return grid ? (*grid = tail_grid_m<T, 1, OBS>(b), cudaSuccess) : tail_m<T, 1, OBS>(b, s);
+        case 2: return grid ? (*grid = tail_grid_m<T, 2, OBS>(b), cudaSuccess) : tail_m<T, 2, OBS>(b, s);
+        case 4: return grid ? (*grid = tail_grid_m<T, 4, OBS>(b), cudaSuccess) : tail_m<T, 4, OBS>(b, s);
+        case 8: return grid ? (*grid = tail_grid_m<T, 8, OBS>(b), cudaSuccess) : tail_m<T, 8, OBS>(b, s);
+        default: return grid ? (*grid = tail_grid_m<T, 16, OBS>(b), cudaSuccess) : tail_m<T, 16, OBS>(b, s);
+    }
+}
+
+template <typename T>
+static cudaError_t tail_dispatch(const IterBufs<T>& b, bool obs, cudaStream_t s, int* grid) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (obs) return tail_window<float, true>(b, s, grid);
+    } else {
+        if (obs) return cudaErrorInvalidValue;
+    }
+    return tail_window<T, false>(b, s, grid);
+}
+
+template <typename T>
+cudaError_t launch_tail(const IterBufs<T>& b, bool obs, cudaStream_t s) {
+    return tail_dispatch<T>(b, obs, s, nullptr);
+}
+
+template <typename T>
+int tail_grid(const IterBufs<T>& b, bool obs) {
+    int g = 0;
+    return tail_dispatch<T>(b, obs, nullptr, &g) == cudaSuccess ? g : 0;
+}
+
+// A cooperative launch of one block that counts itself and, inside a graph,
+// ends its conditional loop: the device-loop capture checks with it once that
+// cooperative kernels can run in a conditional node's body.
+__global__ void k_tail_probe(int* out, int use_cond, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x == 0) {
+        atomicAdd(out, 1);
+        if (use_cond) cudaGraphSetConditional(cond, 0u);
+    }
+}
+
+cudaError_t launch_tail_probe(int* out, cudaGraphConditionalHandle cond, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tail_probe, out, 1, cond);
+}
+
 template <typename T>
 void launch_commit(const IterBufs<T>& b, const LoopCond& lc, cudaStream_t s) {
     k_csr_commit<T><<<b.num_sms * 2, 256, 0, s>>>(b.next, b.cur, b.p, b.ctrl, lc.use, lc.iter);
@@ -2618,6 +3033,8 @@ void launch_gather_s(const void* S, int is_f64, int64_t ld, int64_t m, const int
     template void launch_candidates<T>(const IterBufs<T>&, cudaStream_t);                          \
     template void launch_ls_window<T>(const IterBufs<T>&, const LoopCond&, cudaStream_t);          \
     template void launch_accept<T>(const IterBufs<T>&, cudaStream_t);                              \
+    template cudaError_t launch_tail<T>(const IterBufs<T>&, bool, cudaStream_t);                     \
+    template int tail_grid<T>(const IterBufs<T>&, bool);                                             \
     template void launch_set_identity<T>(Csr<T>, int, cudaStream_t);                               \
     template void launch_row_info<T>(int, Csr<T>, int4*, T*, cudaStream_t);                        \
     template void launch_rowblock_max<T>(const T*, int64_t, int, int, unsigned short*, cudaStream_t); \

@@ -54,7 +54,7 @@ def test_struct_layouts_match_the_header(lib):
     """ctypes mirrors of the header's structs: sizes from the header's field list."""
     assert ctypes.sizeof(lib.Options) == 64
     assert ctypes.sizeof(lib.Stats) == 13 * 8 + 2 * 4 + 8
-    assert ctypes.sizeof(lib.Tuning) == 36
+    assert ctypes.sizeof(lib.Tuning) == 40
     assert ctypes.sizeof(lib.TuneReport) == 8 + lib.TUNE_MAX_TRIALS * 16
 
 

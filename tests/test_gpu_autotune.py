@@ -26,10 +26,11 @@ def test_autotune_picks_valid_shapes_and_keeps_results(lib):
         best, trials = s.autotune(X, iters=2)
         knobs = {t["knob"] for t in trials}
         assert {"gram_band", "gram_maxima", "gram_schedule", "ls_window", "rows_ctas_per_sm",
-                "ls_blocks_per_sm"} <= knobs
+                "ls_blocks_per_sm", "fused_tail"} <= knobs
         assert all(t["ms"] > 0 for t in trials)
         assert s.get_tuning() == best
         assert best["ls_window"] in (2, 4, 8, 16) and 1 <= best["rows_ctas_per_sm"] <= 4
+        assert best["fused_tail"] in (0, 1)
         st = s.solve().as_dict()
         om = s.omega_dense()
     assert np.array_equal(om, om_ref)
@@ -42,6 +43,8 @@ def test_autotune_picks_valid_shapes_and_keeps_results(lib):
     dict(rows_ctas_per_sm=4, ls_blocks_per_sm=0, ls_window=16, gram_band=2, gram_maxima=0),
     dict(gram_schedule=0, gram_band=16),                           # static tile order
     dict(gram_schedule=1, gram_band=4),
+    dict(fused_tail=1, ls_window=4),                               # the one-launch tail
+    dict(fused_tail=1, ls_blocks_per_sm=1, ls_window=16),
 ])
 def test_launch_shapes_give_the_default_iterates(lib, shape):
     """Every form the knobs select reaches the default shapes' estimate, iteration for
@@ -78,6 +81,7 @@ def test_autotune_restores_the_iterate(lib):
 
 @pytest.mark.parametrize("bad", [dict(gram_band=0), dict(ls_window=3), dict(rows_ctas_per_sm=5),
                                  dict(ls_blocks_per_sm=-1), dict(gram_maxima=2), dict(screen_bounds=2),
+                                 dict(fused_tail=2),
                                  dict(gram_schedule=3)])
 def test_set_tuning_rejects_out_of_range(lib, bad):
     torch = _torch()
