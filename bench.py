@@ -709,7 +709,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bf16_p65536")
     ap.add_argument("--precision", default="auto", choices=["auto", "fp32", "bf16x3", "tf32"])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-sample-p", type=int, default=2048)

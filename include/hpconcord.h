@@ -472,9 +472,13 @@ typedef struct {
                                   take the same time to within a few percent (a
                                   barrier costs about a kernel boundary inside the
                                   solve's CUDA graph); the chain is faster where the
-                                  candidate structure is large.  hpc_solve_batch
-                                  runs its problems' iterations concurrently,
-                                  always on the chain (0)                           */
+                                  candidate structure is large, and where other
+                                  streams run kernels during the solve (a cooperative
+                                  kernel waits until its whole grid is resident: it
+                                  queues behind hpc_prefetch_x's transpose).  Not
+                                  touched by the autotuner.  hpc_solve_batch runs its
+                                  problems' iterations concurrently, always on the
+                                  chain (0)                                         */
 } hpc_tuning;
 
 /* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max
@@ -492,8 +496,7 @@ int hpc_set_tuning(hpc_handle h, const hpc_tuning* t);
 #define HPC_TUNE_MAX_TRIALS 48
 typedef struct {
     int32_t knob;              /* 0 gram_band, 1 ls_window, 2 ls_blocks_per_sm,
-                                  3 rows_ctas_per_sm, 4 gram_maxima, 5 gram_schedule,
-                                  6 fused_tail */
+                                  3 rows_ctas_per_sm, 4 gram_maxima, 5 gram_schedule */
     int32_t value;
     double  ms;                /* Gram knobs: one data load (transpose, product, block
                                   maxima); the others: one iteration                */
@@ -511,8 +514,8 @@ typedef struct {
  *    each gram_band candidate, then for gram_maxima 1 and 0: three round-robin
  *    rounds over the candidates, each keeping its fastest load (the SM clock
  *    drifts under the power cap).  S is rewritten with identical values.
- *  - The iteration knobs (ls_window, rows_ctas_per_sm, ls_blocks_per_sm, then
- *    fused_tail) are timed over `iters` outer iterations (>= 1) each,
+ *  - The iteration knobs (ls_window, rows_ctas_per_sm, ls_blocks_per_sm) are
+ *    timed over `iters` outer iterations (>= 1) each,
  *    every trial starting from the handle's current iterate, which is restored
  *    afterwards: the call leaves the estimate unchanged.  Start from a
  *    representative iterate (for example after a few hpc_iterate calls) for

@@ -82,8 +82,7 @@ class Tuning(C.Structure):
 
 
 TUNE_MAX_TRIALS = 48
-TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm", "gram_maxima", "gram_schedule",
-              "fused_tail")
+TUNE_KNOBS = ("gram_band", "ls_window", "ls_blocks_per_sm", "rows_ctas_per_sm", "gram_maxima", "gram_schedule")
 
 
 class TuneTrial(C.Structure):

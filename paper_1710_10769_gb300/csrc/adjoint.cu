@@ -190,6 +190,20 @@ template <> struct Vec16<double> {
     static __device__ __forceinline__ void unpack(const double2& u, double* v) { v[0] = u.x; v[1] = u.y; }
 };
 
+// Row and column block (bi <= bj) of the t-th tile pair, pairs numbered row by row
+// (row bi holds nt - bi pairs): bi from the quadratic's root in FP32, then corrected
+// by exact integer steps.
+__device__ __forceinline__ void pair_of(long long t, int nt, int& bi, int& bj) {
+    const float b2 = 2.0f * (float)nt + 1.0f;
+    int r = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.0f * (float)t, 0.0f))) * 0.5f);
+    r = max(0, min(r, nt - 1));
+    auto start = [&](long long q) { return q * nt - q * (q - 1) / 2; };
+    while (r > 0 && start(r) > t) --r;
+    while (r + 1 < nt && start(r + 1) <= t) ++r;
+    bi = r;
+    bj = r + (int)(t - start(r));
+}
+
 // dL/dOmega = scale ((W + W^T)/2 + lambda2 Omega - diag(1/w_ii)), W = Omega S, on one pair
 // of TL x TL tiles (I <= J) per CTA, so G is written once and never re-read:
 //  1. the tile S[I, J] is read once; it gives the diagonal terms of both W[I, J]
@@ -201,7 +215,7 @@ template <> struct Vec16<double> {
 // The rounding sequence per element is the solver's (W in the canonical order,
 // 0.5 (W_ij + W_ji), the support terms, the scale).
 template <typename T, int TL>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 3)
 k_dense_grad_pair(int p, Csr<T> om, const int4* __restrict__ rinfo, const T* __restrict__ rdv,
                   const T* __restrict__ S, int64_t lds, T* __restrict__ G, int64_t ldg, T lam2, T scale, int nt,
                   int vec /* bit 0: 16-byte G stores; bit 1: 16-byte S loads */) {
@@ -211,9 +225,8 @@ k_dense_grad_pair(int p, Csr<T> om, const int4* __restrict__ rinfo, const T* __r
     __shared__ int imp[2][TL];       // rows of I and of J with off-diagonal entries
     __shared__ int nimp[2];
     constexpr int E = TL * TL / 256;
-    int t = blockIdx.x, bi = 0;
-    while (t >= nt - bi) { t -= nt - bi; ++bi; }
-    const int bj = bi + t;
+    int bi, bj;
+    pair_of(blockIdx.x, nt, bi, bj);
     const int I0 = bi * TL, J0 = bj * TL;
     const bool dtile = bi == bj;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

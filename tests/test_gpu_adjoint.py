@@ -77,6 +77,35 @@ def test_backward_domega_is_the_solvers_gradient_bitwise(lib):
     s.close()
 
 
+@pytest.mark.parametrize("f64", [False, True])
+def test_backward_domega_several_tile_pairs_per_cta(lib, f64):
+    """p = 2600: more tile pairs than resident CTAs, so each CTA takes several and loads
+    the next pair's S tile while it finishes the current one; the last tile is ragged
+    (2600 = 40 x 64 + 40).  dL/dOmega against the FP64 oracle, and bitwise against the
+    solver's own G on its candidates."""
+    import torch
+
+    rng = np.random.default_rng(47)
+    X = rng.standard_normal((1200, 2600))
+    if not f64:
+        X = X.astype(np.float32)
+    lam1, lam2 = 0.15, 0.1
+    Xt = torch.as_tensor(X).cuda()
+    opt = dict(value_dtype=lib.F64, precision=lib.PREC_FP64) if f64 else dict(precision=lib.PREC_FP32)
+    s = lib.Solver(Xt, lam1, lam2, eps=1e-4, max_iter=20000, **opt)
+    s.solve()
+    Om = s.omega_dense()
+    dO, _ = s.backward(Xt, dx=False)
+    dO = dO.double().cpu().numpy()
+    rO, _ = oracle.smooth_loss_grads(X.astype(np.float64), Om, lam2)
+    assert np.max(np.abs(dO - rO)) <= (1e-12 if f64 else REL) * np.max(np.abs(rO))
+    assert np.array_equal(dO, dO.T)
+    s.iterate(1)                       # its gradient pass runs at the estimate backward used
+    r, c, _, g = s.candidates()
+    assert np.array_equal(dO[r, c], g)
+    s.close()
+
+
 def test_smooth_value_matches_oracle(lib):
     X = small_problem(200, 150, 3.0, 43).astype(np.float32)
     s, Xt = _solved(lib, X, 0.1, 0.1)
