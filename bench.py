@@ -250,6 +250,8 @@ def run_row(args):
         lam = sorted(PATH_LAMBDA1, reverse=True)
         X = make_x(w, device="cuda")
         s = hpc.Solver(X, lam[0], PATH_LAMBDA2, eps=w.eps, max_iter=100000, device_loop=args.device_loop)
+        if args.fused_tail is not None:
+            s.set_tuning(fused_tail=args.fused_tail)
         for _ in range(args.warmup):
             s.load_x(X)
             s.solve_path(lam, PATH_LAMBDA2, return_estimates=False)
@@ -267,10 +269,14 @@ def run_row(args):
                 it_ms += sum(q["ms"] for q in pts)
         p = w.p
         t_it = it_ms / its / 1000.0
-        alg = 4.0 * p * p / t_it / 1e9
-        roof = {"kernel": "path iteration", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
-                "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
-                "note": "algorithmic 4p^2 bytes per iteration / measured iteration time"}
+        # An iteration is a chain of dependent, latency-bound steps (bound screening
+        # reads a few MB of S; the candidate, line-search and accept steps touch the
+        # candidate structure only): no bandwidth or tensor roofline bounds it.  For
+        # scale, the time one full read of S would take at the copy figure.
+        roof = {"kernel": "path iteration (screening, candidates, line search, accept)",
+                "bound": "latency (dependent steps)", "iteration_us": t_it * 1e6,
+                "full_S_read_us_at_peak": 4.0 * p * p / (hbm * 1e9) * 1e6, "peak_source": peak_src,
+                "per_kernel": "profiles/path_p8192_launches.md"}
         cpu = None
         if not args.no_cpu:
             # the oracle: warm-started path on the leading 1024 x 1024 sub-problem, first points
@@ -291,7 +297,7 @@ def run_row(args):
         _line("lambda1 path iters/s, 32 points on p=8192 n=4096 (ms_per_step = load + whole path)", its / (ms / 1000),
               "iters/s", ms / args.steps, args, True, "f32",
               {"workload": "path_p8192", "p": p, "n": w.n, "points": len(lam), "lambda2": PATH_LAMBDA2,
-               "gram_precision": s.precision_name(),
+               "gram_precision": s.precision_name(), "fused_tail": int(s.get_tuning()["fused_tail"]),
                "loop": "one graph launch per path" if args.device_loop else "host-driven"},
               roof, clk.summary(), None, cpu, iterations_per_step=its // args.steps,
               iteration_ms=t_it * 1000)
@@ -515,9 +521,13 @@ def run_row(args):
                     per = [q["iterations"] for q in st]
         byt = sum(4.0 * wk.p * wk.p * it for wk, it in zip(BATCH_PROBLEMS, per)) * args.steps
         alg = byt / (ms / 1000) / 1e9
-        roof = {"kernel": "batched solves", "bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
-                "frac": alg / hbm, "traffic": None, "peak_source": peak_src,
-                "note": "algorithmic 4p^2 bytes per iteration of every problem / batch time"}
+        # the problems' iterations run concurrently and are latency-bound (as in the
+        # path); the rate at which one full read of S per iteration of every problem
+        # would have to stream is given for scale only
+        roof = {"kernel": "batched solves (concurrent iteration loops)", "bound": "latency (dependent steps)",
+                "full_S_reads_equivalent_gbs": alg, "peak": hbm, "peak_source": peak_src,
+                "note": "bound screening reads about 1% of each S per iteration, so this equivalent can exceed "
+                        "the copy figure"}
         cpu = None
         if not args.no_cpu:
             # the oracle: full solves of the two smallest problems; seconds per iteration
