@@ -108,3 +108,25 @@ def test_fused_tail_obs_matches_oracle(lib):
         ok, detail = support_diff_ok(om, ref.omega, 0.15, 0.1, X=X)
         assert ok, detail
     assert fused[1]["kernel_launches"] < chain[1]["kernel_launches"]
+
+
+def test_fused_tail_path_matches_chain(lib):
+    """The lambda1 path in one graph launch (each point's iteration loop with the fused
+    tail in its body) gives the chain's points: same iterations, trials and estimates."""
+    import torch
+
+    p, n, lam2 = 320, 220, 0.1
+    X = small_problem(p, n, 4.0, 31).astype(np.float32)
+    grid = np.logspace(np.log10(0.4), np.log10(0.08), 6)
+    out = []
+    for form in (1, 0):
+        with lib.Solver(torch.as_tensor(X).cuda(), grid[0], lam2, precision=lib.PREC_FP32, eps=1e-7,
+                        max_iter=20000) as s:
+            s.set_tuning(fused_tail=form, ls_blocks_per_sm=2)
+            out.append(s.solve_path(grid, lam2))
+    (pf, ef), (pc, ec) = out
+    for t in range(len(grid)):
+        for key in ("status", "iterations", "ls_trials", "nnz"):
+            assert pf[t][key] == pc[t][key], (t, key)
+        assert np.array_equal(ef[t].row_ptr, ec[t].row_ptr) and np.array_equal(ef[t].col, ec[t].col)
+        assert np.array_equal(ef[t].val, ec[t].val)
