@@ -52,7 +52,6 @@ struct Ctrl {
     int ls_done;                  // blocks of the running line-search launch that wrote their partials
     int n_long, pad4_;            // rows of the candidate structure with more than kShortRow entries
     int n_pairs, n_row_items;     // items the bound screening keeps (pure rows; rows with neighbours)
-    int pad5_, pad6_;
 };
 
 // Rows with at most this many candidate entries (before de-dup) are handled one
