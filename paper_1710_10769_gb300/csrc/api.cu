@@ -605,14 +605,6 @@ void capture_window(hpc_ctx* h, const hpc::IterBufs<T>& b, const hpc::LoopCond& 
     hpc::launch_ls_window<T>(b, lc, cs);
 }
 
-// Capture the device loop:
-//   WHILE (iteration condition) {
-//       begin, [stamp], screening pass, [stamp], candidates, gradient
-//       WHILE (line-search condition) { window evaluation, decision }
-//       compaction, stopping rule, commit of the accepted iterate
-//   }
-// k_iter_begin arms the line-search loop, the last block of k_ls_eval ends it, and the commit
-// kernel continues or ends the iteration loop.
 // Capture the iteration loop as a WHILE node of graph g (after dep, if any) on
 // the handle lc.iter, which the caller created for g:
 //   WHILE (iteration condition) {

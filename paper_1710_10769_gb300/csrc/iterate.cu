@@ -23,6 +23,11 @@
 //                     gathers of S on the candidate pattern and FP64 sums.
 //  4. accept          compaction of the accepted Omega+ into CSR (ballot/popc row
 //                     counts, scan, ordered write) and the stopping rule.
+//
+// Steps 2-4 are device functions over a grid of blocks.  They run either as a
+// chain of kernels of their own or, all of them, as one cooperative kernel
+// (k_iter_tail, section 5) with grid-wide barriers between them; both forms give
+// the same entries and decisions.
 #include <algorithm>
 #include <type_traits>
 #include <cstdio>
