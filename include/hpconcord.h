@@ -476,9 +476,10 @@ typedef struct {
                                   streams run kernels during the solve (a cooperative
                                   kernel waits until its whole grid is resident: it
                                   queues behind hpc_prefetch_x's transpose).  Not
-                                  touched by the autotuner.  hpc_solve_batch runs its
-                                  problems' iterations concurrently, always on the
-                                  chain (0)                                         */
+                                  touched by the autotuner.  hpc_solve_batch's single
+                                  graph launch runs its problems' loops concurrently,
+                                  always on the chain; handles solved from its worker
+                                  threads keep their own setting (0)               */
 } hpc_tuning;
 
 /* The bound screening's block maxima of the Cov variant: out[i * nb + jb] = max

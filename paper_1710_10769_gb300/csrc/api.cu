@@ -539,7 +539,9 @@ int add_while(cudaGraph_t g, const cudaGraphNode_t* dep, cudaGraphConditionalHan
 // Whether a cooperative kernel runs inside a conditional WHILE node's body on the
 // current device: checked once per device, before any capture, by a graph whose
 // loop body is one cooperative launch of a one-block kernel that ends the loop.
-bool tail_in_graph_supported() {
+// The kernel counts its runs in word 1 of the handle's barrier buffer (word 0 is
+// the fused tail's arrival counter), so the check allocates no device memory.
+bool tail_in_graph_supported(const hpc_ctx* h) {
     static std::mutex mu;
     static int state[64] = {};     // 0 unknown, 1 supported, 2 not
     int dev = 0;
@@ -547,13 +549,12 @@ bool tail_in_graph_supported() {
     std::lock_guard<std::mutex> lock(mu);
     if (state[dev]) return state[dev] == 1;
     bool ok = false;
-    int* d = nullptr;
+    int* d = h && h->bar ? reinterpret_cast<int*>(h->bar + 1) : nullptr;
     cudaStream_t s = nullptr;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     int coop = 0;
-    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-        cudaMalloc(&d, sizeof(int)) == cudaSuccess &&
+    if (d && cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
         cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
         cudaMemsetAsync(d, 0, sizeof(int), s) == cudaSuccess && cudaGraphCreate(&g, 0) == cudaSuccess) {
         cudaGraphConditionalHandle hnd;
@@ -577,7 +578,7 @@ bool tail_in_graph_supported() {
     if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);
     if (s) cudaStreamDestroy(s);
-    if (d) cudaFree(d);
+    if (!d) return false;       // no handle buffer to check with: decide at the next call
     state[dev] = ok ? 1 : 2;
     return ok;
 }
@@ -586,7 +587,7 @@ bool tail_in_graph_supported() {
 // the one cooperative kernel) where the device runs cooperative kernels in graph
 // loops, else the chain (the host-driven loop needs only the cooperative launch
 // itself, which the same check covers).
-int tail_mode(const hpc_ctx* h) { return h->tune.fused_tail != 0 && tail_in_graph_supported() ? h->tune.fused_tail : 0; }
+int tail_mode(const hpc_ctx* h) { return h->tune.fused_tail != 0 && tail_in_graph_supported(h) ? h->tune.fused_tail : 0; }
 
 template <typename T>
 int capture_screen(hpc_ctx* h, const hpc::IterBufs<T>& b, cudaStream_t cs) {

@@ -200,10 +200,11 @@ constexpr int kLaunchesBegin = 1;
 constexpr int kLaunchesCandidates = 7;
 constexpr int kLaunchesLsWindow = 1;     // k_ls_eval (its last block decides)
 constexpr int kLaunchesAccept = 4;
-constexpr int kLaunchesTail = 1;
-// Words of the fused tail's barrier buffer: the arrival counter on a 128-byte line
-// of its own (k_iter_begin zeroes it).
-constexpr int kBarWords = 32;         // k_iter_tail: candidates, gradient, every window, accept
+constexpr int kLaunchesTail = 1;         // k_iter_tail: candidates, gradient, every window, accept
+// Words of the fused tail's barrier buffer, one 128-byte line: word 0 the arrival
+// counter (k_iter_begin zeroes it), word 1 the count of the one-time check that
+// cooperative kernels run in graph loops.
+constexpr int kBarWords = 32;
 
 // The fused iteration tail (candidates, gradient, line-search windows with their
 // decisions, compaction and stopping rule) as one cooperative launch.  obs selects
